@@ -81,10 +81,21 @@ static void A_of_q(const double *q, double A[9]) { /* A(r,c) = q[3c+r] */
     for (int c = 0; c < 3; ++c) A[3 * r + c] = q[3 * c + r];
 }
 
-/* x(p) = A p + t = J(p) q  (Eq. abd_dof) */
-static void point_of(const double *q, const double p[3], double x[3]) {
-  for (int a = 0; a < 3; ++a)
-    x[a] = q[a] * p[0] + q[3 + a] * p[1] + q[6 + a] * p[2] + q[9 + a];
+/* x_alpha(pa) - x_beta(pb) with x(p) = A p + t (Eq. abd_dof, Eq. ball), grouped as (A_a pa - A_b pb) + (t_a - t_b)
+   so that assemblies far from the origin keep the gap to round-off of the
+   body size rather than of the absolute coordinates; qb == NULL: pb is a
+   world point. */
+static void gap_of(const double *qa, const double pa[3], const double *qb, const double pb[3],
+                   double d[3]) {
+  for (int a = 0; a < 3; ++a) {
+    double la = qa[a] * pa[0] + qa[3 + a] * pa[1] + qa[6 + a] * pa[2];
+    if (qb) {
+      double lb = qb[a] * pb[0] + qb[3 + a] * pb[1] + qb[6 + a] * pb[2];
+      d[a] = (la - lb) + (qa[9 + a] - qb[9 + a]);
+    } else {
+      d[a] = la + (qa[9 + a] - pb[a]);
+    }
+  }
 }
 
 static void normalize3(const double a[3], double b[3]) {
@@ -292,16 +303,12 @@ int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
     pb[0][i] = sc->anchor_b[3 * k + i];
   }
   const double *qa = q + 12 * ja;
-  double xa[3], xb[3];
   if (C == 3) {
     for (int r = 0; r < 3; ++r) {
       pt[r] = 0;
       for (int a = 0; a < 3; ++a) dir[r][a] = (r == a) ? 1.0 : 0.0;
     }
-    point_of(qa, pa[0], xa);
-    if (jb == ORA_WORLD) memcpy(xb, pb[0], sizeof(xb));
-    else point_of(q + 12 * jb, pb[0], xb);
-    for (int a = 0; a < 3; ++a) c[a] = xa[a] - xb[a];
+    gap_of(qa, pa[0], jb == ORA_WORLD ? NULL : q + 12 * jb, pb[0], c);
   } else {
     double ua[3], ub[3], A[9], R[9], a[3], ra[3], RH[9];
     normalize3(sc->axis_a + 3 * k, ua);
@@ -320,14 +327,9 @@ int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
     if (a[1] < 0.0) { a[0] = -a[0]; a[1] = -a[1]; a[2] = -a[2]; }
     ora_hinge_frame(a, RH);
     double d1[3], d2[3], e1[3], e2[3];
-    point_of(qa, pa[0], xa);
-    if (jb == ORA_WORLD) memcpy(xb, pb[0], sizeof(xb));
-    else point_of(q + 12 * jb, pb[0], xb);
-    for (int i = 0; i < 3; ++i) d1[i] = xa[i] - xb[i];
-    point_of(qa, pa[1], xa);
-    if (jb == ORA_WORLD) memcpy(xb, pb[1], sizeof(xb));
-    else point_of(q + 12 * jb, pb[1], xb);
-    for (int i = 0; i < 3; ++i) d2[i] = xa[i] - xb[i];
+    const double *qb = jb == ORA_WORLD ? NULL : q + 12 * jb;
+    gap_of(qa, pa[0], qb, pb[0], d1);
+    gap_of(qa, pa[1], qb, pb[1], d2);
     mv3(RH, d1, e1);
     mv3(RH, d2, e2);
     c[0] = e1[0]; c[1] = e1[1]; c[2] = e1[2];
