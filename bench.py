@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Throughput of the M-ABD step on GB300: body-steps/s on the 1,048,576-body
+pulley-cable chain (alternating ball / hinge joints, both ends pinned,
+h = 1e-2 s, FP64), one implicit step with one Newton iteration per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One process per GPU; with N > 1 (torchrun) every rank steps its own
+independent copy of the chain (replicas: the method's step has no exchange
+between independent assemblies) and rank 0 prints one JSON line whose value
+is the sum over ranks.  ``--impl reference`` times the CPU FP64 oracle on the
+host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "body-steps/s at ≤1e-6 rel err vs FP64 oracle; chosen form vs plain GPU path"
+M_FULL = 1 << 20
+H = 1e-2
+
+
+def workload_config(M: int, K: int, rows: int) -> dict:
+    return {
+        "workload": "pulley-cable chain: %d boxes (sides U[0.5,1.5], rho 10^U[2,4]), %d joints "
+                    "(ball/hinge alternating, both ends pinned), %d dual rows, h=1e-2 s, seed 1"
+                    % (M, K, rows),
+        "bodies": M, "joints": K, "dual_rows": rows, "h": H, "form": "fp64",
+        "solver": "block cyclic reduction (chain)",
+        "l2": "inputs larger than L2 (state alone 192 MB; working set ~1.5 GB), no flush",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def lscpu_model() -> str:
+    try:
+        out = subprocess.check_output(["lscpu"], text=True)
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "mabd_clocks_%d_%d.csv" % (os.getpid(), device_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic work of the dominant kernels (FP64 flops, FMA = 2)
+# --------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 peak of GB300 from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM
+# x 2 flop x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def kernel_model(name: str, M: int, K: int, nh: int):
+    """(bytes, flops) the method must move / compute in one launch of `name`
+    (all levels for the cyclic-reduction kernels are summed by the caller)."""
+    if name == "chain_gram":
+        # per body: R (72 B) + hinv (128 B) + joint rows (RH 72 B x2 + points) in, D/B out
+        return M * (72 + 128 + 2 * 72 + 96 + 8 * (15 + 15 + 25)), M * 2 * 520
+    if name == "body_prep":
+        return M * (24 * 8 + 16 * 8 + 6 * 8 + (9 + 12) * 8), M * 2 * 330
+    return None, None
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2603_08079_gb300 import mabd, scenes
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    M = args.bodies
+    sc = scenes.long_chain(M, seed=1)
+    solver = mabd.Solver(sc)
+    info = solver.info()
+    stream = solver.stream
+
+    def barrier_sync():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    solver.step(args.warmup)
+    solver.synchronize()
+    barrier_sync()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    barrier_sync()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    solver.synchronize()  # surfaces any device-side failure of the timed steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * M * args.steps / (ms_max / 1e3)
+
+    # per-kernel times with CUDA events on the library's stream (separate pass)
+    solver.profile(True)
+    solver.profile_reset()
+    solver.step(args.profile_steps)
+    kt = solver.kernel_times()
+    solver.profile(False)
+    launches_per_step = sum(n for _, n in kt.values()) / args.profile_steps
+
+    # end to end through the C ABI with host buffers: H2D state, step, D2H state
+    q_h = torch.empty((M, 12), dtype=torch.float64).pin_memory().numpy()
+    qd_h = torch.empty((M, 12), dtype=torch.float64).pin_memory().numpy()
+    solver.get_state(q_h, qd_h)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier_sync()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_state(q_h, qd_h)
+        solver.step(1)
+        solver.get_state(q_h, qd_h)
+    barrier_sync()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = ws * M * e2e_steps / e2e_s
+
+    # accuracy of this form against the oracle is checked by the test-suite
+    # (tests/test_gpu_chain.py::test_full_size_pulley_chain); here the joint
+    # residual of one step is reported
+    st = solver.step(1, stats=True)[0]
+    solver.close()
+
+    result = None
+    if rank == 0:
+        peaks, src = measured_peaks()
+        dom = max(kt.items(), key=lambda kv: kv[1][0])
+        dname, (dms, dn) = dom
+        per_launch_ms = dms / dn
+        nh = M // 2
+        byts, flops = kernel_model(dname, M, info["joints"], nh)
+        if flops is not None:
+            achieved = flops / (per_launch_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                    "traffic": None, "kernel": dname, "peak_source": "FP64 unit counts x 2.07 GHz",
+                    "kernel_ms_per_launch": round(per_launch_ms, 4),
+                    "algorithmic_bytes_per_launch": byts,
+                    "hbm_frac_of_measured": round(byts / (per_launch_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)}
+        else:
+            roof = {"bound": "alu", "achieved": None, "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": dname}
+        result = {
+            "metric": METRIC, "value": value, "unit": "body-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator, paper-shaped chain)",
+            "config": workload_config(M, info["joints"], info["dual_rows"]),
+            "e2e": {"value": e2e_value, "unit": "body-steps/s",
+                    "h2d_bytes_per_step": 2 * 12 * 8 * M, "d2h_bytes_per_step": 2 * 12 * 8 * M},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "roofline": roof,
+            "kernels_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in kt.items()},
+            "joint_residual": st["joint_residual"],
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(args)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def cpu_baseline(args, steps: int = 1, M: int | None = None) -> dict:
+    """The CPU FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle as ora
+    from paper_2603_08079_gb300 import scenes
+
+    M = M or args.cpu_bodies
+    sc = scenes.long_chain(M, seed=1)
+    S = ora.Scene(sc)
+    q, qd = sc["q"], sc["qdot"]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        q, qd, _, _ = ora.step(S, q, qd)
+    dt = time.perf_counter() - t0
+    return {"value": M * steps / dt, "unit": "body-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d step(s) of the %d-body pulley chain (same generator, seed 1), "
+                      "single thread, %s" % (steps, M, lscpu_model()),
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    """CPU oracle arm: W untimed + K timed oracle steps, each on a bounded
+    sample of the chain, on the host cores (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle as ora
+    from paper_2603_08079_gb300 import scenes
+
+    M = args.cpu_bodies
+    sc = scenes.long_chain(M, seed=1)
+    S = ora.Scene(sc)
+    q, qd = sc["q"], sc["qdot"]
+    for _ in range(args.warmup):
+        q, qd, _, _ = ora.step(S, q, qd)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q, qd, _, _ = ora.step(S, q, qd)
+    dt = time.perf_counter() - t0
+    value = M * args.steps / dt
+    cfg = workload_config(M_FULL, M_FULL + 1, 4194305)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "body-steps/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator, paper-shaped chain)",
+        "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "body-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: the first %d bodies of the chain generator (seed 1), "
+                                   "single thread, %s" % (M, lscpu_model())},
+        "e2e": {"value": value, "unit": "body-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--bodies", type=int, default=M_FULL)
+    ap.add_argument("--cpu-bodies", type=int, default=M_FULL // 4)
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "own":
+        args.warmup = 3
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * mabd.h -- C ABI of the GB300 (sm_103a) multi-affine-body step library.
+ *
+ * One call of mabd_step advances M affine bodies joined by K joints by one
+ * implicit-Euler step with one Newton iteration, as M-ABD (arXiv 2603.08079)
+ * defines it:
+ *   Sec. 3.3-3.4, Eq. polar / abd_final: co-rotated per-body update with a
+ *       constant prefactored Hbar_A = M_A/h^2 + Kbar_A per body;
+ *   Sec. 4.2-4.3, Eq. ball / hinge, Sec. 5.1 Eq. pcpq: joint constraint
+ *       Jacobians in affine coordinates (hinge frame frozen at q_n);
+ *   Sec. 5, Eq. kkt / dual: the KKT system projected into the dual space of
+ *       the joint rows, S lambda = G H^{-1} f + C(q_n) with S = G H^{-1} G^T
+ *       (the bottom rhs -C(q_n) of the Sec. 5 footnote is included unless
+ *       residual_rhs = 0), solved by block cyclic reduction for chains
+ *       (Sec. 5.2 Eq. chain-btd), level-scheduled body-space elimination for
+ *       trees (Sec. 5.3 Alg. 2 / Eq. module3-kkt) and block-Jacobi
+ *       preconditioned conjugate gradients otherwise (Sec. 5.5);
+ *   Sec. 5.2 Eq. recover-dq-explicit: back-propagation
+ *       dq_j = H_j^{-1}(f_j - sum_k G_kj^T lambda_k), then
+ *       q_{n+1} = q_n + dq and qdot_{n+1} = dq / h.
+ *
+ * Conventions
+ *   Affine coordinates q = [vec(A); t] (12 doubles) with vec stacking the
+ *   three columns of A (Eq. abd_dof): A(r,c) = q[3c+r].  A body's rest frame
+ *   has its origin at the centre of mass and its axes along the principal
+ *   axes, so second_moment must be diagonal (off-diagonal entries at most
+ *   1e-12 of the trace; otherwise mabd_add_bodies returns
+ *   MABD_ERR_UNSUPPORTED).
+ *   Ownership: every host array passed in belongs to the caller; the library
+ *   copies what it needs during the call and keeps no pointer.  All device
+ *   memory belongs to the context (through dev_alloc/dev_free when given,
+ *   else cudaMalloc/cudaFree) and is released by mabd_destroy.
+ *   Ordering: all device work is ordered on cfg.stream (NULL = the legacy
+ *   default stream).  mabd_step returns once the work is enqueued unless
+ *   stats is non-NULL, in which case it synchronizes the stream.
+ *   Errors: no C++ exception crosses this ABI; every call returns a status.
+ *   MABD_ERR_CUDA is sticky (destroy the context).  Device-side failures
+ *   (non-positive det A, non-finite state, polar or PCG non-convergence) set
+ *   a status word that the next synchronizing call (mabd_step with stats,
+ *   mabd_get_state, mabd_get_lambda, mabd_synchronize) returns and clears;
+ *   the state is then undefined until mabd_set_state.
+ *   Call order: mabd_add_* after mabd_prefactor and mabd_step before it
+ *   return MABD_ERR_BAD_STATE.  Threads: one context must not be used from
+ *   two threads at once.  Ids: bodies and joints are numbered densely in
+ *   insertion order; lambda is returned joint by joint in that order, with
+ *   3 rows per ball and 5 per hinge.
+ */
+#ifndef MABD_H
+#define MABD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mabd_ctx mabd_ctx;
+
+#define MABD_WORLD (-1) /* body index of the world in a joint */
+
+typedef enum {
+  MABD_OK = 0,
+  MABD_ERR_INVALID_ARG = 1,
+  MABD_ERR_BAD_STATE = 2,      /* call order */
+  MABD_ERR_OUT_OF_MEMORY = 3,
+  MABD_ERR_CUDA = 4,           /* sticky */
+  MABD_ERR_NOT_SPD = 5,        /* a prefactored or dual block is not positive definite */
+  MABD_ERR_INVERTED = 6,       /* det A <= 0 for some body */
+  MABD_ERR_NONFINITE = 7,
+  MABD_ERR_NO_CONVERGENCE = 8, /* polar iteration or PCG hit its cap */
+  MABD_ERR_TIMEOUT = 9,
+  MABD_ERR_UNSUPPORTED = 10
+} mabd_status;
+
+enum { MABD_FP64 = 0 };
+enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_SOLVER_PCG = 3 };
+enum { MABD_JOINT_BALL = 0, MABD_JOINT_HINGE = 1 };
+enum { MABD_TOPO_NONE = 0, MABD_TOPO_CHAIN = 1, MABD_TOPO_TREE = 2, MABD_TOPO_GRAPH = 3 };
+
+typedef struct {
+  double h;             /* time step [s] > 0 */
+  double gravity[3];    /* [m/s^2], applied at each centre of mass (Eq. module1-wrench-map) */
+  int32_t precision;    /* MABD_FP64 */
+  int32_t solver;       /* MABD_SOLVER_*; AUTO picks chain, then tree, then PCG */
+  int32_t pcg_max_iters;/* cap on PCG iterations (>= 1) */
+  double pcg_rtol;      /* PCG stops when |r| <= pcg_rtol |b| */
+  int32_t refine_steps; /* reserved, 0 */
+  int32_t residual_rhs; /* 1: bottom KKT rhs is -C(q_n) (Sec. 5 footnote); 0: zero as printed */
+  void *stream;         /* cudaStream_t for all work (NULL: default stream) */
+  void *(*dev_alloc)(size_t bytes, void *user); /* optional device allocator */
+  void (*dev_free)(void *ptr, void *user);
+  void *alloc_user;
+} mabd_config;
+
+typedef struct {
+  double mass;             /* m > 0 [kg] */
+  double second_moment[6]; /* Sigma = int rho xbar xbar^T about the COM: xx,yy,zz,xy,xz,yz */
+  double volume;           /* V > 0 [m^3] */
+  double young, poisson;   /* E > 0 [Pa], 0 <= nu < 0.5 */
+  double q[12], qdot[12];  /* initial state */
+  int32_t fixed;           /* 1: the body never moves; joints to it are one-sided */
+} mabd_body_desc;
+
+typedef struct {
+  int32_t type;            /* MABD_JOINT_BALL (3 rows) or MABD_JOINT_HINGE (5 rows) */
+  int64_t body_a, body_b;  /* body_b may be MABD_WORLD; body_a must be a body */
+  double anchor_a[3];      /* joint point in body a's rest frame */
+  double anchor_b[3];      /* ... in body b's rest frame, or a world point */
+  double axis_a[3];        /* hinge axis in body a's rest frame (the frame follows body a) */
+  double axis_b[3];        /* hinge axis in body b's rest frame, or a world axis */
+  double axis_len;         /* distance of the second on-axis point (> 0) */
+} mabd_joint_desc;
+
+typedef struct {
+  double lin_residual;     /* max over rows of |G dq + C(q_n)| */
+  double joint_residual;   /* max over rows of |C(q_{n+1})| (Table 1 |r|) */
+  int32_t pcg_iters;       /* PCG iterations of this step (0 for direct solvers) */
+  double pcg_rel_residual; /* final |r|/|b| of PCG (0 for direct solvers) */
+  double refine_residual;  /* reserved, 0 */
+} mabd_step_stats;
+
+typedef struct {
+  int64_t bodies, joints, dual_rows;
+  int32_t topology;        /* MABD_TOPO_* chosen at prefactor */
+  int32_t solver;          /* MABD_SOLVER_* in use */
+  int64_t device_bytes;    /* device memory held by the context */
+} mabd_info;
+
+/* Fills *cfg with h = 1e-2, gravity (0,0,-9.8), FP64, AUTO, pcg_max_iters 2000,
+   pcg_rtol 1e-13, residual_rhs 1, default stream, library allocator. */
+void mabd_config_default(mabd_config *cfg);
+
+/* Creates a context.  cfg is copied.  INVALID_ARG on h <= 0 or bad fields;
+   CUDA when no device is usable. */
+mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out);
+
+/* Appends n bodies (host array, copied).  *first_id (optional) receives the id
+   of the first.  INVALID_ARG on non-positive mass/volume/E, nu outside
+   [0,0.5) or non-finite state; UNSUPPORTED on a non-diagonal second moment. */
+mabd_status mabd_add_bodies(mabd_ctx *ctx, int64_t n, const mabd_body_desc *d, int64_t *first_id);
+
+/* Appends n joints (host array, copied); body ids are checked at prefactor. */
+mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, int64_t *first_id);
+
+/* Freezes the scene and h: validates joints, classifies the topology,
+   orders bodies/joints for the chosen solver, uploads the state and builds
+   the per-body inverse of Hbar_A = M_A/h^2 + Kbar_A (Eq. abd_final).
+   NOT_SPD if some Hbar_A is not positive definite; UNSUPPORTED if the
+   requested solver does not fit the topology. */
+mabd_status mabd_prefactor(mabd_ctx *ctx);
+
+/* Runs nsteps >= 0 steps.  stats: NULL, or a host array of nsteps entries
+   (then the call synchronizes and returns any device-side failure). */
+mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats);
+
+/* Host arrays of 12*M doubles each, body by body in insertion order.
+   get synchronizes; set enqueues the copy (arrays are staged on the host). */
+mabd_status mabd_get_state(mabd_ctx *ctx, double *q, double *qdot);
+mabd_status mabd_set_state(mabd_ctx *ctx, const double *q, const double *qdot);
+
+/* Multipliers of the last step, dual_rows doubles in joint order (synchronizes). */
+mabd_status mabd_get_lambda(mabd_ctx *ctx, double *lambda);
+
+/* Waits for the context's stream and returns any pending device-side failure. */
+mabd_status mabd_synchronize(mabd_ctx *ctx);
+
+mabd_status mabd_get_info(mabd_ctx *ctx, mabd_info *info);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream.
+   enable = 1 starts recording around every launch (adds event overhead),
+   0 stops.  mabd_kernel_times synchronizes and writes up to cap entries:
+   names[i] (static strings), total milliseconds and launch counts since the
+   last reset; returns the number of kernel names through *count. */
+mabd_status mabd_profile_enable(mabd_ctx *ctx, int32_t enable);
+mabd_status mabd_profile_reset(mabd_ctx *ctx);
+mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, double *ms,
+                              int64_t *launches, int32_t *count);
+
+mabd_status mabd_destroy(mabd_ctx *ctx);
+const char *mabd_status_string(mabd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MABD_H */

@@ -1,0 +1,379 @@
+// Per-body and per-joint kernels of one M-ABD step (FP64):
+//   k_body_prep  (Sec. 3.3-3.4)  R = polar(A), rest-frame rhs, ubar = Hbar^{-1} fbar
+//   k_joint_prep (Sec. 4.2-4.3, Sec. 5.1 Eq. pcpq)  C(q_n), hinge frame, dual rhs
+//   k_backprop   (Sec. 5.2 Eq. recover-dq-explicit) dq, q, qdot
+//   k_residuals  (Table 1 |r|)  max |G dq + C(q_n)| and max |C(q_{n+1})|
+#include "mabd_device.cuh"
+
+namespace mabd {
+
+// One thread per body.  f = M_A qdot/h + [0; m g] - diag4(R)[V vec(P(R^T A)); 0]
+// (Eq. newton_abd rhs at x = x_n, co-rotated linear elasticity of Sec. 3.3),
+// expressed in the rest frame: fbar = diag4(R^T)(M_A qdot/h + [0; m g]) - [V vec P; 0];
+// ubar = Hbar^{-1} fbar (Eq. abd_final).
+__global__ void __launch_bounds__(128) k_body_prep(DevBodies B, StepParams p, int *status) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B.M) return;
+  const int M = B.M;
+  double q[12], qd[12], A[9], R[9];
+  load12(B.q, M, j, q);
+  A_from_q(q, A);
+  int st = polar3(A, R);
+  if (st) {
+    set_status(status, st);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  }
+  if (B.fixed[j]) {  // no unknowns; its rotation may still orient a hinge
+#pragma unroll
+    for (int i = 0; i < 9; ++i) B.R[(size_t)i * M + j] = R[i];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) B.ubar[(size_t)i * M + j] = 0.0;
+    return;
+  }
+  load12(B.qd, M, j, qd);
+  const double s0 = ldg(B.sig + j), s1 = ldg(B.sig + M + j), s2 = ldg(B.sig + 2 * (size_t)M + j);
+  const double m = ldg(B.mass + j);
+  const double vmu = ldg(B.vmu + j), vlam = ldg(B.vlam + j);
+  // world-frame inertial + gravity force, then rotate each 3-block by R^T
+  double fw[12];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fw[a] = s0 * qd[a] * p.inv_h;
+    fw[3 + a] = s1 * qd[3 + a] * p.inv_h;
+    fw[6 + a] = s2 * qd[6 + a] * p.inv_h;
+    fw[9 + a] = m * (qd[9 + a] * p.inv_h + p.g[a]);
+  }
+  double fb[12];
+#pragma unroll
+  for (int blk = 0; blk < 4; ++blk) mtv3(R, fw + 3 * blk, fb + 3 * blk);
+  // F = R^T A ; V P(F) = vmu (F + F^T - 2I) + vlam tr(F - I) I ; fbar_el = -vec(V P)
+  double F[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[3 * r + c] = R[r] * A[c] + R[3 + r] * A[3 + c] + R[6 + r] * A[6 + c];
+  const double tr = vlam * (F[0] + F[4] + F[8] - 3.0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      // vec(P)[3i+a] = P(a,i)
+      double P = vmu * (F[3 * a + i] + F[3 * i + a] - (a == i ? 2.0 : 0.0)) + (a == i ? tr : 0.0);
+      fb[3 * i + a] -= P;
+    }
+  double h[16], u[12];
+  load_hinv(B, j, h);
+  hinv_apply(h, fb, u);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B.R[(size_t)i * M + j] = R[i];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) B.ubar[(size_t)i * M + j] = u[i];
+}
+
+// displacement of rest point p of body j under the unconstrained solve:
+// J(p) u = R (J(p) ubar) with u = diag4(R) ubar
+__device__ __forceinline__ void u_at(const double R[9], const double ub[12], const double p[3],
+                                     double x[3]) {
+  double l[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) l[a] = ub[a] * p[0] + ub[3 + a] * p[1] + ub[6 + a] * p[2] + ub[9 + a];
+  mv3(R, l, x);
+}
+
+// One thread per joint: C(q_n) (Eq. ball / hinge), the hinge frame R_H taken
+// from body a's rotation (axis sign chosen so that a_y >= 0), and the dual rhs
+// b = G u + C(q_n) with G the frozen-frame Jacobian (Eq. pcpq).
+__global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, StepParams p,
+                                                    int *status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= J.K) return;
+  const int K = J.K, M = B.M;
+  const int type = J.type[k];
+  const int ia = J.ja[k], ib = J.jb[k];
+  const uint8_t fl = J.flags[k];
+  double qa[12], pa1[3], pb1[3];
+  load12(B.q, M, ia, qa);
+  load3(J.pa1, K, k, pa1);
+  load3(J.pb1, K, k, pb1);
+  double qb[12];
+  if (fl & JF_B_BODY) load12(B.q, M, ib, qb);
+  double Ra[9], ua[12], Rb[9], ub[12];
+  load_R(B.R, M, ia, Ra);
+  if (fl & JF_A_FREE) load12(B.ubar, M, ia, ua);
+  if (fl & JF_B_FREE) {
+    load_R(B.R, M, ib, Rb);
+    load12(B.ubar, M, ib, ub);
+  }
+  double d1[3];
+  gap_of(qa, pa1, (fl & JF_B_BODY) ? qb : nullptr, pb1, d1);
+  // displacement difference of the first points under u
+  double g1[3] = {0.0, 0.0, 0.0};
+  {
+    double t[3];
+    if (fl & JF_A_FREE) {
+      u_at(Ra, ua, pa1, t);
+      g1[0] += t[0]; g1[1] += t[1]; g1[2] += t[2];
+    }
+    if (fl & JF_B_FREE) {
+      u_at(Rb, ub, pb1, t);
+      g1[0] -= t[0]; g1[1] -= t[1]; g1[2] -= t[2];
+    }
+  }
+  const double rr = p.residual_rhs ? 1.0 : 0.0;
+  if (type == 0) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      J.c[(size_t)r * K + k] = d1[r];
+      J.b[(size_t)r * K + k] = g1[r] + rr * d1[r];
+    }
+    return;
+  }
+  // hinge
+  double pa2[3], pb2[3], uax[3], a[3], RH[9];
+  load3(J.pa2, K, k, pa2);
+  load3(J.pb2, K, k, pb2);
+  load3(J.ua, K, k, uax);
+  mv3(Ra, uax, a);
+  {
+    double n = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    double sgn = a[1] < 0.0 ? -n : n;
+    a[0] *= sgn; a[1] *= sgn; a[2] *= sgn;
+  }
+  hinge_frame(a, RH);
+  double d2[3];
+  gap_of(qa, pa2, (fl & JF_B_BODY) ? qb : nullptr, pb2, d2);
+  double g2[3] = {0.0, 0.0, 0.0};
+  {
+    double t[3];
+    if (fl & JF_A_FREE) {
+      u_at(Ra, ua, pa2, t);
+      g2[0] += t[0]; g2[1] += t[1]; g2[2] += t[2];
+    }
+    if (fl & JF_B_FREE) {
+      u_at(Rb, ub, pb2, t);
+      g2[0] -= t[0]; g2[1] -= t[1]; g2[2] -= t[2];
+    }
+  }
+  double c1[3], e1[3], c2[3], e2[3];
+  mv3(RH, d1, c1);
+  mv3(RH, g1, e1);
+  mv3(RH, d2, c2);
+  mv3(RH, g2, e2);
+  const double cc[5] = {c1[0], c1[1], c1[2], c2[0], c2[2]};
+  const double gg[5] = {e1[0], e1[1], e1[2], e2[0], e2[2]};
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    J.c[(size_t)r * K + k] = cc[r];
+    J.b[(size_t)r * K + k] = gg[r] + rr * cc[r];
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) J.RH[(size_t)i * K + k] = RH[i];
+}
+
+// One thread per body: g = diag4(R^T) sum_k G_kj^T lambda_k accumulated point by
+// point (a row with point p and world direction d contributes [p;1] (x) R^T d),
+// dq = diag4(R)(ubar - Hbar^{-1} g) (Eq. recover-dq-explicit), then the
+// implicit Euler update q += dq, qdot = dq / h.
+__global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevIncidence I,
+                                                  StepParams p) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B.M) return;
+  if (B.fixed[j]) return;
+  const int M = B.M, K = J.K;
+  double R[9], g[12];
+  load_R(B.R, M, j, R);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) g[i] = 0.0;
+  const int e0 = I.off[j], e1 = I.off[j + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int k = I.joint[e];
+    const int side = I.side[e];
+    const int type = J.type[k];
+    const double sgn = side == 0 ? 1.0 : -1.0;
+    double lam[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) lam[r] = J.lambda[(size_t)r * K + k];
+    double F1[3], F2[3] = {0.0, 0.0, 0.0};
+    double P1[3], P2[3];
+    if (side == 0) {
+      load3(J.pa1, K, k, P1);
+    } else {
+      load3(J.pb1, K, k, P1);
+    }
+    if (type == 0) {
+      F1[0] = lam[0]; F1[1] = lam[1]; F1[2] = lam[2];
+    } else {
+      double RH[9];
+      load_R(J.RH, K, k, RH);
+      double l3[3] = {lam[0], lam[1], lam[2]};
+      mtv3(RH, l3, F1);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) F2[a] = lam[3] * RH[a] + lam[4] * RH[6 + a];
+      if (side == 0) load3(J.pa2, K, k, P2);
+      else load3(J.pb2, K, k, P2);
+    }
+    double f1[3];
+    mtv3(R, F1, f1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double v = sgn * f1[a];
+      g[a] += P1[0] * v;
+      g[3 + a] += P1[1] * v;
+      g[6 + a] += P1[2] * v;
+      g[9 + a] += v;
+    }
+    if (type == 1) {
+      double f2[3];
+      mtv3(R, F2, f2);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double v = sgn * f2[a];
+        g[a] += P2[0] * v;
+        g[3 + a] += P2[1] * v;
+        g[6 + a] += P2[2] * v;
+        g[9 + a] += v;
+      }
+    }
+  }
+  double h[16], w[12], ub[12];
+  load_hinv(B, j, h);
+  hinv_apply(h, g, w);
+  load12(B.ubar, M, j, ub);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) ub[i] -= w[i];
+#pragma unroll
+  for (int blk = 0; blk < 4; ++blk) {
+    double dq[3];
+    mv3(R, ub + 3 * blk, dq);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const size_t o = (size_t)(3 * blk + a) * M + j;
+      B.q[o] += dq[a];
+      B.qd[o] = dq[a] * p.inv_h;
+    }
+  }
+}
+
+// One thread per joint (statistics only): linearized residual G dq + C(q_n)
+// with dq = h qdot_{n+1}, and the nonlinear residual C(q_{n+1}) with the hinge
+// frame re-evaluated from body a's new rotation.
+__device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoints &J,
+                                                const StepParams &p, int k, int *status,
+                                                double &lin_out, double &nl_out) {
+  const int K = J.K, M = B.M;
+  const int type = J.type[k];
+  const int ia = J.ja[k], ib = J.jb[k];
+  const uint8_t fl = J.flags[k];
+  const int C = type == 0 ? 3 : 5;
+  double qa[12], qb[12], dqa[12], dqb[12];
+  load12(B.q, M, ia, qa);
+  load12(B.qd, M, ia, dqa);
+  if (fl & JF_B_BODY) {
+    load12(B.q, M, ib, qb);
+    load12(B.qd, M, ib, dqb);
+  }
+  double P[2][3], Q[2][3];
+  load3(J.pa1, K, k, P[0]);
+  load3(J.pb1, K, k, Q[0]);
+  if (type == 1) {
+    load3(J.pa2, K, k, P[1]);
+    load3(J.pb2, K, k, Q[1]);
+  }
+  double RH[9];
+  if (type == 1) load_R(J.RH, K, k, RH);
+  // linearized residual with the frozen frame of this step
+  double lin = 0.0;
+  double da[2][3], db[2][3];
+  for (int pt = 0; pt < 1 + type; ++pt) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      da[pt][a] = 0.0;
+      db[pt][a] = 0.0;
+    }
+    if (fl & JF_A_FREE) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        da[pt][a] = p.h * (dqa[a] * P[pt][0] + dqa[3 + a] * P[pt][1] + dqa[6 + a] * P[pt][2] + dqa[9 + a]);
+    }
+    if (fl & JF_B_FREE) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        db[pt][a] = p.h * (dqb[a] * Q[pt][0] + dqb[3 + a] * Q[pt][1] + dqb[6 + a] * Q[pt][2] + dqb[9 + a]);
+    }
+  }
+  for (int r = 0; r < C; ++r) {
+    double d[3];
+    row_dir(type, RH, r, d);
+    const int pt = r < 3 ? 0 : 1;
+    double v = J.c[(size_t)r * K + k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v += d[a] * (da[pt][a] - db[pt][a]);
+    lin = fmax(lin, fabs(v));
+  }
+  // nonlinear residual at q_{n+1}
+  double nl = 0.0;
+  double d1[3], d2[3];
+  const double *qbp = (fl & JF_B_BODY) ? qb : nullptr;
+  gap_of(qa, P[0], qbp, Q[0], d1);
+  if (type == 0) {
+    nl = fmax(fabs(d1[0]), fmax(fabs(d1[1]), fabs(d1[2])));
+  } else {
+    double A[9], R[9], u[3], a[3], RH1[9];
+    A_from_q(qa, A);
+    int st = polar3(A, R);
+    if (st) set_status(status, st);
+    load3(J.ua, K, k, u);
+    mv3(R, u, a);
+    double n = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    double sgn = a[1] < 0.0 ? -n : n;
+    a[0] *= sgn; a[1] *= sgn; a[2] *= sgn;
+    hinge_frame(a, RH1);
+    gap_of(qa, P[1], qbp, Q[1], d2);
+    double c1[3], c2[3];
+    mv3(RH1, d1, c1);
+    mv3(RH1, d2, c2);
+    nl = fmax(fmax(fabs(c1[0]), fabs(c1[1])), fmax(fabs(c1[2]), fmax(fabs(c2[0]), fabs(c2[2]))));
+  }
+  lin_out = lin;
+  nl_out = nl;
+}
+
+__global__ void __launch_bounds__(128) k_residuals(DevBodies B, DevJoints J, StepParams p,
+                                                   unsigned long long *maxbits, int *status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double lin = 0.0, nl = 0.0;
+  if (k < J.K) joint_residuals(B, J, p, k, status, lin, nl);
+  // warp-level max first (all lanes take part), then one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    lin = fmax(lin, __shfl_xor_sync(0xffffffffu, lin, o));
+    nl = fmax(nl, __shfl_xor_sync(0xffffffffu, nl, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(maxbits, lin);
+    atomic_max_nonneg(maxbits + 1, nl);
+  }
+}
+
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s) {
+  if (B.M > 0) k_body_prep<<<nblk(B.M, 128), 128, 0, s>>>(B, p, status);
+}
+
+void launch_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,
+                       cudaStream_t s) {
+  if (J.K > 0) k_joint_prep<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, status);
+}
+
+void launch_backprop(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                     const StepParams &p, int * /*status*/, cudaStream_t s) {
+  if (B.M > 0) k_backprop<<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+}
+
+void launch_residuals(const DevBodies &B, const DevJoints &J, const StepParams &p,
+                      unsigned long long *maxbits, int *status, cudaStream_t s) {
+  if (J.K > 0) k_residuals<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbits, status);
+}
+
+}  // namespace mabd

@@ -1,0 +1,413 @@
+// Chain path of one M-ABD step (FP64), Sec. 5.2:
+//   k_chain_gram  per body j: the Gram blocks of its (at most two) joints,
+//                 G_kj H_j^{-1} G_k'j^T (Eq. chain-Schur-blocks), formed in the
+//                 body's rest frame with the structured Hbar^{-1};
+//   k_cr_*        block cyclic reduction of the block-tridiagonal dual
+//                 (Eq. chain-btd) with every block padded to 5x5 (a ball's two
+//                 extra rows carry an identity diagonal and decouple exactly).
+// Packed lower-triangular 5x5 storage: entry (r, c), r >= c, at r(r+1)/2 + c.
+#include "mabd_device.cuh"
+
+namespace mabd {
+
+__device__ __forceinline__ int pk(int r, int c) { return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r; }
+
+// ---------------------------------------------------------------------------
+// per-body Gram blocks
+// ---------------------------------------------------------------------------
+// A constraint row of joint k on body j is w = s ([p; 1] (x) d) in world
+// coordinates (Eq. ball / hinge, frozen frame), with s = +1 on body a and -1 on
+// body b.  In the rest frame it becomes [p; 1] (x) (s R^T d), and
+// G_kj H_j^{-1} G_k'j^T = W^T Hbar^{-1} W' (Eq. abd_final).
+__global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, DevIncidence I,
+                                                    DevChain C) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B.M) return;
+  if (B.fixed[j]) return;
+  const int e0 = I.off[j];
+  const int n = I.off[j + 1] - e0;
+  if (n <= 0 || n > 2) return;  // a chain body has one or two joints
+  const int M = B.M, K = J.K;
+  double R[9], h[16];
+  load_R(B.R, M, j, R);
+  load_hinv(B, j, h);
+  // rows: rest-frame direction E[r] and point P[pt[r]] (homogeneous, 4th = 1)
+  double E[10][3];
+  double P[4][3];
+  int pt[10];
+  int kk[2], Cs[2];
+  int nrows = 0;
+  for (int s = 0; s < n; ++s) {
+    const int k = I.joint[e0 + s];
+    const int side = I.side[e0 + s];
+    const int type = J.type[k];
+    kk[s] = k;
+    Cs[s] = type == 0 ? 3 : 5;
+    const double sgn = side == 0 ? 1.0 : -1.0;
+    if (side == 0) load3(J.pa1, K, k, P[2 * s]);
+    else load3(J.pb1, K, k, P[2 * s]);
+    double RH[9];
+    if (type == 1) {
+      if (side == 0) load3(J.pa2, K, k, P[2 * s + 1]);
+      else load3(J.pb2, K, k, P[2 * s + 1]);
+      load_R(J.RH, K, k, RH);
+    }
+    for (int r = 0; r < Cs[s]; ++r) {
+      double d[3], e[3];
+      row_dir(type, RH, r, d);
+      mtv3(R, d, e);
+      E[nrows][0] = sgn * e[0];
+      E[nrows][1] = sgn * e[1];
+      E[nrows][2] = sgn * e[2];
+      pt[nrows] = 2 * s + (r < 3 ? 0 : 1);
+      ++nrows;
+    }
+  }
+  // Gram matrix of the rows: Gm[r][t] = w_r^T Hbar^{-1} w_t, t <= r
+  double Gm[10][10];
+  for (int t = 0; t < nrows; ++t) {
+    double w[12], z[12];
+    const double *p = P[pt[t]];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      w[a] = p[0] * E[t][a];
+      w[3 + a] = p[1] * E[t][a];
+      w[6 + a] = p[2] * E[t][a];
+      w[9 + a] = E[t][a];
+    }
+    hinv_apply(h, w, z);
+    for (int r = t; r < nrows; ++r) {
+      const double *pr = P[pt[r]];
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        v += E[r][a] * (pr[0] * z[a] + pr[1] * z[3 + a] + pr[2] * z[6 + a] + z[9 + a]);
+      Gm[r][t] = v;
+    }
+  }
+  // D of the first joint -> Dfirst, D of the second -> Dsecond, coupling -> B
+  {
+    const int k = kk[0], c0 = Cs[0];
+    for (int r = 0; r < 5; ++r)
+      for (int c = 0; c <= r; ++c)
+        C.Dfirst[(size_t)pk(r, c) * K + k] = (r < c0 && c < c0) ? Gm[r][c] : 0.0;
+  }
+  if (n == 2) {
+    const int k = kk[1], c0 = Cs[0], c1 = Cs[1];
+    for (int r = 0; r < 5; ++r)
+      for (int c = 0; c <= r; ++c)
+        C.Dsecond[(size_t)pk(r, c) * K + k] = (r < c1 && c < c1) ? Gm[c0 + r][c0 + c] : 0.0;
+    const int k0 = kk[0];
+    for (int r = 0; r < 5; ++r)
+      for (int c = 0; c < 5; ++c)
+        C.B[(size_t)(5 * r + c) * K + k0] = (r < c0 && c < c1) ? Gm[c0 + c][r] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5x5 helpers (full row-major in registers)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool chol5(const double A[25], double L[25]) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < 25; ++i) L[i] = 0.0;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double s = A[5 * c + c];
+#pragma unroll
+    for (int k = 0; k < c; ++k) s -= L[5 * c + k] * L[5 * c + k];
+    if (!(s > 0.0)) {
+      ok = false;
+      s = 1.0;
+    }
+    const double d = sqrt(s);
+    const double id = 1.0 / d;
+    L[5 * c + c] = d;
+#pragma unroll
+    for (int r = c + 1; r < 5; ++r) {
+      double t = A[5 * r + c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) t -= L[5 * r + k] * L[5 * c + k];
+      L[5 * r + c] = t * id;
+    }
+  }
+  return ok;
+}
+
+// x = L^{-1} b
+__device__ __forceinline__ void lsolve5(const double L[25], const double b[5], double x[5]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    double s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= L[5 * i + k] * x[k];
+    x[i] = s / L[5 * i + i];
+  }
+}
+
+// x = L^{-T} b
+__device__ __forceinline__ void ltsolve5(const double L[25], const double b[5], double x[5]) {
+#pragma unroll
+  for (int i = 4; i >= 0; --i) {
+    double s = b[i];
+#pragma unroll
+    for (int k = i + 1; k < 5; ++k) s -= L[5 * k + i] * x[k];
+    x[i] = s / L[5 * i + i];
+  }
+}
+
+// level loaders (level 0 assembles from the per-body parts)
+__device__ __forceinline__ void ld_D(const DevChain &C, const DevJoints &J, const CRLevel &L,
+                                     int level, int n, double D[25]) {
+  double p[15];
+  if (level == 0) {
+    const uint8_t f = C.jflags[n];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+      double v = 0.0;
+      if (f & 1) v += C.Dfirst[(size_t)i * C.K + n];
+      if (f & 2) v += C.Dsecond[(size_t)i * C.K + n];
+      p[i] = v;
+    }
+    if (J.type[n] == 0) {
+      p[pk(3, 3)] = 1.0;
+      p[pk(4, 4)] = 1.0;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 15; ++i) p[i] = L.D[(size_t)i * L.N + n];
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) D[5 * r + c] = p[pk(r, c)];
+}
+
+__device__ __forceinline__ void ld_B(const DevChain &C, const CRLevel &L, int level, int n,
+                                     double Bm[25]) {
+  if (level == 0) {
+    const bool has = C.jflags[n] & 4;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) Bm[i] = has ? C.B[(size_t)i * C.K + n] : 0.0;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 25; ++i) Bm[i] = L.B[(size_t)i * L.N + n];
+  }
+}
+
+__device__ __forceinline__ void ld_b(const DevJoints &J, const CRLevel &L, int level, int n,
+                                     double b[5]) {
+  if (level == 0) {
+    const int C = J.type[n] == 0 ? 3 : 5;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) b[r] = r < C ? J.b[(size_t)r * J.K + n] : 0.0;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 5; ++r) b[r] = L.b[(size_t)r * L.N + n];
+  }
+}
+
+// Factor record of an eliminated row (70 doubles): L (packed 15), Ya (25),
+// Yb (25), y (5).  Contributions to a neighbour: packed 15 + 5.
+
+// Odd row n = 2m+1 of the current level:
+//   L L^T = D_n, Ya = L^{-1} B_{n-1}^T, Yb = L^{-1} B_n, y = L^{-1} b_n;
+//   row n-1 receives -Ya^T Ya, -Ya^T y; row n+1 receives -Yb^T Yb, -Yb^T y;
+//   the new coupling between rows n-1 and n+1 is -Ya^T Yb.
+__global__ void __launch_bounds__(128) k_cr_reduce(DevChain C, DevJoints J, CRLevel cur, int level,
+                                                   double *cL, double *cR, double *Bn, int *status) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = 2 * m + 1;
+  const int N = cur.N;
+  if (n >= N) return;
+  const int Nh = N / 2;
+  double D[25], L[25], Bl[25], Br[25], bn[5];
+  ld_D(C, J, cur, level, n, D);
+  ld_B(C, cur, level, n - 1, Bl);
+  if (n + 1 < N) ld_B(C, cur, level, n, Br);
+  else {
+#pragma unroll
+    for (int i = 0; i < 25; ++i) Br[i] = 0.0;
+  }
+  ld_b(J, cur, level, n, bn);
+  if (!chol5(D, L)) set_status(status, ST_NOT_SPD);
+  double Ya[25], Yb[25], y[5];
+  // columns of Ya: L^{-1} (column c of B_{n-1}^T) = L^{-1} (row c of B_{n-1})
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double col[5], x[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) col[r] = Bl[5 * c + r];
+    lsolve5(L, col, x);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) Ya[5 * r + c] = x[r];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) col[r] = Br[5 * r + c];
+    lsolve5(L, col, x);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) Yb[5 * r + c] = x[r];
+  }
+  lsolve5(L, bn, y);
+  double *f = cur.fac;
+  {
+    int o = 0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) f[(size_t)(o++) * Nh + m] = L[5 * r + c];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) f[(size_t)(15 + i) * Nh + m] = Ya[i];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) f[(size_t)(40 + i) * Nh + m] = Yb[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[(size_t)(65 + i) * Nh + m] = y[i];
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+#pragma unroll
+    for (int c = 0; c <= r; ++c) {
+      double sa = 0.0, sb = 0.0;
+#pragma unroll
+      for (int t = 0; t < 5; ++t) {
+        sa += Ya[5 * t + r] * Ya[5 * t + c];
+        sb += Yb[5 * t + r] * Yb[5 * t + c];
+      }
+      cL[(size_t)pk(r, c) * Nh + m] = sa;
+      cR[(size_t)pk(r, c) * Nh + m] = sb;
+    }
+    double ta = 0.0, tb = 0.0;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      ta += Ya[5 * t + r] * y[t];
+      tb += Yb[5 * t + r] * y[t];
+    }
+    cL[(size_t)(15 + r) * Nh + m] = ta;
+    cR[(size_t)(15 + r) * Nh + m] = tb;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < 5; ++t) s += Ya[5 * t + r] * Yb[5 * t + c];
+      Bn[(size_t)(5 * r + c) * Nh + m] = -s;
+    }
+  }
+}
+
+// Even row e = 2m becomes row m of the next level.
+__global__ void __launch_bounds__(128) k_cr_combine(DevChain C, DevJoints J, CRLevel cur, int level,
+                                                    CRLevel next, const double *cL,
+                                                    const double *cR, const double *Bn) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= next.N) return;
+  const int e = 2 * m;
+  const int N = cur.N, Nh = N / 2;
+  double D[25], b[5];
+  ld_D(C, J, cur, level, e, D);
+  ld_b(J, cur, level, e, b);
+  const bool right = e + 1 < N;  // odd row e+1 exists (its index m)
+  const bool left = e >= 1;      // odd row e-1 exists (its index m-1)
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c) {
+      double v = D[5 * r + c];
+      if (right) v -= cL[(size_t)pk(r, c) * Nh + m];
+      if (left) v -= cR[(size_t)pk(r, c) * Nh + m - 1];
+      next.D[(size_t)pk(r, c) * next.N + m] = v;
+    }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    double v = b[r];
+    if (right) v -= cL[(size_t)(15 + r) * Nh + m];
+    if (left) v -= cR[(size_t)(15 + r) * Nh + m - 1];
+    next.b[(size_t)r * next.N + m] = v;
+  }
+#pragma unroll
+  for (int i = 0; i < 25; ++i) next.B[(size_t)i * next.N + m] = right ? Bn[(size_t)i * Nh + m] : 0.0;
+}
+
+// Single remaining row: lambda = D^{-1} b.
+__global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *status) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double D[25], L[25], b[5], y[5], x[5];
+  ld_D(C, J, top, level, 0, D);
+  ld_b(J, top, level, 0, b);
+  if (!chol5(D, L)) set_status(status, ST_NOT_SPD);
+  lsolve5(L, b, y);
+  ltsolve5(L, y, x);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) top.lam[(size_t)r * top.N] = x[r];
+}
+
+// Back-substitution: even rows copy from the next level, odd rows solve
+// lambda_n = L^{-T}(y - Ya lambda_{n-1} - Yb lambda_{n+1}).
+__global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = cur.N;
+  if (n >= N) return;
+  if ((n & 1) == 0) {
+#pragma unroll
+    for (int r = 0; r < 5; ++r) cur.lam[(size_t)r * N + n] = next.lam[(size_t)r * next.N + n / 2];
+    return;
+  }
+  const int m = (n - 1) / 2, Nh = N / 2;
+  const double *f = cur.fac;
+  double L[25], lL[5], lR[5], v[5], x[5];
+  {
+    int o = 0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) L[5 * r + c] = 0.0;
+#pragma unroll
+      for (int c = 0; c <= r; ++c) L[5 * r + c] = f[(size_t)(o++) * Nh + m];
+    }
+  }
+  const bool right = n + 1 < N;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    lL[r] = next.lam[(size_t)r * next.N + m];
+    lR[r] = right ? next.lam[(size_t)r * next.N + m + 1] : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    double s = f[(size_t)(65 + r) * Nh + m];
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      s -= f[(size_t)(15 + 5 * r + c) * Nh + m] * lL[c] + f[(size_t)(40 + 5 * r + c) * Nh + m] * lR[c];
+    v[r] = s;
+  }
+  ltsolve5(L, v, x);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) cur.lam[(size_t)r * N + n] = x[r];
+}
+
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+void launch_chain_gram(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                       const DevChain &C, cudaStream_t s) {
+  if (B.M > 0) k_chain_gram<<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, C);
+}
+
+void launch_cr_reduce(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
+                      double *cL, double *cR, double *Bn, int *status, cudaStream_t s) {
+  const int Nh = cur.N / 2;
+  if (Nh > 0) k_cr_reduce<<<nblk(Nh, 128), 128, 0, s>>>(C, J, cur, level, cL, cR, Bn, status);
+}
+
+void launch_cr_combine(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
+                       const CRLevel &next, const double *cL, const double *cR,
+                       const double *Bn, cudaStream_t s) {
+  if (next.N > 0) k_cr_combine<<<nblk(next.N, 128), 128, 0, s>>>(C, J, cur, level, next, cL, cR, Bn);
+}
+
+void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,
+                   int *status, cudaStream_t s) {
+  k_cr_top<<<1, 32, 0, s>>>(C, J, top, level, status);
+}
+
+void launch_cr_back(const CRLevel &cur, const CRLevel &next, cudaStream_t s) {
+  if (cur.N > 0) k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next);
+}
+
+}  // namespace mabd

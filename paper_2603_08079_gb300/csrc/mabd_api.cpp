@@ -1,0 +1,923 @@
+// Host side of the C ABI declared in include/mabd.h: scene validation,
+// topology classification and ordering, prefactorization of the per-body
+// system matrices (Eq. abd_final), device buffers and the kernel sequence of
+// one step.  No C++ exception crosses the ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mabd.h"
+#include "mabd_internal.h"
+
+using namespace mabd;
+
+namespace {
+
+struct Rec {
+  const char *name;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct mabd_ctx {
+  mabd_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool frozen = false;
+  bool cuda_failed = false;
+  std::vector<mabd_body_desc> bodies;
+  std::vector<mabd_joint_desc> joints;
+
+  // ordering
+  int32_t topology = MABD_TOPO_NONE;
+  int32_t solver = MABD_SOLVER_AUTO;
+  std::vector<int32_t> body_of_internal;   // internal -> user
+  std::vector<int32_t> internal_of_body;   // user -> internal
+  std::vector<int32_t> joint_of_internal;  // internal -> user
+  std::vector<int32_t> internal_of_joint;  // user -> internal
+  std::vector<int64_t> user_row_off;       // user joint -> first lambda row
+  int64_t dual_rows = 0;
+
+  // device memory
+  std::vector<void *> allocs;
+  int64_t device_bytes = 0;
+  DevBodies B{};
+  DevJoints J{};
+  DevIncidence I{};
+  DevChain C{};
+  std::vector<CRLevel> levels;
+  double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
+  int *d_status = nullptr;
+  unsigned long long *d_max = nullptr;
+  int max_cap = 0;
+  StepParams sp{};
+
+  // pinned staging
+  double *h_stage = nullptr;
+  size_t h_stage_n = 0;
+  cudaEvent_t stage_done = nullptr;
+  bool stage_pending = false;
+
+  // profiling
+  bool prof_on = false;
+  std::vector<Rec> recs;
+  std::map<std::string, std::pair<double, int64_t>> prof_acc;
+};
+
+namespace {
+
+mabd_status cuda_fail(mabd_ctx *ctx, cudaError_t e) {
+  if (e == cudaSuccess) return MABD_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return MABD_ERR_OUT_OF_MEMORY;
+  }
+  if (ctx) ctx->cuda_failed = true;
+  return MABD_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t _e = (call);                       \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e); \
+  } while (0)
+
+void *dalloc(mabd_ctx *ctx, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void *p = nullptr;
+  if (ctx->cfg.dev_alloc) {
+    p = ctx->cfg.dev_alloc(bytes, ctx->cfg.alloc_user);
+  } else {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+  }
+  if (p) {
+    ctx->allocs.push_back(p);
+    ctx->device_bytes += (int64_t)bytes;
+  }
+  return p;
+}
+
+template <class T>
+T *dnew(mabd_ctx *ctx, size_t n, bool &ok) {
+  T *p = (T *)dalloc(ctx, n * sizeof(T));
+  if (!p) ok = false;
+  return p;
+}
+
+void free_all(mabd_ctx *ctx) {
+  for (void *p : ctx->allocs) {
+    if (ctx->cfg.dev_free) ctx->cfg.dev_free(p, ctx->cfg.alloc_user);
+    else cudaFree(p);
+  }
+  ctx->allocs.clear();
+  ctx->device_bytes = 0;
+}
+
+mabd_status map_status_bits(int bits) {
+  if (bits & ST_INVERTED) return MABD_ERR_INVERTED;
+  if (bits & ST_NONFINITE) return MABD_ERR_NONFINITE;
+  if (bits & ST_NOT_SPD) return MABD_ERR_NOT_SPD;
+  if (bits & (ST_POLAR_NOCONV | ST_PCG_NOCONV)) return MABD_ERR_NO_CONVERGENCE;
+  return MABD_OK;
+}
+
+inline bool finite_arr(const double *a, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+inline int joint_rows(int type) { return type == MABD_JOINT_HINGE ? 5 : 3; }
+
+// --------------------------------------------------------------------------
+// topology
+// --------------------------------------------------------------------------
+struct Graph {
+  int M = 0, K = 0;
+  std::vector<char> free_body;
+  std::vector<int> fa, fb;                     // free ends of each joint (-1 if none)
+  std::vector<std::vector<int>> inc;           // free body -> incident joints
+};
+
+Graph build_graph(const mabd_ctx *ctx) {
+  Graph g;
+  g.M = (int)ctx->bodies.size();
+  g.K = (int)ctx->joints.size();
+  g.free_body.resize(g.M);
+  for (int j = 0; j < g.M; ++j) g.free_body[j] = ctx->bodies[j].fixed ? 0 : 1;
+  g.fa.resize(g.K);
+  g.fb.resize(g.K);
+  g.inc.resize(g.M);
+  for (int k = 0; k < g.K; ++k) {
+    const auto &d = ctx->joints[k];
+    int a = (int)d.body_a, b = (int)d.body_b;
+    g.fa[k] = g.free_body[a] ? a : -1;
+    g.fb[k] = (b >= 0 && g.free_body[b]) ? b : -1;
+    if (g.fa[k] >= 0) g.inc[a].push_back(k);
+    if (g.fb[k] >= 0) g.inc[b].push_back(k);
+  }
+  return g;
+}
+
+inline int other_end(const Graph &g, int k, int j) { return g.fa[k] == j ? g.fb[k] : g.fa[k]; }
+
+// A chain: the free bodies form one path through joints between free bodies,
+// and ordering the joints along it puts every two joints that share a body
+// next to each other (so the dual is block tridiagonal, Eq. chain-btd).
+bool chain_order(const Graph &g, std::vector<int32_t> &border, std::vector<int32_t> &jorder) {
+  int nfree = 0, nint = 0;
+  for (int j = 0; j < g.M; ++j) nfree += g.free_body[j];
+  for (int k = 0; k < g.K; ++k) nint += (g.fa[k] >= 0 && g.fb[k] >= 0);
+  if (nfree == 0 || g.K == 0 || nint != nfree - 1) return false;
+  int start = -1;
+  for (int j = 0; j < g.M; ++j) {
+    if (!g.free_body[j]) continue;
+    int deg = 0;
+    for (int k : g.inc[j]) deg += other_end(g, k, j) >= 0;
+    if (deg > 2) return false;
+    if (deg <= 1 && start < 0) start = j;
+  }
+  if (start < 0) return false;
+  std::vector<char> used(g.K, 0);
+  border.clear();
+  jorder.clear();
+  int cur = start, prevk = -1;
+  while (cur >= 0) {
+    border.push_back(cur);
+    std::vector<int> side;
+    for (int k : g.inc[cur])
+      if (other_end(g, k, cur) < 0) side.push_back(k);
+    std::sort(side.begin(), side.end());
+    for (int k : side) {
+      jorder.push_back(k);
+      used[k] = 1;
+    }
+    int next = -1, nk = -1;
+    for (int k : g.inc[cur])
+      if (k != prevk && !used[k] && other_end(g, k, cur) >= 0) {
+        nk = k;
+        next = other_end(g, k, cur);
+      }
+    if (nk >= 0) {
+      jorder.push_back(nk);
+      used[nk] = 1;
+    }
+    prevk = nk;
+    cur = next;
+    if ((int)border.size() > nfree) return false;
+  }
+  if ((int)border.size() != nfree || (int)jorder.size() != g.K) return false;
+  std::vector<int> pos(g.K);
+  for (int i = 0; i < g.K; ++i) pos[jorder[i]] = i;
+  for (int j = 0; j < g.M; ++j) {
+    if (!g.free_body[j]) continue;
+    if (g.inc[j].size() > 2) return false;
+    if (g.inc[j].size() == 2 && std::abs(pos[g.inc[j][0]] - pos[g.inc[j][1]]) != 1) return false;
+  }
+  for (int j = 0; j < g.M; ++j)
+    if (!g.free_body[j]) border.push_back(j);
+  return true;
+}
+
+// --------------------------------------------------------------------------
+// per-body structured inverse of Hbar_A = M_A/h^2 + Kbar_A (Eq. abd_final)
+// --------------------------------------------------------------------------
+bool inv2(double a, double b, double d, double out[3]) {
+  // [[a, b], [b, d]]^{-1}
+  if (!(a > 0.0)) return false;
+  double det = a * d - b * b;
+  if (!(det > 0.0)) return false;
+  out[0] = d / det;
+  out[1] = -b / det;
+  out[2] = a / det;
+  return true;
+}
+
+bool structured_hinv(const mabd_body_desc &d, double h, double out[HINV_N]) {
+  const double E = d.young, nu = d.poisson, V = d.volume;
+  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double ih2 = 1.0 / (h * h);
+  const double s[3] = {d.second_moment[0], d.second_moment[1], d.second_moment[2]};
+  // diagonal-entry block X (indices 0, 4, 8): s_i/h^2 + V(2mu + lam) on the
+  // diagonal, V lam off the diagonal; invert by Cholesky
+  double X[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) X[3 * r + c] = (r == c ? s[r] * ih2 + V * (2.0 * mu + lam) : V * lam);
+  double L[9] = {0};
+  for (int c = 0; c < 3; ++c) {
+    double t = X[3 * c + c];
+    for (int k = 0; k < c; ++k) t -= L[3 * c + k] * L[3 * c + k];
+    if (!(t > 0.0)) return false;
+    L[3 * c + c] = std::sqrt(t);
+    for (int r = c + 1; r < 3; ++r) {
+      double v = X[3 * r + c];
+      for (int k = 0; k < c; ++k) v -= L[3 * r + k] * L[3 * c + k];
+      L[3 * r + c] = v / L[3 * c + c];
+    }
+  }
+  double Xi[9];
+  for (int c = 0; c < 3; ++c) {
+    double e[3] = {0, 0, 0}, y[3], x[3];
+    e[c] = 1.0;
+    for (int i = 0; i < 3; ++i) {
+      double v = e[i];
+      for (int k = 0; k < i; ++k) v -= L[3 * i + k] * y[k];
+      y[i] = v / L[3 * i + i];
+    }
+    for (int i = 2; i >= 0; --i) {
+      double v = y[i];
+      for (int k = i + 1; k < 3; ++k) v -= L[3 * k + i] * x[k];
+      x[i] = v / L[3 * i + i];
+    }
+    for (int r = 0; r < 3; ++r) Xi[3 * r + c] = x[r];
+  }
+  out[0] = h * h / d.mass;
+  out[1] = Xi[0];
+  out[2] = 0.5 * (Xi[1] + Xi[3]);
+  out[3] = 0.5 * (Xi[2] + Xi[6]);
+  out[4] = Xi[4];
+  out[5] = 0.5 * (Xi[5] + Xi[7]);
+  out[6] = Xi[8];
+  // transpose pairs: entry (row a, column i) has mass s_i/h^2 and stiffness V mu,
+  // coupled to its transpose by V mu
+  const double vm = V * mu;
+  if (!inv2(s[0] * ih2 + vm, vm, s[1] * ih2 + vm, out + 7)) return false;   // q[1]=A(1,0), q[3]=A(0,1)
+  if (!inv2(s[0] * ih2 + vm, vm, s[2] * ih2 + vm, out + 10)) return false;  // q[2]=A(2,0), q[6]=A(0,2)
+  if (!inv2(s[1] * ih2 + vm, vm, s[2] * ih2 + vm, out + 13)) return false;  // q[5]=A(2,1), q[7]=A(1,2)
+  return out[0] > 0.0 && std::isfinite(out[0]);
+}
+
+// --------------------------------------------------------------------------
+// profiling around launches
+// --------------------------------------------------------------------------
+template <class F>
+void run(mabd_ctx *ctx, const char *name, F &&f) {
+  if (!ctx->prof_on) {
+    f();
+    return;
+  }
+  Rec r{name, nullptr, nullptr};
+  cudaEventCreate(&r.a);
+  cudaEventCreate(&r.b);
+  cudaEventRecord(r.a, ctx->stream);
+  f();
+  cudaEventRecord(r.b, ctx->stream);
+  ctx->recs.push_back(r);
+}
+
+mabd_status harvest_profile(mabd_ctx *ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto &r : ctx->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto &acc = ctx->prof_acc[r.name];
+    acc.first += ms;
+    acc.second += 1;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  ctx->recs.clear();
+  return MABD_OK;
+}
+
+mabd_status read_status(mabd_ctx *ctx) {
+  int bits = 0;
+  CK(cudaMemcpyAsync(&bits, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (bits) {
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return map_status_bits(bits);
+}
+
+mabd_status ensure_stage(mabd_ctx *ctx, size_t n) {
+  if (ctx->stage_pending) {
+    CK(cudaEventSynchronize(ctx->stage_done));
+    ctx->stage_pending = false;
+  }
+  if (ctx->h_stage_n >= n) return MABD_OK;
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  ctx->h_stage = nullptr;
+  ctx->h_stage_n = 0;
+  CK(cudaMallocHost((void **)&ctx->h_stage, n * sizeof(double)));
+  ctx->h_stage_n = n;
+  return MABD_OK;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+void mabd_config_default(mabd_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->h = 1e-2;
+  cfg->gravity[2] = -9.8;
+  cfg->precision = MABD_FP64;
+  cfg->solver = MABD_SOLVER_AUTO;
+  cfg->pcg_max_iters = 2000;
+  cfg->pcg_rtol = 1e-13;
+  cfg->residual_rhs = 1;
+}
+
+const char *mabd_status_string(mabd_status s) {
+  switch (s) {
+    case MABD_OK: return "ok";
+    case MABD_ERR_INVALID_ARG: return "invalid argument";
+    case MABD_ERR_BAD_STATE: return "call out of order";
+    case MABD_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case MABD_ERR_CUDA: return "CUDA error (context unusable)";
+    case MABD_ERR_NOT_SPD: return "matrix not positive definite";
+    case MABD_ERR_INVERTED: return "inverted body (det A <= 0)";
+    case MABD_ERR_NONFINITE: return "non-finite value";
+    case MABD_ERR_NO_CONVERGENCE: return "iteration did not converge";
+    case MABD_ERR_TIMEOUT: return "timeout";
+    case MABD_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
+  if (!cfg || !out) return MABD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!(cfg->h > 0.0) || !std::isfinite(cfg->h) || !finite_arr(cfg->gravity, 3))
+    return MABD_ERR_INVALID_ARG;
+  if (cfg->precision != MABD_FP64) return MABD_ERR_UNSUPPORTED;
+  if (cfg->solver < MABD_SOLVER_AUTO || cfg->solver > MABD_SOLVER_PCG) return MABD_ERR_INVALID_ARG;
+  if (cfg->pcg_max_iters < 1 || !(cfg->pcg_rtol > 0.0)) return MABD_ERR_INVALID_ARG;
+  if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) return MABD_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return MABD_ERR_CUDA;
+  }
+  mabd_ctx *ctx = new (std::nothrow) mabd_ctx();
+  if (!ctx) return MABD_ERR_OUT_OF_MEMORY;
+  ctx->cfg = *cfg;
+  ctx->stream = (cudaStream_t)cfg->stream;
+  cudaGetDevice(&ctx->device);
+  if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return MABD_ERR_CUDA;
+  }
+  *out = ctx;
+  return MABD_OK;
+}
+
+mabd_status mabd_add_bodies(mabd_ctx *ctx, int64_t n, const mabd_body_desc *d, int64_t *first_id) {
+  if (!ctx || n < 0 || (n > 0 && !d)) return MABD_ERR_INVALID_ARG;
+  if (ctx->frozen) return MABD_ERR_BAD_STATE;
+  if ((int64_t)ctx->bodies.size() + n > (int64_t)INT32_MAX / 16) return MABD_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i) {
+    const auto &b = d[i];
+    if (!(b.mass > 0.0) || !(b.volume > 0.0) || !(b.young > 0.0) || !(b.poisson >= 0.0) ||
+        !(b.poisson < 0.5) || !std::isfinite(b.mass) || !std::isfinite(b.volume) ||
+        !std::isfinite(b.young) || !finite_arr(b.second_moment, 6) || !finite_arr(b.q, 12) ||
+        !finite_arr(b.qdot, 12) || (b.fixed != 0 && b.fixed != 1))
+      return MABD_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+      if (!(b.second_moment[a] > 0.0)) return MABD_ERR_INVALID_ARG;
+    const double tr = b.second_moment[0] + b.second_moment[1] + b.second_moment[2];
+    for (int a = 3; a < 6; ++a)
+      if (std::fabs(b.second_moment[a]) > 1e-12 * tr) return MABD_ERR_UNSUPPORTED;
+  }
+  if (first_id) *first_id = (int64_t)ctx->bodies.size();
+  ctx->bodies.insert(ctx->bodies.end(), d, d + n);
+  return MABD_OK;
+}
+
+mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, int64_t *first_id) {
+  if (!ctx || n < 0 || (n > 0 && !d)) return MABD_ERR_INVALID_ARG;
+  if (ctx->frozen) return MABD_ERR_BAD_STATE;
+  if ((int64_t)ctx->joints.size() + n > (int64_t)INT32_MAX / 16) return MABD_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i) {
+    const auto &j = d[i];
+    if (j.type != MABD_JOINT_BALL && j.type != MABD_JOINT_HINGE) return MABD_ERR_INVALID_ARG;
+    if (!finite_arr(j.anchor_a, 3) || !finite_arr(j.anchor_b, 3) || !finite_arr(j.axis_a, 3) ||
+        !finite_arr(j.axis_b, 3))
+      return MABD_ERR_INVALID_ARG;
+    if (j.type == MABD_JOINT_HINGE) {
+      double na = j.axis_a[0] * j.axis_a[0] + j.axis_a[1] * j.axis_a[1] + j.axis_a[2] * j.axis_a[2];
+      double nb = j.axis_b[0] * j.axis_b[0] + j.axis_b[1] * j.axis_b[1] + j.axis_b[2] * j.axis_b[2];
+      if (!(na > 0.0) || !(nb > 0.0) || !(j.axis_len > 0.0) || !std::isfinite(j.axis_len))
+        return MABD_ERR_INVALID_ARG;
+    }
+  }
+  if (first_id) *first_id = (int64_t)ctx->joints.size();
+  ctx->joints.insert(ctx->joints.end(), d, d + n);
+  return MABD_OK;
+}
+
+mabd_status mabd_prefactor(mabd_ctx *ctx) {
+  if (!ctx) return MABD_ERR_INVALID_ARG;
+  if (ctx->cuda_failed) return MABD_ERR_CUDA;
+  if (ctx->frozen) return MABD_ERR_BAD_STATE;
+  const int M = (int)ctx->bodies.size(), K = (int)ctx->joints.size();
+  for (int k = 0; k < K; ++k) {
+    const auto &j = ctx->joints[k];
+    if (j.body_a < 0 || j.body_a >= M || j.body_b < MABD_WORLD || j.body_b >= M ||
+        j.body_a == j.body_b)
+      return MABD_ERR_INVALID_ARG;
+    const bool afree = !ctx->bodies[j.body_a].fixed;
+    const bool bfree = j.body_b >= 0 && !ctx->bodies[j.body_b].fixed;
+    if (!afree && !bfree) return MABD_ERR_INVALID_ARG;  // no unknown: rows would be void
+  }
+  // ---- topology and ordering
+  Graph g = build_graph(ctx);
+  std::vector<int32_t> border, jorder;
+  bool is_chain = K > 0 && chain_order(g, border, jorder);
+  int solver = ctx->cfg.solver;
+  if (K == 0) {
+    ctx->topology = MABD_TOPO_NONE;
+    solver = MABD_SOLVER_AUTO;
+    border.resize(M);
+    for (int j = 0; j < M; ++j) border[j] = j;
+  } else if (is_chain) {
+    ctx->topology = MABD_TOPO_CHAIN;
+    if (solver == MABD_SOLVER_AUTO) solver = MABD_SOLVER_CHAIN;
+  } else {
+    ctx->topology = MABD_TOPO_GRAPH;
+    if (solver == MABD_SOLVER_AUTO) solver = MABD_SOLVER_PCG;
+  }
+  if (K > 0 && solver != MABD_SOLVER_CHAIN) return MABD_ERR_UNSUPPORTED;
+  if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
+  ctx->solver = solver;
+  ctx->body_of_internal = border;
+  ctx->internal_of_body.assign(M, -1);
+  for (int i = 0; i < M; ++i) ctx->internal_of_body[border[i]] = i;
+  ctx->joint_of_internal = jorder;
+  ctx->internal_of_joint.assign(K, -1);
+  for (int i = 0; i < K; ++i) ctx->internal_of_joint[jorder[i]] = i;
+  ctx->user_row_off.assign(K + 1, 0);
+  for (int k = 0; k < K; ++k) ctx->user_row_off[k + 1] = ctx->user_row_off[k] + joint_rows(ctx->joints[k].type);
+  ctx->dual_rows = ctx->user_row_off[K];
+
+  // ---- host arrays in internal order
+  const double h = ctx->cfg.h;
+  std::vector<double> q(12 * (size_t)M), qd(12 * (size_t)M), sig(3 * (size_t)M), mass(M), vmu(M),
+      vlam(M), hinv(HINV_N * (size_t)M);
+  std::vector<uint8_t> fixed(M);
+  for (int i = 0; i < M; ++i) {
+    const auto &d = ctx->bodies[border[i]];
+    for (int c = 0; c < 12; ++c) {
+      q[(size_t)c * M + i] = d.q[c];
+      qd[(size_t)c * M + i] = d.qdot[c];
+    }
+    for (int a = 0; a < 3; ++a) sig[(size_t)a * M + i] = d.second_moment[a];
+    mass[i] = d.mass;
+    const double mu = d.young / (2.0 * (1.0 + d.poisson));
+    const double lam = d.young * d.poisson / ((1.0 + d.poisson) * (1.0 - 2.0 * d.poisson));
+    vmu[i] = d.volume * mu;
+    vlam[i] = d.volume * lam;
+    fixed[i] = d.fixed ? 1 : 0;
+    double hv[HINV_N];
+    if (!fixed[i]) {
+      if (!structured_hinv(d, h, hv)) return MABD_ERR_NOT_SPD;
+    } else {
+      std::memset(hv, 0, sizeof(hv));
+    }
+    for (int c = 0; c < HINV_N; ++c) hinv[(size_t)c * M + i] = hv[c];
+  }
+  std::vector<int8_t> jtype(K);
+  std::vector<int32_t> ja(K), jb(K);
+  std::vector<uint8_t> jfl(K);
+  std::vector<double> pa1(3 * (size_t)K), pb1(3 * (size_t)K), pa2(3 * (size_t)K), pb2(3 * (size_t)K),
+      ua(3 * (size_t)K);
+  for (int i = 0; i < K; ++i) {
+    const auto &d = ctx->joints[jorder[i]];
+    jtype[i] = (int8_t)d.type;
+    ja[i] = ctx->internal_of_body[d.body_a];
+    jb[i] = d.body_b >= 0 ? ctx->internal_of_body[d.body_b] : -1;
+    uint8_t f = 0;
+    if (!ctx->bodies[d.body_a].fixed) f |= JF_A_FREE;
+    if (d.body_b >= 0) {
+      f |= JF_B_BODY;
+      if (!ctx->bodies[d.body_b].fixed) f |= JF_B_FREE;
+    }
+    jfl[i] = f;
+    double na = std::sqrt(d.axis_a[0] * d.axis_a[0] + d.axis_a[1] * d.axis_a[1] + d.axis_a[2] * d.axis_a[2]);
+    double nb = std::sqrt(d.axis_b[0] * d.axis_b[0] + d.axis_b[1] * d.axis_b[1] + d.axis_b[2] * d.axis_b[2]);
+    for (int a = 0; a < 3; ++a) {
+      pa1[(size_t)a * K + i] = d.anchor_a[a];
+      pb1[(size_t)a * K + i] = d.anchor_b[a];
+      double uaa = na > 0 ? d.axis_a[a] / na : 0.0, ubb = nb > 0 ? d.axis_b[a] / nb : 0.0;
+      ua[(size_t)a * K + i] = uaa;
+      pa2[(size_t)a * K + i] = d.anchor_a[a] + d.axis_len * uaa;
+      pb2[(size_t)a * K + i] = d.anchor_b[a] + d.axis_len * ubb;
+    }
+  }
+  // incidence over internal order, joints sorted by internal index
+  std::vector<int32_t> ioff(M + 1, 0), ijoint;
+  std::vector<int8_t> iside;
+  {
+    std::vector<std::vector<std::pair<int, int>>> lists(M);
+    for (int i = 0; i < K; ++i) {
+      if (jfl[i] & JF_A_FREE) lists[ja[i]].push_back({i, 0});
+      if (jfl[i] & JF_B_FREE) lists[jb[i]].push_back({i, 1});
+    }
+    for (int j = 0; j < M; ++j) {
+      std::sort(lists[j].begin(), lists[j].end());
+      ioff[j + 1] = ioff[j] + (int)lists[j].size();
+      for (auto &e : lists[j]) {
+        ijoint.push_back(e.first);
+        iside.push_back((int8_t)e.second);
+      }
+    }
+  }
+  std::vector<uint8_t> cfl(K, 0);
+  if (solver == MABD_SOLVER_CHAIN) {
+    for (int j = 0; j < M; ++j) {
+      const int n = ioff[j + 1] - ioff[j];
+      if (n >= 1) cfl[ijoint[ioff[j]]] |= 1;
+      if (n == 2) {
+        cfl[ijoint[ioff[j] + 1]] |= 2;
+        cfl[ijoint[ioff[j]]] |= 4;
+      }
+    }
+  }
+
+  // ---- device buffers
+  bool ok = true;
+  const int Mx = std::max(M, 1), Kx = std::max(K, 1);
+  auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  };
+  DevBodies &B = ctx->B;
+  B.M = M;
+  B.q = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+  B.qd = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+  double *dsig = dnew<double>(ctx, 3 * (size_t)Mx, ok);
+  double *dmass = dnew<double>(ctx, Mx, ok);
+  double *dvmu = dnew<double>(ctx, Mx, ok);
+  double *dvlam = dnew<double>(ctx, Mx, ok);
+  double *dhinv = dnew<double>(ctx, HINV_N * (size_t)Mx, ok);
+  uint8_t *dfixed = dnew<uint8_t>(ctx, Mx, ok);
+  B.R = dnew<double>(ctx, 9 * (size_t)Mx, ok);
+  B.ubar = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+  DevJoints &J = ctx->J;
+  J.K = K;
+  int8_t *djt = dnew<int8_t>(ctx, Kx, ok);
+  int32_t *dja = dnew<int32_t>(ctx, Kx, ok);
+  int32_t *djb = dnew<int32_t>(ctx, Kx, ok);
+  uint8_t *djf = dnew<uint8_t>(ctx, Kx, ok);
+  double *dpa1 = dnew<double>(ctx, 3 * (size_t)Kx, ok);
+  double *dpb1 = dnew<double>(ctx, 3 * (size_t)Kx, ok);
+  double *dpa2 = dnew<double>(ctx, 3 * (size_t)Kx, ok);
+  double *dpb2 = dnew<double>(ctx, 3 * (size_t)Kx, ok);
+  double *dua = dnew<double>(ctx, 3 * (size_t)Kx, ok);
+  J.RH = dnew<double>(ctx, 9 * (size_t)Kx, ok);
+  J.c = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+  J.b = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+  J.lambda = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+  int32_t *dioff = dnew<int32_t>(ctx, (size_t)M + 1, ok);
+  int32_t *dij = dnew<int32_t>(ctx, std::max<size_t>(ijoint.size(), 1), ok);
+  int8_t *dis = dnew<int8_t>(ctx, std::max<size_t>(iside.size(), 1), ok);
+  ctx->d_status = dnew<int>(ctx, 1, ok);
+  if (!ok) {
+    free_all(ctx);
+    return MABD_ERR_OUT_OF_MEMORY;
+  }
+  CK(up(B.q, q.data(), q.size() * 8));
+  CK(up(B.qd, qd.data(), qd.size() * 8));
+  CK(up(dsig, sig.data(), sig.size() * 8));
+  CK(up(dmass, mass.data(), mass.size() * 8));
+  CK(up(dvmu, vmu.data(), vmu.size() * 8));
+  CK(up(dvlam, vlam.data(), vlam.size() * 8));
+  CK(up(dhinv, hinv.data(), hinv.size() * 8));
+  CK(up(dfixed, fixed.data(), fixed.size()));
+  CK(up(djt, jtype.data(), jtype.size()));
+  CK(up(dja, ja.data(), ja.size() * 4));
+  CK(up(djb, jb.data(), jb.size() * 4));
+  CK(up(djf, jfl.data(), jfl.size()));
+  CK(up(dpa1, pa1.data(), pa1.size() * 8));
+  CK(up(dpb1, pb1.data(), pb1.size() * 8));
+  CK(up(dpa2, pa2.data(), pa2.size() * 8));
+  CK(up(dpb2, pb2.data(), pb2.size() * 8));
+  CK(up(dua, ua.data(), ua.size() * 8));
+  CK(up(dioff, ioff.data(), ioff.size() * 4));
+  CK(up(dij, ijoint.data(), ijoint.size() * 4));
+  CK(up(dis, iside.data(), iside.size()));
+  CK(cudaMemsetAsync(J.lambda, 0, 5 * (size_t)Kx * 8, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  B.sig = dsig;
+  B.mass = dmass;
+  B.vmu = dvmu;
+  B.vlam = dvlam;
+  B.hinv = dhinv;
+  B.fixed = dfixed;
+  J.type = djt;
+  J.ja = dja;
+  J.jb = djb;
+  J.flags = djf;
+  J.pa1 = dpa1;
+  J.pb1 = dpb1;
+  J.pa2 = dpa2;
+  J.pb2 = dpb2;
+  J.ua = dua;
+  ctx->I.off = dioff;
+  ctx->I.joint = dij;
+  ctx->I.side = dis;
+
+  if (solver == MABD_SOLVER_CHAIN) {
+    DevChain &C = ctx->C;
+    C.K = K;
+    C.Dfirst = dnew<double>(ctx, 15 * (size_t)K, ok);
+    C.Dsecond = dnew<double>(ctx, 15 * (size_t)K, ok);
+    C.B = dnew<double>(ctx, 25 * (size_t)K, ok);
+    uint8_t *dcf = dnew<uint8_t>(ctx, K, ok);
+    // cyclic-reduction levels
+    ctx->levels.clear();
+    int N = K;
+    int lvl = 0;
+    while (true) {
+      CRLevel L{};
+      L.N = N;
+      if (lvl > 0) {
+        L.D = dnew<double>(ctx, 15 * (size_t)N, ok);
+        L.B = dnew<double>(ctx, 25 * (size_t)N, ok);
+        L.b = dnew<double>(ctx, 5 * (size_t)N, ok);
+        L.lam = dnew<double>(ctx, 5 * (size_t)N, ok);
+      } else {
+        L.lam = J.lambda;
+      }
+      if (N / 2 > 0) L.fac = dnew<double>(ctx, 70 * (size_t)(N / 2), ok);
+      ctx->levels.push_back(L);
+      if (N == 1) break;
+      N = (N + 1) / 2;
+      ++lvl;
+    }
+    const size_t half = std::max(K / 2, 1);
+    ctx->cL = dnew<double>(ctx, 20 * half, ok);
+    ctx->cR = dnew<double>(ctx, 20 * half, ok);
+    ctx->Bn = dnew<double>(ctx, 25 * half, ok);
+    if (!ok) {
+      free_all(ctx);
+      return MABD_ERR_OUT_OF_MEMORY;
+    }
+    CK(up(dcf, cfl.data(), cfl.size()));
+    C.jflags = dcf;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->sp.h = h;
+  ctx->sp.inv_h = 1.0 / h;
+  for (int a = 0; a < 3; ++a) ctx->sp.g[a] = ctx->cfg.gravity[a];
+  ctx->sp.residual_rhs = ctx->cfg.residual_rhs ? 1 : 0;
+  ctx->frozen = true;
+  return MABD_OK;
+}
+
+static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
+  cudaStream_t s = ctx->stream;
+  const StepParams &p = ctx->sp;
+  run(ctx, "body_prep", [&] { launch_body_prep(ctx->B, p, ctx->d_status, s); });
+  if (ctx->J.K > 0) {
+    run(ctx, "joint_prep", [&] { launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
+    if (ctx->solver == MABD_SOLVER_CHAIN) {
+      run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
+      const int nl = (int)ctx->levels.size();
+      for (int l = 0; l + 1 < nl; ++l) {
+        run(ctx, "cr_reduce", [&] {
+          launch_cr_reduce(ctx->C, ctx->J, ctx->levels[l], l, ctx->cL, ctx->cR, ctx->Bn, ctx->d_status, s);
+        });
+        run(ctx, "cr_combine", [&] {
+          launch_cr_combine(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], ctx->cL, ctx->cR,
+                            ctx->Bn, s);
+        });
+      }
+      run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
+      for (int l = nl - 2; l >= 0; --l)
+        run(ctx, "cr_back", [&] { launch_cr_back(ctx->levels[l], ctx->levels[l + 1], s); });
+    }
+  }
+  run(ctx, "backprop", [&] { launch_backprop(ctx->B, ctx->J, ctx->I, p, ctx->d_status, s); });
+  if (maxbits && ctx->J.K > 0)
+    run(ctx, "residuals", [&] { launch_residuals(ctx->B, ctx->J, p, maxbits, ctx->d_status, s); });
+  cudaError_t e = cudaGetLastError();
+  return cuda_fail(ctx, e);
+}
+
+mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
+  if (!ctx || nsteps < 0) return MABD_ERR_INVALID_ARG;
+  if (ctx->cuda_failed) return MABD_ERR_CUDA;
+  if (!ctx->frozen) return MABD_ERR_BAD_STATE;
+  if (nsteps == 0) return MABD_OK;
+  if (stats) {
+    if (ctx->max_cap < nsteps) {
+      bool ok = true;
+      ctx->d_max = dnew<unsigned long long>(ctx, 2 * (size_t)nsteps, ok);
+      if (!ok) return MABD_ERR_OUT_OF_MEMORY;
+      ctx->max_cap = nsteps;
+    }
+    CK(cudaMemsetAsync(ctx->d_max, 0, 2 * (size_t)nsteps * 8, ctx->stream));
+  }
+  for (int i = 0; i < nsteps; ++i) {
+    mabd_status st = step_once(ctx, stats ? ctx->d_max + 2 * i : nullptr);
+    if (st) return st;
+  }
+  if (!stats) return MABD_OK;
+  std::vector<unsigned long long> hb(2 * (size_t)nsteps);
+  CK(cudaMemcpyAsync(hb.data(), ctx->d_max, hb.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < nsteps; ++i) {
+    double lin, nl;
+    std::memcpy(&lin, &hb[2 * i], 8);
+    std::memcpy(&nl, &hb[2 * i + 1], 8);
+    stats[i].lin_residual = lin;
+    stats[i].joint_residual = nl;
+    stats[i].pcg_iters = 0;
+    stats[i].pcg_rel_residual = 0.0;
+    stats[i].refine_residual = 0.0;
+  }
+  return read_status(ctx);
+}
+
+mabd_status mabd_get_state(mabd_ctx *ctx, double *q, double *qdot) {
+  if (!ctx || (!q && !qdot)) return MABD_ERR_INVALID_ARG;
+  if (ctx->cuda_failed) return MABD_ERR_CUDA;
+  if (!ctx->frozen) return MABD_ERR_BAD_STATE;
+  const int M = ctx->B.M;
+  mabd_status st = ensure_stage(ctx, 24 * (size_t)std::max(M, 1));
+  if (st) return st;
+  double *hq = ctx->h_stage, *hqd = ctx->h_stage + 12 * (size_t)M;
+  CK(cudaMemcpyAsync(hq, ctx->B.q, 12 * (size_t)M * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(hqd, ctx->B.qd, 12 * (size_t)M * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < M; ++i) {
+    const size_t u = (size_t)ctx->body_of_internal[i];
+    for (int c = 0; c < 12; ++c) {
+      if (q) q[12 * u + c] = hq[(size_t)c * M + i];
+      if (qdot) qdot[12 * u + c] = hqd[(size_t)c * M + i];
+    }
+  }
+  return read_status(ctx);
+}
+
+mabd_status mabd_set_state(mabd_ctx *ctx, const double *q, const double *qdot) {
+  if (!ctx || !q || !qdot) return MABD_ERR_INVALID_ARG;
+  if (ctx->cuda_failed) return MABD_ERR_CUDA;
+  if (!ctx->frozen) return MABD_ERR_BAD_STATE;
+  const int M = ctx->B.M;
+  if (!finite_arr(q, 12 * M) || !finite_arr(qdot, 12 * M)) return MABD_ERR_INVALID_ARG;
+  mabd_status st = ensure_stage(ctx, 24 * (size_t)std::max(M, 1));
+  if (st) return st;
+  double *hq = ctx->h_stage, *hqd = ctx->h_stage + 12 * (size_t)M;
+  for (int i = 0; i < M; ++i) {
+    const size_t u = (size_t)ctx->body_of_internal[i];
+    for (int c = 0; c < 12; ++c) {
+      hq[(size_t)c * M + i] = q[12 * u + c];
+      hqd[(size_t)c * M + i] = qdot[12 * u + c];
+    }
+  }
+  CK(cudaMemcpyAsync(ctx->B.q, hq, 12 * (size_t)M * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->B.qd, hqd, 12 * (size_t)M * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaEventRecord(ctx->stage_done, ctx->stream));
+  ctx->stage_pending = true;
+  return MABD_OK;
+}
+
+mabd_status mabd_get_lambda(mabd_ctx *ctx, double *lambda) {
+  if (!ctx || !lambda) return MABD_ERR_INVALID_ARG;
+  if (ctx->cuda_failed) return MABD_ERR_CUDA;
+  if (!ctx->frozen) return MABD_ERR_BAD_STATE;
+  const int K = ctx->J.K;
+  if (K == 0) return read_status(ctx);
+  std::vector<double> hl(5 * (size_t)K);
+  CK(cudaMemcpyAsync(hl.data(), ctx->J.lambda, hl.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < K; ++i) {
+    const int u = ctx->joint_of_internal[i];
+    const int C = joint_rows(ctx->joints[u].type);
+    for (int r = 0; r < C; ++r) lambda[ctx->user_row_off[u] + r] = hl[(size_t)r * K + i];
+  }
+  return read_status(ctx);
+}
+
+mabd_status mabd_synchronize(mabd_ctx *ctx) {
+  if (!ctx) return MABD_ERR_INVALID_ARG;
+  if (ctx->cuda_failed) return MABD_ERR_CUDA;
+  if (!ctx->frozen) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MABD_OK;
+  }
+  return read_status(ctx);
+}
+
+mabd_status mabd_get_info(mabd_ctx *ctx, mabd_info *info) {
+  if (!ctx || !info) return MABD_ERR_INVALID_ARG;
+  info->bodies = (int64_t)ctx->bodies.size();
+  info->joints = (int64_t)ctx->joints.size();
+  int64_t rows = 0;
+  for (auto &j : ctx->joints) rows += joint_rows(j.type);
+  info->dual_rows = rows;
+  info->topology = ctx->topology;
+  info->solver = ctx->solver;
+  info->device_bytes = ctx->device_bytes;
+  return MABD_OK;
+}
+
+mabd_status mabd_profile_enable(mabd_ctx *ctx, int32_t enable) {
+  if (!ctx) return MABD_ERR_INVALID_ARG;
+  ctx->prof_on = enable != 0;
+  return MABD_OK;
+}
+
+mabd_status mabd_profile_reset(mabd_ctx *ctx) {
+  if (!ctx) return MABD_ERR_INVALID_ARG;
+  mabd_status st = harvest_profile(ctx);
+  ctx->prof_acc.clear();
+  return st;
+}
+
+mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, double *ms,
+                              int64_t *launches, int32_t *count) {
+  if (!ctx || cap < 0 || !count) return MABD_ERR_INVALID_ARG;
+  mabd_status st = harvest_profile(ctx);
+  if (st) return st;
+  static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "cr_reduce", "cr_combine",
+                                "cr_top", "cr_back", "backprop", "residuals"};
+  int n = 0;
+  for (const char *k : known) {
+    auto it = ctx->prof_acc.find(k);
+    if (it == ctx->prof_acc.end()) continue;
+    if (n < cap) {
+      if (names) names[n] = k;
+      if (ms) ms[n] = it->second.first;
+      if (launches) launches[n] = it->second.second;
+    }
+    ++n;
+  }
+  *count = n;
+  return MABD_OK;
+}
+
+mabd_status mabd_destroy(mabd_ctx *ctx) {
+  if (!ctx) return MABD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &r : ctx->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  free_all(ctx);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+  delete ctx;
+  return MABD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Device math shared by the kernels: 3x3 algebra (row-major), the polar
+// rotation, the hinge frame and the structured Hbar^{-1} of a body.
+#pragma once
+#include <cstdint>
+
+#include "mabd_internal.h"
+
+namespace mabd {
+
+__device__ __forceinline__ double ldg(const double *p) { return __ldg(p); }
+
+__device__ __forceinline__ void set_status(int *status, int bits) {
+  if (status) atomicOr(status, bits);
+}
+
+// A(r,c) = q[3c+r] (Eq. abd_dof: vec stacks the columns of A)
+__device__ __forceinline__ void A_from_q(const double q[12], double A[9]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A[3 * r + c] = q[3 * c + r];
+}
+
+__device__ __forceinline__ void mv3(const double M[9], const double x[3], double y[3]) {
+  y[0] = M[0] * x[0] + M[1] * x[1] + M[2] * x[2];
+  y[1] = M[3] * x[0] + M[4] * x[1] + M[5] * x[2];
+  y[2] = M[6] * x[0] + M[7] * x[1] + M[8] * x[2];
+}
+
+__device__ __forceinline__ void mtv3(const double M[9], const double x[3], double y[3]) {
+  y[0] = M[0] * x[0] + M[3] * x[1] + M[6] * x[2];
+  y[1] = M[1] * x[0] + M[4] * x[1] + M[7] * x[2];
+  y[2] = M[2] * x[0] + M[5] * x[1] + M[8] * x[2];
+}
+
+// x(p) = A p + t for the affine coordinates q (Eq. abd)
+__device__ __forceinline__ void point_of(const double q[12], const double p[3], double x[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = q[a] * p[0] + q[3 + a] * p[1] + q[6 + a] * p[2] + q[9 + a];
+}
+
+// gap x_a(pa) - x_b(pb) of two joint points (Eq. ball), evaluated as
+// (A_a pa - A_b pb) + (t_a - t_b) so that far-from-origin assemblies keep it
+// at round-off of the body size; qb == nullptr: pb is a world point.
+__device__ __forceinline__ void gap_of(const double qa[12], const double pa[3], const double *qb,
+                                       const double pb[3], double d[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double la = qa[a] * pa[0] + qa[3 + a] * pa[1] + qa[6 + a] * pa[2];
+    if (qb) {
+      const double lb = qb[a] * pb[0] + qb[3 + a] * pb[1] + qb[6 + a] * pb[2];
+      d[a] = (la - lb) + (qa[9 + a] - qb[9 + a]);
+    } else {
+      d[a] = la + (qa[9 + a] - pb[a]);
+    }
+  }
+}
+
+// Eq. polar: R = A (A^T A)^{-1/2} by Newton's iteration X <- (X + X^{-T})/2,
+// X^{-T} = cof(X)/det(X).  Returns a ST_* code (0 on success).
+__device__ __forceinline__ int polar3(const double A[9], double R[9]) {
+  double X[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) X[i] = A[i];
+  {
+    double d = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+               X[2] * (X[3] * X[7] - X[4] * X[6]);
+    if (!(d > 0.0)) return isfinite(d) ? ST_INVERTED : ST_NONFINITE;
+  }
+  int it = 0;
+  for (; it < 40; ++it) {
+    double C[9];
+    C[0] = X[4] * X[8] - X[5] * X[7];
+    C[1] = X[5] * X[6] - X[3] * X[8];
+    C[2] = X[3] * X[7] - X[4] * X[6];
+    C[3] = X[2] * X[7] - X[1] * X[8];
+    C[4] = X[0] * X[8] - X[2] * X[6];
+    C[5] = X[1] * X[6] - X[0] * X[7];
+    C[6] = X[1] * X[5] - X[2] * X[4];
+    C[7] = X[2] * X[3] - X[0] * X[5];
+    C[8] = X[0] * X[4] - X[1] * X[3];
+    double d = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    if (!(d > 0.0)) return isfinite(d) ? ST_INVERTED : ST_NONFINITE;
+    double hid = 0.5 / d;
+    double diff = 0.0, nrm = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      double y = 0.5 * X[i] + hid * C[i];
+      double dx = y - X[i];
+      diff += dx * dx;
+      nrm += y * y;
+      X[i] = y;
+    }
+    if (diff <= 1e-30 * nrm) break;
+  }
+  if (it == 40) return ST_POLAR_NOCONV;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = X[i];
+  return 0;
+}
+
+// Sec. 4.3: R_H = I + [v]x + [v]x^2 / (1 + a_y), v = a x e_y = (-a_z, 0, a_x)
+__device__ __forceinline__ void hinge_frame(const double a[3], double RH[9]) {
+  const double vx = -a[2], vz = a[0];
+  const double k = 1.0 / (1.0 + a[1]);
+  // [v]x with v = (vx, 0, vz): [[0, -vz, 0], [vz, 0, -vx], [0, vx, 0]]
+  // [v]x^2 = v v^T - |v|^2 I
+  const double n2 = vx * vx + vz * vz;
+  RH[0] = 1.0 + k * (vx * vx - n2);
+  RH[1] = -vz;
+  RH[2] = k * (vx * vz);
+  RH[3] = vz;
+  RH[4] = 1.0 - k * n2;
+  RH[5] = -vx;
+  RH[6] = k * (vz * vx);
+  RH[7] = vx;
+  RH[8] = 1.0 + k * (vz * vz - n2);
+}
+
+// world direction of constraint row r (Eq. ball: identity rows; Eq. hinge:
+// rows 0-2 are the rows of R_H, rows 3 and 4 its x and z rows at the second point)
+__device__ __forceinline__ void row_dir(int type, const double RH[9], int r, double d[3]) {
+  if (type == 0) {
+    d[0] = r == 0 ? 1.0 : 0.0;
+    d[1] = r == 1 ? 1.0 : 0.0;
+    d[2] = r == 2 ? 1.0 : 0.0;
+  } else {
+    int rr = r < 3 ? r : (r == 3 ? 0 : 2);
+    d[0] = RH[3 * rr];
+    d[1] = RH[3 * rr + 1];
+    d[2] = RH[3 * rr + 2];
+  }
+}
+
+// y = Hbar^{-1} v with the structured inverse h[16] (see mabd_internal.h)
+__device__ __forceinline__ void hinv_apply(const double h[16], const double v[12], double y[12]) {
+  y[0] = h[1] * v[0] + h[2] * v[4] + h[3] * v[8];
+  y[4] = h[2] * v[0] + h[4] * v[4] + h[5] * v[8];
+  y[8] = h[3] * v[0] + h[5] * v[4] + h[6] * v[8];
+  y[1] = h[7] * v[1] + h[8] * v[3];
+  y[3] = h[8] * v[1] + h[9] * v[3];
+  y[2] = h[10] * v[2] + h[11] * v[6];
+  y[6] = h[11] * v[2] + h[12] * v[6];
+  y[5] = h[13] * v[5] + h[14] * v[7];
+  y[7] = h[14] * v[5] + h[15] * v[7];
+  y[9] = h[0] * v[9];
+  y[10] = h[0] * v[10];
+  y[11] = h[0] * v[11];
+}
+
+__device__ __forceinline__ void load_hinv(const DevBodies &B, int j, double h[16]) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) h[i] = ldg(B.hinv + (size_t)i * B.M + j);
+}
+
+__device__ __forceinline__ void load_R(const double *R, int N, int j, double out[9]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) out[i] = R[(size_t)i * N + j];
+}
+
+__device__ __forceinline__ void load12(const double *p, int N, int j, double out[12]) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) out[i] = p[(size_t)i * N + j];
+}
+
+__device__ __forceinline__ void load3(const double *p, int N, int j, double out[3]) {
+  out[0] = ldg(p + j);
+  out[1] = ldg(p + (size_t)N + j);
+  out[2] = ldg(p + 2 * (size_t)N + j);
+}
+
+// atomic max of a non-negative double through its bit pattern
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
+  if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000ULL);  // NaN -> +inf
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace mabd

@@ -1,0 +1,256 @@
+"""Python binding of the C ABI in include/mabd.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library ``_build/libmabd.so``; this
+module converts scene dictionaries (see ``scenes.py``) into the C structs,
+passes PyTorch's stream and caching allocator to the library, and copies
+states and multipliers between numpy arrays and the library.  There is no
+CPU fallback: if the library is missing or no GPU is usable, construction
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+WORLD = -1
+SOLVERS = {"auto": 0, "chain": 1, "tree": 2, "pcg": 3}
+TOPOLOGIES = {0: "none", 1: "chain", 2: "tree", 3: "graph"}
+STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of device memory",
+          4: "CUDA error", 5: "not positive definite", 6: "inverted body", 7: "non-finite",
+          8: "no convergence", 9: "timeout", 10: "unsupported"}
+
+
+class MabdError(RuntimeError):
+    def __init__(self, what: str, code: int):
+        super().__init__(f"{what}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Config(C.Structure):
+    _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("precision", C.c_int32),
+                ("solver", C.c_int32), ("pcg_max_iters", C.c_int32), ("pcg_rtol", C.c_double),
+                ("refine_steps", C.c_int32), ("residual_rhs", C.c_int32), ("stream", C.c_void_p),
+                ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", C.c_void_p)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("lin_residual", C.c_double), ("joint_residual", C.c_double),
+                ("pcg_iters", C.c_int32), ("pcg_rel_residual", C.c_double),
+                ("refine_residual", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("bodies", C.c_int64), ("joints", C.c_int64), ("dual_rows", C.c_int64),
+                ("topology", C.c_int32), ("solver", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+# numpy mirrors of mabd_body_desc / mabd_joint_desc (C layout, natural alignment)
+BODY_DTYPE = np.dtype([("mass", "f8"), ("second_moment", "f8", 6), ("volume", "f8"),
+                       ("young", "f8"), ("poisson", "f8"), ("q", "f8", 12), ("qdot", "f8", 12),
+                       ("fixed", "i4")], align=True)
+JOINT_DTYPE = np.dtype([("type", "i4"), ("body_a", "i8"), ("body_b", "i8"), ("anchor_a", "f8", 3),
+                        ("anchor_b", "f8", 3), ("axis_a", "f8", 3), ("axis_b", "f8", 3),
+                        ("axis_len", "f8")], align=True)
+assert BODY_DTYPE.itemsize == 280 and JOINT_DTYPE.itemsize == 128
+
+_lib = None
+
+EXPORTS = ["mabd_config_default", "mabd_create", "mabd_add_bodies", "mabd_add_joints",
+           "mabd_prefactor", "mabd_step", "mabd_get_state", "mabd_set_state", "mabd_get_lambda",
+           "mabd_synchronize", "mabd_get_info", "mabd_profile_enable", "mabd_profile_reset",
+           "mabd_kernel_times", "mabd_destroy", "mabd_status_string"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmabd.so (building it in-tree with nvcc if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    lib.mabd_config_default.argtypes = [C.POINTER(Config)]
+    lib.mabd_config_default.restype = None
+    lib.mabd_create.argtypes = [C.POINTER(Config), C.POINTER(P)]
+    lib.mabd_add_bodies.argtypes = [P, i64, P, C.POINTER(i64)]
+    lib.mabd_add_joints.argtypes = [P, i64, P, C.POINTER(i64)]
+    lib.mabd_prefactor.argtypes = [P]
+    lib.mabd_step.argtypes = [P, i32, P]
+    lib.mabd_get_state.argtypes = [P, P, P]
+    lib.mabd_set_state.argtypes = [P, P, P]
+    lib.mabd_get_lambda.argtypes = [P, P]
+    lib.mabd_synchronize.argtypes = [P]
+    lib.mabd_get_info.argtypes = [P, C.POINTER(Info)]
+    lib.mabd_profile_enable.argtypes = [P, i32]
+    lib.mabd_profile_reset.argtypes = [P]
+    lib.mabd_kernel_times.argtypes = [P, i32, P, P, P, C.POINTER(i32)]
+    lib.mabd_destroy.argtypes = [P]
+    lib.mabd_status_string.argtypes = [i32]
+    lib.mabd_status_string.restype = C.c_char_p
+    for f in EXPORTS:
+        if f not in ("mabd_config_default", "mabd_status_string"):
+            getattr(lib, f).restype = i32
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def body_array(sc: dict) -> np.ndarray:
+    M = len(sc["mass"])
+    d = np.zeros(M, dtype=BODY_DTYPE)
+    d["mass"] = sc["mass"]
+    d["second_moment"] = sc["second_moment"]
+    d["volume"] = sc["volume"]
+    d["young"] = sc["young"]
+    d["poisson"] = sc["poisson"]
+    d["q"] = sc["q"]
+    d["qdot"] = sc["qdot"]
+    d["fixed"] = sc["fixed"]
+    return d
+
+
+def joint_array(sc: dict) -> np.ndarray:
+    K = len(sc["jtype"])
+    d = np.zeros(K, dtype=JOINT_DTYPE)
+    for f in ("anchor_a", "anchor_b", "axis_a", "axis_b", "axis_len", "body_a", "body_b"):
+        d[f] = sc[f]
+    d["type"] = sc["jtype"]
+    return d
+
+
+class Solver:
+    """One M-ABD scene on one GPU (a ``mabd_ctx``)."""
+
+    def __init__(self, sc: dict, solver: str = "auto", residual_rhs: int = 1,
+                 stream=None, allocator: str = "torch", pcg_rtol: float = 1e-13,
+                 pcg_max_iters: int = 2000):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("mabd.Solver needs a CUDA device")
+        self._lib = load()
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg = Config()
+        self._lib.mabd_config_default(C.byref(cfg))
+        cfg.h = float(sc["h"])
+        for i in range(3):
+            cfg.gravity[i] = float(sc["gravity"][i])
+        cfg.solver = SOLVERS[solver]
+        cfg.residual_rhs = int(residual_rhs)
+        cfg.pcg_rtol = float(pcg_rtol)
+        cfg.pcg_max_iters = int(pcg_max_iters)
+        cfg.stream = C.c_void_p(self.stream.cuda_stream)
+        if allocator == "torch":
+            dev, strm = self.device, self.stream
+
+            def _alloc(n, user):
+                return torch.cuda.caching_allocator_alloc(int(n), dev, strm)
+
+            def _free(p, user):
+                torch.cuda.caching_allocator_delete(p)
+
+            self._cb = (_ALLOC(_alloc), _FREE(_free))
+            cfg.dev_alloc, cfg.dev_free = self._cb
+        self.M = len(sc["mass"])
+        self.K = len(sc["jtype"])
+        self.rows = int(np.sum(np.where(np.asarray(sc["jtype"]) == 1, 5, 3)))
+        ctx = C.c_void_p()
+        self._check("mabd_create", self._lib.mabd_create(C.byref(cfg), C.byref(ctx)))
+        self.ctx = ctx
+        self._cfg = cfg
+        bodies = body_array(sc)
+        joints = joint_array(sc)
+        first = C.c_int64(0)
+        self._check("mabd_add_bodies", self._lib.mabd_add_bodies(self.ctx, self.M, _ptr(bodies), C.byref(first)))
+        if self.K:
+            self._check("mabd_add_joints", self._lib.mabd_add_joints(self.ctx, self.K, _ptr(joints), C.byref(first)))
+        self._check("mabd_prefactor", self._lib.mabd_prefactor(self.ctx))
+
+    def _check(self, what, st):
+        if st != 0:
+            raise MabdError(what, st)
+
+    def step(self, n: int = 1, stats: bool = False):
+        if stats:
+            arr = (StepStats * max(n, 1))()
+            self._check("mabd_step", self._lib.mabd_step(self.ctx, n, arr))
+            return [{f: getattr(s, f) for f, _ in StepStats._fields_} for s in arr[:n]]
+        self._check("mabd_step", self._lib.mabd_step(self.ctx, n, None))
+        return None
+
+    def get_state(self, q: np.ndarray | None = None, qd: np.ndarray | None = None):
+        q = np.empty((self.M, 12)) if q is None else q
+        qd = np.empty((self.M, 12)) if qd is None else qd
+        self._check("mabd_get_state", self._lib.mabd_get_state(self.ctx, _ptr(q), _ptr(qd)))
+        return q, qd
+
+    def set_state(self, q: np.ndarray, qd: np.ndarray):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        qd = np.ascontiguousarray(qd, dtype=np.float64)
+        assert q.size == 12 * self.M and qd.size == 12 * self.M
+        self._keep = (q, qd)
+        self._check("mabd_set_state", self._lib.mabd_set_state(self.ctx, _ptr(q), _ptr(qd)))
+
+    def get_lambda(self) -> np.ndarray:
+        lam = np.zeros(max(self.rows, 1))
+        self._check("mabd_get_lambda", self._lib.mabd_get_lambda(self.ctx, _ptr(lam)))
+        return lam[:self.rows]
+
+    def synchronize(self):
+        self._check("mabd_synchronize", self._lib.mabd_synchronize(self.ctx))
+
+    def info(self) -> dict:
+        inf = Info()
+        self._check("mabd_get_info", self._lib.mabd_get_info(self.ctx, C.byref(inf)))
+        d = {f: getattr(inf, f) for f, _ in Info._fields_}
+        d["topology"] = TOPOLOGIES.get(d["topology"], d["topology"])
+        d["solver"] = {v: k for k, v in SOLVERS.items()}.get(d["solver"], d["solver"])
+        return d
+
+    def profile(self, enable: bool):
+        self._check("mabd_profile_enable", self._lib.mabd_profile_enable(self.ctx, int(enable)))
+
+    def profile_reset(self):
+        self._check("mabd_profile_reset", self._lib.mabd_profile_reset(self.ctx))
+
+    def kernel_times(self) -> dict:
+        cap = 32
+        names = (C.c_char_p * cap)()
+        ms = (C.c_double * cap)()
+        launches = (C.c_int64 * cap)()
+        count = C.c_int32(0)
+        self._check("mabd_kernel_times", self._lib.mabd_kernel_times(
+            self.ctx, cap, C.cast(names, C.c_void_p), C.cast(ms, C.c_void_p),
+            C.cast(launches, C.c_void_p), C.byref(count)))
+        return {names[i].decode(): (ms[i], launches[i]) for i in range(min(count.value, cap))}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._lib.mabd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
