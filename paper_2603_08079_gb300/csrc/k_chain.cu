@@ -85,18 +85,17 @@ __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, De
       Gm[r][t] = v;
     }
   }
-  // D of the first joint -> Dfirst, D of the second -> Dsecond, coupling -> B
-  {
-    const int k = kk[0], c0 = Cs[0];
+  // each joint's diagonal block goes to the slot of this body (lower or upper
+  // body of the joint along the path); the coupling of the two joints -> B
+  for (int s = 0; s < n; ++s) {
+    const int k = kk[s], cs = Cs[s], o = s == 0 ? 0 : Cs[0];
+    double *dst = C.islot[e0 + s] == 0 ? C.Dfirst : C.Dsecond;
     for (int r = 0; r < 5; ++r)
       for (int c = 0; c <= r; ++c)
-        C.Dfirst[(size_t)pk(r, c) * K + k] = (r < c0 && c < c0) ? Gm[r][c] : 0.0;
+        dst[(size_t)pk(r, c) * K + k] = (r < cs && c < cs) ? Gm[o + r][o + c] : 0.0;
   }
   if (n == 2) {
-    const int k = kk[1], c0 = Cs[0], c1 = Cs[1];
-    for (int r = 0; r < 5; ++r)
-      for (int c = 0; c <= r; ++c)
-        C.Dsecond[(size_t)pk(r, c) * K + k] = (r < c1 && c < c1) ? Gm[c0 + r][c0 + c] : 0.0;
+    const int c0 = Cs[0], c1 = Cs[1];
     const int k0 = kk[0];
     for (int r = 0; r < 5; ++r)
       for (int c = 0; c < 5; ++c)

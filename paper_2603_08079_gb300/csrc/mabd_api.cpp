@@ -52,6 +52,13 @@ struct mabd_ctx {
   DevIncidence I{};
   DevChain C{};
   std::vector<CRLevel> levels;
+  DevTree T{};
+  DevPCG P{};
+  int pcg_last_iters = 0;
+  double pcg_last_rel = 0.0;
+  int *h_iter = nullptr;     // pinned [2]
+  double *h_scal = nullptr;  // pinned [8]
+  std::vector<int32_t> tree_lvl;  // level offsets (internal body order)
   double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
   int *d_status = nullptr;
   unsigned long long *d_max = nullptr;
@@ -229,6 +236,131 @@ bool chain_order(const Graph &g, std::vector<int32_t> &border, std::vector<int32
   return true;
 }
 
+// A forest: joints between free bodies form a forest and one-sided joints
+// (to the world or a fixed body) sit on at most one body of each component,
+// which becomes its root (at most two such joints, Sec. 5.3).  Bodies are
+// ordered breadth-first over all roots at once, so each level is a range and
+// the children of a body are a range; joints follow their body.
+struct TreeOrder {
+  std::vector<int32_t> border, jorder, lvl_off, parent, pjoint, cfirst, ccount, root_id;
+  std::vector<int8_t> pside;
+  std::vector<int32_t> root_joint;  // [2][nroots] user joint ids
+  std::vector<int8_t> root_side;
+  int nroots = 0;
+};
+
+bool tree_order(const mabd_ctx *ctx, const Graph &g, TreeOrder &t) {
+  const int M = g.M;
+  std::vector<int> comp(M, -1), roots;
+  int ncomp = 0;
+  for (int s = 0; s < M; ++s) {
+    if (!g.free_body[s] || comp[s] >= 0) continue;
+    std::vector<int> q{s};
+    comp[s] = ncomp;
+    int root = -1, nroot_cand = 0;
+    long edges2 = 0;
+    for (size_t h = 0; h < q.size(); ++h) {
+      int j = q[h];
+      int nside = 0;
+      for (int k : g.inc[j]) {
+        int o = other_end(g, k, j);
+        if (o < 0) {
+          ++nside;
+          continue;
+        }
+        ++edges2;
+        if (comp[o] < 0) {
+          comp[o] = ncomp;
+          q.push_back(o);
+        }
+      }
+      if (nside > 0) {
+        ++nroot_cand;
+        root = j;
+        if (nside > 2) return false;
+      }
+    }
+    if (edges2 != 2L * ((long)q.size() - 1) || nroot_cand > 1) return false;
+    roots.push_back(root >= 0 ? root : s);
+    ++ncomp;
+  }
+  t.nroots = (int)roots.size();
+  t.border.clear();
+  t.lvl_off.assign(1, 0);
+  std::vector<int> depth(M, -1), par(M, -1), pj(M, -1);
+  std::vector<int> frontier = roots;
+  for (int r : roots) depth[r] = 0;
+  while (!frontier.empty()) {
+    std::vector<int> next;
+    for (int j : frontier) {
+      t.border.push_back(j);
+      std::vector<int> ks;
+      for (int k : g.inc[j]) {
+        int o = other_end(g, k, j);
+        if (o >= 0 && o != par[j]) ks.push_back(k);
+      }
+      std::sort(ks.begin(), ks.end());
+      for (int k : ks) {
+        int o = other_end(g, k, j);
+        if (depth[o] >= 0) return false;
+        depth[o] = depth[j] + 1;
+        par[o] = j;
+        pj[o] = k;
+        next.push_back(o);
+      }
+    }
+    t.lvl_off.push_back((int32_t)t.border.size());
+    frontier.swap(next);
+  }
+  const int nfree = (int)t.border.size();
+  for (int j = 0; j < M; ++j)
+    if (!g.free_body[j]) t.border.push_back(j);
+  std::vector<int> pos(M);
+  for (int i = 0; i < M; ++i) pos[t.border[i]] = i;
+  // joints in body order: a root's one-sided joints, else the parent joint
+  t.jorder.clear();
+  t.root_joint.assign(2 * (size_t)std::max(t.nroots, 1), -1);
+  t.root_side.assign(2 * (size_t)std::max(t.nroots, 1), 0);
+  t.parent.assign(M, -1);
+  t.pjoint.assign(M, -1);
+  t.pside.assign(M, 0);
+  t.cfirst.assign(M, 0);
+  t.ccount.assign(M, 0);
+  t.root_id.assign(M, -1);
+  int rid = 0;
+  for (int i = 0; i < nfree; ++i) {
+    const int j = t.border[i];
+    if (par[j] < 0) {
+      t.root_id[i] = rid;
+      int w = 0;
+      std::vector<int> side;
+      for (int k : g.inc[j])
+        if (other_end(g, k, j) < 0) side.push_back(k);
+      std::sort(side.begin(), side.end());
+      for (int k : side) {
+        t.root_joint[(size_t)w * t.nroots + rid] = k;
+        t.root_side[(size_t)w * t.nroots + rid] = ctx->joints[k].body_a == j ? 0 : 1;
+        ++w;
+        t.jorder.push_back(k);
+      }
+      ++rid;
+    } else {
+      t.parent[i] = pos[par[j]];
+      t.pjoint[i] = pj[j];  // user id
+      t.pside[i] = ctx->joints[pj[j]].body_a == j ? 0 : 1;
+      t.jorder.push_back(pj[j]);
+    }
+  }
+  if ((int)t.jorder.size() != g.K) return false;
+  for (int i = nfree - 1; i >= 0; --i) {
+    const int p = t.parent[i];
+    if (p < 0) continue;
+    t.ccount[p] += 1;
+    t.cfirst[p] = i;  // children of a body are contiguous; the smallest index wins
+  }
+  return true;
+}
+
 // --------------------------------------------------------------------------
 // per-body structured inverse of Hbar_A = M_A/h^2 + Kbar_A (Eq. abd_final)
 // --------------------------------------------------------------------------
@@ -348,6 +480,8 @@ mabd_status ensure_stage(mabd_ctx *ctx, size_t n) {
   }
   if (ctx->h_stage_n >= n) return MABD_OK;
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->h_iter) cudaFreeHost(ctx->h_iter);
+  if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   ctx->h_stage = nullptr;
   ctx->h_stage_n = 0;
   CK(cudaMallocHost((void **)&ctx->h_stage, n * sizeof(double)));
@@ -479,23 +613,33 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   }
   // ---- topology and ordering
   Graph g = build_graph(ctx);
-  std::vector<int32_t> border, jorder;
-  bool is_chain = K > 0 && chain_order(g, border, jorder);
+  std::vector<int32_t> border, jorder, cborder, cjorder;
+  TreeOrder tord;
+  const bool is_chain = K > 0 && chain_order(g, cborder, cjorder);
+  const bool is_tree = K > 0 && tree_order(ctx, g, tord);
   int solver = ctx->cfg.solver;
   if (K == 0) {
     ctx->topology = MABD_TOPO_NONE;
     solver = MABD_SOLVER_AUTO;
+  } else {
+    ctx->topology = is_chain ? MABD_TOPO_CHAIN : (is_tree ? MABD_TOPO_TREE : MABD_TOPO_GRAPH);
+    if (solver == MABD_SOLVER_AUTO)
+      solver = is_chain ? MABD_SOLVER_CHAIN : (is_tree ? MABD_SOLVER_TREE : MABD_SOLVER_PCG);
+  }
+  if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
+  if (solver == MABD_SOLVER_TREE && !is_tree) return MABD_ERR_UNSUPPORTED;
+  if (solver == MABD_SOLVER_CHAIN) {
+    border = cborder;
+    jorder = cjorder;
+  } else if (solver == MABD_SOLVER_TREE) {
+    border = tord.border;
+    jorder = tord.jorder;
+  } else {
     border.resize(M);
     for (int j = 0; j < M; ++j) border[j] = j;
-  } else if (is_chain) {
-    ctx->topology = MABD_TOPO_CHAIN;
-    if (solver == MABD_SOLVER_AUTO) solver = MABD_SOLVER_CHAIN;
-  } else {
-    ctx->topology = MABD_TOPO_GRAPH;
-    if (solver == MABD_SOLVER_AUTO) solver = MABD_SOLVER_PCG;
+    jorder.resize(K);
+    for (int k = 0; k < K; ++k) jorder[k] = k;
   }
-  if (K > 0 && solver != MABD_SOLVER_CHAIN) return MABD_ERR_UNSUPPORTED;
-  if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
   ctx->solver = solver;
   ctx->body_of_internal = border;
   ctx->internal_of_body.assign(M, -1);
@@ -579,15 +723,23 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       }
     }
   }
+  // chain: a joint's diagonal block collects one part from each of its free
+  // bodies, the lower one along the path (slot 0) and the upper one (slot 1)
   std::vector<uint8_t> cfl(K, 0);
+  std::vector<int8_t> islot(std::max<size_t>(ijoint.size(), 1), 0);
   if (solver == MABD_SOLVER_CHAIN) {
     for (int j = 0; j < M; ++j) {
       const int n = ioff[j + 1] - ioff[j];
-      if (n >= 1) cfl[ijoint[ioff[j]]] |= 1;
-      if (n == 2) {
-        cfl[ijoint[ioff[j] + 1]] |= 2;
-        cfl[ijoint[ioff[j]]] |= 4;
+      for (int e = ioff[j]; e < ioff[j + 1]; ++e) {
+        const int k = ijoint[e];
+        int other = -1;
+        if (iside[e] == 0 && (jfl[k] & JF_B_FREE)) other = jb[k];
+        if (iside[e] == 1 && (jfl[k] & JF_A_FREE)) other = ja[k];
+        const int slot = (other >= 0 && other < j) ? 1 : 0;
+        islot[e] = (int8_t)slot;
+        cfl[k] |= slot == 0 ? 1 : 2;
       }
+      if (n == 2) cfl[ijoint[ioff[j]]] |= 4;
     }
   }
 
@@ -681,6 +833,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     C.Dsecond = dnew<double>(ctx, 15 * (size_t)K, ok);
     C.B = dnew<double>(ctx, 25 * (size_t)K, ok);
     uint8_t *dcf = dnew<uint8_t>(ctx, K, ok);
+    int8_t *dslot = dnew<int8_t>(ctx, islot.size(), ok);
     // cyclic-reduction levels
     ctx->levels.clear();
     int N = K;
@@ -711,7 +864,80 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       return MABD_ERR_OUT_OF_MEMORY;
     }
     CK(up(dcf, cfl.data(), cfl.size()));
+    CK(up(dslot, islot.data(), islot.size()));
     C.jflags = dcf;
+    C.islot = dslot;
+  }
+  if (solver == MABD_SOLVER_PCG) {
+    DevPCG &P = ctx->P;
+    P.nblocks = (K + 127) / 128;
+    P.r = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+    P.z = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+    P.p = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+    P.Sp = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+    P.zb = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+    P.Lpre = dnew<double>(ctx, 15 * (size_t)Kx, ok);
+    P.part = dnew<double>(ctx, 2 * (size_t)std::max(P.nblocks, 1), ok);
+    P.scal = dnew<double>(ctx, 8, ok);
+    P.iter = dnew<int>(ctx, 2, ok);
+    if (!ok) {
+      free_all(ctx);
+      return MABD_ERR_OUT_OF_MEMORY;
+    }
+    if (!ctx->h_iter) {
+      CK(cudaMallocHost((void **)&ctx->h_iter, 2 * sizeof(int)));
+      CK(cudaMallocHost((void **)&ctx->h_scal, 8 * sizeof(double)));
+    }
+  }
+  if (solver == MABD_SOLVER_TREE) {
+    DevTree &T = ctx->T;
+    const int nr = std::max(tord.nroots, 1);
+    std::vector<int32_t> rj(2 * (size_t)nr, -1);
+    for (int i = 0; i < 2 * tord.nroots; ++i)
+      rj[i] = tord.root_joint[i] >= 0 ? ctx->internal_of_joint[tord.root_joint[i]] : -1;
+    T.nroots = tord.nroots;
+    int32_t *dpar = dnew<int32_t>(ctx, Mx, ok);
+    int32_t *dpj = dnew<int32_t>(ctx, Mx, ok);
+    int8_t *dps = dnew<int8_t>(ctx, Mx, ok);
+    int32_t *dcf = dnew<int32_t>(ctx, Mx, ok);
+    int32_t *dcc = dnew<int32_t>(ctx, Mx, ok);
+    int32_t *drid = dnew<int32_t>(ctx, Mx, ok);
+    int32_t *drj = dnew<int32_t>(ctx, rj.size(), ok);
+    int8_t *drs = dnew<int8_t>(ctx, tord.root_side.size(), ok);
+    T.X = dnew<double>(ctx, 60 * (size_t)Mx, ok);
+    T.LD = dnew<double>(ctx, 15 * (size_t)Mx, ok);
+    T.y = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+    T.e = dnew<double>(ctx, 5 * (size_t)Mx, ok);
+    T.U = dnew<double>(ctx, 60 * (size_t)Mx, ok);
+    T.v = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+    T.dq = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+    T.rX = dnew<double>(ctx, 120 * (size_t)nr, ok);
+    T.rLD = dnew<double>(ctx, 55 * (size_t)nr, ok);
+    T.re = dnew<double>(ctx, 10 * (size_t)nr, ok);
+    if (!ok) {
+      free_all(ctx);
+      return MABD_ERR_OUT_OF_MEMORY;
+    }
+    std::vector<int32_t> tpj(M, -1);
+    for (int i = 0; i < M; ++i)
+      if (tord.parent[i] >= 0) tpj[i] = ctx->internal_of_joint[tord.pjoint[i]];
+    CK(up(dpar, tord.parent.data(), (size_t)M * 4));
+    CK(up(dpj, tpj.data(), (size_t)M * 4));
+    CK(up(dps, tord.pside.data(), (size_t)M));
+    CK(up(dcf, tord.cfirst.data(), (size_t)M * 4));
+    CK(up(dcc, tord.ccount.data(), (size_t)M * 4));
+    CK(up(drid, tord.root_id.data(), (size_t)M * 4));
+    CK(up(drj, rj.data(), rj.size() * 4));
+    CK(up(drs, tord.root_side.data(), tord.root_side.size()));
+    T.parent = dpar;
+    T.pjoint = dpj;
+    T.pside = dps;
+    T.cfirst = dcf;
+    T.ccount = dcc;
+    T.root_id = drid;
+    T.root_joint = drj;
+    T.root_side = drs;
+    ctx->tree_lvl = tord.lvl_off;
   }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->sp.h = h;
@@ -720,6 +946,42 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   ctx->sp.residual_rhs = ctx->cfg.residual_rhs ? 1 : 0;
   ctx->frozen = true;
   return MABD_OK;
+}
+
+// Block-Jacobi PCG on the dual.  Iterations are enqueued in chunks; between
+// chunks the host reads the device's iteration count and convergence flag
+// (the kernels of a converged iteration return immediately), so the loop is
+// bounded by pcg_max_iters and nothing on the device waits.
+static mabd_status pcg_solve(mabd_ctx *ctx) {
+  cudaStream_t s = ctx->stream;
+  const int max_it = ctx->cfg.pcg_max_iters;
+  run(ctx, "pcg_setup", [&] { launch_pcg_setup(ctx->B, ctx->J, ctx->P, ctx->cfg.pcg_rtol, ctx->d_status, s); });
+  const int chunk = 16;
+  int done = 0;
+  for (int launched = 0; launched < max_it && !done;) {
+    const int n = std::min(chunk, max_it - launched);
+    for (int i = 0; i < n; ++i)
+      run(ctx, "pcg_iteration", [&] { launch_pcg_iteration(ctx->B, ctx->J, ctx->I, ctx->P, max_it, s); });
+    launched += n;
+    CK(cudaMemcpyAsync(ctx->h_iter, ctx->P.iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    done = ctx->h_iter[1];
+  }
+  CK(cudaMemcpyAsync(ctx->h_scal, ctx->P.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ctx->h_iter, ctx->P.iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ctx->pcg_last_iters = ctx->h_iter[0];
+  const double bb = ctx->h_scal[4], rr = ctx->h_scal[3];
+  ctx->pcg_last_rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+  if (!(rr <= ctx->h_scal[5] * bb)) {
+    int bits = ST_PCG_NOCONV;
+    CK(cudaMemcpyAsync(&bits, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bits |= ST_PCG_NOCONV;
+    CK(cudaMemcpyAsync(ctx->d_status, &bits, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return cuda_fail(ctx, cudaGetLastError());
 }
 
 static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
@@ -745,7 +1007,20 @@ static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
         run(ctx, "cr_back", [&] { launch_cr_back(ctx->levels[l], ctx->levels[l + 1], s); });
     }
   }
-  run(ctx, "backprop", [&] { launch_backprop(ctx->B, ctx->J, ctx->I, p, ctx->d_status, s); });
+  if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE) {
+    const auto &lv = ctx->tree_lvl;
+    const int nl = (int)lv.size() - 1;
+    for (int l = nl - 1; l >= 0; --l)
+      run(ctx, "tree_up", [&] { launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+    for (int l = 0; l < nl; ++l)
+      run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+  } else {
+    if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_PCG) {
+      mabd_status st = pcg_solve(ctx);
+      if (st) return st;
+    }
+    run(ctx, "backprop", [&] { launch_backprop(ctx->B, ctx->J, ctx->I, p, ctx->d_status, s); });
+  }
   if (maxbits && ctx->J.K > 0)
     run(ctx, "residuals", [&] { launch_residuals(ctx->B, ctx->J, p, maxbits, ctx->d_status, s); });
   cudaError_t e = cudaGetLastError();
@@ -766,9 +1041,15 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
     }
     CK(cudaMemsetAsync(ctx->d_max, 0, 2 * (size_t)nsteps * 8, ctx->stream));
   }
+  std::vector<int> pit(nsteps, 0);
+  std::vector<double> prel(nsteps, 0.0);
   for (int i = 0; i < nsteps; ++i) {
     mabd_status st = step_once(ctx, stats ? ctx->d_max + 2 * i : nullptr);
     if (st) return st;
+    if (ctx->solver == MABD_SOLVER_PCG) {
+      pit[i] = ctx->pcg_last_iters;
+      prel[i] = ctx->pcg_last_rel;
+    }
   }
   if (!stats) return MABD_OK;
   std::vector<unsigned long long> hb(2 * (size_t)nsteps);
@@ -780,8 +1061,8 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
     std::memcpy(&nl, &hb[2 * i + 1], 8);
     stats[i].lin_residual = lin;
     stats[i].joint_residual = nl;
-    stats[i].pcg_iters = 0;
-    stats[i].pcg_rel_residual = 0.0;
+    stats[i].pcg_iters = pit[i];
+    stats[i].pcg_rel_residual = prel[i];
     stats[i].refine_residual = 0.0;
   }
   return read_status(ctx);
@@ -890,7 +1171,8 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
   mabd_status st = harvest_profile(ctx);
   if (st) return st;
   static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "cr_reduce", "cr_combine",
-                                "cr_top", "cr_back", "backprop", "residuals"};
+                                "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
+                                "pcg_iteration", "backprop", "residuals"};
   int n = 0;
   for (const char *k : known) {
     auto it = ctx->prof_acc.find(k);
@@ -915,6 +1197,8 @@ mabd_status mabd_destroy(mabd_ctx *ctx) {
   }
   free_all(ctx);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->h_iter) cudaFreeHost(ctx->h_iter);
+  if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
   delete ctx;
   return MABD_OK;

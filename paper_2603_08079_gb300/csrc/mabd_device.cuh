@@ -132,22 +132,6 @@ __device__ __forceinline__ void row_dir(int type, const double RH[9], int r, dou
   }
 }
 
-// y = Hbar^{-1} v with the structured inverse h[16] (see mabd_internal.h)
-__device__ __forceinline__ void hinv_apply(const double h[16], const double v[12], double y[12]) {
-  y[0] = h[1] * v[0] + h[2] * v[4] + h[3] * v[8];
-  y[4] = h[2] * v[0] + h[4] * v[4] + h[5] * v[8];
-  y[8] = h[3] * v[0] + h[5] * v[4] + h[6] * v[8];
-  y[1] = h[7] * v[1] + h[8] * v[3];
-  y[3] = h[8] * v[1] + h[9] * v[3];
-  y[2] = h[10] * v[2] + h[11] * v[6];
-  y[6] = h[11] * v[2] + h[12] * v[6];
-  y[5] = h[13] * v[5] + h[14] * v[7];
-  y[7] = h[14] * v[5] + h[15] * v[7];
-  y[9] = h[0] * v[9];
-  y[10] = h[0] * v[10];
-  y[11] = h[0] * v[11];
-}
-
 __device__ __forceinline__ void load_hinv(const DevBodies &B, int j, double h[16]) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) h[i] = ldg(B.hinv + (size_t)i * B.M + j);
@@ -167,6 +151,63 @@ __device__ __forceinline__ void load3(const double *p, int N, int j, double out[
   out[0] = ldg(p + j);
   out[1] = ldg(p + (size_t)N + j);
   out[2] = ldg(p + 2 * (size_t)N + j);
+}
+
+// Rows of joint k on the body with rotation R that is its side `side`
+// (0: body a, 1: body b): row r is s [p; 1] (x) (R^T d_r) in that body's rest
+// frame (frozen frame, Eq. pcpq), s = +1 on a and -1 on b.  Writes the
+// directions E[r], the points P[0..1] and the point index pt[r]; returns C.
+__device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int side,
+                                               const double R[9], double E[5][3],
+                                               double P[2][3], int pt[5]) {
+  const int K = J.K;
+  const int type = J.type[k];
+  const double sgn = side == 0 ? 1.0 : -1.0;
+  load3(side == 0 ? J.pa1 : J.pb1, K, k, P[0]);
+  double RH[9];
+  if (type == 1) {
+    load3(side == 0 ? J.pa2 : J.pb2, K, k, P[1]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) RH[i] = J.RH[(size_t)i * K + k];
+  }
+  const int C = type == 0 ? 3 : 5;
+  for (int r = 0; r < C; ++r) {
+    double d[3], e[3];
+    row_dir(type, RH, r, d);
+    mtv3(R, d, e);
+    E[r][0] = sgn * e[0];
+    E[r][1] = sgn * e[1];
+    E[r][2] = sgn * e[2];
+    pt[r] = r < 3 ? 0 : 1;
+  }
+  return C;
+}
+
+// w = [p; 1] (x) e as a 12-vector
+__device__ __forceinline__ void kron_row(const double p[3], const double e[3], double w[12]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    w[a] = p[0] * e[a];
+    w[3 + a] = p[1] * e[a];
+    w[6 + a] = p[2] * e[a];
+    w[9 + a] = e[a];
+  }
+}
+
+// y = Hbar^{-1} v with the structured inverse h[16] (see mabd_internal.h)
+__device__ __forceinline__ void hinv_apply(const double h[16], const double v[12], double y[12]) {
+  y[0] = h[1] * v[0] + h[2] * v[4] + h[3] * v[8];
+  y[4] = h[2] * v[0] + h[4] * v[4] + h[5] * v[8];
+  y[8] = h[3] * v[0] + h[5] * v[4] + h[6] * v[8];
+  y[1] = h[7] * v[1] + h[8] * v[3];
+  y[3] = h[8] * v[1] + h[9] * v[3];
+  y[2] = h[10] * v[2] + h[11] * v[6];
+  y[6] = h[11] * v[2] + h[12] * v[6];
+  y[5] = h[13] * v[5] + h[14] * v[7];
+  y[7] = h[14] * v[5] + h[15] * v[7];
+  y[9] = h[0] * v[9];
+  y[10] = h[0] * v[10];
+  y[11] = h[0] * v[11];
 }
 
 // atomic max of a non-negative double through its bit pattern

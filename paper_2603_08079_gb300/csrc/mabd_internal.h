@@ -72,10 +72,11 @@ struct DevIncidence {
 // chain dual blocks (block-tridiagonal, 5x5 padded, joint chain order)
 struct DevChain {
   int32_t K;
-  double *Dfirst;        // [15][K] contribution of the body for which the joint is its first
-  double *Dsecond;       // [15][K] ... its second joint
+  double *Dfirst;        // [15][K] contribution of the joint's lower body (path order)
+  double *Dsecond;       // [15][K] contribution of its upper body
   double *B;             // [25][K] coupling of joint k and k+1 (through their shared body)
-  const uint8_t *jflags; // [K] bit0: has first-body part, bit1: has second-body part, bit2: has B
+  const uint8_t *jflags; // [K] bit0: has lower-body part, bit1: has upper-body part, bit2: has B
+  const int8_t *islot;   // [nnz] per incidence entry: 0 -> Dfirst, 1 -> Dsecond
 };
 
 // one level of block cyclic reduction
@@ -86,6 +87,42 @@ struct CRLevel {
   double *b;             // [5][N]
   double *fac;           // [70][N/2] L, Ya, Yb, y of the odd rows
   double *lam;           // [5][N]
+};
+
+// tree (forest) of free bodies in breadth-first order: levels are contiguous
+// ranges and the children of a body are a contiguous range
+struct DevTree {
+  const int32_t *parent;      // [M] parent body (internal index) or -1
+  const int32_t *pjoint;      // [M] joint to the parent (internal index) or -1
+  const int8_t *pside;        // [M] side of the body in that joint (0: a, 1: b)
+  const int32_t *cfirst;      // [M] first child
+  const int32_t *ccount;      // [M] number of children
+  const int32_t *root_id;     // [M] index among roots, -1 otherwise
+  const int32_t *root_joint;  // [2][nroots] one-sided joints of a root (-1: none)
+  const int8_t *root_side;    // [2][nroots]
+  int32_t nroots;
+  double *X;                  // [60][M]  Hhat^{-1} G^T in the rest frame (12 x 5)
+  double *LD;                 // [15][M]  Cholesky factor of D = G Hhat^{-1} G^T
+  double *y;                  // [12][M]  Hhat^{-1} fhat (rest frame)
+  double *e;                  // [5][M]   G y + C(q_n)
+  double *U;                  // [60][M]  P^T L_D^{-T} in the parent's rest frame (12 x 5)
+  double *v;                  // [12][M]  P^T D^{-1} e in the parent's rest frame
+  double *dq;                 // [12][M]  world-frame increment of the step
+  double *rX;                 // [120][nroots] roots: Hhat^{-1} G_w^T (12 x 10)
+  double *rLD;                // [55][nroots]
+  double *re;                 // [10][nroots]
+};
+
+// dual-space preconditioned conjugate gradients (graphs).  Vectors are
+// [5][K] (rows beyond C_k stay zero); scalars live on the device.
+struct DevPCG {
+  double *r, *z, *p, *Sp;     // [5][K]
+  double *zb;                 // [12][M] Hbar^{-1} diag4(R^T) G^T p (rest frame)
+  double *Lpre;               // [15][K] Cholesky of the diagonal blocks D_k
+  double *part;               // [2][nblocks] per-block partial sums
+  double *scal;               // [8]: rz, alpha, beta, rr, bnorm2, rtol2, pSp, spare
+  int *iter;                  // [2]: iterations done, converged flag
+  int nblocks;
 };
 
 struct StepParams {
@@ -116,5 +153,17 @@ void launch_cr_combine(const DevChain &C, const DevJoints &J, const CRLevel &cur
 void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,
                    int *status, cudaStream_t s);
 void launch_cr_back(const CRLevel &cur, const CRLevel &next, cudaStream_t s);
+
+// tree (k_tree.cu): one launch per level, deepest first, then root first
+void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,
+                    const StepParams &p, int *status, cudaStream_t s);
+void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,
+                      const StepParams &p, int *status, cudaStream_t s);
+
+// PCG (k_pcg.cu)
+void launch_pcg_setup(const DevBodies &B, const DevJoints &J, const DevPCG &P, double rtol,
+                      int *status, cudaStream_t s);
+void launch_pcg_iteration(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                          const DevPCG &P, int max_iters, cudaStream_t s);
 
 }  // namespace mabd
