@@ -130,15 +130,43 @@ def measured_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def kernel_model(name: str, M: int, K: int, nh: int):
-    """(bytes, flops) the method must move / compute in one launch of `name`
-    (all levels for the cyclic-reduction kernels are summed by the caller)."""
+def cr_reduce_flops(jtype_chain: np.ndarray) -> float:
+    """FP64 flops of block cyclic reduction over all levels (FMA = 2): for an
+    eliminated row of size n with neighbours of sizes l, r (0 if absent):
+    Cholesky 2*chol(n) + n rsqrt-multiplies, Ya/Yb/y triangular solves
+    (l + r + 1) n(n+1)/2 FMA, Schur updates (l(l+1)/2 + r(r+1)/2 + l r + l + r) n FMA."""
+    sizes = np.where(np.asarray(jtype_chain) == 1, 5, 3).astype(np.int64)
+    chol = {3: 7, 5: 30}
+    total = 0.0
+    while len(sizes) > 1:
+        N = len(sizes)
+        odd = np.arange(1, N, 2)
+        n = sizes[odd]
+        l = sizes[odd - 1]
+        r = np.where(odd + 1 < N, sizes[np.minimum(odd + 1, N - 1)], 0)
+        fma = np.vectorize(chol.get)(n) + (l + r + 1) * n * (n + 1) // 2 + \
+            (l * (l + 1) // 2 + r * (r + 1) // 2 + l * r + l + r) * n
+        total += 2.0 * float(fma.sum()) + 2.0 * float(n.sum())
+        sizes = sizes[0::2]
+    return total
+
+
+def chain_gram_flops(jtype_chain: np.ndarray) -> float:
+    """FP64 flops of the per-body Gram blocks (FMA = 2): a body with n rows
+    forms n rest-frame rows (12 FMA each), applies the structured Hbar^{-1}
+    (9 + 24 FMA per row) and n(n+1)/2 row products (15 FMA each)."""
+    rows = np.where(np.asarray(jtype_chain) == 1, 5, 3).astype(np.int64)
+    n = rows[:-1] + rows[1:]          # body j carries joints j and j+1 (both ends pinned)
+    return 2.0 * float((45 * n + 15 * n * (n + 1) // 2).sum())
+
+
+def kernel_model(name: str, jtype_chain: np.ndarray):
+    """Algorithmic FP64 flops of one step's launches of `name` (all levels)."""
+    if name.startswith("cr_reduce"):
+        return cr_reduce_flops(jtype_chain)
     if name == "chain_gram":
-        # per body: R (72 B) + hinv (128 B) + joint rows (RH 72 B x2 + points) in, D/B out
-        return M * (72 + 128 + 2 * 72 + 96 + 8 * (15 + 15 + 25)), M * 2 * 520
-    if name == "body_prep":
-        return M * (24 * 8 + 16 * 8 + 6 * 8 + (9 + 12) * 8), M * 2 * 330
-    return None, None
+        return chain_gram_flops(jtype_chain)
+    return None
 
 
 def run_gpu(args):
@@ -213,20 +241,20 @@ def run_gpu(args):
 
     result = None
     if rank == 0:
-        peaks, src = measured_peaks()
         dom = max(kt.items(), key=lambda kv: kv[1][0])
         dname, (dms, dn) = dom
         per_launch_ms = dms / dn
-        nh = M // 2
-        byts, flops = kernel_model(dname, M, info["joints"], nh)
-        if flops is not None:
+        launches_per_step = dn / args.profile_steps
+        step_flops = kernel_model(dname, sc["jtype"])
+        if step_flops is not None:
+            flops = step_flops / launches_per_step     # per launch, averaged over the levels
             achieved = flops / (per_launch_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                    "traffic": None, "kernel": dname, "peak_source": "FP64 unit counts x 2.07 GHz",
-                    "kernel_ms_per_launch": round(per_launch_ms, 4),
-                    "algorithmic_bytes_per_launch": byts,
-                    "hbm_frac_of_measured": round(byts / (per_launch_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)}
+                    "traffic": None, "kernel": dname,
+                    "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz (probe measured 1.20)",
+                    "kernel_ms_per_launch": round(per_launch_ms, 5),
+                    "flops_per_step": step_flops, "launches_per_step": launches_per_step}
         else:
             roof = {"bound": "alu", "achieved": None, "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": dname}

@@ -177,6 +177,10 @@ mabd_status mabd_profile_reset(mabd_ctx *ctx);
 mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, double *ms,
                               int64_t *launches, int32_t *count);
 
+/* Text of the last CUDA failure seen by the context (error name, message and
+   the host source line), or "" if none; owned by the context. */
+const char *mabd_error_detail(mabd_ctx *ctx);
+
 mabd_status mabd_destroy(mabd_ctx *ctx);
 const char *mabd_status_string(mabd_status s);
 

@@ -206,8 +206,134 @@ __device__ __forceinline__ void ld_b(const DevJoints &J, const CRLevel &L, int l
   }
 }
 
-// Factor record of an eliminated row (70 doubles): L (packed 15), Ya (25),
-// Yb (25), y (5).  Contributions to a neighbour: packed 15 + 5.
+// Factor record of an eliminated row (70 doubles): L (packed 15, with the
+// reciprocals of its diagonal stored on the diagonal), Ya (25), Yb (25), y (5).
+// Contributions to a neighbour: packed 15 + 5.  Blocks keep the 5x5 padded
+// layout in memory; the arithmetic runs on the true sizes (3 or 5 rows, and 0
+// for a missing right neighbour), chosen per row from the joint types.
+
+// size of row n at `level`: that row is joint n * 2^level of the chain
+__device__ __forceinline__ int row_size(const DevJoints &J, int level, int n) {
+  return J.type[(size_t)n << level] == 0 ? 3 : 5;
+}
+
+template <int CN, int CL, int CR>
+__device__ __forceinline__ void reduce_row(const DevChain &C, const DevJoints &J, const CRLevel &cur,
+                                           int level, int n, int m, int Nh, double *cL, double *cR,
+                                           double *Bn, int *status) {
+  // D_n, B_{n-1} (CL x CN), B_n (CN x CR), b_n
+  double D[25], Bl[25], Br[25], bn[5];
+  ld_D(C, J, cur, level, n, D);
+  ld_B(C, cur, level, n - 1, Bl);
+  if (CR > 0) ld_B(C, cur, level, n, Br);
+  ld_b(J, cur, level, n, bn);
+  // Cholesky with reciprocal diagonal
+  double L[CN][CN], id[CN];
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < CN; ++c) {
+    double sum = D[5 * c + c];
+#pragma unroll
+    for (int k = 0; k < c; ++k) sum -= L[c][k] * L[c][k];
+    if (!(sum > 0.0)) {
+      ok = false;
+      sum = 1.0;
+    }
+    id[c] = rsqrt(sum);
+    L[c][c] = sum * id[c];
+#pragma unroll
+    for (int r = c + 1; r < CN; ++r) {
+      double t = D[5 * r + c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) t -= L[r][k] * L[c][k];
+      L[r][c] = t * id[c];
+    }
+  }
+  if (!ok) set_status(status, ST_NOT_SPD);
+  // Ya = L^{-1} B_{n-1}^T (CN x CL), Yb = L^{-1} B_n (CN x CR), y = L^{-1} b
+  double Ya[CN][CL > 0 ? CL : 1], Yb[CN][CR > 0 ? CR : 1], y[CN];
+#pragma unroll
+  for (int i = 0; i < CN; ++i) {
+#pragma unroll
+    for (int c = 0; c < CL; ++c) {
+      double t = Bl[5 * c + i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) t -= L[i][k] * Ya[k][c];
+      Ya[i][c] = t * id[i];
+    }
+#pragma unroll
+    for (int c = 0; c < CR; ++c) {
+      double t = Br[5 * i + c];
+#pragma unroll
+      for (int k = 0; k < i; ++k) t -= L[i][k] * Yb[k][c];
+      Yb[i][c] = t * id[i];
+    }
+    double t = bn[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+    y[i] = t * id[i];
+  }
+  double *f = cur.fac;
+  {
+    int o = 0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) {
+        double v = 0.0;
+        if (r < CN) v = (r == c) ? id[r] : L[r][c];
+        f[(size_t)(o++) * Nh + m] = v;
+      }
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        f[(size_t)(15 + 5 * r + c) * Nh + m] = (r < CN && c < CL) ? Ya[r][c] : 0.0;
+        f[(size_t)(40 + 5 * r + c) * Nh + m] = (r < CN && c < CR) ? Yb[r][c] : 0.0;
+      }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) f[(size_t)(65 + r) * Nh + m] = r < CN ? y[r] : 0.0;
+  }
+  // neighbour updates: -Ya^T Ya, -Ya^T y to row n-1; -Yb^T Yb, -Yb^T y to row n+1;
+  // new coupling -Ya^T Yb between them
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+#pragma unroll
+    for (int c = 0; c <= r; ++c) {
+      double sa = 0.0, sb = 0.0;
+      if (r < CL && c < CL) {
+#pragma unroll
+        for (int t = 0; t < CN; ++t) sa += Ya[t][r] * Ya[t][c];
+      }
+      if (r < CR && c < CR) {
+#pragma unroll
+        for (int t = 0; t < CN; ++t) sb += Yb[t][r] * Yb[t][c];
+      }
+      cL[(size_t)pk(r, c) * Nh + m] = sa;
+      cR[(size_t)pk(r, c) * Nh + m] = sb;
+    }
+    double ta = 0.0, tb = 0.0;
+    if (r < CL) {
+#pragma unroll
+      for (int t = 0; t < CN; ++t) ta += Ya[t][r] * y[t];
+    }
+    if (r < CR) {
+#pragma unroll
+      for (int t = 0; t < CN; ++t) tb += Yb[t][r] * y[t];
+    }
+    cL[(size_t)(15 + r) * Nh + m] = ta;
+    cR[(size_t)(15 + r) * Nh + m] = tb;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      double sab = 0.0;
+      if (r < CL && c < CR) {
+#pragma unroll
+        for (int t = 0; t < CN; ++t) sab += Ya[t][r] * Yb[t][c];
+      }
+      Bn[(size_t)(5 * r + c) * Nh + m] = -sab;
+    }
+  }
+}
 
 // Odd row n = 2m+1 of the current level:
 //   L L^T = D_n, Ya = L^{-1} B_{n-1}^T, Yb = L^{-1} B_n, y = L^{-1} b_n;
@@ -220,75 +346,18 @@ __global__ void __launch_bounds__(128) k_cr_reduce(DevChain C, DevJoints J, CRLe
   const int N = cur.N;
   if (n >= N) return;
   const int Nh = N / 2;
-  double D[25], L[25], Bl[25], Br[25], bn[5];
-  ld_D(C, J, cur, level, n, D);
-  ld_B(C, cur, level, n - 1, Bl);
-  if (n + 1 < N) ld_B(C, cur, level, n, Br);
-  else {
-#pragma unroll
-    for (int i = 0; i < 25; ++i) Br[i] = 0.0;
-  }
-  ld_b(J, cur, level, n, bn);
-  if (!chol5(D, L)) set_status(status, ST_NOT_SPD);
-  double Ya[25], Yb[25], y[5];
-  // columns of Ya: L^{-1} (column c of B_{n-1}^T) = L^{-1} (row c of B_{n-1})
-#pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    double col[5], x[5];
-#pragma unroll
-    for (int r = 0; r < 5; ++r) col[r] = Bl[5 * c + r];
-    lsolve5(L, col, x);
-#pragma unroll
-    for (int r = 0; r < 5; ++r) Ya[5 * r + c] = x[r];
-#pragma unroll
-    for (int r = 0; r < 5; ++r) col[r] = Br[5 * r + c];
-    lsolve5(L, col, x);
-#pragma unroll
-    for (int r = 0; r < 5; ++r) Yb[5 * r + c] = x[r];
-  }
-  lsolve5(L, bn, y);
-  double *f = cur.fac;
-  {
-    int o = 0;
-#pragma unroll
-    for (int r = 0; r < 5; ++r)
-#pragma unroll
-      for (int c = 0; c <= r; ++c) f[(size_t)(o++) * Nh + m] = L[5 * r + c];
-#pragma unroll
-    for (int i = 0; i < 25; ++i) f[(size_t)(15 + i) * Nh + m] = Ya[i];
-#pragma unroll
-    for (int i = 0; i < 25; ++i) f[(size_t)(40 + i) * Nh + m] = Yb[i];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) f[(size_t)(65 + i) * Nh + m] = y[i];
-  }
-#pragma unroll
-  for (int r = 0; r < 5; ++r) {
-#pragma unroll
-    for (int c = 0; c <= r; ++c) {
-      double sa = 0.0, sb = 0.0;
-#pragma unroll
-      for (int t = 0; t < 5; ++t) {
-        sa += Ya[5 * t + r] * Ya[5 * t + c];
-        sb += Yb[5 * t + r] * Yb[5 * t + c];
-      }
-      cL[(size_t)pk(r, c) * Nh + m] = sa;
-      cR[(size_t)pk(r, c) * Nh + m] = sb;
-    }
-    double ta = 0.0, tb = 0.0;
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-      ta += Ya[5 * t + r] * y[t];
-      tb += Yb[5 * t + r] * y[t];
-    }
-    cL[(size_t)(15 + r) * Nh + m] = ta;
-    cR[(size_t)(15 + r) * Nh + m] = tb;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double s = 0.0;
-#pragma unroll
-      for (int t = 0; t < 5; ++t) s += Ya[5 * t + r] * Yb[5 * t + c];
-      Bn[(size_t)(5 * r + c) * Nh + m] = -s;
-    }
+  const int cn = row_size(J, level, n), cl = row_size(J, level, n - 1);
+  const int cr = n + 1 < N ? row_size(J, level, n + 1) : 0;
+  const int code = (cn == 5 ? 9 : 0) + (cl == 5 ? 3 : 0) + (cr == 5 ? 2 : (cr == 3 ? 1 : 0));
+  switch (code) {
+#define RED(CODE, A, B, D_) \
+  case CODE: reduce_row<A, B, D_>(C, J, cur, level, n, m, Nh, cL, cR, Bn, status); break;
+    RED(0, 3, 3, 0) RED(1, 3, 3, 3) RED(2, 3, 3, 5)
+    RED(3, 3, 5, 0) RED(4, 3, 5, 3) RED(5, 3, 5, 5)
+    RED(9, 5, 3, 0) RED(10, 5, 3, 3) RED(11, 5, 3, 5)
+    RED(12, 5, 5, 0) RED(13, 5, 5, 3) RED(14, 5, 5, 5)
+#undef RED
+    default: break;
   }
 }
 
@@ -340,7 +409,37 @@ __global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *s
 
 // Back-substitution: even rows copy from the next level, odd rows solve
 // lambda_n = L^{-T}(y - Ya lambda_{n-1} - Yb lambda_{n+1}).
-__global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next) {
+template <int CN, int CL, int CR>
+__device__ __forceinline__ void back_row(const CRLevel &cur, const CRLevel &next, int n) {
+  const int N = cur.N, m = (n - 1) / 2, Nh = N / 2;
+  const double *f = cur.fac;
+  double lL[5], lR[5], v[CN], x[CN];
+#pragma unroll
+  for (int r = 0; r < CL; ++r) lL[r] = next.lam[(size_t)r * next.N + m];
+#pragma unroll
+  for (int r = 0; r < CR; ++r) lR[r] = next.lam[(size_t)r * next.N + m + 1];
+#pragma unroll
+  for (int r = 0; r < CN; ++r) {
+    double s = f[(size_t)(65 + r) * Nh + m];
+#pragma unroll
+    for (int c = 0; c < CL; ++c) s -= f[(size_t)(15 + 5 * r + c) * Nh + m] * lL[c];
+#pragma unroll
+    for (int c = 0; c < CR; ++c) s -= f[(size_t)(40 + 5 * r + c) * Nh + m] * lR[c];
+    v[r] = s;
+  }
+  // L^T x = v with L packed (reciprocal diagonal)
+#pragma unroll
+  for (int i = CN - 1; i >= 0; --i) {
+    double s = v[i];
+#pragma unroll
+    for (int k = i + 1; k < CN; ++k) s -= f[(size_t)pk(k, i) * Nh + m] * x[k];
+    x[i] = s * f[(size_t)pk(i, i) * Nh + m];
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) cur.lam[(size_t)r * N + n] = r < CN ? x[r] : 0.0;
+}
+
+__global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next, DevJoints J, int level) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = cur.N;
   if (n >= N) return;
@@ -349,36 +448,19 @@ __global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next) {
     for (int r = 0; r < 5; ++r) cur.lam[(size_t)r * N + n] = next.lam[(size_t)r * next.N + n / 2];
     return;
   }
-  const int m = (n - 1) / 2, Nh = N / 2;
-  const double *f = cur.fac;
-  double L[25], lL[5], lR[5], v[5], x[5];
-  {
-    int o = 0;
-#pragma unroll
-    for (int r = 0; r < 5; ++r) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) L[5 * r + c] = 0.0;
-#pragma unroll
-      for (int c = 0; c <= r; ++c) L[5 * r + c] = f[(size_t)(o++) * Nh + m];
-    }
+  const int cn = row_size(J, level, n), cl = row_size(J, level, n - 1);
+  const int cr = n + 1 < N ? row_size(J, level, n + 1) : 0;
+  const int code = (cn == 5 ? 9 : 0) + (cl == 5 ? 3 : 0) + (cr == 5 ? 2 : (cr == 3 ? 1 : 0));
+  switch (code) {
+#define BCK(CODE, A, B, D_) \
+  case CODE: back_row<A, B, D_>(cur, next, n); break;
+    BCK(0, 3, 3, 0) BCK(1, 3, 3, 3) BCK(2, 3, 3, 5)
+    BCK(3, 3, 5, 0) BCK(4, 3, 5, 3) BCK(5, 3, 5, 5)
+    BCK(9, 5, 3, 0) BCK(10, 5, 3, 3) BCK(11, 5, 3, 5)
+    BCK(12, 5, 5, 0) BCK(13, 5, 5, 3) BCK(14, 5, 5, 5)
+#undef BCK
+    default: break;
   }
-  const bool right = n + 1 < N;
-#pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    lL[r] = next.lam[(size_t)r * next.N + m];
-    lR[r] = right ? next.lam[(size_t)r * next.N + m + 1] : 0.0;
-  }
-#pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    double s = f[(size_t)(65 + r) * Nh + m];
-#pragma unroll
-    for (int c = 0; c < 5; ++c)
-      s -= f[(size_t)(15 + 5 * r + c) * Nh + m] * lL[c] + f[(size_t)(40 + 5 * r + c) * Nh + m] * lR[c];
-    v[r] = s;
-  }
-  ltsolve5(L, v, x);
-#pragma unroll
-  for (int r = 0; r < 5; ++r) cur.lam[(size_t)r * N + n] = x[r];
 }
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
@@ -405,8 +487,9 @@ void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, in
   k_cr_top<<<1, 32, 0, s>>>(C, J, top, level, status);
 }
 
-void launch_cr_back(const CRLevel &cur, const CRLevel &next, cudaStream_t s) {
-  if (cur.N > 0) k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next);
+void launch_cr_back(const DevJoints &J, const CRLevel &cur, const CRLevel &next, int level,
+                    cudaStream_t s) {
+  if (cur.N > 0) k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next, J, level);
 }
 
 }  // namespace mabd

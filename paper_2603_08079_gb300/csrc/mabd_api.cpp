@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -71,6 +72,13 @@ struct mabd_ctx {
   cudaEvent_t stage_done = nullptr;
   bool stage_pending = false;
 
+  // last CUDA failure (for mabd_error_detail)
+  char err_detail[256] = {0};
+
+  // MABD_DEBUG_SYNC=1: check every launch synchronously (diagnostics only)
+  bool debug_sync = false;
+  cudaError_t debug_err = cudaSuccess;
+
   // profiling
   bool prof_on = false;
   std::vector<Rec> recs;
@@ -79,8 +87,11 @@ struct mabd_ctx {
 
 namespace {
 
-mabd_status cuda_fail(mabd_ctx *ctx, cudaError_t e) {
+mabd_status cuda_fail_at(mabd_ctx *ctx, cudaError_t e, int line) {
   if (e == cudaSuccess) return MABD_OK;
+  if (ctx && ctx->err_detail[0] == 0)
+    std::snprintf(ctx->err_detail, sizeof(ctx->err_detail), "%s (%s) at mabd_api.cpp:%d",
+                  cudaGetErrorName(e), cudaGetErrorString(e), line);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return MABD_ERR_OUT_OF_MEMORY;
@@ -88,6 +99,7 @@ mabd_status cuda_fail(mabd_ctx *ctx, cudaError_t e) {
   if (ctx) ctx->cuda_failed = true;
   return MABD_ERR_CUDA;
 }
+#define cuda_fail(ctx, e) cuda_fail_at((ctx), (e), __LINE__)
 
 #define CK(call)                                   \
   do {                                             \
@@ -432,8 +444,35 @@ bool structured_hinv(const mabd_body_desc &d, double h, double out[HINV_N]) {
 // --------------------------------------------------------------------------
 // profiling around launches
 // --------------------------------------------------------------------------
+// debug mode: report an error left pending by an earlier runtime call
+void dbg_pending(const char *where) {
+  static const bool on = [] {
+    const char *d = std::getenv("MABD_DEBUG_SYNC");
+    return d && d[0] == '1';
+  }();
+  if (!on) return;
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) std::fprintf(stderr, "mabd debug: pending %s at %s\n", cudaGetErrorName(e), where);
+}
+
 template <class F>
 void run(mabd_ctx *ctx, const char *name, F &&f) {
+  if (ctx->debug_sync) {
+    cudaError_t e0 = cudaGetLastError();
+    f();
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = e0 != cudaSuccess ? e0 : (e1 != cudaSuccess ? e1 : e2);
+    if (e != cudaSuccess) {
+      if (ctx->err_detail[0] == 0)
+        std::snprintf(ctx->err_detail, sizeof(ctx->err_detail), "%s (%s) %s launch %s",
+                      cudaGetErrorName(e), cudaGetErrorString(e),
+                      e0 != cudaSuccess ? "before" : "in", name);
+      std::fprintf(stderr, "mabd debug: %s\n", ctx->err_detail);
+      ctx->debug_err = e;
+    }
+    return;
+  }
   if (!ctx->prof_on) {
     f();
     return;
@@ -480,8 +519,6 @@ mabd_status ensure_stage(mabd_ctx *ctx, size_t n) {
   }
   if (ctx->h_stage_n >= n) return MABD_OK;
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-  if (ctx->h_iter) cudaFreeHost(ctx->h_iter);
-  if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   ctx->h_stage = nullptr;
   ctx->h_stage_n = 0;
   CK(cudaMallocHost((void **)&ctx->h_stage, n * sizeof(double)));
@@ -526,6 +563,7 @@ const char *mabd_status_string(mabd_status s) {
 }
 
 mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
+  dbg_pending("enter mabd_create");
   if (!cfg || !out) return MABD_ERR_INVALID_ARG;
   *out = nullptr;
   if (!(cfg->h > 0.0) || !std::isfinite(cfg->h) || !finite_arr(cfg->gravity, 3))
@@ -544,6 +582,10 @@ mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
   ctx->cfg = *cfg;
   ctx->stream = (cudaStream_t)cfg->stream;
   cudaGetDevice(&ctx->device);
+  {
+    const char *dbg = std::getenv("MABD_DEBUG_SYNC");
+    ctx->debug_sync = dbg && dbg[0] == '1';
+  }
   if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
@@ -554,6 +596,7 @@ mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
 }
 
 mabd_status mabd_add_bodies(mabd_ctx *ctx, int64_t n, const mabd_body_desc *d, int64_t *first_id) {
+  dbg_pending("enter mabd_add_bodies");
   if (!ctx || n < 0 || (n > 0 && !d)) return MABD_ERR_INVALID_ARG;
   if (ctx->frozen) return MABD_ERR_BAD_STATE;
   if ((int64_t)ctx->bodies.size() + n > (int64_t)INT32_MAX / 16) return MABD_ERR_INVALID_ARG;
@@ -576,6 +619,7 @@ mabd_status mabd_add_bodies(mabd_ctx *ctx, int64_t n, const mabd_body_desc *d, i
 }
 
 mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, int64_t *first_id) {
+  dbg_pending("enter mabd_add_joints");
   if (!ctx || n < 0 || (n > 0 && !d)) return MABD_ERR_INVALID_ARG;
   if (ctx->frozen) return MABD_ERR_BAD_STATE;
   if ((int64_t)ctx->joints.size() + n > (int64_t)INT32_MAX / 16) return MABD_ERR_INVALID_ARG;
@@ -598,6 +642,7 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
 }
 
 mabd_status mabd_prefactor(mabd_ctx *ctx) {
+  dbg_pending("enter mabd_prefactor");
   if (!ctx) return MABD_ERR_INVALID_ARG;
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (ctx->frozen) return MABD_ERR_BAD_STATE;
@@ -1004,7 +1049,7 @@ static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
       }
       run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
       for (int l = nl - 2; l >= 0; --l)
-        run(ctx, "cr_back", [&] { launch_cr_back(ctx->levels[l], ctx->levels[l + 1], s); });
+        run(ctx, "cr_back", [&] { launch_cr_back(ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s); });
     }
   }
   if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE) {
@@ -1024,10 +1069,12 @@ static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
   if (maxbits && ctx->J.K > 0)
     run(ctx, "residuals", [&] { launch_residuals(ctx->B, ctx->J, p, maxbits, ctx->d_status, s); });
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && ctx->debug_err != cudaSuccess) e = ctx->debug_err;
   return cuda_fail(ctx, e);
 }
 
 mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
+  dbg_pending("enter mabd_step");
   if (!ctx || nsteps < 0) return MABD_ERR_INVALID_ARG;
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
@@ -1069,6 +1116,7 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
 }
 
 mabd_status mabd_get_state(mabd_ctx *ctx, double *q, double *qdot) {
+  dbg_pending("enter mabd_get_state");
   if (!ctx || (!q && !qdot)) return MABD_ERR_INVALID_ARG;
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
@@ -1090,6 +1138,7 @@ mabd_status mabd_get_state(mabd_ctx *ctx, double *q, double *qdot) {
 }
 
 mabd_status mabd_set_state(mabd_ctx *ctx, const double *q, const double *qdot) {
+  dbg_pending("enter mabd_set_state");
   if (!ctx || !q || !qdot) return MABD_ERR_INVALID_ARG;
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
@@ -1113,6 +1162,7 @@ mabd_status mabd_set_state(mabd_ctx *ctx, const double *q, const double *qdot) {
 }
 
 mabd_status mabd_get_lambda(mabd_ctx *ctx, double *lambda) {
+  dbg_pending("enter mabd_get_lambda");
   if (!ctx || !lambda) return MABD_ERR_INVALID_ARG;
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
@@ -1130,6 +1180,7 @@ mabd_status mabd_get_lambda(mabd_ctx *ctx, double *lambda) {
 }
 
 mabd_status mabd_synchronize(mabd_ctx *ctx) {
+  dbg_pending("enter mabd_synchronize");
   if (!ctx) return MABD_ERR_INVALID_ARG;
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (!ctx->frozen) {
@@ -1188,7 +1239,13 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
   return MABD_OK;
 }
 
+const char *mabd_error_detail(mabd_ctx *ctx) {
+  if (!ctx) return "";
+  return ctx->err_detail;
+}
+
 mabd_status mabd_destroy(mabd_ctx *ctx) {
+  dbg_pending("enter mabd_destroy");
   if (!ctx) return MABD_ERR_INVALID_ARG;
   cudaStreamSynchronize(ctx->stream);
   for (auto &r : ctx->recs) {

@@ -152,7 +152,8 @@ void launch_cr_combine(const DevChain &C, const DevJoints &J, const CRLevel &cur
                        const double *Bn, cudaStream_t s);
 void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,
                    int *status, cudaStream_t s);
-void launch_cr_back(const CRLevel &cur, const CRLevel &next, cudaStream_t s);
+void launch_cr_back(const DevJoints &J, const CRLevel &cur, const CRLevel &next, int level,
+                    cudaStream_t s);
 
 // tree (k_tree.cu): one launch per level, deepest first, then root first
 void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,

@@ -25,8 +25,9 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of dev
 
 
 class MabdError(RuntimeError):
-    def __init__(self, what: str, code: int):
-        super().__init__(f"{what}: {STATUS.get(code, code)} (status {code})")
+    def __init__(self, what: str, code: int, detail: str = ""):
+        msg = f"{what}: {STATUS.get(code, code)} (status {code})"
+        super().__init__(msg + (f" [{detail}]" if detail else ""))
         self.code = code
 
 
@@ -66,7 +67,7 @@ _lib = None
 EXPORTS = ["mabd_config_default", "mabd_create", "mabd_add_bodies", "mabd_add_joints",
            "mabd_prefactor", "mabd_step", "mabd_get_state", "mabd_set_state", "mabd_get_lambda",
            "mabd_synchronize", "mabd_get_info", "mabd_profile_enable", "mabd_profile_reset",
-           "mabd_kernel_times", "mabd_destroy", "mabd_status_string"]
+           "mabd_kernel_times", "mabd_destroy", "mabd_status_string", "mabd_error_detail"]
 
 
 def library_path() -> str:
@@ -103,8 +104,10 @@ def load(build_if_missing: bool = True):
     lib.mabd_destroy.argtypes = [P]
     lib.mabd_status_string.argtypes = [i32]
     lib.mabd_status_string.restype = C.c_char_p
+    lib.mabd_error_detail.argtypes = [P]
+    lib.mabd_error_detail.restype = C.c_char_p
     for f in EXPORTS:
-        if f not in ("mabd_config_default", "mabd_status_string"):
+        if f not in ("mabd_config_default", "mabd_status_string", "mabd_error_detail"):
             getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -188,7 +191,10 @@ class Solver:
 
     def _check(self, what, st):
         if st != 0:
-            raise MabdError(what, st)
+            detail = ""
+            if getattr(self, "ctx", None):
+                detail = (self._lib.mabd_error_detail(self.ctx) or b"").decode(errors="replace")
+            raise MabdError(what, st, detail)
 
     def step(self, n: int = 1, stats: bool = False):
         if stats:
