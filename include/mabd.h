@@ -177,6 +177,35 @@ mabd_status mabd_profile_reset(mabd_ctx *ctx);
 mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, double *ms,
                               int64_t *launches, int32_t *count);
 
+/* ---- Step without device allocation (the paper has no counterpart) ----
+   For callers that cannot call cudaMalloc -- code running inside another
+   framework that owns the device allocator, or under a fixed memory budget:
+   one implicit step of a single chain of at most MABD_NOALLOC_MAX_BODIES
+   bodies, computed by the same kernels as mabd_step.  Every intermediate
+   lives in one file-scope device array of the library (about 13 MB, held on
+   every device that loads the library until the process exits); nothing is
+   allocated.  The first call on a device looks up that array's device
+   address (cudaGetSymbolAddress), so make it before any stream capture.
+   All calls on a device share the array and it keeps the last call's
+   contents (the call clears what must start at zero): calls that overlap on
+   the GPU (two host threads, or two streams) race and give wrong results.
+     cfg: h, gravity, residual_rhs and stream are used (precision FP64).
+     bodies: device array of M descriptions (their q, qdot are the input
+       state), in path order; fixed must be 0.
+     joints: device array of K in [M-1, M+1] descriptions in path order:
+       an optional pin of body 0 (body_a = 0, body_b = MABD_WORLD), the M-1
+       joints between bodies i and i+1 (either orientation), an optional pin
+       of body M-1.
+     q_out, qdot_out: device arrays of 12*M doubles (body by body);
+     lambda_out: device array of the dual rows (3 per ball, 5 per hinge).
+   Synchronizes cfg->stream.  INVALID_ARG for M outside [1, MAX], K outside
+   [M-1, M+1], or descriptions that break the layout above; device-side
+   failures are returned as by mabd_step. */
+#define MABD_NOALLOC_MAX_BODIES 4096
+mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M, const mabd_body_desc *bodies,
+                                    int32_t K, const mabd_joint_desc *joints, double *q_out,
+                                    double *qdot_out, double *lambda_out);
+
 /* Text of the last CUDA failure seen by the context (error name, message and
    the host source line), or "" if none; owned by the context. */
 const char *mabd_error_detail(mabd_ctx *ctx);
