@@ -30,14 +30,46 @@ M_FULL = 1 << 20
 H = 1e-2
 
 
-def workload_config(M: int, K: int, rows: int) -> dict:
+WORKLOADS = {
+    # name: (generator kwargs, description, solver, oracle sample kwargs)
+    "chain1m": ("pulley-cable chain: %d boxes (sides U[0.5,1.5], rho 10^U[2,4]), %d joints "
+                "(ball/hinge alternating, both ends pinned), %d dual rows, h=1e-2 s, seed 1",
+                "block cyclic reduction (chain)"),
+    "tree256k": ("random tree: %d boxes (sides U[0.2,1], rho 1000, Poisson(1.8) children), %d joints "
+                 "(hinges, axes uniform on the sphere, root pinned), %d dual rows, h=5e-3 s, seed 2",
+                 "level-scheduled body-space elimination (tree)"),
+    "net64x64x16": ("jittered net: %d unit cubes on a 64x64x16 lattice (sigma 0.05, bottom layer fixed), "
+                    "%d ball joints kept with p=0.7, %d dual rows, h=1e-2 s, seed 4",
+                    "block-Jacobi PCG on the dual, rtol 1e-13 (graph)"),
+    "batch4096": ("4096 independent assemblies: %d links (7..64 per assembly, Poisson(1.3) branching, "
+                  "fixed base with a random pose), %d hinge/ball joints, %d dual rows, h=2e-3 s, seed 3",
+                  "one forest: level-scheduled body-space elimination over all assemblies, "
+                  "replayed from one CUDA graph per step"),
+}
+
+
+def make_scene(name: str, M: int | None = None) -> dict:
+    from paper_2603_08079_gb300 import scenes
+    if name == "chain1m":
+        return scenes.long_chain(M or M_FULL, seed=1)
+    if name == "tree256k":
+        return scenes.random_tree(M or 262144, seed=2)
+    if name == "batch4096":
+        return scenes.assemblies(M or 4096, seed=3)
+    if name == "net64x64x16":
+        if M:  # a smaller lattice with the same density, for the CPU sample
+            n = max(4, int(round((M / 16) ** 0.5)))
+            return scenes.jittered_net(n, n, 16 if n >= 16 else 4, seed=4)
+        return scenes.jittered_net(64, 64, 16, seed=4)
+    raise KeyError(name)
+
+
+def workload_config(M: int, K: int, rows: int, name: str = "chain1m") -> dict:
+    desc, solver = WORKLOADS[name]
     return {
-        "workload": "pulley-cable chain: %d boxes (sides U[0.5,1.5], rho 10^U[2,4]), %d joints "
-                    "(ball/hinge alternating, both ends pinned), %d dual rows, h=1e-2 s, seed 1"
-                    % (M, K, rows),
-        "bodies": M, "joints": K, "dual_rows": rows, "h": H, "form": "fp64",
-        "solver": "block cyclic reduction (chain)",
-        "l2": "inputs larger than L2 (state alone 192 MB; working set ~1.5 GB), no flush",
+        "workload": desc % (M, K, rows),
+        "bodies": M, "joints": K, "dual_rows": rows, "form": "fp64", "solver": solver,
+        "l2": "inputs larger than L2 (working set > 129 MB), no flush",
     }
 
 
@@ -178,8 +210,8 @@ def run_gpu(args):
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    M = args.bodies
-    sc = scenes.long_chain(M, seed=1)
+    sc = make_scene(args.workload, args.bodies if args.workload == "chain1m" else None)
+    M = len(sc["mass"])
     solver = mabd.Solver(sc)
     info = solver.info()
     stream = solver.stream
@@ -245,7 +277,7 @@ def run_gpu(args):
         dname, (dms, dn) = dom
         per_launch_ms = dms / dn
         launches_per_step = dn / args.profile_steps
-        step_flops = kernel_model(dname, sc["jtype"])
+        step_flops = kernel_model(dname, sc["jtype"]) if args.workload == "chain1m" else None
         if step_flops is not None:
             flops = step_flops / launches_per_step     # per launch, averaged over the levels
             achieved = flops / (per_launch_ms / 1e3) / 1e12
@@ -263,7 +295,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator, paper-shaped chain)",
-            "config": workload_config(M, info["joints"], info["dual_rows"]),
+            "config": workload_config(M, info["joints"], info["dual_rows"], args.workload),
             "e2e": {"value": e2e_value, "unit": "body-steps/s",
                     "h2d_bytes_per_step": 2 * 12 * 8 * M, "d2h_bytes_per_step": 2 * 12 * 8 * M},
             "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -272,6 +304,8 @@ def run_gpu(args):
             "joint_residual": st["joint_residual"],
             "clocks": clk,
         }
+        if st.get("pcg_iters"):
+            result["pcg_iters_per_step"] = st["pcg_iters"]
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(args)
     if ws > 1:
@@ -285,8 +319,14 @@ def cpu_baseline(args, steps: int = 1, M: int | None = None) -> dict:
     import oracle as ora
     from paper_2603_08079_gb300 import scenes
 
-    M = M or args.cpu_bodies
-    sc = scenes.long_chain(M, seed=1)
+    if args.workload == "chain1m":
+        M = M or args.cpu_bodies
+        sc = scenes.long_chain(M, seed=1)
+    elif args.workload in ("tree256k", "batch4096"):
+        sc = make_scene(args.workload)       # the full scene: a few s per oracle step
+    else:
+        sc = make_scene(args.workload, 16384)  # a 32x32x16 lattice of the same net
+    M = len(sc["mass"])
     S = ora.Scene(sc)
     q, qd = sc["q"], sc["qdot"]
     t0 = time.perf_counter()
@@ -294,8 +334,8 @@ def cpu_baseline(args, steps: int = 1, M: int | None = None) -> dict:
         q, qd, _, _ = ora.step(S, q, qd)
     dt = time.perf_counter() - t0
     return {"value": M * steps / dt, "unit": "body-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d step(s) of the %d-body pulley chain (same generator, seed 1), "
-                      "single thread, %s" % (steps, M, lscpu_model()),
+            "sample": "%d step(s) of a %d-body %s (same generator), single thread, %s"
+                      % (steps, M, args.workload, lscpu_model()),
             "seconds": round(dt, 3)}
 
 
@@ -340,6 +380,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--bodies", type=int, default=M_FULL)
+    ap.add_argument("--workload", default="chain1m", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-bodies", type=int, default=M_FULL // 4)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

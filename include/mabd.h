@@ -32,7 +32,13 @@
  *   else cudaMalloc/cudaFree) and is released by mabd_destroy.
  *   Ordering: all device work is ordered on cfg.stream (NULL = the legacy
  *   default stream).  mabd_step returns once the work is enqueued unless
- *   stats is non-NULL, in which case it synchronizes the stream.
+ *   stats is non-NULL, in which case it synchronizes the stream; with the
+ *   PCG solver it also synchronizes between chunks of 16 iterations (the
+ *   host reads the convergence flag there).  Without statistics the step's
+ *   launches are replayed from CUDA graphs recorded at the first such call
+ *   on a private stream that is ordered after cfg.stream by events
+ *   (environment MABD_NO_GRAPHS=1 launches kernels directly instead;
+ *   MABD_DEBUG_SYNC=1 checks every launch synchronously).
  *   Errors: no C++ exception crosses this ABI; every call returns a status.
  *   MABD_ERR_CUDA is sticky (destroy the context).  Device-side failures
  *   (non-positive det A, non-finite state, polar or PCG non-convergence) set

@@ -75,6 +75,12 @@ struct mabd_ctx {
   // last CUDA failure (for mabd_error_detail)
   char err_detail[256] = {0};
 
+  // CUDA graphs of one step (MABD_NO_GRAPHS=1 turns them off)
+  bool graphs_off = false, graphs_built = false;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t g_step = nullptr, g_pre = nullptr, g_chunk = nullptr, g_post = nullptr;
+
   // MABD_DEBUG_SYNC=1: check every launch synchronously (diagnostics only)
   bool debug_sync = false;
   cudaError_t debug_err = cudaSuccess;
@@ -585,6 +591,8 @@ mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
   {
     const char *dbg = std::getenv("MABD_DEBUG_SYNC");
     ctx->debug_sync = dbg && dbg[0] == '1';
+    const char *ng = std::getenv("MABD_NO_GRAPHS");
+    ctx->graphs_off = ng && ng[0] == '1';
   }
   if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -993,21 +1001,70 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   return MABD_OK;
 }
 
-// Block-Jacobi PCG on the dual.  Iterations are enqueued in chunks; between
-// chunks the host reads the device's iteration count and convergence flag
-// (the kernels of a converged iteration return immediately), so the loop is
-// bounded by pcg_max_iters and nothing on the device waits.
-static mabd_status pcg_solve(mabd_ctx *ctx) {
-  cudaStream_t s = ctx->stream;
+// One step is enqueued in three phases so that it can be captured into CUDA
+// graphs: `pre` runs everything up to the dual solve (the whole solve for
+// chains and trees, the set-up for PCG), the PCG iterations run in chunks,
+// and `post` back-propagates (and, with statistics, computes residuals).
+static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s) {
+  const StepParams &p = ctx->sp;
+  run(ctx, "body_prep", [&] { launch_body_prep(ctx->B, p, ctx->d_status, s); });
+  if (ctx->J.K == 0) return;
+  run(ctx, "joint_prep", [&] { launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
+  if (ctx->solver == MABD_SOLVER_CHAIN) {
+    run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
+    const int nl = (int)ctx->levels.size();
+    for (int l = 0; l + 1 < nl; ++l) {
+      run(ctx, "cr_reduce", [&] {
+        launch_cr_reduce(ctx->C, ctx->J, ctx->levels[l], l, ctx->cL, ctx->cR, ctx->Bn, ctx->d_status, s);
+      });
+      run(ctx, "cr_combine", [&] {
+        launch_cr_combine(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], ctx->cL, ctx->cR,
+                          ctx->Bn, s);
+      });
+    }
+    run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
+    for (int l = nl - 2; l >= 0; --l)
+      run(ctx, "cr_back", [&] { launch_cr_back(ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s); });
+  } else if (ctx->solver == MABD_SOLVER_TREE) {
+    const auto &lv = ctx->tree_lvl;
+    const int nl = (int)lv.size() - 1;
+    for (int l = nl - 1; l >= 0; --l)
+      run(ctx, "tree_up", [&] { launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+    for (int l = 0; l < nl; ++l)
+      run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+  } else if (ctx->solver == MABD_SOLVER_PCG) {
+    run(ctx, "pcg_setup", [&] { launch_pcg_setup(ctx->B, ctx->J, ctx->P, ctx->cfg.pcg_rtol, ctx->d_status, s); });
+  }
+}
+
+constexpr int PCG_CHUNK = 16;
+
+static void enqueue_pcg_chunk(mabd_ctx *ctx, cudaStream_t s) {
+  for (int i = 0; i < PCG_CHUNK; ++i)
+    run(ctx, "pcg_iteration", [&] {
+      launch_pcg_iteration(ctx->B, ctx->J, ctx->I, ctx->P, ctx->cfg.pcg_max_iters, s);
+    });
+}
+
+static void enqueue_post(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
+  const StepParams &p = ctx->sp;
+  if (!(ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE))
+    run(ctx, "backprop", [&] { launch_backprop(ctx->B, ctx->J, ctx->I, p, ctx->d_status, s); });
+  if (maxbits && ctx->J.K > 0)
+    run(ctx, "residuals", [&] { launch_residuals(ctx->B, ctx->J, p, maxbits, ctx->d_status, s); });
+}
+
+// Block-Jacobi PCG on the dual.  Iterations are enqueued in chunks of 16
+// (replayed from a CUDA graph when graphs are on); between chunks the host
+// reads the device's iteration count and convergence flag (the kernels of a
+// converged iteration return immediately), so the loop is bounded by
+// pcg_max_iters and nothing on the device waits.
+static mabd_status pcg_loop(mabd_ctx *ctx, cudaStream_t s, cudaGraphExec_t chunk_graph) {
   const int max_it = ctx->cfg.pcg_max_iters;
-  run(ctx, "pcg_setup", [&] { launch_pcg_setup(ctx->B, ctx->J, ctx->P, ctx->cfg.pcg_rtol, ctx->d_status, s); });
-  const int chunk = 16;
   int done = 0;
-  for (int launched = 0; launched < max_it && !done;) {
-    const int n = std::min(chunk, max_it - launched);
-    for (int i = 0; i < n; ++i)
-      run(ctx, "pcg_iteration", [&] { launch_pcg_iteration(ctx->B, ctx->J, ctx->I, ctx->P, max_it, s); });
-    launched += n;
+  for (int launched = 0; launched < max_it && !done; launched += PCG_CHUNK) {
+    if (chunk_graph) CK(cudaGraphLaunch(chunk_graph, s));
+    else enqueue_pcg_chunk(ctx, s);
     CK(cudaMemcpyAsync(ctx->h_iter, ctx->P.iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     done = ctx->h_iter[1];
@@ -1031,46 +1088,72 @@ static mabd_status pcg_solve(mabd_ctx *ctx) {
 
 static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
   cudaStream_t s = ctx->stream;
-  const StepParams &p = ctx->sp;
-  run(ctx, "body_prep", [&] { launch_body_prep(ctx->B, p, ctx->d_status, s); });
-  if (ctx->J.K > 0) {
-    run(ctx, "joint_prep", [&] { launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
-    if (ctx->solver == MABD_SOLVER_CHAIN) {
-      run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
-      const int nl = (int)ctx->levels.size();
-      for (int l = 0; l + 1 < nl; ++l) {
-        run(ctx, "cr_reduce", [&] {
-          launch_cr_reduce(ctx->C, ctx->J, ctx->levels[l], l, ctx->cL, ctx->cR, ctx->Bn, ctx->d_status, s);
-        });
-        run(ctx, "cr_combine", [&] {
-          launch_cr_combine(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], ctx->cL, ctx->cR,
-                            ctx->Bn, s);
-        });
-      }
-      run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
-      for (int l = nl - 2; l >= 0; --l)
-        run(ctx, "cr_back", [&] { launch_cr_back(ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s); });
-    }
+  enqueue_pre(ctx, s);
+  if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_PCG) {
+    mabd_status st = pcg_loop(ctx, s, nullptr);
+    if (st) return st;
   }
-  if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE) {
-    const auto &lv = ctx->tree_lvl;
-    const int nl = (int)lv.size() - 1;
-    for (int l = nl - 1; l >= 0; --l)
-      run(ctx, "tree_up", [&] { launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
-    for (int l = 0; l < nl; ++l)
-      run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
-  } else {
-    if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_PCG) {
-      mabd_status st = pcg_solve(ctx);
-      if (st) return st;
-    }
-    run(ctx, "backprop", [&] { launch_backprop(ctx->B, ctx->J, ctx->I, p, ctx->d_status, s); });
-  }
-  if (maxbits && ctx->J.K > 0)
-    run(ctx, "residuals", [&] { launch_residuals(ctx->B, ctx->J, p, maxbits, ctx->d_status, s); });
+  enqueue_post(ctx, maxbits, s);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && ctx->debug_err != cudaSuccess) e = ctx->debug_err;
   return cuda_fail(ctx, e);
+}
+
+// ---- CUDA graphs: the step's launches recorded once on a private stream ----
+static cudaGraphExec_t capture(mabd_ctx *ctx, void (*body)(mabd_ctx *, cudaStream_t)) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  if (cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+  body(ctx, ctx->gstream);
+  if (cudaStreamEndCapture(ctx->gstream, &g) != cudaSuccess || !g) return nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+  cudaGraphDestroy(g);
+  return ex;
+}
+
+static void body_pre(mabd_ctx *ctx, cudaStream_t s) { enqueue_pre(ctx, s); }
+static void body_chunk(mabd_ctx *ctx, cudaStream_t s) { enqueue_pcg_chunk(ctx, s); }
+static void body_post(mabd_ctx *ctx, cudaStream_t s) { enqueue_post(ctx, nullptr, s); }
+static void body_step(mabd_ctx *ctx, cudaStream_t s) {
+  enqueue_pre(ctx, s);
+  enqueue_post(ctx, nullptr, s);
+}
+
+// builds the graphs once; on any failure graphs stay off for this context
+static bool graphs_ready(mabd_ctx *ctx) {
+  if (ctx->graphs_off) return false;
+  if (ctx->graphs_built) return true;
+  bool ok = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) == cudaSuccess;
+  if (ok) {
+    if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_PCG) {
+      ctx->g_pre = capture(ctx, body_pre);
+      ctx->g_chunk = capture(ctx, body_chunk);
+      ctx->g_post = capture(ctx, body_post);
+      ok = ctx->g_pre && ctx->g_chunk && ctx->g_post;
+    } else {
+      ctx->g_step = capture(ctx, body_step);
+      ok = ctx->g_step != nullptr;
+    }
+  }
+  cudaGetLastError();
+  if (!ok) ctx->graphs_off = true;
+  ctx->graphs_built = ok;
+  return ok;
+}
+
+static mabd_status step_graph(mabd_ctx *ctx) {
+  cudaStream_t gs = ctx->gstream;
+  if (ctx->g_step) {
+    CK(cudaGraphLaunch(ctx->g_step, gs));
+    return MABD_OK;
+  }
+  CK(cudaGraphLaunch(ctx->g_pre, gs));
+  mabd_status st = pcg_loop(ctx, gs, ctx->g_chunk);
+  if (st) return st;
+  CK(cudaGraphLaunch(ctx->g_post, gs));
+  return MABD_OK;
 }
 
 mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
@@ -1087,6 +1170,18 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
       ctx->max_cap = nsteps;
     }
     CK(cudaMemsetAsync(ctx->d_max, 0, 2 * (size_t)nsteps * 8, ctx->stream));
+  }
+  if (!stats && !ctx->prof_on && !ctx->debug_sync && graphs_ready(ctx)) {
+    // order the private graph stream after the caller's stream and back
+    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0));
+    for (int i = 0; i < nsteps; ++i) {
+      mabd_status st = step_graph(ctx);
+      if (st) return st;
+    }
+    CK(cudaEventRecord(ctx->ev_out, ctx->gstream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0));
+    return MABD_OK;
   }
   std::vector<int> pit(nsteps, 0);
   std::vector<double> prel(nsteps, 0.0);
@@ -1252,6 +1347,14 @@ mabd_status mabd_destroy(mabd_ctx *ctx) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  for (cudaGraphExec_t g : {ctx->g_step, ctx->g_pre, ctx->g_chunk, ctx->g_post})
+    if (g) cudaGraphExecDestroy(g);
+  if (ctx->gstream) {
+    cudaStreamSynchronize(ctx->gstream);
+    cudaStreamDestroy(ctx->gstream);
+  }
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   free_all(ctx);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_iter) cudaFreeHost(ctx->h_iter);

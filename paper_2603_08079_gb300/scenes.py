@@ -304,6 +304,96 @@ def jittered_net(nx: int = 64, ny: int = 64, nz: int = 16, seed: int = 4,
     return sc
 
 
+def assemblies(n: int = 4096, seed: int = 3, h: float = 2e-3, young: float = 1e8,
+               min_links: int = 7, max_links: int = 64, mean_children: float = 1.3,
+               spacing: float = 40.0) -> dict:
+    """Independent articulated assemblies (the batched form): each has a link
+    count uniform in [7, 64] and is a random tree grown breadth-first with
+    Poisson(1.3) children (truncated at its link count; a body whose
+    frontier died out gets one child); joints are hinges or balls with
+    probability 1/2 and hinge axes are uniform on the sphere.  Links are
+    boxes with sides U[0.1,0.5]^3 and masses 10^U[-1,1] kg.  Link 0 is a
+    fixed base with a uniformly random pose, so every subtree hanging from
+    it is an independent tree whose root joint is one-sided.  Assemblies
+    sit on a square grid `spacing` metres apart.  Body ids are contiguous
+    per assembly; joint j>0 of an assembly is the parent joint of its link j
+    with body_a = the parent.
+
+    Random numbers are drawn per assembly in this order: link count, the
+    child counts, sides, log-masses, joint kinds, hinge axes, base pose."""
+    rng = np.random.default_rng(seed)
+    bodies_sides, bodies_mass, centres, rots, fixed = [], [], [], [], []
+    jt, ja, jb, an_a, an_b, ax = [], [], [], [], [], []
+    side_len = int(np.ceil(np.sqrt(n)))
+    base_id = 0
+    for a in range(n):
+        L = int(rng.integers(min_links, max_links + 1))
+        parent = np.full(L, -1, dtype=np.int64)
+        count, head = 1, 0
+        kids = [[] for _ in range(L)]
+        while count < L:
+            if head < count:
+                p_ = head
+                head += 1
+                k = int(rng.poisson(mean_children))
+            else:
+                p_ = count - 1
+                k = 1
+            k = min(k, L - count)
+            for _ in range(k):
+                parent[count] = p_
+                kids[p_].append(count)
+                count += 1
+        sides = rng.uniform(0.1, 0.5, size=(L, 3))
+        mass = 10.0 ** rng.uniform(-1.0, 1.0, size=L)
+        kind = rng.random(L - 1) < 0.5
+        axes = _unit(rng.standard_normal((L - 1, 3)))
+        Q = random_rotations(rng, 1)[0]
+        # local layout: children upright on the parent's +z face
+        loc = np.zeros((L, 3))
+        off = np.zeros((L, 3))
+        for p_ in range(L):
+            ch = kids[p_]
+            for si, c in enumerate(ch):
+                axl = sides[p_, 0]
+                xo = (si + 1.0) / (len(ch) + 1.0) * axl - 0.5 * axl
+                off[c] = (xo, 0.0, 0.5 * sides[p_, 2])
+                loc[c] = loc[p_] + off[c] + (0.0, 0.0, 0.5 * sides[c, 2])
+        origin = np.array([spacing * (a % side_len), spacing * (a // side_len), 0.0])
+        for j in range(L):
+            bodies_sides.append(sides[j])
+            bodies_mass.append(mass[j])
+            centres.append(origin + Q @ loc[j])
+            rots.append(Q)
+            fixed.append(1 if j == 0 else 0)
+        for j in range(1, L):
+            jt.append(HINGE if kind[j - 1] else BALL)
+            ja.append(base_id + parent[j])
+            jb.append(base_id + j)
+            an_a.append(off[j])
+            an_b.append((0.0, 0.0, -0.5 * sides[j, 2]))
+            ax.append(axes[j - 1])
+        base_id += L
+    M = base_id
+    K = len(jt)
+    sc = _empty_scene(M, K, h)
+    sides = np.array(bodies_sides)
+    mass = np.array(bodies_mass)
+    vol = sides.prod(axis=1)
+    _set_boxes(sc, sides, mass / vol, np.array(centres), young)
+    R = np.array(rots)
+    sc["q"][:, 0:9] = np.transpose(R, (0, 2, 1)).reshape(M, 9)  # columns of R stacked
+    sc["fixed"][:] = np.array(fixed, dtype=np.int32)
+    sc["jtype"][:] = jt
+    sc["body_a"][:] = ja
+    sc["body_b"][:] = jb
+    sc["anchor_a"][:] = an_a
+    sc["anchor_b"][:] = an_b
+    sc["axis_a"][:] = ax
+    sc["axis_b"][:] = ax
+    return sc
+
+
 # ---------------------------------------------------------------------------
 # Small scenes for checks
 # ---------------------------------------------------------------------------
@@ -459,4 +549,6 @@ def workload(name: str, **kw) -> dict:
         return random_tree(**kw)
     if name == "net64x64x16":
         return jittered_net(**kw)
+    if name == "batch4096":
+        return assemblies(**kw)
     raise KeyError(name)

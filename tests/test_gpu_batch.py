@@ -1,0 +1,48 @@
+"""GPU parity of the batched form: thousands of independent assemblies
+(each a random tree on a fixed, randomly posed base) stepped together as one
+forest by the tree path."""
+import numpy as np
+import pytest
+
+from paper_2603_08079_gb300 import scenes
+from parity_util import assert_parity, gpu_solver, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n", [1, 7, 64])
+def test_small_batches(ora, n):
+    need_gpu()
+    sc = scenes.assemblies(n, seed=3)
+    s = gpu_solver(sc)
+    try:
+        assert s.info()["solver"] == "tree"
+        assert_parity(ora, sc, sc["q"], sc["qdot"], solver=s)
+        q, qd = scenes.perturb_state(sc, seed=n, rot=0.05, vel=0.3)
+        assert_parity(ora, sc, q, qd, solver=s)
+    finally:
+        s.close()
+
+
+def test_full_batch_of_4096_assemblies(ora):
+    """144,619 links / 140,523 joints: every output compared with the oracle."""
+    need_gpu()
+    sc = scenes.assemblies(4096, seed=3)
+    q, qd = scenes.perturb_state(sc, seed=1, rot=0.02, vel=0.2)
+    assert_parity(ora, sc, q, qd)
+
+
+def test_batch_runs_many_steps_in_one_call(ora):
+    """100 steps replayed from the step's CUDA graph stay finite and keep the
+    joints closed (the config's 1000-step run, shortened)."""
+    need_gpu()
+    sc = scenes.assemblies(256, seed=3)
+    s = gpu_solver(sc)
+    try:
+        s.step(100)
+        st = s.step(1, stats=True)[0]
+        q, qd = s.get_state()
+    finally:
+        s.close()
+    assert np.all(np.isfinite(q)) and np.all(np.isfinite(qd))
+    assert st["joint_residual"] < 1e-6
