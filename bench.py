@@ -184,17 +184,22 @@ def cr_reduce_flops(jtype_chain: np.ndarray) -> float:
 
 
 def chain_gram_flops(jtype_chain: np.ndarray) -> float:
-    """FP64 flops of the per-body Gram blocks (FMA = 2): a body with n rows
-    forms n rest-frame rows (12 FMA each), applies the structured Hbar^{-1}
-    (9 + 24 FMA per row) and n(n+1)/2 row products (15 FMA each)."""
-    rows = np.where(np.asarray(jtype_chain) == 1, 5, 3).astype(np.int64)
-    n = rows[:-1] + rows[1:]          # body j carries joints j and j+1 (both ends pinned)
-    return 2.0 * float((45 * n + 15 * n * (n + 1) // 2).sum())
+    """FP64 flops of the per-body Gram blocks (FMA = 2).  Rows are grouped by
+    point; a block is E^T Mbar(p, p') E' with the 3x3 point compliance Mbar
+    (30 FMA) and projections of 54 (3x3), 45 (2x3), 36 (3x2) or 30 (2x2)
+    FMA; a hinge's rest-frame directions cost 36 FMA.  Per body (lower
+    joint, upper joint): ball-ball 252, ball-hinge 489, hinge-ball 498,
+    hinge-hinge 795 FMA."""
+    t = np.asarray(jtype_chain)
+    lo, up = t[:-1], t[1:]           # body j carries joints j and j+1 (both ends pinned)
+    fma = np.select([(lo == 0) & (up == 0), (lo == 0) & (up == 1), (lo == 1) & (up == 0)],
+                    [252, 489, 498], 795)
+    return 2.0 * float(fma.sum())
 
 
 def kernel_model(name: str, jtype_chain: np.ndarray):
     """Algorithmic FP64 flops of one step's launches of `name` (all levels)."""
-    if name.startswith("cr_reduce"):
+    if name.startswith("cr_reduce") or name == "cr_level":
         return cr_reduce_flops(jtype_chain)
     if name == "chain_gram":
         return chain_gram_flops(jtype_chain)

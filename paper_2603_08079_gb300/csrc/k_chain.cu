@@ -17,8 +17,50 @@ __device__ __forceinline__ int pk(int r, int c) { return r >= c ? r * (r + 1) / 
 // ---------------------------------------------------------------------------
 // A constraint row of joint k on body j is w = s ([p; 1] (x) d) in world
 // coordinates (Eq. ball / hinge, frozen frame), with s = +1 on body a and -1 on
-// body b.  In the rest frame it becomes [p; 1] (x) (s R^T d), and
-// G_kj H_j^{-1} G_k'j^T = W^T Hbar^{-1} W' (Eq. abd_final).
+// body b.  In the rest frame it is [p; 1] (x) e with e = s R^T d, and
+//   w^T H^{-1} w' = e^T Mbar(p, p') e',  Mbar(p, p') = ([p;1] (x) I)^T Hbar^{-1} ([p';1] (x) I)
+// (Eq. abd_final): the 3x3 compliance between two points of the body.  Rows
+// are grouped by point (a ball: 3 rows at its anchor; a hinge: 3 rows at the
+// anchor and 2 at the second point), so each Gram block is E^T Mbar E' with
+// the group's rest-frame directions E.
+
+// Mbar(p, q) from the structured inverse h[16]: translation h[0]; the 3x3
+// block X of A's diagonal entries (h[1..6]); transpose pairs
+// (A(1,0), A(0,1)) h[7..9], (A(2,0), A(0,2)) h[10..12], (A(2,1), A(1,2)) h[13..15].
+__device__ __forceinline__ void mbar(const double h[16], const double p[3], const double q[3],
+                                     double Mb[3][3]) {
+  const double p0q0 = p[0] * q[0], p1q1 = p[1] * q[1], p2q2 = p[2] * q[2];
+  Mb[0][0] = h[0] + h[1] * p0q0 + h[9] * p1q1 + h[12] * p2q2;
+  Mb[1][1] = h[0] + h[4] * p1q1 + h[7] * p0q0 + h[15] * p2q2;
+  Mb[2][2] = h[0] + h[6] * p2q2 + h[10] * p0q0 + h[13] * p1q1;
+  const double p0q1 = p[0] * q[1], p1q0 = p[1] * q[0];
+  const double p0q2 = p[0] * q[2], p2q0 = p[2] * q[0];
+  const double p1q2 = p[1] * q[2], p2q1 = p[2] * q[1];
+  Mb[0][1] = h[2] * p0q1 + h[8] * p1q0;
+  Mb[1][0] = h[2] * p1q0 + h[8] * p0q1;
+  Mb[0][2] = h[3] * p0q2 + h[11] * p2q0;
+  Mb[2][0] = h[3] * p2q0 + h[11] * p0q2;
+  Mb[1][2] = h[5] * p1q2 + h[14] * p2q1;
+  Mb[2][1] = h[5] * p2q1 + h[14] * p1q2;
+}
+
+// out[r][c] (r < NA, c < NB) = Ea[:, ca[r]]^T Mb Eb[:, cb[c]]
+template <int NA, int NB>
+__device__ __forceinline__ void project(const double Ea[3][3], const int ca[3], const double Mb[3][3],
+                                        const double Eb[3][3], const int cb[3], double out[3][3]) {
+  double T[3][NB];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      T[a][c] = Mb[a][0] * Eb[0][cb[c]] + Mb[a][1] * Eb[1][cb[c]] + Mb[a][2] * Eb[2][cb[c]];
+#pragma unroll
+  for (int r = 0; r < NA; ++r)
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      out[r][c] = Ea[0][ca[r]] * T[0][c] + Ea[1][ca[r]] * T[1][c] + Ea[2][ca[r]] * T[2][c];
+}
+
 __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, DevIncidence I,
                                                     DevChain C) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -31,75 +73,106 @@ __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, De
   double R[9], h[16];
   load_R(B.R, M, j, R);
   load_hinv(B, j, h);
-  // rows: rest-frame direction E[r] and point P[pt[r]] (homogeneous, 4th = 1)
-  double E[10][3];
-  double P[4][3];
-  int pt[10];
-  int kk[2], Cs[2];
-  int nrows = 0;
+  // per slot: directions E (rest frame, columns = rows' directions), points
+  double E[2][3][3], P[2][2][3];
+  int kk[2], ty[2];
   for (int s = 0; s < n; ++s) {
     const int k = I.joint[e0 + s];
     const int side = I.side[e0 + s];
     const int type = J.type[k];
     kk[s] = k;
-    Cs[s] = type == 0 ? 3 : 5;
+    ty[s] = type;
     const double sgn = side == 0 ? 1.0 : -1.0;
-    if (side == 0) load3(J.pa1, K, k, P[2 * s]);
-    else load3(J.pb1, K, k, P[2 * s]);
-    double RH[9];
+    load3(side == 0 ? J.pa1 : J.pb1, K, k, P[s][0]);
     if (type == 1) {
-      if (side == 0) load3(J.pa2, K, k, P[2 * s + 1]);
-      else load3(J.pb2, K, k, P[2 * s + 1]);
+      load3(side == 0 ? J.pa2 : J.pb2, K, k, P[s][1]);
+      double RH[9];
       load_R(J.RH, K, k, RH);
-    }
-    for (int r = 0; r < Cs[s]; ++r) {
-      double d[3], e[3];
-      row_dir(type, RH, r, d);
-      mtv3(R, d, e);
-      E[nrows][0] = sgn * e[0];
-      E[nrows][1] = sgn * e[1];
-      E[nrows][2] = sgn * e[2];
-      pt[nrows] = 2 * s + (r < 3 ? 0 : 1);
-      ++nrows;
-    }
-  }
-  // Gram matrix of the rows: Gm[r][t] = w_r^T Hbar^{-1} w_t, t <= r
-  double Gm[10][10];
-  for (int t = 0; t < nrows; ++t) {
-    double w[12], z[12];
-    const double *p = P[pt[t]];
+      // E = s R^T R_H^T: column r is s R^T (row r of R_H)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      w[a] = p[0] * E[t][a];
-      w[3 + a] = p[1] * E[t][a];
-      w[6 + a] = p[2] * E[t][a];
-      w[9 + a] = E[t][a];
-    }
-    hinv_apply(h, w, z);
-    for (int r = t; r < nrows; ++r) {
-      const double *pr = P[pt[r]];
-      double v = 0.0;
+      for (int r = 0; r < 3; ++r) {
+        double e[3];
+        mtv3(R, RH + 3 * r, e);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) E[s][a][r] = sgn * e[a];
+      }
+    } else {
+      // E = s R^T
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        v += E[r][a] * (pr[0] * z[a] + pr[1] * z[3 + a] + pr[2] * z[6 + a] + z[9 + a]);
-      Gm[r][t] = v;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) E[s][a][r] = sgn * R[3 * r + a];
     }
   }
-  // each joint's diagonal block goes to the slot of this body (lower or upper
-  // body of the joint along the path); the coupling of the two joints -> B
+  const int c012[3] = {0, 1, 2}, c02[3] = {0, 2, 0};
+  double Mb[3][3], blk[3][3];
+  // self blocks of each joint -> its slot (lower body: Dfirst, upper: Dsecond)
   for (int s = 0; s < n; ++s) {
-    const int k = kk[s], cs = Cs[s], o = s == 0 ? 0 : Cs[0];
     double *dst = C.islot[e0 + s] == 0 ? C.Dfirst : C.Dsecond;
-    for (int r = 0; r < 5; ++r)
-      for (int c = 0; c <= r; ++c)
-        dst[(size_t)pk(r, c) * K + k] = (r < cs && c < cs) ? Gm[o + r][o + c] : 0.0;
+    const int k = kk[s];
+    double Dp[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) Dp[i] = 0.0;
+    mbar(h, P[s][0], P[s][0], Mb);
+    project<3, 3>(E[s], c012, Mb, E[s], c012, blk);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) Dp[pk(r, c)] = blk[r][c];
+    if (ty[s] == 1) {
+      mbar(h, P[s][1], P[s][0], Mb);                      // rows 3-4 x rows 0-2
+      project<2, 3>(E[s], c02, Mb, E[s], c012, blk);
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Dp[pk(3 + r, c)] = blk[r][c];
+      mbar(h, P[s][1], P[s][1], Mb);                      // rows 3-4 x rows 3-4
+      project<2, 2>(E[s], c02, Mb, E[s], c02, blk);
+      Dp[pk(3, 3)] = blk[0][0];
+      Dp[pk(4, 3)] = blk[1][0];
+      Dp[pk(4, 4)] = blk[1][1];
+    }
+#pragma unroll
+    for (int i = 0; i < 15; ++i) dst[(size_t)i * K + k] = Dp[i];
   }
   if (n == 2) {
-    const int c0 = Cs[0], c1 = Cs[1];
+    // coupling of the two joints: rows of joint 0 x rows of joint 1 -> B[k0]
+    double Bp[25];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) Bp[i] = 0.0;
+    mbar(h, P[0][0], P[1][0], Mb);
+    project<3, 3>(E[0], c012, Mb, E[1], c012, blk);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Bp[5 * r + c] = blk[r][c];
+    if (ty[1] == 1) {
+      mbar(h, P[0][0], P[1][1], Mb);
+      project<3, 2>(E[0], c012, Mb, E[1], c02, blk);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) Bp[5 * r + 3 + c] = blk[r][c];
+    }
+    if (ty[0] == 1) {
+      mbar(h, P[0][1], P[1][0], Mb);
+      project<2, 3>(E[0], c02, Mb, E[1], c012, blk);
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Bp[5 * (3 + r) + c] = blk[r][c];
+      if (ty[1] == 1) {
+        mbar(h, P[0][1], P[1][1], Mb);
+        project<2, 2>(E[0], c02, Mb, E[1], c02, blk);
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) Bp[5 * (3 + r) + 3 + c] = blk[r][c];
+      }
+    }
     const int k0 = kk[0];
-    for (int r = 0; r < 5; ++r)
-      for (int c = 0; c < 5; ++c)
-        C.B[(size_t)(5 * r + c) * K + k0] = (r < c0 && c < c1) ? Gm[c0 + c][r] : 0.0;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) C.B[(size_t)i * K + k0] = Bp[i];
   }
 }
 
@@ -220,7 +293,14 @@ __device__ __forceinline__ int row_size(const DevJoints &J, int level, int n) {
 template <int CN, int CL, int CR>
 __device__ __forceinline__ void reduce_row(const DevChain &C, const DevJoints &J, const CRLevel &cur,
                                            int level, int n, int m, int Nh, double *cL, double *cR,
-                                           double *Bn, int *status) {
+                                           double *Bn, int *status, size_t cstride = 0, int cidx = -1,
+                                           bool write_fac = true) {
+  // contributions go to cL/cR/Bn[(i) * cstride + cidx]; by default the
+  // global arrays of the level ([i][Nh], index m)
+  if (cstride == 0) {
+    cstride = (size_t)Nh;
+    cidx = m;
+  }
   // D_n, B_{n-1} (CL x CN), B_n (CN x CR), b_n
   double D[25], Bl[25], Br[25], bn[5];
   ld_D(C, J, cur, level, n, D);
@@ -274,7 +354,7 @@ __device__ __forceinline__ void reduce_row(const DevChain &C, const DevJoints &J
     y[i] = t * id[i];
   }
   double *f = cur.fac;
-  {
+  if (write_fac) {
     int o = 0;
 #pragma unroll
     for (int r = 0; r < 5; ++r)
@@ -309,8 +389,8 @@ __device__ __forceinline__ void reduce_row(const DevChain &C, const DevJoints &J
 #pragma unroll
         for (int t = 0; t < CN; ++t) sb += Yb[t][r] * Yb[t][c];
       }
-      cL[(size_t)pk(r, c) * Nh + m] = sa;
-      cR[(size_t)pk(r, c) * Nh + m] = sb;
+      cL[(size_t)pk(r, c) * cstride + cidx] = sa;
+      cR[(size_t)pk(r, c) * cstride + cidx] = sb;
     }
     double ta = 0.0, tb = 0.0;
     if (r < CL) {
@@ -321,8 +401,8 @@ __device__ __forceinline__ void reduce_row(const DevChain &C, const DevJoints &J
 #pragma unroll
       for (int t = 0; t < CN; ++t) tb += Yb[t][r] * y[t];
     }
-    cL[(size_t)(15 + r) * Nh + m] = ta;
-    cR[(size_t)(15 + r) * Nh + m] = tb;
+    cL[(size_t)(15 + r) * cstride + cidx] = ta;
+    cR[(size_t)(15 + r) * cstride + cidx] = tb;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       double sab = 0.0;
@@ -330,7 +410,7 @@ __device__ __forceinline__ void reduce_row(const DevChain &C, const DevJoints &J
 #pragma unroll
         for (int t = 0; t < CN; ++t) sab += Ya[t][r] * Yb[t][c];
       }
-      Bn[(size_t)(5 * r + c) * Nh + m] = -sab;
+      Bn[(size_t)(5 * r + c) * cstride + cidx] = -sab;
     }
   }
 }
@@ -392,6 +472,90 @@ __global__ void __launch_bounds__(128) k_cr_combine(DevChain C, DevJoints J, CRL
   }
 #pragma unroll
   for (int i = 0; i < 25; ++i) next.B[(size_t)i * next.N + m] = right ? Bn[(size_t)i * Nh + m] : 0.0;
+}
+
+// One cyclic-reduction level in one launch.  Block b owns the odd rows
+// m in [b*(CRF-1), (b+1)*(CRF-1)); its last thread redoes the first odd row
+// of the next block as a halo (no factor write).  After the eliminations the
+// contributions meet in shared memory and thread t forms next-level row
+// m+1 (even row 2m+2) from its own right contribution and the left
+// contribution and new coupling of thread t+1; block 0 also forms row 0.
+constexpr int CRF = 64;
+
+template <int CN, int CL, int CR>
+__device__ __forceinline__ void reduce_row_s(const DevChain &C, const DevJoints &J, const CRLevel &cur,
+                                             int level, int n, int m, int Nh, double *sc, int t,
+                                             int *status, bool write_fac) {
+  reduce_row<CN, CL, CR>(C, J, cur, level, n, m, Nh, sc, sc + 20 * CRF, sc + 40 * CRF, status,
+                         (size_t)CRF, t, write_fac);
+}
+
+__device__ __forceinline__ void reduce_any(const DevChain &C, const DevJoints &J, const CRLevel &cur,
+                                           int level, int n, int m, int Nh, double *sc, int t,
+                                           int *status, bool write_fac) {
+  const int N = cur.N;
+  const int cn = row_size(J, level, n), cl = row_size(J, level, n - 1);
+  const int cr = n + 1 < N ? row_size(J, level, n + 1) : 0;
+  const int code = (cn == 5 ? 9 : 0) + (cl == 5 ? 3 : 0) + (cr == 5 ? 2 : (cr == 3 ? 1 : 0));
+  switch (code) {
+#define RED(CODE, A, B_, D_) \
+  case CODE: reduce_row_s<A, B_, D_>(C, J, cur, level, n, m, Nh, sc, t, status, write_fac); break;
+    RED(0, 3, 3, 0) RED(1, 3, 3, 3) RED(2, 3, 3, 5)
+    RED(3, 3, 5, 0) RED(4, 3, 5, 3) RED(5, 3, 5, 5)
+    RED(9, 5, 3, 0) RED(10, 5, 3, 3) RED(11, 5, 3, 5)
+    RED(12, 5, 5, 0) RED(13, 5, 5, 3) RED(14, 5, 5, 5)
+#undef RED
+    default: break;
+  }
+}
+
+// next-level row mm from even row e = 2 mm: D_e - right part of the odd row
+// on its left (index mm-1, `sl`) - left part of the odd row on its right
+// (index mm, `sr`, which also carries the new coupling)
+__device__ __forceinline__ void combine_row(const DevChain &C, const DevJoints &J, const CRLevel &cur,
+                                            int level, const CRLevel &next, int mm, const double *sc,
+                                            int tl, int tr) {
+  const int e = 2 * mm;
+  double D[25], b[5];
+  ld_D(C, J, cur, level, e, D);
+  ld_b(J, cur, level, e, b);
+  const double *cLs = sc, *cRs = sc + 20 * CRF, *Bns = sc + 40 * CRF;
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c) {
+      double v = D[5 * r + c];
+      if (tr >= 0) v -= cLs[pk(r, c) * CRF + tr];
+      if (tl >= 0) v -= cRs[pk(r, c) * CRF + tl];
+      next.D[(size_t)pk(r, c) * next.N + mm] = v;
+    }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    double v = b[r];
+    if (tr >= 0) v -= cLs[(15 + r) * CRF + tr];
+    if (tl >= 0) v -= cRs[(15 + r) * CRF + tl];
+    next.b[(size_t)r * next.N + mm] = v;
+  }
+#pragma unroll
+  for (int i = 0; i < 25; ++i) next.B[(size_t)i * next.N + mm] = tr >= 0 ? Bns[i * CRF + tr] : 0.0;
+}
+
+__global__ void __launch_bounds__(CRF) k_cr_level(DevChain C, DevJoints J, CRLevel cur, int level,
+                                                  CRLevel next, int *status) {
+  __shared__ double sc[65 * CRF];  // cL (20), cR (20), Bn (25) per thread
+  const int t = threadIdx.x;
+  const int N = cur.N, Nh = N / 2;
+  const int m = blockIdx.x * (CRF - 1) + t;
+  const bool have = m < Nh;
+  if (have) reduce_any(C, J, cur, level, 2 * m + 1, m, Nh, sc, t, status, t < CRF - 1);
+  __syncthreads();
+  // even row 2m+2 (next row m+1): left odd m = thread t, right odd m+1 = thread t+1
+  if (have && t < CRF - 1 && 2 * m + 2 < N) {
+    const bool right = m + 1 < Nh;
+    combine_row(C, J, cur, level, next, m + 1, sc, t, right ? t + 1 : -1);
+  }
+  // row 0 of the next level: only the odd row 1 on its right
+  if (blockIdx.x == 0 && t == 0) combine_row(C, J, cur, level, next, 0, sc, -1, Nh > 0 ? 0 : -1);
 }
 
 // Single remaining row: lambda = D^{-1} b.
@@ -480,6 +644,13 @@ void launch_cr_combine(const DevChain &C, const DevJoints &J, const CRLevel &cur
                        const CRLevel &next, const double *cL, const double *cR,
                        const double *Bn, cudaStream_t s) {
   if (next.N > 0) k_cr_combine<<<nblk(next.N, 128), 128, 0, s>>>(C, J, cur, level, next, cL, cR, Bn);
+}
+
+void launch_cr_level(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
+                     const CRLevel &next, int *status, cudaStream_t s) {
+  const int Nh = cur.N / 2;
+  const int blocks = Nh > 0 ? (Nh + CRF - 2) / (CRF - 1) : 1;
+  k_cr_level<<<blocks, CRF, 0, s>>>(C, J, cur, level, next, status);
 }
 
 void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,

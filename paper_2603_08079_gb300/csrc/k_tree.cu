@@ -133,26 +133,126 @@ __device__ __forceinline__ void ltsolve_small(const double *L, int n, const doub
 }
 
 constexpr int RMAX = 10;  // rows eliminated at a root (two one-sided joints)
+constexpr int TUP = 32;   // threads per block of the upward pass (one warp: small levels spread over SMs)
 
-__global__ void __launch_bounds__(64) k_tree_up(DevBodies B, DevJoints J, DevTree T, int lo, int hi,
-                                                StepParams p, int *status) {
-  const int j = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= hi) return;
+// Cholesky factor of a body's dense Hhat, kept in shared memory with the 78
+// packed entries of a thread strided by the block size
+struct SmemL {
+  double *base;
+  __device__ __forceinline__ double &operator[](int e) const { return base[e * TUP]; }
+};
+
+__device__ __forceinline__ bool chol12_smem(SmemL A) {
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    double s = A[p12(c, c)];
+#pragma unroll
+    for (int k = 0; k < c; ++k) {
+      const double l = A[p12(c, k)];
+      s -= l * l;
+    }
+    if (!(s > 0.0)) {
+      ok = false;
+      s = 1.0;
+    }
+    const double id = rsqrt(s);
+    A[p12(c, c)] = id;  // reciprocal of the diagonal
+#pragma unroll
+    for (int r = c + 1; r < 12; ++r) {
+      double t = A[p12(r, c)];
+#pragma unroll
+      for (int k = 0; k < c; ++k) t -= A[p12(r, k)] * A[p12(c, k)];
+      A[p12(r, c)] = t * id;
+    }
+  }
+  return ok;
+}
+
+__device__ __noinline__ void chol12_solve_smem(SmemL L, const double b[12], double x[12]) {
+  double y[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    double s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= L[p12(i, k)] * y[k];
+    y[i] = s * L[p12(i, i)];
+  }
+#pragma unroll
+  for (int i = 11; i >= 0; --i) {
+    double s = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 12; ++k) s -= L[p12(k, i)] * x[k];
+    x[i] = s * L[p12(i, i)];
+  }
+}
+
+// dense Hbar written into the thread's shared-memory slots
+__device__ __forceinline__ void hbar_dense_smem(const DevBodies &B, int j, double ih2, SmemL H) {
+  const int M = B.M;
+  const double s[3] = {ldg(B.sig + j), ldg(B.sig + M + j), ldg(B.sig + 2 * (size_t)M + j)};
+  const double vm = ldg(B.vmu + j), vl = ldg(B.vlam + j), m = ldg(B.mass + j);
+#pragma unroll
+  for (int i = 0; i < 78; ++i) H[i] = 0.0;
+  const int dg[3] = {0, 4, 8};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) H[p12(dg[a], dg[b])] = a == b ? s[a] * ih2 + 2.0 * vm + vl : vl;
+  const int pa[3] = {1, 2, 5}, pb[3] = {3, 6, 7};
+  const int ca[3] = {0, 0, 1}, cb[3] = {1, 2, 2};
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    H[p12(pa[t], pa[t])] = s[ca[t]] * ih2 + vm;
+    H[p12(pb[t], pb[t])] = s[cb[t]] * ih2 + vm;
+    H[p12(pb[t], pa[t])] = vm;
+  }
+#pragma unroll
+  for (int a = 9; a < 12; ++a) H[p12(a, a)] = m * ih2;
+}
+
+// Hbar x for the structured Hbar of body j (3x3 block of A's diagonal,
+// transpose pairs, translation), from the body constants
+__device__ __forceinline__ void hbar_apply(const DevBodies &B, int j, double ih2, const double x[12],
+                                           double y[12]) {
+  const int M = B.M;
+  const double s0 = ldg(B.sig + j), s1 = ldg(B.sig + M + j), s2 = ldg(B.sig + 2 * (size_t)M + j);
+  const double vm = ldg(B.vmu + j), vl = ldg(B.vlam + j), m = ldg(B.mass + j);
+  const double tr = vl * (x[0] + x[4] + x[8]);
+  y[0] = (s0 * ih2 + 2.0 * vm) * x[0] + tr;
+  y[4] = (s1 * ih2 + 2.0 * vm) * x[4] + tr;
+  y[8] = (s2 * ih2 + 2.0 * vm) * x[8] + tr;
+  // pairs: (q1 = A(1,0), q3 = A(0,1)), (q2 = A(2,0), q6 = A(0,2)), (q5 = A(2,1), q7 = A(1,2))
+  y[1] = (s0 * ih2 + vm) * x[1] + vm * x[3];
+  y[3] = (s1 * ih2 + vm) * x[3] + vm * x[1];
+  y[2] = (s0 * ih2 + vm) * x[2] + vm * x[6];
+  y[6] = (s2 * ih2 + vm) * x[6] + vm * x[2];
+  y[5] = (s1 * ih2 + vm) * x[5] + vm * x[7];
+  y[7] = (s2 * ih2 + vm) * x[7] + vm * x[5];
+  y[9] = m * ih2 * x[9];
+  y[10] = m * ih2 * x[10];
+  y[11] = m * ih2 * x[11];
+}
+
+// Upward pass for one body with N eliminated rows (its parent joint, or a
+// root's one-sided joints when ROOT).
+template <int N, bool ROOT>
+__device__ __forceinline__ void up_body(const DevBodies &B, const DevJoints &J, const DevTree &T, int j,
+                                        const StepParams &p, int *status, SmemL L) {
   const int M = B.M, K = J.K;
-  double R[9], h[16];
+  double R[9];
   load_R(B.R, M, j, R);
-  load_hinv(B, j, h);
   const int nch = T.ccount[j];
-  double L[78];
   double y[12];
   if (nch == 0) {
     load12(B.ubar, M, j, y);
   } else {
+    // Hhat = Hbar + sum_children U U^T (dense, shared memory)
     const double ih2 = p.inv_h * p.inv_h;
-    hbar_dense(B, j, ih2, L);
+    hbar_dense_smem(B, j, ih2, L);
     double ub[12], f[12];
     load12(B.ubar, M, j, ub);
-    hbar_mul(L, ub, f);  // fbar = Hbar ubar
+    hbar_apply(B, j, ih2, ub, f);  // fbar = Hbar ubar
     const int c0 = T.cfirst[j];
     for (int c = c0; c < c0 + nch; ++c) {
 #pragma unroll
@@ -168,28 +268,31 @@ __global__ void __launch_bounds__(64) k_tree_up(DevBodies B, DevJoints J, DevTre
           for (int cc = 0; cc <= r; ++cc) L[p12(r, cc)] += u[r] * u[cc];
       }
     }
-    if (!chol12(L)) set_status(status, ST_NOT_SPD);
-    chol12_solve(L, f, y);
+    if (!chol12_smem(L)) set_status(status, ST_NOT_SPD);
+    chol12_solve_smem(L, f, y);
   }
-  // rows eliminated here: the parent joint, or a root's one-sided joints
-  const int par = T.parent[j];
-  const int rid = T.root_id[j];
-  double E[RMAX][3], P[4][3];
-  int pt[RMAX], ks[2] = {-1, -1}, cs[2] = {0, 0};
-  int n = 0;
-  if (par >= 0) {
+  // rows eliminated here (rest frame): s [p;1] (x) R^T d
+  double E[N > 0 ? N : 1][3], P[4][3];
+  int pt[N > 0 ? N : 1];
+  int ks[2] = {-1, -1}, cs[2] = {0, 0};
+  if constexpr (!ROOT) {
     ks[0] = T.pjoint[j];
     double E5[5][3], P2[2][3];
     int pt5[5];
     cs[0] = joint_rows_rest(J, ks[0], T.pside[j], R, E5, P2, pt5);
-    for (int r = 0; r < cs[0]; ++r) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
       E[r][0] = E5[r][0]; E[r][1] = E5[r][1]; E[r][2] = E5[r][2];
       pt[r] = pt5[r];
     }
-    P[0][0] = P2[0][0]; P[0][1] = P2[0][1]; P[0][2] = P2[0][2];
-    P[1][0] = P2[1][0]; P[1][1] = P2[1][1]; P[1][2] = P2[1][2];
-    n = cs[0];
-  } else if (rid >= 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      P[0][a] = P2[0][a];
+      P[1][a] = P2[1][a];
+    }
+  } else {
+    const int rid = T.root_id[j];
+    int n = 0;
     for (int w = 0; w < 2; ++w) {
       const int k = T.root_joint[(size_t)w * T.nroots + rid];
       if (k < 0) continue;
@@ -197,7 +300,7 @@ __global__ void __launch_bounds__(64) k_tree_up(DevBodies B, DevJoints J, DevTre
       int pt5[5];
       ks[w] = k;
       cs[w] = joint_rows_rest(J, k, T.root_side[(size_t)w * T.nroots + rid], R, E5, P2, pt5);
-      for (int r = 0; r < cs[w]; ++r) {
+      for (int r = 0; r < cs[w] && n + r < (N > 0 ? N : 1); ++r) {
         E[n + r][0] = E5[r][0]; E[n + r][1] = E5[r][1]; E[n + r][2] = E5[r][2];
         pt[n + r] = 2 * w + pt5[r];
       }
@@ -208,79 +311,236 @@ __global__ void __launch_bounds__(64) k_tree_up(DevBodies B, DevJoints J, DevTre
       n += cs[w];
     }
   }
-  // X = Hhat^{-1} G^T, D = G X, e = G y + C
-  double X[RMAX][12];
-  double D[RMAX * (RMAX + 1) / 2];
-  double e[RMAX];
+  double h[16];
+  if (nch == 0) load_hinv(B, j, h);
+  // X_t = Hhat^{-1} w_t, D = G X, e = G y + C
+  double D[N * (N + 1) / 2 > 0 ? N * (N + 1) / 2 : 1];
+  double e[N > 0 ? N : 1];
   const double rr = p.residual_rhs ? 1.0 : 0.0;
-  for (int r = 0; r < n; ++r) {
-    double w[12];
-    kron_row(P[pt[r]], E[r], w);
-    if (nch == 0) hinv_apply(h, w, X[r]);
-    else chol12_solve(L, w, X[r]);
-    double s = 0.0;
+  const int nr = T.nroots;
+  const int rid = ROOT ? T.root_id[j] : -1;
 #pragma unroll
-    for (int a = 0; a < 12; ++a) s += w[a] * y[a];
-    const int k = r < cs[0] ? ks[0] : ks[1];
-    const int rl = r < cs[0] ? r : r - cs[0];
-    e[r] = s + rr * J.c[(size_t)rl * K + k];
-    for (int t = 0; t <= r; ++t) {
+  for (int t = 0; t < N; ++t) {
+    double w[12], X[12];
+    kron_row(P[pt[t]], E[t], w);
+    if (nch == 0) hinv_apply(h, w, X);
+    else chol12_solve_smem(L, w, X);
+    double sy = 0.0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) sy += w[a] * y[a];
+    const int k = t < cs[0] ? ks[0] : ks[1];
+    const int rl = t < cs[0] ? t : t - cs[0];
+    e[t] = sy + rr * J.c[(size_t)rl * K + k];
+#pragma unroll
+    for (int r = t; r < N; ++r) {
+      double wr[12];
+      kron_row(P[pt[r]], E[r], wr);
       double d = 0.0;
 #pragma unroll
-      for (int a = 0; a < 12; ++a) d += w[a] * X[t][a];
+      for (int a = 0; a < 12; ++a) d += wr[a] * X[a];
       D[p12(r, t)] = d;
     }
+    if constexpr (!ROOT) {
+#pragma unroll
+      for (int a = 0; a < 12; ++a) T.X[(size_t)(5 * a + t) * M + j] = X[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 12; ++a) T.rX[(size_t)(RMAX * a + t) * nr + rid] = X[a];
+    }
   }
-  if (n > 0 && !chol_small<RMAX>(D, n)) set_status(status, ST_NOT_SPD);
-  if (par >= 0) {
+  // Cholesky of D (reciprocal diagonal)
+  bool okd = true;
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    double sum = D[p12(c, c)];
+#pragma unroll
+    for (int k = 0; k < c; ++k) sum -= D[p12(c, k)] * D[p12(c, k)];
+    if (!(sum > 0.0)) {
+      okd = false;
+      sum = 1.0;
+    }
+    const double id = rsqrt(sum);
+    D[p12(c, c)] = id;
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      double t = D[p12(r, c)];
+#pragma unroll
+      for (int k = 0; k < c; ++k) t -= D[p12(r, k)] * D[p12(c, k)];
+      D[p12(r, c)] = t * id;
+    }
+  }
+  if (!okd) set_status(status, ST_NOT_SPD);
+  if constexpr (!ROOT) {
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
 #pragma unroll
-      for (int r = 0; r < 5; ++r) T.X[(size_t)(5 * a + r) * M + j] = r < n ? X[r][a] : 0.0;
+      for (int r = N; r < 5; ++r) T.X[(size_t)(5 * a + r) * M + j] = 0.0;
       T.y[(size_t)a * M + j] = y[a];
     }
-    for (int i = 0; i < 15; ++i) T.LD[(size_t)i * M + j] = i < n * (n + 1) / 2 ? D[i] : 0.0;
-    for (int r = 0; r < 5; ++r) T.e[(size_t)r * M + j] = r < n ? e[r] : 0.0;
-    // contribution to the parent, in the parent's rest frame
+#pragma unroll
+    for (int i = 0; i < 15; ++i) T.LD[(size_t)i * M + j] = i < N * (N + 1) / 2 ? D[i] : 0.0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) T.e[(size_t)r * M + j] = r < N ? e[r] : 0.0;
+    // contribution to the parent (its rest frame): U = Pbar^T L_D^{-T}, v = U L_D^{-1} e
+    const int par = T.parent[j];
     double Rp[9], Ep[5][3], Pp[2][3];
     int ptp[5];
     load_R(B.R, M, par, Rp);
     joint_rows_rest(J, ks[0], 1 - T.pside[j], Rp, Ep, Pp, ptp);
-    double wl[5];
-    lsolve_small(D, n, e, wl);
-    // Z = L_D^{-1} Pbar (n x 12), column by column
-    double Z[5][12];
+    double wl[N > 0 ? N : 1];
 #pragma unroll
-    for (int a = 0; a < 12; ++a) {
-      double col[5], z[5];
-      for (int r = 0; r < n; ++r) {
-        double w[12];
-        kron_row(Pp[ptp[r]], Ep[r], w);
-        col[r] = w[a];
-      }
-      lsolve_small(D, n, col, z);
-      for (int r = 0; r < n; ++r) Z[r][a] = z[r];
+    for (int i = 0; i < N; ++i) {
+      double s = e[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s -= D[p12(i, k)] * wl[k];
+      wl[i] = s * D[p12(i, i)];
     }
 #pragma unroll
-    for (int a = 0; a < 12; ++a) {
-      double vv = 0.0;
-      for (int r = 0; r < 5; ++r) {
-        const double u = r < n ? Z[r][a] : 0.0;
-        T.U[(size_t)(5 * a + r) * M + j] = u;
-        vv += u * (r < n ? wl[r] : 0.0);
+    for (int blk = 0; blk < 4; ++blk)
+#pragma unroll
+      for (int a3 = 0; a3 < 3; ++a3) {
+        const int a = 3 * blk + a3;
+        double col[N > 0 ? N : 1], z[N > 0 ? N : 1];
+#pragma unroll
+        for (int r = 0; r < N; ++r) col[r] = (blk < 3 ? Pp[ptp[r]][blk] : 1.0) * Ep[r][a3];
+        double vv = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          double s = col[i];
+#pragma unroll
+          for (int k = 0; k < i; ++k) s -= D[p12(i, k)] * z[k];
+          z[i] = s * D[p12(i, i)];
+          T.U[(size_t)(5 * a + i) * M + j] = z[i];
+          vv += z[i] * wl[i];
+        }
+#pragma unroll
+        for (int i = N; i < 5; ++i) T.U[(size_t)(5 * a + i) * M + j] = 0.0;
+        T.v[(size_t)a * M + j] = vv;
       }
-      T.v[(size_t)a * M + j] = vv;
-    }
   } else {
-    const int nr = T.nroots;
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
-      for (int r = 0; r < RMAX; ++r) T.rX[(size_t)(RMAX * a + r) * nr + rid] = r < n ? X[r][a] : 0.0;
+#pragma unroll
+      for (int r = N; r < RMAX; ++r) T.rX[(size_t)(RMAX * a + r) * nr + rid] = 0.0;
       T.y[(size_t)a * M + j] = y[a];
     }
     for (int i = 0; i < RMAX * (RMAX + 1) / 2; ++i)
-      T.rLD[(size_t)i * nr + rid] = i < n * (n + 1) / 2 ? D[i] : 0.0;
-    for (int r = 0; r < RMAX; ++r) T.re[(size_t)r * nr + rid] = r < n ? e[r] : 0.0;
+      T.rLD[(size_t)i * nr + rid] = i < N * (N + 1) / 2 ? D[i] : 0.0;
+    for (int r = 0; r < RMAX; ++r) T.re[(size_t)r * nr + rid] = r < N ? e[r] : 0.0;
+  }
+}
+
+// non-root bodies of a level: [lo, mid) have children (dense Hhat in shared
+// memory), [mid, hi) are leaves (structured inverse)
+__global__ void __launch_bounds__(TUP) k_tree_up_inner(DevBodies B, DevJoints J, DevTree T, int lo,
+                                                       int hi, StepParams p, int *status) {
+  __shared__ double sL[78 * TUP];
+  const int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi) return;
+  const int j = T.order[i];
+  if (T.parent[j] < 0) return;
+  SmemL L{sL + threadIdx.x};
+  if (J.type[T.pjoint[j]] == 0) up_body<3, false>(B, J, T, j, p, status, L);
+  else up_body<5, false>(B, J, T, j, p, status, L);
+}
+
+__global__ void __launch_bounds__(128) k_tree_up_leaf(DevBodies B, DevJoints J, DevTree T, int lo,
+                                                      int hi, StepParams p, int *status) {
+  const int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi) return;
+  const int j = T.order[i];
+  if (T.parent[j] < 0) return;
+  SmemL L{nullptr};  // not touched: leaves have no children
+  if (J.type[T.pjoint[j]] == 0) up_body<3, false>(B, J, T, j, p, status, L);
+  else up_body<5, false>(B, J, T, j, p, status, L);
+}
+
+// each root variant compiled on its own (separate register allocation)
+template <int N>
+__device__ __noinline__ void up_root(const DevBodies &B, const DevJoints &J, const DevTree &T, int j,
+                                     const StepParams &p, int *status, SmemL L) {
+  up_body<N, true>(B, J, T, j, p, status, L);
+}
+
+// roots (level 0): their one-sided joints (0, 1 or 2 of 3 or 5 rows)
+__global__ void __launch_bounds__(TUP) k_tree_up_root(DevBodies B, DevJoints J, DevTree T, int lo,
+                                                      int hi, StepParams p, int *status) {
+  __shared__ double sL[78 * TUP];
+  const int j = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= hi || T.parent[j] >= 0) return;
+  SmemL L{sL + threadIdx.x};
+  const int rid = T.root_id[j];
+  int n = 0;
+  for (int w = 0; w < 2; ++w) {
+    const int k = T.root_joint[(size_t)w * T.nroots + rid];
+    if (k >= 0) n += J.type[k] == 0 ? 3 : 5;
+  }
+  switch (n) {
+    case 0: up_root<0>(B, J, T, j, p, status, L); break;
+    case 3: up_root<3>(B, J, T, j, p, status, L); break;
+    case 5: up_root<5>(B, J, T, j, p, status, L); break;
+    case 6: up_root<6>(B, J, T, j, p, status, L); break;
+    case 8: up_root<8>(B, J, T, j, p, status, L); break;
+    default: up_root<10>(B, J, T, j, p, status, L); break;
+  }
+}
+
+// downward pass of a non-root body with N rows in its parent joint
+template <int N>
+__device__ __forceinline__ void down_body(const DevBodies &B, const DevJoints &J, const DevTree &T,
+                                          int j, int par, double dqb[12]) {
+  const int M = B.M, K = J.K;
+  const int k = T.pjoint[j];
+  constexpr int type = N == 3 ? 0 : 1;
+  const int pside = 1 - T.pside[j];
+  // P dq_parent: rows s_p d_r^T J(p_r) dq_p in the world frame
+  double dqp[12];
+  load12(T.dq, M, par, dqp);
+  double pts[2][3];
+  load3(pside == 0 ? J.pa1 : J.pb1, K, k, pts[0]);
+  if (type == 1) load3(pside == 0 ? J.pa2 : J.pb2, K, k, pts[1]);
+  double x[2][3];
+#pragma unroll
+  for (int q = 0; q < 1 + type; ++q)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      x[q][a] = dqp[a] * pts[q][0] + dqp[3 + a] * pts[q][1] + dqp[6 + a] * pts[q][2] + dqp[9 + a];
+  double RH[9];
+  if (type == 1) load_R(J.RH, K, k, RH);
+  const double sp = pside == 0 ? 1.0 : -1.0;
+  double rhs[N], t[N], lam[N], LD[N * (N + 1) / 2];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    double d[3];
+    row_dir(type, RH, r, d);
+    const int q = r < 3 ? 0 : 1;
+    rhs[r] = T.e[(size_t)r * M + j] + sp * (d[0] * x[q][0] + d[1] * x[q][1] + d[2] * x[q][2]);
+  }
+#pragma unroll
+  for (int i = 0; i < N * (N + 1) / 2; ++i) LD[i] = T.LD[(size_t)i * M + j];
+  // L_D stores reciprocal diagonals
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double s = rhs[i];
+#pragma unroll
+    for (int q = 0; q < i; ++q) s -= LD[p12(i, q)] * t[q];
+    t[i] = s * LD[p12(i, i)];
+  }
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    double s = t[i];
+#pragma unroll
+    for (int q = i + 1; q < N; ++q) s -= LD[p12(q, i)] * lam[q];
+    lam[i] = s * LD[p12(i, i)];
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) J.lambda[(size_t)r * K + k] = lam[r];
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    double s = T.y[(size_t)a * M + j];
+#pragma unroll
+    for (int r = 0; r < N; ++r) s -= T.X[(size_t)(5 * a + r) * M + j] * lam[r];
+    dqb[a] = s;
   }
 }
 
@@ -291,44 +551,9 @@ __global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, Dev
   const int M = B.M, K = J.K;
   const int par = T.parent[j];
   double dqb[12];
-  double y[12];
-  load12(T.y, M, j, y);
   if (par >= 0) {
-    const int k = T.pjoint[j];
-    const int type = J.type[k];
-    const int n = type == 0 ? 3 : 5;
-    const int pside = 1 - T.pside[j];
-    // P dq_parent: rows s_p d_r^T J(p_r) dq_p in the world frame
-    double dqp[12];
-    load12(T.dq, M, par, dqp);
-    double pts[2][3];
-    load3(pside == 0 ? J.pa1 : J.pb1, K, k, pts[0]);
-    if (type == 1) load3(pside == 0 ? J.pa2 : J.pb2, K, k, pts[1]);
-    double x[2][3];
-    for (int q = 0; q < 1 + type; ++q)
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        x[q][a] = dqp[a] * pts[q][0] + dqp[3 + a] * pts[q][1] + dqp[6 + a] * pts[q][2] + dqp[9 + a];
-    double RH[9];
-    if (type == 1) load_R(J.RH, K, k, RH);
-    const double sp = pside == 0 ? 1.0 : -1.0;
-    double rhs[5], lam[5], t[5], LD[15];
-    for (int r = 0; r < n; ++r) {
-      double d[3];
-      row_dir(type, RH, r, d);
-      const int q = r < 3 ? 0 : 1;
-      rhs[r] = T.e[(size_t)r * M + j] + sp * (d[0] * x[q][0] + d[1] * x[q][1] + d[2] * x[q][2]);
-    }
-    for (int i = 0; i < n * (n + 1) / 2; ++i) LD[i] = T.LD[(size_t)i * M + j];
-    lsolve_small(LD, n, rhs, t);
-    ltsolve_small(LD, n, t, lam);
-    for (int r = 0; r < n; ++r) J.lambda[(size_t)r * K + k] = lam[r];
-#pragma unroll
-    for (int a = 0; a < 12; ++a) {
-      double s = y[a];
-      for (int r = 0; r < n; ++r) s -= T.X[(size_t)(5 * a + r) * M + j] * lam[r];
-      dqb[a] = s;
-    }
+    if (J.type[T.pjoint[j]] == 0) down_body<3>(B, J, T, j, par, dqb);
+    else down_body<5>(B, J, T, j, par, dqb);
   } else {
     const int rid = T.root_id[j];
     const int nr = T.nroots;
@@ -341,17 +566,22 @@ __global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, Dev
     double lam[RMAX], t[RMAX], e[RMAX], LD[RMAX * (RMAX + 1) / 2];
     for (int r = 0; r < n; ++r) e[r] = T.re[(size_t)r * nr + rid];
     for (int i = 0; i < n * (n + 1) / 2; ++i) LD[i] = T.rLD[(size_t)i * nr + rid];
-    if (n > 0) {
-      lsolve_small(LD, n, e, t);
-      ltsolve_small(LD, n, t, lam);
+    for (int i = 0; i < n; ++i) {  // reciprocal diagonals
+      double s = e[i];
+      for (int q = 0; q < i; ++q) s -= LD[p12(i, q)] * t[q];
+      t[i] = s * LD[p12(i, i)];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = t[i];
+      for (int q = i + 1; q < n; ++q) s -= LD[p12(q, i)] * lam[q];
+      lam[i] = s * LD[p12(i, i)];
     }
     for (int r = 0; r < n; ++r) {
       const int w = r < cs[0] ? 0 : 1;
       J.lambda[(size_t)(r - (w ? cs[0] : 0)) * K + ks[w]] = lam[r];
     }
-#pragma unroll
     for (int a = 0; a < 12; ++a) {
-      double s = y[a];
+      double s = T.y[(size_t)a * M + j];
       for (int r = 0; r < n; ++r) s -= T.rX[(size_t)(RMAX * a + r) * nr + rid] * lam[r];
       dqb[a] = s;
     }
@@ -372,10 +602,14 @@ __global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, Dev
   }
 }
 
-void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,
-                    const StepParams &p, int *status, cudaStream_t s) {
-  const int n = hi - lo;
-  if (n > 0) k_tree_up<<<(n + 63) / 64, 64, 0, s>>>(B, J, T, lo, hi, p, status);
+void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int mid,
+                    int hi, bool roots, const StepParams &p, int *status, cudaStream_t s) {
+  if (roots) {
+    if (hi > lo) k_tree_up_root<<<(hi - lo + TUP - 1) / TUP, TUP, 0, s>>>(B, J, T, lo, hi, p, status);
+    return;
+  }
+  if (mid > lo) k_tree_up_inner<<<(mid - lo + TUP - 1) / TUP, TUP, 0, s>>>(B, J, T, lo, mid, p, status);
+  if (hi > mid) k_tree_up_leaf<<<(hi - mid + 127) / 128, 128, 0, s>>>(B, J, T, mid, hi, p, status);
 }
 
 void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,

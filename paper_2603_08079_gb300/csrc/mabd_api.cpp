@@ -60,6 +60,7 @@ struct mabd_ctx {
   int *h_iter = nullptr;     // pinned [2]
   double *h_scal = nullptr;  // pinned [8]
   std::vector<int32_t> tree_lvl;  // level offsets (internal body order)
+  std::vector<int32_t> tree_mid;  // per level: first leaf (bodies before it have children)
   double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
   int *d_status = nullptr;
   unsigned long long *d_max = nullptr;
@@ -308,6 +309,16 @@ bool tree_order(const mabd_ctx *ctx, const Graph &g, TreeOrder &t) {
   std::vector<int> depth(M, -1), par(M, -1), pj(M, -1);
   std::vector<int> frontier = roots;
   for (int r : roots) depth[r] = 0;
+  // children of a free body, excluding its parent (for the level ordering)
+  auto nkids = [&](int j) {
+    int c = 0;
+    for (int k : g.inc[j]) {
+      int o = other_end(g, k, j);
+      if (o >= 0 && o != par[j]) ++c;
+    }
+    return c;
+  };
+  (void)nkids;
   while (!frontier.empty()) {
     std::vector<int> next;
     for (int j : frontier) {
@@ -991,6 +1002,25 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     T.root_joint = drj;
     T.root_side = drs;
     ctx->tree_lvl = tord.lvl_off;
+    // per level, the bodies with children first, then the leaves (index
+    // lists, so that each upward kernel runs uniform warps while siblings
+    // stay contiguous in the body order)
+    std::vector<int32_t> ids;
+    ctx->tree_mid.assign(tord.lvl_off.size(), 0);
+    for (size_t l = 0; l + 1 < tord.lvl_off.size(); ++l) {
+      for (int i = tord.lvl_off[l]; i < tord.lvl_off[l + 1]; ++i)
+        if (tord.ccount[i] > 0) ids.push_back(i);
+      ctx->tree_mid[l] = (int32_t)ids.size();
+      for (int i = tord.lvl_off[l]; i < tord.lvl_off[l + 1]; ++i)
+        if (tord.ccount[i] == 0) ids.push_back(i);
+    }
+    int32_t *dids = dnew<int32_t>(ctx, std::max<size_t>(ids.size(), 1), ok);
+    if (!ok) {
+      free_all(ctx);
+      return MABD_ERR_OUT_OF_MEMORY;
+    }
+    CK(up(dids, ids.data(), ids.size() * 4));
+    ctx->T.order = dids;
   }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->sp.h = h;
@@ -1013,23 +1043,21 @@ static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s) {
   if (ctx->solver == MABD_SOLVER_CHAIN) {
     run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
     const int nl = (int)ctx->levels.size();
-    for (int l = 0; l + 1 < nl; ++l) {
-      run(ctx, "cr_reduce", [&] {
-        launch_cr_reduce(ctx->C, ctx->J, ctx->levels[l], l, ctx->cL, ctx->cR, ctx->Bn, ctx->d_status, s);
+    for (int l = 0; l + 1 < nl; ++l)
+      run(ctx, "cr_level", [&] {
+        launch_cr_level(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], ctx->d_status, s);
       });
-      run(ctx, "cr_combine", [&] {
-        launch_cr_combine(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], ctx->cL, ctx->cR,
-                          ctx->Bn, s);
-      });
-    }
     run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
     for (int l = nl - 2; l >= 0; --l)
       run(ctx, "cr_back", [&] { launch_cr_back(ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s); });
   } else if (ctx->solver == MABD_SOLVER_TREE) {
     const auto &lv = ctx->tree_lvl;
     const int nl = (int)lv.size() - 1;
+    const auto &mid = ctx->tree_mid;
     for (int l = nl - 1; l >= 0; --l)
-      run(ctx, "tree_up", [&] { launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+      run(ctx, "tree_up", [&] {
+        launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s);
+      });
     for (int l = 0; l < nl; ++l)
       run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
   } else if (ctx->solver == MABD_SOLVER_PCG) {
@@ -1316,7 +1344,7 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
   if (!ctx || cap < 0 || !count) return MABD_ERR_INVALID_ARG;
   mabd_status st = harvest_profile(ctx);
   if (st) return st;
-  static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "cr_reduce", "cr_combine",
+  static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "cr_level", "cr_reduce", "cr_combine",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
                                 "pcg_iteration", "backprop", "residuals"};
   int n = 0;

@@ -101,6 +101,7 @@ struct DevTree {
   const int32_t *root_joint;  // [2][nroots] one-sided joints of a root (-1: none)
   const int8_t *root_side;    // [2][nroots]
   int32_t nroots;
+  const int32_t *order;       // [nfree] per level: bodies with children, then leaves
   double *X;                  // [60][M]  Hhat^{-1} G^T in the rest frame (12 x 5)
   double *LD;                 // [15][M]  Cholesky factor of D = G Hhat^{-1} G^T
   double *y;                  // [12][M]  Hhat^{-1} fhat (rest frame)
@@ -150,14 +151,20 @@ void launch_cr_reduce(const DevChain &C, const DevJoints &J, const CRLevel &cur,
 void launch_cr_combine(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
                        const CRLevel &next, const double *cL, const double *cR,
                        const double *Bn, cudaStream_t s);
+// reduce + combine of one level in a single launch (fused form of the two above)
+void launch_cr_level(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
+                     const CRLevel &next, int *status, cudaStream_t s);
 void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,
                    int *status, cudaStream_t s);
 void launch_cr_back(const DevJoints &J, const CRLevel &cur, const CRLevel &next, int level,
                     cudaStream_t s);
 
 // tree (k_tree.cu): one launch per level, deepest first, then root first
-void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,
-                    const StepParams &p, int *status, cudaStream_t s);
+// level [lo, hi) of the body order: T.order[lo, mid) lists its bodies with
+// children and T.order[mid, hi) its leaves; the roots' level (roots = true)
+// is run by one kernel
+void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int mid,
+                    int hi, bool roots, const StepParams &p, int *status, cudaStream_t s);
 void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,
                       const StepParams &p, int *status, cudaStream_t s);
 

@@ -34,7 +34,9 @@ def test_full_batch_of_4096_assemblies(ora):
 
 def test_batch_runs_many_steps_in_one_call(ora):
     """100 steps replayed from the step's CUDA graph stay finite and keep the
-    joints closed (the config's 1000-step run, shortened)."""
+    joints closed to Table 1's loosest printed tolerance (the oracle's own
+    residual on this scene after 100 steps is 1e-6 to 3e-6; the config's
+    1000-step run, shortened)."""
     need_gpu()
     sc = scenes.assemblies(256, seed=3)
     s = gpu_solver(sc)
@@ -45,4 +47,4 @@ def test_batch_runs_many_steps_in_one_call(ora):
     finally:
         s.close()
     assert np.all(np.isfinite(q)) and np.all(np.isfinite(qd))
-    assert st["joint_residual"] < 1e-6
+    assert st["joint_residual"] < 1e-5
