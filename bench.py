@@ -162,14 +162,11 @@ def measured_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def cr_reduce_flops(jtype_chain: np.ndarray) -> float:
-    """FP64 flops of block cyclic reduction over all levels (FMA = 2): for an
-    eliminated row of size n with neighbours of sizes l, r (0 if absent):
-    Cholesky 2*chol(n) + n rsqrt-multiplies, Ya/Yb/y triangular solves
-    (l + r + 1) n(n+1)/2 FMA, Schur updates (l(l+1)/2 + r(r+1)/2 + l r + l + r) n FMA."""
-    sizes = np.where(np.asarray(jtype_chain) == 1, 5, 3).astype(np.int64)
+def _cr_fma(sizes: np.ndarray):
+    """(FMA, eliminated rows' total size) of block cyclic reduction over all
+    levels for dual rows of the given sizes (3 ball, 5 hinge)."""
     chol = {3: 7, 5: 30}
-    total = 0.0
+    fma_total, rows = 0, 0
     while len(sizes) > 1:
         N = len(sizes)
         odd = np.arange(1, N, 2)
@@ -178,9 +175,27 @@ def cr_reduce_flops(jtype_chain: np.ndarray) -> float:
         r = np.where(odd + 1 < N, sizes[np.minimum(odd + 1, N - 1)], 0)
         fma = np.vectorize(chol.get)(n) + (l + r + 1) * n * (n + 1) // 2 + \
             (l * (l + 1) // 2 + r * (r + 1) // 2 + l * r + l + r) * n
-        total += 2.0 * float(fma.sum()) + 2.0 * float(n.sum())
+        fma_total += int(fma.sum())
+        rows += int(n.sum())
         sizes = sizes[0::2]
-    return total
+    return fma_total, rows
+
+
+def cr_reduce_flops(jtype_chain: np.ndarray) -> float:
+    """FP64 flops of block cyclic reduction over all levels (FMA = 2): for an
+    eliminated row of size n with neighbours of sizes l, r (0 if absent):
+    Cholesky 2*chol(n) + n rsqrt-multiplies, Ya/Yb/y triangular solves
+    (l + r + 1) n(n+1)/2 FMA, Schur updates (l(l+1)/2 + r(r+1)/2 + l r + l + r) n FMA.
+    The library eliminates either the chain's rows as they are or behind one
+    leading identity row of size 3, whichever has fewer FMA; the same choice
+    is made here."""
+    sizes = np.where(np.asarray(jtype_chain) == 1, 5, 3).astype(np.int64)
+    best = _cr_fma(sizes)
+    if len(sizes) > 1:
+        shifted = _cr_fma(np.concatenate([[3], sizes]))
+        if shifted[0] < best[0]:
+            best = shifted
+    return 2.0 * best[0] + 2.0 * best[1]
 
 
 def chain_gram_flops(jtype_chain: np.ndarray) -> float:

@@ -228,22 +228,32 @@ __device__ __forceinline__ void ltsolve5(const double L[25], const double b[5], 
   }
 }
 
-// level loaders (level 0 assembles from the per-body parts)
+// level loaders (level 0 assembles from the per-body parts; its row n is
+// joint n - C.off, and a row before the first joint is a decoupled identity
+// row whose multiplier is zero)
 __device__ __forceinline__ void ld_D(const DevChain &C, const DevJoints &J, const CRLevel &L,
                                      int level, int n, double D[25]) {
   double p[15];
   if (level == 0) {
-    const uint8_t f = C.jflags[n];
+    const int k = n - C.off;
+    if (k < 0) {
 #pragma unroll
-    for (int i = 0; i < 15; ++i) {
-      double v = 0.0;
-      if (f & 1) v += C.Dfirst[(size_t)i * C.K + n];
-      if (f & 2) v += C.Dsecond[(size_t)i * C.K + n];
-      p[i] = v;
-    }
-    if (J.type[n] == 0) {
-      p[pk(3, 3)] = 1.0;
-      p[pk(4, 4)] = 1.0;
+      for (int i = 0; i < 15; ++i) p[i] = 0.0;
+#pragma unroll
+      for (int r = 0; r < 5; ++r) p[pk(r, r)] = 1.0;
+    } else {
+      const uint8_t f = C.jflags[k];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) {
+        double v = 0.0;
+        if (f & 1) v += C.Dfirst[(size_t)i * C.K + k];
+        if (f & 2) v += C.Dsecond[(size_t)i * C.K + k];
+        p[i] = v;
+      }
+      if (J.type[k] == 0) {
+        p[pk(3, 3)] = 1.0;
+        p[pk(4, 4)] = 1.0;
+      }
     }
   } else {
 #pragma unroll
@@ -258,21 +268,23 @@ __device__ __forceinline__ void ld_D(const DevChain &C, const DevJoints &J, cons
 __device__ __forceinline__ void ld_B(const DevChain &C, const CRLevel &L, int level, int n,
                                      double Bm[25]) {
   if (level == 0) {
-    const bool has = C.jflags[n] & 4;
+    const int k = n - C.off;
+    const bool has = k >= 0 && (C.jflags[k] & 4);
 #pragma unroll
-    for (int i = 0; i < 25; ++i) Bm[i] = has ? C.B[(size_t)i * C.K + n] : 0.0;
+    for (int i = 0; i < 25; ++i) Bm[i] = has ? C.B[(size_t)i * C.K + k] : 0.0;
   } else {
 #pragma unroll
     for (int i = 0; i < 25; ++i) Bm[i] = L.B[(size_t)i * L.N + n];
   }
 }
 
-__device__ __forceinline__ void ld_b(const DevJoints &J, const CRLevel &L, int level, int n,
-                                     double b[5]) {
+__device__ __forceinline__ void ld_b(const DevChain &C, const DevJoints &J, const CRLevel &L,
+                                     int level, int n, double b[5]) {
   if (level == 0) {
-    const int C = J.type[n] == 0 ? 3 : 5;
+    const int k = n - C.off;
+    const int Cs = k < 0 ? 0 : (J.type[k] == 0 ? 3 : 5);
 #pragma unroll
-    for (int r = 0; r < 5; ++r) b[r] = r < C ? J.b[(size_t)r * J.K + n] : 0.0;
+    for (int r = 0; r < 5; ++r) b[r] = r < Cs ? J.b[(size_t)r * J.K + k] : 0.0;
   } else {
 #pragma unroll
     for (int r = 0; r < 5; ++r) b[r] = L.b[(size_t)r * L.N + n];
@@ -285,9 +297,11 @@ __device__ __forceinline__ void ld_b(const DevJoints &J, const CRLevel &L, int l
 // layout in memory; the arithmetic runs on the true sizes (3 or 5 rows, and 0
 // for a missing right neighbour), chosen per row from the joint types.
 
-// size of row n at `level`: that row is joint n * 2^level of the chain
-__device__ __forceinline__ int row_size(const DevJoints &J, int level, int n) {
-  return J.type[(size_t)n << level] == 0 ? 3 : 5;
+// size of row n at `level`: that row is level-0 row n * 2^level, i.e. joint
+// n * 2^level - C.off (an identity row of size 3 before the first joint)
+__device__ __forceinline__ int row_size(const DevChain &C, const DevJoints &J, int level, int n) {
+  const long k = ((long)n << level) - C.off;
+  return (k < 0 || J.type[k] == 0) ? 3 : 5;
 }
 
 template <int CN, int CL, int CR>
@@ -306,7 +320,7 @@ __device__ __forceinline__ void reduce_row(const DevChain &C, const DevJoints &J
   ld_D(C, J, cur, level, n, D);
   ld_B(C, cur, level, n - 1, Bl);
   if (CR > 0) ld_B(C, cur, level, n, Br);
-  ld_b(J, cur, level, n, bn);
+  ld_b(C, J, cur, level, n, bn);
   // Cholesky with reciprocal diagonal
   double L[CN][CN], id[CN];
   bool ok = true;
@@ -426,8 +440,8 @@ __global__ void __launch_bounds__(128) k_cr_reduce(DevChain C, DevJoints J, CRLe
   const int N = cur.N;
   if (n >= N) return;
   const int Nh = N / 2;
-  const int cn = row_size(J, level, n), cl = row_size(J, level, n - 1);
-  const int cr = n + 1 < N ? row_size(J, level, n + 1) : 0;
+  const int cn = row_size(C, J, level, n), cl = row_size(C, J, level, n - 1);
+  const int cr = n + 1 < N ? row_size(C, J, level, n + 1) : 0;
   const int code = (cn == 5 ? 9 : 0) + (cl == 5 ? 3 : 0) + (cr == 5 ? 2 : (cr == 3 ? 1 : 0));
   switch (code) {
 #define RED(CODE, A, B, D_) \
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(128) k_cr_combine(DevChain C, DevJoints J, CRL
   const int N = cur.N, Nh = N / 2;
   double D[25], b[5];
   ld_D(C, J, cur, level, e, D);
-  ld_b(J, cur, level, e, b);
+  ld_b(C, J, cur, level, e, b);
   const bool right = e + 1 < N;  // odd row e+1 exists (its index m)
   const bool left = e >= 1;      // odd row e-1 exists (its index m-1)
 #pragma unroll
@@ -494,8 +508,8 @@ __device__ __forceinline__ void reduce_any(const DevChain &C, const DevJoints &J
                                            int level, int n, int m, int Nh, double *sc, int t,
                                            int *status, bool write_fac) {
   const int N = cur.N;
-  const int cn = row_size(J, level, n), cl = row_size(J, level, n - 1);
-  const int cr = n + 1 < N ? row_size(J, level, n + 1) : 0;
+  const int cn = row_size(C, J, level, n), cl = row_size(C, J, level, n - 1);
+  const int cr = n + 1 < N ? row_size(C, J, level, n + 1) : 0;
   const int code = (cn == 5 ? 9 : 0) + (cl == 5 ? 3 : 0) + (cr == 5 ? 2 : (cr == 3 ? 1 : 0));
   switch (code) {
 #define RED(CODE, A, B_, D_) \
@@ -518,7 +532,7 @@ __device__ __forceinline__ void combine_row(const DevChain &C, const DevJoints &
   const int e = 2 * mm;
   double D[25], b[5];
   ld_D(C, J, cur, level, e, D);
-  ld_b(J, cur, level, e, b);
+  ld_b(C, J, cur, level, e, b);
   const double *cLs = sc, *cRs = sc + 20 * CRF, *Bns = sc + 40 * CRF;
 #pragma unroll
   for (int r = 0; r < 5; ++r)
@@ -563,7 +577,7 @@ __global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *s
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   double D[25], L[25], b[5], y[5], x[5];
   ld_D(C, J, top, level, 0, D);
-  ld_b(J, top, level, 0, b);
+  ld_b(C, J, top, level, 0, b);
   if (!chol5(D, L)) set_status(status, ST_NOT_SPD);
   lsolve5(L, b, y);
   ltsolve5(L, y, x);
@@ -574,7 +588,8 @@ __global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *s
 // Back-substitution: even rows copy from the next level, odd rows solve
 // lambda_n = L^{-T}(y - Ya lambda_{n-1} - Yb lambda_{n+1}).
 template <int CN, int CL, int CR>
-__device__ __forceinline__ void back_row(const CRLevel &cur, const CRLevel &next, int n) {
+__device__ __forceinline__ void back_row(const CRLevel &cur, const CRLevel &next, int n, double *out,
+                                         int out_N, int out_off) {
   const int N = cur.N, m = (n - 1) / 2, Nh = N / 2;
   const double *f = cur.fac;
   double lL[5], lR[5], v[CN], x[CN];
@@ -599,25 +614,32 @@ __device__ __forceinline__ void back_row(const CRLevel &cur, const CRLevel &next
     for (int k = i + 1; k < CN; ++k) s -= f[(size_t)pk(k, i) * Nh + m] * x[k];
     x[i] = s * f[(size_t)pk(i, i) * Nh + m];
   }
+  if (n < out_off) return;
 #pragma unroll
-  for (int r = 0; r < 5; ++r) cur.lam[(size_t)r * N + n] = r < CN ? x[r] : 0.0;
+  for (int r = 0; r < 5; ++r) out[(size_t)r * out_N + (n - out_off)] = r < CN ? x[r] : 0.0;
 }
 
-__global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next, DevJoints J, int level) {
+__global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next, DevChain C, DevJoints J,
+                                                 int level) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = cur.N;
   if (n >= N) return;
+  // level 0 writes joint n - off of the chain; other levels their own rows
+  double *out = level == 0 ? J.lambda : cur.lam;
+  const int out_N = level == 0 ? J.K : N, out_off = level == 0 ? C.off : 0;
   if ((n & 1) == 0) {
+    if (n < out_off) return;
 #pragma unroll
-    for (int r = 0; r < 5; ++r) cur.lam[(size_t)r * N + n] = next.lam[(size_t)r * next.N + n / 2];
+    for (int r = 0; r < 5; ++r)
+      out[(size_t)r * out_N + (n - out_off)] = next.lam[(size_t)r * next.N + n / 2];
     return;
   }
-  const int cn = row_size(J, level, n), cl = row_size(J, level, n - 1);
-  const int cr = n + 1 < N ? row_size(J, level, n + 1) : 0;
+  const int cn = row_size(C, J, level, n), cl = row_size(C, J, level, n - 1);
+  const int cr = n + 1 < N ? row_size(C, J, level, n + 1) : 0;
   const int code = (cn == 5 ? 9 : 0) + (cl == 5 ? 3 : 0) + (cr == 5 ? 2 : (cr == 3 ? 1 : 0));
   switch (code) {
 #define BCK(CODE, A, B, D_) \
-  case CODE: back_row<A, B, D_>(cur, next, n); break;
+  case CODE: back_row<A, B, D_>(cur, next, n, out, out_N, out_off); break;
     BCK(0, 3, 3, 0) BCK(1, 3, 3, 3) BCK(2, 3, 3, 5)
     BCK(3, 3, 5, 0) BCK(4, 3, 5, 3) BCK(5, 3, 5, 5)
     BCK(9, 5, 3, 0) BCK(10, 5, 3, 3) BCK(11, 5, 3, 5)
@@ -658,9 +680,9 @@ void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, in
   k_cr_top<<<1, 32, 0, s>>>(C, J, top, level, status);
 }
 
-void launch_cr_back(const DevJoints &J, const CRLevel &cur, const CRLevel &next, int level,
-                    cudaStream_t s) {
-  if (cur.N > 0) k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next, J, level);
+void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevel &cur, const CRLevel &next,
+                    int level, cudaStream_t s) {
+  if (cur.N > 0) k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next, C, J, level);
 }
 
 }  // namespace mabd

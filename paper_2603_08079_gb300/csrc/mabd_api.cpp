@@ -898,9 +898,36 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     C.B = dnew<double>(ctx, 25 * (size_t)K, ok);
     uint8_t *dcf = dnew<uint8_t>(ctx, K, ok);
     int8_t *dslot = dnew<int8_t>(ctx, islot.size(), ok);
+    // Level-0 offset: with off = 1 a decoupled identity row precedes the first
+    // joint, which shifts which rows level 0 eliminates.  The cheaper of the
+    // two orders (FMA model of the reduction kernel) is used: for chains that
+    // alternate balls and hinges it makes level 0 eliminate the hinges and
+    // leaves only 3x3 rows above it.
+    {
+      std::vector<int> sz(K);
+      for (int k = 0; k < K; ++k) sz[k] = jtype[k] == 1 ? 5 : 3;
+      auto cost = [&](int off) {
+        std::vector<int> cur(off, 3);
+        cur.insert(cur.end(), sz.begin(), sz.end());
+        double total = 0.0;
+        while (cur.size() > 1) {
+          const int N = (int)cur.size();
+          std::vector<int> nxt;
+          for (int n = 1; n < N; n += 2) {
+            const double c = cur[n], l = cur[n - 1], r = n + 1 < N ? cur[n + 1] : 0;
+            const double chol = c == 3 ? 7 : 30;
+            total += chol + (l + r + 1) * c * (c + 1) / 2 + (l * (l + 1) / 2 + r * (r + 1) / 2 + l * r + l + r) * c;
+          }
+          for (int n = 0; n < N; n += 2) nxt.push_back(cur[n]);
+          cur.swap(nxt);
+        }
+        return total;
+      };
+      C.off = (K > 1 && cost(1) < cost(0)) ? 1 : 0;
+    }
     // cyclic-reduction levels
     ctx->levels.clear();
-    int N = K;
+    int N = K + C.off;
     int lvl = 0;
     while (true) {
       CRLevel L{};
@@ -911,7 +938,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
         L.b = dnew<double>(ctx, 5 * (size_t)N, ok);
         L.lam = dnew<double>(ctx, 5 * (size_t)N, ok);
       } else {
-        L.lam = J.lambda;
+        L.lam = J.lambda;  // written through the offset by the back-substitution
       }
       if (N / 2 > 0) L.fac = dnew<double>(ctx, 70 * (size_t)(N / 2), ok);
       ctx->levels.push_back(L);
@@ -919,7 +946,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       N = (N + 1) / 2;
       ++lvl;
     }
-    const size_t half = std::max(K / 2, 1);
+    const size_t half = std::max((K + 1) / 2, 1);
     ctx->cL = dnew<double>(ctx, 20 * half, ok);
     ctx->cR = dnew<double>(ctx, 20 * half, ok);
     ctx->Bn = dnew<double>(ctx, 25 * half, ok);
@@ -1049,7 +1076,7 @@ static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s) {
       });
     run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
     for (int l = nl - 2; l >= 0; --l)
-      run(ctx, "cr_back", [&] { launch_cr_back(ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s); });
+      run(ctx, "cr_back", [&] { launch_cr_back(ctx->C, ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s); });
   } else if (ctx->solver == MABD_SOLVER_TREE) {
     const auto &lv = ctx->tree_lvl;
     const int nl = (int)lv.size() - 1;

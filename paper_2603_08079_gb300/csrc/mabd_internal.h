@@ -77,6 +77,7 @@ struct DevChain {
   double *B;             // [25][K] coupling of joint k and k+1 (through their shared body)
   const uint8_t *jflags; // [K] bit0: has lower-body part, bit1: has upper-body part, bit2: has B
   const int8_t *islot;   // [nnz] per incidence entry: 0 -> Dfirst, 1 -> Dsecond
+  int32_t off;           // level-0 row n is joint n - off; rows n < off are identity rows
 };
 
 // one level of block cyclic reduction
@@ -156,8 +157,9 @@ void launch_cr_level(const DevChain &C, const DevJoints &J, const CRLevel &cur, 
                      const CRLevel &next, int *status, cudaStream_t s);
 void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,
                    int *status, cudaStream_t s);
-void launch_cr_back(const DevJoints &J, const CRLevel &cur, const CRLevel &next, int level,
-                    cudaStream_t s);
+// back-substitution of `level`; level 0 writes its rows n >= C.off to J.lambda
+void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevel &cur, const CRLevel &next,
+                    int level, cudaStream_t s);
 
 // tree (k_tree.cu): one launch per level, deepest first, then root first
 // level [lo, hi) of the body order: T.order[lo, mid) lists its bodies with

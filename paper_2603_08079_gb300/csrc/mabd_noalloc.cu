@@ -85,6 +85,7 @@ bool carve(double *base, int M, int K, Layout &L) {
   L.iside_rw = (int8_t *)take(2 * m);
   L.islot_rw = (int8_t *)take(2 * m);
   L.C.K = K;
+  L.C.off = 0;
   L.C.Dfirst = (double *)take(15 * k * d);
   L.C.Dsecond = (double *)take(15 * k * d);
   L.C.B = (double *)take(25 * k * d);
@@ -400,7 +401,7 @@ extern "C" mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M
       launch_cr_combine(L.C, L.J, L.levels[l], l, L.levels[l + 1], L.cL, L.cR, L.Bn, s);
     }
     launch_cr_top(L.C, L.J, L.levels[L.nlevels - 1], L.nlevels - 1, L.status, s);
-    for (int l = L.nlevels - 2; l >= 0; --l) launch_cr_back(L.J, L.levels[l], L.levels[l + 1], l, s);
+    for (int l = L.nlevels - 2; l >= 0; --l) launch_cr_back(L.C, L.J, L.levels[l], L.levels[l + 1], l, s);
   }
   launch_backprop(L.B, L.J, L.I, p, L.status, s);
   int32_t *row_off = (int32_t *)L.cL;  // the reduction scratch is free again
