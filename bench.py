@@ -64,13 +64,30 @@ def make_scene(name: str, M: int | None = None) -> dict:
     raise KeyError(name)
 
 
-def workload_config(M: int, K: int, rows: int, name: str = "chain1m") -> dict:
+FORMS = {
+    "fp64": "FP64 throughout",
+    "mixed": "FP32 per-body/per-joint products and Gram blocks; FP64 polar, rhs, constraint "
+             "values, dual cyclic reduction and %d FP64 residual-correction sweep(s)",
+}
+
+
+def workload_config(M: int, K: int, rows: int, name: str = "chain1m", form: str = "fp64",
+                    refine: int = 1) -> dict:
     desc, solver = WORKLOADS[name]
+    fdesc = FORMS[form] % refine if form == "mixed" else FORMS[form]
     return {
         "workload": desc % (M, K, rows),
-        "bodies": M, "joints": K, "dual_rows": rows, "form": "fp64", "solver": solver,
+        "bodies": M, "joints": K, "dual_rows": rows, "form": form, "form_detail": fdesc,
+        "solver": solver,
         "l2": "inputs larger than L2 (working set > 129 MB), no flush",
     }
+
+
+def chosen_form(args) -> str:
+    """The mixed form exists for chains; other topologies run FP64."""
+    if args.precision != "auto":
+        return args.precision
+    return "mixed" if args.workload == "chain1m" else "fp64"
 
 
 def dist_env():
@@ -105,14 +122,25 @@ class ClockSampler:
         self.path = os.path.join("/tmp", "mabd_clocks_%d_%d.csv" % (os.getpid(), device_index))
 
     def start(self):
+        """Starts nvidia-smi and returns once its first sample is written, so
+        that the samples cover the region timed next."""
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -212,6 +240,12 @@ def chain_gram_flops(jtype_chain: np.ndarray) -> float:
     return 2.0 * float(fma.sum())
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
+# kernel, from one ncu capture of the current kernel on the named workload;
+# an entry is removed when its kernel changes
+TRAFFIC: dict = {}
+
+
 def kernel_model(name: str, jtype_chain: np.ndarray):
     """Algorithmic FP64 flops of one step's launches of `name` (all levels)."""
     if name.startswith("cr_reduce") or name == "cr_level":
@@ -219,6 +253,28 @@ def kernel_model(name: str, jtype_chain: np.ndarray):
     if name == "chain_gram":
         return chain_gram_flops(jtype_chain)
     return None
+
+
+def time_steps(solver, steps: int, warmup: int, barrier_sync, clocks=None):
+    """W untimed steps, then exactly K steps between CUDA events on the
+    library's stream, with a barrier and a device synchronize on both sides."""
+    import torch
+    stream = solver.stream
+    solver.step(warmup)
+    solver.synchronize()
+    barrier_sync()
+    if clocks is not None:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(steps)
+    e1.record(stream)
+    barrier_sync()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks is not None else None
+    solver.synchronize()  # surfaces any device-side failure of the timed steps
+    return ms, clk
 
 
 def run_gpu(args):
@@ -232,34 +288,24 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     sc = make_scene(args.workload, args.bodies if args.workload == "chain1m" else None)
     M = len(sc["mass"])
-    solver = mabd.Solver(sc)
+    form = chosen_form(args)
+    solver = mabd.Solver(sc, precision=form, refine_steps=args.refine)
     info = solver.info()
-    stream = solver.stream
 
     def barrier_sync():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up
-    solver.step(args.warmup)
-    solver.synchronize()
-    barrier_sync()
+    def max_over_ranks(ms):
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    solver.step(args.steps)
-    e1.record(stream)
-    barrier_sync()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    solver.synchronize()  # surfaces any device-side failure of the timed steps
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms, clk = time_steps(solver, args.steps, args.warmup, barrier_sync, clocks)
+    ms_max = max_over_ranks(ms)
     value = ws * M * args.steps / (ms_max / 1e3)
 
     # per-kernel times with CUDA events on the library's stream (separate pass)
@@ -268,7 +314,6 @@ def run_gpu(args):
     solver.step(args.profile_steps)
     kt = solver.kernel_times()
     solver.profile(False)
-    launches_per_step = sum(n for _, n in kt.values()) / args.profile_steps
 
     # end to end through the C ABI with host buffers: H2D state, step, D2H state
     q_h = torch.empty((M, 12), dtype=torch.float64).pin_memory().numpy()
@@ -285,37 +330,50 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = ws * M * e2e_steps / e2e_s
 
-    # accuracy of this form against the oracle is checked by the test-suite
-    # (tests/test_gpu_chain.py::test_full_size_pulley_chain); here the joint
-    # residual of one step is reported
+    # accuracy of each form against the oracle is checked by the test-suite
+    # (tests/test_gpu_chain.py, tests/test_gpu_mixed.py: full-size chain);
+    # here the residuals of one step are reported
     st = solver.step(1, stats=True)[0]
     solver.close()
+
+    # the plain FP64 GPU path on the same workload, timed the same way
+    plain = None
+    if form != "fp64":
+        ref = mabd.Solver(sc, precision="fp64")
+        pms, _ = time_steps(ref, args.steps, args.warmup, barrier_sync)
+        ref.close()
+        pms = max_over_ranks(pms)
+        plain = {"value": ws * M * args.steps / (pms / 1e3), "unit": "body-steps/s",
+                 "ms_per_step": pms / args.steps}
 
     result = None
     if rank == 0:
         dom = max(kt.items(), key=lambda kv: kv[1][0])
         dname, (dms, dn) = dom
         per_launch_ms = dms / dn
-        launches_per_step = dn / args.profile_steps
+        launches_per_step = sum(n for _, n in kt.values()) / args.profile_steps
+        dom_launches = dn / args.profile_steps
         step_flops = kernel_model(dname, sc["jtype"]) if args.workload == "chain1m" else None
         if step_flops is not None:
-            flops = step_flops / launches_per_step     # per launch, averaged over the levels
+            flops = step_flops / dom_launches     # per launch, averaged over the levels
             achieved = flops / (per_launch_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                    "traffic": None, "kernel": dname,
+                    "traffic": TRAFFIC.get((args.workload, dname)), "kernel": dname,
                     "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz (probe measured 1.20)",
                     "kernel_ms_per_launch": round(per_launch_ms, 5),
-                    "flops_per_step": step_flops, "launches_per_step": launches_per_step}
+                    "flops_per_step": step_flops, "launches_per_step": dom_launches}
         else:
             roof = {"bound": "alu", "achieved": None, "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": dname}
         result = {
             "metric": METRIC, "value": value, "unit": "body-steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded generator, paper-shaped chain)",
-            "config": workload_config(M, info["joints"], info["dual_rows"], args.workload),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if form == "fp64" else "f32+f64",
+            "data": "synthetic (seeded generator, paper-shaped %s)" % args.workload,
+            "config": workload_config(M, info["joints"], info["dual_rows"], args.workload, form,
+                                      args.refine),
             "e2e": {"value": e2e_value, "unit": "body-steps/s",
                     "h2d_bytes_per_step": 2 * 12 * 8 * M, "d2h_bytes_per_step": 2 * 12 * 8 * M},
             "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -324,6 +382,9 @@ def run_gpu(args):
             "joint_residual": st["joint_residual"],
             "clocks": clk,
         }
+        if form != "fp64":
+            result["refine_residual"] = st["refine_residual"]
+            result["plain_fp64_gpu"] = plain
         if st.get("pcg_iters"):
             result["pcg_iters_per_step"] = st["pcg_iters"]
         if not args.no_cpu_baseline:
@@ -379,7 +440,7 @@ def run_reference(args):
         q, qd, _, _ = ora.step(S, q, qd)
     dt = time.perf_counter() - t0
     value = M * args.steps / dt
-    cfg = workload_config(M_FULL, M_FULL + 1, 4194305)
+    cfg = workload_config(M_FULL, M_FULL + 1, 4194305, "chain1m", chosen_form(args), args.refine)
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "body-steps/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -404,6 +465,9 @@ def main():
     ap.add_argument("--cpu-bodies", type=int, default=M_FULL // 4)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"],
+                    help="form of the step (auto: mixed for the chain, FP64 otherwise)")
+    ap.add_argument("--refine", type=int, default=1, help="FP64 correction sweeps of the mixed form")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "own":
         args.warmup = 3

@@ -79,7 +79,18 @@ typedef enum {
   MABD_ERR_UNSUPPORTED = 10
 } mabd_status;
 
-enum { MABD_FP64 = 0 };
+/* Arithmetic of the step.
+   MABD_FP64   every product in FP64.
+   MABD_MIXED  chain topologies: the unconstrained solve, the Jacobian
+               products, the dual Gram blocks and the back-propagation in
+               FP32; the polar rotation, the rhs, the constraint values, the
+               prefactorization and the block cyclic reduction of the dual in
+               FP64; then refine_steps FP64 residual-correction sweeps
+               (iterative refinement of the KKT system through the stored
+               FP64 factors).  Other topologies: MABD_ERR_UNSUPPORTED at
+               mabd_prefactor. */
+enum { MABD_FP64 = 0, MABD_MIXED = 1 };
+#define MABD_MAX_REFINE 8
 enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_SOLVER_PCG = 3 };
 enum { MABD_JOINT_BALL = 0, MABD_JOINT_HINGE = 1 };
 enum { MABD_TOPO_NONE = 0, MABD_TOPO_CHAIN = 1, MABD_TOPO_TREE = 2, MABD_TOPO_GRAPH = 3 };
@@ -87,11 +98,11 @@ enum { MABD_TOPO_NONE = 0, MABD_TOPO_CHAIN = 1, MABD_TOPO_TREE = 2, MABD_TOPO_GR
 typedef struct {
   double h;             /* time step [s] > 0 */
   double gravity[3];    /* [m/s^2], applied at each centre of mass (Eq. module1-wrench-map) */
-  int32_t precision;    /* MABD_FP64 */
+  int32_t precision;    /* MABD_FP64 or MABD_MIXED */
   int32_t solver;       /* MABD_SOLVER_*; AUTO picks chain, then tree, then PCG */
   int32_t pcg_max_iters;/* cap on PCG iterations (>= 1) */
   double pcg_rtol;      /* PCG stops when |r| <= pcg_rtol |b| */
-  int32_t refine_steps; /* reserved, 0 */
+  int32_t refine_steps; /* MABD_MIXED: FP64 correction sweeps per step, 0..MABD_MAX_REFINE */
   int32_t residual_rhs; /* 1: bottom KKT rhs is -C(q_n) (Sec. 5 footnote); 0: zero as printed */
   void *stream;         /* cudaStream_t for all work (NULL: default stream) */
   void *(*dev_alloc)(size_t bytes, void *user); /* optional device allocator */
@@ -123,7 +134,8 @@ typedef struct {
   double joint_residual;   /* max over rows of |C(q_{n+1})| (Table 1 |r|) */
   int32_t pcg_iters;       /* PCG iterations of this step (0 for direct solvers) */
   double pcg_rel_residual; /* final |r|/|b| of PCG (0 for direct solvers) */
-  double refine_residual;  /* reserved, 0 */
+  double refine_residual;  /* MABD_MIXED: max over rows of |C(q_n) + G dq| (FP64) entering the
+                              last correction sweep (0 for FP64 or without sweeps) */
 } mabd_step_stats;
 
 typedef struct {
@@ -131,10 +143,12 @@ typedef struct {
   int32_t topology;        /* MABD_TOPO_* chosen at prefactor */
   int32_t solver;          /* MABD_SOLVER_* in use */
   int64_t device_bytes;    /* device memory held by the context */
+  int32_t precision;       /* MABD_FP64 or MABD_MIXED */
+  int32_t refine_steps;    /* correction sweeps per step (MABD_MIXED) */
 } mabd_info;
 
 /* Fills *cfg with h = 1e-2, gravity (0,0,-9.8), FP64, AUTO, pcg_max_iters 2000,
-   pcg_rtol 1e-13, residual_rhs 1, default stream, library allocator. */
+   pcg_rtol 1e-13, refine_steps 1, residual_rhs 1, default stream, library allocator. */
 void mabd_config_default(mabd_config *cfg);
 
 /* Creates a context.  cfg is copied.  INVALID_ARG on h <= 0 or bad fields;

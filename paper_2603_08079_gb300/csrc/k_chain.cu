@@ -27,15 +27,15 @@ __device__ __forceinline__ int pk(int r, int c) { return r >= c ? r * (r + 1) / 
 // Mbar(p, q) from the structured inverse h[16]: translation h[0]; the 3x3
 // block X of A's diagonal entries (h[1..6]); transpose pairs
 // (A(1,0), A(0,1)) h[7..9], (A(2,0), A(0,2)) h[10..12], (A(2,1), A(1,2)) h[13..15].
-__device__ __forceinline__ void mbar(const double h[16], const double p[3], const double q[3],
-                                     double Mb[3][3]) {
-  const double p0q0 = p[0] * q[0], p1q1 = p[1] * q[1], p2q2 = p[2] * q[2];
+template <typename T>
+__device__ __forceinline__ void mbar(const T h[16], const T p[3], const T q[3], T Mb[3][3]) {
+  const T p0q0 = p[0] * q[0], p1q1 = p[1] * q[1], p2q2 = p[2] * q[2];
   Mb[0][0] = h[0] + h[1] * p0q0 + h[9] * p1q1 + h[12] * p2q2;
   Mb[1][1] = h[0] + h[4] * p1q1 + h[7] * p0q0 + h[15] * p2q2;
   Mb[2][2] = h[0] + h[6] * p2q2 + h[10] * p0q0 + h[13] * p1q1;
-  const double p0q1 = p[0] * q[1], p1q0 = p[1] * q[0];
-  const double p0q2 = p[0] * q[2], p2q0 = p[2] * q[0];
-  const double p1q2 = p[1] * q[2], p2q1 = p[2] * q[1];
+  const T p0q1 = p[0] * q[1], p1q0 = p[1] * q[0];
+  const T p0q2 = p[0] * q[2], p2q0 = p[2] * q[0];
+  const T p1q2 = p[1] * q[2], p2q1 = p[2] * q[1];
   Mb[0][1] = h[2] * p0q1 + h[8] * p1q0;
   Mb[1][0] = h[2] * p1q0 + h[8] * p0q1;
   Mb[0][2] = h[3] * p0q2 + h[11] * p2q0;
@@ -45,36 +45,40 @@ __device__ __forceinline__ void mbar(const double h[16], const double p[3], cons
 }
 
 // out[r][c] (r < NA, c < NB) = Ea[:, ca[r]]^T Mb Eb[:, cb[c]]
-template <int NA, int NB>
-__device__ __forceinline__ void project(const double Ea[3][3], const int ca[3], const double Mb[3][3],
-                                        const double Eb[3][3], const int cb[3], double out[3][3]) {
-  double T[3][NB];
+template <int NA, int NB, typename T>
+__device__ __forceinline__ void project(const T Ea[3][3], const int ca[3], const T Mb[3][3],
+                                        const T Eb[3][3], const int cb[3], T out[3][3]) {
+  T tmp[3][NB];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int c = 0; c < NB; ++c)
-      T[a][c] = Mb[a][0] * Eb[0][cb[c]] + Mb[a][1] * Eb[1][cb[c]] + Mb[a][2] * Eb[2][cb[c]];
+      tmp[a][c] = Mb[a][0] * Eb[0][cb[c]] + Mb[a][1] * Eb[1][cb[c]] + Mb[a][2] * Eb[2][cb[c]];
 #pragma unroll
   for (int r = 0; r < NA; ++r)
 #pragma unroll
     for (int c = 0; c < NB; ++c)
-      out[r][c] = Ea[0][ca[r]] * T[0][c] + Ea[1][ca[r]] * T[1][c] + Ea[2][ca[r]] * T[2][c];
+      out[r][c] = Ea[0][ca[r]] * tmp[0][c] + Ea[1][ca[r]] * tmp[1][c] + Ea[2][ca[r]] * tmp[2][c];
 }
 
-__global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, DevIncidence I,
-                                                    DevChain C) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= B.M) return;
+// Gram blocks of body j with products in T (double: the FP64 form; float:
+// the mixed form, inputs rounded to FP32); the blocks are stored in FP64.
+template <typename T, typename HT>
+__device__ __forceinline__ void chain_gram_body(const DevBodies &B, const DevJoints &J,
+                                                const DevIncidence &I, const DevChain &C,
+                                                const HT *hinv, int j) {
   if (B.fixed[j]) return;
   const int e0 = I.off[j];
   const int n = I.off[j + 1] - e0;
   if (n <= 0 || n > 2) return;  // a chain body has one or two joints
   const int M = B.M, K = J.K;
-  double R[9], h[16];
-  load_R(B.R, M, j, R);
-  load_hinv(B, j, h);
+  T R[9], h[16];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = (T)B.R[(size_t)i * M + j];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) h[i] = (T)__ldg(hinv + (size_t)i * M + j);
   // per slot: directions E (rest frame, columns = rows' directions), points
-  double E[2][3][3], P[2][2][3];
+  T E[2][3][3], P[2][2][3];
   int kk[2], ty[2];
   for (int s = 0; s < n; ++s) {
     const int k = I.joint[e0 + s];
@@ -82,20 +86,23 @@ __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, De
     const int type = J.type[k];
     kk[s] = k;
     ty[s] = type;
-    const double sgn = side == 0 ? 1.0 : -1.0;
-    load3(side == 0 ? J.pa1 : J.pb1, K, k, P[s][0]);
+    const T sgn = side == 0 ? T(1) : T(-1);
+    const double *p1 = side == 0 ? J.pa1 : J.pb1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P[s][0][a] = (T)__ldg(p1 + (size_t)a * K + k);
     if (type == 1) {
-      load3(side == 0 ? J.pa2 : J.pb2, K, k, P[s][1]);
-      double RH[9];
-      load_R(J.RH, K, k, RH);
+      const double *p2 = side == 0 ? J.pa2 : J.pb2;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) P[s][1][a] = (T)__ldg(p2 + (size_t)a * K + k);
+      T RH[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) RH[i] = (T)J.RH[(size_t)i * K + k];
       // E = s R^T R_H^T: column r is s R^T (row r of R_H)
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        double e[3];
-        mtv3(R, RH + 3 * r, e);
+      for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) E[s][a][r] = sgn * e[a];
-      }
+        for (int a = 0; a < 3; ++a)
+          E[s][a][r] = sgn * (R[a] * RH[3 * r] + R[3 + a] * RH[3 * r + 1] + R[6 + a] * RH[3 * r + 2]);
     } else {
       // E = s R^T
 #pragma unroll
@@ -105,7 +112,7 @@ __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, De
     }
   }
   const int c012[3] = {0, 1, 2}, c02[3] = {0, 2, 0};
-  double Mb[3][3], blk[3][3];
+  T Mb[3][3], blk[3][3];
   // self blocks of each joint -> its slot (lower body: Dfirst, upper: Dsecond)
   for (int s = 0; s < n; ++s) {
     double *dst = C.islot[e0 + s] == 0 ? C.Dfirst : C.Dsecond;
@@ -118,19 +125,19 @@ __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, De
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int c = 0; c <= r; ++c) Dp[pk(r, c)] = blk[r][c];
+      for (int c = 0; c <= r; ++c) Dp[pk(r, c)] = (double)blk[r][c];
     if (ty[s] == 1) {
       mbar(h, P[s][1], P[s][0], Mb);                      // rows 3-4 x rows 0-2
       project<2, 3>(E[s], c02, Mb, E[s], c012, blk);
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Dp[pk(3 + r, c)] = blk[r][c];
+        for (int c = 0; c < 3; ++c) Dp[pk(3 + r, c)] = (double)blk[r][c];
       mbar(h, P[s][1], P[s][1], Mb);                      // rows 3-4 x rows 3-4
       project<2, 2>(E[s], c02, Mb, E[s], c02, blk);
-      Dp[pk(3, 3)] = blk[0][0];
-      Dp[pk(4, 3)] = blk[1][0];
-      Dp[pk(4, 4)] = blk[1][1];
+      Dp[pk(3, 3)] = (double)blk[0][0];
+      Dp[pk(4, 3)] = (double)blk[1][0];
+      Dp[pk(4, 4)] = (double)blk[1][1];
     }
 #pragma unroll
     for (int i = 0; i < 15; ++i) dst[(size_t)i * K + k] = Dp[i];
@@ -145,14 +152,14 @@ __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, De
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Bp[5 * r + c] = blk[r][c];
+      for (int c = 0; c < 3; ++c) Bp[5 * r + c] = (double)blk[r][c];
     if (ty[1] == 1) {
       mbar(h, P[0][0], P[1][1], Mb);
       project<3, 2>(E[0], c012, Mb, E[1], c02, blk);
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) Bp[5 * r + 3 + c] = blk[r][c];
+        for (int c = 0; c < 2; ++c) Bp[5 * r + 3 + c] = (double)blk[r][c];
     }
     if (ty[0] == 1) {
       mbar(h, P[0][1], P[1][0], Mb);
@@ -160,20 +167,33 @@ __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, De
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Bp[5 * (3 + r) + c] = blk[r][c];
+        for (int c = 0; c < 3; ++c) Bp[5 * (3 + r) + c] = (double)blk[r][c];
       if (ty[1] == 1) {
         mbar(h, P[0][1], P[1][1], Mb);
         project<2, 2>(E[0], c02, Mb, E[1], c02, blk);
 #pragma unroll
         for (int r = 0; r < 2; ++r)
 #pragma unroll
-          for (int c = 0; c < 2; ++c) Bp[5 * (3 + r) + 3 + c] = blk[r][c];
+          for (int c = 0; c < 2; ++c) Bp[5 * (3 + r) + 3 + c] = (double)blk[r][c];
       }
     }
     const int k0 = kk[0];
 #pragma unroll
     for (int i = 0; i < 25; ++i) C.B[(size_t)i * K + k0] = Bp[i];
   }
+}
+
+__global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, DevIncidence I,
+                                                    DevChain C) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < B.M) chain_gram_body<double>(B, J, I, C, B.hinv, j);
+}
+
+// mixed-precision form: the same blocks with FP32 products
+__global__ void __launch_bounds__(128) k_mx_chain_gram(DevBodies B, DevJoints J, DevIncidence I,
+                                                       DevChain C) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < B.M) chain_gram_body<float>(B, J, I, C, B.hinvf, j);
 }
 
 // ---------------------------------------------------------------------------
@@ -573,7 +593,7 @@ __global__ void __launch_bounds__(CRF) k_cr_level(DevChain C, DevJoints J, CRLev
 }
 
 // Single remaining row: lambda = D^{-1} b.
-__global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *status) {
+__global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *status, double *acc) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   double D[25], L[25], b[5], y[5], x[5];
   ld_D(C, J, top, level, 0, D);
@@ -582,14 +602,17 @@ __global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *s
   lsolve5(L, b, y);
   ltsolve5(L, y, x);
 #pragma unroll
-  for (int r = 0; r < 5; ++r) top.lam[(size_t)r * top.N] = x[r];
+  for (int r = 0; r < 5; ++r) {
+    top.lam[(size_t)r * top.N] = x[r];
+    if (acc) acc[(size_t)r * top.N] += x[r];
+  }
 }
 
 // Back-substitution: even rows copy from the next level, odd rows solve
 // lambda_n = L^{-T}(y - Ya lambda_{n-1} - Yb lambda_{n+1}).
 template <int CN, int CL, int CR>
 __device__ __forceinline__ void back_row(const CRLevel &cur, const CRLevel &next, int n, double *out,
-                                         int out_N, int out_off) {
+                                         int out_N, int out_off, double *acc) {
   const int N = cur.N, m = (n - 1) / 2, Nh = N / 2;
   const double *f = cur.fac;
   double lL[5], lR[5], v[CN], x[CN];
@@ -616,22 +639,32 @@ __device__ __forceinline__ void back_row(const CRLevel &cur, const CRLevel &next
   }
   if (n < out_off) return;
 #pragma unroll
-  for (int r = 0; r < 5; ++r) out[(size_t)r * out_N + (n - out_off)] = r < CN ? x[r] : 0.0;
+  for (int r = 0; r < 5; ++r) {
+    const size_t o = (size_t)r * out_N + (n - out_off);
+    const double v = r < CN ? x[r] : 0.0;
+    out[o] = v;
+    if (acc) acc[o] += v;
+  }
 }
 
 __global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next, DevChain C, DevJoints J,
-                                                 int level) {
+                                                 int level, double *acc) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = cur.N;
   if (n >= N) return;
   // level 0 writes joint n - off of the chain; other levels their own rows
   double *out = level == 0 ? J.lambda : cur.lam;
   const int out_N = level == 0 ? J.K : N, out_off = level == 0 ? C.off : 0;
+  if (level != 0) acc = nullptr;
   if ((n & 1) == 0) {
     if (n < out_off) return;
 #pragma unroll
-    for (int r = 0; r < 5; ++r)
-      out[(size_t)r * out_N + (n - out_off)] = next.lam[(size_t)r * next.N + n / 2];
+    for (int r = 0; r < 5; ++r) {
+      const size_t o = (size_t)r * out_N + (n - out_off);
+      const double v = next.lam[(size_t)r * next.N + n / 2];
+      out[o] = v;
+      if (acc) acc[o] += v;
+    }
     return;
   }
   const int cn = row_size(C, J, level, n), cl = row_size(C, J, level, n - 1);
@@ -639,7 +672,7 @@ __global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next, DevC
   const int code = (cn == 5 ? 9 : 0) + (cl == 5 ? 3 : 0) + (cr == 5 ? 2 : (cr == 3 ? 1 : 0));
   switch (code) {
 #define BCK(CODE, A, B, D_) \
-  case CODE: back_row<A, B, D_>(cur, next, n, out, out_N, out_off); break;
+  case CODE: back_row<A, B, D_>(cur, next, n, out, out_N, out_off, acc); break;
     BCK(0, 3, 3, 0) BCK(1, 3, 3, 3) BCK(2, 3, 3, 5)
     BCK(3, 3, 5, 0) BCK(4, 3, 5, 3) BCK(5, 3, 5, 5)
     BCK(9, 5, 3, 0) BCK(10, 5, 3, 3) BCK(11, 5, 3, 5)
@@ -647,6 +680,71 @@ __global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next, DevC
 #undef BCK
     default: break;
   }
+}
+
+// ---------------------------------------------------------------------------
+// a new right-hand side through the stored factors
+// ---------------------------------------------------------------------------
+// y = L^{-1} b for odd row m (factor record: packed L with reciprocal diagonal)
+template <int CO>
+__device__ __forceinline__ void rhs_y(const double *f, int Nh, int m, const double b[5], double y[5]) {
+#pragma unroll
+  for (int i = 0; i < CO; ++i) {
+    double t = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t -= f[(size_t)pk(i, k) * Nh + m] * y[k];
+    y[i] = t * f[(size_t)pk(i, i) * Nh + m];
+  }
+}
+
+// be -= Y^T y with Y (CO x CE) the record's block at `slot` (15: Ya, 40: Yb)
+template <int CO, int CE>
+__device__ __forceinline__ void rhs_sub(const double *f, int Nh, int m, int slot, const double y[5],
+                                        double be[5]) {
+#pragma unroll
+  for (int c = 0; c < CE; ++c) {
+    double t = 0.0;
+#pragma unroll
+    for (int r = 0; r < CO; ++r) t += f[(size_t)(slot + 5 * r + c) * Nh + m] * y[r];
+    be[c] -= t;
+  }
+}
+
+template <int CO>
+__device__ __forceinline__ void rhs_odd(const double *f, int Nh, int m, int slot, const double bo[5],
+                                        int ce, double be[5], double y[5]) {
+  rhs_y<CO>(f, Nh, m, bo, y);
+  if (ce == 5) rhs_sub<CO, 5>(f, Nh, m, slot, y, be);
+  else rhs_sub<CO, 3>(f, Nh, m, slot, y, be);
+}
+
+// One thread per next-level row mm (even row e = 2 mm): the odd rows beside
+// it give y = L^{-1} b (the right one stores its y in its factor record for
+// the back-substitution) and next.b[mm] = b_e - Yb_{e-1}^T y_{e-1} - Ya_{e+1}^T y_{e+1}.
+__global__ void __launch_bounds__(128) k_cr_rhs(DevChain C, DevJoints J, CRLevel cur, int level,
+                                                CRLevel next) {
+  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mm >= next.N) return;
+  const int N = cur.N, Nh = N / 2, e = 2 * mm;
+  const int ce = row_size(C, J, level, e);
+  double be[5], bo[5], y[5];
+  ld_b(C, J, cur, level, e, be);
+  if (e >= 1) {  // odd row e-1 (index mm-1): its Yb couples it to e
+    const int co = row_size(C, J, level, e - 1);
+    ld_b(C, J, cur, level, e - 1, bo);
+    if (co == 5) rhs_odd<5>(cur.fac, Nh, mm - 1, 40, bo, ce, be, y);
+    else rhs_odd<3>(cur.fac, Nh, mm - 1, 40, bo, ce, be, y);
+  }
+  if (e + 1 < N) {  // odd row e+1 (index mm): its Ya couples it to e
+    const int co = row_size(C, J, level, e + 1);
+    ld_b(C, J, cur, level, e + 1, bo);
+    if (co == 5) rhs_odd<5>(cur.fac, Nh, mm, 15, bo, ce, be, y);
+    else rhs_odd<3>(cur.fac, Nh, mm, 15, bo, ce, be, y);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) cur.fac[(size_t)(65 + r) * Nh + mm] = r < co ? y[r] : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) next.b[(size_t)r * next.N + mm] = r < ce ? be[r] : 0.0;
 }
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
@@ -676,13 +774,23 @@ void launch_cr_level(const DevChain &C, const DevJoints &J, const CRLevel &cur, 
 }
 
 void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,
-                   int *status, cudaStream_t s) {
-  k_cr_top<<<1, 32, 0, s>>>(C, J, top, level, status);
+                   int *status, cudaStream_t s, double *acc) {
+  k_cr_top<<<1, 32, 0, s>>>(C, J, top, level, status, acc);
 }
 
 void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevel &cur, const CRLevel &next,
-                    int level, cudaStream_t s) {
-  if (cur.N > 0) k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next, C, J, level);
+                    int level, cudaStream_t s, double *acc) {
+  if (cur.N > 0) k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next, C, J, level, acc);
+}
+
+void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
+                   const CRLevel &next, cudaStream_t s) {
+  if (next.N > 0) k_cr_rhs<<<nblk(next.N, 128), 128, 0, s>>>(C, J, cur, level, next);
+}
+
+void launch_mx_chain_gram(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                          const DevChain &C, cudaStream_t s) {
+  if (B.M > 0) k_mx_chain_gram<<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, C);
 }
 
 }  // namespace mabd

@@ -1,0 +1,485 @@
+// Mixed-precision form of the chain step.  The step solves the same
+// linearized KKT system as the FP64 form (Eq. newton_abd with the frozen-frame
+// Jacobian of Eq. pcpq):
+//     H dq + G^T lambda = f,     G dq = -C(q_n)
+// by iterative refinement:
+//   approximate solve  u = H^{-1} f, Gram blocks, then back-propagation
+//                      dq = u - H^{-1} G^T lambda (Sec. 5.2), with every
+//                      per-body and per-joint product in FP32, and the
+//                      block cyclic reduction of the dual in FP64;
+//   correction sweep   FP64 residuals r_p = f - H dq - G^T lambda and
+//                      r_d = -C - G dq, then the same approximate solve for
+//                      (r_p, r_d) through the stored FP64 factors.
+// The polar rotation R, the rhs f, the constraint values C(q_n) and the hinge
+// frames are computed in FP64, so the system being refined is the FP64 one.
+// All body-space work is done in the body's rest frame: with
+// dqb = diag4(R^T) dq, H dq = diag4(R) Hbar dqb (Eq. abd_final).
+#include "mabd_device.cuh"
+
+namespace mabd {
+
+// y = Hbar^{-1} v with the structured inverse (see mabd_internal.h)
+template <typename T>
+__device__ __forceinline__ void hinv_apply_t(const T h[16], const T v[12], T y[12]) {
+  y[0] = h[1] * v[0] + h[2] * v[4] + h[3] * v[8];
+  y[4] = h[2] * v[0] + h[4] * v[4] + h[5] * v[8];
+  y[8] = h[3] * v[0] + h[5] * v[4] + h[6] * v[8];
+  y[1] = h[7] * v[1] + h[8] * v[3];
+  y[3] = h[8] * v[1] + h[9] * v[3];
+  y[2] = h[10] * v[2] + h[11] * v[6];
+  y[6] = h[11] * v[2] + h[12] * v[6];
+  y[5] = h[13] * v[5] + h[14] * v[7];
+  y[7] = h[14] * v[5] + h[15] * v[7];
+  y[9] = h[0] * v[9];
+  y[10] = h[0] * v[10];
+  y[11] = h[0] * v[11];
+}
+
+__device__ __forceinline__ void load_hinvf(const DevBodies &B, int j, float h[16]) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) h[i] = __ldg(B.hinvf + (size_t)i * B.M + j);
+}
+
+// y = Hbar x in FP64 for Hbar = M_A/h^2 + Kbar_A of a body with diagonal second
+// moment s (Sec. 3.3): translation m/h^2; diagonal entries of A
+// (s_i/h^2 + 2 V mu) x_i + V lambda (x_0 + x_4 + x_8); each transpose pair
+// (A(a,i), A(i,a)) couples through V mu with masses s_i/h^2 and s_a/h^2.
+__device__ __forceinline__ void hbar_apply(const double s[3], double m, double vmu, double vlam,
+                                           double ih2, const double x[12], double y[12]) {
+  const double tr = vlam * (x[0] + x[4] + x[8]);
+  y[0] = (s[0] * ih2 + 2.0 * vmu) * x[0] + tr;
+  y[4] = (s[1] * ih2 + 2.0 * vmu) * x[4] + tr;
+  y[8] = (s[2] * ih2 + 2.0 * vmu) * x[8] + tr;
+  // (q1 = A(1,0), q3 = A(0,1)), (q2 = A(2,0), q6 = A(0,2)), (q5 = A(2,1), q7 = A(1,2))
+  y[1] = (s[0] * ih2 + vmu) * x[1] + vmu * x[3];
+  y[3] = vmu * x[1] + (s[1] * ih2 + vmu) * x[3];
+  y[2] = (s[0] * ih2 + vmu) * x[2] + vmu * x[6];
+  y[6] = vmu * x[2] + (s[2] * ih2 + vmu) * x[6];
+  y[5] = (s[1] * ih2 + vmu) * x[5] + vmu * x[7];
+  y[7] = vmu * x[5] + (s[2] * ih2 + vmu) * x[7];
+  const double mt = m * ih2;
+  y[9] = mt * x[9];
+  y[10] = mt * x[10];
+  y[11] = mt * x[11];
+}
+
+// g = diag4(R^T) sum_k G_kj^T lam_k for body j: a row with point p and world
+// direction d contributes s [p; 1] (x) (R^T d) lam_r (s = +1 on body a, -1 on b)
+template <typename T>
+__device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence &I, int j,
+                                          const T R[9], const double *lam, T g[12]) {
+  const int K = J.K;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) g[i] = T(0);
+  const int e0 = I.off[j], e1 = I.off[j + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int k = I.joint[e];
+    const int side = I.side[e];
+    const int type = J.type[k];
+    const T sgn = side == 0 ? T(1) : T(-1);
+    T l[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) l[r] = (T)lam[(size_t)r * K + k];
+    const double *p1 = side == 0 ? J.pa1 : J.pb1;
+    const double *p2 = side == 0 ? J.pa2 : J.pb2;
+    T F1[3], F2[3], P1[3], P2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P1[a] = (T)__ldg(p1 + (size_t)a * K + k);
+    if (type == 0) {
+      F1[0] = l[0];
+      F1[1] = l[1];
+      F1[2] = l[2];
+    } else {
+      T RH[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) RH[i] = (T)J.RH[(size_t)i * K + k];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        F1[a] = RH[a] * l[0] + RH[3 + a] * l[1] + RH[6 + a] * l[2];
+        F2[a] = l[3] * RH[a] + l[4] * RH[6 + a];
+        P2[a] = (T)__ldg(p2 + (size_t)a * K + k);
+      }
+    }
+    T f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = sgn * (R[a] * F1[0] + R[3 + a] * F1[1] + R[6 + a] * F1[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      g[a] += P1[0] * f[a];
+      g[3 + a] += P1[1] * f[a];
+      g[6 + a] += P1[2] * f[a];
+      g[9 + a] += f[a];
+    }
+    if (type == 1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) f[a] = sgn * (R[a] * F2[0] + R[3 + a] * F2[1] + R[6 + a] * F2[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        g[a] += P2[0] * f[a];
+        g[3 + a] += P2[1] * f[a];
+        g[6 + a] += P2[2] * f[a];
+        g[9 + a] += f[a];
+      }
+    }
+  }
+}
+
+// world displacement of rest point p under the rest-frame increment x:
+// J(p) diag4(R) x = R (J(p) x)
+template <typename T>
+__device__ __forceinline__ void disp_at(const T R[9], const T x[12], const T p[3], T out[3]) {
+  T l[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) l[a] = x[a] * p[0] + x[3 + a] * p[1] + x[6 + a] * p[2] + x[9 + a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[a] = R[3 * a] * l[0] + R[3 * a + 1] * l[1] + R[3 * a + 2] * l[2];
+}
+
+// One thread per body: R = polar(A) and the rest-frame rhs
+// fbar = diag4(R^T)(M_A qdot/h + [0; m g]) - [V vec P(R^T A); 0] in FP64
+// (Sec. 3.3-3.4); u = Hbar^{-1} fbar in FP32.
+__global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p, int *status) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B.M) return;
+  const int M = B.M;
+  double q[12], qd[12], A[9], R[9];
+  load12(B.q, M, j, q);
+  A_from_q(q, A);
+  int st = polar3(A, R);
+  if (st) {
+    set_status(status, st);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B.R[(size_t)i * M + j] = R[i];
+  if (B.fixed[j]) return;  // no unknowns; its rotation may still orient a hinge
+  load12(B.qd, M, j, qd);
+  const double s0 = ldg(B.sig + j), s1 = ldg(B.sig + M + j), s2 = ldg(B.sig + 2 * (size_t)M + j);
+  const double m = ldg(B.mass + j);
+  const double vmu = ldg(B.vmu + j), vlam = ldg(B.vlam + j);
+  double fw[12];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fw[a] = s0 * qd[a] * p.inv_h;
+    fw[3 + a] = s1 * qd[3 + a] * p.inv_h;
+    fw[6 + a] = s2 * qd[6 + a] * p.inv_h;
+    fw[9 + a] = m * (qd[9 + a] * p.inv_h + p.g[a]);
+  }
+  double fb[12];
+#pragma unroll
+  for (int blk = 0; blk < 4; ++blk) mtv3(R, fw + 3 * blk, fb + 3 * blk);
+  double F[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[3 * r + c] = R[r] * A[c] + R[3 + r] * A[3 + c] + R[6 + r] * A[6 + c];
+  const double tr = vlam * (F[0] + F[4] + F[8] - 3.0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double P = vmu * (F[3 * a + i] + F[3 * i + a] - (a == i ? 2.0 : 0.0)) + (a == i ? tr : 0.0);
+      fb[3 * i + a] -= P;
+    }
+  float hf[16], ff[12], u[12];
+  load_hinvf(B, j, hf);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    B.fbar[(size_t)i * M + j] = fb[i];
+    ff[i] = (float)fb[i];
+  }
+  hinv_apply_t(hf, ff, u);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) B.ubf[(size_t)i * M + j] = u[i];
+}
+
+// One thread per joint: C(q_n) and the hinge frame in FP64 (Eq. ball / hinge,
+// axis from body a with a_y >= 0), b = G u + C(q_n) with G u in FP32.
+__global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J, StepParams p,
+                                                       int *status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= J.K) return;
+  const int K = J.K, M = B.M;
+  const int type = J.type[k];
+  const int ia = J.ja[k], ib = J.jb[k];
+  const uint8_t fl = J.flags[k];
+  const int npt = type == 0 ? 1 : 2;
+  double qa[12], qb[12], pa[2][3], pb[2][3];
+  load12(B.q, M, ia, qa);
+  if (fl & JF_B_BODY) load12(B.q, M, ib, qb);
+  load3(J.pa1, K, k, pa[0]);
+  load3(J.pb1, K, k, pb[0]);
+  if (type == 1) {
+    load3(J.pa2, K, k, pa[1]);
+    load3(J.pb2, K, k, pb[1]);
+  }
+  // gaps of the constrained points (FP64) and their displacements under u (FP32)
+  double d[2][3];
+  float g[2][3];
+  for (int t = 0; t < npt; ++t) {
+    gap_of(qa, pa[t], (fl & JF_B_BODY) ? qb : nullptr, pb[t], d[t]);
+    g[t][0] = g[t][1] = g[t][2] = 0.f;
+  }
+  for (int sd = 0; sd < 2; ++sd) {
+    if (!(fl & (sd == 0 ? JF_A_FREE : JF_B_FREE))) continue;
+    const int i = sd == 0 ? ia : ib;
+    float R[9], u[12];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) R[c] = (float)B.R[(size_t)c * M + i];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) u[c] = B.ubf[(size_t)c * M + i];
+    for (int t = 0; t < npt; ++t) {
+      const double *pp = sd == 0 ? pa[t] : pb[t];
+      const float pf[3] = {(float)pp[0], (float)pp[1], (float)pp[2]};
+      float x[3];
+      disp_at(R, u, pf, x);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) g[t][a] += sd == 0 ? x[a] : -x[a];
+    }
+  }
+  const double rr = p.residual_rhs ? 1.0 : 0.0;
+  if (type == 0) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      J.c[(size_t)r * K + k] = d[0][r];
+      J.b[(size_t)r * K + k] = (double)g[0][r] + rr * d[0][r];
+    }
+    return;
+  }
+  double uax[3], a[3], Ra[9], RH[9];
+  load3(J.ua, K, k, uax);
+  load_R(B.R, M, ia, Ra);
+  mv3(Ra, uax, a);
+  {
+    const double n = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double sgn = a[1] < 0.0 ? -n : n;
+    a[0] *= sgn; a[1] *= sgn; a[2] *= sgn;
+  }
+  hinge_frame(a, RH);
+  float RHf[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) RHf[i] = (float)RH[i];
+  double c1[3], c2[3];
+  float e1[3], e2[3];
+  mv3(RH, d[0], c1);
+  mv3(RH, d[1], c2);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    e1[r] = RHf[3 * r] * g[0][0] + RHf[3 * r + 1] * g[0][1] + RHf[3 * r + 2] * g[0][2];
+    e2[r] = RHf[3 * r] * g[1][0] + RHf[3 * r + 1] * g[1][1] + RHf[3 * r + 2] * g[1][2];
+  }
+  const double cc[5] = {c1[0], c1[1], c1[2], c2[0], c2[2]};
+  const float gg[5] = {e1[0], e1[1], e1[2], e2[0], e2[2]};
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    J.c[(size_t)r * K + k] = cc[r];
+    J.b[(size_t)r * K + k] = (double)gg[r] + rr * cc[r];
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) J.RH[(size_t)i * K + k] = RH[i];
+}
+
+// One thread per body, start of a correction sweep.  First sweep:
+// dqb = u - Hbar^{-1} g(lambda) in FP32 (back-propagation of the approximate
+// solve); later sweeps: dqb += z - Hbar^{-1} g(dlambda) (the previous
+// correction).  Then the FP64 primal residual
+// rb = fbar - Hbar dqb - g(lambda) and the correction's unconstrained solve
+// z = Hbar^{-1} rb in FP32 (kept in ubf).
+template <bool FIRST>
+__global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, DevIncidence I,
+                                                     StepParams p) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B.M) return;
+  if (B.fixed[j]) return;
+  const int M = B.M;
+  double R[9], g64[12], dq[12];
+  load_R(B.R, M, j, R);
+  float hf[16], uf[12], w[12], gf[12];
+  load_hinvf(B, j, hf);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) uf[i] = B.ubf[(size_t)i * M + j];
+  gen_force<double>(J, I, j, R, J.lambda, g64);
+  if (FIRST) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) gf[i] = (float)g64[i];
+    hinv_apply_t(hf, gf, w);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) dq[i] = (double)(uf[i] - w[i]);
+  } else {
+    float Rf[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rf[i] = (float)R[i];
+    gen_force<float>(J, I, j, Rf, J.dlam, gf);
+    hinv_apply_t(hf, gf, w);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) dq[i] = B.dqb[(size_t)i * M + j] + (double)(uf[i] - w[i]);
+  }
+  const double s[3] = {ldg(B.sig + j), ldg(B.sig + M + j), ldg(B.sig + 2 * (size_t)M + j)};
+  double hq[12];
+  hbar_apply(s, ldg(B.mass + j), ldg(B.vmu + j), ldg(B.vlam + j), p.inv_h * p.inv_h, dq, hq);
+  float rf[12], z[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) rf[i] = (float)(B.fbar[(size_t)i * M + j] - hq[i] - g64[i]);
+  hinv_apply_t(hf, rf, z);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    B.dqb[(size_t)i * M + j] = dq[i];
+    B.ubf[(size_t)i * M + j] = z[i];
+  }
+}
+
+// One thread per joint: correction rhs b = G z + (C(q_n) + G dq), the
+// bracket (the FP64 dual residual, negated) in FP64 and G z in FP32; the
+// largest |C + G dq| goes to *maxbit when it is given.  With the printed zero
+// bottom rhs (residual_rhs = 0) the constraint is G dq = 0 and C drops out.
+__global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, StepParams p,
+                                                      unsigned long long *maxbit) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double worst = 0.0;
+  if (k < J.K) {
+    const int K = J.K, M = B.M;
+    const int type = J.type[k];
+    const int ia = J.ja[k], ib = J.jb[k];
+    const uint8_t fl = J.flags[k];
+    const int npt = type == 0 ? 1 : 2;
+    double pa[2][3], pb[2][3], d[2][3];
+    float e[2][3];
+    load3(J.pa1, K, k, pa[0]);
+    load3(J.pb1, K, k, pb[0]);
+    if (type == 1) {
+      load3(J.pa2, K, k, pa[1]);
+      load3(J.pb2, K, k, pb[1]);
+    }
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        d[t][a] = 0.0;
+        e[t][a] = 0.f;
+      }
+    for (int sd = 0; sd < 2; ++sd) {
+      if (!(fl & (sd == 0 ? JF_A_FREE : JF_B_FREE))) continue;
+      const int i = sd == 0 ? ia : ib;
+      double R[9], x[12];
+      float Rf[9], z[12];
+      load_R(B.R, M, i, R);
+      load12(B.dqb, M, i, x);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) Rf[c] = (float)R[c];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) z[c] = B.ubf[(size_t)c * M + i];
+      for (int t = 0; t < npt; ++t) {
+        const double *pp = sd == 0 ? pa[t] : pb[t];
+        const float pf[3] = {(float)pp[0], (float)pp[1], (float)pp[2]};
+        double xd[3];
+        float xf[3];
+        disp_at(R, x, pp, xd);
+        disp_at(Rf, z, pf, xf);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          d[t][a] += sd == 0 ? xd[a] : -xd[a];
+          e[t][a] += sd == 0 ? xf[a] : -xf[a];
+        }
+      }
+    }
+    double v[5];
+    float w[5];
+    int C = 3;
+    if (type == 0) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        v[r] = d[0][r];
+        w[r] = e[0][r];
+      }
+    } else {
+      C = 5;
+      double RH[9];
+      load_R(J.RH, K, k, RH);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        v[r] = RH[3 * r] * d[0][0] + RH[3 * r + 1] * d[0][1] + RH[3 * r + 2] * d[0][2];
+        w[r] = (float)RH[3 * r] * e[0][0] + (float)RH[3 * r + 1] * e[0][1] + (float)RH[3 * r + 2] * e[0][2];
+      }
+      v[3] = RH[0] * d[1][0] + RH[1] * d[1][1] + RH[2] * d[1][2];
+      v[4] = RH[6] * d[1][0] + RH[7] * d[1][1] + RH[8] * d[1][2];
+      w[3] = (float)RH[0] * e[1][0] + (float)RH[1] * e[1][1] + (float)RH[2] * e[1][2];
+      w[4] = (float)RH[6] * e[1][0] + (float)RH[7] * e[1][1] + (float)RH[8] * e[1][2];
+    }
+    for (int r = 0; r < C; ++r) {
+      const double res = (p.residual_rhs ? J.c[(size_t)r * K + k] : 0.0) + v[r];
+      worst = fmax(worst, fabs(res));
+      J.b[(size_t)r * K + k] = (double)w[r] + res;
+    }
+  }
+  if (maxbit) {
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(maxbit, worst);
+  }
+}
+
+// One thread per body, end of the step: dqb (+)= z - Hbar^{-1} g(l) with
+// l = lambda after the approximate solve alone (from_u: z is u and dqb starts
+// at zero), else l = the last correction dlambda; then dq = diag4(R) dqb,
+// q += dq, qdot = dq / h (implicit Euler, Sec. 3.4).
+__global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevIncidence I,
+                                                  StepParams p, bool from_u) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B.M) return;
+  if (B.fixed[j]) return;
+  const int M = B.M;
+  double R[9];
+  load_R(B.R, M, j, R);
+  float Rf[9], hf[16], gf[12], w[12];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Rf[i] = (float)R[i];
+  load_hinvf(B, j, hf);
+  gen_force<float>(J, I, j, Rf, from_u ? J.lambda : J.dlam, gf);
+  hinv_apply_t(hf, gf, w);
+  double x[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const double base = from_u ? 0.0 : B.dqb[(size_t)i * M + j];
+    x[i] = base + (double)(B.ubf[(size_t)i * M + j] - w[i]);
+  }
+#pragma unroll
+  for (int blk = 0; blk < 4; ++blk) {
+    double dq[3];
+    mv3(R, x + 3 * blk, dq);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const size_t o = (size_t)(3 * blk + a) * M + j;
+      B.q[o] += dq[a];
+      B.qd[o] = dq[a] * p.inv_h;
+    }
+  }
+}
+
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s) {
+  if (B.M > 0) k_mx_body_prep<<<nblk(B.M, 128), 128, 0, s>>>(B, p, status);
+}
+
+void launch_mx_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,
+                          cudaStream_t s) {
+  if (J.K > 0) k_mx_joint_prep<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, status);
+}
+
+void launch_mx_res_body(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                        const StepParams &p, bool first, cudaStream_t s) {
+  if (B.M <= 0) return;
+  if (first) k_mx_res_body<true><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+  else k_mx_res_body<false><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+}
+
+void launch_mx_res_joint(const DevBodies &B, const DevJoints &J, const StepParams &p,
+                         unsigned long long *maxbit, cudaStream_t s) {
+  if (J.K > 0) k_mx_res_joint<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbit);
+}
+
+void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                     const StepParams &p, bool from_u, cudaStream_t s) {
+  if (B.M > 0) k_mx_final<<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p, from_u);
+}
+
+}  // namespace mabd

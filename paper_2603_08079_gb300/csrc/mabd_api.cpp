@@ -559,6 +559,7 @@ void mabd_config_default(mabd_config *cfg) {
   cfg->solver = MABD_SOLVER_AUTO;
   cfg->pcg_max_iters = 2000;
   cfg->pcg_rtol = 1e-13;
+  cfg->refine_steps = 1;
   cfg->residual_rhs = 1;
 }
 
@@ -585,7 +586,8 @@ mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
   *out = nullptr;
   if (!(cfg->h > 0.0) || !std::isfinite(cfg->h) || !finite_arr(cfg->gravity, 3))
     return MABD_ERR_INVALID_ARG;
-  if (cfg->precision != MABD_FP64) return MABD_ERR_UNSUPPORTED;
+  if (cfg->precision != MABD_FP64 && cfg->precision != MABD_MIXED) return MABD_ERR_INVALID_ARG;
+  if (cfg->refine_steps < 0 || cfg->refine_steps > MABD_MAX_REFINE) return MABD_ERR_INVALID_ARG;
   if (cfg->solver < MABD_SOLVER_AUTO || cfg->solver > MABD_SOLVER_PCG) return MABD_ERR_INVALID_ARG;
   if (cfg->pcg_max_iters < 1 || !(cfg->pcg_rtol > 0.0)) return MABD_ERR_INVALID_ARG;
   if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) return MABD_ERR_INVALID_ARG;
@@ -692,6 +694,11 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   }
   if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
   if (solver == MABD_SOLVER_TREE && !is_tree) return MABD_ERR_UNSUPPORTED;
+  if (ctx->cfg.precision == MABD_MIXED && K > 0 && solver != MABD_SOLVER_CHAIN) {
+    std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
+                  "the mixed-precision form is implemented for chain topologies only");
+    return MABD_ERR_UNSUPPORTED;
+  }
   if (solver == MABD_SOLVER_CHAIN) {
     border = cborder;
     jorder = cjorder;
@@ -841,6 +848,15 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   J.c = dnew<double>(ctx, 5 * (size_t)Kx, ok);
   J.b = dnew<double>(ctx, 5 * (size_t)Kx, ok);
   J.lambda = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+  const bool mixed = ctx->cfg.precision == MABD_MIXED;
+  float *dhinvf = nullptr;
+  if (mixed) {
+    dhinvf = dnew<float>(ctx, HINV_N * (size_t)Mx, ok);
+    B.fbar = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+    B.dqb = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+    B.ubf = dnew<float>(ctx, 12 * (size_t)Mx, ok);
+    J.dlam = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+  }
   int32_t *dioff = dnew<int32_t>(ctx, (size_t)M + 1, ok);
   int32_t *dij = dnew<int32_t>(ctx, std::max<size_t>(ijoint.size(), 1), ok);
   int8_t *dis = dnew<int8_t>(ctx, std::max<size_t>(iside.size(), 1), ok);
@@ -856,6 +872,13 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   CK(up(dvmu, vmu.data(), vmu.size() * 8));
   CK(up(dvlam, vlam.data(), vlam.size() * 8));
   CK(up(dhinv, hinv.data(), hinv.size() * 8));
+  std::vector<float> hinvf;
+  if (mixed) {
+    hinvf.assign(hinv.begin(), hinv.end());
+    CK(up(dhinvf, hinvf.data(), hinvf.size() * 4));
+    CK(cudaMemsetAsync(B.dqb, 0, 12 * (size_t)Mx * 8, ctx->stream));
+    CK(cudaMemsetAsync(J.dlam, 0, 5 * (size_t)Kx * 8, ctx->stream));
+  }
   CK(up(dfixed, fixed.data(), fixed.size()));
   CK(up(djt, jtype.data(), jtype.size()));
   CK(up(dja, ja.data(), ja.size() * 4));
@@ -876,6 +899,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   B.vmu = dvmu;
   B.vlam = dvlam;
   B.hinv = dhinv;
+  B.hinvf = dhinvf;
   B.fixed = dfixed;
   J.type = djt;
   J.ja = dja;
@@ -1062,21 +1086,69 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
 // graphs: `pre` runs everything up to the dual solve (the whole solve for
 // chains and trees, the set-up for PCG), the PCG iterations run in chunks,
 // and `post` back-propagates (and, with statistics, computes residuals).
+// cyclic reduction of the chain's dual: factorization of the current blocks
+// with the current rhs, or (rhs_only) a new rhs J.b through the stored
+// factors; level 0 writes its solution to Jout.lambda and adds it to acc
+static void enqueue_cr(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout,
+                       double *acc) {
+  const int nl = (int)ctx->levels.size();
+  for (int l = 0; l + 1 < nl; ++l) {
+    if (rhs_only)
+      run(ctx, "cr_rhs", [&] { launch_cr_rhs(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], s); });
+    else
+      run(ctx, "cr_level", [&] {
+        launch_cr_level(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], ctx->d_status, s);
+      });
+  }
+  if (nl == 1) {
+    // a single row (one joint): level 0 is the top row
+    CRLevel top = ctx->levels[0];
+    top.lam = Jout.lambda;
+    run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, top, 0, ctx->d_status, s, acc); });
+    return;
+  }
+  run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
+  for (int l = nl - 2; l >= 0; --l)
+    run(ctx, "cr_back", [&] {
+      launch_cr_back(ctx->C, l == 0 ? Jout : ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s,
+                     l == 0 ? acc : nullptr);
+    });
+}
+
+// mixed-precision chain step (k_mixed.cu): approximate solve with FP32
+// products and the FP64 reduction, then refine_steps FP64 residual-correction
+// sweeps through the stored factors, then the state update
+static void enqueue_mixed_chain(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
+  const StepParams &p = ctx->sp;
+  run(ctx, "mx_body_prep", [&] { launch_mx_body_prep(ctx->B, p, ctx->d_status, s); });
+  if (ctx->J.K == 0) {
+    run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, true, s); });
+    return;
+  }
+  run(ctx, "mx_joint_prep", [&] { launch_mx_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
+  run(ctx, "mx_chain_gram", [&] { launch_mx_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
+  enqueue_cr(ctx, s, false, ctx->J, nullptr);
+  const int sweeps = ctx->cfg.refine_steps;
+  DevJoints Jc = ctx->J;
+  Jc.lambda = ctx->J.dlam;
+  for (int it = 0; it < sweeps; ++it) {
+    run(ctx, "mx_res_body", [&] { launch_mx_res_body(ctx->B, ctx->J, ctx->I, p, it == 0, s); });
+    unsigned long long *mb = (maxbits && it == sweeps - 1) ? maxbits + 2 : nullptr;
+    run(ctx, "mx_res_joint", [&] { launch_mx_res_joint(ctx->B, ctx->J, p, mb, s); });
+    enqueue_cr(ctx, s, true, Jc, ctx->J.lambda);
+  }
+  run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, sweeps == 0, s); });
+}
+
 static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s) {
   const StepParams &p = ctx->sp;
+  if (ctx->cfg.precision == MABD_MIXED) return;  // the whole step is in enqueue_post
   run(ctx, "body_prep", [&] { launch_body_prep(ctx->B, p, ctx->d_status, s); });
   if (ctx->J.K == 0) return;
   run(ctx, "joint_prep", [&] { launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
   if (ctx->solver == MABD_SOLVER_CHAIN) {
     run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
-    const int nl = (int)ctx->levels.size();
-    for (int l = 0; l + 1 < nl; ++l)
-      run(ctx, "cr_level", [&] {
-        launch_cr_level(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], ctx->d_status, s);
-      });
-    run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
-    for (int l = nl - 2; l >= 0; --l)
-      run(ctx, "cr_back", [&] { launch_cr_back(ctx->C, ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s); });
+    enqueue_cr(ctx, s, false, ctx->J, nullptr);
   } else if (ctx->solver == MABD_SOLVER_TREE) {
     const auto &lv = ctx->tree_lvl;
     const int nl = (int)lv.size() - 1;
@@ -1103,7 +1175,9 @@ static void enqueue_pcg_chunk(mabd_ctx *ctx, cudaStream_t s) {
 
 static void enqueue_post(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
   const StepParams &p = ctx->sp;
-  if (!(ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE))
+  if (ctx->cfg.precision == MABD_MIXED)
+    enqueue_mixed_chain(ctx, maxbits, s);
+  else if (!(ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE))
     run(ctx, "backprop", [&] { launch_backprop(ctx->B, ctx->J, ctx->I, p, ctx->d_status, s); });
   if (maxbits && ctx->J.K > 0)
     run(ctx, "residuals", [&] { launch_residuals(ctx->B, ctx->J, p, maxbits, ctx->d_status, s); });
@@ -1220,11 +1294,11 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
   if (stats) {
     if (ctx->max_cap < nsteps) {
       bool ok = true;
-      ctx->d_max = dnew<unsigned long long>(ctx, 2 * (size_t)nsteps, ok);
+      ctx->d_max = dnew<unsigned long long>(ctx, 3 * (size_t)nsteps, ok);
       if (!ok) return MABD_ERR_OUT_OF_MEMORY;
       ctx->max_cap = nsteps;
     }
-    CK(cudaMemsetAsync(ctx->d_max, 0, 2 * (size_t)nsteps * 8, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_max, 0, 3 * (size_t)nsteps * 8, ctx->stream));
   }
   if (!stats && !ctx->prof_on && !ctx->debug_sync && graphs_ready(ctx)) {
     // order the private graph stream after the caller's stream and back
@@ -1241,7 +1315,7 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
   std::vector<int> pit(nsteps, 0);
   std::vector<double> prel(nsteps, 0.0);
   for (int i = 0; i < nsteps; ++i) {
-    mabd_status st = step_once(ctx, stats ? ctx->d_max + 2 * i : nullptr);
+    mabd_status st = step_once(ctx, stats ? ctx->d_max + 3 * i : nullptr);
     if (st) return st;
     if (ctx->solver == MABD_SOLVER_PCG) {
       pit[i] = ctx->pcg_last_iters;
@@ -1249,18 +1323,20 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
     }
   }
   if (!stats) return MABD_OK;
-  std::vector<unsigned long long> hb(2 * (size_t)nsteps);
+  std::vector<unsigned long long> hb(3 * (size_t)nsteps);
   CK(cudaMemcpyAsync(hb.data(), ctx->d_max, hb.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < nsteps; ++i) {
     double lin, nl;
-    std::memcpy(&lin, &hb[2 * i], 8);
-    std::memcpy(&nl, &hb[2 * i + 1], 8);
+    double ref;
+    std::memcpy(&lin, &hb[3 * i], 8);
+    std::memcpy(&nl, &hb[3 * i + 1], 8);
+    std::memcpy(&ref, &hb[3 * i + 2], 8);
     stats[i].lin_residual = lin;
     stats[i].joint_residual = nl;
     stats[i].pcg_iters = pit[i];
     stats[i].pcg_rel_residual = prel[i];
-    stats[i].refine_residual = 0.0;
+    stats[i].refine_residual = ctx->cfg.precision == MABD_MIXED ? ref : 0.0;
   }
   return read_status(ctx);
 }
@@ -1350,6 +1426,8 @@ mabd_status mabd_get_info(mabd_ctx *ctx, mabd_info *info) {
   info->topology = ctx->topology;
   info->solver = ctx->solver;
   info->device_bytes = ctx->device_bytes;
+  info->precision = ctx->cfg.precision;
+  info->refine_steps = ctx->cfg.refine_steps;
   return MABD_OK;
 }
 
@@ -1371,7 +1449,9 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
   if (!ctx || cap < 0 || !count) return MABD_ERR_INVALID_ARG;
   mabd_status st = harvest_profile(ctx);
   if (st) return st;
-  static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "cr_level", "cr_reduce", "cr_combine",
+  static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "mx_body_prep", "mx_joint_prep",
+                                "mx_chain_gram", "mx_res_body", "mx_res_joint", "cr_rhs", "mx_final",
+                                "cr_level", "cr_reduce", "cr_combine",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
                                 "pcg_iteration", "backprop", "residuals"};
   int n = 0;

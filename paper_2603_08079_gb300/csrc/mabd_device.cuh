@@ -91,7 +91,9 @@ __device__ __forceinline__ int polar3(const double A[9], double R[9]) {
       nrm += y * y;
       X[i] = y;
     }
-    if (diff <= 1e-30 * nrm) break;
+    // quadratic convergence: a relative change below 1e-9 leaves an error
+    // of order 1e-18 in the iterate just formed
+    if (diff <= 1e-18 * nrm) break;
   }
   if (it == 40) return ST_POLAR_NOCONV;
 #pragma unroll

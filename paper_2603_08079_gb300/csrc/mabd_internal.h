@@ -40,6 +40,11 @@ struct DevBodies {
   const uint8_t *fixed; // [M]
   double *R;            // [9][M]  rotation of the step (row-major 3x3)
   double *ubar;         // [12][M] unconstrained solve in the rest frame
+  // mixed-precision form only (null otherwise)
+  const float *hinvf;   // [16][M] structured Hbar^{-1} rounded to FP32
+  double *fbar;         // [12][M] rest-frame rhs of the step (FP64)
+  double *dqb;          // [12][M] rest-frame increment diag4(R^T) dq (FP64 accumulator)
+  float *ubf;           // [12][M] FP32 Hbar^{-1} of the current rhs (u, then each correction)
 };
 
 // joint flags
@@ -60,6 +65,7 @@ struct DevJoints {
   double *c;             // [5][K] C(q_n)
   double *b;             // [5][K] dual rhs G u + C(q_n)
   double *lambda;        // [5][K] multipliers (rows beyond C_k are zero)
+  double *dlam;          // [5][K] mixed form: multiplier correction of a refinement sweep
 };
 
 // body -> incident joints (CSR over internal body order)
@@ -156,10 +162,29 @@ void launch_cr_combine(const DevChain &C, const DevJoints &J, const CRLevel &cur
 void launch_cr_level(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
                      const CRLevel &next, int *status, cudaStream_t s);
 void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,
-                   int *status, cudaStream_t s);
-// back-substitution of `level`; level 0 writes its rows n >= C.off to J.lambda
+                   int *status, cudaStream_t s, double *acc = nullptr);
+// back-substitution of `level`; level 0 writes its rows n >= C.off to
+// J.lambda and, when acc is not null, also adds them to acc ([5][K])
 void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevel &cur, const CRLevel &next,
-                    int level, cudaStream_t s);
+                    int level, cudaStream_t s, double *acc = nullptr);
+// new right-hand side through the stored factors: forward elimination of
+// `level` (level 0 reads J.b) writing next.b and the odd rows' y; the top
+// row and the back-substitution then run as for a factorization
+void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
+                   const CRLevel &next, cudaStream_t s);
+
+// mixed-precision form of the chain step (k_mixed.cu)
+void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s);
+void launch_mx_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,
+                          cudaStream_t s);
+void launch_mx_chain_gram(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                          const DevChain &C, cudaStream_t s);
+void launch_mx_res_body(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                        const StepParams &p, bool first, cudaStream_t s);
+void launch_mx_res_joint(const DevBodies &B, const DevJoints &J, const StepParams &p,
+                         unsigned long long *maxbit, cudaStream_t s);
+void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                     const StepParams &p, bool from_u, cudaStream_t s);
 
 // tree (k_tree.cu): one launch per level, deepest first, then root first
 // level [lo, hi) of the body order: T.order[lo, mid) lists its bodies with

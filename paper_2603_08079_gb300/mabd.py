@@ -18,6 +18,7 @@ from . import build as _build
 
 WORLD = -1
 SOLVERS = {"auto": 0, "chain": 1, "tree": 2, "pcg": 3}
+PRECISIONS = {"fp64": 0, "mixed": 1}
 TOPOLOGIES = {0: "none", 1: "chain", 2: "tree", 3: "graph"}
 STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of device memory",
           4: "CUDA error", 5: "not positive definite", 6: "inverted body", 7: "non-finite",
@@ -50,7 +51,8 @@ class StepStats(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("bodies", C.c_int64), ("joints", C.c_int64), ("dual_rows", C.c_int64),
-                ("topology", C.c_int32), ("solver", C.c_int32), ("device_bytes", C.c_int64)]
+                ("topology", C.c_int32), ("solver", C.c_int32), ("device_bytes", C.c_int64),
+                ("precision", C.c_int32), ("refine_steps", C.c_int32)]
 
 
 # numpy mirrors of mabd_body_desc / mabd_joint_desc (C layout, natural alignment)
@@ -145,7 +147,7 @@ class Solver:
 
     def __init__(self, sc: dict, solver: str = "auto", residual_rhs: int = 1,
                  stream=None, allocator: str = "torch", pcg_rtol: float = 1e-13,
-                 pcg_max_iters: int = 2000):
+                 pcg_max_iters: int = 2000, precision: str = "fp64", refine_steps: int = 1):
         import torch
 
         if not torch.cuda.is_available():
@@ -162,6 +164,8 @@ class Solver:
         cfg.residual_rhs = int(residual_rhs)
         cfg.pcg_rtol = float(pcg_rtol)
         cfg.pcg_max_iters = int(pcg_max_iters)
+        cfg.precision = PRECISIONS[precision]
+        cfg.refine_steps = int(refine_steps)
         cfg.stream = C.c_void_p(self.stream.cuda_stream)
         if allocator == "torch":
             dev, strm = self.device, self.stream
@@ -231,6 +235,7 @@ class Solver:
         d = {f: getattr(inf, f) for f, _ in Info._fields_}
         d["topology"] = TOPOLOGIES.get(d["topology"], d["topology"])
         d["solver"] = {v: k for k, v in SOLVERS.items()}.get(d["solver"], d["solver"])
+        d["precision"] = {v: k for k, v in PRECISIONS.items()}.get(d["precision"], d["precision"])
         return d
 
     def profile(self, enable: bool):
