@@ -592,22 +592,6 @@ __global__ void __launch_bounds__(CRF) k_cr_level(DevChain C, DevJoints J, CRLev
   if (blockIdx.x == 0 && t == 0) combine_row(C, J, cur, level, next, 0, sc, -1, Nh > 0 ? 0 : -1);
 }
 
-// Single remaining row: lambda = D^{-1} b.
-__global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *status, double *acc) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double D[25], L[25], b[5], y[5], x[5];
-  ld_D(C, J, top, level, 0, D);
-  ld_b(C, J, top, level, 0, b);
-  if (!chol5(D, L)) set_status(status, ST_NOT_SPD);
-  lsolve5(L, b, y);
-  ltsolve5(L, y, x);
-#pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    top.lam[(size_t)r * top.N] = x[r];
-    if (acc) acc[(size_t)r * top.N] += x[r];
-  }
-}
-
 // Back-substitution: even rows copy from the next level, odd rows solve
 // lambda_n = L^{-T}(y - Ya lambda_{n-1} - Yb lambda_{n+1}).
 template <int CN, int CL, int CR>
@@ -679,6 +663,336 @@ __global__ void __launch_bounds__(128) k_cr_back(CRLevel cur, CRLevel next, DevC
     BCK(12, 5, 5, 0) BCK(13, 5, 5, 3) BCK(14, 5, 5, 5)
 #undef BCK
     default: break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small levels: one warp per eliminated row
+// ---------------------------------------------------------------------------
+// On this GPU a warp-wide FP64 instruction occupies the warp for tens of
+// cycles whatever the number of active lanes, so a level with few rows costs
+// (FP64 instructions of one row) x (that latency).  The kernels below spread
+// the work of a row over the lanes: every lane factors the (at most 5x5)
+// diagonal block, lane c solves right-hand-side column c, and the Schur
+// entries are dealt out over the lanes.
+
+// single entries of the level's arrays (level 0 assembles them as ld_D/ld_B/ld_b do)
+__device__ __forceinline__ double ldD1(const DevChain &C, const DevJoints &J, const CRLevel &L,
+                                       int level, int n, int i) {
+  if (level != 0) return L.D[(size_t)i * L.N + n];
+  const int k = n - C.off;
+  const bool diag = i == 0 || i == 2 || i == 5 || i == 9 || i == 14;
+  if (k < 0) return diag ? 1.0 : 0.0;
+  if (J.type[k] == 0 && (i == 9 || i == 14)) return 1.0;
+  const uint8_t f = C.jflags[k];
+  double v = 0.0;
+  if (f & 1) v += C.Dfirst[(size_t)i * C.K + k];
+  if (f & 2) v += C.Dsecond[(size_t)i * C.K + k];
+  return v;
+}
+
+__device__ __forceinline__ double ldB1(const DevChain &C, const CRLevel &L, int level, int n, int i) {
+  if (level != 0) return L.B[(size_t)i * L.N + n];
+  const int k = n - C.off;
+  return (k >= 0 && (C.jflags[k] & 4)) ? C.B[(size_t)i * C.K + k] : 0.0;
+}
+
+__device__ __forceinline__ double ldb1(const DevChain &C, const DevJoints &J, const CRLevel &L,
+                                       int level, int n, int r) {
+  if (level != 0) return L.b[(size_t)r * L.N + n];
+  const int k = n - C.off;
+  if (k < 0) return 0.0;
+  const int Cs = J.type[k] == 0 ? 3 : 5;
+  return r < Cs ? J.b[(size_t)r * J.K + k] : 0.0;
+}
+
+// per-warp shared workspace of one eliminated row
+struct WRow {
+  double D[15];       // packed diagonal block
+  double Z[5][11];    // right-hand sides [B_{n-1}^T | B_n | b], then Y = L^{-1} Z
+  double cl[20];      // contribution to the left row: packed -Ya^T Ya (15), -Ya^T y (5) (stored positive)
+  double cr[20];      // ... to the right row
+  double bn[25];      // new coupling -Ya^T Yb
+};
+
+// Cholesky with reciprocal diagonal of the packed n x n block (every lane)
+__device__ __forceinline__ bool chol_rd(const double *Dp, int cn, double L[5][5], double id[5]) {
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double sum = Dp[pk(c, c)];
+#pragma unroll
+    for (int k = 0; k < c; ++k) sum -= L[c][k] * L[c][k];
+    if (c < cn && !(sum > 0.0)) ok = false;
+    if (!(sum > 0.0)) sum = 1.0;  // rows beyond cn (and a failed pivot) get a harmless 1
+    id[c] = rsqrt(sum);
+    L[c][c] = sum * id[c];
+#pragma unroll
+    for (int r = c + 1; r < 5; ++r) {
+      double t = r < cn ? Dp[pk(r, c)] : 0.0;
+#pragma unroll
+      for (int k = 0; k < c; ++k) t -= L[r][k] * L[c][k];
+      L[r][c] = t * id[c];
+    }
+  }
+  return ok;
+}
+
+// eliminate odd row n (index m) with one warp; fills w (contributions) and,
+// when write_fac, the factor record of the row
+__device__ __forceinline__ void warp_reduce_row(const DevChain &C, const DevJoints &J,
+                                                const CRLevel &cur, int level, int n, int m,
+                                                WRow &w, bool write_fac, int *status) {
+  const int lane = threadIdx.x & 31;
+  const int N = cur.N, Nh = N / 2;
+  const int cn = row_size(C, J, level, n), cl = row_size(C, J, level, n - 1);
+  const int cr = n + 1 < N ? row_size(C, J, level, n + 1) : 0;
+  const int ncol = cl + cr + 1;
+  if (lane < 15) w.D[lane] = ldD1(C, J, cur, level, n, lane);
+  for (int e = lane; e < 55; e += 32) (&w.Z[0][0])[e] = 0.0;
+  __syncwarp();
+  if (lane < 25) {
+    const int r = lane / 5, c = lane % 5;
+    // B_{n-1} (cl x cn): column r of the first block of Z is its row r
+    if (r < cl && c < cn) w.Z[c][r] = ldB1(C, cur, level, n - 1, lane);
+    if (r < cn && c < cr) w.Z[r][cl + c] = ldB1(C, cur, level, n, lane);
+  }
+  if (lane < cn) w.Z[lane][cl + cr] = ldb1(C, J, cur, level, n, lane);
+  __syncwarp();
+  double L[5][5], id[5];
+  const bool ok = chol_rd(w.D, cn, L, id);
+  if (!ok && lane == 0) set_status(status, ST_NOT_SPD);
+  // packed L with reciprocal diagonal (selected with constant indices so L
+  // stays in registers); replaces D in the workspace
+  double lp = 0.0;
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c)
+      if (lane == r * (r + 1) / 2 + c && r < cn) lp = r == c ? id[r] : L[r][c];
+  __syncwarp();
+  if (lane < 15) w.D[lane] = lp;
+  // lane c: column c of Y = L^{-1} Z
+  double y[5];
+  if (lane < ncol) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      double t = i < cn ? w.Z[i][lane] : 0.0;
+#pragma unroll
+      for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+      y[i] = t * id[i];
+    }
+  }
+  __syncwarp();
+  if (lane < ncol) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (i < cn) w.Z[i][lane] = y[i];
+  }
+  __syncwarp();
+  if (write_fac) {
+    double *f = cur.fac;
+    for (int o = lane; o < 70; o += 32) {
+      double v = 0.0;
+      if (o < 15) {
+        v = w.D[o];
+      } else if (o < 40) {
+        const int r = (o - 15) / 5, c = (o - 15) % 5;
+        if (r < cn && c < cl) v = w.Z[r][c];
+      } else if (o < 65) {
+        const int r = (o - 40) / 5, c = (o - 40) % 5;
+        if (r < cn && c < cr) v = w.Z[r][cl + c];
+      } else {
+        const int r = o - 65;
+        if (r < cn) v = w.Z[r][cl + cr];
+      }
+      f[(size_t)o * Nh + m] = v;
+    }
+  }
+  // Schur entries: 0-14 Ya^T Ya packed, 15-19 Ya^T y, 20-34 Yb^T Yb packed,
+  // 35-39 Yb^T y, 40-64 Ya^T Yb
+  for (int e = lane; e < 65; e += 32) {
+    int a = -1, b = -1;    // Z columns of the two factors
+    double *dst;
+    bool neg = false;
+    if (e < 15 || (e >= 20 && e < 35)) {
+      const int o = e < 15 ? e : e - 20;
+      int r = 0;
+      while ((r + 1) * (r + 2) / 2 <= o) ++r;
+      const int c = o - r * (r + 1) / 2;
+      if (e < 15) {
+        if (r < cl && c < cl) { a = r; b = c; }
+        dst = &w.cl[o];
+      } else {
+        if (r < cr && c < cr) { a = cl + r; b = cl + c; }
+        dst = &w.cr[o];
+      }
+    } else if (e < 20) {
+      const int r = e - 15;
+      if (r < cl) { a = r; b = cl + cr; }
+      dst = &w.cl[e];
+    } else if (e < 40) {
+      const int r = e - 35;
+      if (r < cr) { a = cl + r; b = cl + cr; }
+      dst = &w.cr[15 + r];
+    } else {
+      const int r = (e - 40) / 5, c = (e - 40) % 5;
+      if (r < cl && c < cr) { a = r; b = cl + c; }
+      dst = &w.bn[e - 40];
+      neg = true;
+    }
+    double t = 0.0;
+    if (a >= 0) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+        if (i < cn) t += w.Z[i][a] * w.Z[i][b];
+    }
+    *dst = neg ? -t : t;
+  }
+}
+
+// next-level row mm from even row e: D_e - (right part of the odd row on its
+// left) - (left part of the odd row on its right); B from the right odd row
+__device__ __forceinline__ void warp_combine_row(const DevChain &C, const DevJoints &J,
+                                                 const CRLevel &cur, int level, const CRLevel &next,
+                                                 int mm, const WRow *left, const WRow *right) {
+  const int lane = threadIdx.x & 31;
+  const int e = 2 * mm;
+  for (int o = lane; o < 45; o += 32) {
+    if (o < 15) {
+      double v = ldD1(C, J, cur, level, e, o);
+      if (right) v -= right->cl[o];
+      if (left) v -= left->cr[o];
+      next.D[(size_t)o * next.N + mm] = v;
+    } else if (o < 20) {
+      const int r = o - 15;
+      double v = ldb1(C, J, cur, level, e, r);
+      if (right) v -= right->cl[15 + r];
+      if (left) v -= left->cr[15 + r];
+      next.b[(size_t)r * next.N + mm] = v;
+    } else {
+      next.B[(size_t)(o - 20) * next.N + mm] = right ? right->bn[o - 20] : 0.0;
+    }
+  }
+}
+
+// One level: block b owns odd rows m in [b RW, b RW + RW) (warps 0..RW-1) and
+// redoes odd row b RW + RW in warp RW (halo, no factor write), then forms the
+// next-level rows m + 1 of its own rows (block 0 also row 0).
+constexpr int RW = 4;
+
+__global__ void __launch_bounds__(32 * (RW + 1)) k_cr_level_w(DevChain C, DevJoints J, CRLevel cur,
+                                                              int level, CRLevel next, int *status) {
+  __shared__ WRow ws[RW + 1];
+  const int wi = threadIdx.x >> 5;
+  const int N = cur.N, Nh = N / 2;
+  const int m = blockIdx.x * RW + wi;
+  const bool have = m < Nh;
+  if (have) warp_reduce_row(C, J, cur, level, 2 * m + 1, m, ws[wi], wi < RW, status);
+  __syncthreads();
+  if (wi < RW && have && 2 * m + 2 < N) {
+    const bool right = m + 1 < Nh;
+    warp_combine_row(C, J, cur, level, next, m + 1, &ws[wi], right ? &ws[wi + 1] : nullptr);
+  }
+  if (blockIdx.x == 0 && wi == 0) warp_combine_row(C, J, cur, level, next, 0, nullptr, &ws[0]);
+}
+
+// Back-substitution with one warp per odd row 2m+1 (lanes r < C_n form
+// v_r = y_r - Ya lambda_{n-1} - Yb lambda_{n+1}, then every lane solves
+// L^T x = v); the same warp copies even row 2m from the next level.
+__global__ void __launch_bounds__(128) k_cr_back_w(CRLevel cur, CRLevel next, DevChain C, DevJoints J,
+                                                   int level, double *acc) {
+  const int lane = threadIdx.x & 31;
+  const int m = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int N = cur.N, Nh = N / 2;
+  if (m >= (N + 1) / 2) return;
+  double *out = level == 0 ? J.lambda : cur.lam;
+  const int out_N = level == 0 ? J.K : N, out_off = level == 0 ? C.off : 0;
+  if (level != 0) acc = nullptr;
+  {
+    const int n = 2 * m;
+    if (lane < 5 && n >= out_off) {
+      const size_t o = (size_t)lane * out_N + (n - out_off);
+      const double v = next.lam[(size_t)lane * next.N + m];
+      out[o] = v;
+      if (acc) acc[o] += v;
+    }
+  }
+  if (m >= Nh) return;
+  const int n = 2 * m + 1;
+  const int cn = row_size(C, J, level, n), cl = row_size(C, J, level, n - 1);
+  const int cr = n + 1 < N ? row_size(C, J, level, n + 1) : 0;
+  const double *f = cur.fac;
+  double v = 0.0;
+  if (lane < cn) {
+    v = f[(size_t)(65 + lane) * Nh + m];
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      if (c < cl) v -= f[(size_t)(15 + 5 * lane + c) * Nh + m] * next.lam[(size_t)c * next.N + m];
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      if (c < cr) v -= f[(size_t)(40 + 5 * lane + c) * Nh + m] * next.lam[(size_t)c * next.N + m + 1];
+  }
+  double vv[5], x[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) vv[r] = __shfl_sync(0xffffffffu, v, r);
+  // L^T x = v with L packed (reciprocal diagonal), every lane
+#pragma unroll
+  for (int i = 4; i >= 0; --i) {
+    if (i >= cn) {
+      x[i] = 0.0;
+      continue;
+    }
+    double t = vv[i];
+#pragma unroll
+    for (int k = i + 1; k < 5; ++k)
+      if (k < cn) t -= f[(size_t)pk(k, i) * Nh + m] * x[k];
+    x[i] = t * f[(size_t)pk(i, i) * Nh + m];
+  }
+  if (lane < 5 && n >= out_off) {
+    double xv = 0.0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+      if (r == lane) xv = x[r];
+    const size_t o = (size_t)lane * out_N + (n - out_off);
+    out[o] = xv;
+    if (acc) acc[o] += xv;
+  }
+}
+
+// Single remaining row: lambda = D^{-1} b (Cholesky with reciprocal diagonal).
+__global__ void k_cr_top(DevChain C, DevJoints J, CRLevel top, int level, int *status, double *acc) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int cn = row_size(C, J, level, 0);
+  double Dp[15], b[5], L[5][5], id[5], y[5], x[5];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) Dp[i] = ldD1(C, J, top, level, 0, i);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) b[r] = ldb1(C, J, top, level, 0, r);
+  if (!chol_rd(Dp, cn, L, id)) set_status(status, ST_NOT_SPD);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    y[i] = 0.0;
+    if (i >= cn) continue;
+    double t = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+    y[i] = t * id[i];
+  }
+#pragma unroll
+  for (int i = 4; i >= 0; --i) {
+    x[i] = 0.0;
+    if (i >= cn) continue;
+    double t = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 5; ++k)
+      if (k < cn) t -= L[k][i] * x[k];
+    x[i] = t * id[i];
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    top.lam[(size_t)r * top.N] = x[r];
+    if (acc) acc[(size_t)r * top.N] += x[r];
   }
 }
 
@@ -766,9 +1080,16 @@ void launch_cr_combine(const DevChain &C, const DevJoints &J, const CRLevel &cur
   if (next.N > 0) k_cr_combine<<<nblk(next.N, 128), 128, 0, s>>>(C, J, cur, level, next, cL, cR, Bn);
 }
 
+// levels with at most this many eliminations use one warp per row
+constexpr int CR_WARP_ROWS = 2048;
+
 void launch_cr_level(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
                      const CRLevel &next, int *status, cudaStream_t s) {
   const int Nh = cur.N / 2;
+  if (Nh >= 1 && Nh <= CR_WARP_ROWS) {
+    k_cr_level_w<<<(Nh + RW - 1) / RW, 32 * (RW + 1), 0, s>>>(C, J, cur, level, next, status);
+    return;
+  }
   const int blocks = Nh > 0 ? (Nh + CRF - 2) / (CRF - 1) : 1;
   k_cr_level<<<blocks, CRF, 0, s>>>(C, J, cur, level, next, status);
 }
@@ -780,7 +1101,13 @@ void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, in
 
 void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevel &cur, const CRLevel &next,
                     int level, cudaStream_t s, double *acc) {
-  if (cur.N > 0) k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next, C, J, level, acc);
+  if (cur.N <= 0) return;
+  if (cur.N / 2 <= CR_WARP_ROWS) {
+    const int rows = (cur.N + 1) / 2;
+    k_cr_back_w<<<(rows + 3) / 4, 128, 0, s>>>(cur, next, C, J, level, acc);
+    return;
+  }
+  k_cr_back<<<nblk(cur.N, 128), 128, 0, s>>>(cur, next, C, J, level, acc);
 }
 
 void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
