@@ -66,8 +66,9 @@ def make_scene(name: str, M: int | None = None) -> dict:
 
 FORMS = {
     "fp64": "FP64 throughout",
-    "mixed": "FP32 per-body/per-joint products and Gram blocks; FP64 polar, rhs, constraint "
-             "values, dual cyclic reduction and %d FP64 residual-correction sweep(s)",
+    "mixed": "FP32 per-body/per-joint products (and Gram blocks on chains, PCG iterations on "
+             "graphs); FP64 polar, rhs, constraint values, chain cyclic reduction and %d FP64 "
+             "residual-correction sweep(s)",
 }
 
 
@@ -84,10 +85,11 @@ def workload_config(M: int, K: int, rows: int, name: str = "chain1m", form: str 
 
 
 def chosen_form(args) -> str:
-    """The mixed form exists for chains; other topologies run FP64."""
+    """The mixed form exists for chains and for the PCG path (nets); trees
+    and the batched forest run FP64."""
     if args.precision != "auto":
         return args.precision
-    return "mixed" if args.workload == "chain1m" else "fp64"
+    return "mixed" if args.workload in ("chain1m", "net64x64x16") else "fp64"
 
 
 def dist_env():

@@ -63,6 +63,20 @@ __device__ __forceinline__ void project(const T Ea[3][3], const int ca[3], const
 
 // Gram blocks of body j with products in T (double: the FP64 form; float:
 // the mixed form, inputs rounded to FP32); the blocks are stored in FP64.
+template <typename T> struct GP;
+template <> struct GP<double> {
+  __device__ static const double *R(const DevBodies &B) { return B.R; }
+  __device__ static const double *RH(const DevJoints &J) { return J.RH; }
+  __device__ static const double *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1 : J.pb1; }
+  __device__ static const double *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2 : J.pb2; }
+};
+template <> struct GP<float> {
+  __device__ static const float *R(const DevBodies &B) { return B.Rf; }
+  __device__ static const float *RH(const DevJoints &J) { return J.RHf; }
+  __device__ static const float *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1f : J.pb1f; }
+  __device__ static const float *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2f : J.pb2f; }
+};
+
 template <typename T, typename HT>
 __device__ __forceinline__ void chain_gram_body(const DevBodies &B, const DevJoints &J,
                                                 const DevIncidence &I, const DevChain &C,
@@ -74,7 +88,7 @@ __device__ __forceinline__ void chain_gram_body(const DevBodies &B, const DevJoi
   const int M = B.M, K = J.K;
   T R[9], h[16];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) R[i] = (T)B.R[(size_t)i * M + j];
+  for (int i = 0; i < 9; ++i) R[i] = GP<T>::R(B)[(size_t)i * M + j];
 #pragma unroll
   for (int i = 0; i < 16; ++i) h[i] = (T)__ldg(hinv + (size_t)i * M + j);
   // per slot: directions E (rest frame, columns = rows' directions), points
@@ -87,16 +101,16 @@ __device__ __forceinline__ void chain_gram_body(const DevBodies &B, const DevJoi
     kk[s] = k;
     ty[s] = type;
     const T sgn = side == 0 ? T(1) : T(-1);
-    const double *p1 = side == 0 ? J.pa1 : J.pb1;
+    const T *p1 = GP<T>::p1(J, side);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) P[s][0][a] = (T)__ldg(p1 + (size_t)a * K + k);
+    for (int a = 0; a < 3; ++a) P[s][0][a] = __ldg(p1 + (size_t)a * K + k);
     if (type == 1) {
-      const double *p2 = side == 0 ? J.pa2 : J.pb2;
+      const T *p2 = GP<T>::p2(J, side);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) P[s][1][a] = (T)__ldg(p2 + (size_t)a * K + k);
+      for (int a = 0; a < 3; ++a) P[s][1][a] = __ldg(p2 + (size_t)a * K + k);
       T RH[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) RH[i] = (T)J.RH[(size_t)i * K + k];
+      for (int i = 0; i < 9; ++i) RH[i] = GP<T>::RH(J)[(size_t)i * K + k];
       // E = s R^T R_H^T: column r is s R^T (row r of R_H)
 #pragma unroll
       for (int r = 0; r < 3; ++r)

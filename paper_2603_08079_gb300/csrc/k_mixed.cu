@@ -14,7 +14,7 @@
 // frames are computed in FP64, so the system being refined is the FP64 one.
 // All body-space work is done in the body's rest frame: with
 // dqb = diag4(R^T) dq, H dq = diag4(R) Hbar dqb (Eq. abd_final).
-#include "mabd_device.cuh"
+#include "mabd_f32.cuh"
 
 namespace mabd {
 
@@ -63,6 +63,19 @@ __device__ __forceinline__ void hbar_apply(const double s[3], double m, double v
   y[11] = mt * x[11];
 }
 
+// joint points and hinge frames in the precision of the products
+template <typename T> struct JP;
+template <> struct JP<double> {
+  __device__ static const double *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1 : J.pb1; }
+  __device__ static const double *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2 : J.pb2; }
+  __device__ static const double *RH(const DevJoints &J) { return J.RH; }
+};
+template <> struct JP<float> {
+  __device__ static const float *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1f : J.pb1f; }
+  __device__ static const float *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2f : J.pb2f; }
+  __device__ static const float *RH(const DevJoints &J) { return J.RHf; }
+};
+
 // g = diag4(R^T) sum_k G_kj^T lam_k for body j: a row with point p and world
 // direction d contributes s [p; 1] (x) (R^T d) lam_r (s = +1 on body a, -1 on b)
 template <typename T>
@@ -80,11 +93,11 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
     T l[5];
 #pragma unroll
     for (int r = 0; r < 5; ++r) l[r] = (T)lam[(size_t)r * K + k];
-    const double *p1 = side == 0 ? J.pa1 : J.pb1;
-    const double *p2 = side == 0 ? J.pa2 : J.pb2;
+    const T *p1 = JP<T>::p1(J, side);
+    const T *p2 = JP<T>::p2(J, side);
     T F1[3], F2[3], P1[3], P2[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) P1[a] = (T)__ldg(p1 + (size_t)a * K + k);
+    for (int a = 0; a < 3; ++a) P1[a] = __ldg(p1 + (size_t)a * K + k);
     if (type == 0) {
       F1[0] = l[0];
       F1[1] = l[1];
@@ -92,12 +105,12 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
     } else {
       T RH[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) RH[i] = (T)J.RH[(size_t)i * K + k];
+      for (int i = 0; i < 9; ++i) RH[i] = JP<T>::RH(J)[(size_t)i * K + k];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         F1[a] = RH[a] * l[0] + RH[3 + a] * l[1] + RH[6 + a] * l[2];
         F2[a] = l[3] * RH[a] + l[4] * RH[6 + a];
-        P2[a] = (T)__ldg(p2 + (size_t)a * K + k);
+        P2[a] = __ldg(p2 + (size_t)a * K + k);
       }
     }
     T f[3];
@@ -152,7 +165,10 @@ __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p,
     for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
   }
 #pragma unroll
-  for (int i = 0; i < 9; ++i) B.R[(size_t)i * M + j] = R[i];
+  for (int i = 0; i < 9; ++i) {
+    B.R[(size_t)i * M + j] = R[i];
+    B.Rf[(size_t)i * M + j] = (float)R[i];
+  }
   if (B.fixed[j]) return;  // no unknowns; its rotation may still orient a hinge
   load12(B.qd, M, j, qd);
   const double s0 = ldg(B.sig + j), s1 = ldg(B.sig + M + j), s2 = ldg(B.sig + 2 * (size_t)M + j);
@@ -225,13 +241,12 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
     if (!(fl & (sd == 0 ? JF_A_FREE : JF_B_FREE))) continue;
     const int i = sd == 0 ? ia : ib;
     float R[9], u[12];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) R[c] = (float)B.R[(size_t)c * M + i];
+    load_Rf(B, i, R);
 #pragma unroll
     for (int c = 0; c < 12; ++c) u[c] = B.ubf[(size_t)c * M + i];
     for (int t = 0; t < npt; ++t) {
-      const double *pp = sd == 0 ? pa[t] : pb[t];
-      const float pf[3] = {(float)pp[0], (float)pp[1], (float)pp[2]};
+      float pf[3];
+      load3f(sd == 0 ? (t == 0 ? J.pa1f : J.pa2f) : (t == 0 ? J.pb1f : J.pb2f), K, k, pf);
       float x[3];
       disp_at(R, u, pf, x);
 #pragma unroll
@@ -277,7 +292,10 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
     J.b[(size_t)r * K + k] = (double)gg[r] + rr * cc[r];
   }
 #pragma unroll
-  for (int i = 0; i < 9; ++i) J.RH[(size_t)i * K + k] = RH[i];
+  for (int i = 0; i < 9; ++i) {
+    J.RH[(size_t)i * K + k] = RH[i];
+    J.RHf[(size_t)i * K + k] = RHf[i];
+  }
 }
 
 // One thread per body, start of a correction sweep.  First sweep:
@@ -308,8 +326,7 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
     for (int i = 0; i < 12; ++i) dq[i] = (double)(uf[i] - w[i]);
   } else {
     float Rf[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Rf[i] = (float)R[i];
+    load_Rf(B, j, Rf);
     gen_force<float>(J, I, j, Rf, J.dlam, gf);
     hinv_apply_t(hf, gf, w);
 #pragma unroll
@@ -364,13 +381,13 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
       float Rf[9], z[12];
       load_R(B.R, M, i, R);
       load12(B.dqb, M, i, x);
-#pragma unroll
-      for (int c = 0; c < 9; ++c) Rf[c] = (float)R[c];
+      load_Rf(B, i, Rf);
 #pragma unroll
       for (int c = 0; c < 12; ++c) z[c] = B.ubf[(size_t)c * M + i];
       for (int t = 0; t < npt; ++t) {
         const double *pp = sd == 0 ? pa[t] : pb[t];
-        const float pf[3] = {(float)pp[0], (float)pp[1], (float)pp[2]};
+        float pf[3];
+        load3f(sd == 0 ? (t == 0 ? J.pa1f : J.pa2f) : (t == 0 ? J.pb1f : J.pb2f), K, k, pf);
         double xd[3];
         float xf[3];
         disp_at(R, x, pp, xd);
@@ -398,12 +415,17 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         v[r] = RH[3 * r] * d[0][0] + RH[3 * r + 1] * d[0][1] + RH[3 * r + 2] * d[0][2];
-        w[r] = (float)RH[3 * r] * e[0][0] + (float)RH[3 * r + 1] * e[0][1] + (float)RH[3 * r + 2] * e[0][2];
       }
+      float RHf[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) RHf[i] = J.RHf[(size_t)i * K + k];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        w[r] = RHf[3 * r] * e[0][0] + RHf[3 * r + 1] * e[0][1] + RHf[3 * r + 2] * e[0][2];
       v[3] = RH[0] * d[1][0] + RH[1] * d[1][1] + RH[2] * d[1][2];
       v[4] = RH[6] * d[1][0] + RH[7] * d[1][1] + RH[8] * d[1][2];
-      w[3] = (float)RH[0] * e[1][0] + (float)RH[1] * e[1][1] + (float)RH[2] * e[1][2];
-      w[4] = (float)RH[6] * e[1][0] + (float)RH[7] * e[1][1] + (float)RH[8] * e[1][2];
+      w[3] = RHf[0] * e[1][0] + RHf[1] * e[1][1] + RHf[2] * e[1][2];
+      w[4] = RHf[6] * e[1][0] + RHf[7] * e[1][1] + RHf[8] * e[1][2];
     }
     for (int r = 0; r < C; ++r) {
       const double res = (p.residual_rhs ? J.c[(size_t)r * K + k] : 0.0) + v[r];
@@ -430,8 +452,7 @@ __global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevI
   double R[9];
   load_R(B.R, M, j, R);
   float Rf[9], hf[16], gf[12], w[12];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) Rf[i] = (float)R[i];
+  load_Rf(B, j, Rf);
   load_hinvf(B, j, hf);
   gen_force<float>(J, I, j, Rf, from_u ? J.lambda : J.dlam, gf);
   hinv_apply_t(hf, gf, w);

@@ -1,0 +1,341 @@
+// FP32 preconditioned conjugate gradients on the dual S x = rhs with
+// S = G H^{-1} G^T (Eq. dual), matrix-free as in the FP64 graph path, for
+// the mixed-precision form: every product in FP32 from the FP32 copies of R,
+// Hbar^{-1}, the joint points and the hinge frames; dot products are summed
+// per thread in FP32 and across threads and blocks in FP64, in a fixed
+// order.  The FP64 residual-correction sweeps of the mixed form call one
+// such solve per sweep (from x = 0), so each solve only has to reduce its
+// own residual by the inner tolerance.
+#include "mabd_f32.cuh"
+
+namespace mabd {
+
+constexpr int P32_THREADS = 256;
+
+__device__ __forceinline__ int pkf(int r, int c) { return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r; }
+
+// z = D^{-1} r with the packed Cholesky factor (reciprocal diagonal)
+__device__ __forceinline__ void dsolve(const float L[15], int C, const float r[5], float z[5]) {
+  float y[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float t = i < C ? r[i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < i; ++q) t -= L[pkf(i, q)] * y[q];
+    y[i] = t * L[pkf(i, i)];
+  }
+#pragma unroll
+  for (int i = 4; i >= 0; --i) {
+    float t = y[i];
+#pragma unroll
+    for (int q = i + 1; q < 5; ++q) t -= L[pkf(q, i)] * z[q];
+    z[i] = i < C ? t * L[pkf(i, i)] : 0.f;
+  }
+}
+
+// block-level sums of two per-thread values into part[blockIdx], part[nb + blockIdx]
+__device__ __forceinline__ void block_partials(double a, double b, double *part, int nb) {
+  __shared__ double s1[128], s2[128];
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s1[0];
+    part[nb + blockIdx.x] = s2[0];
+  }
+}
+
+__device__ __forceinline__ void block_sum2_32(const double *part, int n, int nb, double &a, double &b) {
+  __shared__ double s1[P32_THREADS], s2[P32_THREADS];
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    x += part[i];
+    y += part[nb + i];
+  }
+  s1[threadIdx.x] = x;
+  s2[threadIdx.x] = y;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  a = s1[0];
+  b = s2[0];
+}
+
+// per joint: D_k in FP32, its Cholesky factor; x = 0, r = rhs, z = D^{-1} r, p = 0
+__global__ void __launch_bounds__(128) k_p32_setup(DevBodies B, DevJoints J, DevPCG32 P,
+                                                   const double *rhs, int *status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int K = J.K;
+  float rz = 0.f, rr = 0.f;
+  if (k < K) {
+    const int C = J.type[k] == 0 ? 3 : 5;
+    const uint8_t fl = J.flags[k];
+    float D[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) D[i] = 0.f;
+    for (int side = 0; side < 2; ++side) {
+      if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
+      const int j = side == 0 ? J.ja[k] : J.jb[k];
+      float R[9], h[16], E[5][3], Pt[2][3];
+      int pt[5];
+      load_Rf(B, j, R);
+      load_hf(B, j, h);
+      rows_rest_f(J, k, side, R, E, Pt, pt);
+      float W[5][12], Z[5][12];
+      for (int r = 0; r < C; ++r) {
+        const float *pp = Pt[pt[r]];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          W[r][a] = pp[0] * E[r][a];
+          W[r][3 + a] = pp[1] * E[r][a];
+          W[r][6 + a] = pp[2] * E[r][a];
+          W[r][9 + a] = E[r][a];
+        }
+        hinvf_apply(h, W[r], Z[r]);
+      }
+      for (int r = 0; r < C; ++r)
+        for (int t = 0; t <= r; ++t) {
+          float v = 0.f;
+#pragma unroll
+          for (int a = 0; a < 12; ++a) v += W[r][a] * Z[t][a];
+          D[pkf(r, t)] += v;
+        }
+    }
+    // Cholesky with reciprocal diagonal
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float sum = c < C ? D[pkf(c, c)] : 1.f;
+#pragma unroll
+      for (int q = 0; q < c; ++q) sum -= D[pkf(c, q)] * D[pkf(c, q)];
+      if (!(sum > 0.f)) {
+        if (c < C) ok = false;
+        sum = 1.f;
+      }
+      const float id = rsqrtf(sum);
+      D[pkf(c, c)] = id;
+#pragma unroll
+      for (int r = c + 1; r < 5; ++r) {
+        float t = r < C ? D[pkf(r, c)] : 0.f;
+#pragma unroll
+        for (int q = 0; q < c; ++q) t -= D[pkf(r, q)] * D[pkf(c, q)];
+        D[pkf(r, c)] = t * id;
+      }
+    }
+    if (!ok) set_status(status, ST_NOT_SPD);
+#pragma unroll
+    for (int i = 0; i < 15; ++i) P.Lpre[(size_t)i * K + k] = D[i];
+    float rv[5], z[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      rv[r] = r < C ? (float)rhs[(size_t)r * K + k] : 0.f;
+      const size_t o = (size_t)r * K + k;
+      P.r[o] = rv[r];
+      P.p[o] = 0.f;
+      P.x[o] = 0.f;
+    }
+    dsolve(D, C, rv, z);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      P.z[(size_t)r * K + k] = z[r];
+      rz += rv[r] * z[r];
+      rr += rv[r] * rv[r];
+    }
+  }
+  block_partials((double)rz, (double)rr, P.part, P.nblocks);
+}
+
+__global__ void k_p32_setup_reduce(DevPCG32 P, double rtol) {
+  double rz, rr;
+  block_sum2_32(P.part, P.nblocks, P.nblocks, rz, rr);
+  if (threadIdx.x == 0) {
+    P.scal[0] = rz;
+    P.scal[2] = 0.0;
+    P.scal[3] = rr;
+    P.scal[4] = rr;
+    P.scal[5] = rtol * rtol;
+    P.iter[0] = 0;
+    P.iter[1] = (rr == 0.0) ? 1 : 0;
+  }
+}
+
+// per body: zb_j = Hbar^{-1} sum_rows p_r W_r with p = z + beta p_old
+__global__ void __launch_bounds__(128) k_p32_body(DevBodies B, DevJoints J, DevIncidence I, DevPCG32 P) {
+  if (P.iter[1]) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B.M || B.fixed[j]) return;
+  const int K = J.K, M = B.M;
+  const float beta = (float)P.scal[2];
+  float R[9], g[12];
+  load_Rf(B, j, R);
+#pragma unroll
+  for (int a = 0; a < 12; ++a) g[a] = 0.f;
+  for (int e = I.off[j]; e < I.off[j + 1]; ++e) {
+    const int k = I.joint[e];
+    float E[5][3], Pt[2][3];
+    int pt[5];
+    const int C = rows_rest_f(J, k, I.side[e], R, E, Pt, pt);
+    for (int r = 0; r < C; ++r) {
+      const float pr = P.z[(size_t)r * K + k] + beta * P.p[(size_t)r * K + k];
+      const float *pp = Pt[pt[r]];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float v = pr * E[r][a];
+        g[a] += pp[0] * v;
+        g[3 + a] += pp[1] * v;
+        g[6 + a] += pp[2] * v;
+        g[9 + a] += v;
+      }
+    }
+  }
+  float h[16], z[12];
+  load_hf(B, j, h);
+  hinvf_apply(h, g, z);
+#pragma unroll
+  for (int a = 0; a < 12; ++a) P.zb[(size_t)a * M + j] = z[a];
+}
+
+// per joint: p = z + beta p_old (stored), Sp = sum_bodies W zb, partial p.Sp
+__global__ void __launch_bounds__(128) k_p32_joint_sp(DevBodies B, DevJoints J, DevPCG32 P) {
+  if (P.iter[1]) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int K = J.K;
+  float psp = 0.f;
+  if (k < K) {
+    const int C = J.type[k] == 0 ? 3 : 5;
+    const uint8_t fl = J.flags[k];
+    const float beta = (float)P.scal[2];
+    float pv[5], sp[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      pv[r] = r < C ? P.z[(size_t)r * K + k] + beta * P.p[(size_t)r * K + k] : 0.f;
+      sp[r] = 0.f;
+    }
+    for (int side = 0; side < 2; ++side) {
+      if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
+      const int j = side == 0 ? J.ja[k] : J.jb[k];
+      float R[9], E[5][3], Pt[2][3], zb[12];
+      int pt[5];
+      load_Rf(B, j, R);
+      rows_rest_f(J, k, side, R, E, Pt, pt);
+#pragma unroll
+      for (int a = 0; a < 12; ++a) zb[a] = P.zb[(size_t)a * B.M + j];
+      for (int r = 0; r < C; ++r) {
+        const float *pp = Pt[pt[r]];
+        float v = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          v += E[r][a] * (pp[0] * zb[a] + pp[1] * zb[3 + a] + pp[2] * zb[6 + a] + zb[9 + a]);
+        sp[r] += v;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      P.p[(size_t)r * K + k] = pv[r];
+      P.Sp[(size_t)r * K + k] = sp[r];
+      psp += pv[r] * sp[r];
+    }
+  }
+  block_partials((double)psp, 0.0, P.part, P.nblocks);
+}
+
+__global__ void k_p32_alpha(DevPCG32 P) {
+  if (P.iter[1]) return;
+  double psp, dummy;
+  block_sum2_32(P.part, P.nblocks, P.nblocks, psp, dummy);
+  if (threadIdx.x == 0) {
+    P.scal[6] = psp;
+    P.scal[1] = psp > 0.0 ? P.scal[0] / psp : 0.0;
+  }
+}
+
+// per joint: x += alpha p, r -= alpha Sp, z = D^{-1} r, partials r.z, r.r
+__global__ void __launch_bounds__(128) k_p32_joint_update(DevJoints J, DevPCG32 P) {
+  if (P.iter[1]) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int K = J.K;
+  float rz = 0.f, rr = 0.f;
+  if (k < K) {
+    const int C = J.type[k] == 0 ? 3 : 5;
+    const float alpha = (float)P.scal[1];
+    float rv[5], L[15], z[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const size_t o = (size_t)r * K + k;
+      P.x[o] += alpha * P.p[o];
+      rv[r] = P.r[o] - alpha * P.Sp[o];
+      P.r[o] = rv[r];
+    }
+#pragma unroll
+    for (int i = 0; i < 15; ++i) L[i] = P.Lpre[(size_t)i * K + k];
+    dsolve(L, C, rv, z);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      P.z[(size_t)r * K + k] = z[r];
+      rz += rv[r] * z[r];
+      rr += rv[r] * rv[r];
+    }
+  }
+  block_partials((double)rz, (double)rr, P.part, P.nblocks);
+}
+
+__global__ void k_p32_beta(DevPCG32 P, int max_iters) {
+  if (P.iter[1]) return;
+  double rz, rr;
+  block_sum2_32(P.part, P.nblocks, P.nblocks, rz, rr);
+  if (threadIdx.x == 0) {
+    const double rz_old = P.scal[0];
+    P.scal[2] = rz_old != 0.0 ? rz / rz_old : 0.0;
+    P.scal[0] = rz;
+    P.scal[3] = rr;
+    const int it = P.iter[0] + 1;
+    P.iter[0] = it;
+    if (rr <= P.scal[5] * P.scal[4] || it >= max_iters) P.iter[1] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_p32_finish(DevJoints J, DevPCG32 P, double *out, double *acc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int K = J.K;
+  if (k >= K) return;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const size_t o = (size_t)r * K + k;
+    const double v = (double)P.x[o];
+    out[o] = v;
+    if (acc) acc[o] += v;
+  }
+}
+
+void launch_p32_setup(const DevBodies &B, const DevJoints &J, const DevPCG32 &P, const double *rhs,
+                      double rtol, int *status, cudaStream_t s) {
+  k_p32_setup<<<P.nblocks, 128, 0, s>>>(B, J, P, rhs, status);
+  k_p32_setup_reduce<<<1, P32_THREADS, 0, s>>>(P, rtol);
+}
+
+void launch_p32_iteration(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                          const DevPCG32 &P, int max_iters, cudaStream_t s) {
+  k_p32_body<<<(B.M + 127) / 128, 128, 0, s>>>(B, J, I, P);
+  k_p32_joint_sp<<<P.nblocks, 128, 0, s>>>(B, J, P);
+  k_p32_alpha<<<1, P32_THREADS, 0, s>>>(P);
+  k_p32_joint_update<<<P.nblocks, 128, 0, s>>>(J, P);
+  k_p32_beta<<<1, P32_THREADS, 0, s>>>(P, max_iters);
+}
+
+void launch_p32_finish(const DevJoints &J, const DevPCG32 &P, double *out, double *acc, cudaStream_t s) {
+  if (J.K > 0) k_p32_finish<<<(J.K + 127) / 128, 128, 0, s>>>(J, P, out, acc);
+}
+
+}  // namespace mabd

@@ -55,6 +55,7 @@ struct mabd_ctx {
   std::vector<CRLevel> levels;
   DevTree T{};
   DevPCG P{};
+  DevPCG32 P32{};
   int pcg_last_iters = 0;
   double pcg_last_rel = 0.0;
   int *h_iter = nullptr;     // pinned [2]
@@ -694,9 +695,9 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   }
   if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
   if (solver == MABD_SOLVER_TREE && !is_tree) return MABD_ERR_UNSUPPORTED;
-  if (ctx->cfg.precision == MABD_MIXED && K > 0 && solver != MABD_SOLVER_CHAIN) {
+  if (ctx->cfg.precision == MABD_MIXED && K > 0 && solver == MABD_SOLVER_TREE) {
     std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
-                  "the mixed-precision form is implemented for chain topologies only");
+                  "the mixed-precision form is implemented for chains and for the PCG path only");
     return MABD_ERR_UNSUPPORTED;
   }
   if (solver == MABD_SOLVER_CHAIN) {
@@ -850,12 +851,16 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   J.lambda = dnew<double>(ctx, 5 * (size_t)Kx, ok);
   const bool mixed = ctx->cfg.precision == MABD_MIXED;
   float *dhinvf = nullptr;
+  float *dpf[4] = {nullptr, nullptr, nullptr, nullptr};
   if (mixed) {
     dhinvf = dnew<float>(ctx, HINV_N * (size_t)Mx, ok);
     B.fbar = dnew<double>(ctx, 12 * (size_t)Mx, ok);
     B.dqb = dnew<double>(ctx, 12 * (size_t)Mx, ok);
     B.ubf = dnew<float>(ctx, 12 * (size_t)Mx, ok);
+    B.Rf = dnew<float>(ctx, 9 * (size_t)Mx, ok);
     J.dlam = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+    J.RHf = dnew<float>(ctx, 9 * (size_t)Kx, ok);
+    for (int i = 0; i < 4; ++i) dpf[i] = dnew<float>(ctx, 3 * (size_t)Kx, ok);
   }
   int32_t *dioff = dnew<int32_t>(ctx, (size_t)M + 1, ok);
   int32_t *dij = dnew<int32_t>(ctx, std::max<size_t>(ijoint.size(), 1), ok);
@@ -878,6 +883,16 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     CK(up(dhinvf, hinvf.data(), hinvf.size() * 4));
     CK(cudaMemsetAsync(B.dqb, 0, 12 * (size_t)Mx * 8, ctx->stream));
     CK(cudaMemsetAsync(J.dlam, 0, 5 * (size_t)Kx * 8, ctx->stream));
+    CK(cudaMemsetAsync(J.RHf, 0, 9 * (size_t)Kx * 4, ctx->stream));
+    const std::vector<double> *src[4] = {&pa1, &pb1, &pa2, &pb2};
+    for (int i = 0; i < 4; ++i) {
+      std::vector<float> f(src[i]->begin(), src[i]->end());
+      CK(up(dpf[i], f.data(), f.size() * 4));
+    }
+    J.pa1f = dpf[0];
+    J.pb1f = dpf[1];
+    J.pa2f = dpf[2];
+    J.pb2f = dpf[3];
   }
   CK(up(dfixed, fixed.data(), fixed.size()));
   CK(up(djt, jtype.data(), jtype.size()));
@@ -983,7 +998,29 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     C.jflags = dcf;
     C.islot = dslot;
   }
-  if (solver == MABD_SOLVER_PCG) {
+  if (solver == MABD_SOLVER_PCG && mixed) {
+    DevPCG32 &Q = ctx->P32;
+    Q.nblocks = (K + 127) / 128;
+    Q.r = dnew<float>(ctx, 5 * (size_t)Kx, ok);
+    Q.z = dnew<float>(ctx, 5 * (size_t)Kx, ok);
+    Q.p = dnew<float>(ctx, 5 * (size_t)Kx, ok);
+    Q.Sp = dnew<float>(ctx, 5 * (size_t)Kx, ok);
+    Q.x = dnew<float>(ctx, 5 * (size_t)Kx, ok);
+    Q.zb = dnew<float>(ctx, 12 * (size_t)Mx, ok);
+    Q.Lpre = dnew<float>(ctx, 15 * (size_t)Kx, ok);
+    Q.part = dnew<double>(ctx, 2 * (size_t)std::max(Q.nblocks, 1), ok);
+    Q.scal = dnew<double>(ctx, 8, ok);
+    Q.iter = dnew<int>(ctx, 2, ok);
+    if (!ok) {
+      free_all(ctx);
+      return MABD_ERR_OUT_OF_MEMORY;
+    }
+    if (!ctx->h_iter) {
+      CK(cudaMallocHost((void **)&ctx->h_iter, 2 * sizeof(int)));
+      CK(cudaMallocHost((void **)&ctx->h_scal, 8 * sizeof(double)));
+    }
+  }
+  if (solver == MABD_SOLVER_PCG && !mixed) {
     DevPCG &P = ctx->P;
     P.nblocks = (K + 127) / 128;
     P.r = dnew<double>(ctx, 5 * (size_t)Kx, ok);
@@ -1215,8 +1252,67 @@ static mabd_status pcg_loop(mabd_ctx *ctx, cudaStream_t s, cudaGraphExec_t chunk
   return cuda_fail(ctx, cudaGetLastError());
 }
 
+// FP32 PCG solve of S x = rhs from x = 0 (mixed form, graphs); x goes to out,
+// acc += x when acc is given.  Iterations are enqueued in chunks with a host
+// check of the device's convergence flag between chunks, as for FP64 PCG.
+constexpr double MIXED_INNER_RTOL = 1e-6;
+
+static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, double *out, double *acc) {
+  const double rtol = std::max(ctx->cfg.pcg_rtol, MIXED_INNER_RTOL);
+  run(ctx, "p32_setup", [&] { launch_p32_setup(ctx->B, ctx->J, ctx->P32, rhs, rtol, ctx->d_status, s); });
+  const int max_it = ctx->cfg.pcg_max_iters;
+  int done = 0;
+  for (int launched = 0; launched < max_it && !done; launched += PCG_CHUNK) {
+    for (int i = 0; i < PCG_CHUNK; ++i)
+      run(ctx, "p32_iteration", [&] {
+        launch_p32_iteration(ctx->B, ctx->J, ctx->I, ctx->P32, max_it, s);
+      });
+    CK(cudaMemcpyAsync(ctx->h_iter, ctx->P32.iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    done = ctx->h_iter[1];
+  }
+  CK(cudaMemcpyAsync(ctx->h_scal, ctx->P32.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ctx->h_iter, ctx->P32.iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ctx->pcg_last_iters += ctx->h_iter[0];
+  const double bb = ctx->h_scal[4], rr = ctx->h_scal[3];
+  ctx->pcg_last_rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+  run(ctx, "p32_finish", [&] { launch_p32_finish(ctx->J, ctx->P32, out, acc, s); });
+  return MABD_OK;
+}
+
+// mixed-precision step on a graph: as the chain's (k_mixed.cu) with each dual
+// solve an FP32 PCG solve
+static mabd_status step_mixed_pcg(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
+  const StepParams &p = ctx->sp;
+  ctx->pcg_last_iters = 0;
+  run(ctx, "mx_body_prep", [&] { launch_mx_body_prep(ctx->B, p, ctx->d_status, s); });
+  run(ctx, "mx_joint_prep", [&] { launch_mx_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
+  mabd_status st = p32_solve(ctx, s, ctx->J.b, ctx->J.lambda, nullptr);
+  if (st) return st;
+  const int sweeps = ctx->cfg.refine_steps;
+  for (int it = 0; it < sweeps; ++it) {
+    run(ctx, "mx_res_body", [&] { launch_mx_res_body(ctx->B, ctx->J, ctx->I, p, it == 0, s); });
+    unsigned long long *mb = (maxbits && it == sweeps - 1) ? maxbits + 2 : nullptr;
+    run(ctx, "mx_res_joint", [&] { launch_mx_res_joint(ctx->B, ctx->J, p, mb, s); });
+    st = p32_solve(ctx, s, ctx->J.b, ctx->J.dlam, ctx->J.lambda);
+    if (st) return st;
+  }
+  run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, sweeps == 0, s); });
+  if (maxbits)
+    run(ctx, "residuals", [&] { launch_residuals(ctx->B, ctx->J, p, maxbits, ctx->d_status, s); });
+  return MABD_OK;
+}
+
 static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
   cudaStream_t s = ctx->stream;
+  if (ctx->cfg.precision == MABD_MIXED && ctx->solver == MABD_SOLVER_PCG && ctx->J.K > 0) {
+    mabd_status st = step_mixed_pcg(ctx, maxbits, s);
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && ctx->debug_err != cudaSuccess) e = ctx->debug_err;
+    return cuda_fail(ctx, e);
+  }
   enqueue_pre(ctx, s);
   if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_PCG) {
     mabd_status st = pcg_loop(ctx, s, nullptr);
@@ -1251,6 +1347,10 @@ static void body_step(mabd_ctx *ctx, cudaStream_t s) {
 // builds the graphs once; on any failure graphs stay off for this context
 static bool graphs_ready(mabd_ctx *ctx) {
   if (ctx->graphs_off) return false;
+  if (ctx->cfg.precision == MABD_MIXED && ctx->solver == MABD_SOLVER_PCG && ctx->J.K > 0) {
+    ctx->graphs_off = true;  // host-checked inner solves: launched directly
+    return false;
+  }
   if (ctx->graphs_built) return true;
   bool ok = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) == cudaSuccess &&
@@ -1451,6 +1551,7 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
   if (st) return st;
   static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "mx_body_prep", "mx_joint_prep",
                                 "mx_chain_gram", "mx_res_body", "mx_res_joint", "cr_rhs", "mx_final",
+                                "p32_setup", "p32_iteration", "p32_finish",
                                 "cr_level", "cr_reduce", "cr_combine",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
                                 "pcg_iteration", "backprop", "residuals"};

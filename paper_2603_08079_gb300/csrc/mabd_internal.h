@@ -45,6 +45,7 @@ struct DevBodies {
   double *fbar;         // [12][M] rest-frame rhs of the step (FP64)
   double *dqb;          // [12][M] rest-frame increment diag4(R^T) dq (FP64 accumulator)
   float *ubf;           // [12][M] FP32 Hbar^{-1} of the current rhs (u, then each correction)
+  float *Rf;            // [9][M]  R rounded to FP32 (written with R)
 };
 
 // joint flags
@@ -66,6 +67,9 @@ struct DevJoints {
   double *b;             // [5][K] dual rhs G u + C(q_n)
   double *lambda;        // [5][K] multipliers (rows beyond C_k are zero)
   double *dlam;          // [5][K] mixed form: multiplier correction of a refinement sweep
+  // mixed form: FP32 copies of the joint points and of the hinge frame
+  const float *pa1f, *pb1f, *pa2f, *pb2f;  // [3][K]
+  float *RHf;                              // [9][K]
 };
 
 // body -> incident joints (CSR over internal body order)
@@ -133,6 +137,18 @@ struct DevPCG {
   int nblocks;
 };
 
+// FP32 preconditioned conjugate gradients on the dual (mixed form on graphs):
+// one solve of S x = rhs from x = 0, block-Jacobi preconditioned; vectors [5][K]
+struct DevPCG32 {
+  float *r, *z, *p, *Sp, *x;  // [5][K]
+  float *zb;                  // [12][M]
+  float *Lpre;                // [15][K] Cholesky of D_k, reciprocal diagonal
+  double *part;               // [2][nblocks]
+  double *scal;               // [8]: rz, alpha, beta, rr, bnorm2, rtol2, pSp, spare
+  int *iter;                  // [2]: iterations done, converged flag
+  int nblocks;
+};
+
 struct StepParams {
   double h, inv_h;
   double g[3];
@@ -172,6 +188,14 @@ void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevel &cur, c
 // row and the back-substitution then run as for a factorization
 void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
                    const CRLevel &next, cudaStream_t s);
+
+// FP32 PCG (k_pcg32.cu): setup from rhs (FP64 [5][K]), iterations, and the
+// final copy of x to out (FP64 [5][K]) with acc += x when acc is given
+void launch_p32_setup(const DevBodies &B, const DevJoints &J, const DevPCG32 &P, const double *rhs,
+                      double rtol, int *status, cudaStream_t s);
+void launch_p32_iteration(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
+                          const DevPCG32 &P, int max_iters, cudaStream_t s);
+void launch_p32_finish(const DevJoints &J, const DevPCG32 &P, double *out, double *acc, cudaStream_t s);
 
 // mixed-precision form of the chain step (k_mixed.cu)
 void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s);

@@ -1,8 +1,9 @@
-"""GPU parity of the mixed-precision chain form against the FP64 CPU oracle.
+"""GPU parity of the mixed-precision form against the FP64 CPU oracle.
 
 The mixed form solves the same linearized KKT system as the FP64 form:
-per-body and per-joint products in FP32, the block cyclic reduction of the
-dual in FP64, then FP64 residual-correction sweeps (iterative refinement).
+per-body and per-joint products in FP32, the dual solve (FP64 block cyclic
+reduction on chains, FP32 PCG on graphs), then FP64 residual-correction
+sweeps (iterative refinement).
 Its stated bound is 1e-6 normwise relative error on qdot_{n+1} and lambda
 for one step from an identical state."""
 import numpy as np
@@ -114,7 +115,44 @@ def test_refinement_sweeps_reduce_the_error(ora):
     assert e[0][1] == 0.0 and 0.0 < e[2][1] < e[1][1], e
 
 
+NET_SWEEPS = 1
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 2), (6, 6, 3), (10, 10, 4), (16, 16, 8)])
+def test_mixed_jittered_net(ora, dims):
+    """Closed-loop ball-joint net: FP32 PCG for each dual solve, FP64
+    residual-correction sweeps."""
+    need_gpu()
+    sc = scenes.jittered_net(*dims, seed=4)
+    errs = {}
+    for sweeps in (1, 2):
+        e_qd, e_lam, st = mixed_errors(ora, sc, sc["q"], sc["qdot"], refine_steps=sweeps)
+        errs[sweeps] = (e_qd, e_lam, st["pcg_iters"], st["refine_residual"])
+    assert max(errs[NET_SWEEPS][:2]) <= TOL, errs
+    assert max(errs[2][:2]) < max(errs[1][:2]), errs   # a second sweep still gains
+    q, qd = scenes.perturb_state(sc, seed=1, rot=0.05, vel=0.2)
+    assert_parity(ora, sc, q, qd, tol=TOL, gpu_kw=dict(MIXED, refine_steps=NET_SWEEPS))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mixed_loops_and_graphs(ora, seed):
+    need_gpu()
+    for topo, M in (("loop", 5 + seed), ("graph", 6 + 3 * seed)):
+        sc = scenes.random_small(topo, M, seed=seed)
+        q, qd = scenes.perturb_state(sc, seed=seed, rot=0.2)
+        assert_parity(ora, sc, q, qd, tol=TOL, gpu_kw=dict(MIXED, refine_steps=NET_SWEEPS))
+
+
+def test_mixed_full_size_net(ora):
+    """64x64x16 lattice (65,536 bodies, 4,096 fixed), ~128k ball joints."""
+    need_gpu()
+    sc = scenes.jittered_net(64, 64, 16, seed=4)
+    e_qd, e_lam, st = mixed_errors(ora, sc, sc["q"], sc["qdot"], refine_steps=NET_SWEEPS)
+    assert max(e_qd, e_lam) <= TOL
+
+
 def test_mixed_rejects_other_topologies():
+    """Trees have no mixed form (their elimination is FP64 only)."""
     need_gpu()
     from paper_2603_08079_gb300 import mabd
     sc = scenes.random_small("tree", 12, seed=3)
