@@ -226,6 +226,56 @@ mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M, const mab
                                     int32_t K, const mabd_joint_desc *joints, double *q_out,
                                     double *qdot_out, double *lambda_out);
 
+/* ---- Learned block preconditioner of the mixed-precision PCG path -------
+   The paper has no counterpart: this extends its dual solve for closed loops
+   and irregular networks (Sec. 5.5).  For ball-joint graphs the dual S is
+   normalized by the inverse Cholesky factors C_k of its 3x3 diagonal blocks,
+   S~ = C S C^T with off-diagonal blocks E (joints sharing a free body); a
+   three-layer message-passing network (hidden width 64, BF16 tensor-core
+   products with FP32 accumulation) over that joint graph gives per-joint
+   scales s and per-edge weights alpha, and the preconditioner is
+   M^{-1} = C^T G^T G C with G = diag(s)(I - A), A_kn = alpha_kn E_kn for
+   n < k (symmetric positive definite for any parameters; block Jacobi for
+   alpha = 0, s = 1).  Parameters are a float vector of mabd_lpc_num_params()
+   entries: W1 [16][64], b1 [64], W2 [128][64], b2, W3 [128][64], b3,
+   Wa [64][8], Wb [64][8], wd [64], cd, we [2], ce (row-major). */
+int32_t mabd_lpc_num_params(void);
+
+/* Uses the learned preconditioner in every FP32 PCG solve of the context
+   (params: host array, copied; NULL turns it off).  Needs a prefactored
+   MABD_MIXED context on the PCG path whose joints are all balls, else
+   MABD_ERR_UNSUPPORTED; non-finite parameters give MABD_ERR_INVALID_ARG.
+   A learned solve that misses the tolerance within pcg_max_iters is redone
+   with block Jacobi (counted by mabd_lpc_fallbacks). */
+mabd_status mabd_set_preconditioner(mabd_ctx *ctx, const float *params);
+mabd_status mabd_lpc_fallbacks(mabd_ctx *ctx, int32_t *count);
+
+/* Trainer on the current device: holds captured normalized dual systems of
+   one joint graph and trains the parameters with the library's own forward
+   and backward kernels (Adam). */
+typedef struct mabd_lpc mabd_lpc;
+mabd_status mabd_lpc_create(mabd_lpc **out);
+/* Captures the normalized dual of ctx at its current state as one batch
+   (*batch: its index).  ctx as for mabd_set_preconditioner; every capture
+   must come from contexts with the first capture's joint graph. */
+mabd_status mabd_lpc_capture(mabd_lpc *t, mabd_ctx *ctx, int32_t *batch);
+/* Copies a captured batch out (host arrays): the joint graph's CSR offsets
+   off[K+1] and neighbours nbr[nnz] (per joint sorted by neighbour, then by
+   shared body) and the normalized blocks E[nnz][9] (row-major, rows: the
+   joint, columns: the neighbour). */
+mabd_status mabd_lpc_batch_blocks(mabd_lpc *t, int32_t batch, int32_t *off, int32_t *nbr, float *E);
+/* Loss L = sum_v |G S~ G^T v - v|^2 / (nv 3K) of one batch over nv probe
+   vectors V (host, [nv][K][3] in joint order; NULL: drawn on the device from
+   SplitMix64(seed + i), uniform with unit variance) and, when grad is not
+   NULL, dL/dparams (host, mabd_lpc_num_params floats). */
+mabd_status mabd_lpc_loss_grad(mabd_lpc *t, int32_t batch, const float *params, int32_t nv,
+                               const float *V, uint64_t seed, double *loss, float *grad);
+/* iters Adam steps (learning rate lr, fresh moments) on batches drawn from
+   the seed; params (host) in: start, out: result; losses[iters] if given. */
+mabd_status mabd_lpc_train(mabd_lpc *t, float *params, int32_t iters, float lr, int32_t nv,
+                           uint64_t seed, double *losses);
+mabd_status mabd_lpc_destroy(mabd_lpc *t);
+
 /* Text of the last CUDA failure seen by the context (error name, message and
    the host source line), or "" if none; owned by the context. */
 const char *mabd_error_detail(mabd_ctx *ctx);

@@ -33,6 +33,13 @@ __device__ __forceinline__ void dsolve(const float L[15], int C, const float r[5
   }
 }
 
+// t_k = C_k r_k (rows 0-2) with C packed lower (c00 c10 c11 c20 c21 c22)
+__device__ __forceinline__ void ctimes(const float *Cp, const float r[5], float *t, int K, int k) {
+  t[k] = Cp[0] * r[0];
+  t[(size_t)K + k] = Cp[1] * r[0] + Cp[2] * r[1];
+  t[2 * (size_t)K + k] = Cp[3] * r[0] + Cp[4] * r[1] + Cp[5] * r[2];
+}
+
 // block-level sums of two per-thread values into part[blockIdx], part[nb + blockIdx]
 __device__ __forceinline__ void block_partials(double a, double b, double *part, int nb) {
   __shared__ double s1[128], s2[128];
@@ -146,12 +153,18 @@ __global__ void __launch_bounds__(128) k_p32_setup(DevBodies B, DevJoints J, Dev
       P.p[o] = 0.f;
       P.x[o] = 0.f;
     }
-    dsolve(D, C, rv, z);
+    if (P.t) {
+      ctimes(P.Cl + (size_t)6 * k, rv, P.t, K, k);
 #pragma unroll
-    for (int r = 0; r < 5; ++r) {
-      P.z[(size_t)r * K + k] = z[r];
-      rz += rv[r] * z[r];
-      rr += rv[r] * rv[r];
+      for (int r = 0; r < 5; ++r) rr += rv[r] * rv[r];
+    } else {
+      dsolve(D, C, rv, z);
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        P.z[(size_t)r * K + k] = z[r];
+        rz += rv[r] * z[r];
+        rr += rv[r] * rv[r];
+      }
     }
   }
   block_partials((double)rz, (double)rr, P.part, P.nblocks);
@@ -278,14 +291,20 @@ __global__ void __launch_bounds__(128) k_p32_joint_update(DevJoints J, DevPCG32 
       rv[r] = P.r[o] - alpha * P.Sp[o];
       P.r[o] = rv[r];
     }
+    if (P.t) {
+      ctimes(P.Cl + (size_t)6 * k, rv, P.t, K, k);
 #pragma unroll
-    for (int i = 0; i < 15; ++i) L[i] = P.Lpre[(size_t)i * K + k];
-    dsolve(L, C, rv, z);
+      for (int r = 0; r < 5; ++r) rr += rv[r] * rv[r];
+    } else {
 #pragma unroll
-    for (int r = 0; r < 5; ++r) {
-      P.z[(size_t)r * K + k] = z[r];
-      rz += rv[r] * z[r];
-      rr += rv[r] * rv[r];
+      for (int i = 0; i < 15; ++i) L[i] = P.Lpre[(size_t)i * K + k];
+      dsolve(L, C, rv, z);
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        P.z[(size_t)r * K + k] = z[r];
+        rz += rv[r] * z[r];
+        rr += rv[r] * rv[r];
+      }
     }
   }
   block_partials((double)rz, (double)rr, P.part, P.nblocks);
@@ -320,17 +339,20 @@ __global__ void __launch_bounds__(128) k_p32_finish(DevJoints J, DevPCG32 P, dou
 }
 
 void launch_p32_setup(const DevBodies &B, const DevJoints &J, const DevPCG32 &P, const double *rhs,
-                      double rtol, int *status, cudaStream_t s) {
+                      double rtol, int *status, cudaStream_t s, const LpcGraph *lg, const LpcAct *la) {
   k_p32_setup<<<P.nblocks, 128, 0, s>>>(B, J, P, rhs, status);
+  if (P.t) launch_lpc_apply(*lg, *la, P.t, P.y, P.r, P.z, P.part, P.nblocks, s, nullptr);
   k_p32_setup_reduce<<<1, P32_THREADS, 0, s>>>(P, rtol);
 }
 
 void launch_p32_iteration(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
-                          const DevPCG32 &P, int max_iters, cudaStream_t s) {
+                          const DevPCG32 &P, int max_iters, cudaStream_t s, const LpcGraph *lg,
+                          const LpcAct *la) {
   k_p32_body<<<(B.M + 127) / 128, 128, 0, s>>>(B, J, I, P);
   k_p32_joint_sp<<<P.nblocks, 128, 0, s>>>(B, J, P);
   k_p32_alpha<<<1, P32_THREADS, 0, s>>>(P);
   k_p32_joint_update<<<P.nblocks, 128, 0, s>>>(J, P);
+  if (P.t) launch_lpc_apply(*lg, *la, P.t, P.y, P.r, P.z, P.part, P.nblocks, s, P.iter);
   k_p32_beta<<<1, P32_THREADS, 0, s>>>(P, max_iters);
 }
 

@@ -56,6 +56,12 @@ struct mabd_ctx {
   DevTree T{};
   DevPCG P{};
   DevPCG32 P32{};
+  // learned preconditioner of the mixed PCG (joint graph, activations, weights)
+  bool lpc_graph = false, lpc_on = false;
+  LpcGraph lg{};
+  LpcAct la{};
+  LpcNet ln{};
+  int lpc_fallbacks = 0;
   int pcg_last_iters = 0;
   double pcg_last_rel = 0.0;
   int *h_iter = nullptr;     // pinned [2]
@@ -1257,16 +1263,39 @@ static mabd_status pcg_loop(mabd_ctx *ctx, cudaStream_t s, cudaGraphExec_t chunk
 // check of the device's convergence flag between chunks, as for FP64 PCG.
 constexpr double MIXED_INNER_RTOL = 1e-6;
 
-static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, double *out, double *acc) {
+static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, double *out, double *acc,
+                             bool learned);
+
+// one FP32 PCG solve with the learned preconditioner when it is on; a learned
+// solve that does not reach the tolerance within pcg_max_iters is repeated
+// with block Jacobi (the fallback), which is then the solve that counts
+static mabd_status p32_solve_any(mabd_ctx *ctx, cudaStream_t s, const double *rhs, double *out,
+                                 double *acc) {
+  if (!ctx->lpc_on) return p32_solve(ctx, s, rhs, out, acc, false);
+  mabd_status st = p32_solve(ctx, s, rhs, out, nullptr, true);
+  if (st) return st;
+  const double bb = ctx->h_scal[4], rr = ctx->h_scal[3], tol2 = ctx->h_scal[5];
+  if (std::isfinite(rr) && rr <= tol2 * bb) {
+    if (acc) run(ctx, "p32_finish", [&] { launch_p32_finish(ctx->J, ctx->P32, out, acc, s); });
+    return MABD_OK;
+  }
+  ++ctx->lpc_fallbacks;
+  return p32_solve(ctx, s, rhs, out, acc, false);
+}
+
+static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, double *out, double *acc,
+                             bool learned) {
   const double rtol = std::max(ctx->cfg.pcg_rtol, MIXED_INNER_RTOL);
-  run(ctx, "p32_setup", [&] { launch_p32_setup(ctx->B, ctx->J, ctx->P32, rhs, rtol, ctx->d_status, s); });
+  DevPCG32 P = ctx->P32;
+  if (!learned) P.t = nullptr;
+  const LpcGraph *lg = learned ? &ctx->lg : nullptr;
+  const LpcAct *la = learned ? &ctx->la : nullptr;
+  run(ctx, "p32_setup", [&] { launch_p32_setup(ctx->B, ctx->J, P, rhs, rtol, ctx->d_status, s, lg, la); });
   const int max_it = ctx->cfg.pcg_max_iters;
   int done = 0;
   for (int launched = 0; launched < max_it && !done; launched += PCG_CHUNK) {
     for (int i = 0; i < PCG_CHUNK; ++i)
-      run(ctx, "p32_iteration", [&] {
-        launch_p32_iteration(ctx->B, ctx->J, ctx->I, ctx->P32, max_it, s);
-      });
+      run(ctx, "p32_iteration", [&] { launch_p32_iteration(ctx->B, ctx->J, ctx->I, P, max_it, s, lg, la); });
     CK(cudaMemcpyAsync(ctx->h_iter, ctx->P32.iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     done = ctx->h_iter[1];
@@ -1277,7 +1306,7 @@ static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, d
   ctx->pcg_last_iters += ctx->h_iter[0];
   const double bb = ctx->h_scal[4], rr = ctx->h_scal[3];
   ctx->pcg_last_rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
-  run(ctx, "p32_finish", [&] { launch_p32_finish(ctx->J, ctx->P32, out, acc, s); });
+  run(ctx, "p32_finish", [&] { launch_p32_finish(ctx->J, P, out, learned ? nullptr : acc, s); });
   return MABD_OK;
 }
 
@@ -1288,14 +1317,18 @@ static mabd_status step_mixed_pcg(mabd_ctx *ctx, unsigned long long *maxbits, cu
   ctx->pcg_last_iters = 0;
   run(ctx, "mx_body_prep", [&] { launch_mx_body_prep(ctx->B, p, ctx->d_status, s); });
   run(ctx, "mx_joint_prep", [&] { launch_mx_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
-  mabd_status st = p32_solve(ctx, s, ctx->J.b, ctx->J.lambda, nullptr);
+  if (ctx->lpc_on) {
+    run(ctx, "lpc_blocks", [&] { launch_lpc_blocks(ctx->B, ctx->J, ctx->lg, ctx->la, ctx->d_status, s); });
+    run(ctx, "lpc_forward", [&] { launch_lpc_forward(ctx->lg, ctx->ln, ctx->la, false, s); });
+  }
+  mabd_status st = p32_solve_any(ctx, s, ctx->J.b, ctx->J.lambda, nullptr);
   if (st) return st;
   const int sweeps = ctx->cfg.refine_steps;
   for (int it = 0; it < sweeps; ++it) {
     run(ctx, "mx_res_body", [&] { launch_mx_res_body(ctx->B, ctx->J, ctx->I, p, it == 0, s); });
     unsigned long long *mb = (maxbits && it == sweeps - 1) ? maxbits + 2 : nullptr;
     run(ctx, "mx_res_joint", [&] { launch_mx_res_joint(ctx->B, ctx->J, p, mb, s); });
-    st = p32_solve(ctx, s, ctx->J.b, ctx->J.dlam, ctx->J.lambda);
+    st = p32_solve_any(ctx, s, ctx->J.b, ctx->J.dlam, ctx->J.lambda);
     if (st) return st;
   }
   run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, sweeps == 0, s); });
@@ -1551,7 +1584,7 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
   if (st) return st;
   static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "mx_body_prep", "mx_joint_prep",
                                 "mx_chain_gram", "mx_res_body", "mx_res_joint", "cr_rhs", "mx_final",
-                                "p32_setup", "p32_iteration", "p32_finish",
+                                "p32_setup", "p32_iteration", "p32_finish", "lpc_blocks", "lpc_forward",
                                 "cr_level", "cr_reduce", "cr_combine",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
                                 "pcg_iteration", "backprop", "residuals"};
@@ -1573,6 +1606,421 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
 const char *mabd_error_detail(mabd_ctx *ctx) {
   if (!ctx) return "";
   return ctx->err_detail;
+}
+
+// --------------------------------------------------------------------------
+// learned preconditioner
+// --------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+// joint graph of a mixed-precision PCG context (ball joints only): joints
+// sharing a free body are adjacent; entries sorted by (neighbour, body)
+mabd_status build_lpc_graph(mabd_ctx *ctx) {
+  if (ctx->lpc_graph) return MABD_OK;
+  if (!ctx->frozen) return MABD_ERR_BAD_STATE;
+  if (ctx->cfg.precision != MABD_MIXED || ctx->solver != MABD_SOLVER_PCG || ctx->J.K <= 0) {
+    std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
+                  "the learned preconditioner needs the mixed-precision PCG path");
+    return MABD_ERR_UNSUPPORTED;
+  }
+  const int K = ctx->J.K, M = ctx->B.M;
+  struct Inc { int k, side; };
+  std::vector<std::vector<Inc>> inc(M);
+  std::vector<uint8_t> ones(K, 0);
+  for (int k = 0; k < K; ++k) {
+    const auto &d = ctx->joints[ctx->joint_of_internal[k]];
+    if (d.type != MABD_JOINT_BALL) {
+      std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
+                    "the learned preconditioner supports ball joints only");
+      return MABD_ERR_UNSUPPORTED;
+    }
+    int nfree = 0;
+    if (!ctx->bodies[d.body_a].fixed) {
+      inc[ctx->internal_of_body[d.body_a]].push_back({k, 0});
+      ++nfree;
+    }
+    if (d.body_b >= 0 && !ctx->bodies[d.body_b].fixed) {
+      inc[ctx->internal_of_body[d.body_b]].push_back({k, 1});
+      ++nfree;
+    }
+    ones[k] = nfree == 1 ? 1 : 0;
+  }
+  struct Ent { int n, body; int8_t sk, sn; };
+  std::vector<std::vector<Ent>> ent(K);
+  for (int j = 0; j < M; ++j)
+    for (const Inc &a : inc[j])
+      for (const Inc &b : inc[j])
+        if (a.k != b.k) ent[a.k].push_back({b.k, j, (int8_t)a.side, (int8_t)b.side});
+  std::vector<int32_t> off(K + 1, 0), nbr, body, rev;
+  std::vector<int8_t> sk, sn;
+  for (int k = 0; k < K; ++k) {
+    auto &v = ent[k];
+    std::sort(v.begin(), v.end(), [](const Ent &x, const Ent &y) {
+      return x.n != y.n ? x.n < y.n : x.body < y.body;
+    });
+    off[k + 1] = off[k] + (int)v.size();
+    for (const Ent &e : v) {
+      nbr.push_back(e.n);
+      body.push_back(e.body);
+      sk.push_back(e.sk);
+      sn.push_back(e.sn);
+    }
+  }
+  const int nnz = off[K];
+  rev.assign(nnz, -1);
+  for (int k = 0; k < K; ++k)
+    for (int e = off[k]; e < off[k + 1]; ++e) {
+      const int n = nbr[e];
+      for (int f = off[n]; f < off[n + 1]; ++f)
+        if (nbr[f] == k && body[f] == body[e]) {
+          rev[e] = f;
+          break;
+        }
+    }
+  bool ok = true;
+  const size_t nz = std::max(nnz, 1);
+  int32_t *doff = dnew<int32_t>(ctx, K + 1, ok), *dnbr = dnew<int32_t>(ctx, nz, ok);
+  int32_t *dbody = dnew<int32_t>(ctx, nz, ok), *drev = dnew<int32_t>(ctx, nz, ok);
+  int8_t *dsk = dnew<int8_t>(ctx, nz, ok), *dsn = dnew<int8_t>(ctx, nz, ok);
+  uint8_t *dones = dnew<uint8_t>(ctx, K, ok);
+  LpcAct &A = ctx->la;
+  A.E = dnew<float>(ctx, 9 * nz, ok);
+  A.C = dnew<float>(ctx, 6 * (size_t)K, ok);
+  A.x = dnew<float>(ctx, LPC_F * (size_t)K, ok);
+  A.h1 = dnew<float>(ctx, LPC_H * (size_t)K, ok);
+  A.h2 = dnew<float>(ctx, LPC_H * (size_t)K, ok);
+  A.h3 = dnew<float>(ctx, LPC_H * (size_t)K, ok);
+  A.a = dnew<float>(ctx, LPC_R * (size_t)K, ok);
+  A.b = dnew<float>(ctx, LPC_R * (size_t)K, ok);
+  A.s = dnew<float>(ctx, K, ok);
+  A.alpha = dnew<float>(ctx, nz, ok);
+  ctx->P32.t = dnew<float>(ctx, 5 * (size_t)K, ok);
+  ctx->P32.y = dnew<float>(ctx, 5 * (size_t)K, ok);
+  float *dP = dnew<float>(ctx, LPC_NPARAM, ok);
+  uint16_t *w1 = dnew<uint16_t>(ctx, 2 * LPC_F * LPC_H, ok), *w2 = dnew<uint16_t>(ctx, 2 * LPC_H * LPC_H, ok),
+           *w3 = dnew<uint16_t>(ctx, 2 * LPC_H * LPC_H, ok);
+  if (!ok) return MABD_ERR_OUT_OF_MEMORY;
+  auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  };
+  CK(up(doff, off.data(), off.size() * 4));
+  CK(up(dnbr, nbr.data(), nbr.size() * 4));
+  CK(up(dbody, body.data(), body.size() * 4));
+  CK(up(drev, rev.data(), rev.size() * 4));
+  CK(up(dsk, sk.data(), sk.size()));
+  CK(up(dsn, sn.data(), sn.size()));
+  CK(up(dones, ones.data(), ones.size()));
+  CK(cudaStreamSynchronize(ctx->stream));
+  LpcGraph &G = ctx->lg;
+  G.K = K;
+  G.nnz = nnz;
+  G.off = doff;
+  G.nbr = dnbr;
+  G.body = dbody;
+  G.sk = dsk;
+  G.sn = dsn;
+  G.rev = drev;
+  G.onesided = dones;
+  ctx->P32.Cl = A.C;
+  ctx->ln.P = dP;
+  ctx->ln.W1t = w1;
+  ctx->ln.W2t = w2;
+  ctx->ln.W3t = w3;
+  ctx->lpc_graph = true;
+  return MABD_OK;
+}
+
+}  // namespace
+
+// trainer: captured batches of normalized dual systems of one joint graph
+struct mabd_lpc {
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocs;
+  bool have_graph = false;
+  LpcGraph g{};
+  std::vector<float *> batches;  // [nnz][9] each
+  LpcAct act{};
+  LpcNet net{};
+  float *P = nullptr, *m = nullptr, *v = nullptr;
+  LpcTrainWork W{};
+  float *V = nullptr;
+  double *losses = nullptr;
+  int losses_cap = 0;
+  int nv_cap = 0;
+};
+
+namespace {
+
+template <typename T>
+T *tnew(mabd_lpc *t, size_t n, bool &ok) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    ok = false;
+    return nullptr;
+  }
+  t->allocs.push_back(p);
+  return (T *)p;
+}
+
+mabd_status lpc_alloc_work(mabd_lpc *t, int nv) {
+  if (nv <= t->nv_cap) return MABD_OK;
+  const size_t K = t->g.K, n3 = (size_t)nv * K * 3;
+  bool ok = true;
+  LpcTrainWork &W = t->W;
+  t->V = tnew<float>(t, n3, ok);
+  W.t = tnew<float>(t, n3, ok);
+  W.u = tnew<float>(t, n3, ok);
+  W.w = tnew<float>(t, n3, ok);
+  W.q = tnew<float>(t, n3, ok);
+  W.gw = tnew<float>(t, n3, ok);
+  W.gu = tnew<float>(t, n3, ok);
+  if (!ok) return MABD_ERR_OUT_OF_MEMORY;
+  t->nv_cap = nv;
+  return MABD_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// forward with kept activations and the loss (and gradient) of one batch
+mabd_status lpc_eval(mabd_lpc *t, int batch, int nv, const float *V, uint64_t seed, bool grad,
+                     double *dloss) {
+  cudaStream_t s = t->stream;
+  mabd_status st = lpc_alloc_work(t, nv);
+  if (st) return st;
+  LpcAct A = t->act;
+  A.E = t->batches[batch];
+  launch_lpc_weights(t->P, (uint16_t *)t->net.W1t, (uint16_t *)t->net.W2t, (uint16_t *)t->net.W3t, s);
+  launch_lpc_forward(t->g, t->net, A, true, s);
+  const size_t n3 = (size_t)nv * t->g.K * 3;
+  if (V) {
+    if (cudaMemcpyAsync(t->V, V, n3 * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return MABD_ERR_CUDA;
+  } else {
+    launch_lpc_probe(t->V, n3, seed, s);
+  }
+  LpcTrainWork W = t->W;
+  W.nv = nv;
+  W.V = t->V;
+  W.loss = dloss;
+  launch_lpc_loss_grad(t->g, A, t->net, W, grad, s);
+  return cudaGetLastError() == cudaSuccess ? MABD_OK : MABD_ERR_CUDA;
+}
+
+mabd_status lpc_losses(mabd_lpc *t, int n) {
+  if (n <= t->losses_cap) return MABD_OK;
+  bool ok = true;
+  t->losses = tnew<double>(t, n, ok);
+  if (!ok) return MABD_ERR_OUT_OF_MEMORY;
+  t->losses_cap = n;
+  return MABD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t mabd_lpc_num_params(void) { return LPC_NPARAM; }
+
+mabd_status mabd_set_preconditioner(mabd_ctx *ctx, const float *params) {
+  dbg_pending("enter mabd_set_preconditioner");
+  if (!ctx) return MABD_ERR_INVALID_ARG;
+  if (ctx->cuda_failed) return MABD_ERR_CUDA;
+  if (!params) {
+    ctx->lpc_on = false;
+    return MABD_OK;
+  }
+  for (int i = 0; i < LPC_NPARAM; ++i)
+    if (!std::isfinite(params[i])) return MABD_ERR_INVALID_ARG;
+  mabd_status st = build_lpc_graph(ctx);
+  if (st) return st;
+  CK(cudaMemcpyAsync((void *)ctx->ln.P, params, sizeof(float) * LPC_NPARAM, cudaMemcpyHostToDevice, ctx->stream));
+  launch_lpc_weights(ctx->ln.P, (uint16_t *)ctx->ln.W1t, (uint16_t *)ctx->ln.W2t, (uint16_t *)ctx->ln.W3t,
+                     ctx->stream);
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->lpc_on = true;
+  return MABD_OK;
+}
+
+mabd_status mabd_lpc_fallbacks(mabd_ctx *ctx, int32_t *count) {
+  if (!ctx || !count) return MABD_ERR_INVALID_ARG;
+  *count = ctx->lpc_fallbacks;
+  return MABD_OK;
+}
+
+mabd_status mabd_lpc_create(mabd_lpc **out) {
+  if (!out) return MABD_ERR_INVALID_ARG;
+  *out = nullptr;
+  mabd_lpc *t = new (std::nothrow) mabd_lpc();
+  if (!t) return MABD_ERR_OUT_OF_MEMORY;
+  if (cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete t;
+    return MABD_ERR_CUDA;
+  }
+  *out = t;
+  return MABD_OK;
+}
+
+mabd_status mabd_lpc_destroy(mabd_lpc *t) {
+  if (!t) return MABD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(t->stream);
+  for (void *p : t->allocs) cudaFree(p);
+  cudaStreamDestroy(t->stream);
+  delete t;
+  return MABD_OK;
+}
+
+mabd_status mabd_lpc_capture(mabd_lpc *t, mabd_ctx *ctx, int32_t *batch) {
+  dbg_pending("enter mabd_lpc_capture");
+  if (!t || !ctx) return MABD_ERR_INVALID_ARG;
+  if (ctx->cuda_failed) return MABD_ERR_CUDA;
+  mabd_status st = build_lpc_graph(ctx);
+  if (st) return st;
+  cudaStream_t s = ctx->stream;
+  launch_mx_body_prep(ctx->B, ctx->sp, ctx->d_status, s);
+  launch_lpc_blocks(ctx->B, ctx->J, ctx->lg, ctx->la, ctx->d_status, s);
+  CK(cudaStreamSynchronize(s));
+  st = read_status(ctx);
+  if (st) return st;
+  const LpcGraph &G = ctx->lg;
+  bool ok = true;
+  if (!t->have_graph) {
+    const size_t K = G.K, nz = std::max(G.nnz, 1);
+    LpcGraph g = G;
+    int32_t *off = tnew<int32_t>(t, K + 1, ok), *nbr = tnew<int32_t>(t, nz, ok), *body = tnew<int32_t>(t, nz, ok),
+            *rev = tnew<int32_t>(t, nz, ok);
+    int8_t *sk = tnew<int8_t>(t, nz, ok), *sn = tnew<int8_t>(t, nz, ok);
+    uint8_t *ones = tnew<uint8_t>(t, K, ok);
+    LpcAct &A = t->act;
+    A.x = tnew<float>(t, LPC_F * K, ok);
+    A.A1 = tnew<float>(t, 2 * LPC_F * K, ok);
+    A.A2 = tnew<float>(t, 2 * LPC_H * K, ok);
+    A.A3 = tnew<float>(t, 2 * LPC_H * K, ok);
+    A.pre1 = tnew<float>(t, LPC_H * K, ok);
+    A.pre2 = tnew<float>(t, LPC_H * K, ok);
+    A.pre3 = tnew<float>(t, LPC_H * K, ok);
+    A.h1 = tnew<float>(t, LPC_H * K, ok);
+    A.h2 = tnew<float>(t, LPC_H * K, ok);
+    A.h3 = tnew<float>(t, LPC_H * K, ok);
+    A.a = tnew<float>(t, LPC_R * K, ok);
+    A.b = tnew<float>(t, LPC_R * K, ok);
+    A.s = tnew<float>(t, K, ok);
+    A.alpha = tnew<float>(t, nz, ok);
+    t->P = tnew<float>(t, LPC_NPARAM, ok);
+    t->m = tnew<float>(t, LPC_NPARAM, ok);
+    t->v = tnew<float>(t, LPC_NPARAM, ok);
+    t->net.P = t->P;
+    t->net.W1t = tnew<uint16_t>(t, 2 * LPC_F * LPC_H, ok);
+    t->net.W2t = tnew<uint16_t>(t, 2 * LPC_H * LPC_H, ok);
+    t->net.W3t = tnew<uint16_t>(t, 2 * LPC_H * LPC_H, ok);
+    LpcTrainWork &W = t->W;
+    W.dalpha = tnew<float>(t, nz, ok);
+    W.ds = tnew<float>(t, K, ok);
+    W.dh = tnew<float>(t, LPC_H * K, ok);
+    W.dh2 = tnew<float>(t, LPC_H * K, ok);
+    W.dA = tnew<float>(t, 2 * LPC_H * K, ok);
+    W.dpre = tnew<float>(t, LPC_H * K, ok);
+    W.grad = tnew<float>(t, LPC_NPARAM, ok);
+    W.part = tnew<double>(t, (K + 127) / 128 + 1, ok);
+    if (!ok) return MABD_ERR_OUT_OF_MEMORY;
+    CK(cudaMemcpyAsync(off, G.off, (K + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(nbr, G.nbr, nz * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(body, G.body, nz * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(rev, G.rev, nz * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(sk, G.sk, nz, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(sn, G.sn, nz, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ones, G.onesided, K, cudaMemcpyDeviceToDevice, s));
+    g.off = off;
+    g.nbr = nbr;
+    g.body = body;
+    g.rev = rev;
+    g.sk = sk;
+    g.sn = sn;
+    g.onesided = ones;
+    t->g = g;
+    t->have_graph = true;
+  } else if (t->g.K != G.K || t->g.nnz != G.nnz) {
+    return MABD_ERR_INVALID_ARG;  // every batch has the first context's joint graph
+  }
+  float *E = tnew<float>(t, 9 * (size_t)std::max(G.nnz, 1), ok);
+  if (!ok) return MABD_ERR_OUT_OF_MEMORY;
+  CK(cudaMemcpyAsync(E, ctx->la.E, 9 * (size_t)G.nnz * 4, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  t->batches.push_back(E);
+  if (batch) *batch = (int32_t)t->batches.size() - 1;
+  return MABD_OK;
+}
+
+mabd_status mabd_lpc_batch_blocks(mabd_lpc *t, int32_t batch, int32_t *off, int32_t *nbr, float *E) {
+  if (!t || !off || !nbr || !E || !t->have_graph || batch < 0 || batch >= (int)t->batches.size())
+    return MABD_ERR_INVALID_ARG;
+  const LpcGraph &g = t->g;
+  if (cudaMemcpyAsync(off, g.off, 4 * ((size_t)g.K + 1), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
+      cudaMemcpyAsync(nbr, g.nbr, 4 * (size_t)g.nnz, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
+      cudaMemcpyAsync(E, t->batches[batch], 36 * (size_t)g.nnz, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
+      cudaStreamSynchronize(t->stream) != cudaSuccess)
+    return MABD_ERR_CUDA;
+  return MABD_OK;
+}
+
+mabd_status mabd_lpc_loss_grad(mabd_lpc *t, int32_t batch, const float *params, int32_t nv, const float *V,
+                               uint64_t seed, double *loss, float *grad) {
+  if (!t || !params || !loss || nv < 1 || !t->have_graph || batch < 0 || batch >= (int)t->batches.size())
+    return MABD_ERR_INVALID_ARG;
+  mabd_status st = lpc_losses(t, 1);
+  if (st) return st;
+  if (cudaMemcpyAsync(t->P, params, sizeof(float) * LPC_NPARAM, cudaMemcpyHostToDevice, t->stream) != cudaSuccess)
+    return MABD_ERR_CUDA;
+  st = lpc_eval(t, batch, nv, V, seed, grad != nullptr, t->losses);
+  if (st) return st;
+  double l = 0.0;
+  if (cudaMemcpyAsync(&l, t->losses, 8, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess) return MABD_ERR_CUDA;
+  if (grad && cudaMemcpyAsync(grad, t->W.grad, sizeof(float) * LPC_NPARAM, cudaMemcpyDeviceToHost, t->stream) !=
+                  cudaSuccess)
+    return MABD_ERR_CUDA;
+  if (cudaStreamSynchronize(t->stream) != cudaSuccess) return MABD_ERR_CUDA;
+  *loss = l / ((double)nv * 3.0 * t->g.K);
+  return MABD_OK;
+}
+
+mabd_status mabd_lpc_train(mabd_lpc *t, float *params, int32_t iters, float lr, int32_t nv, uint64_t seed,
+                           double *losses) {
+  if (!t || !params || iters < 0 || nv < 1 || !(lr > 0.f) || !t->have_graph || t->batches.empty())
+    return MABD_ERR_INVALID_ARG;
+  cudaStream_t s = t->stream;
+  mabd_status st = lpc_losses(t, std::max(iters, 1));
+  if (st) return st;
+  if (cudaMemcpyAsync(t->P, params, sizeof(float) * LPC_NPARAM, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(t->m, 0, sizeof(float) * LPC_NPARAM, s) != cudaSuccess ||
+      cudaMemsetAsync(t->v, 0, sizeof(float) * LPC_NPARAM, s) != cudaSuccess)
+    return MABD_ERR_CUDA;
+  const int nb = (int)t->batches.size();
+  uint64_t x = seed;
+  for (int it = 0; it < iters; ++it) {
+    // batch order from a SplitMix64 stream of the seed
+    x += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    const int b = (int)(z % (uint64_t)nb);
+    st = lpc_eval(t, b, nv, nullptr, z, true, t->losses + it);
+    if (st) return st;
+    launch_lpc_adam(t->P, t->W.grad, t->m, t->v, lr, it + 1, s);
+  }
+  std::vector<double> hl(std::max(iters, 1));
+  if (cudaMemcpyAsync(params, t->P, sizeof(float) * LPC_NPARAM, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hl.data(), t->losses, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MABD_ERR_CUDA;
+  if (losses)
+    for (int i = 0; i < iters; ++i) losses[i] = hl[i] / ((double)nv * 3.0 * t->g.K);
+  return MABD_OK;
 }
 
 mabd_status mabd_destroy(mabd_ctx *ctx) {

@@ -212,6 +212,27 @@ __device__ __forceinline__ void hinv_apply(const double h[16], const double v[12
   y[11] = h[0] * v[11];
 }
 
+// Mbar(p, q) = ([p;1] (x) I)^T Hbar^{-1} ([q;1] (x) I), the 3x3 compliance between
+// two rest-frame points of a body, from the structured inverse h[16]: translation h[0]; the 3x3
+// block X of A's diagonal entries (h[1..6]); transpose pairs
+// (A(1,0), A(0,1)) h[7..9], (A(2,0), A(0,2)) h[10..12], (A(2,1), A(1,2)) h[13..15].
+template <typename T>
+__device__ __forceinline__ void mbar(const T h[16], const T p[3], const T q[3], T Mb[3][3]) {
+  const T p0q0 = p[0] * q[0], p1q1 = p[1] * q[1], p2q2 = p[2] * q[2];
+  Mb[0][0] = h[0] + h[1] * p0q0 + h[9] * p1q1 + h[12] * p2q2;
+  Mb[1][1] = h[0] + h[4] * p1q1 + h[7] * p0q0 + h[15] * p2q2;
+  Mb[2][2] = h[0] + h[6] * p2q2 + h[10] * p0q0 + h[13] * p1q1;
+  const T p0q1 = p[0] * q[1], p1q0 = p[1] * q[0];
+  const T p0q2 = p[0] * q[2], p2q0 = p[2] * q[0];
+  const T p1q2 = p[1] * q[2], p2q1 = p[2] * q[1];
+  Mb[0][1] = h[2] * p0q1 + h[8] * p1q0;
+  Mb[1][0] = h[2] * p1q0 + h[8] * p0q1;
+  Mb[0][2] = h[3] * p0q2 + h[11] * p2q0;
+  Mb[2][0] = h[3] * p2q0 + h[11] * p0q2;
+  Mb[1][2] = h[5] * p1q2 + h[14] * p2q1;
+  Mb[2][1] = h[5] * p2q1 + h[14] * p1q2;
+}
+
 // atomic max of a non-negative double through its bit pattern
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
   if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000ULL);  // NaN -> +inf

@@ -147,6 +147,62 @@ struct DevPCG32 {
   double *scal;               // [8]: rz, alpha, beta, rr, bnorm2, rtol2, pSp, spare
   int *iter;                  // [2]: iterations done, converged flag
   int nblocks;
+  // learned preconditioner (t null: block Jacobi): t = C r, y = G t
+  float *t, *y;               // [5][K]
+  const float *Cl;            // [K][6] inverse Cholesky factors C_k of the learned form
+};
+
+// Learned block preconditioner of the dual PCG (k_lpc.cu), ball joints.
+// Joints are the nodes of a graph whose edges join joints sharing a free
+// body; S~ = C S C^T is the dual normalized by the inverse Cholesky factors
+// C_k of its diagonal blocks, E_kk' its off-diagonal blocks.  A message-passing
+// network over that graph gives per-edge weights alpha (edges to lower-index
+// neighbours) and per-joint scales s; the preconditioner is
+//   M^{-1} = C^T G^T G C,  G = diag(s) (I - A),  A_kk' = alpha_kk' E_kk' (k' < k).
+constexpr int LPC_F = 8;    // input features per joint
+constexpr int LPC_H = 64;   // hidden width
+constexpr int LPC_R = 8;    // rank of the bilinear edge head
+// parameter vector (FP32): W1 [2F][H], b1, W2 [2H][H], b2, W3 [2H][H], b3,
+// Wa [H][R], Wb [H][R], wd [H], cd, we [2], ce
+constexpr int LPC_OFF_W1 = 0;
+constexpr int LPC_OFF_B1 = LPC_OFF_W1 + 2 * LPC_F * LPC_H;
+constexpr int LPC_OFF_W2 = LPC_OFF_B1 + LPC_H;
+constexpr int LPC_OFF_B2 = LPC_OFF_W2 + 2 * LPC_H * LPC_H;
+constexpr int LPC_OFF_W3 = LPC_OFF_B2 + LPC_H;
+constexpr int LPC_OFF_B3 = LPC_OFF_W3 + 2 * LPC_H * LPC_H;
+constexpr int LPC_OFF_WA = LPC_OFF_B3 + LPC_H;
+constexpr int LPC_OFF_WB = LPC_OFF_WA + LPC_H * LPC_R;
+constexpr int LPC_OFF_WD = LPC_OFF_WB + LPC_H * LPC_R;
+constexpr int LPC_OFF_CD = LPC_OFF_WD + LPC_H;
+constexpr int LPC_OFF_WE = LPC_OFF_CD + 1;
+constexpr int LPC_OFF_CE = LPC_OFF_WE + 2;
+constexpr int LPC_NPARAM = LPC_OFF_CE + 1;
+
+struct LpcGraph {
+  int32_t K, nnz;
+  const int32_t *off;       // [K+1] CSR over joints
+  const int32_t *nbr;       // [nnz] adjacent joint
+  const int32_t *body;      // [nnz] the shared free body
+  const int8_t *sk, *sn;    // [nnz] side (0: a, 1: b) of the joint and of the neighbour on it
+  const int32_t *rev;       // [nnz] entry of the neighbour that points back
+  const uint8_t *onesided;  // [K] 1 if the joint has a single free body
+};
+
+struct LpcAct {
+  float *E;                     // [nnz][9] E_kk' row-major (rows: joint k, columns: neighbour)
+  float *C;                     // [K][6] inverse Cholesky factor of D_k, packed lower
+  float *x;                     // [K][F]
+  float *A1, *A2, *A3;          // [K][2F], [K][2H], [K][2H] layer inputs as multiplied (training)
+  float *pre1, *pre2, *pre3;    // [K][H] pre-activations (training)
+  float *h1, *h2, *h3;          // [K][H]
+  float *a, *b;                 // [K][R]
+  float *s;                     // [K]
+  float *alpha;                 // [nnz] (entries to higher-index neighbours hold 0)
+};
+
+struct LpcNet {
+  const float *P;               // [LPC_NPARAM]
+  const uint16_t *W1t, *W2t, *W3t;  // bf16 bits, transposed: [H][2F], [H][2H], [H][2H]
 };
 
 struct StepParams {
@@ -191,11 +247,50 @@ void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevel &cur, in
 
 // FP32 PCG (k_pcg32.cu): setup from rhs (FP64 [5][K]), iterations, and the
 // final copy of x to out (FP64 [5][K]) with acc += x when acc is given
+// (lg, la: the learned preconditioner when P.t is set)
+struct LpcGraph;
+struct LpcAct;
 void launch_p32_setup(const DevBodies &B, const DevJoints &J, const DevPCG32 &P, const double *rhs,
-                      double rtol, int *status, cudaStream_t s);
+                      double rtol, int *status, cudaStream_t s, const LpcGraph *lg = nullptr,
+                      const LpcAct *la = nullptr);
 void launch_p32_iteration(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
-                          const DevPCG32 &P, int max_iters, cudaStream_t s);
+                          const DevPCG32 &P, int max_iters, cudaStream_t s, const LpcGraph *lg = nullptr,
+                          const LpcAct *la = nullptr);
 void launch_p32_finish(const DevJoints &J, const DevPCG32 &P, double *out, double *acc, cudaStream_t s);
+
+// learned preconditioner (k_lpc.cu)
+// C_k and the normalized blocks E of the current state (needs R/Rf, hinvf)
+void launch_lpc_blocks(const DevBodies &B, const DevJoints &J, const LpcGraph &G, const LpcAct &A,
+                       int *status, cudaStream_t s);
+// bf16 transposed copies of the layer weights from P
+void launch_lpc_weights(const float *P, uint16_t *W1t, uint16_t *W2t, uint16_t *W3t, cudaStream_t s);
+// features, three message-passing layers, heads: alpha and s (training: also
+// keeps the layer inputs and pre-activations)
+void launch_lpc_forward(const LpcGraph &G, const LpcNet &N, const LpcAct &A, bool keep, cudaStream_t s);
+// z = M^{-1} r for PCG vectors [5][K] (rows 0-2): t = C r is formed by the
+// caller's kernel; y = G t (tmp), z = C^T G^T y, partial sums of r.z per block
+void launch_lpc_apply(const LpcGraph &G, const LpcAct &A, const float *t, float *y, const float *r,
+                      float *z, double *part, int nblocks, cudaStream_t s, const int *iter);
+
+// training (k_lpc_train.cu): work arrays of one batch
+struct LpcTrainWork {
+  int nv;
+  const float *V;                    // [nv][K][3]
+  float *t, *u, *w, *q, *gw, *gu;    // [nv][K][3]
+  float *dalpha;                     // [nnz]
+  float *ds;                         // [K]
+  float *dh, *dh2;                   // [K][H]
+  float *dA;                         // [K][2H]
+  float *dpre;                       // [K][H]
+  float *grad;                       // [NPARAM]
+  double *part;                      // [nblocks]
+  double *loss;                      // [1]
+};
+
+void launch_lpc_probe(float *V, size_t n, uint64_t seed, cudaStream_t s);
+void launch_lpc_loss_grad(const LpcGraph &G, const LpcAct &A, const LpcNet &N, const LpcTrainWork &W,
+                          bool grad, cudaStream_t s);
+void launch_lpc_adam(float *P, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
 
 // mixed-precision form of the chain step (k_mixed.cu)
 void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s);

@@ -69,7 +69,10 @@ _lib = None
 EXPORTS = ["mabd_config_default", "mabd_create", "mabd_add_bodies", "mabd_add_joints",
            "mabd_prefactor", "mabd_step", "mabd_get_state", "mabd_set_state", "mabd_get_lambda",
            "mabd_synchronize", "mabd_get_info", "mabd_profile_enable", "mabd_profile_reset",
-           "mabd_kernel_times", "mabd_destroy", "mabd_status_string", "mabd_error_detail"]
+           "mabd_kernel_times", "mabd_destroy", "mabd_status_string", "mabd_error_detail",
+           "mabd_lpc_num_params", "mabd_set_preconditioner", "mabd_lpc_fallbacks",
+           "mabd_lpc_create", "mabd_lpc_capture", "mabd_lpc_batch_blocks", "mabd_lpc_loss_grad",
+           "mabd_lpc_train", "mabd_lpc_destroy"]
 
 
 def library_path() -> str:
@@ -108,6 +111,16 @@ def load(build_if_missing: bool = True):
     lib.mabd_status_string.restype = C.c_char_p
     lib.mabd_error_detail.argtypes = [P]
     lib.mabd_error_detail.restype = C.c_char_p
+    u64 = C.c_uint64
+    lib.mabd_lpc_num_params.argtypes = []
+    lib.mabd_set_preconditioner.argtypes = [P, P]
+    lib.mabd_lpc_fallbacks.argtypes = [P, C.POINTER(i32)]
+    lib.mabd_lpc_create.argtypes = [C.POINTER(P)]
+    lib.mabd_lpc_capture.argtypes = [P, P, C.POINTER(i32)]
+    lib.mabd_lpc_batch_blocks.argtypes = [P, i32, P, P, P]
+    lib.mabd_lpc_loss_grad.argtypes = [P, i32, P, i32, P, u64, C.POINTER(C.c_double), P]
+    lib.mabd_lpc_train.argtypes = [P, P, i32, C.c_float, i32, u64, P]
+    lib.mabd_lpc_destroy.argtypes = [P]
     for f in EXPORTS:
         if f not in ("mabd_config_default", "mabd_status_string", "mabd_error_detail"):
             getattr(lib, f).restype = i32
@@ -255,10 +268,91 @@ class Solver:
             C.cast(launches, C.c_void_p), C.byref(count)))
         return {names[i].decode(): (ms[i], launches[i]) for i in range(min(count.value, cap))}
 
+    def set_preconditioner(self, params):
+        """Learned preconditioner parameters (float32 vector) or None."""
+        if params is None:
+            self._check("mabd_set_preconditioner", self._lib.mabd_set_preconditioner(self.ctx, None))
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == lpc_num_params()
+        self._check("mabd_set_preconditioner", self._lib.mabd_set_preconditioner(self.ctx, _ptr(p)))
+
+    def lpc_fallbacks(self) -> int:
+        n = C.c_int32(0)
+        self._check("mabd_lpc_fallbacks", self._lib.mabd_lpc_fallbacks(self.ctx, C.byref(n)))
+        return n.value
+
     def close(self):
         if getattr(self, "ctx", None):
             self._lib.mabd_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lpc_num_params() -> int:
+    return int(load().mabd_lpc_num_params())
+
+
+class LpcTrainer:
+    """Captured normalized dual systems and on-device training of the learned
+    preconditioner (mabd_lpc_*)."""
+
+    def __init__(self):
+        self._lib = load()
+        t = C.c_void_p()
+        st = self._lib.mabd_lpc_create(C.byref(t))
+        if st != 0:
+            raise MabdError("mabd_lpc_create", st)
+        self.t = t
+        self.n = lpc_num_params()
+
+    def _check(self, what, st):
+        if st != 0:
+            raise MabdError(what, st)
+
+    def capture(self, solver: Solver) -> int:
+        b = C.c_int32(-1)
+        self._check("mabd_lpc_capture", self._lib.mabd_lpc_capture(self.t, solver.ctx, C.byref(b)))
+        return b.value
+
+    def blocks(self, batch: int, K: int, nnz: int):
+        """(off [K+1], nbr [nnz], E [nnz,3,3]) of a captured batch."""
+        off = np.zeros(K + 1, dtype=np.int32)
+        nbr = np.zeros(max(nnz, 1), dtype=np.int32)
+        E = np.zeros((max(nnz, 1), 9), dtype=np.float32)
+        self._check("mabd_lpc_batch_blocks",
+                    self._lib.mabd_lpc_batch_blocks(self.t, batch, _ptr(off), _ptr(nbr), _ptr(E)))
+        return off, nbr[:nnz], E[:nnz].reshape(nnz, 3, 3)
+
+    def loss_grad(self, batch: int, params, V=None, nv: int = 2, seed: int = 0, grad: bool = True):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        g = np.zeros(self.n, dtype=np.float32) if grad else None
+        Vp = None
+        if V is not None:
+            V = np.ascontiguousarray(V, dtype=np.float32)
+            nv = V.shape[0]
+            Vp = _ptr(V)
+        loss = C.c_double(0.0)
+        self._check("mabd_lpc_loss_grad", self._lib.mabd_lpc_loss_grad(
+            self.t, batch, _ptr(p), nv, Vp, seed, C.byref(loss), _ptr(g) if grad else None))
+        return loss.value, g
+
+    def train(self, params, iters: int, lr: float = 1e-3, nv: int = 2, seed: int = 0):
+        p = np.ascontiguousarray(params, dtype=np.float32).copy()
+        losses = np.zeros(max(iters, 1))
+        self._check("mabd_lpc_train", self._lib.mabd_lpc_train(
+            self.t, _ptr(p), iters, C.c_float(lr), nv, seed, _ptr(losses)))
+        return p, losses[:iters]
+
+    def close(self):
+        if getattr(self, "t", None):
+            self._lib.mabd_lpc_destroy(self.t)
+            self.t = None
 
     def __del__(self):
         try:

@@ -534,6 +534,80 @@ def rotate_scene(sc: dict, Q: np.ndarray) -> dict:
     return out
 
 
+def concat_scenes(parts: list[dict], spacing: float = 100.0) -> dict:
+    """Disjoint union of scenes with the same h and gravity: part i is moved
+    by i * spacing along x and its body and joint ids are offset."""
+    out = {}
+    h, g = parts[0]["h"], parts[0]["gravity"]
+    boff = 0
+    chunks: dict[str, list] = {}
+    for i, sc in enumerate(parts):
+        M = len(sc["mass"])
+        c = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+        c["q"][:, 9] += i * spacing
+        for key in ("body_a", "body_b"):
+            v = c[key]
+            c[key] = np.where(v == WORLD, WORLD, v + boff)
+        w = c["body_b"] == WORLD
+        c["anchor_b"][w, 0] += i * spacing
+        for k, v in c.items():
+            if isinstance(v, np.ndarray):
+                chunks.setdefault(k, []).append(v)
+        boff += M
+    for k, vs in chunks.items():
+        out[k] = np.concatenate(vs, axis=0)
+    out["h"], out["gravity"] = h, g
+    return out
+
+
+def net_collection(n: int = 48, seed: int = 10, size_range=((4, 10), (4, 10), (3, 6))) -> dict:
+    """n disjoint jittered nets of the closed-loop form (jittered_net) with
+    sizes drawn uniformly from size_range and their own seeds: the training
+    scenes of the learned preconditioner."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i in range(n):
+        dims = [int(rng.integers(lo, hi + 1)) for lo, hi in size_range]
+        parts.append(jittered_net(*dims, seed=int(rng.integers(1 << 30))))
+    return concat_scenes(parts)
+
+
+# parameter layout of the learned preconditioner (sizes only; the network
+# itself lives in the library and in the oracle)
+LPC_SIZES = (("W1", (16, 64)), ("b1", (64,)), ("W2", (128, 64)), ("b2", (64,)),
+             ("W3", (128, 64)), ("b3", (64,)), ("Wa", (64, 8)), ("Wb", (64, 8)),
+             ("wd", (64,)), ("cd", (1,)), ("we", (2,)), ("ce", (1,)))
+
+
+def lpc_param_count() -> int:
+    return int(sum(np.prod(shape) for _, shape in LPC_SIZES))
+
+
+def lpc_init_params(seed: int = 0) -> np.ndarray:
+    """Random starting parameters (float32): layer weights N(0, 2/fan_in),
+    biases 0, edge-head factors N(0, 0.01/64), scale head 0, edge gate
+    offset ln(1/2) (alpha = 0.5 where the bilinear term is 0)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, shape in LPC_SIZES:
+        if name in ("W1", "W2", "W3"):
+            v = rng.standard_normal(shape) * np.sqrt(2.0 / shape[0])
+        elif name in ("Wa", "Wb"):
+            v = rng.standard_normal(shape) * np.sqrt(0.01 / shape[0])
+        elif name == "ce":
+            v = np.full(shape, np.log(0.5))
+        else:
+            v = np.zeros(shape)
+        out.append(np.asarray(v, dtype=np.float64).ravel())
+    return np.concatenate(out).astype(np.float32)
+
+
+def lpc_probe(nv: int, K: int, seed: int) -> np.ndarray:
+    """Probe vectors [nv][K][3] (float32), uniform with unit variance."""
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(-1.0, 1.0, size=(nv, K, 3)) * np.sqrt(3.0)).astype(np.float32)
+
+
 def dual_rows(sc: dict) -> int:
     return int(np.sum(np.where(sc["jtype"] == HINGE, 5, 3)))
 
