@@ -84,6 +84,20 @@ def workload_config(M: int, K: int, rows: int, name: str = "chain1m", form: str 
     }
 
 
+LPC_PARAMS_REL = "paper_2603_08079_gb300/data/lpc_params.npy"
+
+
+def use_learned(args, form: str):
+    """Trained parameters of the learned preconditioner for the net workload
+    in the mixed form (None otherwise or with --no-lpc)."""
+    if args.no_lpc or form != "mixed" or args.workload != "net64x64x16":
+        return None
+    path = os.path.join(ROOT, LPC_PARAMS_REL)
+    if not os.path.exists(path):
+        return None
+    return np.load(path).astype(np.float32)
+
+
 def chosen_form(args) -> str:
     """The mixed form exists for chains and for the PCG path (nets); trees
     and the batched forest run FP64."""
@@ -291,7 +305,10 @@ def run_gpu(args):
     sc = make_scene(args.workload, args.bodies if args.workload == "chain1m" else None)
     M = len(sc["mass"])
     form = chosen_form(args)
-    solver = mabd.Solver(sc, precision=form, refine_steps=args.refine)
+    solver = mabd.Solver(sc, precision=form, refine_steps=args.refine, pcg_max_iters=20000)
+    learned = use_learned(args, form)
+    if learned is not None:
+        solver.set_preconditioner(learned)
     info = solver.info()
 
     def barrier_sync():
@@ -338,15 +355,26 @@ def run_gpu(args):
     st = solver.step(1, stats=True)[0]
     solver.close()
 
-    # the plain FP64 GPU path on the same workload, timed the same way
+    # the plain FP64 GPU path on the same workload (and, for the learned
+    # form, the mixed form with block Jacobi), timed the same way
     plain = None
+    others = {}
     if form != "fp64":
-        ref = mabd.Solver(sc, precision="fp64")
-        pms, _ = time_steps(ref, args.steps, args.warmup, barrier_sync)
-        ref.close()
-        pms = max_over_ranks(pms)
-        plain = {"value": ws * M * args.steps / (pms / 1e3), "unit": "body-steps/s",
-                 "ms_per_step": pms / args.steps}
+        variants = [("plain_fp64_gpu", dict(precision="fp64"), None)]
+        if learned is not None:
+            variants.append(("mixed_block_jacobi_gpu", dict(precision="mixed", refine_steps=args.refine),
+                             None))
+        for key, kw, lp in variants:
+            ref = mabd.Solver(sc, pcg_max_iters=20000, **kw)
+            pms, _ = time_steps(ref, args.steps, args.warmup, barrier_sync)
+            rst = ref.step(1, stats=True)[0]
+            ref.close()
+            pms = max_over_ranks(pms)
+            others[key] = {"value": ws * M * args.steps / (pms / 1e3), "unit": "body-steps/s",
+                           "ms_per_step": pms / args.steps}
+            if rst.get("pcg_iters"):
+                others[key]["pcg_iters_per_step"] = rst["pcg_iters"]
+        plain = others["plain_fp64_gpu"]
 
     result = None
     if rank == 0:
@@ -386,7 +414,10 @@ def run_gpu(args):
         }
         if form != "fp64":
             result["refine_residual"] = st["refine_residual"]
-            result["plain_fp64_gpu"] = plain
+            result.update(others)
+        if learned is not None:
+            result["config"]["preconditioner"] = ("learned (3-layer message passing, hidden 64, BF16 "
+                                                  "tensor cores), trained parameters %s" % LPC_PARAMS_REL)
         if st.get("pcg_iters"):
             result["pcg_iters_per_step"] = st["pcg_iters"]
         if not args.no_cpu_baseline:
@@ -470,6 +501,8 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"],
                     help="form of the step (auto: mixed for the chain, FP64 otherwise)")
     ap.add_argument("--refine", type=int, default=1, help="FP64 correction sweeps of the mixed form")
+    ap.add_argument("--no-lpc", action="store_true",
+                    help="net workload: block Jacobi instead of the learned preconditioner")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "own":
         args.warmup = 3

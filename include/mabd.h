@@ -264,16 +264,21 @@ mabd_status mabd_lpc_capture(mabd_lpc *t, mabd_ctx *ctx, int32_t *batch);
    shared body) and the normalized blocks E[nnz][9] (row-major, rows: the
    joint, columns: the neighbour). */
 mabd_status mabd_lpc_batch_blocks(mabd_lpc *t, int32_t batch, int32_t *off, int32_t *nbr, float *E);
-/* Loss L = sum_v |G S~ G^T v - v|^2 / (nv 3K) of one batch over nv probe
+/* Training objective of one batch, X = G S~ G^T, n = 3K, over nv probe
    vectors V (host, [nv][K][3] in joint order; NULL: drawn on the device from
-   SplitMix64(seed + i), uniform with unit variance) and, when grad is not
-   NULL, dL/dparams (host, mabd_lpc_num_params floats). */
-mabd_status mabd_lpc_loss_grad(mabd_lpc *t, int32_t batch, const float *params, int32_t nv,
-                               const float *V, uint64_t seed, double *loss, float *grad);
-/* iters Adam steps (learning rate lr, fresh moments) on batches drawn from
-   the seed; params (host) in: start, out: result; losses[iters] if given. */
-mabd_status mabd_lpc_train(mabd_lpc *t, float *params, int32_t iters, float lr, int32_t nv,
-                           uint64_t seed, double *losses);
+   SplitMix64(seed + i), uniform with unit variance):
+     kind 0 (Frobenius)  L = sum_v |X v - v|^2 / (nv n);
+     kind 1 (Kaporin)    L = log(sum_v v.X v / (nv n)) - (2/K) sum_k log s_k,
+                         the log of Kaporin's condition number of X up to a
+                         constant (tr X estimated by the probes, det exact);
+   and, when grad is not NULL, dL/dparams (host, mabd_lpc_num_params floats). */
+mabd_status mabd_lpc_loss_grad(mabd_lpc *t, int32_t batch, const float *params, int32_t kind,
+                               int32_t nv, const float *V, uint64_t seed, double *loss, float *grad);
+/* iters Adam steps on `kind` (learning rate lr, fresh moments) on batches
+   drawn from the seed; params (host) in: start, out: result; losses[iters]
+   if given. */
+mabd_status mabd_lpc_train(mabd_lpc *t, float *params, int32_t kind, int32_t iters, float lr,
+                           int32_t nv, uint64_t seed, double *losses);
 mabd_status mabd_lpc_destroy(mabd_lpc *t);
 
 /* Text of the last CUDA failure seen by the context (error name, message and

@@ -20,10 +20,14 @@ with dense matrices (small systems only):
 * heads s_k = exp(clip(wd.h_k + cd, -8, 8)), a = h Wa, b = h Wb,
   alpha_kn = 1.5 sigmoid(a_k.b_n + we0 |E_kn|_F + we1 tr E_kn + ce) for n < k;
 * G = diag(s)(I - A), A_kn = alpha_kn E_kn (n < k); M^{-1} = C^T G^T G C;
-* loss L = |G S~ G^T V - V|_F^2 / (nv 3K) for probe vectors V, and its
-  gradient with respect to every parameter by dense backpropagation
-  (dL/dG = (D V^T + V D^T) G S~ with D = dL/dY; the GPU uses the sparse
-  chain rule instead).
+* with X = G S~ G^T, n = 3K and probe vectors V (nv columns): the Frobenius
+  objective L = |X V - V|_F^2 / (nv n), or Kaporin's objective
+  L = log(tr(V^T X V) / (nv n)) - (2/K) sum_k log s_k (the log of Kaporin's
+  condition number (tr X / n)^n / det X, per row and up to the constant
+  log det S~ / n; det G = prod s_k^3 since G is block triangular);
+* the gradient with respect to every parameter by dense backpropagation
+  (dL/dG = (D V^T + V D^T) G S~ with D = dL/dY, Y = X V; the GPU uses the
+  sparse chain rule instead).
 
 Parity unpinned by the paper (there is nothing to pin it to there); the
 tests pin this module by finite differences of the loss, by the block-Jacobi
@@ -199,16 +203,22 @@ def G_matrix(cache, E, ent) -> np.ndarray:
     return np.repeat(cache["s"], 3)[:, None] * (np.eye(3 * K) - A), A
 
 
-def loss(theta, St, E, ent, ones, V, use_bf16: bool = True) -> float:
+def _objective(kind: str, Y, Vm, s, K):
+    if kind == "frobenius":
+        return float(np.sum((Y - Vm) ** 2) / Vm.size)
+    return float(np.log(np.sum(Vm * Y) / Vm.size) - 2.0 / K * np.sum(np.log(s)))
+
+
+def loss(theta, St, E, ent, ones, V, use_bf16: bool = True, kind: str = "kaporin") -> float:
     """V: probe vectors [nv][K][3]."""
     cache = forward(theta, E, ent, ones, use_bf16)
     G, _ = G_matrix(cache, E, ent)
     Vm = np.asarray(V, dtype=np.float64).reshape(V.shape[0], -1).T
     Y = G @ St @ G.T @ Vm
-    return float(np.sum((Y - Vm) ** 2) / Vm.size)
+    return _objective(kind, Y, Vm, cache["s"], len(ent))
 
 
-def loss_grad(theta, St, E, ent, ones, V, use_bf16: bool = True):
+def loss_grad(theta, St, E, ent, ones, V, use_bf16: bool = True, kind: str = "kaporin"):
     """Loss and its gradient (a flat vector in the parameter layout)."""
     p = unpack(theta)
     cache = forward(theta, E, ent, ones, use_bf16)
@@ -216,13 +226,17 @@ def loss_grad(theta, St, E, ent, ones, V, use_bf16: bool = True):
     K = len(ent)
     Vm = np.asarray(V, dtype=np.float64).reshape(V.shape[0], -1).T
     Y = G @ St @ G.T @ Vm
-    Res = Y - Vm
-    L = float(np.sum(Res ** 2) / Vm.size)
-    D = 2.0 * Res / Vm.size
-    dG = (D @ Vm.T + Vm @ D.T) @ G @ St
     s = cache["s"]
+    L = _objective(kind, Y, Vm, s, K)
+    if kind == "frobenius":
+        D = 2.0 * (Y - Vm) / Vm.size
+    else:
+        D = Vm / np.sum(Vm * Y)
+    dG = (D @ Vm.T + Vm @ D.T) @ G @ St
     IA = np.eye(3 * K) - A
     ds = np.array([np.sum(dG[3 * k:3 * k + 3] * IA[3 * k:3 * k + 3]) for k in range(K)])
+    if kind != "frobenius":
+        ds = ds - 2.0 / (K * s)
     dA = -np.repeat(s, 3)[:, None] * dG
     g = {name: np.zeros(shape) for name, shape in SIZES}
     a, b = cache["a"], cache["b"]

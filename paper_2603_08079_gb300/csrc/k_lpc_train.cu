@@ -1,13 +1,18 @@
 // Learned block preconditioner: training (forward in the inference kernels,
 // backward and the optimizer here).
 //
-// Loss of a batch of normalized dual systems S~ (unit diagonal blocks,
-// off-diagonal blocks E) over probe vectors v:
-//   L = sum_v |G S~ G^T v - v|^2 / (nv 3K),   G = diag(s)(I - A)
-// (G S~ G^T = I would make the preconditioned operator the identity).  With
+// Two objectives over a batch of normalized dual systems S~ (unit diagonal
+// blocks, off-diagonal blocks E), X = G S~ G^T, G = diag(s)(I - A), n = 3K,
+// estimated with probe vectors v (E[v v^T] = I):
+//   Frobenius  L = sum_v |X v - v|^2 / (nv n);
+//   Kaporin    L = log(tr X / n) - log det(X)^{1/n} + const
+//              = log(sum_v v.X v / (nv n)) - (2/K) sum_k log s_k,
+// the log of Kaporin's condition number (which bounds the CG iteration
+// count); det G = prod s_k^3 because G is block lower triangular.  With
 // t = s v, u = t - A^T t, w = S~ u, m = w - A w, y = s m the gradients are
 //   q = s dL/dy,  dL/dw = q - A^T q,  dL/du = S~ dL/dw,  dL/dt = dL/du - A dL/du,
-//   dL/ds_k = dL/dy_k . m_k + dL/dt_k . v_k,
+//   dL/ds_k = dL/dy_k . m_k + dL/dt_k . v_k (- 2/(K s_k), Kaporin),
+// where dL/dy = 2 (y - v) / (nv n) (Frobenius) or v / sum_v v.y (Kaporin);
 //   dL/dalpha_kn = -q_k^T E_kn w_n - t_k^T E_kn (dL/du)_n   (n < k),
 // then through the heads and the three layers (the BF16 rounding of the layer
 // inputs is passed straight through).  Probe vectors are drawn on the device
@@ -105,49 +110,81 @@ __global__ void __launch_bounds__(128) k_lpc_spmv(LpcGraph G, LpcAct A, const fl
   }
 }
 
-// m = w - A w, y = s m, residual y - v, loss partial; q = s dL/dy, ds (first
-// part), dalpha (first part)
-__global__ void __launch_bounds__(128) k_lpc_l4(LpcGraph G, LpcAct A, LpcTrainWork W, float cscale) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int K = G.K;
-  double lsum = 0.0;
-  if (k < K) {
-    const float sk = A.s[k];
-    float ds = 0.f;
-    for (int e = G.off[k]; e < G.off[k + 1]; ++e)
-      if (G.nbr[e] < k) W.dalpha[e] = 0.f;
-    for (int i = 0; i < W.nv; ++i) {
-      const float *wi = W.w + (size_t)i * K * 3;
-      float m[3];
-      spmv_row<LPC_LOWER>(G, A, k, wi, nullptr, -1.f, K, m);
-      const size_t o = ((size_t)i * K + k) * 3;
-      float q[3];
-      for (int c = 0; c < 3; ++c) {
-        const float res = sk * m[c] - W.V[o + c];
-        lsum += (double)res * res;
-        const float gy = cscale * res;
-        ds += gy * m[c];
-        q[c] = sk * gy;
-        W.q[o + c] = q[c];
-      }
-      for (int e = G.off[k]; e < G.off[k + 1]; ++e) {
-        const int n = G.nbr[e];
-        if (n >= k) continue;
-        float y[3];
-        mv3f(A.E + (size_t)9 * e, wi + (size_t)3 * n, y);
-        W.dalpha[e] -= q[0] * y[0] + q[1] * y[1] + q[2] * y[2];
-      }
-    }
-    W.ds[k] = ds;
-  }
-  __shared__ double sh[128];
-  sh[threadIdx.x] = lsum;
+// pass 1: m = w - A w, y = s m; per block the sum of |y - v|^2 (Frobenius
+// objective) or of v.y (Kaporin objective) into part[b], and of log s_k into
+// part[nb + b]
+__device__ __forceinline__ void block_sum2d(double a, double b, double *part, int nb) {
+  __shared__ double sh[128], sh2[128];
+  sh[threadIdx.x] = a;
+  sh2[threadIdx.x] = b;
   __syncthreads();
-  for (int o2 = 64; o2 > 0; o2 >>= 1) {
-    if (threadIdx.x < o2) sh[threadIdx.x] += sh[threadIdx.x + o2];
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[threadIdx.x] += sh[threadIdx.x + o];
+      sh2[threadIdx.x] += sh2[threadIdx.x + o];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) W.part[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sh[0];
+    part[nb + blockIdx.x] = sh2[0];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_lpc_l4a(LpcGraph G, LpcAct A, LpcTrainWork W, int kind) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int K = G.K;
+  double acc = 0.0, lsum = 0.0;
+  if (k < K) {
+    const float sk = A.s[k];
+    lsum = log((double)sk);
+    for (int i = 0; i < W.nv; ++i) {
+      float m[3];
+      spmv_row<LPC_LOWER>(G, A, k, W.w + (size_t)i * K * 3, nullptr, -1.f, K, m);
+      const size_t o = ((size_t)i * K + k) * 3;
+      for (int c = 0; c < 3; ++c) {
+        const double y = (double)(sk * m[c]), v = (double)W.V[o + c];
+        acc += kind == 0 ? (y - v) * (y - v) : v * y;
+      }
+    }
+  }
+  block_sum2d(acc, lsum, W.part, gridDim.x);
+}
+
+// pass 2 (gradient): dL/dy = 2 (y - v) / N (Frobenius) or v / sum(v.y)
+// (Kaporin, from loss[0]); q = s dL/dy, ds = dL/dy . m (- 2 / (K s) for
+// Kaporin's determinant term), dalpha = -q_k^T E w_n
+__global__ void __launch_bounds__(128) k_lpc_l4b(LpcGraph G, LpcAct A, LpcTrainWork W, int kind,
+                                                 float cscale) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int K = G.K;
+  if (k >= K) return;
+  const float sk = A.s[k];
+  const float ck = kind == 0 ? cscale : (float)(1.0 / W.loss[0]);
+  float ds = kind == 0 ? 0.f : -2.f / ((float)K * sk);
+  for (int e = G.off[k]; e < G.off[k + 1]; ++e)
+    if (G.nbr[e] < k) W.dalpha[e] = 0.f;
+  for (int i = 0; i < W.nv; ++i) {
+    const float *wi = W.w + (size_t)i * K * 3;
+    float m[3];
+    spmv_row<LPC_LOWER>(G, A, k, wi, nullptr, -1.f, K, m);
+    const size_t o = ((size_t)i * K + k) * 3;
+    float q[3];
+    for (int c = 0; c < 3; ++c) {
+      const float gy = kind == 0 ? ck * (sk * m[c] - W.V[o + c]) : ck * W.V[o + c];
+      ds += gy * m[c];
+      q[c] = sk * gy;
+      W.q[o + c] = q[c];
+    }
+    for (int e = G.off[k]; e < G.off[k + 1]; ++e) {
+      const int n = G.nbr[e];
+      if (n >= k) continue;
+      float y[3];
+      mv3f(A.E + (size_t)9 * e, wi + (size_t)3 * n, y);
+      W.dalpha[e] -= q[0] * y[0] + q[1] * y[1] + q[2] * y[2];
+    }
+  }
+  W.ds[k] = ds;
 }
 
 // dL/dt = gu - A gu; ds += dL/dt . v; dalpha -= t_k^T E gu_n
@@ -174,17 +211,28 @@ __global__ void __launch_bounds__(128) k_lpc_l7(LpcGraph G, LpcAct A, LpcTrainWo
   W.ds[k] = ds;
 }
 
+// loss[0] = sum of part[0..n), loss[1] = sum of part[n..2n)
 __global__ void k_lpc_loss_sum(const double *part, int n, double *loss) {
-  __shared__ double sh[256];
-  double x = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x += part[i];
+  __shared__ double sh[256], sh2[256];
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    x += part[i];
+    y += part[n + i];
+  }
   sh[threadIdx.x] = x;
+  sh2[threadIdx.x] = y;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    if (threadIdx.x < o) {
+      sh[threadIdx.x] += sh[threadIdx.x + o];
+      sh2[threadIdx.x] += sh2[threadIdx.x + o];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *loss = sh[0];
+  if (threadIdx.x == 0) {
+    loss[0] = sh[0];
+    loss[1] = sh2[0];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -367,15 +415,16 @@ void launch_lpc_probe(float *V, size_t n, uint64_t seed, cudaStream_t s) {
 // loss of the batch (W.loss) and, when grad, the gradient of every
 // parameter (W.grad, zeroed here); the forward pass must have run with keep
 void launch_lpc_loss_grad(const LpcGraph &G, const LpcAct &A, const LpcNet &N, const LpcTrainWork &W,
-                          bool grad, cudaStream_t s) {
+                          int kind, bool grad, cudaStream_t s) {
   const int K = G.K, nb = (K + 127) / 128;
   const float cscale = 2.f / (float)(W.nv * 3 * (size_t)K);
   k_lpc_l1<<<nb, 128, 0, s>>>(G, A, W);
   k_lpc_spmv<LPC_UPPER><<<nb, 128, 0, s>>>(G, A, W.t, W.u, -1.f, W.nv);
   k_lpc_spmv<LPC_ALL><<<nb, 128, 0, s>>>(G, A, W.u, W.w, 1.f, W.nv);
-  k_lpc_l4<<<nb, 128, 0, s>>>(G, A, W, cscale);
+  k_lpc_l4a<<<nb, 128, 0, s>>>(G, A, W, kind);
   k_lpc_loss_sum<<<1, 256, 0, s>>>(W.part, nb, W.loss);
   if (!grad) return;
+  k_lpc_l4b<<<nb, 128, 0, s>>>(G, A, W, kind, cscale);
   cudaMemsetAsync(W.grad, 0, sizeof(float) * LPC_NPARAM, s);
   k_lpc_spmv<LPC_UPPER><<<nb, 128, 0, s>>>(G, A, W.q, W.gw, -1.f, W.nv);
   k_lpc_spmv<LPC_ALL><<<nb, 128, 0, s>>>(G, A, W.gw, W.gu, 1.f, W.nv);

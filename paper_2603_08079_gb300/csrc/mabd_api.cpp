@@ -1788,7 +1788,7 @@ mabd_status lpc_alloc_work(mabd_lpc *t, int nv) {
 namespace {
 
 // forward with kept activations and the loss (and gradient) of one batch
-mabd_status lpc_eval(mabd_lpc *t, int batch, int nv, const float *V, uint64_t seed, bool grad,
+mabd_status lpc_eval(mabd_lpc *t, int batch, int nv, const float *V, uint64_t seed, int kind, bool grad,
                      double *dloss) {
   cudaStream_t s = t->stream;
   mabd_status st = lpc_alloc_work(t, nv);
@@ -1807,14 +1807,20 @@ mabd_status lpc_eval(mabd_lpc *t, int batch, int nv, const float *V, uint64_t se
   W.nv = nv;
   W.V = t->V;
   W.loss = dloss;
-  launch_lpc_loss_grad(t->g, A, t->net, W, grad, s);
+  launch_lpc_loss_grad(t->g, A, t->net, W, kind, grad, s);
   return cudaGetLastError() == cudaSuccess ? MABD_OK : MABD_ERR_CUDA;
+}
+
+// loss of a kind from the two sums of the loss kernels
+double lpc_loss_value(int kind, const double *sums, int nv, int K) {
+  const double n = (double)nv * 3.0 * K;
+  return kind == 0 ? sums[0] / n : std::log(sums[0] / n) - 2.0 / K * sums[1];
 }
 
 mabd_status lpc_losses(mabd_lpc *t, int n) {
   if (n <= t->losses_cap) return MABD_OK;
   bool ok = true;
-  t->losses = tnew<double>(t, n, ok);
+  t->losses = tnew<double>(t, 2 * (size_t)n, ok);
   if (!ok) return MABD_ERR_OUT_OF_MEMORY;
   t->losses_cap = n;
   return MABD_OK;
@@ -1926,7 +1932,7 @@ mabd_status mabd_lpc_capture(mabd_lpc *t, mabd_ctx *ctx, int32_t *batch) {
     W.dA = tnew<float>(t, 2 * LPC_H * K, ok);
     W.dpre = tnew<float>(t, LPC_H * K, ok);
     W.grad = tnew<float>(t, LPC_NPARAM, ok);
-    W.part = tnew<double>(t, (K + 127) / 128 + 1, ok);
+    W.part = tnew<double>(t, 2 * ((K + 127) / 128) + 2, ok);
     if (!ok) return MABD_ERR_OUT_OF_MEMORY;
     CK(cudaMemcpyAsync(off, G.off, (K + 1) * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(nbr, G.nbr, nz * 4, cudaMemcpyDeviceToDevice, s));
@@ -1968,29 +1974,31 @@ mabd_status mabd_lpc_batch_blocks(mabd_lpc *t, int32_t batch, int32_t *off, int3
   return MABD_OK;
 }
 
-mabd_status mabd_lpc_loss_grad(mabd_lpc *t, int32_t batch, const float *params, int32_t nv, const float *V,
-                               uint64_t seed, double *loss, float *grad) {
-  if (!t || !params || !loss || nv < 1 || !t->have_graph || batch < 0 || batch >= (int)t->batches.size())
+mabd_status mabd_lpc_loss_grad(mabd_lpc *t, int32_t batch, const float *params, int32_t kind, int32_t nv,
+                               const float *V, uint64_t seed, double *loss, float *grad) {
+  if (!t || !params || !loss || nv < 1 || !t->have_graph || batch < 0 || batch >= (int)t->batches.size() ||
+      (kind != 0 && kind != 1))
     return MABD_ERR_INVALID_ARG;
   mabd_status st = lpc_losses(t, 1);
   if (st) return st;
   if (cudaMemcpyAsync(t->P, params, sizeof(float) * LPC_NPARAM, cudaMemcpyHostToDevice, t->stream) != cudaSuccess)
     return MABD_ERR_CUDA;
-  st = lpc_eval(t, batch, nv, V, seed, grad != nullptr, t->losses);
+  st = lpc_eval(t, batch, nv, V, seed, kind, grad != nullptr, t->losses);
   if (st) return st;
-  double l = 0.0;
-  if (cudaMemcpyAsync(&l, t->losses, 8, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess) return MABD_ERR_CUDA;
+  double l[2] = {0.0, 0.0};
+  if (cudaMemcpyAsync(l, t->losses, 16, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess) return MABD_ERR_CUDA;
   if (grad && cudaMemcpyAsync(grad, t->W.grad, sizeof(float) * LPC_NPARAM, cudaMemcpyDeviceToHost, t->stream) !=
                   cudaSuccess)
     return MABD_ERR_CUDA;
   if (cudaStreamSynchronize(t->stream) != cudaSuccess) return MABD_ERR_CUDA;
-  *loss = l / ((double)nv * 3.0 * t->g.K);
+  *loss = lpc_loss_value(kind, l, nv, t->g.K);
   return MABD_OK;
 }
 
-mabd_status mabd_lpc_train(mabd_lpc *t, float *params, int32_t iters, float lr, int32_t nv, uint64_t seed,
-                           double *losses) {
-  if (!t || !params || iters < 0 || nv < 1 || !(lr > 0.f) || !t->have_graph || t->batches.empty())
+mabd_status mabd_lpc_train(mabd_lpc *t, float *params, int32_t kind, int32_t iters, float lr, int32_t nv,
+                           uint64_t seed, double *losses) {
+  if (!t || !params || iters < 0 || nv < 1 || !(lr > 0.f) || !t->have_graph || t->batches.empty() ||
+      (kind != 0 && kind != 1))
     return MABD_ERR_INVALID_ARG;
   cudaStream_t s = t->stream;
   mabd_status st = lpc_losses(t, std::max(iters, 1));
@@ -2009,17 +2017,17 @@ mabd_status mabd_lpc_train(mabd_lpc *t, float *params, int32_t iters, float lr, 
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     z ^= z >> 31;
     const int b = (int)(z % (uint64_t)nb);
-    st = lpc_eval(t, b, nv, nullptr, z, true, t->losses + it);
+    st = lpc_eval(t, b, nv, nullptr, z, kind, true, t->losses + 2 * it);
     if (st) return st;
     launch_lpc_adam(t->P, t->W.grad, t->m, t->v, lr, it + 1, s);
   }
-  std::vector<double> hl(std::max(iters, 1));
+  std::vector<double> hl(2 * (size_t)std::max(iters, 1));
   if (cudaMemcpyAsync(params, t->P, sizeof(float) * LPC_NPARAM, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(hl.data(), t->losses, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hl.data(), t->losses, 16 * (size_t)iters, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return MABD_ERR_CUDA;
   if (losses)
-    for (int i = 0; i < iters; ++i) losses[i] = hl[i] / ((double)nv * 3.0 * t->g.K);
+    for (int i = 0; i < iters; ++i) losses[i] = lpc_loss_value(kind, &hl[2 * (size_t)i], nv, t->g.K);
   return MABD_OK;
 }
 

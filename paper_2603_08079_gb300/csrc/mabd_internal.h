@@ -283,13 +283,15 @@ struct LpcTrainWork {
   float *dA;                         // [K][2H]
   float *dpre;                       // [K][H]
   float *grad;                       // [NPARAM]
-  double *part;                      // [nblocks]
-  double *loss;                      // [1]
+  double *part;                      // [2][nblocks]
+  double *loss;                      // [2]
 };
 
 void launch_lpc_probe(float *V, size_t n, uint64_t seed, cudaStream_t s);
+// kind 0: Frobenius objective, 1: Kaporin objective; W.loss[0..1] receive the
+// sums the loss is formed from (see k_lpc_train.cu)
 void launch_lpc_loss_grad(const LpcGraph &G, const LpcAct &A, const LpcNet &N, const LpcTrainWork &W,
-                          bool grad, cudaStream_t s);
+                          int kind, bool grad, cudaStream_t s);
 void launch_lpc_adam(float *P, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
 
 // mixed-precision form of the chain step (k_mixed.cu)

@@ -118,8 +118,8 @@ def load(build_if_missing: bool = True):
     lib.mabd_lpc_create.argtypes = [C.POINTER(P)]
     lib.mabd_lpc_capture.argtypes = [P, P, C.POINTER(i32)]
     lib.mabd_lpc_batch_blocks.argtypes = [P, i32, P, P, P]
-    lib.mabd_lpc_loss_grad.argtypes = [P, i32, P, i32, P, u64, C.POINTER(C.c_double), P]
-    lib.mabd_lpc_train.argtypes = [P, P, i32, C.c_float, i32, u64, P]
+    lib.mabd_lpc_loss_grad.argtypes = [P, i32, P, i32, i32, P, u64, C.POINTER(C.c_double), P]
+    lib.mabd_lpc_train.argtypes = [P, P, i32, i32, C.c_float, i32, u64, P]
     lib.mabd_lpc_destroy.argtypes = [P]
     for f in EXPORTS:
         if f not in ("mabd_config_default", "mabd_status_string", "mabd_error_detail"):
@@ -329,7 +329,10 @@ class LpcTrainer:
                     self._lib.mabd_lpc_batch_blocks(self.t, batch, _ptr(off), _ptr(nbr), _ptr(E)))
         return off, nbr[:nnz], E[:nnz].reshape(nnz, 3, 3)
 
-    def loss_grad(self, batch: int, params, V=None, nv: int = 2, seed: int = 0, grad: bool = True):
+    KINDS = {"frobenius": 0, "kaporin": 1}
+
+    def loss_grad(self, batch: int, params, V=None, nv: int = 2, seed: int = 0, grad: bool = True,
+                  kind: str = "kaporin"):
         p = np.ascontiguousarray(params, dtype=np.float32)
         g = np.zeros(self.n, dtype=np.float32) if grad else None
         Vp = None
@@ -339,14 +342,16 @@ class LpcTrainer:
             Vp = _ptr(V)
         loss = C.c_double(0.0)
         self._check("mabd_lpc_loss_grad", self._lib.mabd_lpc_loss_grad(
-            self.t, batch, _ptr(p), nv, Vp, seed, C.byref(loss), _ptr(g) if grad else None))
+            self.t, batch, _ptr(p), self.KINDS[kind], nv, Vp, seed, C.byref(loss),
+            _ptr(g) if grad else None))
         return loss.value, g
 
-    def train(self, params, iters: int, lr: float = 1e-3, nv: int = 2, seed: int = 0):
+    def train(self, params, iters: int, lr: float = 1e-3, nv: int = 2, seed: int = 0,
+              kind: str = "kaporin"):
         p = np.ascontiguousarray(params, dtype=np.float32).copy()
         losses = np.zeros(max(iters, 1))
         self._check("mabd_lpc_train", self._lib.mabd_lpc_train(
-            self.t, _ptr(p), iters, C.c_float(lr), nv, seed, _ptr(losses)))
+            self.t, _ptr(p), self.KINDS[kind], iters, C.c_float(lr), nv, seed, _ptr(losses)))
         return p, losses[:iters]
 
     def close(self):

@@ -71,7 +71,7 @@ def test_loss_and_gradient_match_oracle(ora, lpc):
         ent, ones = lpc.joint_graph(sc)
         C, St = lpc.normalized(lpc.dual_dense(sc, q, qd))
         E = lpc.blocks(St, ent)
-        for seed in (0, 1):
+        for seed, kind in ((0, "frobenius"), (1, "kaporin"), (2, "kaporin")):
             theta = scenes.lpc_init_params(seed)
             pr = lpc.unpack(theta.astype(np.float64))
             rng = np.random.default_rng(seed)
@@ -80,9 +80,10 @@ def test_loss_and_gradient_match_oracle(ora, lpc):
             pr["wd"][:] = rng.standard_normal(pr["wd"].shape) * 0.02
             theta = lpc.pack(pr).astype(np.float32)
             V = scenes.lpc_probe(2, len(ent), seed=10 + seed)
-            L_gpu, g_gpu = t.loss_grad(b, theta, V=V)
-            L_ora, g_ora = lpc.loss_grad(theta.astype(np.float64), St, E, ent, ones, V.astype(np.float64))
-            assert abs(L_gpu - L_ora) <= 1e-4 * L_ora, (L_gpu, L_ora)
+            L_gpu, g_gpu = t.loss_grad(b, theta, V=V, kind=kind)
+            L_ora, g_ora = lpc.loss_grad(theta.astype(np.float64), St, E, ent, ones, V.astype(np.float64),
+                                         kind=kind)
+            assert abs(L_gpu - L_ora) <= 1e-4 * max(abs(L_ora), 1e-2), (kind, L_gpu, L_ora)
             assert rel(g_gpu, g_ora) <= 2e-3, rel(g_gpu, g_ora)
     finally:
         t.close()
@@ -107,7 +108,7 @@ def test_training_lowers_the_loss_on_held_out_systems():
         p, losses = t.train(p0, 300, lr=1e-3, nv=2, seed=3)
         assert np.all(np.isfinite(losses)) and np.mean(losses[-30:]) < np.mean(losses[:30])
         after = np.mean([t.loss_grad(held, p, seed=k, grad=False)[0] for k in range(4)])
-        assert after < 0.9 * before, (before, after)
+        assert after < before - 0.05 * abs(before), (before, after)
     finally:
         t.close()
         s.close()
@@ -137,9 +138,10 @@ def test_learned_beats_block_jacobi(dims):
     from paper_2603_08079_gb300.train_lpc import pcg_iterations
     p = trained_params()
     sc = scenes.jittered_net(*dims, seed=4)
-    it_bj, it_learned = pcg_iterations(sc, p)
-    print("pcg iterations", dims, it_bj, it_learned)
+    it_bj, it_init, it_learned = pcg_iterations(sc, scenes.lpc_init_params(0), p)
+    print("pcg iterations (block Jacobi, untrained, trained)", dims, it_bj, it_init, it_learned)
     assert it_learned < 0.9 * it_bj, (it_bj, it_learned)
+    assert it_learned <= 1.05 * it_init, (it_init, it_learned)   # training does not undo the structure
 
 
 def test_untrained_parameters_stay_exact(ora):

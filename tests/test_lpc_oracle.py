@@ -68,7 +68,13 @@ def test_block_jacobi_special_case(small_system, lpc):
     V = scenes.lpc_probe(2, len(ent), seed=5).astype(np.float64)
     Vm = V.reshape(2, -1).T
     want = np.sum((St @ Vm - Vm) ** 2) / Vm.size
-    assert abs(lpc.loss(theta, St, E, ent, ones, V) - want) <= 1e-12 * want
+    assert abs(lpc.loss(theta, St, E, ent, ones, V, kind="frobenius") - want) <= 1e-12 * want
+    # Kaporin: log(tr(V^T S~ V) / N) with s = 1; with many probes tr(V^T S~ V)/N
+    # tends to tr(S~)/n = 1 (unit diagonal blocks), so the loss tends to 0
+    wantk = np.log(np.sum(Vm * (St @ Vm)) / Vm.size)
+    assert abs(lpc.loss(theta, St, E, ent, ones, V, kind="kaporin") - wantk) <= 1e-12 * max(1.0, abs(wantk))
+    Vmany = scenes.lpc_probe(4000, len(ent), seed=8).astype(np.float64)
+    assert abs(lpc.loss(theta, St, E, ent, ones, Vmany, kind="kaporin")) < 0.02
     Minv = lpc.preconditioner(theta, S, ent, ones)
     K = len(ent)
     Dinv = np.zeros_like(S)
@@ -77,7 +83,8 @@ def test_block_jacobi_special_case(small_system, lpc):
     np.testing.assert_allclose(Minv, Dinv, rtol=1e-10, atol=1e-10 * np.max(np.abs(Dinv)))
 
 
-def test_gradient_by_finite_differences(small_system, lpc):
+@pytest.mark.parametrize("kind", ["frobenius", "kaporin"])
+def test_gradient_by_finite_differences(small_system, lpc, kind):
     """Central differences of the loss (FP64 network, no bf16 rounding)
     against the dense backpropagation, coordinate by coordinate."""
     sc, S, C, St, E, ent, ones = small_system
@@ -90,8 +97,8 @@ def test_gradient_by_finite_differences(small_system, lpc):
     p["we"][:] = [0.3, -0.2]
     theta = lpc.pack(p)
     V = scenes.lpc_probe(2, len(ent), seed=6).astype(np.float64)
-    L0, g = lpc.loss_grad(theta, St, E, ent, ones, V, use_bf16=False)
-    assert abs(L0 - lpc.loss(theta, St, E, ent, ones, V, use_bf16=False)) <= 1e-13 * L0
+    L0, g = lpc.loss_grad(theta, St, E, ent, ones, V, use_bf16=False, kind=kind)
+    assert abs(L0 - lpc.loss(theta, St, E, ent, ones, V, use_bf16=False, kind=kind)) <= 1e-13 * abs(L0)
     # every head parameter, and samples of each layer's weights and biases
     offs, o = {}, 0
     for name, shape in lpc.SIZES:
@@ -107,9 +114,9 @@ def test_gradient_by_finite_differences(small_system, lpc):
         tp, tm = theta.copy(), theta.copy()
         tp[i] += eps
         tm[i] -= eps
-        fd = (lpc.loss(tp, St, E, ent, ones, V, use_bf16=False) -
-              lpc.loss(tm, St, E, ent, ones, V, use_bf16=False)) / (2 * eps)
-        assert abs(fd - g[i]) <= 1e-5 * max(abs(fd), 1e-3 * np.max(np.abs(g))), (i, fd, g[i])
+        fd = (lpc.loss(tp, St, E, ent, ones, V, use_bf16=False, kind=kind) -
+              lpc.loss(tm, St, E, ent, ones, V, use_bf16=False, kind=kind)) / (2 * eps)
+        assert abs(fd - g[i]) <= 2e-5 * max(abs(fd), 1e-3 * np.max(np.abs(g))), (i, fd, g[i])
         checked += 1
     assert checked > 150
 
