@@ -1,7 +1,12 @@
 #!/usr/bin/env python3
 """Throughput of the M-ABD step on GB300: body-steps/s on the 1,048,576-body
 pulley-cable chain (alternating ball / hinge joints, both ends pinned,
-h = 1e-2 s, FP64), one implicit step with one Newton iteration per step.
+h = 1e-2 s), one implicit step with one Newton iteration per step, in the
+chosen form (mixed precision: FP32 products, FP64 cyclic reduction and one
+FP64 residual-correction sweep, 1e-6 against the FP64 oracle) with the
+plain FP64 GPU path timed beside it.  Other workloads: --workload
+tree256k | net64x64x16 (mixed form with the learned preconditioner) |
+batch4096.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -258,8 +263,10 @@ def chain_gram_flops(jtype_chain: np.ndarray) -> float:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel, from one ncu capture of the current kernel on the named workload;
-# an entry is removed when its kernel changes
-TRAFFIC: dict = {}
+# an entry is removed when its kernel changes.  cr_level: all 21 launches of
+# a step of the 524,288-body chain (675.4 MB) scaled to 1,048,576 bodies and
+# averaged per launch (profiles/chain512k_mixed_dram_launch_list.md).
+TRAFFIC: dict = {("chain1m", "cr_level"): 64.3e6}
 
 
 def kernel_model(name: str, jtype_chain: np.ndarray):
