@@ -317,6 +317,7 @@ def run_gpu(args):
     if learned is not None:
         solver.set_preconditioner(learned)
     info = solver.info()
+    tree_sched = solver.tree_schedule() if info["solver"] == "tree" else None
 
     def barrier_sync():
         if ws > 1:
@@ -427,6 +428,8 @@ def run_gpu(args):
                                                   "tensor cores), trained parameters %s" % LPC_PARAMS_REL)
         if st.get("pcg_iters"):
             result["pcg_iters_per_step"] = st["pcg_iters"]
+        if tree_sched is not None:
+            result["config"]["tree_schedule"] = tree_sched
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(args)
     if ws > 1:

@@ -226,6 +226,12 @@ mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M, const mab
                                     int32_t K, const mabd_joint_desc *joints, double *q_out,
                                     double *qdot_out, double *lambda_out);
 
+/* Level schedule of a tree context's upward pass (tuned at mabd_prefactor
+   by timing each variant on each level; MABD_TREE_VARIANT=0|1|2 in the
+   environment forces one): counts[0..2] = number of levels with bodies that
+   have children eliminated one per thread, by 8 lanes, by 4 lanes per body. */
+mabd_status mabd_tree_schedule(mabd_ctx *ctx, int32_t *counts);
+
 /* ---- Learned block preconditioner of the mixed-precision PCG path -------
    The paper has no counterpart: this extends its dual solve for closed loops
    and irregular networks (Sec. 5.5).  For ball-joint graphs the dual S is

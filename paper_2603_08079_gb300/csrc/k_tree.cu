@@ -455,6 +455,265 @@ __global__ void __launch_bounds__(128) k_tree_up_leaf(DevBodies B, DevJoints J, 
   else up_body<5, false>(B, J, T, j, p, status, L);
 }
 
+// ---------------------------------------------------------------------------
+// lane-cooperative upward pass of the bodies with children
+// ---------------------------------------------------------------------------
+// The same elimination as up_body<N, false> for a body with children, done
+// by a group of LANES lanes: the dense Hhat (78 packed entries), the rank
+// updates of the children, the right-looking Cholesky's trailing updates and
+// the Gram entries are dealt out over the lanes, and the lanes take the
+// right-hand sides (f, then the N constraint rows) in turn.  A level with few such
+// bodies then runs each body's dependent FP64 chain several times shorter.
+constexpr int CG = 16;  // bodies (lane groups) per block
+
+// entry (r, c), r >= c, of the packed lower triangle index e
+__device__ __forceinline__ void unpack12(int e, int &r, int &c) {
+  r = 0;
+  while ((r + 1) * (r + 2) / 2 <= e) ++r;
+  c = e - r * (r + 1) / 2;
+}
+
+// entry e of the dense Hbar (as hbar_dense)
+__device__ __forceinline__ double hbar_entry(int e, const double s[3], double vm, double vl, double m,
+                                             double ih2) {
+  int r, c;
+  unpack12(e, r, c);
+  const bool dr = (r == 0 || r == 4 || r == 8), dc = (c == 0 || c == 4 || c == 8);
+  if (dr && dc) return r == c ? s[r / 4] * ih2 + 2.0 * vm + vl : vl;
+  if (r >= 9) return r == c ? m * ih2 : 0.0;
+  // transpose pairs (1,3), (2,6), (5,7); the first index has column ca, the second cb
+  if (r == c) {
+    switch (r) {
+      case 1: case 2: return s[0] * ih2 + vm;
+      case 3: case 5: return s[1] * ih2 + vm;
+      case 6: case 7: return s[2] * ih2 + vm;
+      default: return 0.0;
+    }
+  }
+  if ((r == 3 && c == 1) || (r == 6 && c == 2) || (r == 7 && c == 5)) return vm;
+  return 0.0;
+}
+
+template <int LANES, int N>
+__device__ __forceinline__ void up_coop_body(const DevBodies &B, const DevJoints &J, const DevTree &T, int j,
+                                             const StepParams &p, int *status, int l, unsigned gmask,
+                                             double *H, double (*Z)[6], double (*W)[5], double *Dg,
+                                             double *Eg) {
+  const int M = B.M, K = J.K;
+  const double ih2 = p.inv_h * p.inv_h;
+  // Hbar and f = Hbar ubar - sum_children v
+  {
+    const double s3[3] = {ldg(B.sig + j), ldg(B.sig + M + j), ldg(B.sig + 2 * (size_t)M + j)};
+    const double vm = ldg(B.vmu + j), vl = ldg(B.vlam + j), m = ldg(B.mass + j);
+    for (int e = l; e < 78; e += LANES) H[e] = hbar_entry(e, s3, vm, vl, m, ih2);
+    double ub[12], hu[12];
+    load12(B.ubar, M, j, ub);
+    hbar_apply(B, j, ih2, ub, hu);
+    const int c0 = T.cfirst[j], nch = T.ccount[j];
+    for (int a = l; a < 12; a += LANES) {
+      double f = 0.0;
+#pragma unroll
+      for (int q = 0; q < 12; ++q)
+        if (q == a) f = hu[q];
+      for (int c = c0; c < c0 + nch; ++c) f -= T.v[(size_t)a * M + c];
+      Z[a][0] = f;
+    }
+    __syncwarp(gmask);
+    // Hhat = Hbar + sum_children U U^T (child's U staged in W)
+    for (int c = c0; c < c0 + nch; ++c) {
+      const int Cc = J.type[T.pjoint[c]] == 0 ? 3 : 5;
+      for (int e = l; e < 12 * Cc; e += LANES) {
+        const int a = e / Cc, t = e % Cc;
+        W[a][t] = T.U[(size_t)(5 * a + t) * M + c];
+      }
+      __syncwarp(gmask);
+      for (int e = l; e < 78; e += LANES) {
+        int r, cc;
+        unpack12(e, r, cc);
+        double acc = 0.0;
+        for (int t = 0; t < Cc; ++t) acc += W[r][t] * W[cc][t];
+        H[e] += acc;
+      }
+      __syncwarp(gmask);
+    }
+  }
+  // Cholesky, right-looking, reciprocal diagonal in place
+  bool ok = true;
+  for (int c = 0; c < 12; ++c) {
+    if (l == 0) {
+      double d = H[p12(c, c)];
+      if (!(d > 0.0)) {
+        ok = false;
+        d = 1.0;
+      }
+      H[p12(c, c)] = rsqrt(d);
+    }
+    __syncwarp(gmask);
+    const double idc = H[p12(c, c)];
+    for (int r = c + 1 + l; r < 12; r += LANES) H[p12(r, c)] *= idc;
+    __syncwarp(gmask);
+    int cnt = 0;
+    for (int cc = c + 1; cc < 12; ++cc) {
+      const double lcc = H[p12(cc, c)];
+      for (int r = cc; r < 12; ++r, ++cnt)
+        if (cnt % LANES == l) H[p12(r, cc)] -= H[p12(r, c)] * lcc;
+    }
+    __syncwarp(gmask);
+  }
+  if (!ok && l == 0) set_status(status, ST_NOT_SPD);
+  // constraint rows of the parent joint on this body (rest frame), as
+  // right-hand sides 1..N and kept in W
+  const int kp = T.pjoint[j];
+  {
+    double R[9], E5[5][3], P2[2][3];
+    int pt5[5];
+    load_R(B.R, M, j, R);
+    joint_rows_rest(J, kp, T.pside[j], R, E5, P2, pt5);
+    for (int e = l; e < 12 * N; e += LANES) {
+      const int a = e / N, t = e % N;
+      const int blk = a / 3, a3 = a % 3;
+      const double v = (blk < 3 ? P2[pt5[t]][blk] : 1.0) * E5[t][a3];
+      W[a][t] = v;
+      Z[a][1 + t] = v;
+    }
+  }
+  __syncwarp(gmask);
+  // lanes solve the columns in turn: y (column 0) and X_t = Hhat^{-1} w_t
+  for (int col = l; col <= N; col += LANES) {
+    double x[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      double v = Z[i][col];
+#pragma unroll
+      for (int k = 0; k < i; ++k) v -= H[p12(i, k)] * x[k];
+      x[i] = v * H[p12(i, i)];
+    }
+#pragma unroll
+    for (int i = 11; i >= 0; --i) {
+      double v = x[i];
+#pragma unroll
+      for (int k = i + 1; k < 12; ++k) v -= H[p12(k, i)] * x[k];
+      x[i] = v * H[p12(i, i)];
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) Z[i][col] = x[i];
+  }
+  __syncwarp(gmask);
+  // D_rt = w_r . X_t (packed), e_t = w_t . y + C
+  constexpr int ND = N * (N + 1) / 2;
+  const double rr = p.residual_rhs ? 1.0 : 0.0;
+  for (int e = l; e < ND + N; e += LANES) {
+    if (e < ND) {
+      int r, t;
+      unpack12(e, r, t);
+      double d = 0.0;
+#pragma unroll
+      for (int a = 0; a < 12; ++a) d += W[a][r] * Z[a][1 + t];
+      Dg[e] = d;
+    } else {
+      const int t = e - ND;
+      double d = 0.0;
+#pragma unroll
+      for (int a = 0; a < 12; ++a) d += W[a][t] * Z[a][0];
+      Eg[t] = d + rr * J.c[(size_t)t * K + kp];
+    }
+  }
+  // X and y out
+  for (int e = l; e < 12 * 6; e += LANES) {
+    const int a = e / 6, t = e % 6;
+    if (t == 0) T.y[(size_t)a * M + j] = Z[a][0];
+    else if (t <= 5) T.X[(size_t)(5 * a + t - 1) * M + j] = (t - 1 < N) ? Z[a][t] : 0.0;
+  }
+  __syncwarp(gmask);
+  // Cholesky of D (every lane), reciprocal diagonal
+  double D[ND], ev[N];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) D[i] = Dg[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) ev[i] = Eg[i];
+  bool okd = true;
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    double sum = D[p12(c, c)];
+#pragma unroll
+    for (int k = 0; k < c; ++k) sum -= D[p12(c, k)] * D[p12(c, k)];
+    if (!(sum > 0.0)) {
+      okd = false;
+      sum = 1.0;
+    }
+    const double id = rsqrt(sum);
+    D[p12(c, c)] = id;
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      double t = D[p12(r, c)];
+#pragma unroll
+      for (int k = 0; k < c; ++k) t -= D[p12(r, k)] * D[p12(c, k)];
+      D[p12(r, c)] = t * id;
+    }
+  }
+  if (!okd && l == 0) set_status(status, ST_NOT_SPD);
+  if (l == 0) {
+#pragma unroll
+    for (int i = 0; i < 15; ++i) T.LD[(size_t)i * M + j] = i < ND ? D[i] : 0.0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) T.e[(size_t)r * M + j] = r < N ? ev[r] : 0.0;
+  }
+  // contribution to the parent (its rest frame): U = Pbar^T L_D^{-T}, v = U L_D^{-1} e
+  const int par = T.parent[j];
+  double Rp[9], Ep[5][3], Pp[2][3];
+  int ptp[5];
+  load_R(B.R, M, par, Rp);
+  joint_rows_rest(J, kp, 1 - T.pside[j], Rp, Ep, Pp, ptp);
+  double wl[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double s = ev[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= D[p12(i, k)] * wl[k];
+    wl[i] = s * D[p12(i, i)];
+  }
+  for (int a = l; a < 12; a += LANES) {
+    const int blk = a / 3, a3 = a % 3;
+    double col[N], z[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) col[r] = (blk < 3 ? Pp[ptp[r]][blk] : 1.0) * Ep[r][a3];
+    double vv = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = col[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s -= D[p12(i, k)] * z[k];
+      z[i] = s * D[p12(i, i)];
+      T.U[(size_t)(5 * a + i) * M + j] = z[i];
+      vv += z[i] * wl[i];
+    }
+#pragma unroll
+    for (int i = N; i < 5; ++i) T.U[(size_t)(5 * a + i) * M + j] = 0.0;
+    T.v[(size_t)a * M + j] = vv;
+  }
+}
+
+template <int LANES>
+__global__ void __launch_bounds__(CG * LANES) k_tree_up_coop(DevBodies B, DevJoints J, DevTree T, int lo,
+                                                             int hi, StepParams p, int *status) {
+  __shared__ double sH[CG][78];
+  __shared__ double sZ[CG][12][6];
+  __shared__ double sW[CG][12][5];
+  __shared__ double sD[CG][15];
+  __shared__ double sE[CG][5];
+  const int g = threadIdx.x / LANES, l = threadIdx.x % LANES;
+  const unsigned gmask = (LANES == 32) ? 0xffffffffu
+                                       : (((1u << LANES) - 1u) << (((threadIdx.x & 31) / LANES) * LANES));
+  const int i = lo + blockIdx.x * CG + g;
+  if (i >= hi) return;  // uniform within the group
+  const int j = T.order[i];
+  if (T.parent[j] < 0) return;
+  if (J.type[T.pjoint[j]] == 0)
+    up_coop_body<LANES, 3>(B, J, T, j, p, status, l, gmask, sH[g], sZ[g], sW[g], sD[g], sE[g]);
+  else
+    up_coop_body<LANES, 5>(B, J, T, j, p, status, l, gmask, sH[g], sZ[g], sW[g], sD[g], sE[g]);
+}
+
 // each root variant compiled on its own (separate register allocation)
 template <int N>
 __device__ __noinline__ void up_root(const DevBodies &B, const DevJoints &J, const DevTree &T, int j,
@@ -603,12 +862,20 @@ __global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, Dev
 }
 
 void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int mid,
-                    int hi, bool roots, const StepParams &p, int *status, cudaStream_t s) {
+                    int hi, bool roots, const StepParams &p, int *status, cudaStream_t s, int variant) {
   if (roots) {
     if (hi > lo) k_tree_up_root<<<(hi - lo + TUP - 1) / TUP, TUP, 0, s>>>(B, J, T, lo, hi, p, status);
     return;
   }
-  if (mid > lo) k_tree_up_inner<<<(mid - lo + TUP - 1) / TUP, TUP, 0, s>>>(B, J, T, lo, mid, p, status);
+  if (mid > lo) {
+    const int n = mid - lo;
+    if (variant == TREE_UP_COOP8)
+      k_tree_up_coop<8><<<(n + CG - 1) / CG, CG * 8, 0, s>>>(B, J, T, lo, mid, p, status);
+    else if (variant == TREE_UP_COOP4)
+      k_tree_up_coop<4><<<(n + CG - 1) / CG, CG * 4, 0, s>>>(B, J, T, lo, mid, p, status);
+    else
+      k_tree_up_inner<<<(n + TUP - 1) / TUP, TUP, 0, s>>>(B, J, T, lo, mid, p, status);
+  }
   if (hi > mid) k_tree_up_leaf<<<(hi - mid + 127) / 128, 128, 0, s>>>(B, J, T, mid, hi, p, status);
 }
 

@@ -68,6 +68,7 @@ struct mabd_ctx {
   double *h_scal = nullptr;  // pinned [8]
   std::vector<int32_t> tree_lvl;  // level offsets (internal body order)
   std::vector<int32_t> tree_mid;  // per level: first leaf (bodies before it have children)
+  std::vector<int32_t> tree_variant;  // per level: TREE_UP_* chosen by the tuner
   double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
   int *d_status = nullptr;
   unsigned long long *d_max = nullptr;
@@ -669,6 +670,64 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
   return MABD_OK;
 }
 
+}  // extern "C"
+
+// Level schedule of the tree's upward pass.  Each level's bodies with
+// children can be eliminated one per thread or by a group of 8 or 4 lanes
+// per body (k_tree.cu); which is faster depends on how many such bodies the
+// level has and on their rows.  The tuner runs the body and joint kernels
+// on the initial state, then, deepest level first, times every variant on
+// the level (best of two CUDA-event timings) and keeps the fastest; every
+// variant computes the same outputs, so the level's results are in place for
+// the next level up.  MABD_TREE_VARIANT=0|1|2 forces one variant everywhere.
+static mabd_status tune_tree(mabd_ctx *ctx) {
+  const auto &lv = ctx->tree_lvl;
+  const auto &mid = ctx->tree_mid;
+  const int nl = (int)lv.size() - 1;
+  ctx->tree_variant.assign(std::max(nl, 0), TREE_UP_THREAD);
+  if (const char *f = std::getenv("MABD_TREE_VARIANT")) {
+    const int v = std::atoi(f);
+    if (v >= 0 && v < TREE_UP_NVARIANTS) ctx->tree_variant.assign(std::max(nl, 0), v);
+    return MABD_OK;
+  }
+  cudaStream_t s = ctx->stream;
+  const StepParams &p = ctx->sp;
+  launch_body_prep(ctx->B, p, ctx->d_status, s);
+  launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int l = nl - 1; l >= 1; --l) {
+    if (mid[l] <= lv[l]) {
+      launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s);
+      continue;
+    }
+    float best = 1e30f;
+    for (int v = 0; v < TREE_UP_NVARIANTS; ++v)
+      for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaEventRecord(e0, s));
+        launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s, v);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          ctx->tree_variant[l] = v;
+        }
+      }
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+  CK(cudaStreamSynchronize(s));
+  return MABD_OK;
+}
+
+extern "C" {
+
 mabd_status mabd_prefactor(mabd_ctx *ctx) {
   dbg_pending("enter mabd_prefactor");
   if (!ctx) return MABD_ERR_INVALID_ARG;
@@ -1121,6 +1180,10 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   ctx->sp.inv_h = 1.0 / h;
   for (int a = 0; a < 3; ++a) ctx->sp.g[a] = ctx->cfg.gravity[a];
   ctx->sp.residual_rhs = ctx->cfg.residual_rhs ? 1 : 0;
+  if (solver == MABD_SOLVER_TREE && K > 0) {
+    mabd_status st = tune_tree(ctx);
+    if (st) return st;
+  }
   ctx->frozen = true;
   return MABD_OK;
 }
@@ -1198,7 +1261,8 @@ static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s) {
     const auto &mid = ctx->tree_mid;
     for (int l = nl - 1; l >= 0; --l)
       run(ctx, "tree_up", [&] {
-        launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s);
+        launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s,
+                       ctx->tree_variant.empty() ? TREE_UP_THREAD : ctx->tree_variant[l]);
       });
     for (int l = 0; l < nl; ++l)
       run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
@@ -1829,6 +1893,16 @@ mabd_status lpc_losses(mabd_lpc *t, int n) {
 }  // namespace
 
 extern "C" {
+
+mabd_status mabd_tree_schedule(mabd_ctx *ctx, int32_t *counts) {
+  if (!ctx || !counts) return MABD_ERR_INVALID_ARG;
+  if (!ctx->frozen) return MABD_ERR_BAD_STATE;
+  for (int v = 0; v < TREE_UP_NVARIANTS; ++v) counts[v] = 0;
+  const int nl = (int)ctx->tree_variant.size();
+  for (int l = 1; l < nl; ++l)
+    if (ctx->tree_mid[l] > ctx->tree_lvl[l]) ++counts[ctx->tree_variant[l]];
+  return MABD_OK;
+}
 
 int32_t mabd_lpc_num_params(void) { return LPC_NPARAM; }
 

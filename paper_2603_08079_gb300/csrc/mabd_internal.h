@@ -311,8 +311,12 @@ void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence 
 // level [lo, hi) of the body order: T.order[lo, mid) lists its bodies with
 // children and T.order[mid, hi) its leaves; the roots' level (roots = true)
 // is run by one kernel
+// variants of the upward pass for the bodies with children: one thread per
+// body, or a group of 8 or 4 lanes per body (chosen per level by the tuner)
+enum { TREE_UP_THREAD = 0, TREE_UP_COOP8 = 1, TREE_UP_COOP4 = 2, TREE_UP_NVARIANTS = 3 };
 void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int mid,
-                    int hi, bool roots, const StepParams &p, int *status, cudaStream_t s);
+                    int hi, bool roots, const StepParams &p, int *status, cudaStream_t s,
+                    int variant = TREE_UP_THREAD);
 void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,
                       const StepParams &p, int *status, cudaStream_t s);
 

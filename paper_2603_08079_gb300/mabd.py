@@ -72,7 +72,7 @@ EXPORTS = ["mabd_config_default", "mabd_create", "mabd_add_bodies", "mabd_add_jo
            "mabd_kernel_times", "mabd_destroy", "mabd_status_string", "mabd_error_detail",
            "mabd_lpc_num_params", "mabd_set_preconditioner", "mabd_lpc_fallbacks",
            "mabd_lpc_create", "mabd_lpc_capture", "mabd_lpc_batch_blocks", "mabd_lpc_loss_grad",
-           "mabd_lpc_train", "mabd_lpc_destroy"]
+           "mabd_lpc_train", "mabd_lpc_destroy", "mabd_tree_schedule"]
 
 
 def library_path() -> str:
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True):
     lib.mabd_lpc_loss_grad.argtypes = [P, i32, P, i32, i32, P, u64, C.POINTER(C.c_double), P]
     lib.mabd_lpc_train.argtypes = [P, P, i32, i32, C.c_float, i32, u64, P]
     lib.mabd_lpc_destroy.argtypes = [P]
+    lib.mabd_tree_schedule.argtypes = [P, P]
     for f in EXPORTS:
         if f not in ("mabd_config_default", "mabd_status_string", "mabd_error_detail"):
             getattr(lib, f).restype = i32
@@ -276,6 +277,12 @@ class Solver:
         p = np.ascontiguousarray(params, dtype=np.float32)
         assert p.size == lpc_num_params()
         self._check("mabd_set_preconditioner", self._lib.mabd_set_preconditioner(self.ctx, _ptr(p)))
+
+    def tree_schedule(self) -> dict:
+        """Levels of the tree's upward pass per variant (thread, 8 lanes, 4 lanes)."""
+        c = np.zeros(3, dtype=np.int32)
+        self._check("mabd_tree_schedule", self._lib.mabd_tree_schedule(self.ctx, _ptr(c)))
+        return {"thread": int(c[0]), "lanes8": int(c[1]), "lanes4": int(c[2])}
 
     def lpc_fallbacks(self) -> int:
         n = C.c_int32(0)

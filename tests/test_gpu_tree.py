@@ -85,3 +85,53 @@ def test_full_size_tree(ora):
     sc = scenes.random_tree(262144, seed=2)
     e_qd, e_lam, st, ost = assert_parity(ora, sc, sc["q"], sc["qdot"])
     assert st["joint_residual"] < 1e-6  # Table 1, tree rows
+
+
+@pytest.fixture
+def forced_variant():
+    """Sets MABD_TREE_VARIANT for the contexts created inside the test."""
+    import os
+    old = os.environ.get("MABD_TREE_VARIANT")
+
+    def set_(v):
+        os.environ["MABD_TREE_VARIANT"] = str(v)
+
+    yield set_
+    if old is None:
+        os.environ.pop("MABD_TREE_VARIANT", None)
+    else:
+        os.environ["MABD_TREE_VARIANT"] = old
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_every_upward_variant(ora, forced_variant, variant):
+    """Each elimination variant of the bodies with children (one thread per
+    body, 8 lanes, 4 lanes) alone: hinge and mixed trees, a root with two
+    world joints, a fixed-base assembly batch."""
+    need_gpu()
+    forced_variant(variant)
+    cases = [scenes.random_tree(3000, seed=2),
+             scenes.random_small("tree", 30, seed=7),
+             scenes.assemblies(16, seed=3)]
+    for sc in cases:
+        s = gpu_solver(sc, solver="tree")
+        try:
+            sched = s.tree_schedule()
+            assert sum(sched.values()) > 0 and list(sched.values())[variant] == sum(sched.values())
+            q, qd = scenes.perturb_state(sc, seed=11, rot=0.05, vel=0.3)
+            assert_parity(ora, sc, q, qd, solver=s)
+        finally:
+            s.close()
+
+
+def test_tuned_schedule(ora):
+    """The tuner picks a variant per level; the tuned step keeps parity."""
+    need_gpu()
+    sc = scenes.random_tree(20000, seed=2)
+    s = gpu_solver(sc, solver="tree")
+    try:
+        sched = s.tree_schedule()
+        assert sum(sched.values()) > 0
+        assert_parity(ora, sc, sc["q"], sc["qdot"], solver=s)
+    finally:
+        s.close()
