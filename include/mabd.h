@@ -226,10 +226,14 @@ mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M, const mab
                                     int32_t K, const mabd_joint_desc *joints, double *q_out,
                                     double *qdot_out, double *lambda_out);
 
-/* Level schedule of a tree context's upward pass (tuned at mabd_prefactor
-   by timing each variant on each level; MABD_TREE_VARIANT=0|1|2 in the
-   environment forces one): counts[0..2] = number of levels with bodies that
-   have children eliminated one per thread, by 8 lanes, by 4 lanes per body. */
+/* Schedule of a tree context's elimination, tuned at mabd_prefactor by
+   timing the candidates on the scene's first state: counts[0..2] = number
+   of levels whose bodies with children are eliminated one per thread, by 8
+   lanes, by 4 lanes per body (level-scheduled path); counts[3] = 0 for the
+   level-scheduled path (one launch per level), or 8 / 4 for the persistent
+   kernel (one block per tree, both passes in one launch, that many lanes per
+   body with children).  MABD_TREE_VARIANT=0|1|2 and MABD_TREE_MODE=
+   levels|forest8|forest4 in the environment force a choice (tests). */
 mabd_status mabd_tree_schedule(mabd_ctx *ctx, int32_t *counts);
 
 /* ---- Learned block preconditioner of the mixed-precision PCG path -------

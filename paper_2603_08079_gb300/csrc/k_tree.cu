@@ -803,10 +803,10 @@ __device__ __forceinline__ void down_body(const DevBodies &B, const DevJoints &J
   }
 }
 
-__global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, DevTree T, int lo,
-                                                   int hi, StepParams p) {
-  const int j = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= hi) return;
+// downward pass of body j: lambda of its parent joint (or of a root's
+// one-sided joints), dq, and the state update
+__device__ __forceinline__ void tree_down_one(const DevBodies &B, const DevJoints &J, const DevTree &T,
+                                              int j, const StepParams &p) {
   const int M = B.M, K = J.K;
   const int par = T.parent[j];
   double dqb[12];
@@ -858,6 +858,123 @@ __global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, Dev
       B.q[o] += dq[a];
       B.qd[o] = dq[a] * p.inv_h;
     }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, DevTree T, int lo,
+                                                   int hi, StepParams p) {
+  const int j = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < hi) tree_down_one(B, J, T, j, p);
+}
+
+// ---------------------------------------------------------------------------
+// persistent forest kernel: one block per tree, both passes
+// ---------------------------------------------------------------------------
+constexpr int FT = 128;  // threads per block
+
+template <int LANES>
+constexpr size_t forest_smem() {
+  return sizeof(double) * (78 * TUP + (FT / LANES) * (78 + 12 * 6 + 12 * 5 + 15 + 5));
+}
+
+// each per-body path compiled on its own (separate register allocation)
+template <int LANES, int N>
+__device__ __noinline__ void coop_one(const DevBodies &B, const DevJoints &J, const DevTree &T, int j,
+                                      const StepParams &p, int *status, int l, unsigned gmask, double *H,
+                                      double (*Z)[6], double (*W)[5], double *Dg, double *Eg) {
+  up_coop_body<LANES, N>(B, J, T, j, p, status, l, gmask, H, Z, W, Dg, Eg);
+}
+
+template <int N>
+__device__ __noinline__ void leaf_one(const DevBodies &B, const DevJoints &J, const DevTree &T, int j,
+                                      const StepParams &p, int *status) {
+  SmemL L{nullptr};
+  up_body<N, false>(B, J, T, j, p, status, L);
+}
+
+__device__ __noinline__ void down_one(const DevBodies &B, const DevJoints &J, const DevTree &T, int j,
+                                      const StepParams &p) {
+  tree_down_one(B, J, T, j, p);
+}
+
+template <int LANES>
+__global__ void __launch_bounds__(FT) k_tree_forest(DevBodies B, DevJoints J, DevTree T, DevForest F,
+                                                    StepParams p, int *status) {
+  extern __shared__ double smem[];
+  constexpr int NG = FT / LANES;
+  double *sL = smem;                       // root's dense factor, stride TUP
+  double *gbase = smem + 78 * TUP;
+  const int g = threadIdx.x / LANES, l = threadIdx.x % LANES;
+  const unsigned gmask = (((1u << LANES) - 1u) << (((threadIdx.x & 31) / LANES) * LANES));
+  double *H = gbase + (size_t)g * (78 + 72 + 60 + 15 + 5);
+  double(*Z)[6] = reinterpret_cast<double(*)[6]>(H + 78);
+  double(*W)[5] = reinterpret_cast<double(*)[5]>(H + 78 + 72);
+  double *Dg = H + 78 + 72 + 60, *Eg = Dg + 15;
+  for (int t = blockIdx.x; t < F.ntrees; t += gridDim.x) {
+    const int r0 = F.tlvl[t], nl = F.tnl[t];
+    // upward, deepest level first
+    for (int d = nl - 1; d >= 1; --d) {
+      const int lo = F.lo[r0 + d], mid = F.mid[r0 + d], hi = F.lo[r0 + d + 1];
+      for (int i = lo + g; i < mid; i += NG) {
+        const int j = F.order[i];
+        if (J.type[T.pjoint[j]] == 0) coop_one<LANES, 3>(B, J, T, j, p, status, l, gmask, H, Z, W, Dg, Eg);
+        else coop_one<LANES, 5>(B, J, T, j, p, status, l, gmask, H, Z, W, Dg, Eg);
+      }
+      for (int i = mid + threadIdx.x; i < hi; i += FT) {
+        const int j = F.order[i];
+        if (J.type[T.pjoint[j]] == 0) leaf_one<3>(B, J, T, j, p, status);
+        else leaf_one<5>(B, J, T, j, p, status);
+      }
+      __syncthreads();
+    }
+    // the root
+    if (threadIdx.x == 0) {
+      const int j = F.order[F.lo[r0]];
+      const int rid = T.root_id[j];
+      int n = 0;
+      for (int w = 0; w < 2; ++w) {
+        const int k = T.root_joint[(size_t)w * T.nroots + rid];
+        if (k >= 0) n += J.type[k] == 0 ? 3 : 5;
+      }
+      SmemL L{sL};
+      switch (n) {
+        case 0: up_root<0>(B, J, T, j, p, status, L); break;
+        case 3: up_root<3>(B, J, T, j, p, status, L); break;
+        case 5: up_root<5>(B, J, T, j, p, status, L); break;
+        case 6: up_root<6>(B, J, T, j, p, status, L); break;
+        case 8: up_root<8>(B, J, T, j, p, status, L); break;
+        default: up_root<10>(B, J, T, j, p, status, L); break;
+      }
+    }
+    __syncthreads();
+    // downward, root first
+    for (int d = 0; d < nl; ++d) {
+      const int lo = F.lo[r0 + d], hi = F.lo[r0 + d + 1];
+      for (int i = lo + threadIdx.x; i < hi; i += FT) down_one(B, J, T, F.order[i], p);
+      __syncthreads();
+    }
+  }
+}
+
+void launch_tree_forest(const DevBodies &B, const DevJoints &J, const DevTree &T, const DevForest &F,
+                        const StepParams &p, int *status, cudaStream_t s, int lanes) {
+  if (F.ntrees <= 0) return;
+  if (lanes == 4) {
+    constexpr size_t sm = forest_smem<4>();
+    static bool set = false;
+    if (!set) {
+      cudaFuncSetAttribute(k_tree_forest<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      set = true;
+    }
+    k_tree_forest<4><<<F.ntrees, FT, sm, s>>>(B, J, T, F, p, status);
+  } else {
+    constexpr size_t sm = forest_smem<8>();
+    static bool set = false;
+    if (!set) {
+      cudaFuncSetAttribute(k_tree_forest<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      set = true;
+    }
+    k_tree_forest<8><<<F.ntrees, FT, sm, s>>>(B, J, T, F, p, status);
   }
 }
 

@@ -69,6 +69,8 @@ struct mabd_ctx {
   std::vector<int32_t> tree_lvl;  // level offsets (internal body order)
   std::vector<int32_t> tree_mid;  // per level: first leaf (bodies before it have children)
   std::vector<int32_t> tree_variant;  // per level: TREE_UP_* chosen by the tuner
+  DevForest F{};                       // the forest tree by tree (persistent kernel)
+  int tree_mode = 0;                   // 0: level-scheduled launches; 8 or 4: persistent kernel, lanes
   double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
   int *d_status = nullptr;
   unsigned long long *d_max = nullptr;
@@ -679,16 +681,22 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
 // on the initial state, then, deepest level first, times every variant on
 // the level (best of two CUDA-event timings) and keeps the fastest; every
 // variant computes the same outputs, so the level's results are in place for
-// the next level up.  MABD_TREE_VARIANT=0|1|2 forces one variant everywhere.
+// the next level up.  Then the whole elimination with that schedule is
+// timed against the persistent forest kernel (one block per tree, both
+// passes in one launch) and the faster is kept.  MABD_TREE_VARIANT=0|1|2
+// forces one level variant (and the level path); MABD_TREE_MODE=levels|
+// forest8|forest4 forces the path.
 static mabd_status tune_tree(mabd_ctx *ctx) {
   const auto &lv = ctx->tree_lvl;
   const auto &mid = ctx->tree_mid;
   const int nl = (int)lv.size() - 1;
   ctx->tree_variant.assign(std::max(nl, 0), TREE_UP_THREAD);
-  if (const char *f = std::getenv("MABD_TREE_VARIANT")) {
-    const int v = std::atoi(f);
+  const char *fv = std::getenv("MABD_TREE_VARIANT");
+  if (fv) {
+    const int v = std::atoi(fv);
     if (v >= 0 && v < TREE_UP_NVARIANTS) ctx->tree_variant.assign(std::max(nl, 0), v);
-    return MABD_OK;
+    // a forced level variant also forces the level-scheduled path
+    if (!std::getenv("MABD_TREE_MODE")) return MABD_OK;
   }
   cudaStream_t s = ctx->stream;
   const StepParams &p = ctx->sp;
@@ -697,7 +705,7 @@ static mabd_status tune_tree(mabd_ctx *ctx) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (int l = nl - 1; l >= 1; --l) {
+  for (int l = nl - 1; l >= 1 && !fv; --l) {
     if (mid[l] <= lv[l]) {
       launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s);
       continue;
@@ -716,6 +724,43 @@ static mabd_status tune_tree(mabd_ctx *ctx) {
           ctx->tree_variant[l] = v;
         }
       }
+  }
+  // whole elimination: the tuned level schedule against the persistent
+  // kernel (8 or 4 lanes per body with children); the downward pass moves
+  // the state, so it is saved and put back around every trial
+  const int M = ctx->B.M;
+  const char *fm = std::getenv("MABD_TREE_MODE");
+  if (fm) {
+    ctx->tree_mode = std::strcmp(fm, "forest8") == 0 ? 8 : (std::strcmp(fm, "forest4") == 0 ? 4 : 0);
+  } else if (ctx->F.ntrees > 0) {
+    double *sq = nullptr;
+    CK(cudaMallocAsync((void **)&sq, 24 * (size_t)M * sizeof(double), s));
+    CK(cudaMemcpyAsync(sq, ctx->B.q, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(sq + 12 * (size_t)M, ctx->B.qd, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+    float best = 1e30f;
+    for (int mode : {0, 8, 4})
+      for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaEventRecord(e0, s));
+        if (mode == 0) {
+          for (int l = nl - 1; l >= 0; --l)
+            launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s,
+                           ctx->tree_variant[l]);
+          for (int l = 0; l < nl; ++l) launch_tree_down(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s);
+        } else {
+          launch_tree_forest(ctx->B, ctx->J, ctx->T, ctx->F, p, ctx->d_status, s, mode);
+        }
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          ctx->tree_mode = mode;
+        }
+        CK(cudaMemcpyAsync(ctx->B.q, sq, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->B.qd, sq + 12 * (size_t)M, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+      }
+    CK(cudaFreeAsync(sq, s));
   }
   CK(cudaStreamSynchronize(s));
   cudaEventDestroy(e0);
@@ -1174,6 +1219,60 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     }
     CK(up(dids, ids.data(), ids.size() * 4));
     ctx->T.order = dids;
+    // the same bodies tree by tree: per tree and depth, bodies with children
+    // first, then leaves; a sentinel record closes each tree
+    {
+      const int nlev = (int)tord.lvl_off.size() - 1;
+      const int ntrees = nlev > 0 ? tord.lvl_off[1] - tord.lvl_off[0] : 0;
+      std::vector<int32_t> root_of(M, -1), depth(M, 0);
+      for (int l = 0; l < nlev; ++l)
+        for (int i = tord.lvl_off[l]; i < tord.lvl_off[l + 1]; ++i) {
+          depth[i] = l;
+          root_of[i] = tord.parent[i] < 0 ? i : root_of[tord.parent[i]];
+        }
+      std::vector<std::vector<std::vector<int32_t>>> bucket(ntrees);
+      for (int l = 0; l < nlev; ++l)
+        for (int i = tord.lvl_off[l]; i < tord.lvl_off[l + 1]; ++i) {
+          auto &bt = bucket[root_of[i] - tord.lvl_off[0]];
+          if ((int)bt.size() <= l) bt.resize(l + 1);
+          bt[l].push_back(i);
+        }
+      std::vector<int32_t> tlvl(std::max(ntrees, 1)), tnl(std::max(ntrees, 1)), flo, fmid, ford;
+      for (int t = 0; t < ntrees; ++t) {
+        tlvl[t] = (int32_t)flo.size();
+        tnl[t] = (int32_t)bucket[t].size();
+        for (auto &lvl : bucket[t]) {
+          flo.push_back((int32_t)ford.size());
+          for (int i : lvl)
+            if (tord.ccount[i] > 0) ford.push_back(i);
+          fmid.push_back((int32_t)ford.size());
+          for (int i : lvl)
+            if (tord.ccount[i] == 0) ford.push_back(i);
+        }
+        flo.push_back((int32_t)ford.size());
+        fmid.push_back((int32_t)ford.size());
+      }
+      int32_t *d1 = dnew<int32_t>(ctx, tlvl.size(), ok), *d2 = dnew<int32_t>(ctx, tnl.size(), ok);
+      int32_t *d3 = dnew<int32_t>(ctx, std::max<size_t>(flo.size(), 1), ok);
+      int32_t *d4 = dnew<int32_t>(ctx, std::max<size_t>(fmid.size(), 1), ok);
+      int32_t *d5 = dnew<int32_t>(ctx, std::max<size_t>(ford.size(), 1), ok);
+      if (!ok) {
+        free_all(ctx);
+        return MABD_ERR_OUT_OF_MEMORY;
+      }
+      CK(up(d1, tlvl.data(), tlvl.size() * 4));
+      CK(up(d2, tnl.data(), tnl.size() * 4));
+      CK(up(d3, flo.data(), flo.size() * 4));
+      CK(up(d4, fmid.data(), fmid.size() * 4));
+      CK(up(d5, ford.data(), ford.size() * 4));
+      DevForest &F = ctx->F;
+      F.ntrees = ntrees;
+      F.tlvl = d1;
+      F.tnl = d2;
+      F.lo = d3;
+      F.mid = d4;
+      F.order = d5;
+    }
   }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->sp.h = h;
@@ -1255,6 +1354,10 @@ static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s) {
   if (ctx->solver == MABD_SOLVER_CHAIN) {
     run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
     enqueue_cr(ctx, s, false, ctx->J, nullptr);
+  } else if (ctx->solver == MABD_SOLVER_TREE && ctx->tree_mode != 0) {
+    run(ctx, "tree_forest", [&] {
+      launch_tree_forest(ctx->B, ctx->J, ctx->T, ctx->F, p, ctx->d_status, s, ctx->tree_mode);
+    });
   } else if (ctx->solver == MABD_SOLVER_TREE) {
     const auto &lv = ctx->tree_lvl;
     const int nl = (int)lv.size() - 1;
@@ -1649,6 +1752,7 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
   static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "mx_body_prep", "mx_joint_prep",
                                 "mx_chain_gram", "mx_res_body", "mx_res_joint", "cr_rhs", "mx_final",
                                 "p32_setup", "p32_iteration", "p32_finish", "lpc_blocks", "lpc_forward",
+                                "tree_forest",
                                 "cr_level", "cr_reduce", "cr_combine",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
                                 "pcg_iteration", "backprop", "residuals"};
@@ -1901,6 +2005,7 @@ mabd_status mabd_tree_schedule(mabd_ctx *ctx, int32_t *counts) {
   const int nl = (int)ctx->tree_variant.size();
   for (int l = 1; l < nl; ++l)
     if (ctx->tree_mid[l] > ctx->tree_lvl[l]) ++counts[ctx->tree_variant[l]];
+  counts[3] = ctx->tree_mode;
   return MABD_OK;
 }
 

@@ -125,6 +125,19 @@ struct DevTree {
   double *re;                 // [10][nroots]
 };
 
+// the forest regrouped tree by tree for the persistent kernel: tree t has
+// levels lvl[t] .. lvl[t] + nlvl[t] - 1 (records), record r covers
+// order[lo[r], lo[r + 1]) with its bodies with children first (up to mid[r]);
+// every tree's record list ends with a sentinel record
+struct DevForest {
+  int32_t ntrees;
+  const int32_t *tlvl;   // [ntrees] first record of tree t
+  const int32_t *tnl;    // [ntrees] levels of tree t
+  const int32_t *lo;     // [records] start of a level in order (sentinels: end of the tree)
+  const int32_t *mid;    // [records] first leaf of the level
+  const int32_t *order;  // [free bodies] body ids
+};
+
 // dual-space preconditioned conjugate gradients (graphs).  Vectors are
 // [5][K] (rows beyond C_k stay zero); scalars live on the device.
 struct DevPCG {
@@ -311,6 +324,10 @@ void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence 
 // level [lo, hi) of the body order: T.order[lo, mid) lists its bodies with
 // children and T.order[mid, hi) its leaves; the roots' level (roots = true)
 // is run by one kernel
+// whole tree elimination (upward and downward passes) of every tree of the
+// forest in one launch, one block per tree; lanes = 8 or 4 per body with children
+void launch_tree_forest(const DevBodies &B, const DevJoints &J, const DevTree &T, const DevForest &F,
+                        const StepParams &p, int *status, cudaStream_t s, int lanes);
 // variants of the upward pass for the bodies with children: one thread per
 // body, or a group of 8 or 4 lanes per body (chosen per level by the tuner)
 enum { TREE_UP_THREAD = 0, TREE_UP_COOP8 = 1, TREE_UP_COOP4 = 2, TREE_UP_NVARIANTS = 3 };

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2603_08079_gb300 import scenes
-from parity_util import assert_parity, gpu_solver, need_gpu
+from parity_util import assert_parity, gpu_solver, need_gpu, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -89,18 +89,25 @@ def test_full_size_tree(ora):
 
 @pytest.fixture
 def forced_variant():
-    """Sets MABD_TREE_VARIANT for the contexts created inside the test."""
+    """Sets MABD_TREE_VARIANT (or MABD_TREE_MODE) for the contexts created
+    inside the test."""
     import os
-    old = os.environ.get("MABD_TREE_VARIANT")
+    keys = ("MABD_TREE_VARIANT", "MABD_TREE_MODE")
+    old = {k: os.environ.get(k) for k in keys}
 
-    def set_(v):
-        os.environ["MABD_TREE_VARIANT"] = str(v)
+    def set_(v, key="MABD_TREE_VARIANT"):
+        os.environ[key] = str(v)
 
     yield set_
-    if old is None:
-        os.environ.pop("MABD_TREE_VARIANT", None)
-    else:
-        os.environ["MABD_TREE_VARIANT"] = old
+    for k, v in old.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+
+
+def level_counts(sched):
+    return [sched["thread"], sched["lanes8"], sched["lanes4"]]
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2])
@@ -117,21 +124,50 @@ def test_every_upward_variant(ora, forced_variant, variant):
         s = gpu_solver(sc, solver="tree")
         try:
             sched = s.tree_schedule()
-            assert sum(sched.values()) > 0 and list(sched.values())[variant] == sum(sched.values())
+            c = level_counts(sched)
+            assert sched["path"] == "levels" and sum(c) > 0 and c[variant] == sum(c)
             q, qd = scenes.perturb_state(sc, seed=11, rot=0.05, vel=0.3)
             assert_parity(ora, sc, q, qd, solver=s)
         finally:
             s.close()
 
 
-def test_tuned_schedule(ora):
-    """The tuner picks a variant per level; the tuned step keeps parity."""
+@pytest.mark.parametrize("mode", ["forest8", "forest4"])
+def test_persistent_forest_kernel(ora, forced_variant, mode):
+    """One block per tree, both passes in one launch: forests of fixed-base
+    assemblies (many small trees), a single large tree, mixed joints, and
+    several steps in one call."""
     need_gpu()
-    sc = scenes.random_tree(20000, seed=2)
+    forced_variant(mode, "MABD_TREE_MODE")
+    for sc in (scenes.assemblies(64, seed=3), scenes.random_tree(3000, seed=2),
+               scenes.random_small("free", 9, seed=4), scenes.random_small("tree", 30, seed=7)):
+        s = gpu_solver(sc, solver="tree")
+        try:
+            assert s.tree_schedule()["path"] == mode
+            q, qd = scenes.perturb_state(sc, seed=5, rot=0.05, vel=0.3)
+            assert_parity(ora, sc, q, qd, solver=s)
+        finally:
+            s.close()
+    sc = scenes.assemblies(32, seed=5)
     s = gpu_solver(sc, solver="tree")
     try:
-        sched = s.tree_schedule()
-        assert sum(sched.values()) > 0
-        assert_parity(ora, sc, sc["q"], sc["qdot"], solver=s)
+        s.step(20)
+        q, qd = s.get_state()
     finally:
         s.close()
+    oq, oqd, _, _ = ora.run(sc, 20)
+    assert rel(qd, oqd) < 1e-7
+
+
+def test_tuned_schedule(ora):
+    """The tuner picks a variant per level and a path; the tuned step keeps
+    parity."""
+    need_gpu()
+    for sc in (scenes.random_tree(20000, seed=2), scenes.assemblies(256, seed=3)):
+        s = gpu_solver(sc, solver="tree")
+        try:
+            sched = s.tree_schedule()
+            assert sum(level_counts(sched)) > 0 and sched["path"] in ("levels", "forest8", "forest4")
+            assert_parity(ora, sc, sc["q"], sc["qdot"], solver=s)
+        finally:
+            s.close()
