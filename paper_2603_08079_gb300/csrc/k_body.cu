@@ -355,7 +355,53 @@ __global__ void __launch_bounds__(128) k_residuals(DevBodies B, DevJoints J, Ste
   }
 }
 
+// ---------------------------------------------------------------------------
+// state transfer between the caller's layout and the device layout
+// ---------------------------------------------------------------------------
+// stage: the caller's arrays as given, q then qdot, each [M][12] in user body
+// order; the device keeps [12][M] in internal order (boi: internal -> user)
+__global__ void k_state_check(const double *stage, size_t n, int *flag) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(stage[i])) atomicOr(flag, 1);
+}
+
+__global__ void __launch_bounds__(128) k_state_in(const double *stage, const int32_t *boi, DevBodies B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int M = B.M;
+  if (i >= M) return;
+  const size_t u = (size_t)boi[i];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    B.q[(size_t)c * M + i] = stage[12 * u + c];
+    B.qd[(size_t)c * M + i] = stage[12 * (size_t)M + 12 * u + c];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_state_out(DevBodies B, const int32_t *boi, double *stage) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int M = B.M;
+  if (i >= M) return;
+  const size_t u = (size_t)boi[i];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    stage[12 * u + c] = B.q[(size_t)c * M + i];
+    stage[12 * (size_t)M + 12 * u + c] = B.qd[(size_t)c * M + i];
+  }
+}
+
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+void launch_state_check(const double *stage, size_t n, int *flag, cudaStream_t s) {
+  if (n) k_state_check<<<1216, 256, 0, s>>>(stage, n, flag);
+}
+
+void launch_state_in(const double *stage, const int32_t *boi, const DevBodies &B, cudaStream_t s) {
+  if (B.M > 0) k_state_in<<<nblk(B.M, 128), 128, 0, s>>>(stage, boi, B);
+}
+
+void launch_state_out(const DevBodies &B, const int32_t *boi, double *stage, cudaStream_t s) {
+  if (B.M > 0) k_state_out<<<nblk(B.M, 128), 128, 0, s>>>(B, boi, stage);
+}
 
 void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s) {
   if (B.M > 0) k_body_prep<<<nblk(B.M, 128), 128, 0, s>>>(B, p, status);

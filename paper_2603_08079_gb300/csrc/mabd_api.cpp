@@ -82,6 +82,11 @@ struct mabd_ctx {
   size_t h_stage_n = 0;
   cudaEvent_t stage_done = nullptr;
   bool stage_pending = false;
+  // device-side state transfer: the caller's arrays as given, and the
+  // internal -> user body map
+  double *d_stage = nullptr;
+  int32_t *d_boi = nullptr;
+  int *d_flag = nullptr;
 
   // last CUDA failure (for mabd_error_detail)
   char err_detail[256] = {0};
@@ -1641,25 +1646,44 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
   return read_status(ctx);
 }
 
+}  // extern "C"
+
+// device buffers of the state transfer (allocated on first use)
+static mabd_status ensure_dstage(mabd_ctx *ctx) {
+  if (ctx->d_stage) return MABD_OK;
+  const int M = ctx->B.M;
+  bool ok = true;
+  double *st = dnew<double>(ctx, 24 * (size_t)std::max(M, 1), ok);
+  int32_t *boi = dnew<int32_t>(ctx, std::max(M, 1), ok);
+  int *flag = dnew<int>(ctx, 1, ok);
+  if (!ok) return MABD_ERR_OUT_OF_MEMORY;
+  if (M > 0)
+    CK(cudaMemcpyAsync(boi, ctx->body_of_internal.data(), (size_t)M * 4, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->d_stage = st;
+  ctx->d_boi = boi;
+  ctx->d_flag = flag;
+  return MABD_OK;
+}
+
+extern "C" {
+
+// The caller's arrays are copied to the device as given (at DMA speed when
+// they are pinned) and reordered there; both calls return after the copy
+// has completed, so the caller keeps ownership of its arrays.
 mabd_status mabd_get_state(mabd_ctx *ctx, double *q, double *qdot) {
   dbg_pending("enter mabd_get_state");
   if (!ctx || (!q && !qdot)) return MABD_ERR_INVALID_ARG;
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
   const int M = ctx->B.M;
-  mabd_status st = ensure_stage(ctx, 24 * (size_t)std::max(M, 1));
+  mabd_status st = ensure_dstage(ctx);
   if (st) return st;
-  double *hq = ctx->h_stage, *hqd = ctx->h_stage + 12 * (size_t)M;
-  CK(cudaMemcpyAsync(hq, ctx->B.q, 12 * (size_t)M * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(hqd, ctx->B.qd, 12 * (size_t)M * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  for (int i = 0; i < M; ++i) {
-    const size_t u = (size_t)ctx->body_of_internal[i];
-    for (int c = 0; c < 12; ++c) {
-      if (q) q[12 * u + c] = hq[(size_t)c * M + i];
-      if (qdot) qdot[12 * u + c] = hqd[(size_t)c * M + i];
-    }
-  }
+  cudaStream_t s = ctx->stream;
+  launch_state_out(ctx->B, ctx->d_boi, ctx->d_stage, s);
+  if (q) CK(cudaMemcpyAsync(q, ctx->d_stage, 12 * (size_t)M * 8, cudaMemcpyDeviceToHost, s));
+  if (qdot) CK(cudaMemcpyAsync(qdot, ctx->d_stage + 12 * (size_t)M, 12 * (size_t)M * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   return read_status(ctx);
 }
 
@@ -1669,21 +1693,20 @@ mabd_status mabd_set_state(mabd_ctx *ctx, const double *q, const double *qdot) {
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
   const int M = ctx->B.M;
-  if (!finite_arr(q, 12 * M) || !finite_arr(qdot, 12 * M)) return MABD_ERR_INVALID_ARG;
-  mabd_status st = ensure_stage(ctx, 24 * (size_t)std::max(M, 1));
+  mabd_status st = ensure_dstage(ctx);
   if (st) return st;
-  double *hq = ctx->h_stage, *hqd = ctx->h_stage + 12 * (size_t)M;
-  for (int i = 0; i < M; ++i) {
-    const size_t u = (size_t)ctx->body_of_internal[i];
-    for (int c = 0; c < 12; ++c) {
-      hq[(size_t)c * M + i] = q[12 * u + c];
-      hqd[(size_t)c * M + i] = qdot[12 * u + c];
-    }
-  }
-  CK(cudaMemcpyAsync(ctx->B.q, hq, 12 * (size_t)M * 8, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->B.qd, hqd, 12 * (size_t)M * 8, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaEventRecord(ctx->stage_done, ctx->stream));
-  ctx->stage_pending = true;
+  cudaStream_t s = ctx->stream;
+  const size_t n = 12 * (size_t)M;
+  CK(cudaMemcpyAsync(ctx->d_stage, q, n * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->d_stage + n, qdot, n * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+  launch_state_check(ctx->d_stage, 2 * n, ctx->d_flag, s);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return MABD_ERR_INVALID_ARG;  // nothing of the device state changed
+  launch_state_in(ctx->d_stage, ctx->d_boi, ctx->B, s);
+  CK(cudaGetLastError());
   return MABD_OK;
 }
 

@@ -233,6 +233,12 @@ void launch_backprop(const DevBodies &B, const DevJoints &J, const DevIncidence 
 void launch_residuals(const DevBodies &B, const DevJoints &J, const StepParams &p,
                       unsigned long long *maxbits /*2*/, int *status, cudaStream_t s);
 
+// state transfer (k_body.cu): stage = the caller's q then qdot, [M][12] each
+// in user body order; boi[internal] = user body index
+void launch_state_check(const double *stage, size_t n, int *flag, cudaStream_t s);
+void launch_state_in(const double *stage, const int32_t *boi, const DevBodies &B, cudaStream_t s);
+void launch_state_out(const DevBodies &B, const int32_t *boi, double *stage, cudaStream_t s);
+
 // chain (k_chain.cu): per-body Gram blocks, then block cyclic reduction.
 // Level 0 reads D = Dfirst + Dsecond (+ identity on the padded rows of ball
 // joints), B and the joint rhs b directly; its multipliers go to J.lambda.
