@@ -897,6 +897,12 @@ __device__ __noinline__ void down_one(const DevBodies &B, const DevJoints &J, co
   tree_down_one(B, J, T, j, p);
 }
 
+template <int N>
+__device__ __noinline__ void inner_one(const DevBodies &B, const DevJoints &J, const DevTree &T, int j,
+                                       const StepParams &p, int *status, SmemL L) {
+  up_body<N, false>(B, J, T, j, p, status, L);
+}
+
 template <int LANES>
 __global__ void __launch_bounds__(FT) k_tree_forest(DevBodies B, DevJoints J, DevTree T, DevForest F,
                                                     StepParams p, int *status) {
@@ -978,8 +984,67 @@ void launch_tree_forest(const DevBodies &B, const DevJoints &J, const DevTree &T
   }
 }
 
+// One tree level in one launch: blocks [0, nbi) eliminate the bodies with
+// children (one per thread, TUP threads per block, or LANES lanes per body),
+// the other blocks the leaves (one per thread); the two sets do not depend on
+// each other, so their latencies overlap instead of adding up.
+template <int LANES>
+__global__ void __launch_bounds__(LANES == 0 ? TUP : CG * LANES)
+    k_tree_up_level(DevBodies B, DevJoints J, DevTree T, int lo, int mid, int hi, int nbi, StepParams p,
+                    int *status) {
+  if ((int)blockIdx.x >= nbi) {
+    const int i = mid + ((int)blockIdx.x - nbi) * blockDim.x + threadIdx.x;
+    if (i >= hi) return;
+    const int j = T.order[i];
+    if (T.parent[j] < 0) return;
+    if (J.type[T.pjoint[j]] == 0) leaf_one<3>(B, J, T, j, p, status);
+    else leaf_one<5>(B, J, T, j, p, status);
+    return;
+  }
+  if constexpr (LANES == 0) {
+    __shared__ double sL[78 * TUP];
+    const int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mid) return;
+    const int j = T.order[i];
+    if (T.parent[j] < 0) return;
+    SmemL L{sL + threadIdx.x};
+    if (J.type[T.pjoint[j]] == 0) inner_one<3>(B, J, T, j, p, status, L);
+    else inner_one<5>(B, J, T, j, p, status, L);
+  } else {
+    __shared__ double sH[CG][78];
+    __shared__ double sZ[CG][12][6];
+    __shared__ double sW[CG][12][5];
+    __shared__ double sD[CG][15];
+    __shared__ double sE[CG][5];
+    const int g = threadIdx.x / LANES, l = threadIdx.x % LANES;
+    const unsigned gmask = (((1u << LANES) - 1u) << (((threadIdx.x & 31) / LANES) * LANES));
+    const int i = lo + blockIdx.x * CG + g;
+    if (i >= mid) return;
+    const int j = T.order[i];
+    if (T.parent[j] < 0) return;
+    if (J.type[T.pjoint[j]] == 0)
+      coop_one<LANES, 3>(B, J, T, j, p, status, l, gmask, sH[g], sZ[g], sW[g], sD[g], sE[g]);
+    else
+      coop_one<LANES, 5>(B, J, T, j, p, status, l, gmask, sH[g], sZ[g], sW[g], sD[g], sE[g]);
+  }
+}
+
 void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int mid,
                     int hi, bool roots, const StepParams &p, int *status, cudaStream_t s, int variant) {
+  if (!roots && mid > lo && hi > mid) {
+    const int ni = mid - lo, nl = hi - mid;
+    if (variant == TREE_UP_COOP8) {
+      const int nbi = (ni + CG - 1) / CG, nbl = (nl + CG * 8 - 1) / (CG * 8);
+      k_tree_up_level<8><<<nbi + nbl, CG * 8, 0, s>>>(B, J, T, lo, mid, hi, nbi, p, status);
+    } else if (variant == TREE_UP_COOP4) {
+      const int nbi = (ni + CG - 1) / CG, nbl = (nl + CG * 4 - 1) / (CG * 4);
+      k_tree_up_level<4><<<nbi + nbl, CG * 4, 0, s>>>(B, J, T, lo, mid, hi, nbi, p, status);
+    } else {
+      const int nbi = (ni + TUP - 1) / TUP, nbl = (nl + TUP - 1) / TUP;
+      k_tree_up_level<0><<<nbi + nbl, TUP, 0, s>>>(B, J, T, lo, mid, hi, nbi, p, status);
+    }
+    return;
+  }
   if (roots) {
     if (hi > lo) k_tree_up_root<<<(hi - lo + TUP - 1) / TUP, TUP, 0, s>>>(B, J, T, lo, hi, p, status);
     return;
