@@ -2,9 +2,10 @@
 """Throughput of the M-ABD step on GB300: body-steps/s on the 1,048,576-body
 pulley-cable chain (alternating ball / hinge joints, both ends pinned,
 h = 1e-2 s), one implicit step with one Newton iteration per step, in the
-chosen form (mixed precision: FP32 products, FP64 cyclic reduction and one
-FP64 residual-correction sweep, 1e-6 against the FP64 oracle) with the
-plain FP64 GPU path timed beside it.  Other workloads: --workload
+chosen form (mixed precision: FP32 products and cyclic reduction, one FP64
+residual-correction sweep of the FP64 system, within 1e-6 of the FP64
+oracle) with the plain FP64 GPU path and the mixed form with the FP64
+reduction timed beside it.  Other workloads: --workload
 tree256k | net64x64x16 (mixed form with the learned preconditioner) |
 batch4096.
 
@@ -74,13 +75,16 @@ FORMS = {
     "mixed": "FP32 per-body/per-joint products (and Gram blocks on chains, PCG iterations on "
              "graphs); FP64 polar, rhs, constraint values, chain cyclic reduction and %d FP64 "
              "residual-correction sweep(s)",
+    "mixed_fp32_dual": "FP32 per-body/per-joint products, Gram blocks and chain cyclic reduction "
+                       "(FP32 PCG on graphs); FP64 polar, rhs, constraint values and %d FP64 "
+                       "residual-correction sweep(s) of the FP64 system",
 }
 
 
 def workload_config(M: int, K: int, rows: int, name: str = "chain1m", form: str = "fp64",
                     refine: int = 1) -> dict:
     desc, solver = WORKLOADS[name]
-    fdesc = FORMS[form] % refine if form == "mixed" else FORMS[form]
+    fdesc = FORMS[form] % refine if form != "fp64" else FORMS[form]
     return {
         "workload": desc % (M, K, rows),
         "bodies": M, "joints": K, "dual_rows": rows, "form": form, "form_detail": fdesc,
@@ -95,7 +99,7 @@ LPC_PARAMS_REL = "paper_2603_08079_gb300/data/lpc_params.npy"
 def use_learned(args, form: str):
     """Trained parameters of the learned preconditioner for the net workload
     in the mixed form (None otherwise or with --no-lpc)."""
-    if args.no_lpc or form != "mixed" or args.workload != "net64x64x16":
+    if args.no_lpc or form == "fp64" or args.workload != "net64x64x16":
         return None
     path = os.path.join(ROOT, LPC_PARAMS_REL)
     if not os.path.exists(path):
@@ -108,7 +112,9 @@ def chosen_form(args) -> str:
     and the batched forest run FP64."""
     if args.precision != "auto":
         return args.precision
-    return "mixed" if args.workload in ("chain1m", "net64x64x16") else "fp64"
+    if args.workload == "chain1m":
+        return "mixed_fp32_dual"
+    return "mixed" if args.workload == "net64x64x16" else "fp64"
 
 
 def dist_env():
@@ -247,6 +253,38 @@ def cr_reduce_flops(jtype_chain: np.ndarray) -> float:
     return 2.0 * best[0] + 2.0 * best[1]
 
 
+def _cr_sizes(jtype_chain: np.ndarray) -> np.ndarray:
+    """Level-0 row sizes with the library's choice of the leading identity row."""
+    sizes = np.where(np.asarray(jtype_chain) == 1, 5, 3).astype(np.int64)
+    if len(sizes) > 1 and _cr_fma(np.concatenate([[3], sizes]))[0] < _cr_fma(sizes)[0]:
+        return np.concatenate([[3], sizes])
+    return sizes
+
+
+def cr_back_bytes(jtype_chain: np.ndarray, elem: int) -> float:
+    """Algorithmic bytes of the back-substitution over all levels (one
+    pass): an eliminated row of size n between neighbours of sizes l, r reads
+    its factor (n(n+1)/2 + n l + n r + n entries) and the neighbours'
+    multipliers (l + r) and writes its own (n); a kept row copies its C
+    multipliers from the next level.  elem: bytes of the reduction's type;
+    level 0 writes FP64 multipliers."""
+    sizes = _cr_sizes(jtype_chain)
+    total, level = 0.0, 0
+    while len(sizes) > 1:
+        N = len(sizes)
+        odd = np.arange(1, N, 2)
+        n = sizes[odd]
+        l = sizes[odd - 1]
+        r = np.where(odd + 1 < N, sizes[np.minimum(odd + 1, N - 1)], 0)
+        out = 8 if level == 0 else elem
+        total += float(np.sum((n * (n + 1) // 2 + n * l + n * r + n + l + r) * elem + n * out))
+        even = sizes[0::2]
+        total += float(np.sum(even * (elem + out)))
+        sizes = sizes[0::2]
+        level += 1
+    return total
+
+
 def chain_gram_flops(jtype_chain: np.ndarray) -> float:
     """FP64 flops of the per-body Gram blocks (FMA = 2).  Rows are grouped by
     point; a block is E^T Mbar(p, p') E' with the 3x3 point compliance Mbar
@@ -266,15 +304,28 @@ def chain_gram_flops(jtype_chain: np.ndarray) -> float:
 # an entry is removed when its kernel changes.  cr_level: all 21 launches of
 # a step of the 524,288-body chain (675.4 MB) scaled to 1,048,576 bodies and
 # averaged per launch (profiles/chain512k_mixed_dram_launch_list.md).
-TRAFFIC: dict = {("chain1m", "cr_level"): 64.3e6}
+TRAFFIC: dict = {("chain1m", "mixed", "cr_level"): 64.3e6}
 
 
-def kernel_model(name: str, jtype_chain: np.ndarray):
-    """Algorithmic FP64 flops of one step's launches of `name` (all levels)."""
-    if name.startswith("cr_reduce") or name == "cr_level":
-        return cr_reduce_flops(jtype_chain)
+def measured_hbm_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0   # the profiling recipe's fallback
+
+
+def kernel_model(name: str, jtype_chain: np.ndarray, form: str = "fp64"):
+    """(bound, algorithmic work of one step's launches of `name`): FP64 flops
+    ("alu") or HBM bytes ("hbm"), or None without a model."""
+    if form != "mixed_fp32_dual" and (name.startswith("cr_reduce") or name == "cr_level"):
+        return "alu", cr_reduce_flops(jtype_chain)
     if name == "chain_gram":
-        return chain_gram_flops(jtype_chain)
+        return "alu", chain_gram_flops(jtype_chain)
+    if name == "cr_back":
+        passes = 1 if form == "fp64" else 2   # factorization + the correction sweep's pass
+        return "hbm", passes * cr_back_bytes(jtype_chain, 4 if form == "mixed_fp32_dual" else 8)
+    return None
     return None
 
 
@@ -369,6 +420,9 @@ def run_gpu(args):
     others = {}
     if form != "fp64":
         variants = [("plain_fp64_gpu", dict(precision="fp64"), None)]
+        if form == "mixed_fp32_dual":
+            variants.append(("mixed_fp64_reduction_gpu", dict(precision="mixed", refine_steps=args.refine),
+                             None))
         if learned is not None:
             variants.append(("mixed_block_jacobi_gpu", dict(precision="mixed", refine_steps=args.refine),
                              None))
@@ -391,16 +445,26 @@ def run_gpu(args):
         per_launch_ms = dms / dn
         launches_per_step = sum(n for _, n in kt.values()) / args.profile_steps
         dom_launches = dn / args.profile_steps
-        step_flops = kernel_model(dname, sc["jtype"]) if args.workload == "chain1m" else None
-        if step_flops is not None:
+        model = kernel_model(dname, sc["jtype"], form) if args.workload == "chain1m" else None
+        if model is not None and model[0] == "alu":
+            step_flops = model[1]
             flops = step_flops / dom_launches     # per launch, averaged over the levels
             achieved = flops / (per_launch_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                    "traffic": TRAFFIC.get((args.workload, dname)), "kernel": dname,
+                    "traffic": TRAFFIC.get((args.workload, form, dname)), "kernel": dname,
                     "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz (probe measured 1.20)",
                     "kernel_ms_per_launch": round(per_launch_ms, 5),
                     "flops_per_step": step_flops, "launches_per_step": dom_launches}
+        elif model is not None:
+            step_bytes = model[1]
+            achieved = step_bytes / dom_launches / (per_launch_ms / 1e3) / 1e9
+            peak = measured_hbm_gbs()
+            roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get((args.workload, form, dname)),
+                    "kernel": dname, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                    "kernel_ms_per_launch": round(per_launch_ms, 5),
+                    "bytes_per_step": step_bytes, "launches_per_step": dom_launches}
         else:
             roof = {"bound": "alu", "achieved": None, "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": dname}
@@ -508,8 +572,9 @@ def main():
     ap.add_argument("--cpu-bodies", type=int, default=M_FULL // 4)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"],
-                    help="form of the step (auto: mixed for the chain, FP64 otherwise)")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "mixed_fp32_dual"],
+                    help="form of the step (auto: mixed with the FP32 reduction for the chain, "
+                         "mixed with the learned preconditioner for the net, FP64 otherwise)")
     ap.add_argument("--refine", type=int, default=1, help="FP64 correction sweeps of the mixed form")
     ap.add_argument("--no-lpc", action="store_true",
                     help="net workload: block Jacobi instead of the learned preconditioner")

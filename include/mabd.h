@@ -88,8 +88,14 @@ typedef enum {
                FP64; then refine_steps FP64 residual-correction sweeps
                (iterative refinement of the KKT system through the stored
                FP64 factors).  Other topologies: MABD_ERR_UNSUPPORTED at
-               mabd_prefactor. */
-enum { MABD_FP64 = 0, MABD_MIXED = 1 };
+               mabd_prefactor.
+   MABD_MIXED_FP32_DUAL  as MABD_MIXED, but the chain's cyclic reduction
+               runs in FP32 as well (Gram blocks, factors and levels in
+               FP32); the FP64 correction sweeps still refine the FP64
+               system, so the result keeps the mixed form's accuracy while the
+               reduction leaves the FP64 pipe.  On the PCG path it equals
+               MABD_MIXED. */
+enum { MABD_FP64 = 0, MABD_MIXED = 1, MABD_MIXED_FP32_DUAL = 2 };
 #define MABD_MAX_REFINE 8
 enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_SOLVER_PCG = 3 };
 enum { MABD_JOINT_BALL = 0, MABD_JOINT_HINGE = 1 };
@@ -98,7 +104,7 @@ enum { MABD_TOPO_NONE = 0, MABD_TOPO_CHAIN = 1, MABD_TOPO_TREE = 2, MABD_TOPO_GR
 typedef struct {
   double h;             /* time step [s] > 0 */
   double gravity[3];    /* [m/s^2], applied at each centre of mass (Eq. module1-wrench-map) */
-  int32_t precision;    /* MABD_FP64 or MABD_MIXED */
+  int32_t precision;    /* MABD_FP64, MABD_MIXED or MABD_MIXED_FP32_DUAL */
   int32_t solver;       /* MABD_SOLVER_*; AUTO picks chain, then tree, then PCG */
   int32_t pcg_max_iters;/* cap on PCG iterations (>= 1) */
   double pcg_rtol;      /* PCG stops when |r| <= pcg_rtol |b| */
@@ -143,7 +149,7 @@ typedef struct {
   int32_t topology;        /* MABD_TOPO_* chosen at prefactor */
   int32_t solver;          /* MABD_SOLVER_* in use */
   int64_t device_bytes;    /* device memory held by the context */
-  int32_t precision;       /* MABD_FP64 or MABD_MIXED */
+  int32_t precision;       /* MABD_FP64, MABD_MIXED or MABD_MIXED_FP32_DUAL */
   int32_t refine_steps;    /* correction sweeps per step (MABD_MIXED) */
 } mabd_info;
 

@@ -53,6 +53,7 @@ struct mabd_ctx {
   DevIncidence I{};
   DevChain C{};
   std::vector<CRLevel> levels;
+  std::vector<CRLevelT<float>> levels_f;  // FP32 reduction of MABD_MIXED_FP32_DUAL
   DevTree T{};
   DevPCG P{};
   DevPCG32 P32{};
@@ -601,7 +602,8 @@ mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
   *out = nullptr;
   if (!(cfg->h > 0.0) || !std::isfinite(cfg->h) || !finite_arr(cfg->gravity, 3))
     return MABD_ERR_INVALID_ARG;
-  if (cfg->precision != MABD_FP64 && cfg->precision != MABD_MIXED) return MABD_ERR_INVALID_ARG;
+  if (cfg->precision != MABD_FP64 && cfg->precision != MABD_MIXED && cfg->precision != MABD_MIXED_FP32_DUAL)
+    return MABD_ERR_INVALID_ARG;
   if (cfg->refine_steps < 0 || cfg->refine_steps > MABD_MAX_REFINE) return MABD_ERR_INVALID_ARG;
   if (cfg->solver < MABD_SOLVER_AUTO || cfg->solver > MABD_SOLVER_PCG) return MABD_ERR_INVALID_ARG;
   if (cfg->pcg_max_iters < 1 || !(cfg->pcg_rtol > 0.0)) return MABD_ERR_INVALID_ARG;
@@ -810,7 +812,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   }
   if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
   if (solver == MABD_SOLVER_TREE && !is_tree) return MABD_ERR_UNSUPPORTED;
-  if (ctx->cfg.precision == MABD_MIXED && K > 0 && solver == MABD_SOLVER_TREE) {
+  if (ctx->cfg.precision != MABD_FP64 && K > 0 && solver == MABD_SOLVER_TREE) {
     std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
                   "the mixed-precision form is implemented for chains and for the PCG path only");
     return MABD_ERR_UNSUPPORTED;
@@ -964,7 +966,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   J.c = dnew<double>(ctx, 5 * (size_t)Kx, ok);
   J.b = dnew<double>(ctx, 5 * (size_t)Kx, ok);
   J.lambda = dnew<double>(ctx, 5 * (size_t)Kx, ok);
-  const bool mixed = ctx->cfg.precision == MABD_MIXED;
+  const bool mixed = ctx->cfg.precision != MABD_FP64;
+  const bool f32dual = ctx->cfg.precision == MABD_MIXED_FP32_DUAL;
   float *dhinvf = nullptr;
   float *dpf[4] = {nullptr, nullptr, nullptr, nullptr};
   if (mixed) {
@@ -1099,6 +1102,25 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       if (N == 1) break;
       N = (N + 1) / 2;
       ++lvl;
+    }
+    if (f32dual) {
+      ctx->levels_f.clear();
+      for (size_t l = 0; l < ctx->levels.size(); ++l) {
+        CRLevelT<float> Lf{};
+        const int Nl = ctx->levels[l].N;
+        Lf.N = Nl;
+        if (l > 0) {
+          Lf.D = dnew<float>(ctx, 15 * (size_t)Nl, ok);
+          Lf.B = dnew<float>(ctx, 25 * (size_t)Nl, ok);
+          Lf.b = dnew<float>(ctx, 5 * (size_t)Nl, ok);
+          Lf.lam = dnew<float>(ctx, 5 * (size_t)Nl, ok);
+        }
+        if (Nl / 2 > 0) Lf.fac = dnew<float>(ctx, 70 * (size_t)(Nl / 2), ok);
+        ctx->levels_f.push_back(Lf);
+      }
+      C.Dfirst_f = dnew<float>(ctx, 15 * (size_t)K, ok);
+      C.Dsecond_f = dnew<float>(ctx, 15 * (size_t)K, ok);
+      C.B_f = dnew<float>(ctx, 25 * (size_t)K, ok);
     }
     const size_t half = std::max((K + 1) / 2, 1);
     ctx->cL = dnew<double>(ctx, 20 * half, ok);
@@ -1299,31 +1321,37 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
 // cyclic reduction of the chain's dual: factorization of the current blocks
 // with the current rhs, or (rhs_only) a new rhs J.b through the stored
 // factors; level 0 writes its solution to Jout.lambda and adds it to acc
-static void enqueue_cr(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout,
-                       double *acc) {
-  const int nl = (int)ctx->levels.size();
+}  // extern "C"
+
+template <typename T>
+static void enqueue_cr_t(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout, double *acc,
+                         std::vector<CRLevelT<T>> &levels) {
+  const int nl = (int)levels.size();
   for (int l = 0; l + 1 < nl; ++l) {
     if (rhs_only)
-      run(ctx, "cr_rhs", [&] { launch_cr_rhs(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], s); });
+      run(ctx, "cr_rhs", [&] { launch_cr_rhs<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], s); });
     else
-      run(ctx, "cr_level", [&] {
-        launch_cr_level(ctx->C, ctx->J, ctx->levels[l], l, ctx->levels[l + 1], ctx->d_status, s);
-      });
+      run(ctx, "cr_level", [&] { launch_cr_level<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], ctx->d_status, s); });
   }
   if (nl == 1) {
-    // a single row (one joint): level 0 is the top row
-    CRLevel top = ctx->levels[0];
-    top.lam = Jout.lambda;
-    run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, top, 0, ctx->d_status, s, acc); });
+    // a single row (one joint): level 0 is the top row, written to Jout.lambda
+    run(ctx, "cr_top", [&] { launch_cr_top<T>(ctx->C, ctx->J, levels[0], 0, ctx->d_status, s, Jout.lambda, acc); });
     return;
   }
-  run(ctx, "cr_top", [&] { launch_cr_top(ctx->C, ctx->J, ctx->levels[nl - 1], nl - 1, ctx->d_status, s); });
+  run(ctx, "cr_top", [&] { launch_cr_top<T>(ctx->C, ctx->J, levels[nl - 1], nl - 1, ctx->d_status, s); });
   for (int l = nl - 2; l >= 0; --l)
     run(ctx, "cr_back", [&] {
-      launch_cr_back(ctx->C, l == 0 ? Jout : ctx->J, ctx->levels[l], ctx->levels[l + 1], l, s,
-                     l == 0 ? acc : nullptr);
+      launch_cr_back<T>(ctx->C, l == 0 ? Jout : ctx->J, levels[l], levels[l + 1], l, s, l == 0 ? acc : nullptr);
     });
 }
+
+// the chain's reduction in the precision of the form in use
+static void enqueue_cr(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout, double *acc) {
+  if (ctx->cfg.precision == MABD_MIXED_FP32_DUAL) enqueue_cr_t<float>(ctx, s, rhs_only, Jout, acc, ctx->levels_f);
+  else enqueue_cr_t<double>(ctx, s, rhs_only, Jout, acc, ctx->levels);
+}
+
+extern "C" {
 
 // mixed-precision chain step (k_mixed.cu): approximate solve with FP32
 // products and the FP64 reduction, then refine_steps FP64 residual-correction
@@ -1336,7 +1364,9 @@ static void enqueue_mixed_chain(mabd_ctx *ctx, unsigned long long *maxbits, cuda
     return;
   }
   run(ctx, "mx_joint_prep", [&] { launch_mx_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
-  run(ctx, "mx_chain_gram", [&] { launch_mx_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
+  run(ctx, "mx_chain_gram", [&] {
+    launch_mx_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s, ctx->cfg.precision == MABD_MIXED_FP32_DUAL);
+  });
   enqueue_cr(ctx, s, false, ctx->J, nullptr);
   const int sweeps = ctx->cfg.refine_steps;
   DevJoints Jc = ctx->J;
@@ -1352,7 +1382,7 @@ static void enqueue_mixed_chain(mabd_ctx *ctx, unsigned long long *maxbits, cuda
 
 static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s) {
   const StepParams &p = ctx->sp;
-  if (ctx->cfg.precision == MABD_MIXED) return;  // the whole step is in enqueue_post
+  if (ctx->cfg.precision != MABD_FP64) return;  // the whole step is in enqueue_post
   run(ctx, "body_prep", [&] { launch_body_prep(ctx->B, p, ctx->d_status, s); });
   if (ctx->J.K == 0) return;
   run(ctx, "joint_prep", [&] { launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
@@ -1390,7 +1420,7 @@ static void enqueue_pcg_chunk(mabd_ctx *ctx, cudaStream_t s) {
 
 static void enqueue_post(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
   const StepParams &p = ctx->sp;
-  if (ctx->cfg.precision == MABD_MIXED)
+  if (ctx->cfg.precision != MABD_FP64)
     enqueue_mixed_chain(ctx, maxbits, s);
   else if (!(ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE))
     run(ctx, "backprop", [&] { launch_backprop(ctx->B, ctx->J, ctx->I, p, ctx->d_status, s); });
@@ -1511,7 +1541,7 @@ static mabd_status step_mixed_pcg(mabd_ctx *ctx, unsigned long long *maxbits, cu
 
 static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
   cudaStream_t s = ctx->stream;
-  if (ctx->cfg.precision == MABD_MIXED && ctx->solver == MABD_SOLVER_PCG && ctx->J.K > 0) {
+  if (ctx->cfg.precision != MABD_FP64 && ctx->solver == MABD_SOLVER_PCG && ctx->J.K > 0) {
     mabd_status st = step_mixed_pcg(ctx, maxbits, s);
     if (st) return st;
     cudaError_t e = cudaGetLastError();
@@ -1552,7 +1582,7 @@ static void body_step(mabd_ctx *ctx, cudaStream_t s) {
 // builds the graphs once; on any failure graphs stay off for this context
 static bool graphs_ready(mabd_ctx *ctx) {
   if (ctx->graphs_off) return false;
-  if (ctx->cfg.precision == MABD_MIXED && ctx->solver == MABD_SOLVER_PCG && ctx->J.K > 0) {
+  if (ctx->cfg.precision != MABD_FP64 && ctx->solver == MABD_SOLVER_PCG && ctx->J.K > 0) {
     ctx->graphs_off = true;  // host-checked inner solves: launched directly
     return false;
   }
@@ -1641,7 +1671,7 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
     stats[i].joint_residual = nl;
     stats[i].pcg_iters = pit[i];
     stats[i].pcg_rel_residual = prel[i];
-    stats[i].refine_residual = ctx->cfg.precision == MABD_MIXED ? ref : 0.0;
+    stats[i].refine_residual = ctx->cfg.precision != MABD_FP64 ? ref : 0.0;
   }
   return read_status(ctx);
 }
@@ -1811,7 +1841,7 @@ namespace {
 mabd_status build_lpc_graph(mabd_ctx *ctx) {
   if (ctx->lpc_graph) return MABD_OK;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
-  if (ctx->cfg.precision != MABD_MIXED || ctx->solver != MABD_SOLVER_PCG || ctx->J.K <= 0) {
+  if (ctx->cfg.precision == MABD_FP64 || ctx->solver != MABD_SOLVER_PCG || ctx->J.K <= 0) {
     std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
                   "the learned preconditioner needs the mixed-precision PCG path");
     return MABD_ERR_UNSUPPORTED;

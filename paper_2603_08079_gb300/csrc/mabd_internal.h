@@ -88,17 +88,21 @@ struct DevChain {
   const uint8_t *jflags; // [K] bit0: has lower-body part, bit1: has upper-body part, bit2: has B
   const int8_t *islot;   // [nnz] per incidence entry: 0 -> Dfirst, 1 -> Dsecond
   int32_t off;           // level-0 row n is joint n - off; rows n < off are identity rows
+  // FP32 Gram parts for the FP32 reduction of the mixed form (else null)
+  float *Dfirst_f, *Dsecond_f, *B_f;
 };
 
-// one level of block cyclic reduction
-struct CRLevel {
+// one level of block cyclic reduction (T: the reduction's precision)
+template <typename T>
+struct CRLevelT {
   int32_t N;             // rows at this level
-  double *D;             // [15][N] (level 0: assembled from DevChain)
-  double *B;             // [25][N]
-  double *b;             // [5][N]
-  double *fac;           // [70][N/2] L, Ya, Yb, y of the odd rows
-  double *lam;           // [5][N]
+  T *D;                  // [15][N] (level 0: assembled from DevChain)
+  T *B;                  // [25][N]
+  T *b;                  // [5][N]
+  T *fac;                // [70][N/2] L, Ya, Yb, y of the odd rows
+  T *lam;                // [5][N]
 };
+using CRLevel = CRLevelT<double>;
 
 // tree (forest) of free bodies in breadth-first order: levels are contiguous
 // ranges and the children of a body are a contiguous range
@@ -249,20 +253,26 @@ void launch_cr_reduce(const DevChain &C, const DevJoints &J, const CRLevel &cur,
 void launch_cr_combine(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
                        const CRLevel &next, const double *cL, const double *cR,
                        const double *Bn, cudaStream_t s);
-// reduce + combine of one level in a single launch (fused form of the two above)
-void launch_cr_level(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
-                     const CRLevel &next, int *status, cudaStream_t s);
-void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevel &top, int level,
-                   int *status, cudaStream_t s, double *acc = nullptr);
+// reduce + combine of one level in a single launch (fused form of the two
+// above); T = double or float (the reduction's precision)
+template <typename T>
+void launch_cr_level(const DevChain &C, const DevJoints &J, const CRLevelT<T> &cur, int level,
+                     const CRLevelT<T> &next, int *status, cudaStream_t s);
+// the single remaining row; out64 (FP64, with acc) when the top row is level 0
+template <typename T>
+void launch_cr_top(const DevChain &C, const DevJoints &J, const CRLevelT<T> &top, int level,
+                   int *status, cudaStream_t s, double *out64 = nullptr, double *acc = nullptr);
 // back-substitution of `level`; level 0 writes its rows n >= C.off to
-// J.lambda and, when acc is not null, also adds them to acc ([5][K])
-void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevel &cur, const CRLevel &next,
+// J.lambda (FP64) and, when acc is not null, also adds them to acc ([5][K])
+template <typename T>
+void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevelT<T> &cur, const CRLevelT<T> &next,
                     int level, cudaStream_t s, double *acc = nullptr);
 // new right-hand side through the stored factors: forward elimination of
 // `level` (level 0 reads J.b) writing next.b and the odd rows' y; the top
 // row and the back-substitution then run as for a factorization
-void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevel &cur, int level,
-                   const CRLevel &next, cudaStream_t s);
+template <typename T>
+void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevelT<T> &cur, int level,
+                   const CRLevelT<T> &next, cudaStream_t s);
 
 // FP32 PCG (k_pcg32.cu): setup from rhs (FP64 [5][K]), iterations, and the
 // final copy of x to out (FP64 [5][K]) with acc += x when acc is given
@@ -318,7 +328,7 @@ void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, c
 void launch_mx_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,
                           cudaStream_t s);
 void launch_mx_chain_gram(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
-                          const DevChain &C, cudaStream_t s);
+                          const DevChain &C, cudaStream_t s, bool f32_blocks = false);
 void launch_mx_res_body(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
                         const StepParams &p, bool first, cudaStream_t s);
 void launch_mx_res_joint(const DevBodies &B, const DevJoints &J, const StepParams &p,

@@ -18,7 +18,7 @@ from . import build as _build
 
 WORLD = -1
 SOLVERS = {"auto": 0, "chain": 1, "tree": 2, "pcg": 3}
-PRECISIONS = {"fp64": 0, "mixed": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_fp32_dual": 2}
 TOPOLOGIES = {0: "none", 1: "chain", 2: "tree", 3: "graph"}
 STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of device memory",
           4: "CUDA error", 5: "not positive definite", 6: "inverted body", 7: "non-finite",

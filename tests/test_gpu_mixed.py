@@ -21,7 +21,7 @@ TOL = 1e-6
 def mixed_errors(ora, sc, q, qd, **kw):
     solver = gpu_solver(sc, **dict(MIXED, **kw))
     try:
-        assert solver.info()["precision"] == "mixed"
+        assert solver.info()["precision"] == dict(MIXED, **kw)["precision"]
         _, qd1, lam, st = gpu_step(solver, q, qd)
     finally:
         solver.close()
@@ -167,4 +167,55 @@ def test_mixed_full_size_pulley_chain(ora):
     need_gpu()
     sc = scenes.long_chain(1 << 20, seed=1)
     e_qd, e_lam, st, _ = assert_parity(ora, sc, sc["q"], sc["qdot"], tol=TOL, gpu_kw=MIXED)
+    assert st["joint_residual"] < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# mixed form with the chain's cyclic reduction in FP32 (MABD_MIXED_FP32_DUAL)
+# ---------------------------------------------------------------------------
+F32 = {"precision": "mixed_fp32_dual"}
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 17, 255, 4097, 65537])
+def test_fp32_reduction_long_chain(ora, M):
+    need_gpu()
+    sc = scenes.long_chain(M, seed=1)
+    q, qd = scenes.perturb_state(sc, seed=M, rot=0.05, vel=0.2)
+    assert_parity(ora, sc, sc["q"], sc["qdot"], tol=TOL, gpu_kw=F32)
+    assert_parity(ora, sc, q, qd, tol=TOL, gpu_kw=F32)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fp32_reduction_random_chains(ora, seed):
+    need_gpu()
+    M = [3, 13, 40][seed]
+    sc = scenes.random_small("chain", M, seed=seed, hinge_frac=0.5)
+    q, qd = scenes.perturb_state(sc, seed=seed, rot=0.3)
+    assert_parity(ora, sc, q, qd, tol=TOL, gpu_kw=F32)
+    assert_parity(ora, sc, q, qd, tol=TOL, residual_rhs=0, gpu_kw=F32)
+
+
+def test_fp32_reduction_sweeps(ora):
+    """The FP32 reduction alone is FP32-accurate; the FP64 sweeps restore
+    the FP64 system's solution."""
+    need_gpu()
+    sc = scenes.long_chain(4097, seed=1)
+    q, qd = scenes.perturb_state(sc, seed=11, rot=0.05, vel=0.2)
+    e = {}
+    for sweeps in (0, 1, 2):
+        e_qd, e_lam, st = mixed_errors(ora, sc, q, qd, refine_steps=sweeps, **{"precision": "mixed_fp32_dual"})
+        e[sweeps] = max(e_qd, e_lam)
+    assert e[0] > 1e-8 and e[1] <= TOL and e[2] < e[1], e
+
+
+def test_fp32_reduction_on_the_pcg_path(ora):
+    need_gpu()
+    sc = scenes.jittered_net(6, 6, 3, seed=4)
+    assert_parity(ora, sc, sc["q"], sc["qdot"], tol=TOL, gpu_kw=F32)
+
+
+def test_fp32_reduction_full_size_pulley_chain(ora):
+    need_gpu()
+    sc = scenes.long_chain(1 << 20, seed=1)
+    e_qd, e_lam, st, _ = assert_parity(ora, sc, sc["q"], sc["qdot"], tol=TOL, gpu_kw=F32)
     assert st["joint_residual"] < 1e-5
