@@ -151,6 +151,9 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the context */
   int32_t precision;       /* MABD_FP64, MABD_MIXED or MABD_MIXED_FP32_DUAL */
   int32_t refine_steps;    /* correction sweeps per step (MABD_MIXED) */
+  int32_t cr_levels;       /* chain solver: levels of the block cyclic reduction (0 otherwise) */
+  int32_t cr_tail_level;   /* chain solver: first level run by the single-CTA tail launch
+                              (= cr_levels when every level has its own launches) */
 } mabd_info;
 
 /* Fills *cfg with h = 1e-2, gravity (0,0,-9.8), FP64, AUTO, pcg_max_iters 2000,

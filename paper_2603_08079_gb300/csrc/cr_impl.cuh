@@ -248,9 +248,9 @@ __device__ __forceinline__ void reduce_row(const DevChain &C, const DevJoints &J
 //   row n-1 receives -Ya^T Ya, -Ya^T y; row n+1 receives -Yb^T Yb, -Yb^T y;
 //   the new coupling between rows n-1 and n+1 is -Ya^T Yb.
 template <typename T>
-__global__ void __launch_bounds__(128) k_cr_reduce(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
-                                                   T *cL, T *cR, T *Bn, int *status) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cr_reduce_one(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
+                                                   T *cL, T *cR, T *Bn, int *status, int m) {
+  
   const int n = 2 * m + 1;
   const int N = cur.N;
   if (n >= N) return;
@@ -270,12 +270,18 @@ __global__ void __launch_bounds__(128) k_cr_reduce(DevChain C, DevJoints J, CRLe
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) k_cr_reduce(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
+                                                   T *cL, T *cR, T *Bn, int *status) {
+  cr_reduce_one<T>(C, J, cur, level, cL, cR, Bn, status, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Even row e = 2m becomes row m of the next level.
 template <typename T>
-__global__ void __launch_bounds__(128) k_cr_combine(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
+__device__ __forceinline__ void cr_combine_one(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
                                                     CRLevelT<T> next, const T *cL,
-                                                    const T *cR, const T *Bn) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+                                                    const T *cR, const T *Bn, int m) {
+  
   if (m >= next.N) return;
   const int e = 2 * m;
   const int N = cur.N, Nh = N / 2;
@@ -302,6 +308,13 @@ __global__ void __launch_bounds__(128) k_cr_combine(DevChain C, DevJoints J, CRL
   }
 #pragma unroll
   for (int i = 0; i < 25; ++i) next.B[(size_t)i * next.N + m] = right ? Bn[(size_t)i * Nh + m] : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_cr_combine(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
+                                                    CRLevelT<T> next, const T *cL,
+                                                    const T *cR, const T *Bn) {
+  cr_combine_one<T>(C, J, cur, level, next, cL, cR, Bn, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // One cyclic-reduction level in one launch.  Block b owns the odd rows
@@ -429,9 +442,9 @@ __device__ __forceinline__ void back_row(const CRLevelT<T> &cur, const CRLevelT<
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_cr_back(CRLevelT<T> cur, CRLevelT<T> next, DevChain C, DevJoints J,
-                                                 int level, double *acc) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cr_back_one(CRLevelT<T> cur, CRLevelT<T> next, DevChain C, DevJoints J,
+                                                 int level, double *acc, int n) {
+  
   const int N = cur.N;
   if (n >= N) return;
   // level 0 writes joint n - off of the chain (FP64); other levels their own rows
@@ -461,6 +474,12 @@ __global__ void __launch_bounds__(128) k_cr_back(CRLevelT<T> cur, CRLevelT<T> ne
 #undef BCK
     default: break;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_cr_back(CRLevelT<T> cur, CRLevelT<T> next, DevChain C, DevJoints J,
+                                                 int level, double *acc) {
+  cr_back_one<T>(cur, next, C, J, level, acc, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -766,9 +785,8 @@ __global__ void __launch_bounds__(128) k_cr_back_w(CRLevelT<T> cur, CRLevelT<T> 
 
 // Single remaining row: lambda = D^{-1} b (Cholesky with reciprocal diagonal).
 template <typename T>
-__global__ void k_cr_top(DevChain C, DevJoints J, CRLevelT<T> top, int level, int *status, double *out64,
-                         double *acc) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+__device__ __forceinline__ void cr_top_one(const DevChain &C, const DevJoints &J, const CRLevelT<T> &top,
+                                           int level, int *status, double *out64, double *acc) {
   const int cn = row_size(C, J, level, 0);
   T Dp[15], b[5], L[5][5], id[5], y[5], x[5];
 #pragma unroll
@@ -797,6 +815,12 @@ __global__ void k_cr_top(DevChain C, DevJoints J, CRLevelT<T> top, int level, in
   }
 #pragma unroll
   for (int r = 0; r < 5; ++r) cr_put(out64, top.lam, (size_t)r * top.N, x[r], out64 ? acc : nullptr);
+}
+
+template <typename T>
+__global__ void k_cr_top(DevChain C, DevJoints J, CRLevelT<T> top, int level, int *status, double *out64,
+                         double *acc) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) cr_top_one<T>(C, J, top, level, status, out64, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -839,9 +863,9 @@ __device__ __forceinline__ void rhs_odd(const T *f, int Nh, int m, int slot, con
 // it give y = L^{-1} b (the right one stores its y in its factor record for
 // the back-substitution) and next.b[mm] = b_e - Yb_{e-1}^T y_{e-1} - Ya_{e+1}^T y_{e+1}.
 template <typename T>
-__global__ void __launch_bounds__(128) k_cr_rhs(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
-                                                CRLevelT<T> next) {
-  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cr_rhs_one(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
+                                                CRLevelT<T> next, int mm) {
+  
   if (mm >= next.N) return;
   const int N = cur.N, Nh = N / 2, e = 2 * mm;
   const int ce = row_size(C, J, level, e);
@@ -863,6 +887,59 @@ __global__ void __launch_bounds__(128) k_cr_rhs(DevChain C, DevJoints J, CRLevel
   }
 #pragma unroll
   for (int r = 0; r < 5; ++r) next.b[(size_t)r * next.N + mm] = r < ce ? be[r] : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_cr_rhs(DevChain C, DevJoints J, CRLevelT<T> cur, int level,
+                                                CRLevelT<T> next) {
+  cr_rhs_one<T>(C, J, cur, level, next, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
+// ---------------------------------------------------------------------------
+// the small levels in one CTA
+// ---------------------------------------------------------------------------
+// Levels l0 .. nl-2 (elimination or right-hand-side pass), the top row and the
+// back-substitution down to level l0, with a CTA barrier between levels: the
+// rows of a level are dealt out over the threads with the thread-per-row
+// bodies of the multi-CTA kernels.  This replaces two launches per level with
+// one launch, which pays where a row's serial latency is short (FP32) and the
+// levels hold at most a few hundred rows.  cL/cR/Bn hold (20, 20, 25) x Nh of
+// the largest level.
+// (FP64 rows need more registers than 512 threads leave)
+template <typename T>
+constexpr int cr_tail_threads() { return sizeof(T) == 4 ? 512 : 256; }
+
+template <typename T>
+__global__ void __launch_bounds__(cr_tail_threads<T>()) k_cr_tail(DevChain C, DevJoints J, DevJoints Jout,
+                                                             const CRLevelT<T> *lv, int l0, int nl,
+                                                             int rhs_only, T *cL, T *cR, T *Bn, int *status,
+                                                             double *acc) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int l = l0; l + 1 < nl; ++l) {
+    const CRLevelT<T> cur = lv[l], next = lv[l + 1];
+    if (rhs_only) {
+      for (int mm = t; mm < next.N; mm += nt) cr_rhs_one<T>(C, J, cur, l, next, mm);
+    } else {
+      const int Nh = cur.N / 2;
+      for (int m = t; m < Nh; m += nt) cr_reduce_one<T>(C, J, cur, l, cL, cR, Bn, status, m);
+      __syncthreads();
+      for (int m = t; m < next.N; m += nt) cr_combine_one<T>(C, J, cur, l, next, cL, cR, Bn, m);
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    // a single row at level 0 (one joint) is the top row and the output
+    if (nl == 1) cr_top_one<T>(C, J, lv[0], 0, status, Jout.lambda, acc);
+    else cr_top_one<T>(C, J, lv[nl - 1], nl - 1, status, nullptr, nullptr);
+  }
+  __syncthreads();
+  for (int l = nl - 2; l >= l0; --l) {
+    const CRLevelT<T> cur = lv[l], next = lv[l + 1];
+    for (int n = t; n < cur.N; n += nt)
+      cr_back_one<T>(cur, next, C, l == 0 ? Jout : J, l, l == 0 ? acc : nullptr, n);
+    __syncthreads();
+  }
 }
 
 

@@ -251,6 +251,13 @@ void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevelT<T> &cur
   if (next.N > 0) k_cr_rhs<T><<<nblk(next.N, 128), 128, 0, s>>>(C, J, cur, level, next);
 }
 
+template <typename T>
+void launch_cr_tail(const DevChain &C, const DevJoints &J, const DevJoints &Jout, const CRLevelT<T> *d_lv,
+                    int l0, int nl, bool rhs_only, T *cL, T *cR, T *Bn, int *status, double *acc,
+                    cudaStream_t s) {
+  k_cr_tail<T><<<1, cr_tail_threads<T>(), 0, s>>>(C, J, Jout, d_lv, l0, nl, rhs_only ? 1 : 0, cL, cR, Bn, status, acc);
+}
+
 #define MABD_CR_INSTANTIATE(T)                                                                       \
   template void launch_cr_level<T>(const DevChain &, const DevJoints &, const CRLevelT<T> &, int,     \
                                    const CRLevelT<T> &, int *, cudaStream_t);                       \
@@ -259,7 +266,10 @@ void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevelT<T> &cur
   template void launch_cr_back<T>(const DevChain &, const DevJoints &, const CRLevelT<T> &,           \
                                   const CRLevelT<T> &, int, cudaStream_t, double *);                \
   template void launch_cr_rhs<T>(const DevChain &, const DevJoints &, const CRLevelT<T> &, int,       \
-                                 const CRLevelT<T> &, cudaStream_t);
+                                 const CRLevelT<T> &, cudaStream_t);                               \
+  template void launch_cr_tail<T>(const DevChain &, const DevJoints &, const DevJoints &,             \
+                                  const CRLevelT<T> *, int, int, bool, T *, T *, T *, int *, double *, \
+                                  cudaStream_t);
 MABD_CR_INSTANTIATE(double)
 MABD_CR_INSTANTIATE(float)
 #undef MABD_CR_INSTANTIATE

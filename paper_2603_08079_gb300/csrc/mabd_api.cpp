@@ -54,6 +54,11 @@ struct mabd_ctx {
   DevChain C{};
   std::vector<CRLevel> levels;
   std::vector<CRLevelT<float>> levels_f;  // FP32 reduction of MABD_MIXED_FP32_DUAL
+  // device copies of the level arrays and the first level of the single-CTA
+  // tail of the reduction (levels.size() when the tail is off)
+  CRLevel *d_levels = nullptr;
+  CRLevelT<float> *d_levels_f = nullptr;
+  int cr_tail_level = 0;
   DevTree T{};
   DevPCG P{};
   DevPCG32 P32{};
@@ -1122,6 +1127,30 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       C.Dsecond_f = dnew<float>(ctx, 15 * (size_t)K, ok);
       C.B_f = dnew<float>(ctx, 25 * (size_t)K, ok);
     }
+    // The small levels run in one single-CTA launch per pass where a row's
+    // serial latency is short (FP32 reduction): from the first level with at
+    // most CR_TAIL_ROWS rows.  MABD_CR_TAIL=<rows> sets the bound for either
+    // precision (0: off).
+    {
+      const int nl = (int)ctx->levels.size();
+      int tail_rows = f32dual ? CR_TAIL_ROWS : 0;
+      if (const char *e = std::getenv("MABD_CR_TAIL")) tail_rows = std::atoi(e);
+      ctx->cr_tail_level = nl;
+      if (tail_rows > 0)
+        for (int l = 0; l < nl; ++l)
+          if (ctx->levels[l].N <= tail_rows) {
+            ctx->cr_tail_level = l;
+            break;
+          }
+      ctx->d_levels = dnew<CRLevel>(ctx, nl, ok);
+      if (ok) CK(cudaMemcpy(ctx->d_levels, ctx->levels.data(), nl * sizeof(CRLevel), cudaMemcpyHostToDevice));
+      if (f32dual) {
+        ctx->d_levels_f = dnew<CRLevelT<float>>(ctx, nl, ok);
+        if (ok)
+          CK(cudaMemcpy(ctx->d_levels_f, ctx->levels_f.data(), nl * sizeof(CRLevelT<float>),
+                        cudaMemcpyHostToDevice));
+      }
+    }
     const size_t half = std::max((K + 1) / 2, 1);
     ctx->cL = dnew<double>(ctx, 20 * half, ok);
     ctx->cR = dnew<double>(ctx, 20 * half, ok);
@@ -1325,8 +1354,28 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
 
 template <typename T>
 static void enqueue_cr_t(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout, double *acc,
-                         std::vector<CRLevelT<T>> &levels) {
+                         std::vector<CRLevelT<T>> &levels, const CRLevelT<T> *d_levels) {
   const int nl = (int)levels.size();
+  const int l0 = ctx->cr_tail_level;
+  if (l0 < nl) {
+    // large levels one launch each, the rest in the single-CTA tail
+    for (int l = 0; l < l0; ++l) {
+      if (rhs_only)
+        run(ctx, "cr_rhs", [&] { launch_cr_rhs<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], s); });
+      else
+        run(ctx, "cr_level",
+            [&] { launch_cr_level<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], ctx->d_status, s); });
+    }
+    run(ctx, "cr_tail", [&] {
+      launch_cr_tail<T>(ctx->C, ctx->J, Jout, d_levels, l0, nl, rhs_only, (T *)ctx->cL, (T *)ctx->cR,
+                        (T *)ctx->Bn, ctx->d_status, l0 == 0 ? acc : nullptr, s);
+    });
+    for (int l = l0 - 1; l >= 0; --l)
+      run(ctx, "cr_back", [&] {
+        launch_cr_back<T>(ctx->C, l == 0 ? Jout : ctx->J, levels[l], levels[l + 1], l, s, l == 0 ? acc : nullptr);
+      });
+    return;
+  }
   for (int l = 0; l + 1 < nl; ++l) {
     if (rhs_only)
       run(ctx, "cr_rhs", [&] { launch_cr_rhs<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], s); });
@@ -1347,8 +1396,10 @@ static void enqueue_cr_t(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const Dev
 
 // the chain's reduction in the precision of the form in use
 static void enqueue_cr(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout, double *acc) {
-  if (ctx->cfg.precision == MABD_MIXED_FP32_DUAL) enqueue_cr_t<float>(ctx, s, rhs_only, Jout, acc, ctx->levels_f);
-  else enqueue_cr_t<double>(ctx, s, rhs_only, Jout, acc, ctx->levels);
+  if (ctx->cfg.precision == MABD_MIXED_FP32_DUAL)
+    enqueue_cr_t<float>(ctx, s, rhs_only, Jout, acc, ctx->levels_f, ctx->d_levels_f);
+  else
+    enqueue_cr_t<double>(ctx, s, rhs_only, Jout, acc, ctx->levels, ctx->d_levels);
 }
 
 extern "C" {
@@ -1781,6 +1832,8 @@ mabd_status mabd_get_info(mabd_ctx *ctx, mabd_info *info) {
   info->device_bytes = ctx->device_bytes;
   info->precision = ctx->cfg.precision;
   info->refine_steps = ctx->cfg.refine_steps;
+  info->cr_levels = ctx->solver == MABD_SOLVER_CHAIN ? (int32_t)ctx->levels.size() : 0;
+  info->cr_tail_level = ctx->solver == MABD_SOLVER_CHAIN ? ctx->cr_tail_level : 0;
   return MABD_OK;
 }
 
@@ -1806,7 +1859,7 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
                                 "mx_chain_gram", "mx_res_body", "mx_res_joint", "cr_rhs", "mx_final",
                                 "p32_setup", "p32_iteration", "p32_finish", "lpc_blocks", "lpc_forward",
                                 "tree_forest",
-                                "cr_level", "cr_reduce", "cr_combine",
+                                "cr_level", "cr_reduce", "cr_combine", "cr_tail",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
                                 "pcg_iteration", "backprop", "residuals"};
   int n = 0;

@@ -273,6 +273,16 @@ void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevelT<T> &cu
 template <typename T>
 void launch_cr_rhs(const DevChain &C, const DevJoints &J, const CRLevelT<T> &cur, int level,
                    const CRLevelT<T> &next, cudaStream_t s);
+// levels with at most this many rows run in the single-CTA tail (FP32 reduction)
+constexpr int CR_TAIL_ROWS = 512;
+// levels l0 .. nl-1 of a pass (elimination, or right-hand side when rhs_only),
+// the top row and their back-substitution in one single-CTA launch; d_lv is a
+// device copy of the level array, cL/cR/Bn scratch of (20, 20, 25) x (rows of
+// level l0) / 2; level 0 (when l0 = 0) writes to Jout.lambda and acc
+template <typename T>
+void launch_cr_tail(const DevChain &C, const DevJoints &J, const DevJoints &Jout, const CRLevelT<T> *d_lv,
+                    int l0, int nl, bool rhs_only, T *cL, T *cR, T *Bn, int *status, double *acc,
+                    cudaStream_t s);
 
 // FP32 PCG (k_pcg32.cu): setup from rhs (FP64 [5][K]), iterations, and the
 // final copy of x to out (FP64 [5][K]) with acc += x when acc is given
