@@ -86,8 +86,9 @@ __device__ __forceinline__ void u_at(const double R[9], const double ub[12], con
 // b = G u + C(q_n) with G the frozen-frame Jacobian (Eq. pcpq).
 __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, StepParams p,
                                                     int *status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= J.K) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J.K) return;
+  const int k = ordered(J.order, t);
   const int K = J.K, M = B.M;
   const int type = J.type[k];
   const int ia = J.ja[k], ib = J.jb[k];
@@ -177,8 +178,9 @@ __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, St
 // implicit Euler update q += dq, qdot = dq / h.
 __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevIncidence I,
                                                   StepParams p) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= B.M) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B.M) return;
+  const int j = ordered(B.order, t);
   if (B.fixed[j]) return;
   const int M = B.M, K = J.K;
   double R[9], g[12];
@@ -341,9 +343,9 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
 
 __global__ void __launch_bounds__(128) k_residuals(DevBodies B, DevJoints J, StepParams p,
                                                    unsigned long long *maxbits, int *status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double lin = 0.0, nl = 0.0;
-  if (k < J.K) joint_residuals(B, J, p, k, status, lin, nl);
+  if (t < J.K) joint_residuals(B, J, p, ordered(J.order, t), status, lin, nl);
   // warp-level max first (all lanes take part), then one atomic per warp
   for (int o = 16; o > 0; o >>= 1) {
     lin = fmax(lin, __shfl_xor_sync(0xffffffffu, lin, o));

@@ -180,8 +180,8 @@ __device__ __forceinline__ void chain_gram_body(const DevBodies &B, const DevJoi
 
 __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, DevIncidence I,
                                                     DevChain C) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < B.M) chain_gram_body<double>(B, J, I, C, B.hinv, j);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < B.M) chain_gram_body<double>(B, J, I, C, B.hinv, ordered(B.order, t));
 }
 
 // mixed-precision form: the same blocks with FP32 products, stored in FP64
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(128) k_chain_gram(DevBodies B, DevJoints J, De
 template <typename OT>
 __global__ void __launch_bounds__(128) k_mx_chain_gram(DevBodies B, DevJoints J, DevIncidence I,
                                                        DevChain C) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < B.M) chain_gram_body<float, float, OT>(B, J, I, C, B.hinvf, j);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < B.M) chain_gram_body<float, float, OT>(B, J, I, C, B.hinvf, ordered(B.order, t));
 }
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }

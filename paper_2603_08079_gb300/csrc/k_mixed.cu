@@ -214,8 +214,9 @@ __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p,
 // axis from body a with a_y >= 0), b = G u + C(q_n) with G u in FP32.
 __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J, StepParams p,
                                                        int *status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= J.K) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J.K) return;
+  const int k = ordered(J.order, t);
   const int K = J.K, M = B.M;
   const int type = J.type[k];
   const int ia = J.ja[k], ib = J.jb[k];
@@ -307,8 +308,9 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
 template <bool FIRST>
 __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, DevIncidence I,
                                                      StepParams p) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= B.M) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B.M) return;
+  const int j = ordered(B.order, t);
   if (B.fixed[j]) return;
   const int M = B.M;
   double R[9], g64[12], dq[12];
@@ -352,9 +354,10 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
 // bottom rhs (residual_rhs = 0) the constraint is G dq = 0 and C drops out.
 __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, StepParams p,
                                                       unsigned long long *maxbit) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double worst = 0.0;
-  if (k < J.K) {
+  if (t < J.K) {
+    const int k = ordered(J.order, t);
     const int K = J.K, M = B.M;
     const int type = J.type[k];
     const int ia = J.ja[k], ib = J.jb[k];
@@ -445,8 +448,9 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
 // q += dq, qdot = dq / h (implicit Euler, Sec. 3.4).
 __global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevIncidence I,
                                                   StepParams p, bool from_u) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= B.M) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B.M) return;
+  const int j = ordered(B.order, t);
   if (B.fixed[j]) return;
   const int M = B.M;
   double R[9];

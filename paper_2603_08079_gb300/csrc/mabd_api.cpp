@@ -917,6 +917,33 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       }
     }
   }
+  // processing orders of the per-joint and per-body kernels (CHUNK_ORDER):
+  // each run of CHUNK_ORDER entries stably partitioned by a type key; left
+  // out (identity) when no run mixes keys
+  std::vector<int32_t> jord, bord;
+  {
+    auto chunk_order = [](int n, const std::vector<int> &key, std::vector<int32_t> &out) {
+      out.resize(n);
+      bool moved = false;
+      for (int c0 = 0; c0 < n; c0 += CHUNK_ORDER) {
+        const int c1 = std::min(n, c0 + CHUNK_ORDER);
+        for (int i = c0; i < c1; ++i) out[i] = i;
+        std::stable_sort(out.begin() + c0, out.begin() + c1, [&](int a, int b) { return key[a] < key[b]; });
+        for (int i = c0; i < c1 && !moved; ++i) moved = out[i] != i;
+      }
+      if (!moved) out.clear();
+    };
+    std::vector<int> jkey(K), bkey(M);
+    for (int i = 0; i < K; ++i) jkey[i] = jtype[i];
+    for (int j = 0; j < M; ++j) {
+      // joint types in incidence order, base 3 (0: none), first four joints
+      int kv = 0;
+      for (int e = ioff[j], t = 0; e < ioff[j + 1] && t < 4; ++e, ++t) kv = kv * 3 + 1 + jtype[ijoint[e]];
+      bkey[j] = kv;
+    }
+    chunk_order(K, jkey, jord);
+    chunk_order(M, bkey, bord);
+  }
   // chain: a joint's diagonal block collects one part from each of its free
   // bodies, the lower one along the path (slot 0) and the upper one (slot 1)
   std::vector<uint8_t> cfl(K, 0);
@@ -985,6 +1012,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     J.RHf = dnew<float>(ctx, 9 * (size_t)Kx, ok);
     for (int i = 0; i < 4; ++i) dpf[i] = dnew<float>(ctx, 3 * (size_t)Kx, ok);
   }
+  int32_t *djord = jord.empty() ? nullptr : dnew<int32_t>(ctx, jord.size(), ok);
+  int32_t *dbord = bord.empty() ? nullptr : dnew<int32_t>(ctx, bord.size(), ok);
   int32_t *dioff = dnew<int32_t>(ctx, (size_t)M + 1, ok);
   int32_t *dij = dnew<int32_t>(ctx, std::max<size_t>(ijoint.size(), 1), ok);
   int8_t *dis = dnew<int8_t>(ctx, std::max<size_t>(iside.size(), 1), ok);
@@ -1027,6 +1056,10 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   CK(up(dpa2, pa2.data(), pa2.size() * 8));
   CK(up(dpb2, pb2.data(), pb2.size() * 8));
   CK(up(dua, ua.data(), ua.size() * 8));
+  if (djord) CK(up(djord, jord.data(), jord.size() * 4));
+  if (dbord) CK(up(dbord, bord.data(), bord.size() * 4));
+  J.order = djord;
+  B.order = dbord;
   CK(up(dioff, ioff.data(), ioff.size() * 4));
   CK(up(dij, ijoint.data(), ijoint.size() * 4));
   CK(up(dis, iside.data(), iside.size()));

@@ -8,6 +8,8 @@
 namespace mabd {
 
 __device__ __forceinline__ double ldg(const double *p) { return __ldg(p); }
+// index of the entry that thread t handles under a processing order (CHUNK_ORDER)
+__device__ __forceinline__ int ordered(const int32_t *order, int t) { return order ? __ldg(order + t) : t; }
 
 __device__ __forceinline__ void set_status(int *status, int bits) {
   if (status) atomicOr(status, bits);

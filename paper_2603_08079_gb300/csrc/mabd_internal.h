@@ -46,6 +46,9 @@ struct DevBodies {
   double *dqb;          // [12][M] rest-frame increment diag4(R^T) dq (FP64 accumulator)
   float *ubf;           // [12][M] FP32 Hbar^{-1} of the current rhs (u, then each correction)
   float *Rf;            // [9][M]  R rounded to FP32 (written with R)
+  // processing order of the per-body kernels that visit joints: thread t
+  // handles body order[t] (null: body t); see CHUNK_ORDER
+  const int32_t *order;
 };
 
 // joint flags
@@ -70,7 +73,18 @@ struct DevJoints {
   // mixed form: FP32 copies of the joint points and of the hinge frame
   const float *pa1f, *pb1f, *pa2f, *pb2f;  // [3][K]
   float *RHf;                              // [9][K]
+  // processing order of the per-joint kernels: thread t handles joint
+  // order[t] (null: joint t); see CHUNK_ORDER
+  const int32_t *order;
 };
+
+// Per-joint and per-body kernels run CTAs of CHUNK_ORDER threads over runs of
+// CHUNK_ORDER consecutive entries; the processing order partitions each run
+// stably by joint type (for a body: by the types of its joints, in incidence
+// order), so that a warp sees a single type.  On this GPU an FP64
+// instruction occupies a warp for the same time however many of its lanes
+// are active, so a warp that mixes ball and hinge joints pays for both paths.
+constexpr int CHUNK_ORDER = 128;
 
 // body -> incident joints (CSR over internal body order)
 struct DevIncidence {

@@ -53,6 +53,12 @@ bool carve(double *base, int M, int K, Layout &L) {
     return p;
   };
   const size_t m = (size_t)M, k = (size_t)K, d = sizeof(double);
+  // every pointer the step does not use stays null (no processing orders,
+  // no mixed-form arrays)
+  L.B = DevBodies{};
+  L.J = DevJoints{};
+  L.I = DevIncidence{};
+  L.C = DevChain{};
   L.status = (int *)take(2 * sizeof(int));
   L.bad = L.status + 1;
   L.B.M = M;
