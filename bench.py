@@ -301,10 +301,10 @@ def chain_gram_flops(jtype_chain: np.ndarray) -> float:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel, from one ncu capture of the current kernel on the named workload;
-# an entry is removed when its kernel changes.  cr_level: all 21 launches of
-# a step of the 524,288-body chain (675.4 MB) scaled to 1,048,576 bodies and
-# averaged per launch (profiles/chain512k_mixed_dram_launch_list.md).
-TRAFFIC: dict = {("chain1m", "mixed", "cr_level"): 64.3e6}
+# an entry is removed when its kernel changes.  mx_body_prep: one launch on
+# the 524,288-body chain (147.4 + 87.5 MB), scaled to 1,048,576 bodies (the
+# kernel's traffic is per body; profiles/chain512k_mixed_fp32_dual_kernels.md).
+TRAFFIC: dict = {("chain1m", "mixed_fp32_dual", "mx_body_prep"): 469.8e6}
 
 
 def measured_hbm_gbs() -> float:
@@ -315,9 +315,23 @@ def measured_hbm_gbs() -> float:
         return 6800.0   # the profiling recipe's fallback
 
 
-def kernel_model(name: str, jtype_chain: np.ndarray, form: str = "fp64"):
+def body_prep_flops(M: int, polar_iters: float, form: str) -> float:
+    """FP64 flops (FMA = 2) of the per-body kernel over M bodies.  One Newton
+    step of the polar iteration: cofactors 27, determinant 5, reciprocal 1,
+    X <- X/2 + C/(2 det) 27, step and its squared norm 27 (87); the rest-frame
+    rhs: 1/h scalings 4, M_A qdot/h + m g 18, four R^T rotations 60,
+    F = R^T A 45, trace 4, V P(F) 24, subtraction 9 (164); the FP64 form also
+    applies Hbar^{-1} in FP64 (36).  polar_iters: mean Newton steps per body,
+    counted by the kernel (mabd_step_stats.polar_iterations)."""
+    rest = 164 + (36 if form == "fp64" else 0)
+    return float(M) * (rest + 87.0 * polar_iters)
+
+
+def kernel_model(name: str, jtype_chain: np.ndarray, form: str = "fp64", polar_iters: float | None = None):
     """(bound, algorithmic work of one step's launches of `name`): FP64 flops
     ("alu") or HBM bytes ("hbm"), or None without a model."""
+    if name in ("body_prep", "mx_body_prep") and polar_iters is not None:
+        return "alu", body_prep_flops(len(jtype_chain) - 1, polar_iters, form)
     if form != "mixed_fp32_dual" and (name.startswith("cr_reduce") or name == "cr_level"):
         return "alu", cr_reduce_flops(jtype_chain)
     if name == "chain_gram":
@@ -445,7 +459,8 @@ def run_gpu(args):
         per_launch_ms = dms / dn
         launches_per_step = sum(n for _, n in kt.values()) / args.profile_steps
         dom_launches = dn / args.profile_steps
-        model = kernel_model(dname, sc["jtype"], form) if args.workload == "chain1m" else None
+        model = (kernel_model(dname, sc["jtype"], form, st.get("polar_iterations"))
+                 if args.workload == "chain1m" else None)
         if model is not None and model[0] == "alu":
             step_flops = model[1]
             flops = step_flops / dom_launches     # per launch, averaged over the levels
@@ -456,6 +471,8 @@ def run_gpu(args):
                     "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz (probe measured 1.20)",
                     "kernel_ms_per_launch": round(per_launch_ms, 5),
                     "flops_per_step": step_flops, "launches_per_step": dom_launches}
+            if dname in ("body_prep", "mx_body_prep"):
+                roof["polar_iterations_per_body"] = round(st["polar_iterations"], 4)
         elif model is not None:
             step_bytes = model[1]
             achieved = step_bytes / dom_launches / (per_launch_ms / 1e3) / 1e9

@@ -142,6 +142,8 @@ typedef struct {
   double pcg_rel_residual; /* final |r|/|b| of PCG (0 for direct solvers) */
   double refine_residual;  /* MABD_MIXED: max over rows of |C(q_n) + G dq| (FP64) entering the
                               last correction sweep (0 for FP64 or without sweeps) */
+  double polar_iterations; /* mean Newton iterations per body of the polar decomposition
+                              R = polar(A) (Eq. polar) in this step */
 } mabd_step_stats;
 
 typedef struct {

@@ -11,8 +11,6 @@ namespace mabd {
 
 __device__ __forceinline__ int pk(int r, int c) { return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r; }
 
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
 // the per-body Gram parts of level 0 in the reduction's precision
 template <typename T> struct CRS;
@@ -32,8 +30,9 @@ template <> struct CRS<float> {
 template <typename T>
 __device__ __forceinline__ void cr_put(double *out64, T *outT, size_t o, T v, double *acc) {
   if (out64) {
-    out64[o] = (double)v;
-    if (acc) acc[o] += (double)v;
+    const double v64 = to_f64(v);
+    out64[o] = v64;
+    if (acc) acc[o] += v64;
   } else {
     outT[o] = v;
   }
@@ -98,7 +97,7 @@ __device__ __forceinline__ void ld_b(const DevChain &C, const DevJoints &J, cons
     const int k = n - C.off;
     const int Cs = k < 0 ? 0 : (J.type[k] == 0 ? 3 : 5);
 #pragma unroll
-    for (int r = 0; r < 5; ++r) b[r] = r < Cs ? (T)J.b[(size_t)r * J.K + k] : T(0);
+    for (int r = 0; r < 5; ++r) b[r] = r < Cs ? from_f64<T>(J.b[(size_t)r * J.K + k]) : T(0);
   } else {
 #pragma unroll
     for (int r = 0; r < 5; ++r) b[r] = L.b[(size_t)r * L.N + n];
@@ -522,7 +521,7 @@ __device__ __forceinline__ T ldb1(const DevChain &C, const DevJoints &J, const C
   const int k = n - C.off;
   if (k < 0) return T(0);
   const int Cs = J.type[k] == 0 ? 3 : 5;
-  return r < Cs ? (T)J.b[(size_t)r * J.K + k] : T(0);
+  return r < Cs ? from_f64<T>(J.b[(size_t)r * J.K + k]) : T(0);
 }
 
 // per-warp shared workspace of one eliminated row

@@ -11,14 +11,17 @@ namespace mabd {
 // (Eq. newton_abd rhs at x = x_n, co-rotated linear elasticity of Sec. 3.3),
 // expressed in the rest frame: fbar = diag4(R^T)(M_A qdot/h + [0; m g]) - [V vec P; 0];
 // ubar = Hbar^{-1} fbar (Eq. abd_final).
-__global__ void __launch_bounds__(128) k_body_prep(DevBodies B, StepParams p, int *status) {
+__global__ void __launch_bounds__(128) k_body_prep(DevBodies B, StepParams p, int *status,
+                                                      unsigned long long *iters) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= B.M) return;
   const int M = B.M;
   double q[12], qd[12], A[9], R[9];
   load12(B.q, M, j, q);
   A_from_q(q, A);
-  int st = polar3(A, R);
+  int nit = 0;
+  int st = polar3(A, R, &nit);
+  if (iters) count_add(iters, (unsigned)nit);
   if (st) {
     set_status(status, st);
 #pragma unroll
@@ -34,15 +37,16 @@ __global__ void __launch_bounds__(128) k_body_prep(DevBodies B, StepParams p, in
   load12(B.qd, M, j, qd);
   const double s0 = ldg(B.sig + j), s1 = ldg(B.sig + M + j), s2 = ldg(B.sig + 2 * (size_t)M + j);
   const double m = ldg(B.mass + j);
+  const double sh0 = s0 * p.inv_h, sh1 = s1 * p.inv_h, sh2 = s2 * p.inv_h, mh = m * p.inv_h;
   const double vmu = ldg(B.vmu + j), vlam = ldg(B.vlam + j);
   // world-frame inertial + gravity force, then rotate each 3-block by R^T
   double fw[12];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    fw[a] = s0 * qd[a] * p.inv_h;
-    fw[3 + a] = s1 * qd[3 + a] * p.inv_h;
-    fw[6 + a] = s2 * qd[6 + a] * p.inv_h;
-    fw[9 + a] = m * (qd[9 + a] * p.inv_h + p.g[a]);
+    fw[a] = sh0 * qd[a];
+    fw[3 + a] = sh1 * qd[3 + a];
+    fw[6 + a] = sh2 * qd[6 + a];
+    fw[9 + a] = mh * qd[9 + a] + m * p.g[a];
   }
   double fb[12];
 #pragma unroll
@@ -405,8 +409,9 @@ void launch_state_out(const DevBodies &B, const int32_t *boi, double *stage, cud
   if (B.M > 0) k_state_out<<<nblk(B.M, 128), 128, 0, s>>>(B, boi, stage);
 }
 
-void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s) {
-  if (B.M > 0) k_body_prep<<<nblk(B.M, 128), 128, 0, s>>>(B, p, status);
+void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s,
+                      unsigned long long *iters) {
+  if (B.M > 0) k_body_prep<<<nblk(B.M, 128), 128, 0, s>>>(B, p, status, iters);
 }
 
 void launch_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,

@@ -63,22 +63,13 @@ __device__ __forceinline__ void hbar_apply(const double s[3], double m, double v
   y[11] = mt * x[11];
 }
 
-// joint points and hinge frames in the precision of the products
-template <typename T> struct JP;
-template <> struct JP<double> {
-  __device__ static const double *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1 : J.pb1; }
-  __device__ static const double *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2 : J.pb2; }
-  __device__ static const double *RH(const DevJoints &J) { return J.RH; }
-};
-template <> struct JP<float> {
-  __device__ static const float *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1f : J.pb1f; }
-  __device__ static const float *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2f : J.pb2f; }
-  __device__ static const float *RH(const DevJoints &J) { return J.RHf; }
-};
 
 // g = diag4(R^T) sum_k G_kj^T lam_k for body j: a row with point p and world
 // direction d contributes s [p; 1] (x) (R^T d) lam_r (s = +1 on body a, -1 on b)
-template <typename T>
+// (HWCVT: multipliers converted with the conversion instruction instead of
+// fconv.h's integer path; the final kernel, which is not bound by the FP64
+// unit, runs faster that way)
+template <typename T, bool HWCVT = false>
 __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence &I, int j,
                                           const T R[9], const double *lam, T g[12]) {
   const int K = J.K;
@@ -92,7 +83,7 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
     const T sgn = side == 0 ? T(1) : T(-1);
     T l[5];
 #pragma unroll
-    for (int r = 0; r < 5; ++r) l[r] = (T)lam[(size_t)r * K + k];
+    for (int r = 0; r < 5; ++r) l[r] = HWCVT ? (T)lam[(size_t)r * K + k] : from_f64<T>(lam[(size_t)r * K + k]);
     const T *p1 = JP<T>::p1(J, side);
     const T *p2 = JP<T>::p2(J, side);
     T F1[3], F2[3], P1[3], P2[3];
@@ -151,14 +142,17 @@ __device__ __forceinline__ void disp_at(const T R[9], const T x[12], const T p[3
 // One thread per body: R = polar(A) and the rest-frame rhs
 // fbar = diag4(R^T)(M_A qdot/h + [0; m g]) - [V vec P(R^T A); 0] in FP64
 // (Sec. 3.3-3.4); u = Hbar^{-1} fbar in FP32.
-__global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p, int *status) {
+__global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p, int *status,
+                                                      unsigned long long *iters) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= B.M) return;
   const int M = B.M;
   double q[12], qd[12], A[9], R[9];
   load12(B.q, M, j, q);
   A_from_q(q, A);
-  int st = polar3(A, R);
+  int nit = 0;
+  int st = polar3(A, R, &nit);
+  if (iters) count_add(iters, (unsigned)nit);
   if (st) {
     set_status(status, st);
 #pragma unroll
@@ -167,20 +161,21 @@ __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p,
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     B.R[(size_t)i * M + j] = R[i];
-    B.Rf[(size_t)i * M + j] = (float)R[i];
+    B.Rf[(size_t)i * M + j] = d2f(R[i]);
   }
   if (B.fixed[j]) return;  // no unknowns; its rotation may still orient a hinge
   load12(B.qd, M, j, qd);
   const double s0 = ldg(B.sig + j), s1 = ldg(B.sig + M + j), s2 = ldg(B.sig + 2 * (size_t)M + j);
   const double m = ldg(B.mass + j);
+  const double sh0 = s0 * p.inv_h, sh1 = s1 * p.inv_h, sh2 = s2 * p.inv_h, mh = m * p.inv_h;
   const double vmu = ldg(B.vmu + j), vlam = ldg(B.vlam + j);
   double fw[12];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    fw[a] = s0 * qd[a] * p.inv_h;
-    fw[3 + a] = s1 * qd[3 + a] * p.inv_h;
-    fw[6 + a] = s2 * qd[6 + a] * p.inv_h;
-    fw[9 + a] = m * (qd[9 + a] * p.inv_h + p.g[a]);
+    fw[a] = sh0 * qd[a];
+    fw[3 + a] = sh1 * qd[3 + a];
+    fw[6 + a] = sh2 * qd[6 + a];
+    fw[9 + a] = mh * qd[9 + a] + m * p.g[a];
   }
   double fb[12];
 #pragma unroll
@@ -203,7 +198,7 @@ __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p,
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
     B.fbar[(size_t)i * M + j] = fb[i];
-    ff[i] = (float)fb[i];
+    ff[i] = d2f(fb[i]);
   }
   hinv_apply_t(hf, ff, u);
 #pragma unroll
@@ -259,7 +254,7 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       J.c[(size_t)r * K + k] = d[0][r];
-      J.b[(size_t)r * K + k] = (double)g[0][r] + rr * d[0][r];
+      J.b[(size_t)r * K + k] = f2d(g[0][r]) + rr * d[0][r];
     }
     return;
   }
@@ -275,7 +270,7 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
   hinge_frame(a, RH);
   float RHf[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) RHf[i] = (float)RH[i];
+  for (int i = 0; i < 9; ++i) RHf[i] = d2f(RH[i]);
   double c1[3], c2[3];
   float e1[3], e2[3];
   mv3(RH, d[0], c1);
@@ -290,7 +285,7 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
     J.c[(size_t)r * K + k] = cc[r];
-    J.b[(size_t)r * K + k] = (double)gg[r] + rr * cc[r];
+    J.b[(size_t)r * K + k] = f2d(gg[r]) + rr * cc[r];
   }
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -322,24 +317,24 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
   gen_force<double>(J, I, j, R, J.lambda, g64);
   if (FIRST) {
 #pragma unroll
-    for (int i = 0; i < 12; ++i) gf[i] = (float)g64[i];
+    for (int i = 0; i < 12; ++i) gf[i] = d2f(g64[i]);
     hinv_apply_t(hf, gf, w);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) dq[i] = (double)(uf[i] - w[i]);
+    for (int i = 0; i < 12; ++i) dq[i] = f2d(uf[i] - w[i]);
   } else {
     float Rf[9];
     load_Rf(B, j, Rf);
     gen_force<float>(J, I, j, Rf, J.dlam, gf);
     hinv_apply_t(hf, gf, w);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) dq[i] = B.dqb[(size_t)i * M + j] + (double)(uf[i] - w[i]);
+    for (int i = 0; i < 12; ++i) dq[i] = B.dqb[(size_t)i * M + j] + f2d(uf[i] - w[i]);
   }
   const double s[3] = {ldg(B.sig + j), ldg(B.sig + M + j), ldg(B.sig + 2 * (size_t)M + j)};
   double hq[12];
   hbar_apply(s, ldg(B.mass + j), ldg(B.vmu + j), ldg(B.vlam + j), p.inv_h * p.inv_h, dq, hq);
   float rf[12], z[12];
 #pragma unroll
-  for (int i = 0; i < 12; ++i) rf[i] = (float)(B.fbar[(size_t)i * M + j] - hq[i] - g64[i]);
+  for (int i = 0; i < 12; ++i) rf[i] = d2f(B.fbar[(size_t)i * M + j] - hq[i] - g64[i]);
   hinv_apply_t(hf, rf, z);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
@@ -433,7 +428,7 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
     for (int r = 0; r < C; ++r) {
       const double res = (p.residual_rhs ? J.c[(size_t)r * K + k] : 0.0) + v[r];
       worst = fmax(worst, fabs(res));
-      J.b[(size_t)r * K + k] = (double)w[r] + res;
+      J.b[(size_t)r * K + k] = f2d(w[r]) + res;
     }
   }
   if (maxbit) {
@@ -458,7 +453,7 @@ __global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevI
   float Rf[9], hf[16], gf[12], w[12];
   load_Rf(B, j, Rf);
   load_hinvf(B, j, hf);
-  gen_force<float>(J, I, j, Rf, from_u ? J.lambda : J.dlam, gf);
+  gen_force<float, true>(J, I, j, Rf, from_u ? J.lambda : J.dlam, gf);
   hinv_apply_t(hf, gf, w);
   double x[12];
 #pragma unroll
@@ -481,8 +476,9 @@ __global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevI
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
-void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s) {
-  if (B.M > 0) k_mx_body_prep<<<nblk(B.M, 128), 128, 0, s>>>(B, p, status);
+void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s,
+                         unsigned long long *iters) {
+  if (B.M > 0) k_mx_body_prep<<<nblk(B.M, 128), 128, 0, s>>>(B, p, status, iters);
 }
 
 void launch_mx_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,

@@ -1442,7 +1442,9 @@ extern "C" {
 // sweeps through the stored factors, then the state update
 static void enqueue_mixed_chain(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
   const StepParams &p = ctx->sp;
-  run(ctx, "mx_body_prep", [&] { launch_mx_body_prep(ctx->B, p, ctx->d_status, s); });
+  run(ctx, "mx_body_prep", [&] {
+    launch_mx_body_prep(ctx->B, p, ctx->d_status, s, maxbits ? maxbits + 3 : nullptr);
+  });
   if (ctx->J.K == 0) {
     run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, true, s); });
     return;
@@ -1464,10 +1466,11 @@ static void enqueue_mixed_chain(mabd_ctx *ctx, unsigned long long *maxbits, cuda
   run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, sweeps == 0, s); });
 }
 
-static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s) {
+// iters (may be null): the step's polar-iteration counter
+static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s, unsigned long long *iters = nullptr) {
   const StepParams &p = ctx->sp;
   if (ctx->cfg.precision != MABD_FP64) return;  // the whole step is in enqueue_post
-  run(ctx, "body_prep", [&] { launch_body_prep(ctx->B, p, ctx->d_status, s); });
+  run(ctx, "body_prep", [&] { launch_body_prep(ctx->B, p, ctx->d_status, s, iters); });
   if (ctx->J.K == 0) return;
   run(ctx, "joint_prep", [&] { launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
   if (ctx->solver == MABD_SOLVER_CHAIN) {
@@ -1601,7 +1604,9 @@ static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, d
 static mabd_status step_mixed_pcg(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
   const StepParams &p = ctx->sp;
   ctx->pcg_last_iters = 0;
-  run(ctx, "mx_body_prep", [&] { launch_mx_body_prep(ctx->B, p, ctx->d_status, s); });
+  run(ctx, "mx_body_prep", [&] {
+    launch_mx_body_prep(ctx->B, p, ctx->d_status, s, maxbits ? maxbits + 3 : nullptr);
+  });
   run(ctx, "mx_joint_prep", [&] { launch_mx_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
   if (ctx->lpc_on) {
     run(ctx, "lpc_blocks", [&] { launch_lpc_blocks(ctx->B, ctx->J, ctx->lg, ctx->la, ctx->d_status, s); });
@@ -1623,6 +1628,10 @@ static mabd_status step_mixed_pcg(mabd_ctx *ctx, unsigned long long *maxbits, cu
   return MABD_OK;
 }
 
+// per-step statistics slots: max |G dq + C|, max |C(q_{n+1})|, the refinement
+// residual (bit patterns of non-negative doubles), polar iterations (count)
+constexpr int STAT_SLOTS = 4;
+
 static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
   cudaStream_t s = ctx->stream;
   if (ctx->cfg.precision != MABD_FP64 && ctx->solver == MABD_SOLVER_PCG && ctx->J.K > 0) {
@@ -1632,7 +1641,7 @@ static mabd_status step_once(mabd_ctx *ctx, unsigned long long *maxbits) {
     if (e == cudaSuccess && ctx->debug_err != cudaSuccess) e = ctx->debug_err;
     return cuda_fail(ctx, e);
   }
-  enqueue_pre(ctx, s);
+  enqueue_pre(ctx, s, maxbits ? maxbits + 3 : nullptr);
   if (ctx->J.K > 0 && ctx->solver == MABD_SOLVER_PCG) {
     mabd_status st = pcg_loop(ctx, s, nullptr);
     if (st) return st;
@@ -1713,11 +1722,11 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
   if (stats) {
     if (ctx->max_cap < nsteps) {
       bool ok = true;
-      ctx->d_max = dnew<unsigned long long>(ctx, 3 * (size_t)nsteps, ok);
+      ctx->d_max = dnew<unsigned long long>(ctx, STAT_SLOTS * (size_t)nsteps, ok);
       if (!ok) return MABD_ERR_OUT_OF_MEMORY;
       ctx->max_cap = nsteps;
     }
-    CK(cudaMemsetAsync(ctx->d_max, 0, 3 * (size_t)nsteps * 8, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_max, 0, STAT_SLOTS * (size_t)nsteps * 8, ctx->stream));
   }
   if (!stats && !ctx->prof_on && !ctx->debug_sync && graphs_ready(ctx)) {
     // order the private graph stream after the caller's stream and back
@@ -1734,7 +1743,7 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
   std::vector<int> pit(nsteps, 0);
   std::vector<double> prel(nsteps, 0.0);
   for (int i = 0; i < nsteps; ++i) {
-    mabd_status st = step_once(ctx, stats ? ctx->d_max + 3 * i : nullptr);
+    mabd_status st = step_once(ctx, stats ? ctx->d_max + STAT_SLOTS * i : nullptr);
     if (st) return st;
     if (ctx->solver == MABD_SOLVER_PCG) {
       pit[i] = ctx->pcg_last_iters;
@@ -1742,20 +1751,21 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
     }
   }
   if (!stats) return MABD_OK;
-  std::vector<unsigned long long> hb(3 * (size_t)nsteps);
+  std::vector<unsigned long long> hb(STAT_SLOTS * (size_t)nsteps);
   CK(cudaMemcpyAsync(hb.data(), ctx->d_max, hb.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < nsteps; ++i) {
     double lin, nl;
     double ref;
-    std::memcpy(&lin, &hb[3 * i], 8);
-    std::memcpy(&nl, &hb[3 * i + 1], 8);
-    std::memcpy(&ref, &hb[3 * i + 2], 8);
+    std::memcpy(&lin, &hb[STAT_SLOTS * i], 8);
+    std::memcpy(&nl, &hb[STAT_SLOTS * i + 1], 8);
+    std::memcpy(&ref, &hb[STAT_SLOTS * i + 2], 8);
     stats[i].lin_residual = lin;
     stats[i].joint_residual = nl;
     stats[i].pcg_iters = pit[i];
     stats[i].pcg_rel_residual = prel[i];
     stats[i].refine_residual = ctx->cfg.precision != MABD_FP64 ? ref : 0.0;
+    stats[i].polar_iterations = ctx->B.M > 0 ? (double)hb[STAT_SLOTS * i + 3] / ctx->B.M : 0.0;
   }
   return read_status(ctx);
 }

@@ -4,6 +4,7 @@
 #include <cstdint>
 
 #include "mabd_internal.h"
+#include "fconv.h"
 
 namespace mabd {
 
@@ -23,13 +24,15 @@ __device__ __forceinline__ void A_from_q(const double q[12], double A[9]) {
     for (int c = 0; c < 3; ++c) A[3 * r + c] = q[3 * c + r];
 }
 
-__device__ __forceinline__ void mv3(const double M[9], const double x[3], double y[3]) {
+template <typename S>
+__device__ __forceinline__ void mv3(const S M[9], const S x[3], S y[3]) {
   y[0] = M[0] * x[0] + M[1] * x[1] + M[2] * x[2];
   y[1] = M[3] * x[0] + M[4] * x[1] + M[5] * x[2];
   y[2] = M[6] * x[0] + M[7] * x[1] + M[8] * x[2];
 }
 
-__device__ __forceinline__ void mtv3(const double M[9], const double x[3], double y[3]) {
+template <typename S>
+__device__ __forceinline__ void mtv3(const S M[9], const S x[3], S y[3]) {
   y[0] = M[0] * x[0] + M[3] * x[1] + M[6] * x[2];
   y[1] = M[1] * x[0] + M[4] * x[1] + M[7] * x[2];
   y[2] = M[2] * x[0] + M[5] * x[1] + M[8] * x[2];
@@ -60,15 +63,13 @@ __device__ __forceinline__ void gap_of(const double qa[12], const double pa[3], 
 
 // Eq. polar: R = A (A^T A)^{-1/2} by Newton's iteration X <- (X + X^{-T})/2,
 // X^{-T} = cof(X)/det(X).  Returns a ST_* code (0 on success).
-__device__ __forceinline__ int polar3(const double A[9], double R[9]) {
+// The first step's determinant is det A, so the step loop also makes the
+// det A <= 0 check.  The stopping test compares the squared step with
+// 1e-18 |R|^2 = 3e-18 (the iterate tends to a rotation, |R|_F^2 = 3).
+__device__ __forceinline__ int polar3(const double A[9], double R[9], int *iters = nullptr) {
   double X[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) X[i] = A[i];
-  {
-    double d = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
-               X[2] * (X[3] * X[7] - X[4] * X[6]);
-    if (!(d > 0.0)) return isfinite(d) ? ST_INVERTED : ST_NONFINITE;
-  }
   int it = 0;
   for (; it < 40; ++it) {
     double C[9];
@@ -84,23 +85,30 @@ __device__ __forceinline__ int polar3(const double A[9], double R[9]) {
     double d = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
     if (!(d > 0.0)) return isfinite(d) ? ST_INVERTED : ST_NONFINITE;
     double hid = 0.5 / d;
-    double diff = 0.0, nrm = 0.0;
+    double diff = 0.0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       double y = 0.5 * X[i] + hid * C[i];
       double dx = y - X[i];
       diff += dx * dx;
-      nrm += y * y;
       X[i] = y;
     }
     // quadratic convergence: a relative change below 1e-9 leaves an error
     // of order 1e-18 in the iterate just formed
-    if (diff <= 1e-18 * nrm) break;
+    if (diff <= 3e-18) break;
   }
   if (it == 40) return ST_POLAR_NOCONV;
 #pragma unroll
   for (int i = 0; i < 9; ++i) R[i] = X[i];
+  if (iters) *iters = it + 1;
   return 0;
+}
+
+// *c += v summed over the converged lanes of the warp (one atomic per warp)
+__device__ __forceinline__ void count_add(unsigned long long *c, unsigned v) {
+  const unsigned mask = __activemask();
+  const unsigned sum = __reduce_add_sync(mask, v);
+  if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(c, (unsigned long long)sum);
 }
 
 // Sec. 4.3: R_H = I + [v]x + [v]x^2 / (1 + a_y), v = a x e_y = (-a_z, 0, a_x)
@@ -123,11 +131,12 @@ __device__ __forceinline__ void hinge_frame(const double a[3], double RH[9]) {
 
 // world direction of constraint row r (Eq. ball: identity rows; Eq. hinge:
 // rows 0-2 are the rows of R_H, rows 3 and 4 its x and z rows at the second point)
-__device__ __forceinline__ void row_dir(int type, const double RH[9], int r, double d[3]) {
+template <typename S>
+__device__ __forceinline__ void row_dir(int type, const S RH[9], int r, S d[3]) {
   if (type == 0) {
-    d[0] = r == 0 ? 1.0 : 0.0;
-    d[1] = r == 1 ? 1.0 : 0.0;
-    d[2] = r == 2 ? 1.0 : 0.0;
+    d[0] = r == 0 ? S(1) : S(0);
+    d[1] = r == 1 ? S(1) : S(0);
+    d[2] = r == 2 ? S(1) : S(0);
   } else {
     int rr = r < 3 ? r : (r == 3 ? 0 : 2);
     d[0] = RH[3 * rr];
@@ -141,42 +150,62 @@ __device__ __forceinline__ void load_hinv(const DevBodies &B, int j, double h[16
   for (int i = 0; i < 16; ++i) h[i] = ldg(B.hinv + (size_t)i * B.M + j);
 }
 
-__device__ __forceinline__ void load_R(const double *R, int N, int j, double out[9]) {
+template <typename S>
+__device__ __forceinline__ void load_R(const S *R, int N, int j, S out[9]) {
 #pragma unroll
   for (int i = 0; i < 9; ++i) out[i] = R[(size_t)i * N + j];
 }
 
-__device__ __forceinline__ void load12(const double *p, int N, int j, double out[12]) {
+template <typename S>
+__device__ __forceinline__ void load12(const S *p, int N, int j, S out[12]) {
 #pragma unroll
   for (int i = 0; i < 12; ++i) out[i] = p[(size_t)i * N + j];
 }
 
-__device__ __forceinline__ void load3(const double *p, int N, int j, double out[3]) {
-  out[0] = ldg(p + j);
-  out[1] = ldg(p + (size_t)N + j);
-  out[2] = ldg(p + 2 * (size_t)N + j);
+template <typename S>
+__device__ __forceinline__ void load3(const S *p, int N, int j, S out[3]) {
+  out[0] = __ldg(p + j);
+  out[1] = __ldg(p + (size_t)N + j);
+  out[2] = __ldg(p + 2 * (size_t)N + j);
 }
+
+// joint points and hinge frames in the precision of the products (the FP32
+// copies exist in the mixed-precision forms)
+template <typename S> struct JP;
+template <> struct JP<double> {
+  __device__ static const double *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1 : J.pb1; }
+  __device__ static const double *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2 : J.pb2; }
+  __device__ static const double *RH(const DevJoints &J) { return J.RH; }
+};
+template <> struct JP<float> {
+  __device__ static const float *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1f : J.pb1f; }
+  __device__ static const float *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2f : J.pb2f; }
+  __device__ static const float *RH(const DevJoints &J) { return J.RHf; }
+};
+
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
 // Rows of joint k on the body with rotation R that is its side `side`
 // (0: body a, 1: body b): row r is s [p; 1] (x) (R^T d_r) in that body's rest
 // frame (frozen frame, Eq. pcpq), s = +1 on a and -1 on b.  Writes the
 // directions E[r], the points P[0..1] and the point index pt[r]; returns C.
-__device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int side,
-                                               const double R[9], double E[5][3],
-                                               double P[2][3], int pt[5]) {
+template <typename S>
+__device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int side, const S R[9],
+                                               S E[5][3], S P[2][3], int pt[5]) {
   const int K = J.K;
   const int type = J.type[k];
-  const double sgn = side == 0 ? 1.0 : -1.0;
-  load3(side == 0 ? J.pa1 : J.pb1, K, k, P[0]);
-  double RH[9];
+  const S sgn = side == 0 ? S(1) : S(-1);
+  load3(JP<S>::p1(J, side), K, k, P[0]);
+  S RH[9];
   if (type == 1) {
-    load3(side == 0 ? J.pa2 : J.pb2, K, k, P[1]);
+    load3(JP<S>::p2(J, side), K, k, P[1]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) RH[i] = J.RH[(size_t)i * K + k];
+    for (int i = 0; i < 9; ++i) RH[i] = JP<S>::RH(J)[(size_t)i * K + k];
   }
   const int C = type == 0 ? 3 : 5;
   for (int r = 0; r < C; ++r) {
-    double d[3], e[3];
+    S d[3], e[3];
     row_dir(type, RH, r, d);
     mtv3(R, d, e);
     E[r][0] = sgn * e[0];
@@ -188,7 +217,8 @@ __device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int si
 }
 
 // w = [p; 1] (x) e as a 12-vector
-__device__ __forceinline__ void kron_row(const double p[3], const double e[3], double w[12]) {
+template <typename S>
+__device__ __forceinline__ void kron_row(const S p[3], const S e[3], S w[12]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     w[a] = p[0] * e[a];
@@ -199,7 +229,8 @@ __device__ __forceinline__ void kron_row(const double p[3], const double e[3], d
 }
 
 // y = Hbar^{-1} v with the structured inverse h[16] (see mabd_internal.h)
-__device__ __forceinline__ void hinv_apply(const double h[16], const double v[12], double y[12]) {
+template <typename S>
+__device__ __forceinline__ void hinv_apply(const S h[16], const S v[12], S y[12]) {
   y[0] = h[1] * v[0] + h[2] * v[4] + h[3] * v[8];
   y[4] = h[2] * v[0] + h[4] * v[4] + h[5] * v[8];
   y[8] = h[3] * v[0] + h[5] * v[4] + h[6] * v[8];

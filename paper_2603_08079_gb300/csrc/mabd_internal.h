@@ -243,7 +243,9 @@ struct StepParams {
 };
 
 // kernel launchers (k_body.cu)
-void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s);
+// iters (may be null): += Newton iterations of the polar decomposition, summed over bodies
+void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s,
+                      unsigned long long *iters = nullptr);
 void launch_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,
                        cudaStream_t s);
 void launch_backprop(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
@@ -348,7 +350,8 @@ void launch_lpc_loss_grad(const LpcGraph &G, const LpcAct &A, const LpcNet &N, c
 void launch_lpc_adam(float *P, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
 
 // mixed-precision form of the chain step (k_mixed.cu)
-void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s);
+void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s,
+                         unsigned long long *iters = nullptr);
 void launch_mx_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,
                           cudaStream_t s);
 void launch_mx_chain_gram(const DevBodies &B, const DevJoints &J, const DevIncidence &I,

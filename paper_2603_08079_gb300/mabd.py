@@ -46,7 +46,7 @@ class Config(C.Structure):
 class StepStats(C.Structure):
     _fields_ = [("lin_residual", C.c_double), ("joint_residual", C.c_double),
                 ("pcg_iters", C.c_int32), ("pcg_rel_residual", C.c_double),
-                ("refine_residual", C.c_double)]
+                ("refine_residual", C.c_double), ("polar_iterations", C.c_double)]
 
 
 class Info(C.Structure):

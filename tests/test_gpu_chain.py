@@ -127,3 +127,28 @@ def test_full_size_pulley_chain(ora):
     sc = scenes.long_chain(1 << 20, seed=1)
     e_qd, e_lam, st, ost = assert_parity(ora, sc, sc["q"], sc["qdot"])
     assert st["joint_residual"] < 1e-5  # Table 1, huge pulley row
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_polar_iteration_count(ora, precision):
+    """mabd_step_stats.polar_iterations: one Newton step where A is a
+    rotation already (the first step does not move it), three where A
+    carries a 1e-3 symmetric stretch (steps ~1e-3, ~5e-7, then below the
+    1e-9 stopping size); the step stays within parity either way."""
+    need_gpu()
+    sc = scenes.chain_cubes(16)
+    s = gpu_solver(sc, precision=precision)
+    try:
+        _, _, _, st = gpu_step(s, sc["q"], sc["qdot"])
+        assert st[0]["polar_iterations"] == 1.0
+        q, qd = scenes.perturb_state(sc, seed=4, rot=0.3, vel=0.1)
+        rng = np.random.default_rng(9)
+        for j in range(len(q)):
+            E = rng.standard_normal((3, 3)) * 1e-3
+            A = q[j, :9].reshape(3, 3).T @ (np.eye(3) + 0.5 * (E + E.T))  # q stacks A's columns
+            q[j, :9] = A.T.reshape(9)
+        _, _, _, st = gpu_step(s, q, qd)
+        assert 3.0 <= st[0]["polar_iterations"] <= 4.0
+    finally:
+        s.close()
+    assert_parity(ora, sc, q, qd, tol=1e-9 if precision == "fp64" else 1e-6, gpu_kw={"precision": precision})
