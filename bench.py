@@ -76,8 +76,8 @@ FORMS = {
              "graphs); FP64 polar, rhs, constraint values, chain cyclic reduction and %d FP64 "
              "residual-correction sweep(s)",
     "mixed_fp32_dual": "FP32 per-body/per-joint products, Gram blocks and chain cyclic reduction "
-                       "(FP32 PCG on graphs); FP64 polar, rhs, constraint values and %d FP64 "
-                       "residual-correction sweep(s) of the FP64 system",
+                       "or tree elimination (FP32 PCG on graphs); FP64 polar, rhs, constraint "
+                       "values and %d FP64 residual-correction sweep(s) of the FP64 system",
 }
 
 
@@ -108,13 +108,12 @@ def use_learned(args, form: str):
 
 
 def chosen_form(args) -> str:
-    """The mixed form exists for chains and for the PCG path (nets); trees
-    and the batched forest run FP64."""
+    """Chains, trees and the batched forest: the FP32 elimination refined by
+    FP64 sweeps; nets: the FP32 PCG (learned preconditioner) refined by FP64
+    sweeps."""
     if args.precision != "auto":
         return args.precision
-    if args.workload == "chain1m":
-        return "mixed_fp32_dual"
-    return "mixed" if args.workload == "net64x64x16" else "fp64"
+    return "mixed" if args.workload == "net64x64x16" else "mixed_fp32_dual"
 
 
 def dist_env():
@@ -434,7 +433,7 @@ def run_gpu(args):
     others = {}
     if form != "fp64":
         variants = [("plain_fp64_gpu", dict(precision="fp64"), None)]
-        if form == "mixed_fp32_dual":
+        if form == "mixed_fp32_dual" and args.workload == "chain1m":
             variants.append(("mixed_fp64_reduction_gpu", dict(precision="mixed", refine_steps=args.refine),
                              None))
         if learned is not None:

@@ -294,13 +294,13 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
   }
 }
 
-// One thread per body, start of a correction sweep.  First sweep:
+// One thread per body, start of a correction sweep.  First chain sweep:
 // dqb = u - Hbar^{-1} g(lambda) in FP32 (back-propagation of the approximate
-// solve); later sweeps: dqb += z - Hbar^{-1} g(dlambda) (the previous
-// correction).  Then the FP64 primal residual
+// solve); later chain sweeps: dqb += z - Hbar^{-1} g(dlambda) (the previous
+// correction); tree: dqb as the elimination left it.  Then the FP64 primal residual
 // rb = fbar - Hbar dqb - g(lambda) and the correction's unconstrained solve
 // z = Hbar^{-1} rb in FP32 (kept in ubf).
-template <bool FIRST>
+template <int MODE>
 __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, DevIncidence I,
                                                      StepParams p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -315,19 +315,21 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
 #pragma unroll
   for (int i = 0; i < 12; ++i) uf[i] = B.ubf[(size_t)i * M + j];
   gen_force<double>(J, I, j, R, J.lambda, g64);
-  if (FIRST) {
+  if (MODE == MX_FROM_U) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) gf[i] = d2f(g64[i]);
     hinv_apply_t(hf, gf, w);
 #pragma unroll
     for (int i = 0; i < 12; ++i) dq[i] = f2d(uf[i] - w[i]);
-  } else {
+  } else if (MODE == MX_FROM_CORRECTION) {
     float Rf[9];
     load_Rf(B, j, Rf);
     gen_force<float>(J, I, j, Rf, J.dlam, gf);
     hinv_apply_t(hf, gf, w);
 #pragma unroll
     for (int i = 0; i < 12; ++i) dq[i] = B.dqb[(size_t)i * M + j] + f2d(uf[i] - w[i]);
+  } else {
+    load12(B.dqb, M, j, dq);
   }
   const double s[3] = {ldg(B.sig + j), ldg(B.sig + M + j), ldg(B.sig + 2 * (size_t)M + j)};
   double hq[12];
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
   hinv_apply_t(hf, rf, z);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    B.dqb[(size_t)i * M + j] = dq[i];
+    if (MODE != MX_FROM_DQB) B.dqb[(size_t)i * M + j] = dq[i];
     B.ubf[(size_t)i * M + j] = z[i];
   }
 }
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
 // largest |C + G dq| goes to *maxbit when it is given.  With the printed zero
 // bottom rhs (residual_rhs = 0) the constraint is G dq = 0 and C drops out.
 __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, StepParams p,
-                                                      unsigned long long *maxbit) {
+                                                      unsigned long long *maxbit, bool add_gz) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double worst = 0.0;
   if (t < J.K) {
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
     for (int r = 0; r < C; ++r) {
       const double res = (p.residual_rhs ? J.c[(size_t)r * K + k] : 0.0) + v[r];
       worst = fmax(worst, fabs(res));
-      J.b[(size_t)r * K + k] = f2d(w[r]) + res;
+      J.b[(size_t)r * K + k] = add_gz ? f2d(w[r]) + res : res;
     }
   }
   if (maxbit) {
@@ -437,12 +439,13 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
   }
 }
 
-// One thread per body, end of the step: dqb (+)= z - Hbar^{-1} g(l) with
-// l = lambda after the approximate solve alone (from_u: z is u and dqb starts
-// at zero), else l = the last correction dlambda; then dq = diag4(R) dqb,
-// q += dq, qdot = dq / h (implicit Euler, Sec. 3.4).
+// One thread per body, end of the step.  Chain: dqb (+)= z - Hbar^{-1} g(l)
+// with l = lambda after the approximate solve alone (MX_FROM_U: z is u and dqb
+// starts at zero), else l = the last correction dlambda; tree (MX_FROM_DQB):
+// dqb as the eliminations left it.  Then dq = diag4(R) dqb, q += dq,
+// qdot = dq / h (implicit Euler, Sec. 3.4).
 __global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevIncidence I,
-                                                  StepParams p, bool from_u) {
+                                                  StepParams p, int mode) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= B.M) return;
   const int j = ordered(B.order, t);
@@ -450,16 +453,21 @@ __global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevI
   const int M = B.M;
   double R[9];
   load_R(B.R, M, j, R);
-  float Rf[9], hf[16], gf[12], w[12];
-  load_Rf(B, j, Rf);
-  load_hinvf(B, j, hf);
-  gen_force<float, true>(J, I, j, Rf, from_u ? J.lambda : J.dlam, gf);
-  hinv_apply_t(hf, gf, w);
   double x[12];
+  if (mode == MX_FROM_DQB) {
+    load12(B.dqb, M, j, x);
+  } else {
+    const bool from_u = mode == MX_FROM_U;
+    float Rf[9], hf[16], gf[12], w[12];
+    load_Rf(B, j, Rf);
+    load_hinvf(B, j, hf);
+    gen_force<float, true>(J, I, j, Rf, from_u ? J.lambda : J.dlam, gf);
+    hinv_apply_t(hf, gf, w);
 #pragma unroll
-  for (int i = 0; i < 12; ++i) {
-    const double base = from_u ? 0.0 : B.dqb[(size_t)i * M + j];
-    x[i] = base + (double)(B.ubf[(size_t)i * M + j] - w[i]);
+    for (int i = 0; i < 12; ++i) {
+      const double base = from_u ? 0.0 : B.dqb[(size_t)i * M + j];
+      x[i] = base + (double)(B.ubf[(size_t)i * M + j] - w[i]);
+    }
   }
 #pragma unroll
   for (int blk = 0; blk < 4; ++blk) {
@@ -487,20 +495,21 @@ void launch_mx_joint_prep(const DevBodies &B, const DevJoints &J, const StepPara
 }
 
 void launch_mx_res_body(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
-                        const StepParams &p, bool first, cudaStream_t s) {
+                        const StepParams &p, int mode, cudaStream_t s) {
   if (B.M <= 0) return;
-  if (first) k_mx_res_body<true><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
-  else k_mx_res_body<false><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+  if (mode == MX_FROM_U) k_mx_res_body<MX_FROM_U><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+  else if (mode == MX_FROM_CORRECTION) k_mx_res_body<MX_FROM_CORRECTION><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+  else k_mx_res_body<MX_FROM_DQB><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
 }
 
 void launch_mx_res_joint(const DevBodies &B, const DevJoints &J, const StepParams &p,
-                         unsigned long long *maxbit, cudaStream_t s) {
-  if (J.K > 0) k_mx_res_joint<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbit);
+                         unsigned long long *maxbit, cudaStream_t s, bool add_gz) {
+  if (J.K > 0) k_mx_res_joint<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbit, add_gz);
 }
 
 void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
-                     const StepParams &p, bool from_u, cudaStream_t s) {
-  if (B.M > 0) k_mx_final<<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p, from_u);
+                     const StepParams &p, int mode, cudaStream_t s) {
+  if (B.M > 0) k_mx_final<<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p, mode);
 }
 
 }  // namespace mabd

@@ -76,6 +76,7 @@ struct mabd_ctx {
   std::vector<int32_t> tree_mid;  // per level: first leaf (bodies before it have children)
   std::vector<int32_t> tree_variant;  // per level: TREE_UP_* chosen by the tuner
   DevForest F{};                       // the forest tree by tree (persistent kernel)
+  DevTreeT<float> Tf{};                // FP32 elimination of the mixed tree form
   int tree_mode = 0;                   // 0: level-scheduled launches; 8 or 4: persistent kernel, lanes
   double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
   int *d_status = nullptr;
@@ -698,7 +699,8 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
 // passes in one launch) and the faster is kept.  MABD_TREE_VARIANT=0|1|2
 // forces one level variant (and the level path); MABD_TREE_MODE=levels|
 // forest8|forest4 forces the path.
-static mabd_status tune_tree(mabd_ctx *ctx) {
+template <typename S>
+static mabd_status tune_tree_t(mabd_ctx *ctx, const DevTreeT<S> &TT) {
   const auto &lv = ctx->tree_lvl;
   const auto &mid = ctx->tree_mid;
   const int nl = (int)lv.size() - 1;
@@ -712,21 +714,27 @@ static mabd_status tune_tree(mabd_ctx *ctx) {
   }
   cudaStream_t s = ctx->stream;
   const StepParams &p = ctx->sp;
-  launch_body_prep(ctx->B, p, ctx->d_status, s);
-  launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s);
+  // inputs of the elimination in its precision
+  if (sizeof(S) == 8) {
+    launch_body_prep(ctx->B, p, ctx->d_status, s);
+    launch_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s);
+  } else {
+    launch_mx_body_prep(ctx->B, p, ctx->d_status, s);
+    launch_mx_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s);
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   for (int l = nl - 1; l >= 1 && !fv; --l) {
     if (mid[l] <= lv[l]) {
-      launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s);
+      launch_tree_up(ctx->B, ctx->J, TT, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s);
       continue;
     }
     float best = 1e30f;
     for (int v = 0; v < TREE_UP_NVARIANTS; ++v)
       for (int rep = 0; rep < 2; ++rep) {
         CK(cudaEventRecord(e0, s));
-        launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s, v);
+        launch_tree_up(ctx->B, ctx->J, TT, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s, v);
         CK(cudaEventRecord(e1, s));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -755,11 +763,11 @@ static mabd_status tune_tree(mabd_ctx *ctx) {
         CK(cudaEventRecord(e0, s));
         if (mode == 0) {
           for (int l = nl - 1; l >= 0; --l)
-            launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s,
+            launch_tree_up(ctx->B, ctx->J, TT, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s,
                            ctx->tree_variant[l]);
-          for (int l = 0; l < nl; ++l) launch_tree_down(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s);
+          for (int l = 0; l < nl; ++l) launch_tree_down(ctx->B, ctx->J, TT, lv[l], lv[l + 1], p, ctx->d_status, s);
         } else {
-          launch_tree_forest(ctx->B, ctx->J, ctx->T, ctx->F, p, ctx->d_status, s, mode);
+          launch_tree_forest(ctx->B, ctx->J, TT, ctx->F, p, ctx->d_status, s, mode);
         }
         CK(cudaEventRecord(e1, s));
         CK(cudaEventSynchronize(e1));
@@ -781,6 +789,11 @@ static mabd_status tune_tree(mabd_ctx *ctx) {
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
   CK(cudaStreamSynchronize(s));
   return MABD_OK;
+}
+
+static mabd_status tune_tree(mabd_ctx *ctx) {
+  if (ctx->cfg.precision == MABD_MIXED_FP32_DUAL) return tune_tree_t<float>(ctx, ctx->Tf);
+  return tune_tree_t<double>(ctx, ctx->T);
 }
 
 extern "C" {
@@ -817,9 +830,9 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   }
   if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
   if (solver == MABD_SOLVER_TREE && !is_tree) return MABD_ERR_UNSUPPORTED;
-  if (ctx->cfg.precision != MABD_FP64 && K > 0 && solver == MABD_SOLVER_TREE) {
+  if (ctx->cfg.precision == MABD_MIXED && K > 0 && solver == MABD_SOLVER_TREE) {
     std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
-                  "the mixed-precision form is implemented for chains and for the PCG path only");
+                  "the mixed-precision form of the tree solver is MABD_MIXED_FP32_DUAL");
     return MABD_ERR_UNSUPPORTED;
   }
   if (solver == MABD_SOLVER_CHAIN) {
@@ -1265,6 +1278,34 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     T.rX = dnew<double>(ctx, 120 * (size_t)nr, ok);
     T.rLD = dnew<double>(ctx, 55 * (size_t)nr, ok);
     T.re = dnew<double>(ctx, 10 * (size_t)nr, ok);
+    // the FP64 form's solve: C(q_n) weighted by residual_rhs, multipliers to
+    // J.lambda, the state updated by the downward pass
+    T.c = J.c;
+    T.crr = ctx->cfg.residual_rhs ? 1.0 : 0.0;
+    T.lam = J.lambda;
+    T.lam_acc = nullptr;
+    T.dqb = nullptr;
+    T.dqb_add = 0;
+    if (f32dual) {
+      DevTreeT<float> &Tf = ctx->Tf;
+      Tf.X = dnew<float>(ctx, 60 * (size_t)Mx, ok);
+      Tf.LD = dnew<float>(ctx, 15 * (size_t)Mx, ok);
+      Tf.y = dnew<float>(ctx, 12 * (size_t)Mx, ok);
+      Tf.e = dnew<float>(ctx, 5 * (size_t)Mx, ok);
+      Tf.U = dnew<float>(ctx, 60 * (size_t)Mx, ok);
+      Tf.v = dnew<float>(ctx, 12 * (size_t)Mx, ok);
+      Tf.dq = dnew<float>(ctx, 12 * (size_t)Mx, ok);
+      Tf.rX = dnew<float>(ctx, 120 * (size_t)nr, ok);
+      Tf.rLD = dnew<float>(ctx, 55 * (size_t)nr, ok);
+      Tf.re = dnew<float>(ctx, 10 * (size_t)nr, ok);
+      // the first solve of a step; the correction solves set their own
+      Tf.c = J.c;
+      Tf.crr = T.crr;
+      Tf.lam = J.lambda;
+      Tf.lam_acc = nullptr;
+      Tf.dqb = B.dqb;
+      Tf.dqb_add = 0;
+    }
     if (!ok) {
       free_all(ctx);
       return MABD_ERR_OUT_OF_MEMORY;
@@ -1308,6 +1349,19 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     }
     CK(up(dids, ids.data(), ids.size() * 4));
     ctx->T.order = dids;
+    if (f32dual) {
+      DevTreeT<float> &Tf = ctx->Tf;
+      Tf.parent = T.parent;
+      Tf.pjoint = T.pjoint;
+      Tf.pside = T.pside;
+      Tf.cfirst = T.cfirst;
+      Tf.ccount = T.ccount;
+      Tf.root_id = T.root_id;
+      Tf.root_joint = T.root_joint;
+      Tf.root_side = T.root_side;
+      Tf.nroots = T.nroots;
+      Tf.order = dids;
+    }
     // the same bodies tree by tree: per tree and depth, bodies with children
     // first, then leaves; a sentinel record closes each tree
     {
@@ -1446,7 +1500,7 @@ static void enqueue_mixed_chain(mabd_ctx *ctx, unsigned long long *maxbits, cuda
     launch_mx_body_prep(ctx->B, p, ctx->d_status, s, maxbits ? maxbits + 3 : nullptr);
   });
   if (ctx->J.K == 0) {
-    run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, true, s); });
+    run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, MX_FROM_U, s); });
     return;
   }
   run(ctx, "mx_joint_prep", [&] { launch_mx_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
@@ -1458,12 +1512,75 @@ static void enqueue_mixed_chain(mabd_ctx *ctx, unsigned long long *maxbits, cuda
   DevJoints Jc = ctx->J;
   Jc.lambda = ctx->J.dlam;
   for (int it = 0; it < sweeps; ++it) {
-    run(ctx, "mx_res_body", [&] { launch_mx_res_body(ctx->B, ctx->J, ctx->I, p, it == 0, s); });
+    run(ctx, "mx_res_body", [&] {
+      launch_mx_res_body(ctx->B, ctx->J, ctx->I, p, it == 0 ? MX_FROM_U : MX_FROM_CORRECTION, s);
+    });
     unsigned long long *mb = (maxbits && it == sweeps - 1) ? maxbits + 2 : nullptr;
     run(ctx, "mx_res_joint", [&] { launch_mx_res_joint(ctx->B, ctx->J, p, mb, s); });
     enqueue_cr(ctx, s, true, Jc, ctx->J.lambda);
   }
-  run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, sweeps == 0, s); });
+  run(ctx, "mx_final", [&] {
+    launch_mx_final(ctx->B, ctx->J, ctx->I, p, sweeps == 0 ? MX_FROM_U : MX_FROM_CORRECTION, s);
+  });
+}
+
+}  // extern "C"
+
+// One solve of the KKT system by the tree elimination with T's right-hand
+// side and outputs: the upward levels (deepest first, the tuned variant per
+// level), then the downward levels, or the persistent kernel when the tuner
+// chose it.
+template <typename S>
+static void enqueue_tree_solve(mabd_ctx *ctx, const DevTreeT<S> &T, cudaStream_t s) {
+  const StepParams &p = ctx->sp;
+  if (ctx->tree_mode != 0) {
+    run(ctx, "tree_forest", [&] {
+      launch_tree_forest(ctx->B, ctx->J, T, ctx->F, p, ctx->d_status, s, ctx->tree_mode);
+    });
+    return;
+  }
+  const auto &lv = ctx->tree_lvl;
+  const int nl = (int)lv.size() - 1;
+  const auto &mid = ctx->tree_mid;
+  for (int l = nl - 1; l >= 0; --l)
+    run(ctx, "tree_up", [&] {
+      launch_tree_up(ctx->B, ctx->J, T, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s,
+                     ctx->tree_variant.empty() ? TREE_UP_THREAD : ctx->tree_variant[l]);
+    });
+  for (int l = 0; l < nl; ++l)
+    run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+}
+
+extern "C" {
+
+// Mixed-precision tree step (MABD_MIXED_FP32_DUAL): FP64 polar, rhs and
+// constraint values; the tree elimination in FP32 gives lambda and the
+// rest-frame increment dqb; each sweep forms the FP64 residuals (primal
+// r = fbar - Hbar dqb - g(lambda) with z = Hbar^{-1} r, dual C + G dqb) and
+// solves the correction system by the same FP32 elimination with z and
+// C + G dqb as its right-hand side, adding to lambda and dqb; then the state
+// update.
+static void enqueue_mixed_tree(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
+  const StepParams &p = ctx->sp;
+  run(ctx, "mx_body_prep", [&] {
+    launch_mx_body_prep(ctx->B, p, ctx->d_status, s, maxbits ? maxbits + 3 : nullptr);
+  });
+  run(ctx, "mx_joint_prep", [&] { launch_mx_joint_prep(ctx->B, ctx->J, p, ctx->d_status, s); });
+  enqueue_tree_solve(ctx, ctx->Tf, s);
+  DevTreeT<float> Tc = ctx->Tf;
+  Tc.c = ctx->J.b;
+  Tc.crr = 1.0;
+  Tc.lam = ctx->J.dlam;
+  Tc.lam_acc = ctx->J.lambda;
+  Tc.dqb_add = 1;
+  const int sweeps = ctx->cfg.refine_steps;
+  for (int it = 0; it < sweeps; ++it) {
+    run(ctx, "mx_res_body", [&] { launch_mx_res_body(ctx->B, ctx->J, ctx->I, p, MX_FROM_DQB, s); });
+    unsigned long long *mb = (maxbits && it == sweeps - 1) ? maxbits + 2 : nullptr;
+    run(ctx, "mx_res_joint", [&] { launch_mx_res_joint(ctx->B, ctx->J, p, mb, s, false); });
+    enqueue_tree_solve(ctx, Tc, s);
+  }
+  run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, MX_FROM_DQB, s); });
 }
 
 // iters (may be null): the step's polar-iteration counter
@@ -1476,21 +1593,8 @@ static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s, unsigned long long *iters
   if (ctx->solver == MABD_SOLVER_CHAIN) {
     run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
     enqueue_cr(ctx, s, false, ctx->J, nullptr);
-  } else if (ctx->solver == MABD_SOLVER_TREE && ctx->tree_mode != 0) {
-    run(ctx, "tree_forest", [&] {
-      launch_tree_forest(ctx->B, ctx->J, ctx->T, ctx->F, p, ctx->d_status, s, ctx->tree_mode);
-    });
   } else if (ctx->solver == MABD_SOLVER_TREE) {
-    const auto &lv = ctx->tree_lvl;
-    const int nl = (int)lv.size() - 1;
-    const auto &mid = ctx->tree_mid;
-    for (int l = nl - 1; l >= 0; --l)
-      run(ctx, "tree_up", [&] {
-        launch_tree_up(ctx->B, ctx->J, ctx->T, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s,
-                       ctx->tree_variant.empty() ? TREE_UP_THREAD : ctx->tree_variant[l]);
-      });
-    for (int l = 0; l < nl; ++l)
-      run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, ctx->T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+    enqueue_tree_solve(ctx, ctx->T, s);
   } else if (ctx->solver == MABD_SOLVER_PCG) {
     run(ctx, "pcg_setup", [&] { launch_pcg_setup(ctx->B, ctx->J, ctx->P, ctx->cfg.pcg_rtol, ctx->d_status, s); });
   }
@@ -1507,7 +1611,9 @@ static void enqueue_pcg_chunk(mabd_ctx *ctx, cudaStream_t s) {
 
 static void enqueue_post(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
   const StepParams &p = ctx->sp;
-  if (ctx->cfg.precision != MABD_FP64)
+  if (ctx->cfg.precision != MABD_FP64 && ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE)
+    enqueue_mixed_tree(ctx, maxbits, s);
+  else if (ctx->cfg.precision != MABD_FP64)
     enqueue_mixed_chain(ctx, maxbits, s);
   else if (!(ctx->J.K > 0 && ctx->solver == MABD_SOLVER_TREE))
     run(ctx, "backprop", [&] { launch_backprop(ctx->B, ctx->J, ctx->I, p, ctx->d_status, s); });
@@ -1616,13 +1722,17 @@ static mabd_status step_mixed_pcg(mabd_ctx *ctx, unsigned long long *maxbits, cu
   if (st) return st;
   const int sweeps = ctx->cfg.refine_steps;
   for (int it = 0; it < sweeps; ++it) {
-    run(ctx, "mx_res_body", [&] { launch_mx_res_body(ctx->B, ctx->J, ctx->I, p, it == 0, s); });
+    run(ctx, "mx_res_body", [&] {
+      launch_mx_res_body(ctx->B, ctx->J, ctx->I, p, it == 0 ? MX_FROM_U : MX_FROM_CORRECTION, s);
+    });
     unsigned long long *mb = (maxbits && it == sweeps - 1) ? maxbits + 2 : nullptr;
     run(ctx, "mx_res_joint", [&] { launch_mx_res_joint(ctx->B, ctx->J, p, mb, s); });
     st = p32_solve_any(ctx, s, ctx->J.b, ctx->J.dlam, ctx->J.lambda);
     if (st) return st;
   }
-  run(ctx, "mx_final", [&] { launch_mx_final(ctx->B, ctx->J, ctx->I, p, sweeps == 0, s); });
+  run(ctx, "mx_final", [&] {
+    launch_mx_final(ctx->B, ctx->J, ctx->I, p, sweeps == 0 ? MX_FROM_U : MX_FROM_CORRECTION, s);
+  });
   if (maxbits)
     run(ctx, "residuals", [&] { launch_residuals(ctx->B, ctx->J, p, maxbits, ctx->d_status, s); });
   return MABD_OK;

@@ -120,7 +120,10 @@ using CRLevel = CRLevelT<double>;
 
 // tree (forest) of free bodies in breadth-first order: levels are contiguous
 // ranges and the children of a body are a contiguous range
-struct DevTree {
+// S: the elimination's type (double: FP64 form; float: the FP32 elimination
+// of the mixed form, refined by FP64 correction sweeps)
+template <typename S>
+struct DevTreeT {
   const int32_t *parent;      // [M] parent body (internal index) or -1
   const int32_t *pjoint;      // [M] joint to the parent (internal index) or -1
   const int8_t *pside;        // [M] side of the body in that joint (0: a, 1: b)
@@ -131,17 +134,26 @@ struct DevTree {
   const int8_t *root_side;    // [2][nroots]
   int32_t nroots;
   const int32_t *order;       // [nfree] per level: bodies with children, then leaves
-  double *X;                  // [60][M]  Hhat^{-1} G^T in the rest frame (12 x 5)
-  double *LD;                 // [15][M]  Cholesky factor of D = G Hhat^{-1} G^T
-  double *y;                  // [12][M]  Hhat^{-1} fhat (rest frame)
-  double *e;                  // [5][M]   G y + C(q_n)
-  double *U;                  // [60][M]  P^T L_D^{-T} in the parent's rest frame (12 x 5)
-  double *v;                  // [12][M]  P^T D^{-1} e in the parent's rest frame
-  double *dq;                 // [12][M]  world-frame increment of the step
-  double *rX;                 // [120][nroots] roots: Hhat^{-1} G_w^T (12 x 10)
-  double *rLD;                // [55][nroots]
-  double *re;                 // [10][nroots]
+  S *X;                       // [60][M]  Hhat^{-1} G^T in the rest frame (12 x 5)
+  S *LD;                      // [15][M]  Cholesky factor of D = G Hhat^{-1} G^T
+  S *y;                       // [12][M]  Hhat^{-1} fhat (rest frame)
+  S *e;                       // [5][M]   G y + C(q_n)
+  S *U;                       // [60][M]  P^T L_D^{-T} in the parent's rest frame (12 x 5)
+  S *v;                       // [12][M]  P^T D^{-1} e in the parent's rest frame
+  S *dq;                      // [12][M]  world-frame increment of the step
+  S *rX;                      // [120][nroots] roots: Hhat^{-1} G_w^T (12 x 10)
+  S *rLD;                     // [55][nroots]
+  S *re;                      // [10][nroots]
+  // right-hand side and outputs of one solve of the KKT system
+  // [H G^T; G 0][dq; lambda] = [f; -crr c] (the body rhs enters as ubar = Hbar^{-1} fbar)
+  const double *c;            // [5][K] joint values: C(q_n), or a correction's C + G dq
+  double crr;                 // their weight: residual_rhs (0 or 1) for a step, 1 for a correction
+  double *lam;                // [5][K] multipliers out (FP64)
+  double *lam_acc;            // [5][K] multipliers also added here (null: not)
+  double *dqb;                // [12][M] null: the state update (FP64 form); else the rest-frame
+  int32_t dqb_add;            //   increment, written (0) or added (1)
 };
+using DevTree = DevTreeT<double>;
 
 // the forest regrouped tree by tree for the persistent kernel: tree t has
 // levels lvl[t] .. lvl[t] + nlvl[t] - 1 (records), record r covers
@@ -356,12 +368,18 @@ void launch_mx_joint_prep(const DevBodies &B, const DevJoints &J, const StepPara
                           cudaStream_t s);
 void launch_mx_chain_gram(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
                           const DevChain &C, cudaStream_t s, bool f32_blocks = false);
+// where a sweep's increment dqb comes from: the approximate solve's u and
+// lambda (first chain sweep), the previous correction z and dlambda (later
+// chain sweeps), or dqb itself (the tree elimination writes it)
+enum { MX_FROM_U = 0, MX_FROM_CORRECTION = 1, MX_FROM_DQB = 2 };
 void launch_mx_res_body(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
-                        const StepParams &p, bool first, cudaStream_t s);
+                        const StepParams &p, int mode, cudaStream_t s);
+// add_gz: b = G z + (C + G dq) (the chain's dual rhs); false: b = C + G dq
+// (the joint values of the tree's correction solve)
 void launch_mx_res_joint(const DevBodies &B, const DevJoints &J, const StepParams &p,
-                         unsigned long long *maxbit, cudaStream_t s);
+                         unsigned long long *maxbit, cudaStream_t s, bool add_gz = true);
 void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
-                     const StepParams &p, bool from_u, cudaStream_t s);
+                     const StepParams &p, int mode, cudaStream_t s);
 
 // tree (k_tree.cu): one launch per level, deepest first, then root first
 // level [lo, hi) of the body order: T.order[lo, mid) lists its bodies with
@@ -369,15 +387,19 @@ void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence 
 // is run by one kernel
 // whole tree elimination (upward and downward passes) of every tree of the
 // forest in one launch, one block per tree; lanes = 8 or 4 per body with children
-void launch_tree_forest(const DevBodies &B, const DevJoints &J, const DevTree &T, const DevForest &F,
+// (S = double or float, the elimination's type, for these three launchers)
+template <typename S>
+void launch_tree_forest(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, const DevForest &F,
                         const StepParams &p, int *status, cudaStream_t s, int lanes);
 // variants of the upward pass for the bodies with children: one thread per
 // body, or a group of 8 or 4 lanes per body (chosen per level by the tuner)
 enum { TREE_UP_THREAD = 0, TREE_UP_COOP8 = 1, TREE_UP_COOP4 = 2, TREE_UP_NVARIANTS = 3 };
-void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int mid,
+template <typename S>
+void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int lo, int mid,
                     int hi, bool roots, const StepParams &p, int *status, cudaStream_t s,
                     int variant = TREE_UP_THREAD);
-void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTree &T, int lo, int hi,
+template <typename S>
+void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int lo, int hi,
                       const StepParams &p, int *status, cudaStream_t s);
 
 // PCG (k_pcg.cu)

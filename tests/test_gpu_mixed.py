@@ -152,7 +152,8 @@ def test_mixed_full_size_net(ora):
 
 
 def test_mixed_rejects_other_topologies():
-    """Trees have no mixed form (their elimination is FP64 only)."""
+    """MABD_MIXED (FP64 dual elimination) has no tree form: the tree's mixed
+    form is MABD_MIXED_FP32_DUAL (tests/test_gpu_tree_mixed.py)."""
     need_gpu()
     from paper_2603_08079_gb300 import mabd
     sc = scenes.random_small("tree", 12, seed=3)
