@@ -97,15 +97,23 @@ typedef enum {
                MABD_MIXED. */
 enum { MABD_FP64 = 0, MABD_MIXED = 1, MABD_MIXED_FP32_DUAL = 2 };
 #define MABD_MAX_REFINE 8
-enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_SOLVER_PCG = 3 };
+/* MABD_SOLVER_LOOP: a single closed loop of bodies (every body joined to two
+   others, every joint between two bodies; Sec. 5.4, Case III, eq. loop):
+   one joint is the loop breaker, the others form a chain solved by the
+   chain's block cyclic reduction, and the breaker's multipliers come from the
+   Schur complement of the chain (a few right-hand-side passes through the
+   chain's factors).  FP64 form only. */
+enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_SOLVER_PCG = 3,
+       MABD_SOLVER_LOOP = 4 };
 enum { MABD_JOINT_BALL = 0, MABD_JOINT_HINGE = 1 };
-enum { MABD_TOPO_NONE = 0, MABD_TOPO_CHAIN = 1, MABD_TOPO_TREE = 2, MABD_TOPO_GRAPH = 3 };
+enum { MABD_TOPO_NONE = 0, MABD_TOPO_CHAIN = 1, MABD_TOPO_TREE = 2, MABD_TOPO_GRAPH = 3,
+       MABD_TOPO_LOOP = 4 };
 
 typedef struct {
   double h;             /* time step [s] > 0 */
   double gravity[3];    /* [m/s^2], applied at each centre of mass (Eq. module1-wrench-map) */
   int32_t precision;    /* MABD_FP64, MABD_MIXED or MABD_MIXED_FP32_DUAL */
-  int32_t solver;       /* MABD_SOLVER_*; AUTO picks chain, then tree, then PCG */
+  int32_t solver;       /* MABD_SOLVER_*; AUTO picks chain, then tree, then loop (FP64), then PCG */
   int32_t pcg_max_iters;/* cap on PCG iterations (>= 1) */
   double pcg_rtol;      /* PCG stops when |r| <= pcg_rtol |b| */
   int32_t refine_steps; /* MABD_MIXED: FP64 correction sweeps per step, 0..MABD_MAX_REFINE */

@@ -171,7 +171,13 @@ __device__ __forceinline__ void chain_gram_body(const DevBodies &B, const DevJoi
       }
     }
     const int k0 = kk[0];
+    if (kk[1] != k0 + 1) {
+      // the body that closes a loop: joint 0 and the loop breaker K - 1
+      if (C.corner && sizeof(OT) == 8)
 #pragma unroll
+        for (int i = 0; i < 25; ++i) C.corner[i] = (double)Bp[i];
+      return;
+    }
     OT *Bd = const_cast<OT *>(CRS<OT>::Bc(C));
 #pragma unroll
     for (int i = 0; i < 25; ++i) Bd[(size_t)i * K + k0] = Bp[i];

@@ -77,6 +77,10 @@ struct mabd_ctx {
   std::vector<int32_t> tree_variant;  // per level: TREE_UP_* chosen by the tuner
   DevForest F{};                       // the forest tree by tree (persistent kernel)
   DevTreeT<float> Tf{};                // FP32 elimination of the mixed tree form
+  // loop solver: right-hand side and solution of a pass through the chain's
+  // factors ([5][K]), and the chain's response at its two ends per breaker row
+  double *loop_b = nullptr, *loop_x = nullptr, *loop_w = nullptr;
+  int loop_rows = 0;  // rows of the loop breaker (3 or 5)
   int tree_mode = 0;                   // 0: level-scheduled launches; 8 or 4: persistent kernel, lanes
   double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
   int *d_status = nullptr;
@@ -195,6 +199,7 @@ struct Graph {
   std::vector<char> free_body;
   std::vector<int> fa, fb;                     // free ends of each joint (-1 if none)
   std::vector<std::vector<int>> inc;           // free body -> incident joints
+  std::vector<int> jtype;                      // joint types
 };
 
 Graph build_graph(const mabd_ctx *ctx) {
@@ -206,8 +211,10 @@ Graph build_graph(const mabd_ctx *ctx) {
   g.fa.resize(g.K);
   g.fb.resize(g.K);
   g.inc.resize(g.M);
+  g.jtype.resize(g.K);
   for (int k = 0; k < g.K; ++k) {
     const auto &d = ctx->joints[k];
+    g.jtype[k] = d.type;
     int a = (int)d.body_a, b = (int)d.body_b;
     g.fa[k] = g.free_body[a] ? a : -1;
     g.fb[k] = (b >= 0 && g.free_body[b]) ? b : -1;
@@ -271,6 +278,48 @@ bool chain_order(const Graph &g, std::vector<int32_t> &border, std::vector<int32
     if (!g.free_body[j]) continue;
     if (g.inc[j].size() > 2) return false;
     if (g.inc[j].size() == 2 && std::abs(pos[g.inc[j][0]] - pos[g.inc[j][1]]) != 1) return false;
+  }
+  for (int j = 0; j < g.M; ++j)
+    if (!g.free_body[j]) border.push_back(j);
+  return true;
+}
+
+// A single closed loop (Sec. 5.4, Case III): every joint joins two free
+// bodies, every free body has exactly two joints, and they form one cycle of
+// at least three bodies.  Bodies follow the cycle; joint p joins bodies p and
+// p + 1 for p < K - 1, and the last joint (the loop breaker) closes the loop
+// between bodies K - 1 and 0.  The breaker is a ball joint when there is one
+// (its rows count the right-hand-side passes of the Schur complement).
+bool ring_order(const Graph &g, std::vector<int32_t> &border, std::vector<int32_t> &jorder) {
+  int nfree = 0;
+  for (int j = 0; j < g.M; ++j) nfree += g.free_body[j];
+  if (g.K < 3 || g.K != nfree) return false;
+  for (int k = 0; k < g.K; ++k)
+    if (g.fa[k] < 0 || g.fb[k] < 0) return false;
+  for (int j = 0; j < g.M; ++j)
+    if (g.free_body[j] && g.inc[j].size() != 2) return false;
+  int kb = 0;  // the breaker: the first ball joint, else joint 0
+  for (int k = 0; k < g.K; ++k)
+    if (g.jtype[k] == 0) {
+      kb = k;
+      break;
+    }
+  border.clear();
+  jorder.clear();
+  const int start = g.fb[kb];
+  int cur = start, prevk = kb;
+  for (int step = 0; step < g.K; ++step) {
+    border.push_back(cur);
+    const int k = g.inc[cur][0] == prevk ? g.inc[cur][1] : g.inc[cur][0];
+    jorder.push_back(k);
+    prevk = k;
+    cur = other_end(g, k, cur);
+  }
+  if (cur != start || jorder.back() != kb || (int)border.size() != nfree) return false;
+  std::vector<char> seen(g.M, 0);
+  for (int j : border) {
+    if (seen[j]) return false;
+    seen[j] = 1;
   }
   for (int j = 0; j < g.M; ++j)
     if (!g.free_body[j]) border.push_back(j);
@@ -611,7 +660,7 @@ mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
   if (cfg->precision != MABD_FP64 && cfg->precision != MABD_MIXED && cfg->precision != MABD_MIXED_FP32_DUAL)
     return MABD_ERR_INVALID_ARG;
   if (cfg->refine_steps < 0 || cfg->refine_steps > MABD_MAX_REFINE) return MABD_ERR_INVALID_ARG;
-  if (cfg->solver < MABD_SOLVER_AUTO || cfg->solver > MABD_SOLVER_PCG) return MABD_ERR_INVALID_ARG;
+  if (cfg->solver < MABD_SOLVER_AUTO || cfg->solver > MABD_SOLVER_LOOP) return MABD_ERR_INVALID_ARG;
   if (cfg->pcg_max_iters < 1 || !(cfg->pcg_rtol > 0.0)) return MABD_ERR_INVALID_ARG;
   if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) return MABD_ERR_INVALID_ARG;
   int ndev = 0;
@@ -819,17 +868,28 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   TreeOrder tord;
   const bool is_chain = K > 0 && chain_order(g, cborder, cjorder);
   const bool is_tree = K > 0 && tree_order(ctx, g, tord);
+  std::vector<int32_t> rborder, rjorder;
+  const bool is_ring = K > 0 && !is_chain && !is_tree && ring_order(g, rborder, rjorder);
   int solver = ctx->cfg.solver;
   if (K == 0) {
     ctx->topology = MABD_TOPO_NONE;
     solver = MABD_SOLVER_AUTO;
   } else {
-    ctx->topology = is_chain ? MABD_TOPO_CHAIN : (is_tree ? MABD_TOPO_TREE : MABD_TOPO_GRAPH);
+    ctx->topology = is_chain ? MABD_TOPO_CHAIN
+                             : (is_tree ? MABD_TOPO_TREE : (is_ring ? MABD_TOPO_LOOP : MABD_TOPO_GRAPH));
     if (solver == MABD_SOLVER_AUTO)
-      solver = is_chain ? MABD_SOLVER_CHAIN : (is_tree ? MABD_SOLVER_TREE : MABD_SOLVER_PCG);
+      solver = is_chain ? MABD_SOLVER_CHAIN
+                        : (is_tree ? MABD_SOLVER_TREE
+                                   : ((is_ring && ctx->cfg.precision == MABD_FP64) ? MABD_SOLVER_LOOP
+                                                                                   : MABD_SOLVER_PCG));
   }
   if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
   if (solver == MABD_SOLVER_TREE && !is_tree) return MABD_ERR_UNSUPPORTED;
+  if (solver == MABD_SOLVER_LOOP && (!is_ring || ctx->cfg.precision != MABD_FP64)) {
+    std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
+                  "the loop solver takes a single closed loop of bodies, in the FP64 form");
+    return MABD_ERR_UNSUPPORTED;
+  }
   if (ctx->cfg.precision == MABD_MIXED && K > 0 && solver == MABD_SOLVER_TREE) {
     std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
                   "the mixed-precision form of the tree solver is MABD_MIXED_FP32_DUAL");
@@ -838,6 +898,9 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   if (solver == MABD_SOLVER_CHAIN) {
     border = cborder;
     jorder = cjorder;
+  } else if (solver == MABD_SOLVER_LOOP) {
+    border = rborder;
+    jorder = rjorder;
   } else if (solver == MABD_SOLVER_TREE) {
     border = tord.border;
     jorder = tord.jorder;
@@ -961,7 +1024,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   // bodies, the lower one along the path (slot 0) and the upper one (slot 1)
   std::vector<uint8_t> cfl(K, 0);
   std::vector<int8_t> islot(std::max<size_t>(ijoint.size(), 1), 0);
-  if (solver == MABD_SOLVER_CHAIN) {
+  const bool chainlike = solver == MABD_SOLVER_CHAIN || solver == MABD_SOLVER_LOOP;
+  if (chainlike) {
     for (int j = 0; j < M; ++j) {
       const int n = ioff[j + 1] - ioff[j];
       for (int e = ioff[j]; e < ioff[j + 1]; ++e) {
@@ -1098,12 +1162,22 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   ctx->I.joint = dij;
   ctx->I.side = dis;
 
-  if (solver == MABD_SOLVER_CHAIN) {
+  if (chainlike) {
     DevChain &C = ctx->C;
     C.K = K;
     C.Dfirst = dnew<double>(ctx, 15 * (size_t)K, ok);
     C.Dsecond = dnew<double>(ctx, 15 * (size_t)K, ok);
     C.B = dnew<double>(ctx, 25 * (size_t)K, ok);
+    // a loop reduces the chain of its first K - 1 joints; the last joint is
+    // the loop breaker (Sec. 5.4, Case III)
+    const int Kr = solver == MABD_SOLVER_LOOP ? K - 1 : K;
+    if (solver == MABD_SOLVER_LOOP) {
+      C.corner = dnew<double>(ctx, 25, ok);
+      ctx->loop_b = dnew<double>(ctx, 5 * (size_t)K, ok);
+      ctx->loop_x = dnew<double>(ctx, 5 * (size_t)K, ok);
+      ctx->loop_w = dnew<double>(ctx, 5 * 10, ok);
+      ctx->loop_rows = jtype[K - 1] == 1 ? 5 : 3;
+    }
     uint8_t *dcf = dnew<uint8_t>(ctx, K, ok);
     int8_t *dslot = dnew<int8_t>(ctx, islot.size(), ok);
     // Level-0 offset: with off = 1 a decoupled identity row precedes the first
@@ -1112,8 +1186,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     // alternate balls and hinges it makes level 0 eliminate the hinges and
     // leaves only 3x3 rows above it.
     {
-      std::vector<int> sz(K);
-      for (int k = 0; k < K; ++k) sz[k] = jtype[k] == 1 ? 5 : 3;
+      std::vector<int> sz(Kr);
+      for (int k = 0; k < Kr; ++k) sz[k] = jtype[k] == 1 ? 5 : 3;
       auto cost = [&](int off) {
         std::vector<int> cur(off, 3);
         cur.insert(cur.end(), sz.begin(), sz.end());
@@ -1131,11 +1205,11 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
         }
         return total;
       };
-      C.off = (K > 1 && cost(1) < cost(0)) ? 1 : 0;
+      C.off = (Kr > 1 && cost(1) < cost(0)) ? 1 : 0;
     }
     // cyclic-reduction levels
     ctx->levels.clear();
-    int N = K + C.off;
+    int N = Kr + C.off;
     int lvl = 0;
     while (true) {
       CRLevel L{};
@@ -1209,6 +1283,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     CK(up(dslot, islot.data(), islot.size()));
     C.jflags = dcf;
     C.islot = dslot;
+    if (ctx->loop_b) CK(cudaMemsetAsync(ctx->loop_b, 0, 5 * (size_t)K * 8, ctx->stream));
   }
   if (solver == MABD_SOLVER_PCG && mixed) {
     DevPCG32 &Q = ctx->P32;
@@ -1440,53 +1515,77 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
 }  // extern "C"
 
 template <typename T>
-static void enqueue_cr_t(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout, double *acc,
-                         std::vector<CRLevelT<T>> &levels, const CRLevelT<T> *d_levels) {
+static void enqueue_cr_t(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jin,
+                         const DevJoints &Jout, double *acc, std::vector<CRLevelT<T>> &levels,
+                         const CRLevelT<T> *d_levels) {
   const int nl = (int)levels.size();
   const int l0 = ctx->cr_tail_level;
   if (l0 < nl) {
     // large levels one launch each, the rest in the single-CTA tail
     for (int l = 0; l < l0; ++l) {
       if (rhs_only)
-        run(ctx, "cr_rhs", [&] { launch_cr_rhs<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], s); });
+        run(ctx, "cr_rhs", [&] { launch_cr_rhs<T>(ctx->C, Jin, levels[l], l, levels[l + 1], s); });
       else
         run(ctx, "cr_level",
-            [&] { launch_cr_level<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], ctx->d_status, s); });
+            [&] { launch_cr_level<T>(ctx->C, Jin, levels[l], l, levels[l + 1], ctx->d_status, s); });
     }
     run(ctx, "cr_tail", [&] {
-      launch_cr_tail<T>(ctx->C, ctx->J, Jout, d_levels, l0, nl, rhs_only, (T *)ctx->cL, (T *)ctx->cR,
+      launch_cr_tail<T>(ctx->C, Jin, Jout, d_levels, l0, nl, rhs_only, (T *)ctx->cL, (T *)ctx->cR,
                         (T *)ctx->Bn, ctx->d_status, l0 == 0 ? acc : nullptr, s);
     });
     for (int l = l0 - 1; l >= 0; --l)
       run(ctx, "cr_back", [&] {
-        launch_cr_back<T>(ctx->C, l == 0 ? Jout : ctx->J, levels[l], levels[l + 1], l, s, l == 0 ? acc : nullptr);
+        launch_cr_back<T>(ctx->C, l == 0 ? Jout : Jin, levels[l], levels[l + 1], l, s, l == 0 ? acc : nullptr);
       });
     return;
   }
   for (int l = 0; l + 1 < nl; ++l) {
     if (rhs_only)
-      run(ctx, "cr_rhs", [&] { launch_cr_rhs<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], s); });
+      run(ctx, "cr_rhs", [&] { launch_cr_rhs<T>(ctx->C, Jin, levels[l], l, levels[l + 1], s); });
     else
-      run(ctx, "cr_level", [&] { launch_cr_level<T>(ctx->C, ctx->J, levels[l], l, levels[l + 1], ctx->d_status, s); });
+      run(ctx, "cr_level", [&] { launch_cr_level<T>(ctx->C, Jin, levels[l], l, levels[l + 1], ctx->d_status, s); });
   }
   if (nl == 1) {
     // a single row (one joint): level 0 is the top row, written to Jout.lambda
-    run(ctx, "cr_top", [&] { launch_cr_top<T>(ctx->C, ctx->J, levels[0], 0, ctx->d_status, s, Jout.lambda, acc); });
+    run(ctx, "cr_top", [&] { launch_cr_top<T>(ctx->C, Jin, levels[0], 0, ctx->d_status, s, Jout.lambda, acc); });
     return;
   }
-  run(ctx, "cr_top", [&] { launch_cr_top<T>(ctx->C, ctx->J, levels[nl - 1], nl - 1, ctx->d_status, s); });
+  run(ctx, "cr_top", [&] { launch_cr_top<T>(ctx->C, Jin, levels[nl - 1], nl - 1, ctx->d_status, s); });
   for (int l = nl - 2; l >= 0; --l)
     run(ctx, "cr_back", [&] {
-      launch_cr_back<T>(ctx->C, l == 0 ? Jout : ctx->J, levels[l], levels[l + 1], l, s, l == 0 ? acc : nullptr);
+      launch_cr_back<T>(ctx->C, l == 0 ? Jout : Jin, levels[l], levels[l + 1], l, s, l == 0 ? acc : nullptr);
     });
 }
 
-// the chain's reduction in the precision of the form in use
-static void enqueue_cr(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout, double *acc) {
+// the chain's reduction in the precision of the form in use; the rhs comes
+// from Jin.b (level 0), the solution goes to Jout.lambda (and acc)
+static void enqueue_cr(mabd_ctx *ctx, cudaStream_t s, bool rhs_only, const DevJoints &Jout, double *acc,
+                       const DevJoints *Jin = nullptr) {
+  const DevJoints &Ji = Jin ? *Jin : ctx->J;
   if (ctx->cfg.precision == MABD_MIXED_FP32_DUAL)
-    enqueue_cr_t<float>(ctx, s, rhs_only, Jout, acc, ctx->levels_f, ctx->d_levels_f);
+    enqueue_cr_t<float>(ctx, s, rhs_only, Ji, Jout, acc, ctx->levels_f, ctx->d_levels_f);
   else
-    enqueue_cr_t<double>(ctx, s, rhs_only, Jout, acc, ctx->levels, ctx->d_levels);
+    enqueue_cr_t<double>(ctx, s, rhs_only, Ji, Jout, acc, ctx->levels, ctx->d_levels);
+}
+
+// Loop solver (k_loop.cu; Sec. 5.4, Case III): factor the chain of joints
+// 0..K-2 with its rhs, one rhs pass per row of the breaker K-1 for
+// S_cc^{-1} S_cl, the breaker's Schur complement, then a last rhs pass with
+// b_c - S_cl lambda_L for the chain's multipliers
+static void enqueue_loop(mabd_ctx *ctx, cudaStream_t s) {
+  const int K = ctx->J.K;
+  enqueue_cr(ctx, s, false, ctx->J, nullptr);
+  DevJoints Jin = ctx->J, Jx = ctx->J;
+  Jin.b = ctx->loop_b;
+  Jx.lambda = ctx->loop_x;
+  const int n = ctx->loop_rows;
+  for (int t = 0; t < n; ++t) {
+    run(ctx, "loop_schur", [&] { launch_loop_column(ctx->C, K, ctx->loop_b, t, s); });
+    enqueue_cr(ctx, s, true, Jx, nullptr, &Jin);
+    run(ctx, "loop_schur", [&] { launch_loop_gather(K, ctx->loop_x, ctx->loop_w, t, s); });
+  }
+  run(ctx, "loop_schur", [&] { launch_loop_schur(ctx->C, ctx->J, ctx->loop_w, ctx->d_status, s); });
+  enqueue_cr(ctx, s, true, ctx->J, nullptr);
 }
 
 extern "C" {
@@ -1593,6 +1692,9 @@ static void enqueue_pre(mabd_ctx *ctx, cudaStream_t s, unsigned long long *iters
   if (ctx->solver == MABD_SOLVER_CHAIN) {
     run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
     enqueue_cr(ctx, s, false, ctx->J, nullptr);
+  } else if (ctx->solver == MABD_SOLVER_LOOP) {
+    run(ctx, "chain_gram", [&] { launch_chain_gram(ctx->B, ctx->J, ctx->I, ctx->C, s); });
+    enqueue_loop(ctx, s);
   } else if (ctx->solver == MABD_SOLVER_TREE) {
     enqueue_tree_solve(ctx, ctx->T, s);
   } else if (ctx->solver == MABD_SOLVER_PCG) {
@@ -1985,8 +2087,9 @@ mabd_status mabd_get_info(mabd_ctx *ctx, mabd_info *info) {
   info->device_bytes = ctx->device_bytes;
   info->precision = ctx->cfg.precision;
   info->refine_steps = ctx->cfg.refine_steps;
-  info->cr_levels = ctx->solver == MABD_SOLVER_CHAIN ? (int32_t)ctx->levels.size() : 0;
-  info->cr_tail_level = ctx->solver == MABD_SOLVER_CHAIN ? ctx->cr_tail_level : 0;
+  const bool cr = ctx->solver == MABD_SOLVER_CHAIN || ctx->solver == MABD_SOLVER_LOOP;
+  info->cr_levels = cr ? (int32_t)ctx->levels.size() : 0;
+  info->cr_tail_level = cr ? ctx->cr_tail_level : 0;
   return MABD_OK;
 }
 
@@ -2012,7 +2115,7 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
                                 "mx_chain_gram", "mx_res_body", "mx_res_joint", "cr_rhs", "mx_final",
                                 "p32_setup", "p32_iteration", "p32_finish", "lpc_blocks", "lpc_forward",
                                 "tree_forest",
-                                "cr_level", "cr_reduce", "cr_combine", "cr_tail",
+                                "cr_level", "cr_reduce", "cr_combine", "cr_tail", "loop_schur",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
                                 "pcg_iteration", "backprop", "residuals"};
   int n = 0;

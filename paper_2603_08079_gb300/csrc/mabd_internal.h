@@ -104,6 +104,9 @@ struct DevChain {
   int32_t off;           // level-0 row n is joint n - off; rows n < off are identity rows
   // FP32 Gram parts for the FP32 reduction of the mixed form (else null)
   float *Dfirst_f, *Dsecond_f, *B_f;
+  // loop solver: coupling of joint 0 (rows) and the loop breaker K - 1
+  // (columns) through body 0 (5x5 padded); null otherwise
+  double *corner;
 };
 
 // one level of block cyclic reduction (T: the reduction's precision)
@@ -311,6 +314,13 @@ template <typename T>
 void launch_cr_tail(const DevChain &C, const DevJoints &J, const DevJoints &Jout, const CRLevelT<T> *d_lv,
                     int l0, int nl, bool rhs_only, T *cL, T *cR, T *Bn, int *status, double *acc,
                     cudaStream_t s);
+
+// loop solver (k_loop.cu): column t of the breaker's coupling as a chain
+// rhs ([5][K], only joints 0 and K-2 written), the chain's solution at joints
+// 0 and K-2 into w[10 t..], and the breaker's Schur complement solve
+void launch_loop_column(const DevChain &C, int K, double *rb, int t, cudaStream_t s);
+void launch_loop_gather(int K, const double *x, double *w, int t, cudaStream_t s);
+void launch_loop_schur(const DevChain &C, const DevJoints &J, const double *w, int *status, cudaStream_t s);
 
 // FP32 PCG (k_pcg32.cu): setup from rhs (FP64 [5][K]), iterations, and the
 // final copy of x to out (FP64 [5][K]) with acc += x when acc is given

@@ -17,9 +17,9 @@ import numpy as np
 from . import build as _build
 
 WORLD = -1
-SOLVERS = {"auto": 0, "chain": 1, "tree": 2, "pcg": 3}
+SOLVERS = {"auto": 0, "chain": 1, "tree": 2, "pcg": 3, "loop": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_fp32_dual": 2}
-TOPOLOGIES = {0: "none", 1: "chain", 2: "tree", 3: "graph"}
+TOPOLOGIES = {0: "none", 1: "chain", 2: "tree", 3: "graph", 4: "loop"}
 STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of device memory",
           4: "CUDA error", 5: "not positive definite", 6: "inverted body", 7: "non-finite",
           8: "no convergence", 9: "timeout", 10: "unsupported"}
