@@ -47,6 +47,11 @@ WORKLOADS = {
     "net64x64x16": ("jittered net: %d unit cubes on a 64x64x16 lattice (sigma 0.05, bottom layer fixed), "
                     "%d ball joints kept with p=0.7, %d dual rows, h=1e-2 s, seed 4",
                     "block-Jacobi PCG on the dual, rtol 1e-13 (graph)"),
+    "loop1m": ("pulley-cable loop: %d boxes (sides U[0.5,1.5], rho 10^U[2,4]) along a closed polygon, "
+               "%d joints (ball/hinge alternating, the last one closing the loop, no world joints), "
+               "%d dual rows, h=1e-2 s, seed 1",
+               "loop Schur complement (Case III): one breaker joint, the chain of the others by block "
+               "cyclic reduction"),
     "batch4096": ("4096 independent assemblies: %d links (7..64 per assembly, Poisson(1.3) branching, "
                   "fixed base with a random pose), %d hinge/ball joints, %d dual rows, h=2e-3 s, seed 3",
                   "one forest: level-scheduled body-space elimination over all assemblies, "
@@ -62,6 +67,8 @@ def make_scene(name: str, M: int | None = None) -> dict:
         return scenes.random_tree(M or 262144, seed=2)
     if name == "batch4096":
         return scenes.assemblies(M or 4096, seed=3)
+    if name == "loop1m":
+        return scenes.ring_chain(M or M_FULL, seed=1)
     if name == "net64x64x16":
         if M:  # a smaller lattice with the same density, for the CPU sample
             n = max(4, int(round((M / 16) ** 0.5)))
@@ -113,6 +120,8 @@ def chosen_form(args) -> str:
     sweeps."""
     if args.precision != "auto":
         return args.precision
+    if args.workload == "loop1m":
+        return "fp64"  # the loop solver is FP64; the PCG path is timed beside it
     return "mixed" if args.workload == "net64x64x16" else "mixed_fp32_dual"
 
 
@@ -373,7 +382,7 @@ def run_gpu(args):
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    sc = make_scene(args.workload, args.bodies if args.workload == "chain1m" else None)
+    sc = make_scene(args.workload, args.bodies if args.workload in ("chain1m", "loop1m") else None)
     M = len(sc["mass"])
     form = chosen_form(args)
     solver = mabd.Solver(sc, precision=form, refine_steps=args.refine, pcg_max_iters=20000)
@@ -431,8 +440,11 @@ def run_gpu(args):
     # form, the mixed form with block Jacobi), timed the same way
     plain = None
     others = {}
-    if form != "fp64":
-        variants = [("plain_fp64_gpu", dict(precision="fp64"), None)]
+    if args.workload == "loop1m":
+        variants = [("pcg_fp64_gpu", dict(precision="fp64", solver="pcg"), None)]
+    else:
+        variants = [("plain_fp64_gpu", dict(precision="fp64"), None)] if form != "fp64" else []
+    if variants:
         if form == "mixed_fp32_dual" and args.workload == "chain1m":
             variants.append(("mixed_fp64_reduction_gpu", dict(precision="mixed", refine_steps=args.refine),
                              None))
@@ -449,7 +461,7 @@ def run_gpu(args):
                            "ms_per_step": pms / args.steps}
             if rst.get("pcg_iters"):
                 others[key]["pcg_iters_per_step"] = rst["pcg_iters"]
-        plain = others["plain_fp64_gpu"]
+        plain = others.get("plain_fp64_gpu")
 
     result = None
     if rank == 0:
@@ -502,7 +514,7 @@ def run_gpu(args):
         }
         if form != "fp64":
             result["refine_residual"] = st["refine_residual"]
-            result.update(others)
+        result.update(others)
         if learned is not None:
             result["config"]["preconditioner"] = ("learned (3-layer message passing, hidden 64, BF16 "
                                                   "tensor cores), trained parameters %s" % LPC_PARAMS_REL)
@@ -526,6 +538,8 @@ def cpu_baseline(args, steps: int = 1, M: int | None = None) -> dict:
     if args.workload == "chain1m":
         M = M or args.cpu_bodies
         sc = scenes.long_chain(M, seed=1)
+    elif args.workload == "loop1m":
+        sc = scenes.ring_chain(M or args.cpu_bodies, seed=1)
     elif args.workload in ("tree256k", "batch4096"):
         sc = make_scene(args.workload)       # the full scene: a few s per oracle step
     else:

@@ -131,6 +131,53 @@ def chain_cubes(M: int = 64, h: float = 1e-2, young: float = 1e8) -> dict:
     return sc
 
 
+def ring_chain(M: int = 1 << 20, seed: int = 1, h: float = 1e-2, young: float = 1e8) -> dict:
+    """The pulley-cable chain closed into a loop (Sec. 5.4, Case III): M boxes
+    with sides U[0.5,1.5]^3 and densities 10^U[2,4] laid along a horizontal
+    circle, each box's x axis along its chord of a closed polygon whose edge
+    lengths are the boxes' x sides, consecutive boxes touching at face
+    centres; joint j (bodies j, j+1 mod M) is a ball for even j and a hinge
+    with an axis uniform on the sphere for odd j; no world joints.  The
+    polygon's radius solves sum_j 2 asin(L_j / 2R) = 2 pi (bisection)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.uniform(0.5, 1.5, size=(M, 3))
+    rho = 10.0 ** rng.uniform(2.0, 4.0, size=M)
+    L = sides[:, 0]
+    lo, hi = 0.5 * L.max(), L.sum()
+    for _ in range(200):
+        R = 0.5 * (lo + hi)
+        if np.sum(2.0 * np.arcsin(np.minimum(1.0, L / (2.0 * R)))) > 2.0 * np.pi:
+            lo = R
+        else:
+            hi = R
+    R = 0.5 * (lo + hi)
+    phi = np.cumsum(2.0 * np.arcsin(np.minimum(1.0, L / (2.0 * R))))
+    P = np.stack([R * np.cos(phi), R * np.sin(phi), np.zeros(M)], axis=1)  # joint j's point
+    Pm = np.roll(P, 1, axis=0)                                              # box j spans Pm[j] .. P[j]
+    d = _unit(P - Pm)
+    centres = 0.5 * (P + Pm)
+    K = M
+    sc = _empty_scene(M, K, h)
+    _set_boxes(sc, sides, rho, centres, young)
+    A = np.zeros((M, 3, 3))
+    A[:, :, 0] = d
+    A[:, :, 1] = np.stack([-d[:, 1], d[:, 0], np.zeros(M)], axis=1)
+    A[:, 2, 2] = 1.0
+    sc["q"][:, 0:9] = np.transpose(A, (0, 2, 1)).reshape(M, 9)  # q stacks A's columns
+    j = np.arange(M)
+    nxt = (j + 1) % M
+    sc["body_a"][:] = j
+    sc["body_b"][:] = nxt
+    sc["anchor_a"][:, 0] = 0.5 * L
+    sc["anchor_b"][:, 0] = -0.5 * L[nxt]
+    is_h = (j % 2) == 1
+    sc["jtype"][:] = np.where(is_h, HINGE, BALL)
+    w = _unit(rng.standard_normal((M, 3)))
+    sc["axis_a"][:] = np.einsum("kji,kj->ki", A, w)          # A_a^T w
+    sc["axis_b"][:] = np.einsum("kji,kj->ki", A[nxt], w)     # A_b^T w
+    return sc
+
+
 def long_chain(M: int = 1 << 20, seed: int = 1, h: float = 1e-2,
                young: float = 1e8) -> dict:
     """Pulley-cable chain: M boxes with sides U[0.5,1.5]^3 and densities

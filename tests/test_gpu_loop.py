@@ -76,3 +76,22 @@ def test_loop_solver_is_fp64_only():
         assert s.info()["solver"] == "pcg"
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("M", [3, 10, 4096])
+def test_pulley_ring(ora, M):
+    """The pulley-cable chain closed into a loop (scenes.ring_chain)."""
+    need_gpu()
+    sc = scenes.ring_chain(M, seed=1)
+    q, qd = scenes.perturb_state(sc, seed=M, rot=0.05, vel=0.2)
+    assert_parity(ora, sc, q, qd)
+
+
+def test_full_size_pulley_ring(ora):
+    """1,048,576 bodies closed into one loop, the launch configuration the
+    benchmark's loop workload times."""
+    need_gpu()
+    sc = scenes.ring_chain(1 << 20, seed=1)
+    q, qd = scenes.perturb_state(sc, seed=3, rot=0.05, vel=0.2)
+    e_qd, e_lam, st, _ = assert_parity(ora, sc, q, qd)
+    assert st["lin_residual"] < 1e-8
