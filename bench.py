@@ -125,6 +125,23 @@ def chosen_form(args) -> str:
     return "mixed" if args.workload == "net64x64x16" else "mixed_fp32_dual"
 
 
+def max_over_ranks(ms: float, device: str = "cuda") -> float:
+    """The largest of the ranks' timings (the job's time), via all_reduce MAX
+    when a process group with more than one rank is up."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, M: int, steps: int, ms_max: float) -> float:
+    """Whole-job body-steps/s: every rank steps its own replica of M bodies
+    (weak scaling), the job lasts as long as the slowest rank."""
+    return ws * M * steps / (ms_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -397,16 +414,10 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(ms):
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     clocks = ClockSampler(torch.cuda.current_device())
     ms, clk = time_steps(solver, args.steps, args.warmup, barrier_sync, clocks)
     ms_max = max_over_ranks(ms)
-    value = ws * M * args.steps / (ms_max / 1e3)
+    value = job_value(ws, M, args.steps, ms_max)
 
     # per-kernel times with CUDA events on the library's stream (separate pass)
     solver.profile(True)
@@ -457,7 +468,7 @@ def run_gpu(args):
             rst = ref.step(1, stats=True)[0]
             ref.close()
             pms = max_over_ranks(pms)
-            others[key] = {"value": ws * M * args.steps / (pms / 1e3), "unit": "body-steps/s",
+            others[key] = {"value": job_value(ws, M, args.steps, pms), "unit": "body-steps/s",
                            "ms_per_step": pms / args.steps}
             if rst.get("pcg_iters"):
                 others[key]["pcg_iters_per_step"] = rst["pcg_iters"]
@@ -566,8 +577,15 @@ def run_reference(args):
     import oracle as ora
     from paper_2603_08079_gb300 import scenes
 
-    M = args.cpu_bodies
-    sc = scenes.long_chain(M, seed=1)
+    if args.workload == "chain1m":
+        sc = scenes.long_chain(args.cpu_bodies, seed=1)
+    elif args.workload == "loop1m":
+        sc = scenes.ring_chain(args.cpu_bodies, seed=1)
+    elif args.workload in ("tree256k", "batch4096"):
+        sc = make_scene(args.workload)
+    else:
+        sc = make_scene(args.workload, 16384)
+    M = len(sc["mass"])
     S = ora.Scene(sc)
     q, qd = sc["q"], sc["qdot"]
     for _ in range(args.warmup):
@@ -577,7 +595,13 @@ def run_reference(args):
         q, qd, _, _ = ora.step(S, q, qd)
     dt = time.perf_counter() - t0
     value = M * args.steps / dt
-    cfg = workload_config(M_FULL, M_FULL + 1, 4194305, "chain1m", chosen_form(args), args.refine)
+    full = make_scene(args.workload) if args.workload != "chain1m" else None
+    if full is None:
+        cfg = workload_config(M_FULL, M_FULL + 1, 4194305, "chain1m", chosen_form(args), args.refine)
+    else:
+        rows = int(sum(5 if t == 1 else 3 for t in full["jtype"]))
+        cfg = workload_config(len(full["mass"]), len(full["jtype"]), rows, args.workload, chosen_form(args),
+                              args.refine)
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "body-steps/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -585,8 +609,8 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator, paper-shaped chain)",
         "config": cfg,
         "cpu_baseline": {"value": value, "unit": "body-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": "each step: the first %d bodies of the chain generator (seed 1), "
-                                   "single thread, %s" % (M, lscpu_model())},
+                         "sample": "each step: a %d-body %s from the same generator, single thread, %s"
+                                   % (M, args.workload, lscpu_model())},
         "e2e": {"value": value, "unit": "body-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
