@@ -535,10 +535,81 @@ def run_gpu(args):
             result["config"]["tree_schedule"] = tree_sched
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(args)
+            if args.workload == "batch4096":
+                result["cpu_baseline_all_cores"] = cpu_baseline_parallel(args)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def split_assemblies(sc: dict) -> list:
+    """The batch scene's assemblies as scenes of their own: an assembly's
+    bodies are contiguous from its fixed base body, its joints are those whose
+    body a (the parent) lies in that range."""
+    M = len(sc["mass"])
+    starts = np.flatnonzero(np.asarray(sc["fixed"]) != 0)
+    ends = np.append(starts[1:], M)
+    owner = np.searchsorted(starts, np.asarray(sc["body_a"]), side="right") - 1
+    out = []
+    for a, (lo, hi) in enumerate(zip(starts, ends)):
+        ks = np.flatnonzero(owner == a)
+        sub = {"h": sc["h"], "gravity": sc["gravity"]}
+        for key in ("mass", "second_moment", "volume", "young", "poisson", "fixed", "q", "qdot"):
+            sub[key] = np.ascontiguousarray(sc[key][lo:hi])
+        for key in ("jtype", "anchor_a", "anchor_b", "axis_a", "axis_b", "axis_len"):
+            sub[key] = np.ascontiguousarray(sc[key][ks])
+        sub["body_a"] = np.ascontiguousarray(sc["body_a"][ks] - lo)
+        bb = sc["body_b"][ks]
+        sub["body_b"] = np.ascontiguousarray(np.where(bb >= 0, bb - lo, bb))
+        out.append(sub)
+    return out
+
+
+_BATCH = None
+
+
+def _batch_worker_init(n: int, seed: int):
+    global _BATCH
+    import oracle as ora
+    from paper_2603_08079_gb300 import scenes
+    subs = split_assemblies(scenes.assemblies(n, seed=seed))
+    _BATCH = [(sub, ora.Scene(sub)) for sub in subs]
+
+
+def _batch_worker_step(rng) -> int:
+    import oracle as ora
+    lo, hi = rng
+    for sub, S in _BATCH[lo:hi]:
+        ora.step(S, sub["q"], sub["qdot"])
+    return int(sum(len(sub["mass"]) for sub, _ in _BATCH[lo:hi]))
+
+
+def batch_oracle_parallel(steps: int, warmup: int, n: int = 4096, seed: int = 3):
+    """The oracle, as it stands, on the 4096 independent assemblies run on all
+    host cores: one oracle scene per assembly, spread over spawned worker
+    processes (each builds the batch in its initializer).  Returns
+    (body-steps per step, seconds of the timed steps, workers)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    nch = 4 * cores
+    chunks = [(i * n // nch, (i + 1) * n // nch) for i in range(nch)]
+    with mp.get_context("spawn").Pool(cores, initializer=_batch_worker_init, initargs=(n, seed)) as pool:
+        for _ in range(max(warmup, 1)):
+            pool.map(_batch_worker_step, chunks)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            bodies = sum(pool.map(_batch_worker_step, chunks))
+        dt = time.perf_counter() - t0
+    return bodies, dt, cores
+
+
+def cpu_baseline_parallel(args) -> dict:
+    bodies, dt, cores = batch_oracle_parallel(1, 1)
+    return {"value": bodies / dt, "unit": "body-steps/s", "cores": cores, "kind": "oracle",
+            "sample": "1 step of all 4096 assemblies, one oracle scene per assembly, over %d spawned "
+                      "worker processes, %s" % (cores, lscpu_model()),
+            "seconds": round(dt, 3)}
 
 
 def cpu_baseline(args, steps: int = 1, M: int | None = None) -> dict:
@@ -577,23 +648,32 @@ def run_reference(args):
     import oracle as ora
     from paper_2603_08079_gb300 import scenes
 
-    if args.workload == "chain1m":
-        sc = scenes.long_chain(args.cpu_bodies, seed=1)
-    elif args.workload == "loop1m":
-        sc = scenes.ring_chain(args.cpu_bodies, seed=1)
-    elif args.workload in ("tree256k", "batch4096"):
-        sc = make_scene(args.workload)
+    cores = 1
+    if args.workload == "batch4096":
+        # independent assemblies: one oracle scene each, on all host cores
+        M, dt, cores = batch_oracle_parallel(args.steps, args.warmup)
+        sample = "each step: all 4096 assemblies, one oracle scene per assembly, %d worker processes, %s" % (
+            cores, lscpu_model())
     else:
-        sc = make_scene(args.workload, 16384)
-    M = len(sc["mass"])
-    S = ora.Scene(sc)
-    q, qd = sc["q"], sc["qdot"]
-    for _ in range(args.warmup):
-        q, qd, _, _ = ora.step(S, q, qd)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        q, qd, _, _ = ora.step(S, q, qd)
-    dt = time.perf_counter() - t0
+        if args.workload == "chain1m":
+            sc = scenes.long_chain(args.cpu_bodies, seed=1)
+        elif args.workload == "loop1m":
+            sc = scenes.ring_chain(args.cpu_bodies, seed=1)
+        elif args.workload == "tree256k":
+            sc = make_scene(args.workload)
+        else:
+            sc = make_scene(args.workload, 16384)
+        M = len(sc["mass"])
+        S = ora.Scene(sc)
+        q, qd = sc["q"], sc["qdot"]
+        for _ in range(args.warmup):
+            q, qd, _, _ = ora.step(S, q, qd)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            q, qd, _, _ = ora.step(S, q, qd)
+        dt = time.perf_counter() - t0
+        sample = "each step: a %d-body %s from the same generator, single thread, %s" % (
+            M, args.workload, lscpu_model())
     value = M * args.steps / dt
     full = make_scene(args.workload) if args.workload != "chain1m" else None
     if full is None:
@@ -608,9 +688,8 @@ def run_reference(args):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator, paper-shaped chain)",
         "config": cfg,
-        "cpu_baseline": {"value": value, "unit": "body-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": "each step: a %d-body %s from the same generator, single thread, %s"
-                                   % (M, args.workload, lscpu_model())},
+        "cpu_baseline": {"value": value, "unit": "body-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": "body-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

@@ -1,0 +1,40 @@
+"""Host-side pieces of the benchmark: the batch's assemblies split into
+scenes of their own give, step by step, the oracle's result on the whole
+batch (they are independent), and the all-core oracle baseline runs them in
+spawned worker processes."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_split_assemblies_matches_the_whole_batch(ora):
+    import bench
+    from paper_2603_08079_gb300 import scenes
+    sc = scenes.assemblies(6, seed=3)
+    q, qd = scenes.perturb_state(sc, seed=1, rot=0.05, vel=0.3)
+    full = dict(sc, q=q, qdot=qd)
+    q1, qd1, lam, _ = ora.step(ora.Scene(full), q, qd)
+    subs = bench.split_assemblies(full)
+    assert len(subs) == 6 and sum(len(s["mass"]) for s in subs) == len(sc["mass"])
+    assert sum(len(s["jtype"]) for s in subs) == len(sc["jtype"])
+    parts_q, parts_qd, parts_lam = [], [], []
+    for s in subs:
+        a, b, l, _ = ora.step(ora.Scene(s), s["q"], s["qdot"])
+        parts_q.append(a)
+        parts_qd.append(b)
+        parts_lam.append(l)
+    np.testing.assert_allclose(np.concatenate(parts_qd), qd1, rtol=0, atol=1e-12 * np.max(np.abs(qd1)))
+    np.testing.assert_allclose(np.concatenate(parts_q), q1, rtol=0, atol=1e-12 * np.max(np.abs(q1)))
+    np.testing.assert_allclose(np.concatenate(parts_lam), lam, rtol=0, atol=1e-10 * np.max(np.abs(lam)))
+
+
+def test_parallel_oracle_baseline_runs():
+    import bench
+    bodies, dt, cores = bench.batch_oracle_parallel(1, 1, n=16, seed=3)
+    from paper_2603_08079_gb300 import scenes
+    assert bodies == len(scenes.assemblies(16, seed=3)["mass"])
+    assert dt > 0 and cores >= 1
