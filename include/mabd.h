@@ -81,20 +81,22 @@ typedef enum {
 
 /* Arithmetic of the step.
    MABD_FP64   every product in FP64.
-   MABD_MIXED  chain topologies: the unconstrained solve, the Jacobian
-               products, the dual Gram blocks and the back-propagation in
-               FP32; the polar rotation, the rhs, the constraint values, the
+   MABD_MIXED  chains: the unconstrained solve, the Jacobian products, the
+               dual Gram blocks and the back-propagation in FP32; the polar
+               rotation, the rhs, the constraint values, the
                prefactorization and the block cyclic reduction of the dual in
                FP64; then refine_steps FP64 residual-correction sweeps
                (iterative refinement of the KKT system through the stored
-               FP64 factors).  Other topologies: MABD_ERR_UNSUPPORTED at
-               mabd_prefactor.
+               FP64 factors).  Graphs (PCG solver): every dual solve by FP32
+               PCG, refined the same way.  Trees and the loop solver:
+               MABD_ERR_UNSUPPORTED at mabd_prefactor.
    MABD_MIXED_FP32_DUAL  as MABD_MIXED, but the chain's cyclic reduction
                runs in FP32 as well (Gram blocks, factors and levels in
-               FP32); the FP64 correction sweeps still refine the FP64
-               system, so the result keeps the mixed form's accuracy while the
-               reduction leaves the FP64 pipe.  On the PCG path it equals
-               MABD_MIXED. */
+               FP32); on trees the body-space elimination runs in FP32; the
+               FP64 correction sweeps still refine the FP64 system, so the
+               result keeps the mixed form's accuracy while the dual solve
+               leaves the FP64 pipe.  On the PCG path it equals MABD_MIXED;
+               the loop solver is FP64 only (AUTO picks PCG for loops). */
 enum { MABD_FP64 = 0, MABD_MIXED = 1, MABD_MIXED_FP32_DUAL = 2 };
 #define MABD_MAX_REFINE 8
 /* MABD_SOLVER_LOOP: a single closed loop of bodies (every body joined to two

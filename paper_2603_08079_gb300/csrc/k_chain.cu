@@ -1,10 +1,12 @@
-// Chain path of one M-ABD step (FP64), Sec. 5.2:
+// Chain path of one M-ABD step, Sec. 5.2 (also the chain part of the loop
+// solver, Sec. 5.4, whose closing body writes the corner block):
 //   k_chain_gram  per body j: the Gram blocks of its (at most two) joints,
 //                 G_kj H_j^{-1} G_k'j^T (Eq. chain-Schur-blocks), formed in the
 //                 body's rest frame with the structured Hbar^{-1};
 //   k_cr_*        block cyclic reduction of the block-tridiagonal dual
-//                 (Eq. chain-btd) with every block padded to 5x5 (a ball's two
-//                 extra rows carry an identity diagonal and decouple exactly).
+//                 (Eq. chain-btd, cr_impl.cuh, in FP64 or FP32) with every
+//                 block padded to 5x5 (a ball's two extra rows carry an
+//                 identity diagonal and decouple exactly).
 // Packed lower-triangular 5x5 storage: entry (r, c), r >= c, at r(r+1)/2 + c.
 #include "cr_impl.cuh"
 

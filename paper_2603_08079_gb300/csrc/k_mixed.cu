@@ -1,15 +1,18 @@
-// Mixed-precision form of the chain step.  The step solves the same
-// linearized KKT system as the FP64 form (Eq. newton_abd with the frozen-frame
-// Jacobian of Eq. pcpq):
+// Mixed-precision forms of the step (chains, trees and the PCG path share
+// these kernels).  The step solves the same linearized KKT system as the FP64
+// form (Eq. newton_abd with the frozen-frame Jacobian of Eq. pcpq):
 //     H dq + G^T lambda = f,     G dq = -C(q_n)
 // by iterative refinement:
 //   approximate solve  u = H^{-1} f, Gram blocks, then back-propagation
 //                      dq = u - H^{-1} G^T lambda (Sec. 5.2), with every
-//                      per-body and per-joint product in FP32, and the
-//                      block cyclic reduction of the dual in FP64;
+//                      per-body and per-joint product in FP32, and the dual
+//                      solve by the chain's block cyclic reduction (FP64, or
+//                      FP32 in MABD_MIXED_FP32_DUAL), the tree's FP32
+//                      elimination, or FP32 PCG on graphs;
 //   correction sweep   FP64 residuals r_p = f - H dq - G^T lambda and
 //                      r_d = -C - G dq, then the same approximate solve for
-//                      (r_p, r_d) through the stored FP64 factors.
+//                      (r_p, r_d) (through the stored factors on chains).
+// Float/double conversions on the FP64-bound paths go through fconv.h.
 // The polar rotation R, the rhs f, the constraint values C(q_n) and the hinge
 // frames are computed in FP64, so the system being refined is the FP64 one.
 // All body-space work is done in the body's rest frame: with

@@ -1,5 +1,7 @@
-// Tree path of one M-ABD step (FP64), Sec. 5.3 (Alg. 2, Eq. module3-kkt),
-// read as the exact constraint-row elimination in body space:
+// Tree path of one M-ABD step, Sec. 5.3 (Alg. 2, Eq. module3-kkt), read as
+// the exact constraint-row elimination in body space, templated on the
+// elimination's type S (double: the FP64 form; float: the FP32 elimination of
+// the mixed form, whose right-hand side and outputs DevTreeT names):
 //   upward (deepest level first), body j with parent joint rows G (on j) and
 //   P (on the parent):
 //     Hhat_j = Hbar_j + sum_children U_i U_i^T,  fhat_j = fbar_j - sum_children v_i
@@ -9,7 +11,9 @@
 //     lambda = D^{-1}(e + P dq_parent),  dq_j = y - X lambda.
 // Everything of body j is kept in its rest frame (rows s [p;1] (x) R_j^T d),
 // so a leaf uses the structured Hbar^{-1}; bodies with children factor their
-// dense 12x12 Hhat (packed lower storage).
+// dense 12x12 Hhat (packed lower storage).  Variants for the bodies with
+// children (one thread, or 8 or 4 lanes per body) and a persistent kernel
+// (one CTA per tree) are chosen by the tuner in mabd_api.cpp.
 #include "mabd_device.cuh"
 
 namespace mabd {
