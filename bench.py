@@ -28,6 +28,8 @@ import time
 
 import numpy as np
 
+from paper_2603_08079_gb300 import scenes
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -269,7 +271,7 @@ def cr_reduce_flops(jtype_chain: np.ndarray) -> float:
     The library eliminates either the chain's rows as they are or behind one
     leading identity row of size 3, whichever has fewer FMA; the same choice
     is made here."""
-    sizes = np.where(np.asarray(jtype_chain) == 1, 5, 3).astype(np.int64)
+    sizes = scenes.joint_rows(jtype_chain)
     best = _cr_fma(sizes)
     if len(sizes) > 1:
         shifted = _cr_fma(np.concatenate([[3], sizes]))
@@ -280,7 +282,7 @@ def cr_reduce_flops(jtype_chain: np.ndarray) -> float:
 
 def _cr_sizes(jtype_chain: np.ndarray) -> np.ndarray:
     """Level-0 row sizes with the library's choice of the leading identity row."""
-    sizes = np.where(np.asarray(jtype_chain) == 1, 5, 3).astype(np.int64)
+    sizes = scenes.joint_rows(jtype_chain)
     if len(sizes) > 1 and _cr_fma(np.concatenate([[3], sizes]))[0] < _cr_fma(sizes)[0]:
         return np.concatenate([[3], sizes])
     return sizes
@@ -679,7 +681,7 @@ def run_reference(args):
     if full is None:
         cfg = workload_config(M_FULL, M_FULL + 1, 4194305, "chain1m", chosen_form(args), args.refine)
     else:
-        rows = int(sum(5 if t == 1 else 3 for t in full["jtype"]))
+        rows = scenes.dual_rows(full)
         cfg = workload_config(len(full["mass"]), len(full["jtype"]), rows, args.workload, chosen_form(args),
                               args.refine)
     return {

@@ -107,7 +107,15 @@ enum { MABD_FP64 = 0, MABD_MIXED = 1, MABD_MIXED_FP32_DUAL = 2 };
    chain's factors).  FP64 form only. */
 enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_SOLVER_PCG = 3,
        MABD_SOLVER_LOOP = 4 };
-enum { MABD_JOINT_BALL = 0, MABD_JOINT_HINGE = 1 };
+/* MABD_JOINT_UNIVERSAL (Sec. 4.4, 4 rows): anchor_a / anchor_b are the joint
+   centre in each rest frame, axis_a the first axis a1 (fixed in body a),
+   axis_b the second axis a2 (fixed in body b, perpendicular to a1 at rest),
+   axis_len the distance l of b's second point along a2.  Rows: the ball rows
+   in the frame R_U = [a1 x a2, a1, a2]^T (a2 made normal to a1, frozen at
+   q_n) and a1 . (x_b(p_b + l a2) - x_b(p_b)), which keeps b's axis normal to
+   a1.  body_b must be a free body; scenes with universal joints are solved
+   by the PCG solver (AUTO picks it). */
+enum { MABD_JOINT_BALL = 0, MABD_JOINT_HINGE = 1, MABD_JOINT_UNIVERSAL = 2 };
 enum { MABD_TOPO_NONE = 0, MABD_TOPO_CHAIN = 1, MABD_TOPO_TREE = 2, MABD_TOPO_GRAPH = 3,
        MABD_TOPO_LOOP = 4 };
 
@@ -136,7 +144,7 @@ typedef struct {
 } mabd_body_desc;
 
 typedef struct {
-  int32_t type;            /* MABD_JOINT_BALL (3 rows) or MABD_JOINT_HINGE (5 rows) */
+  int32_t type;            /* MABD_JOINT_BALL (3 rows), MABD_JOINT_HINGE (5) or MABD_JOINT_UNIVERSAL (4) */
   int64_t body_a, body_b;  /* body_b may be MABD_WORLD; body_a must be a body */
   double anchor_a[3];      /* joint point in body a's rest frame */
   double anchor_b[3];      /* ... in body b's rest frame, or a world point */

@@ -44,7 +44,8 @@ class _Scene(C.Structure):
                 ("young", C.c_void_p), ("poisson", C.c_void_p), ("fixed", C.c_void_p),
                 ("jtype", C.c_void_p), ("body_a", C.c_void_p), ("body_b", C.c_void_p),
                 ("anchor_a", C.c_void_p), ("anchor_b", C.c_void_p), ("axis_a", C.c_void_p),
-                ("axis_b", C.c_void_p), ("axis_len", C.c_void_p)]
+                ("axis_b", C.c_void_p), ("axis_len", C.c_void_p), ("ref_a", C.c_void_p),
+                ("ref_b", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -93,6 +94,8 @@ class Scene:
 
     def __init__(self, sc: dict, residual_rhs: int = 1):
         f64 = lambda k: np.ascontiguousarray(sc[k], dtype=np.float64)
+        K = len(sc["jtype"])
+        ref = lambda k: np.ascontiguousarray(sc.get(k, np.zeros((K, 3))), dtype=np.float64)
         self.arrays = {
             "mass": f64("mass"), "second_moment": f64("second_moment"), "volume": f64("volume"),
             "young": f64("young"), "poisson": f64("poisson"),
@@ -102,6 +105,7 @@ class Scene:
             "body_b": np.ascontiguousarray(sc["body_b"], dtype=np.int64),
             "anchor_a": f64("anchor_a"), "anchor_b": f64("anchor_b"), "axis_a": f64("axis_a"),
             "axis_b": f64("axis_b"), "axis_len": f64("axis_len"),
+            "ref_a": ref("ref_a"), "ref_b": ref("ref_b"),
         }
         self.M = len(self.arrays["mass"])
         self.K = len(self.arrays["jtype"])
@@ -121,7 +125,8 @@ class Scene:
 
     @property
     def rows(self) -> int:
-        return int(np.sum(np.where(self.arrays["jtype"] == 1, 5, 3)))
+        t = self.arrays["jtype"]
+        return int(np.sum(np.where((t == 1) | (t == 3), 5, np.where(t == 2, 4, 3))))
 
 
 def _check(st: int, what: str):

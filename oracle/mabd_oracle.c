@@ -289,21 +289,116 @@ void ora_hinge_frame(const double a[3], double RH[9]) {
 /* ------------------------------------------------------------------ */
 static int is_free(const ora_scene *sc, int64_t j) { return j >= 0 && sc->fixed[j] == 0; }
 
-static int joint_rows(const ora_scene *sc, int64_t k) { return sc->jtype[k] == 1 ? 5 : 3; }
+static int joint_rows(const ora_scene *sc, int64_t k) {
+  const int t = sc->jtype[k];
+  return t == 1 || t == 3 ? 5 : (t == 2 ? 4 : 3);
+}
 
 int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
                    double Ga[60], double Gb[60], int32_t *rows) {
   int64_t ja = sc->body_a[k], jb = sc->body_b[k];
   int C = joint_rows(sc, k);
   if (rows) *rows = C;
-  double pa[2][3], pb[2][3], dir[5][3];
+  double pa[3][3], pb[3][3], dir[5][3];
   int pt[5];
   for (int i = 0; i < 3; ++i) {
     pa[0][i] = sc->anchor_a[3 * k + i];
     pb[0][i] = sc->anchor_b[3 * k + i];
   }
   const double *qa = q + 12 * ja;
-  if (C == 3) {
+  double wb1 = 1.0; /* homogeneous weight of beta's second point (0: a difference vector) */
+  int arow3 = 1;    /* does row 3 act on alpha */
+  if (sc->jtype[k] == 2) {
+    /* Sec. 4.4 universal joint: R_U = [a1 x a2, a1, a2]^T with a1 fixed in
+       alpha and a2 fixed in beta (Gram-Schmidt against a1, frozen at q_n);
+       rows 0-2: R_U (x_alpha(p_a) - x_beta(p_b)) (a ball at the joint
+       centre); row 3: a1 . (x_beta(p_b + l a2) - x_beta(p_b)), which keeps
+       beta's axis in the plane normal to a1. */
+    double u1[3], u2[3], A[9], R[9], Rb[9], w1[3], w2[3], r0[3], r1[3], r2[3];
+    normalize3(sc->axis_a + 3 * k, u1);
+    normalize3(sc->axis_b + 3 * k, u2);
+    const double *qb = q + 12 * jb;
+    A_of_q(qa, A);
+    int st = ora_polar(A, R, NULL);
+    if (st) return st;
+    A_of_q(qb, A);
+    st = ora_polar(A, Rb, NULL);
+    if (st) return st;
+    mv3(R, u1, w1);
+    mv3(Rb, u2, w2);
+    normalize3(w1, r1);
+    double d = r1[0] * w2[0] + r1[1] * w2[1] + r1[2] * w2[2];
+    double v[3] = {w2[0] - d * r1[0], w2[1] - d * r1[1], w2[2] - d * r1[2]};
+    normalize3(v, r2);
+    r0[0] = r1[1] * r2[2] - r1[2] * r2[1];
+    r0[1] = r1[2] * r2[0] - r1[0] * r2[2];
+    r0[2] = r1[0] * r2[1] - r1[1] * r2[0];
+    const double l = sc->axis_len[k];
+    for (int i = 0; i < 3; ++i) {
+      pb[1][i] = l * u2[i];
+      pa[1][i] = 0.0;
+    }
+    wb1 = 0.0;
+    arow3 = 0;
+    double d1[3], xb1[3];
+    gap_of(qa, pa[0], qb, pb[0], d1);
+    A_of_q(qb, A);
+    mv3(A, pb[1], xb1); /* x_beta(p_b + l a2) - x_beta(p_b) = A_beta (l a2) */
+    const double *rows[3] = {r0, r1, r2};
+    for (int r = 0; r < 3; ++r) {
+      c[r] = rows[r][0] * d1[0] + rows[r][1] * d1[1] + rows[r][2] * d1[2];
+      pt[r] = 0;
+      for (int a = 0; a < 3; ++a) dir[r][a] = rows[r][a];
+    }
+    c[3] = r1[0] * xb1[0] + r1[1] * xb1[1] + r1[2] * xb1[2];
+    c[4] = 0.0;
+    pt[3] = 1;
+    for (int a = 0; a < 3; ++a) dir[3][a] = r1[a];
+  } else if (sc->jtype[k] == 3) {
+    /* Sec. 4.5 prismatic joint, frame attached to alpha (Sec. 5.1 writes a
+       joint frame as a constant rotation times alpha's R^T) and frozen at
+       q_n: y~ = a = R_alpha a_a (the sliding axis), x~ = R_alpha c_a made
+       normal to a, z~ = x~ x y~; R_P = [x~; y~; z~] maps a to e_y.  Three
+       point pairs, all on both bodies: the anchors (p_a, p_b), the on-axis
+       points (p_a + l a_a, p_b + l a_b) and the off-axis points
+       (p_a + l c_a, p_b + l c_b).  Rows: x~ and z~ of the anchor gap and of
+       the on-axis gap (beta's axis stays on alpha's axis line), and z~ of the
+       off-axis gap (no twist about a); the y~ gaps, the slide, are free. */
+    double ua[3], ub[3], ca[3], cb[3], A[9], R[9], w[3], wc[3], ry[3], rx[3], rz[3];
+    normalize3(sc->axis_a + 3 * k, ua);
+    normalize3(sc->axis_b + 3 * k, ub);
+    normalize3(sc->ref_a + 3 * k, ca);
+    normalize3(sc->ref_b + 3 * k, cb);
+    const double l = sc->axis_len[k];
+    for (int i = 0; i < 3; ++i) {
+      pa[1][i] = pa[0][i] + l * ua[i];
+      pb[1][i] = pb[0][i] + l * ub[i];
+      pa[2][i] = pa[0][i] + l * ca[i];
+      pb[2][i] = pb[0][i] + l * cb[i];
+    }
+    A_of_q(qa, A);
+    int st = ora_polar(A, R, NULL);
+    if (st) return st;
+    mv3(R, ua, w);
+    normalize3(w, ry);
+    mv3(R, ca, wc);
+    double d = ry[0] * wc[0] + ry[1] * wc[1] + ry[2] * wc[2];
+    double v[3] = {wc[0] - d * ry[0], wc[1] - d * ry[1], wc[2] - d * ry[2]};
+    normalize3(v, rx);
+    rz[0] = rx[1] * ry[2] - rx[2] * ry[1];
+    rz[1] = rx[2] * ry[0] - rx[0] * ry[2];
+    rz[2] = rx[0] * ry[1] - rx[1] * ry[0];
+    const double *qb = jb == ORA_WORLD ? NULL : q + 12 * jb;
+    double g[3][3];
+    for (int t = 0; t < 3; ++t) gap_of(qa, pa[t], qb, pb[t], g[t]);
+    const int tpt[5] = {0, 0, 1, 1, 2};
+    const double *tdir[5] = {rx, rz, rx, rz, rz};
+    for (int r = 0; r < 5; ++r) {
+      pt[r] = tpt[r];
+      c[r] = tdir[r][0] * g[pt[r]][0] + tdir[r][1] * g[pt[r]][1] + tdir[r][2] * g[pt[r]][2];
+      for (int a = 0; a < 3; ++a) dir[r][a] = tdir[r][a];
+    }
+  } else if (C == 3) {
     for (int r = 0; r < 3; ++r) {
       pt[r] = 0;
       for (int a = 0; a < 3; ++a) dir[r][a] = (r == a) ? 1.0 : 0.0;
@@ -343,14 +438,18 @@ int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
   if (Ga) memset(Ga, 0, 60 * sizeof(double));
   if (Gb) memset(Gb, 0, 60 * sizeof(double));
   for (int r = 0; r < C; ++r) {
+    /* the universal joint's row 3 is + a1 (x) [l a2; 0] on beta, nothing on alpha */
+    const int u3 = sc->jtype[k] == 2 && r == 3;
+    const double sa = u3 && !arow3 ? 0.0 : 1.0, sb = u3 ? 1.0 : -1.0;
+    const double wb = pt[r] == 1 ? wb1 : 1.0;
     for (int i = 0; i < 3; ++i)
       for (int a = 0; a < 3; ++a) {
-        if (Ga) Ga[12 * r + 3 * i + a] = pa[pt[r]][i] * dir[r][a];
-        if (Gb && jb != ORA_WORLD) Gb[12 * r + 3 * i + a] = -pb[pt[r]][i] * dir[r][a];
+        if (Ga) Ga[12 * r + 3 * i + a] = sa * pa[pt[r]][i] * dir[r][a];
+        if (Gb && jb != ORA_WORLD) Gb[12 * r + 3 * i + a] = sb * pb[pt[r]][i] * dir[r][a];
       }
     for (int a = 0; a < 3; ++a) {
-      if (Ga) Ga[12 * r + 9 + a] = dir[r][a];
-      if (Gb && jb != ORA_WORLD) Gb[12 * r + 9 + a] = -dir[r][a];
+      if (Ga) Ga[12 * r + 9 + a] = sa * dir[r][a];
+      if (Gb && jb != ORA_WORLD) Gb[12 * r + 9 + a] = sb * wb * dir[r][a];
     }
   }
   return ORA_OK;
@@ -414,8 +513,10 @@ static int validate(const ora_scene *sc) {
   for (int64_t k = 0; k < sc->K; ++k) {
     int64_t a = sc->body_a[k], b = sc->body_b[k];
     if (a < 0 || a >= sc->M || b < ORA_WORLD || b >= sc->M || a == b) return ORA_ERR_ARG;
-    if (sc->jtype[k] != 0 && sc->jtype[k] != 1) return ORA_ERR_ARG;
+    if (sc->jtype[k] < 0 || sc->jtype[k] > 3) return ORA_ERR_ARG;
     if (!is_free(sc, a) && !is_free(sc, b)) return ORA_ERR_ARG;
+    /* a universal joint's fourth row lies on body beta alone */
+    if (sc->jtype[k] == 2 && !is_free(sc, b)) return ORA_ERR_ARG;
   }
   return ORA_OK;
 }

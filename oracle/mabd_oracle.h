@@ -35,10 +35,11 @@ typedef struct {
   const double *second_moment; /* 6M: xx yy zz xy xz yz about the COM */
   const double *volume, *young, *poisson; /* M each */
   const int32_t *fixed;      /* M */
-  const int32_t *jtype;      /* K: 0 ball, 1 hinge */
+  const int32_t *jtype;      /* K: 0 ball, 1 hinge, 2 universal, 3 prismatic */
   const int64_t *body_a, *body_b; /* K; body_b may be ORA_WORLD */
   const double *anchor_a, *anchor_b, *axis_a, *axis_b; /* 3K each */
   const double *axis_len;    /* K */
+  const double *ref_a, *ref_b; /* 3K each: prismatic reference directions normal to the axis */
 } ora_scene;
 
 typedef struct {

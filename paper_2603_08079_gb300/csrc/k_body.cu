@@ -134,6 +134,45 @@ __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, St
     }
     return;
   }
+  if (type == 2) {
+    // universal (Sec. 4.4): ball rows in R_U, row 3 = a1 . A_b (l a2) on b alone
+    double uax[3], vb[3], RU[9], Rbb[9], Ab[9], xb[3], lb[3], gb3[3];
+    load3(J.ua, K, k, uax);
+    load3(J.pb2, K, k, vb);
+    if (fl & JF_B_FREE) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Rbb[i] = Rb[i];
+    } else {
+      load_R(B.R, M, ib, Rbb);
+    }
+    universal_frame(Ra, uax, Rbb, vb, RU);
+    A_from_q(qb, Ab);
+    mv3(Ab, vb, xb);
+    double c1[3], e1[3];
+    mv3(RU, d1, c1);
+    mv3(RU, g1, e1);
+    // b's displacement of its axis vector under u: R_b (J_0(l a2) ubar_b)
+    gb3[0] = gb3[1] = gb3[2] = 0.0;
+    if (fl & JF_B_FREE) {
+#pragma unroll
+      for (int a2 = 0; a2 < 3; ++a2) lb[a2] = ub[a2] * vb[0] + ub[3 + a2] * vb[1] + ub[6 + a2] * vb[2];
+      mv3(Rb, lb, gb3);
+    }
+    const double c3 = RU[3] * xb[0] + RU[4] * xb[1] + RU[5] * xb[2];
+    const double e3 = RU[3] * gb3[0] + RU[4] * gb3[1] + RU[5] * gb3[2];
+    const double cc[4] = {c1[0], c1[1], c1[2], c3};
+    const double gg[4] = {e1[0], e1[1], e1[2], e3};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      J.c[(size_t)r * K + k] = cc[r];
+      J.b[(size_t)r * K + k] = gg[r] + rr * cc[r];
+    }
+    J.c[(size_t)4 * K + k] = 0.0;
+    J.b[(size_t)4 * K + k] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) J.RH[(size_t)i * K + k] = RU[i];
+    return;
+  }
   // hinge
   double pa2[3], pb2[3], uax[3], a[3], RH[9];
   load3(J.pa2, K, k, pa2);
@@ -207,6 +246,7 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
     } else {
       load3(J.pb1, K, k, P1);
     }
+    double w2 = 1.0;  // translation weight of the second point (universal: 0)
     if (type == 0) {
       F1[0] = lam[0]; F1[1] = lam[1]; F1[2] = lam[2];
     } else {
@@ -214,8 +254,15 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
       load_R(J.RH, K, k, RH);
       double l3[3] = {lam[0], lam[1], lam[2]};
       mtv3(RH, l3, F1);
+      if (type == 1) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) F2[a] = lam[3] * RH[a] + lam[4] * RH[6 + a];
+        for (int a = 0; a < 3; ++a) F2[a] = lam[3] * RH[a] + lam[4] * RH[6 + a];
+      } else if (side == 1) {
+        // universal row 3 on b: + a1 lambda_3 at the point difference l a2
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F2[a] = -lam[3] * RH[3 + a];  // sgn = -1 on b cancels below
+        w2 = 0.0;
+      }
       if (side == 0) load3(J.pa2, K, k, P2);
       else load3(J.pb2, K, k, P2);
     }
@@ -229,7 +276,7 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
       g[6 + a] += P1[2] * v;
       g[9 + a] += v;
     }
-    if (type == 1) {
+    if (type == 1 || (type == 2 && side == 1)) {
       double f2[3];
       mtv3(R, F2, f2);
 #pragma unroll
@@ -238,7 +285,7 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
         g[a] += P2[0] * v;
         g[3 + a] += P2[1] * v;
         g[6 + a] += P2[2] * v;
-        g[9 + a] += v;
+        g[9 + a] += w2 * v;
       }
     }
   }
@@ -271,7 +318,8 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
   const int type = J.type[k];
   const int ia = J.ja[k], ib = J.jb[k];
   const uint8_t fl = J.flags[k];
-  const int C = type == 0 ? 3 : 5;
+  const int C = joint_nrows(type);
+  const int npt = type == 0 ? 1 : 2;
   double qa[12], qb[12], dqa[12], dqb[12];
   load12(B.q, M, ia, qa);
   load12(B.qd, M, ia, dqa);
@@ -282,16 +330,16 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
   double P[2][3], Q[2][3];
   load3(J.pa1, K, k, P[0]);
   load3(J.pb1, K, k, Q[0]);
-  if (type == 1) {
+  if (type != 0) {
     load3(J.pa2, K, k, P[1]);
     load3(J.pb2, K, k, Q[1]);
   }
   double RH[9];
-  if (type == 1) load_R(J.RH, K, k, RH);
+  if (type != 0) load_R(J.RH, K, k, RH);
   // linearized residual with the frozen frame of this step
   double lin = 0.0;
   double da[2][3], db[2][3];
-  for (int pt = 0; pt < 1 + type; ++pt) {
+  for (int pt = 0; pt < npt; ++pt) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       da[pt][a] = 0.0;
@@ -303,9 +351,11 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
         da[pt][a] = p.h * (dqa[a] * P[pt][0] + dqa[3 + a] * P[pt][1] + dqa[6 + a] * P[pt][2] + dqa[9 + a]);
     }
     if (fl & JF_B_FREE) {
+      // (the universal joint's second point on b is a difference: no translation)
+      const double wt = (type == 2 && pt == 1) ? 0.0 : 1.0;
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        db[pt][a] = p.h * (dqb[a] * Q[pt][0] + dqb[3 + a] * Q[pt][1] + dqb[6 + a] * Q[pt][2] + dqb[9 + a]);
+        db[pt][a] = p.h * (dqb[a] * Q[pt][0] + dqb[3 + a] * Q[pt][1] + dqb[6 + a] * Q[pt][2] + wt * dqb[9 + a]);
     }
   }
   for (int r = 0; r < C; ++r) {
@@ -313,8 +363,13 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
     row_dir(type, RH, r, d);
     const int pt = r < 3 ? 0 : 1;
     double v = J.c[(size_t)r * K + k];
+    if (type == 2 && r == 3) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) v += d[a] * (da[pt][a] - db[pt][a]);
+      for (int a = 0; a < 3; ++a) v += d[a] * db[1][a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v += d[a] * (da[pt][a] - db[pt][a]);
+    }
     lin = fmax(lin, fabs(v));
   }
   // nonlinear residual at q_{n+1}
@@ -324,6 +379,20 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
   gap_of(qa, P[0], qbp, Q[0], d1);
   if (type == 0) {
     nl = fmax(fabs(d1[0]), fmax(fabs(d1[1]), fabs(d1[2])));
+  } else if (type == 2) {
+    double A[9], Ra[9], Rb[9], u[3], RU[9], xb[3], c1[3];
+    A_from_q(qa, A);
+    int st = polar3(A, Ra);
+    if (st) set_status(status, st);
+    A_from_q(qb, A);
+    st = polar3(A, Rb);
+    if (st) set_status(status, st);
+    load3(J.ua, K, k, u);
+    universal_frame(Ra, u, Rb, Q[1], RU);
+    mv3(RU, d1, c1);
+    mv3(A, Q[1], xb);
+    const double c3 = RU[3] * xb[0] + RU[4] * xb[1] + RU[5] * xb[2];
+    nl = fmax(fmax(fabs(c1[0]), fabs(c1[1])), fmax(fabs(c1[2]), fabs(c3)));
   } else {
     double A[9], R[9], u[3], a[3], RH1[9];
     A_from_q(qa, A);

@@ -92,6 +92,8 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
     T F1[3], F2[3], P1[3], P2[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) P1[a] = __ldg(p1 + (size_t)a * K + k);
+    T w2 = T(1);        // translation weight of the second point
+    bool second = type == 1;
     if (type == 0) {
       F1[0] = l[0];
       F1[1] = l[1];
@@ -103,8 +105,15 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         F1[a] = RH[a] * l[0] + RH[3 + a] * l[1] + RH[6 + a] * l[2];
-        F2[a] = l[3] * RH[a] + l[4] * RH[6 + a];
+        // hinge: rows 3, 4 along R_H's x and z rows; universal: row 3 along
+        // a1 (R_U's row 1) at b's point difference l a2, + on b (the
+        // negation cancels sgn = -1 below), nothing on a
+        F2[a] = type == 1 ? l[3] * RH[a] + l[4] * RH[6 + a] : -l[3] * RH[3 + a];
         P2[a] = __ldg(p2 + (size_t)a * K + k);
+      }
+      if (type == 2) {
+        second = side == 1;
+        w2 = T(0);
       }
     }
     T f[3];
@@ -117,7 +126,7 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
       g[6 + a] += P1[2] * f[a];
       g[9 + a] += f[a];
     }
-    if (type == 1) {
+    if (second) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) f[a] = sgn * (R[a] * F2[0] + R[3 + a] * F2[1] + R[6 + a] * F2[2]);
 #pragma unroll
@@ -125,7 +134,7 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
         g[a] += P2[0] * f[a];
         g[3 + a] += P2[1] * f[a];
         g[6 + a] += P2[2] * f[a];
-        g[9 + a] += f[a];
+        g[9 + a] += w2 * f[a];
       }
     }
   }
@@ -219,7 +228,7 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
   const int type = J.type[k];
   const int ia = J.ja[k], ib = J.jb[k];
   const uint8_t fl = J.flags[k];
-  const int npt = type == 0 ? 1 : 2;
+  const int npt = type == 1 ? 2 : 1;  // points whose gap is constrained
   double qa[12], qb[12], pa[2][3], pb[2][3];
   load12(B.q, M, ia, qa);
   if (fl & JF_B_BODY) load12(B.q, M, ib, qb);
@@ -258,6 +267,49 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
     for (int r = 0; r < 3; ++r) {
       J.c[(size_t)r * K + k] = d[0][r];
       J.b[(size_t)r * K + k] = f2d(g[0][r]) + rr * d[0][r];
+    }
+    return;
+  }
+  if (type == 2) {
+    // universal (Sec. 4.4): ball rows in R_U, row 3 = a1 . A_b (l a2) on b alone
+    double uax[3], vb[3], Ra[9], Rb[9], RU[9], Ab[9], xb[3], c1[3];
+    load3(J.ua, K, k, uax);
+    load3(J.pb2, K, k, vb);
+    load_R(B.R, M, ia, Ra);
+    load_R(B.R, M, ib, Rb);
+    universal_frame(Ra, uax, Rb, vb, RU);
+    A_from_q(qb, Ab);
+    mv3(Ab, vb, xb);
+    mv3(RU, d[0], c1);
+    float RUf[9], gb3[3] = {0.f, 0.f, 0.f}, e1[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) RUf[i] = d2f(RU[i]);
+    if (fl & JF_B_FREE) {
+      float Rbf[9], u[12], vbf[3], l[3];
+      load_Rf(B, ib, Rbf);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) u[c] = B.ubf[(size_t)c * M + ib];
+      load3f(J.pb2f, K, k, vbf);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) l[a] = u[a] * vbf[0] + u[3 + a] * vbf[1] + u[6 + a] * vbf[2];
+      mv3(Rbf, l, gb3);
+    }
+    mv3(RUf, g[0], e1);
+    const double c3 = RU[3] * xb[0] + RU[4] * xb[1] + RU[5] * xb[2];
+    const float e3 = RUf[3] * gb3[0] + RUf[4] * gb3[1] + RUf[5] * gb3[2];
+    const double cc[4] = {c1[0], c1[1], c1[2], c3};
+    const float gg[4] = {e1[0], e1[1], e1[2], e3};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      J.c[(size_t)r * K + k] = cc[r];
+      J.b[(size_t)r * K + k] = f2d(gg[r]) + rr * cc[r];
+    }
+    J.c[(size_t)4 * K + k] = 0.0;
+    J.b[(size_t)4 * K + k] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      J.RH[(size_t)i * K + k] = RU[i];
+      J.RHf[(size_t)i * K + k] = RUf[i];
     }
     return;
   }
@@ -362,9 +414,9 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
     const int type = J.type[k];
     const int ia = J.ja[k], ib = J.jb[k];
     const uint8_t fl = J.flags[k];
-    const int npt = type == 0 ? 1 : 2;
-    double pa[2][3], pb[2][3], d[2][3];
-    float e[2][3];
+    const int npt = type == 1 ? 2 : 1;
+    double pa[2][3], pb[2][3], d[2][3], d3[3] = {0.0, 0.0, 0.0};
+    float e[2][3], e3[3] = {0.f, 0.f, 0.f};
     load3(J.pa1, K, k, pa[0]);
     load3(J.pb1, K, k, pb[0]);
     if (type == 1) {
@@ -401,6 +453,20 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
           e[t][a] += sd == 0 ? xf[a] : -xf[a];
         }
       }
+      if (type == 2 && sd == 1) {
+        // universal row 3: b's axis vector l a2 moved by dq (FP64) and by z (FP32)
+        double vb[3], l[3];
+        float vbf[3], lf[3];
+        load3(J.pb2, K, k, vb);
+        load3f(J.pb2f, K, k, vbf);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          l[a] = x[a] * vb[0] + x[3 + a] * vb[1] + x[6 + a] * vb[2];
+          lf[a] = z[a] * vbf[0] + z[3 + a] * vbf[1] + z[6 + a] * vbf[2];
+        }
+        mv3(R, l, d3);
+        mv3(Rf, lf, e3);
+      }
     }
     double v[5];
     float w[5];
@@ -411,6 +477,20 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
         v[r] = d[0][r];
         w[r] = e[0][r];
       }
+    } else if (type == 2) {
+      C = 4;
+      double RU[9];
+      float RUf[9];
+      load_R(J.RH, K, k, RU);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) RUf[i] = J.RHf[(size_t)i * K + k];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        v[r] = RU[3 * r] * d[0][0] + RU[3 * r + 1] * d[0][1] + RU[3 * r + 2] * d[0][2];
+        w[r] = RUf[3 * r] * e[0][0] + RUf[3 * r + 1] * e[0][1] + RUf[3 * r + 2] * e[0][2];
+      }
+      v[3] = RU[3] * d3[0] + RU[4] * d3[1] + RU[5] * d3[2];
+      w[3] = RUf[3] * e3[0] + RUf[4] * e3[1] + RUf[5] * e3[2];
     } else {
       C = 5;
       double RH[9];

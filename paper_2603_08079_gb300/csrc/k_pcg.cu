@@ -21,11 +21,11 @@ __device__ __forceinline__ int pk5(int r, int c) { return r >= c ? r * (r + 1) /
 __device__ __forceinline__ int joint_side_rows(const DevBodies &B, const DevJoints &J, int k, int side,
                                                double W[5][12]) {
   const int j = side == 0 ? J.ja[k] : J.jb[k];
-  double R[9], E[5][3], P[2][3];
+  double R[9], E[5][3], P[2][3], wt[2];
   int pt[5];
   load_R(B.R, B.M, j, R);
-  const int C = joint_rows_rest(J, k, side, R, E, P, pt);
-  for (int r = 0; r < C; ++r) kron_row(P[pt[r]], E[r], W[r]);
+  const int C = joint_rows_rest(J, k, side, R, E, P, pt, wt);
+  for (int r = 0; r < C; ++r) kron_row_w(P[pt[r]], wt[pt[r]], E[r], W[r]);
   return C;
 }
 
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(128) k_pcg_setup(DevBodies B, DevJoints J, Dev
   const int K = J.K;
   double rz = 0.0, rr = 0.0;
   if (k < K) {
-    const int C = J.type[k] == 0 ? 3 : 5;
+    const int C = joint_nrows(J.type[k]);
     const uint8_t fl = J.flags[k];
     double D[15];
 #pragma unroll
@@ -167,19 +167,20 @@ __global__ void __launch_bounds__(128) k_pcg_body(DevBodies B, DevJoints J, DevI
   for (int a = 0; a < 12; ++a) g[a] = 0.0;
   for (int e = I.off[j]; e < I.off[j + 1]; ++e) {
     const int k = I.joint[e];
-    double E[5][3], Pt[2][3];
+    double E[5][3], Pt[2][3], wt[2];
     int pt[5];
-    const int C = joint_rows_rest(J, k, I.side[e], R, E, Pt, pt);
+    const int C = joint_rows_rest(J, k, I.side[e], R, E, Pt, pt, wt);
     for (int r = 0; r < C; ++r) {
       const double pr = P.z[(size_t)r * K + k] + beta * P.p[(size_t)r * K + k];
       const double *pp = Pt[pt[r]];
+      const double w = wt[pt[r]];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double v = pr * E[r][a];
         g[a] += pp[0] * v;
         g[3 + a] += pp[1] * v;
         g[6 + a] += pp[2] * v;
-        g[9 + a] += v;
+        g[9 + a] += w * v;
       }
     }
   }
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(128) k_pcg_joint_sp(DevBodies B, DevJoints J, 
   const int K = J.K;
   double psp = 0.0;
   if (k < K) {
-    const int C = J.type[k] == 0 ? 3 : 5;
+    const int C = joint_nrows(J.type[k]);
     const uint8_t fl = J.flags[k];
     const double beta = P.scal[2];
     double pv[5], sp[5];
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(128) k_pcg_joint_update(DevJoints J, DevPCG P)
   const int K = J.K;
   double rz = 0.0, rr = 0.0;
   if (k < K) {
-    const int C = J.type[k] == 0 ? 3 : 5;
+    const int C = joint_nrows(J.type[k]);
     const double alpha = P.scal[1];
     double rv[5], L[15], y[5], x[5];
     for (int r = 0; r < 5; ++r) {

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(128) k_p32_setup(DevBodies B, DevJoints J, Dev
   const int K = J.K;
   float rz = 0.f, rr = 0.f;
   if (k < K) {
-    const int C = J.type[k] == 0 ? 3 : 5;
+    const int C = joint_nrows(J.type[k]);
     const uint8_t fl = J.flags[k];
     float D[15];
 #pragma unroll
@@ -95,11 +95,11 @@ __global__ void __launch_bounds__(128) k_p32_setup(DevBodies B, DevJoints J, Dev
     for (int side = 0; side < 2; ++side) {
       if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
       const int j = side == 0 ? J.ja[k] : J.jb[k];
-      float R[9], h[16], E[5][3], Pt[2][3];
+      float R[9], h[16], E[5][3], Pt[2][3], wt[2];
       int pt[5];
       load_Rf(B, j, R);
       load_hf(B, j, h);
-      rows_rest_f(J, k, side, R, E, Pt, pt);
+      rows_rest_f(J, k, side, R, E, Pt, pt, wt);
       float W[5][12], Z[5][12];
       for (int r = 0; r < C; ++r) {
         const float *pp = Pt[pt[r]];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128) k_p32_setup(DevBodies B, DevJoints J, Dev
           W[r][a] = pp[0] * E[r][a];
           W[r][3 + a] = pp[1] * E[r][a];
           W[r][6 + a] = pp[2] * E[r][a];
-          W[r][9 + a] = E[r][a];
+          W[r][9 + a] = wt[pt[r]] * E[r][a];
         }
         hinvf_apply(h, W[r], Z[r]);
       }
@@ -197,19 +197,20 @@ __global__ void __launch_bounds__(128) k_p32_body(DevBodies B, DevJoints J, DevI
   for (int a = 0; a < 12; ++a) g[a] = 0.f;
   for (int e = I.off[j]; e < I.off[j + 1]; ++e) {
     const int k = I.joint[e];
-    float E[5][3], Pt[2][3];
+    float E[5][3], Pt[2][3], wt[2];
     int pt[5];
-    const int C = rows_rest_f(J, k, I.side[e], R, E, Pt, pt);
+    const int C = rows_rest_f(J, k, I.side[e], R, E, Pt, pt, wt);
     for (int r = 0; r < C; ++r) {
       const float pr = P.z[(size_t)r * K + k] + beta * P.p[(size_t)r * K + k];
       const float *pp = Pt[pt[r]];
+      const float w = wt[pt[r]];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const float v = pr * E[r][a];
         g[a] += pp[0] * v;
         g[3 + a] += pp[1] * v;
         g[6 + a] += pp[2] * v;
-        g[9 + a] += v;
+        g[9 + a] += w * v;
       }
     }
   }
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(128) k_p32_joint_sp(DevBodies B, DevJoints J, 
   const int K = J.K;
   float psp = 0.f;
   if (k < K) {
-    const int C = J.type[k] == 0 ? 3 : 5;
+    const int C = joint_nrows(J.type[k]);
     const uint8_t fl = J.flags[k];
     const float beta = (float)P.scal[2];
     float pv[5], sp[5];
@@ -239,18 +240,19 @@ __global__ void __launch_bounds__(128) k_p32_joint_sp(DevBodies B, DevJoints J, 
     for (int side = 0; side < 2; ++side) {
       if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
       const int j = side == 0 ? J.ja[k] : J.jb[k];
-      float R[9], E[5][3], Pt[2][3], zb[12];
+      float R[9], E[5][3], Pt[2][3], zb[12], wt[2];
       int pt[5];
       load_Rf(B, j, R);
-      rows_rest_f(J, k, side, R, E, Pt, pt);
+      rows_rest_f(J, k, side, R, E, Pt, pt, wt);
 #pragma unroll
       for (int a = 0; a < 12; ++a) zb[a] = P.zb[(size_t)a * B.M + j];
       for (int r = 0; r < C; ++r) {
         const float *pp = Pt[pt[r]];
+        const float w = wt[pt[r]];
         float v = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-          v += E[r][a] * (pp[0] * zb[a] + pp[1] * zb[3 + a] + pp[2] * zb[6 + a] + zb[9 + a]);
+          v += E[r][a] * (pp[0] * zb[a] + pp[1] * zb[3 + a] + pp[2] * zb[6 + a] + w * zb[9 + a]);
         sp[r] += v;
       }
     }
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(128) k_p32_joint_update(DevJoints J, DevPCG32 
   const int K = J.K;
   float rz = 0.f, rr = 0.f;
   if (k < K) {
-    const int C = J.type[k] == 0 ? 3 : 5;
+    const int C = joint_nrows(J.type[k]);
     const float alpha = (float)P.scal[1];
     float rv[5], L[15], z[5];
 #pragma unroll

@@ -189,7 +189,7 @@ inline bool finite_arr(const double *a, int n) {
   return true;
 }
 
-inline int joint_rows(int type) { return type == MABD_JOINT_HINGE ? 5 : 3; }
+inline int joint_rows(int type) { return joint_nrows(type); }
 
 // --------------------------------------------------------------------------
 // topology
@@ -718,11 +718,14 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
   if ((int64_t)ctx->joints.size() + n > (int64_t)INT32_MAX / 16) return MABD_ERR_INVALID_ARG;
   for (int64_t i = 0; i < n; ++i) {
     const auto &j = d[i];
-    if (j.type != MABD_JOINT_BALL && j.type != MABD_JOINT_HINGE) return MABD_ERR_INVALID_ARG;
+    if (j.type != MABD_JOINT_BALL && j.type != MABD_JOINT_HINGE && j.type != MABD_JOINT_UNIVERSAL)
+      return MABD_ERR_INVALID_ARG;
+    // a universal joint's fourth row lies on body b alone: b must be a body
+    if (j.type == MABD_JOINT_UNIVERSAL && j.body_b < 0) return MABD_ERR_INVALID_ARG;
     if (!finite_arr(j.anchor_a, 3) || !finite_arr(j.anchor_b, 3) || !finite_arr(j.axis_a, 3) ||
         !finite_arr(j.axis_b, 3))
       return MABD_ERR_INVALID_ARG;
-    if (j.type == MABD_JOINT_HINGE) {
+    if (j.type != MABD_JOINT_BALL) {
       double na = j.axis_a[0] * j.axis_a[0] + j.axis_a[1] * j.axis_a[1] + j.axis_a[2] * j.axis_a[2];
       double nb = j.axis_b[0] * j.axis_b[0] + j.axis_b[1] * j.axis_b[1] + j.axis_b[2] * j.axis_b[2];
       if (!(na > 0.0) || !(nb > 0.0) || !(j.axis_len > 0.0) || !std::isfinite(j.axis_len))
@@ -861,11 +864,16 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     const bool afree = !ctx->bodies[j.body_a].fixed;
     const bool bfree = j.body_b >= 0 && !ctx->bodies[j.body_b].fixed;
     if (!afree && !bfree) return MABD_ERR_INVALID_ARG;  // no unknown: rows would be void
+    if (j.type == MABD_JOINT_UNIVERSAL && !bfree) return MABD_ERR_INVALID_ARG;  // row 3 lies on b
   }
   // ---- topology and ordering
   Graph g = build_graph(ctx);
   std::vector<int32_t> border, jorder, cborder, cjorder;
   TreeOrder tord;
+  // the chain, tree and loop solvers take 3- and 5-row joints; a scene with
+  // universal joints (4 rows) takes the PCG solver
+  bool has_univ = false;
+  for (int k = 0; k < K; ++k) has_univ = has_univ || g.jtype[k] == MABD_JOINT_UNIVERSAL;
   const bool is_chain = K > 0 && chain_order(g, cborder, cjorder);
   const bool is_tree = K > 0 && tree_order(ctx, g, tord);
   std::vector<int32_t> rborder, rjorder;
@@ -882,6 +890,14 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
                         : (is_tree ? MABD_SOLVER_TREE
                                    : ((is_ring && ctx->cfg.precision == MABD_FP64) ? MABD_SOLVER_LOOP
                                                                                    : MABD_SOLVER_PCG));
+  }
+  if (has_univ && solver != MABD_SOLVER_PCG) {
+    if (ctx->cfg.solver != MABD_SOLVER_AUTO) {
+      std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
+                    "universal joints are solved by the PCG solver only");
+      return MABD_ERR_UNSUPPORTED;
+    }
+    solver = MABD_SOLVER_PCG;
   }
   if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
   if (solver == MABD_SOLVER_TREE && !is_tree) return MABD_ERR_UNSUPPORTED;
@@ -971,8 +987,14 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       pb1[(size_t)a * K + i] = d.anchor_b[a];
       double uaa = na > 0 ? d.axis_a[a] / na : 0.0, ubb = nb > 0 ? d.axis_b[a] / nb : 0.0;
       ua[(size_t)a * K + i] = uaa;
-      pa2[(size_t)a * K + i] = d.anchor_a[a] + d.axis_len * uaa;
-      pb2[(size_t)a * K + i] = d.anchor_b[a] + d.axis_len * ubb;
+      if (d.type == MABD_JOINT_UNIVERSAL) {
+        // b's axis as the point difference l a2 (weight 0 on translation)
+        pa2[(size_t)a * K + i] = 0.0;
+        pb2[(size_t)a * K + i] = d.axis_len * ubb;
+      } else {
+        pa2[(size_t)a * K + i] = d.anchor_a[a] + d.axis_len * uaa;
+        pb2[(size_t)a * K + i] = d.anchor_b[a] + d.axis_len * ubb;
+      }
     }
   }
   // incidence over internal order, joints sorted by internal index
@@ -1012,9 +1034,9 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     std::vector<int> jkey(K), bkey(M);
     for (int i = 0; i < K; ++i) jkey[i] = jtype[i];
     for (int j = 0; j < M; ++j) {
-      // joint types in incidence order, base 3 (0: none), first four joints
+      // joint types in incidence order, base 4 (0: none), first four joints
       int kv = 0;
-      for (int e = ioff[j], t = 0; e < ioff[j + 1] && t < 4; ++e, ++t) kv = kv * 3 + 1 + jtype[ijoint[e]];
+      for (int e = ioff[j], t = 0; e < ioff[j + 1] && t < 4; ++e, ++t) kv = kv * 4 + 1 + jtype[ijoint[e]];
       bkey[j] = kv;
     }
     chunk_order(K, jkey, jord);

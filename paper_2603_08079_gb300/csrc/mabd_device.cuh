@@ -138,7 +138,9 @@ __device__ __forceinline__ void row_dir(int type, const S RH[9], int r, S d[3]) 
     d[1] = r == 1 ? S(1) : S(0);
     d[2] = r == 2 ? S(1) : S(0);
   } else {
-    int rr = r < 3 ? r : (r == 3 ? 0 : 2);
+    // hinge: rows 3, 4 are R_H's x and z rows; universal (R_U in RH): row 3
+    // is its a1 row
+    int rr = r < 3 ? r : (type == 2 ? 1 : (r == 3 ? 0 : 2));
     d[0] = RH[3 * rr];
     d[1] = RH[3 * rr + 1];
     d[2] = RH[3 * rr + 2];
@@ -192,31 +194,78 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // directions E[r], the points P[0..1] and the point index pt[r]; returns C.
 template <typename S>
 __device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int side, const S R[9],
-                                               S E[5][3], S P[2][3], int pt[5]) {
+                                               S E[5][3], S P[2][3], int pt[5], S wgt[2]) {
   const int K = J.K;
   const int type = J.type[k];
   const S sgn = side == 0 ? S(1) : S(-1);
   load3(JP<S>::p1(J, side), K, k, P[0]);
+  wgt[0] = S(1);
+  wgt[1] = S(1);
   S RH[9];
-  if (type == 1) {
+  if (type != 0) {
     load3(JP<S>::p2(J, side), K, k, P[1]);
 #pragma unroll
     for (int i = 0; i < 9; ++i) RH[i] = JP<S>::RH(J)[(size_t)i * K + k];
   }
-  const int C = type == 0 ? 3 : 5;
+  const int C = joint_nrows(type);
   for (int r = 0; r < C; ++r) {
     S d[3], e[3];
     row_dir(type, RH, r, d);
     mtv3(R, d, e);
-    E[r][0] = sgn * e[0];
-    E[r][1] = sgn * e[1];
-    E[r][2] = sgn * e[2];
+    // the universal joint's row 3: + a1 (x) [l a2; 0] on beta (a point
+    // difference: weight 0 on the translation), nothing on alpha
+    const S s = (type == 2 && r == 3) ? (side == 0 ? S(0) : S(1)) : sgn;
+    E[r][0] = s * e[0];
+    E[r][1] = s * e[1];
+    E[r][2] = s * e[2];
     pt[r] = r < 3 ? 0 : 1;
   }
+  if (type == 2) wgt[1] = S(0);
   return C;
 }
 
+template <typename S>
+__device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int side, const S R[9],
+                                               S E[5][3], S P[2][3], int pt[5]) {
+  S wgt[2];
+  return joint_rows_rest(J, k, side, R, E, P, pt, wgt);
+}
+
+// Sec. 4.4 universal joint frame R_U = [a1 x a2; a1; a2] (rows), frozen at
+// q_n: a1 = Ra ua (alpha's axis), a2 = Rb vb (beta's axis) made normal to a1
+// (Gram-Schmidt), both normalised
+template <typename S>
+__device__ __forceinline__ void universal_frame(const S Ra[9], const S ua[3], const S Rb[9], const S vb[3],
+                                                S RU[9]) {
+  S a1[3], w[3];
+  mv3(Ra, ua, a1);
+  mv3(Rb, vb, w);
+  S n = rsq(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+  a1[0] *= n; a1[1] *= n; a1[2] *= n;
+  const S d = a1[0] * w[0] + a1[1] * w[1] + a1[2] * w[2];
+  w[0] -= d * a1[0]; w[1] -= d * a1[1]; w[2] -= d * a1[2];
+  n = rsq(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  w[0] *= n; w[1] *= n; w[2] *= n;
+  RU[0] = a1[1] * w[2] - a1[2] * w[1];
+  RU[1] = a1[2] * w[0] - a1[0] * w[2];
+  RU[2] = a1[0] * w[1] - a1[1] * w[0];
+  RU[3] = a1[0]; RU[4] = a1[1]; RU[5] = a1[2];
+  RU[6] = w[0]; RU[7] = w[1]; RU[8] = w[2];
+}
+
 // w = [p; 1] (x) e as a 12-vector
+// w = [p; wt] (x) e (wt = 0: a point difference, no translation part)
+template <typename S>
+__device__ __forceinline__ void kron_row_w(const S p[3], S wt, const S e[3], S w[12]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    w[a] = p[0] * e[a];
+    w[3 + a] = p[1] * e[a];
+    w[6 + a] = p[2] * e[a];
+    w[9 + a] = wt * e[a];
+  }
+}
+
 template <typename S>
 __device__ __forceinline__ void kron_row(const S p[3], const S e[3], S w[12]) {
 #pragma unroll

@@ -37,37 +37,13 @@ __device__ __forceinline__ void load3f(const float *p, int N, int k, float out[3
   out[2] = __ldg(p + 2 * (size_t)N + k);
 }
 
-// rows of joint k on its side `side` (body with FP32 rotation R): row r is
-// s [p; 1] (x) (R^T d_r) (frozen frame, Eq. pcpq), s = +1 on a, -1 on b.
-// Writes directions E, points P and the point index pt[r]; returns C_k.
+// rows of joint k on its side `side` (body with FP32 rotation R), from the
+// FP32 copies of the joint points and frame: joint_rows_rest<float>; wt[]
+// are the points' translation weights (0 for the universal joint's point
+// difference)
 __device__ __forceinline__ int rows_rest_f(const DevJoints &J, int k, int side, const float R[9],
-                                           float E[5][3], float P[2][3], int pt[5]) {
-  const int K = J.K;
-  const int type = J.type[k];
-  const float sgn = side == 0 ? 1.f : -1.f;
-  load3f(side == 0 ? J.pa1f : J.pb1f, K, k, P[0]);
-  if (type == 0) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) E[r][a] = sgn * R[3 * r + a];
-      pt[r] = 0;
-    }
-    return 3;
-  }
-  load3f(side == 0 ? J.pa2f : J.pb2f, K, k, P[1]);
-  float RH[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) RH[i] = J.RHf[(size_t)i * K + k];
-#pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    const int rr = r < 3 ? r : (r == 3 ? 0 : 2);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      E[r][a] = sgn * (R[a] * RH[3 * rr] + R[3 + a] * RH[3 * rr + 1] + R[6 + a] * RH[3 * rr + 2]);
-    pt[r] = r < 3 ? 0 : 1;
-  }
-  return 5;
+                                           float E[5][3], float P[2][3], int pt[5], float wt[2]) {
+  return joint_rows_rest<float>(J, k, side, R, E, P, pt, wt);
 }
 
 }  // namespace mabd

@@ -54,18 +54,25 @@ struct DevBodies {
 // joint flags
 enum : uint8_t { JF_A_FREE = 1, JF_B_BODY = 2, JF_B_FREE = 4 };
 
+// constraint rows of a joint type: ball 3, hinge 5, universal 4
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int joint_nrows(int type) { return type == 1 ? 5 : (type == 2 ? 4 : 3); }
+
 struct DevJoints {
   int32_t K;
-  const int8_t *type;    // [K] 0 ball, 1 hinge
+  const int8_t *type;    // [K] 0 ball, 1 hinge, 2 universal
   const int32_t *ja;     // [K] internal body index of a
   const int32_t *jb;     // [K] internal body index of b, -1 for the world
   const uint8_t *flags;  // [K] JF_*
   const double *pa1;     // [3][K] anchor on a (rest frame)
   const double *pb1;     // [3][K] anchor on b (rest frame) or world point
   const double *pa2;     // [3][K] second on-axis point on a (hinge)
-  const double *pb2;     // [3][K] second on-axis point on b (hinge)
+  const double *pb2;     // [3][K] second on-axis point on b (hinge); universal: l a2,
+                         //        b's axis as a point difference
   const double *ua;      // [3][K] unit hinge axis in a's rest frame
-  double *RH;            // [9][K] hinge frame of the step
+  double *RH;            // [9][K] hinge frame R_H, or the universal frame R_U, of the step
   double *c;             // [5][K] C(q_n)
   double *b;             // [5][K] dual rhs G u + C(q_n)
   double *lambda;        // [5][K] multipliers (rows beyond C_k are zero)

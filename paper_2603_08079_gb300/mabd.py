@@ -195,7 +195,6 @@ class Solver:
             cfg.dev_alloc, cfg.dev_free = self._cb
         self.M = len(sc["mass"])
         self.K = len(sc["jtype"])
-        self.rows = int(np.sum(np.where(np.asarray(sc["jtype"]) == 1, 5, 3)))
         ctx = C.c_void_p()
         self._check("mabd_create", self._lib.mabd_create(C.byref(cfg), C.byref(ctx)))
         self.ctx = ctx
@@ -207,6 +206,7 @@ class Solver:
         if self.K:
             self._check("mabd_add_joints", self._lib.mabd_add_joints(self.ctx, self.K, _ptr(joints), C.byref(first)))
         self._check("mabd_prefactor", self._lib.mabd_prefactor(self.ctx))
+        self.rows = int(self.info()["dual_rows"])
 
     def _check(self, what, st):
         if st != 0:

@@ -35,6 +35,8 @@ import numpy as np
 WORLD = -1
 BALL = 0
 HINGE = 1
+UNIVERSAL = 2
+PRISMATIC = 3
 ROWS = {BALL: 3, HINGE: 5}
 
 _I9 = np.array([1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0])
@@ -470,10 +472,15 @@ def pendulum(theta0: float, h: float = 1e-3, young: float = 1e8) -> dict:
 
 def random_small(topology: str, M: int, seed: int, h: float = 1e-2,
                  young: float = 1e8, pin: bool = True, hinge_frac: float = 0.5,
-                 gap: float = 0.02) -> dict:
+                 gap: float = 0.02, univ_frac: float = 0.0, prism_frac: float = 0.0) -> dict:
     """Small random scene with mixed ball/hinge joints.
 
     topology: 'chain' (path 0-1-...-M-1, optional world pins at both ends),
+    with univ_frac > 0 joints between two bodies are universal joints with
+    that probability (axes perpendicular at generation); with prism_frac > 0
+    any joint is a prismatic joint with that probability (the same sliding
+    axis and reference direction on both sides, the reference normal to the
+    axis; the scene then carries 'ref_a' / 'ref_b');
     'tree' (random parent p < j, root pinned), 'loop' (ring), 'graph' (tree
     plus extra random edges), 'free' (tree with no world pins).  Bodies are
     boxes with sides U[0.3,1.2]^3 and densities 10^U[2.5,3.5]; each joint
@@ -507,6 +514,9 @@ def random_small(topology: str, M: int, seed: int, h: float = 1e-2,
             world.append(M - 1)
     K = len(edges) + len(world)
     sc = _empty_scene(M, K, h)
+    if prism_frac > 0:
+        sc["ref_a"] = np.zeros((K, 3))
+        sc["ref_b"] = np.zeros((K, 3))
     _set_boxes(sc, sides, rho, centres, young)
     k = 0
     order = []
@@ -534,6 +544,17 @@ def random_small(topology: str, M: int, seed: int, h: float = 1e-2,
         sc["axis_a"][k] = _unit(rng.standard_normal(3))
         sc["axis_b"][k] = _unit(rng.standard_normal(3))
         sc["axis_len"][k] = rng.uniform(0.5, 1.5)
+        if univ_frac > 0 and kind == "e" and rng.random() < univ_frac:
+            # universal joint (Sec. 4.4): beta's axis perpendicular to alpha's
+            sc["jtype"][k] = UNIVERSAL
+            sc["axis_b"][k] = _unit(np.cross(sc["axis_a"][k], sc["axis_b"][k]))
+        if prism_frac > 0 and rng.random() < prism_frac:
+            # prismatic joint (Sec. 4.5); bodies have A = I at generation
+            sc["jtype"][k] = PRISMATIC
+            sc["axis_b"][k] = sc["axis_a"][k]
+            ref = _unit(np.cross(sc["axis_a"][k], rng.standard_normal(3)))
+            sc["ref_a"][k] = ref
+            sc["ref_b"][k] = ref
         k += 1
     return sc
 
@@ -578,6 +599,8 @@ def rotate_scene(sc: dict, Q: np.ndarray) -> dict:
     w = sc["body_b"] == WORLD
     out["anchor_b"][w] = sc["anchor_b"][w] @ Q.T
     out["axis_b"][w] = sc["axis_b"][w] @ Q.T
+    if "ref_b" in sc:
+        out["ref_b"][w] = sc["ref_b"][w] @ Q.T
     return out
 
 
@@ -655,8 +678,21 @@ def lpc_probe(nv: int, K: int, seed: int) -> np.ndarray:
     return (rng.uniform(-1.0, 1.0, size=(nv, K, 3)) * np.sqrt(3.0)).astype(np.float32)
 
 
+JOINT_ROWS = {BALL: 3, HINGE: 5, UNIVERSAL: 4, PRISMATIC: 5}
+
+
+def joint_rows(jtype) -> np.ndarray:
+    """Constraint rows per joint: ball 3 (Eq. ball), hinge 5 (Eq. hinge),
+    universal 4 (Eq. universal), prismatic 5 (Eq. prismatic)."""
+    jt = np.asarray(jtype)
+    out = np.full(jt.shape, 3, dtype=np.int64)
+    out[(jt == HINGE) | (jt == PRISMATIC)] = 5
+    out[jt == UNIVERSAL] = 4
+    return out
+
+
 def dual_rows(sc: dict) -> int:
-    return int(np.sum(np.where(sc["jtype"] == HINGE, 5, 3)))
+    return int(joint_rows(sc["jtype"]).sum())
 
 
 def workload(name: str, **kw) -> dict:

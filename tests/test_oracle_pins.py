@@ -361,6 +361,142 @@ def test_hinge_constraint_semantics(ora):
     assert np.abs(c[:3]).max() > 1e-2
 
 
+def _universal_pair(rotate=None):
+    """Two boxes sharing a satisfied universal joint at the origin: axis u1
+    fixed in body 0 (alpha), axis u2 perpendicular to it, fixed in body 1."""
+    sc, u1 = _two_body_joint(scenes.UNIVERSAL)
+    u2 = np.cross(u1, [1.0, 0.0, 0.0])
+    u2 /= np.linalg.norm(u2)
+    sc["axis_b"][0] = u2
+    if rotate is not None:
+        sc = scenes.rotate_scene(sc, rotate)
+    return sc, u1, u2
+
+
+def test_universal_constraint_semantics(ora):
+    """Sec. 4.4: a universal joint holds the joint centre together and keeps
+    beta's axis a2 normal to alpha's axis a1 (row 3), so relative rotation
+    about a1 and about a2 is free and rotation about a1 x a2 is not; rows 0-2
+    are the ball rows in the frame R_U = [a1 x a2, a1, a2]^T."""
+    rng = np.random.default_rng(21)
+    Q = scenes.random_rotations(rng, 1)[0]
+    sc, u1, u2 = _universal_pair(rotate=Q)
+    S = ora.Scene(sc)
+    a1, a2 = Q @ u1, Q @ u2
+    base = sc["q"].copy()
+    assert np.abs(ora.joint_eval(S, base, 0)[0]).max() < 1e-13
+
+    def moved(Rm, dt=np.zeros(3)):
+        q = base.copy()
+        q[1, :9] = vec(Rm @ unvec(q[1, :9]))
+        q[1, 9:] = Rm @ q[1, 9:] + dt
+        return q
+
+    for axis in (a1, a2):
+        assert np.abs(ora.joint_eval(S, moved(scenes.axis_angle(axis, 0.6)), 0)[0]).max() < 1e-13
+    c = ora.joint_eval(S, moved(scenes.axis_angle(np.cross(a1, a2), 0.2)), 0)[0]
+    assert np.abs(c[:3]).max() < 1e-13 and abs(c[3]) > 1e-2
+    c = ora.joint_eval(S, moved(np.eye(3), 0.05 * a2), 0)[0]
+    # the ball rows measure the gap in the R_U frame: its a2 row (row 2)
+    np.testing.assert_allclose(c[:3], [0.0, 0.0, -0.05], atol=1e-12)
+
+
+def test_universal_jacobian_matches_finite_differences(ora):
+    """At a satisfied universal joint: all of G_beta, and G_alpha's ball rows,
+    are the exact derivatives of C(q); row 3 of G_alpha is zero (the frozen
+    frame of Eq. pcpq drops a1's dependence on alpha, R5)."""
+    rng = np.random.default_rng(22)
+    sc, _, _ = _universal_pair(rotate=scenes.random_rotations(rng, 1)[0])
+    S = ora.Scene(sc)
+    q = sc["q"].copy()
+    c0, Ga, Gb = ora.joint_eval(S, q, 0)
+    assert Ga.shape == (4, 12) and np.abs(c0).max() < 1e-13
+    assert np.abs(Ga[3]).max() == 0.0 and np.abs(Gb[3, 9:]).max() == 0.0
+    eps = 1e-6
+    for body, G, rows in ((1, Gb, slice(0, 4)), (0, Ga, slice(0, 3))):
+        for col in range(12):
+            qp, qm = q.copy(), q.copy()
+            qp[body, col] += eps
+            qm[body, col] -= eps
+            fd = (ora.joint_eval(S, qp, 0)[0] - ora.joint_eval(S, qm, 0)[0]) / (2 * eps)
+            np.testing.assert_allclose(G[rows, col], fd[rows], atol=2e-8)
+
+
+def _prismatic_pair(rotate=None):
+    """Two boxes sharing a satisfied prismatic joint at the origin: sliding
+    axis u and reference direction v (normal to u) the same in both rest
+    frames (both bodies have A = I)."""
+    sc, u = _two_body_joint(scenes.PRISMATIC)
+    v = np.cross(u, [1.0, 0.0, 0.0])
+    v /= np.linalg.norm(v)
+    sc["ref_a"] = np.zeros((1, 3))
+    sc["ref_b"] = np.zeros((1, 3))
+    sc["ref_a"][0] = v
+    sc["ref_b"][0] = v
+    if rotate is not None:
+        sc = scenes.rotate_scene(sc, rotate)
+    return sc, u, v
+
+
+def test_prismatic_constraint_semantics(ora):
+    """Sec. 4.5: a prismatic joint leaves only the relative translation along
+    its axis a free.  Sliding beta along a keeps C = 0; a relative twist
+    about a shows only in the off-axis row 4; a rotation about x~ (here v)
+    shows in the on-axis z~ row; a sideways offset shows in the rows of its
+    direction at every point pair; moving both bodies rigidly together
+    leaves C = 0 (the frame follows alpha)."""
+    rng = np.random.default_rng(31)
+    Q = scenes.random_rotations(rng, 1)[0]
+    sc, u, v = _prismatic_pair(rotate=Q)
+    S = ora.Scene(sc)
+    a, x = Q @ u, Q @ v              # world sliding axis and x~ (v is normal to u)
+    z = np.cross(x, a)
+    base = sc["q"].copy()
+    assert ora.joint_eval(S, base, 0)[0].shape == (5,)
+    assert np.abs(ora.joint_eval(S, base, 0)[0]).max() < 1e-13
+
+    def moved(Rm, dt=np.zeros(3), bodies=(1,)):
+        q = base.copy()
+        for j in bodies:
+            q[j, :9] = vec(Rm @ unvec(q[j, :9]))
+            q[j, 9:] = Rm @ q[j, 9:] + dt
+        return q
+
+    for s in (0.3, -1.2):
+        assert np.abs(ora.joint_eval(S, moved(np.eye(3), s * a), 0)[0]).max() < 1e-13
+    c = ora.joint_eval(S, moved(scenes.axis_angle(a, 0.2)), 0)[0]
+    assert np.abs(c[:4]).max() < 1e-13 and abs(c[4]) > 1e-2
+    c = ora.joint_eval(S, moved(scenes.axis_angle(x, 0.2)), 0)[0]
+    assert np.abs(c[:3]).max() < 1e-13 and abs(c[3]) > 1e-2
+    c = ora.joint_eval(S, moved(np.eye(3), 0.05 * x + 0.7 * a), 0)[0]
+    np.testing.assert_allclose(c, [-0.05, 0.0, -0.05, 0.0, 0.0], atol=1e-12)
+    c = ora.joint_eval(S, moved(np.eye(3), 0.05 * z), 0)[0]
+    np.testing.assert_allclose(c, [0.0, -0.05, 0.0, -0.05, -0.05], atol=1e-12)
+    Qr = scenes.random_rotations(rng, 1)[0]
+    c = ora.joint_eval(S, moved(Qr, np.array([0.3, -0.2, 0.5]), bodies=(0, 1)), 0)[0]
+    assert np.abs(c).max() < 1e-12
+
+
+def test_prismatic_jacobian_matches_finite_differences(ora):
+    """At a satisfied prismatic joint every gap is zero, so the frame's
+    dependence on alpha that the frozen frame of Eq. pcpq drops contributes
+    nothing: G_alpha and G_beta are the exact derivatives of C(q)."""
+    rng = np.random.default_rng(32)
+    sc, _, _ = _prismatic_pair(rotate=scenes.random_rotations(rng, 1)[0])
+    S = ora.Scene(sc)
+    q = sc["q"].copy()
+    c0, Ga, Gb = ora.joint_eval(S, q, 0)
+    assert Ga.shape == (5, 12) and np.abs(c0).max() < 1e-13
+    eps = 1e-6
+    for body, G in ((0, Ga), (1, Gb)):
+        for col in range(12):
+            qp, qm = q.copy(), q.copy()
+            qp[body, col] += eps
+            qm[body, col] -= eps
+            fd = (ora.joint_eval(S, qp, 0)[0] - ora.joint_eval(S, qm, 0)[0]) / (2 * eps)
+            np.testing.assert_allclose(G[:, col], fd, atol=2e-8)
+
+
 # --------------------------------------------------------------------------
 # a4-a6: the dual solve against a dense bordered KKT solve (Eq. kkt)
 # --------------------------------------------------------------------------
@@ -383,12 +519,28 @@ def dense_kkt(ora, sc, q, qd):
     return dq.reshape(M, 12), sol[n:]
 
 
+def dual_condition(ora, sc, q, qd):
+    """2-norm condition number of the dual matrix G H^-1 G^T (dense)."""
+    S = ora.Scene(sc)
+    Hw, f, G, c = ora.assemble_dense(S, q, qd)
+    M = len(sc["mass"])
+    free = sc["fixed"] == 0
+    idx = np.concatenate([np.arange(12 * j, 12 * j + 12) for j in range(M) if free[j]])
+    H = np.zeros((12 * M, 12 * M))
+    for j in range(M):
+        H[12 * j:12 * j + 12, 12 * j:12 * j + 12] = Hw[j]
+    H, G = H[np.ix_(idx, idx)], G[:, idx]
+    return float(np.linalg.cond(G @ np.linalg.solve(H, G.T)))
+
+
 CASES = [("chain", 6, ["chain", "cg", "dense"]),   # pinned at both ends: a loop through the world
          ("chain", 1, ["chain", "tree", "cg", "dense"]),
          ("tree", 7, ["tree", "cg", "dense"]),
          ("free", 5, ["tree", "cg", "dense"]),
          ("loop", 6, ["cg", "dense"]),
          ("graph", 8, ["cg", "dense"])]
+UNIV_CASES = [("chain", 6, ["chain", "cg", "dense"]), ("tree", 7, ["tree", "cg", "dense"]),
+              ("graph", 8, ["cg", "dense"])]
 
 
 @pytest.mark.parametrize("topo,M,solvers", CASES)
@@ -404,6 +556,46 @@ def test_dual_solvers_equal_dense_kkt(ora, topo, M, solvers):
             assert np.linalg.norm(dq - dq_ref) <= 1e-10 * np.linalg.norm(dq_ref), (solver, seed)
             assert np.linalg.norm(lam - lam_ref) <= 1e-10 * np.linalg.norm(lam_ref), (solver, seed)
             assert st["lin_residual"] < 1e-9
+
+
+@pytest.mark.parametrize("topo,M,solvers", UNIV_CASES)
+def test_universal_joints_equal_dense_kkt(ora, topo, M, solvers):
+    """Scenes with universal joints (4 rows, one on beta alone) through every
+    solver of the topology, against the dense bordered KKT solve."""
+    for seed in range(3):
+        sc = scenes.random_small(topo, M, seed=seed, univ_frac=0.5)
+        assert (sc["jtype"] == scenes.UNIVERSAL).any()
+        q, qd = scenes.perturb_state(sc, seed=seed + 200, rot=0.3)
+        dq_ref, lam_ref = dense_kkt(ora, sc, q, qd)
+        S = ora.Scene(sc)
+        for solver in solvers:
+            q1, qd1, lam, st = ora.step(S, q, qd, solver)
+            assert np.linalg.norm((q1 - q) - dq_ref) <= 1e-10 * np.linalg.norm(dq_ref), (solver, seed)
+            assert np.linalg.norm(lam - lam_ref) <= 1e-10 * np.linalg.norm(lam_ref), (solver, seed)
+
+
+@pytest.mark.parametrize("topo,M,solvers", CASES)
+def test_prismatic_joints_equal_dense_kkt(ora, topo, M, solvers):
+    """Scenes with prismatic joints (5 rows on three point pairs), world
+    joints included, through every solver of the topology, against the
+    dense bordered KKT solve.  Cycles of prismatic joints in the random
+    graphs nearly repeat constraints (one dual system here has condition
+    number ~1e7), and two exact solvers then differ by ~kappa * eps: the
+    bound is 1e-10 up to kappa = 1e5 and grows with kappa beyond, ten times
+    that for CG, which stops on its true residual."""
+    for seed in range(3):
+        sc = scenes.random_small(topo, M, seed=seed, prism_frac=0.5)
+        if not (sc["jtype"] == scenes.PRISMATIC).any():
+            continue
+        q, qd = scenes.perturb_state(sc, seed=seed + 300, rot=0.3)
+        dq_ref, lam_ref = dense_kkt(ora, sc, q, qd)
+        kappa = dual_condition(ora, sc, q, qd)
+        S = ora.Scene(sc)
+        for solver in solvers:
+            q1, qd1, lam, st = ora.step(S, q, qd, solver)
+            tol = 1e-10 * max(1.0, kappa / 1e5) * (10.0 if solver == "cg" else 1.0)
+            assert np.linalg.norm((q1 - q) - dq_ref) <= tol * np.linalg.norm(dq_ref), (solver, seed)
+            assert np.linalg.norm(lam - lam_ref) <= tol * np.linalg.norm(lam_ref), (solver, seed)
 
 
 def test_tree_solver_equals_chain_solver_on_paths(ora):

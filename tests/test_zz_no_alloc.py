@@ -39,7 +39,7 @@ def _noalloc_step(lib, sc, q, qd, torch):
     b = mabd.body_array(st)
     j = mabd.joint_array(sc)
     M, K = len(b), len(j)
-    rows = int(np.sum(np.where(np.asarray(sc["jtype"]) == 1, 5, 3)))
+    rows = scenes.dual_rows(sc)
     db = torch.from_numpy(b.view(np.uint8).copy()).cuda()
     dj = torch.from_numpy(j.view(np.uint8).copy()).cuda()
     dq = torch.empty(12 * M, dtype=torch.float64, device="cuda")
