@@ -62,7 +62,6 @@ WORKLOADS = {
 
 
 def make_scene(name: str, M: int | None = None) -> dict:
-    from paper_2603_08079_gb300 import scenes
     if name == "chain1m":
         return scenes.long_chain(M or M_FULL, seed=1)
     if name == "tree256k":
@@ -574,7 +573,6 @@ _BATCH = None
 def _batch_worker_init(n: int, seed: int):
     global _BATCH
     import oracle as ora
-    from paper_2603_08079_gb300 import scenes
     subs = split_assemblies(scenes.assemblies(n, seed=seed))
     _BATCH = [(sub, ora.Scene(sub)) for sub in subs]
 
@@ -617,7 +615,6 @@ def cpu_baseline_parallel(args) -> dict:
 def cpu_baseline(args, steps: int = 1, M: int | None = None) -> dict:
     """The CPU FP64 oracle as it stands, single-threaded, on a bounded sample."""
     import oracle as ora
-    from paper_2603_08079_gb300 import scenes
 
     if args.workload == "chain1m":
         M = M or args.cpu_bodies
@@ -648,7 +645,6 @@ def run_reference(args):
     if rank != 0:
         return None
     import oracle as ora
-    from paper_2603_08079_gb300 import scenes
 
     cores = 1
     if args.workload == "batch4096":

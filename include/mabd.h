@@ -114,8 +114,19 @@ enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_S
    in the frame R_U = [a1 x a2, a1, a2]^T (a2 made normal to a1, frozen at
    q_n) and a1 . (x_b(p_b + l a2) - x_b(p_b)), which keeps b's axis normal to
    a1.  body_b must be a free body; scenes with universal joints are solved
-   by the PCG solver (AUTO picks it). */
-enum { MABD_JOINT_BALL = 0, MABD_JOINT_HINGE = 1, MABD_JOINT_UNIVERSAL = 2 };
+   by the PCG solver (AUTO picks it; the chain, tree and loop solvers return
+   MABD_ERR_UNSUPPORTED). */
+/* MABD_JOINT_PRISMATIC (Sec. 4.5, 5 rows): body b slides along the axis
+   of body a and nothing else.  anchor_a / anchor_b are a point of the
+   sliding line in each rest frame, axis_a / axis_b the sliding direction in
+   each rest frame (axis_b a world direction when body_b is MABD_WORLD),
+   ref_a / ref_b a direction normal to the axis, the same at rest in both
+   frames, axis_len l the spacing of the further points.  The frame R_P =
+   [x; y; z] follows body a (y = the axis, x = ref_a made normal to it,
+   z = x cross y; frozen at q_n).  Rows: the x and z components of the gaps
+   between the points p_a / p_b, p_a + l axis_a / p_b + l axis_b, and
+   (z only) p_a + l ref_a / p_b + l ref_b.  Solved by the PCG solver. */
+enum { MABD_JOINT_BALL = 0, MABD_JOINT_HINGE = 1, MABD_JOINT_UNIVERSAL = 2, MABD_JOINT_PRISMATIC = 3 };
 enum { MABD_TOPO_NONE = 0, MABD_TOPO_CHAIN = 1, MABD_TOPO_TREE = 2, MABD_TOPO_GRAPH = 3,
        MABD_TOPO_LOOP = 4 };
 
@@ -144,13 +155,16 @@ typedef struct {
 } mabd_body_desc;
 
 typedef struct {
-  int32_t type;            /* MABD_JOINT_BALL (3 rows), MABD_JOINT_HINGE (5) or MABD_JOINT_UNIVERSAL (4) */
+  int32_t type;            /* MABD_JOINT_BALL (3 rows), MABD_JOINT_HINGE (5), MABD_JOINT_UNIVERSAL (4)
+                              or MABD_JOINT_PRISMATIC (5) */
   int64_t body_a, body_b;  /* body_b may be MABD_WORLD; body_a must be a body */
   double anchor_a[3];      /* joint point in body a's rest frame */
   double anchor_b[3];      /* ... in body b's rest frame, or a world point */
   double axis_a[3];        /* hinge axis in body a's rest frame (the frame follows body a) */
   double axis_b[3];        /* hinge axis in body b's rest frame, or a world axis */
   double axis_len;         /* distance of the second on-axis point (> 0) */
+  double ref_a[3];         /* prismatic: reference direction normal to the axis in a's rest frame */
+  double ref_b[3];         /* prismatic: the same direction in b's rest frame, or a world direction */
 } mabd_joint_desc;
 
 typedef struct {

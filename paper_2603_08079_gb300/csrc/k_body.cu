@@ -85,9 +85,11 @@ __device__ __forceinline__ void u_at(const double R[9], const double ub[12], con
   mv3(R, l, x);
 }
 
-// One thread per joint: C(q_n) (Eq. ball / hinge), the hinge frame R_H taken
-// from body a's rotation (axis sign chosen so that a_y >= 0), and the dual rhs
-// b = G u + C(q_n) with G the frozen-frame Jacobian (Eq. pcpq).
+// One thread per joint: C(q_n) (Eq. ball / hinge / universal / prismatic),
+// the joint frame taken from the bodies' rotations (hinge: axis sign chosen
+// so that a_y >= 0), and the dual rhs b = G u + C(q_n) with G the
+// frozen-frame Jacobian (Eq. pcpq).
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, StepParams p,
                                                     int *status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, St
     }
     return;
   }
-  if (type == 2) {
+  if ((XJ && type == 2)) {
     // universal (Sec. 4.4): ball rows in R_U, row 3 = a1 . A_b (l a2) on b alone
     double uax[3], vb[3], RU[9], Rbb[9], Ab[9], xb[3], lb[3], gb3[3];
     load3(J.ua, K, k, uax);
@@ -171,6 +173,47 @@ __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, St
     J.b[(size_t)4 * K + k] = 0.0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) J.RH[(size_t)i * K + k] = RU[i];
+    return;
+  }
+  if ((XJ && type == 3)) {
+    // prismatic (Sec. 4.5): x~ and z~ rows of the anchor and on-axis gaps,
+    // the z~ row of the off-axis gap, in R_P attached to a
+    double uax[3], P[2][3], Q[2][3], ca[3], RP[9], dd[2][3], gg[2][3];
+    load3(J.ua, K, k, uax);
+    load3(J.pa2, K, k, P[0]);
+    load3(J.pb2, K, k, Q[0]);
+    load3(J.pa3, K, k, P[1]);
+    load3(J.pb3, K, k, Q[1]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ca[a] = P[1][a] - pa1[a];
+    prismatic_frame(Ra, uax, ca, RP);
+#pragma unroll
+    for (int t2 = 0; t2 < 2; ++t2) {
+      gap_of(qa, P[t2], (fl & JF_B_BODY) ? qb : nullptr, Q[t2], dd[t2]);
+      gg[t2][0] = gg[t2][1] = gg[t2][2] = 0.0;
+      double t[3];
+      if (fl & JF_A_FREE) {
+        u_at(Ra, ua, P[t2], t);
+        gg[t2][0] += t[0]; gg[t2][1] += t[1]; gg[t2][2] += t[2];
+      }
+      if (fl & JF_B_FREE) {
+        u_at(Rb, ub, Q[t2], t);
+        gg[t2][0] -= t[0]; gg[t2][1] -= t[1]; gg[t2][2] -= t[2];
+      }
+    }
+    const double *x = RP, *z = RP + 6;
+    const double *dv[5] = {d1, d1, dd[0], dd[0], dd[1]};
+    const double *gv[5] = {g1, g1, gg[0], gg[0], gg[1]};
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const double *e = (r == 0 || r == 2) ? x : z;
+      const double c = e[0] * dv[r][0] + e[1] * dv[r][1] + e[2] * dv[r][2];
+      const double g = e[0] * gv[r][0] + e[1] * gv[r][1] + e[2] * gv[r][2];
+      J.c[(size_t)r * K + k] = c;
+      J.b[(size_t)r * K + k] = g + rr * c;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) J.RH[(size_t)i * K + k] = RP[i];
     return;
   }
   // hinge
@@ -219,6 +262,7 @@ __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, St
 // point (a row with point p and world direction d contributes [p;1] (x) R^T d),
 // dq = diag4(R)(ubar - Hbar^{-1} g) (Eq. recover-dq-explicit), then the
 // implicit Euler update q += dq, qdot = dq / h.
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevIncidence I,
                                                   StepParams p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,8 +283,8 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
     double lam[5];
 #pragma unroll
     for (int r = 0; r < 5; ++r) lam[r] = J.lambda[(size_t)r * K + k];
-    double F1[3], F2[3] = {0.0, 0.0, 0.0};
-    double P1[3], P2[3];
+    double F1[3], F2[3] = {0.0, 0.0, 0.0}, F3[3] = {0.0, 0.0, 0.0};
+    double P1[3], P2[3], P3[3];
     if (side == 0) {
       load3(J.pa1, K, k, P1);
     } else {
@@ -257,7 +301,17 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
       if (type == 1) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) F2[a] = lam[3] * RH[a] + lam[4] * RH[6 + a];
-      } else if (side == 1) {
+      } else if ((XJ && type == 3)) {
+        // prismatic: x~, z~ at the anchors, x~, z~ on the axis, z~ off it
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          F1[a] = lam[0] * RH[a] + lam[1] * RH[6 + a];
+          F2[a] = lam[2] * RH[a] + lam[3] * RH[6 + a];
+          F3[a] = lam[4] * RH[6 + a];
+        }
+        if (side == 0) load3(J.pa3, K, k, P3);
+        else load3(J.pb3, K, k, P3);
+      } else if (XJ && side == 1) {
         // universal row 3 on b: + a1 lambda_3 at the point difference l a2
 #pragma unroll
         for (int a = 0; a < 3; ++a) F2[a] = -lam[3] * RH[3 + a];  // sgn = -1 on b cancels below
@@ -276,7 +330,7 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
       g[6 + a] += P1[2] * v;
       g[9 + a] += v;
     }
-    if (type == 1 || (type == 2 && side == 1)) {
+    if (type == 1 || (XJ && type == 3) || ((XJ && type == 2) && side == 1)) {
       double f2[3];
       mtv3(R, F2, f2);
 #pragma unroll
@@ -286,6 +340,18 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
         g[3 + a] += P2[1] * v;
         g[6 + a] += P2[2] * v;
         g[9 + a] += w2 * v;
+      }
+    }
+    if ((XJ && type == 3)) {
+      double f3[3];
+      mtv3(R, F3, f3);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double v = sgn * f3[a];
+        g[a] += P3[0] * v;
+        g[3 + a] += P3[1] * v;
+        g[6 + a] += P3[2] * v;
+        g[9 + a] += v;
       }
     }
   }
@@ -311,6 +377,7 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
 // One thread per joint (statistics only): linearized residual G dq + C(q_n)
 // with dq = h qdot_{n+1}, and the nonlinear residual C(q_{n+1}) with the hinge
 // frame re-evaluated from body a's new rotation.
+template <bool XJ>
 __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoints &J,
                                                 const StepParams &p, int k, int *status,
                                                 double &lin_out, double &nl_out) {
@@ -319,7 +386,7 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
   const int ia = J.ja[k], ib = J.jb[k];
   const uint8_t fl = J.flags[k];
   const int C = joint_nrows(type);
-  const int npt = type == 0 ? 1 : 2;
+  const int npt = type == 0 ? 1 : ((XJ && type == 3) ? 3 : 2);
   double qa[12], qb[12], dqa[12], dqb[12];
   load12(B.q, M, ia, qa);
   load12(B.qd, M, ia, dqa);
@@ -327,18 +394,22 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
     load12(B.q, M, ib, qb);
     load12(B.qd, M, ib, dqb);
   }
-  double P[2][3], Q[2][3];
+  double P[3][3], Q[3][3];
   load3(J.pa1, K, k, P[0]);
   load3(J.pb1, K, k, Q[0]);
   if (type != 0) {
     load3(J.pa2, K, k, P[1]);
     load3(J.pb2, K, k, Q[1]);
   }
+  if ((XJ && type == 3)) {
+    load3(J.pa3, K, k, P[2]);
+    load3(J.pb3, K, k, Q[2]);
+  }
   double RH[9];
   if (type != 0) load_R(J.RH, K, k, RH);
   // linearized residual with the frozen frame of this step
   double lin = 0.0;
-  double da[2][3], db[2][3];
+  double da[3][3], db[3][3];
   for (int pt = 0; pt < npt; ++pt) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -352,7 +423,7 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
     }
     if (fl & JF_B_FREE) {
       // (the universal joint's second point on b is a difference: no translation)
-      const double wt = (type == 2 && pt == 1) ? 0.0 : 1.0;
+      const double wt = ((XJ && type == 2) && pt == 1) ? 0.0 : 1.0;
 #pragma unroll
       for (int a = 0; a < 3; ++a)
         db[pt][a] = p.h * (dqb[a] * Q[pt][0] + dqb[3 + a] * Q[pt][1] + dqb[6 + a] * Q[pt][2] + wt * dqb[9 + a]);
@@ -361,9 +432,9 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
   for (int r = 0; r < C; ++r) {
     double d[3];
     row_dir(type, RH, r, d);
-    const int pt = r < 3 ? 0 : 1;
+    const int pt = (XJ && type == 3) ? (r >> 1) : (r < 3 ? 0 : 1);
     double v = J.c[(size_t)r * K + k];
-    if (type == 2 && r == 3) {
+    if ((XJ && type == 2) && r == 3) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) v += d[a] * db[1][a];
     } else {
@@ -379,7 +450,7 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
   gap_of(qa, P[0], qbp, Q[0], d1);
   if (type == 0) {
     nl = fmax(fabs(d1[0]), fmax(fabs(d1[1]), fabs(d1[2])));
-  } else if (type == 2) {
+  } else if ((XJ && type == 2)) {
     double A[9], Ra[9], Rb[9], u[3], RU[9], xb[3], c1[3];
     A_from_q(qa, A);
     int st = polar3(A, Ra);
@@ -393,6 +464,23 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
     mv3(A, Q[1], xb);
     const double c3 = RU[3] * xb[0] + RU[4] * xb[1] + RU[5] * xb[2];
     nl = fmax(fmax(fabs(c1[0]), fabs(c1[1])), fmax(fabs(c1[2]), fabs(c3)));
+  } else if ((XJ && type == 3)) {
+    double A[9], Ra[9], u[3], ca[3], RP[9], d3[3];
+    A_from_q(qa, A);
+    int st = polar3(A, Ra);
+    if (st) set_status(status, st);
+    load3(J.ua, K, k, u);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ca[a] = P[2][a] - P[0][a];
+    prismatic_frame(Ra, u, ca, RP);
+    gap_of(qa, P[1], qbp, Q[1], d2);
+    gap_of(qa, P[2], qbp, Q[2], d3);
+    const double *x = RP, *z = RP + 6;
+    const double *dv[5] = {d1, d1, d2, d2, d3};
+    for (int r = 0; r < 5; ++r) {
+      const double *e = (r == 0 || r == 2) ? x : z;
+      nl = fmax(nl, fabs(e[0] * dv[r][0] + e[1] * dv[r][1] + e[2] * dv[r][2]));
+    }
   } else {
     double A[9], R[9], u[3], a[3], RH1[9];
     A_from_q(qa, A);
@@ -414,11 +502,12 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
   nl_out = nl;
 }
 
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_residuals(DevBodies B, DevJoints J, StepParams p,
                                                    unsigned long long *maxbits, int *status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double lin = 0.0, nl = 0.0;
-  if (t < J.K) joint_residuals(B, J, p, ordered(J.order, t), status, lin, nl);
+  if (t < J.K) joint_residuals<XJ>(B, J, p, ordered(J.order, t), status, lin, nl);
   // warp-level max first (all lanes take part), then one atomic per warp
   for (int o = 16; o > 0; o >>= 1) {
     lin = fmax(lin, __shfl_xor_sync(0xffffffffu, lin, o));
@@ -485,17 +574,23 @@ void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cuda
 
 void launch_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,
                        cudaStream_t s) {
-  if (J.K > 0) k_joint_prep<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, status);
+  if (J.K == 0) return;
+  if (J.xj) k_joint_prep<true><<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, status);
+  else k_joint_prep<false><<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, status);
 }
 
 void launch_backprop(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
                      const StepParams &p, int * /*status*/, cudaStream_t s) {
-  if (B.M > 0) k_backprop<<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+  if (B.M == 0) return;
+  if (J.xj) k_backprop<true><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+  else k_backprop<false><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
 }
 
 void launch_residuals(const DevBodies &B, const DevJoints &J, const StepParams &p,
                       unsigned long long *maxbits, int *status, cudaStream_t s) {
-  if (J.K > 0) k_residuals<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbits, status);
+  if (J.K == 0) return;
+  if (J.xj) k_residuals<true><<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbits, status);
+  else k_residuals<false><<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbits, status);
 }
 
 }  // namespace mabd

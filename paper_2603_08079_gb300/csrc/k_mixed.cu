@@ -72,7 +72,7 @@ __device__ __forceinline__ void hbar_apply(const double s[3], double m, double v
 // (HWCVT: multipliers converted with the conversion instruction instead of
 // fconv.h's integer path; the final kernel, which is not bound by the FP64
 // unit, runs faster that way)
-template <typename T, bool HWCVT = false>
+template <typename T, bool XJ, bool HWCVT = false>
 __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence &I, int j,
                                           const T R[9], const double *lam, T g[12]) {
   const int K = J.K;
@@ -108,12 +108,35 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
         // hinge: rows 3, 4 along R_H's x and z rows; universal: row 3 along
         // a1 (R_U's row 1) at b's point difference l a2, + on b (the
         // negation cancels sgn = -1 below), nothing on a
-        F2[a] = type == 1 ? l[3] * RH[a] + l[4] * RH[6 + a] : -l[3] * RH[3 + a];
+        F2[a] = (!XJ || type == 1) ? l[3] * RH[a] + l[4] * RH[6 + a] : -l[3] * RH[3 + a];
         P2[a] = __ldg(p2 + (size_t)a * K + k);
       }
-      if (type == 2) {
+      if ((XJ && type == 2)) {
         second = side == 1;
         w2 = T(0);
+      }
+      if ((XJ && type == 3)) {
+        // prismatic: x~, z~ at the anchors, x~, z~ on the axis, z~ off it
+        second = true;
+        const T *p3 = JP<T>::p3(J, side);
+        T F3[3], P3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          F1[a] = RH[a] * l[0] + RH[6 + a] * l[1];
+          F2[a] = RH[a] * l[2] + RH[6 + a] * l[3];
+          F3[a] = RH[6 + a] * l[4];
+          P3[a] = __ldg(p3 + (size_t)a * K + k);
+        }
+        T f3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f3[a] = sgn * (R[a] * F3[0] + R[3 + a] * F3[1] + R[6 + a] * F3[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          g[a] += P3[0] * f3[a];
+          g[3 + a] += P3[1] * f3[a];
+          g[6 + a] += P3[2] * f3[a];
+          g[9 + a] += f3[a];
+        }
       }
     }
     T f[3];
@@ -217,8 +240,10 @@ __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p,
   for (int i = 0; i < 12; ++i) B.ubf[(size_t)i * M + j] = u[i];
 }
 
-// One thread per joint: C(q_n) and the hinge frame in FP64 (Eq. ball / hinge,
-// axis from body a with a_y >= 0), b = G u + C(q_n) with G u in FP32.
+// One thread per joint: C(q_n) and the joint frame in FP64 (Eq. ball / hinge /
+// universal / prismatic; hinge axis from body a with a_y >= 0),
+// b = G u + C(q_n) with G u in FP32.
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J, StepParams p,
                                                        int *status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,19 +253,23 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
   const int type = J.type[k];
   const int ia = J.ja[k], ib = J.jb[k];
   const uint8_t fl = J.flags[k];
-  const int npt = type == 1 ? 2 : 1;  // points whose gap is constrained
-  double qa[12], qb[12], pa[2][3], pb[2][3];
+  const int npt = type == 1 ? 2 : ((XJ && type == 3) ? 3 : 1);  // points whose gap is constrained
+  double qa[12], qb[12], pa[3][3], pb[3][3];
   load12(B.q, M, ia, qa);
   if (fl & JF_B_BODY) load12(B.q, M, ib, qb);
   load3(J.pa1, K, k, pa[0]);
   load3(J.pb1, K, k, pb[0]);
-  if (type == 1) {
+  if (type == 1 || (XJ && type == 3)) {
     load3(J.pa2, K, k, pa[1]);
     load3(J.pb2, K, k, pb[1]);
   }
+  if ((XJ && type == 3)) {
+    load3(J.pa3, K, k, pa[2]);
+    load3(J.pb3, K, k, pb[2]);
+  }
   // gaps of the constrained points (FP64) and their displacements under u (FP32)
-  double d[2][3];
-  float g[2][3];
+  double d[3][3];
+  float g[3][3];
   for (int t = 0; t < npt; ++t) {
     gap_of(qa, pa[t], (fl & JF_B_BODY) ? qb : nullptr, pb[t], d[t]);
     g[t][0] = g[t][1] = g[t][2] = 0.f;
@@ -254,7 +283,9 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
     for (int c = 0; c < 12; ++c) u[c] = B.ubf[(size_t)c * M + i];
     for (int t = 0; t < npt; ++t) {
       float pf[3];
-      load3f(sd == 0 ? (t == 0 ? J.pa1f : J.pa2f) : (t == 0 ? J.pb1f : J.pb2f), K, k, pf);
+      const float *src = sd == 0 ? (t == 0 ? J.pa1f : (t == 1 ? J.pa2f : J.pa3f))
+                                 : (t == 0 ? J.pb1f : (t == 1 ? J.pb2f : J.pb3f));
+      load3f(src, K, k, pf);
       float x[3];
       disp_at(R, u, pf, x);
 #pragma unroll
@@ -262,6 +293,34 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
     }
   }
   const double rr = p.residual_rhs ? 1.0 : 0.0;
+  if ((XJ && type == 3)) {
+    // prismatic (Sec. 4.5): x~, z~ of the anchor and on-axis gaps, z~ of the
+    // off-axis gap, in R_P attached to a
+    double uax[3], ca[3], Ra[9], RP[9];
+    load3(J.ua, K, k, uax);
+    load_R(B.R, M, ia, Ra);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ca[a] = pa[2][a] - pa[0][a];
+    prismatic_frame(Ra, uax, ca, RP);
+    float RPf[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) RPf[i] = d2f(RP[i]);
+    const int tpt[5] = {0, 0, 1, 1, 2};
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const int o = (r == 0 || r == 2) ? 0 : 6, q = tpt[r];
+      const double c = RP[o] * d[q][0] + RP[o + 1] * d[q][1] + RP[o + 2] * d[q][2];
+      const float e = RPf[o] * g[q][0] + RPf[o + 1] * g[q][1] + RPf[o + 2] * g[q][2];
+      J.c[(size_t)r * K + k] = c;
+      J.b[(size_t)r * K + k] = f2d(e) + rr * c;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      J.RH[(size_t)i * K + k] = RP[i];
+      J.RHf[(size_t)i * K + k] = RPf[i];
+    }
+    return;
+  }
   if (type == 0) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -270,7 +329,7 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
     }
     return;
   }
-  if (type == 2) {
+  if ((XJ && type == 2)) {
     // universal (Sec. 4.4): ball rows in R_U, row 3 = a1 . A_b (l a2) on b alone
     double uax[3], vb[3], Ra[9], Rb[9], RU[9], Ab[9], xb[3], c1[3];
     load3(J.ua, K, k, uax);
@@ -355,7 +414,7 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
 // correction); tree: dqb as the elimination left it.  Then the FP64 primal residual
 // rb = fbar - Hbar dqb - g(lambda) and the correction's unconstrained solve
 // z = Hbar^{-1} rb in FP32 (kept in ubf).
-template <int MODE>
+template <int MODE, bool XJ>
 __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, DevIncidence I,
                                                      StepParams p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -369,7 +428,7 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
   load_hinvf(B, j, hf);
 #pragma unroll
   for (int i = 0; i < 12; ++i) uf[i] = B.ubf[(size_t)i * M + j];
-  gen_force<double>(J, I, j, R, J.lambda, g64);
+  gen_force<double, XJ>(J, I, j, R, J.lambda, g64);
   if (MODE == MX_FROM_U) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) gf[i] = d2f(g64[i]);
@@ -379,7 +438,7 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
   } else if (MODE == MX_FROM_CORRECTION) {
     float Rf[9];
     load_Rf(B, j, Rf);
-    gen_force<float>(J, I, j, Rf, J.dlam, gf);
+    gen_force<float, XJ>(J, I, j, Rf, J.dlam, gf);
     hinv_apply_t(hf, gf, w);
 #pragma unroll
     for (int i = 0; i < 12; ++i) dq[i] = B.dqb[(size_t)i * M + j] + f2d(uf[i] - w[i]);
@@ -404,6 +463,7 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
 // bracket (the FP64 dual residual, negated) in FP64 and G z in FP32; the
 // largest |C + G dq| goes to *maxbit when it is given.  With the printed zero
 // bottom rhs (residual_rhs = 0) the constraint is G dq = 0 and C drops out.
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, StepParams p,
                                                       unsigned long long *maxbit, bool add_gz) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,16 +474,20 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
     const int type = J.type[k];
     const int ia = J.ja[k], ib = J.jb[k];
     const uint8_t fl = J.flags[k];
-    const int npt = type == 1 ? 2 : 1;
-    double pa[2][3], pb[2][3], d[2][3], d3[3] = {0.0, 0.0, 0.0};
-    float e[2][3], e3[3] = {0.f, 0.f, 0.f};
+    const int npt = type == 1 ? 2 : ((XJ && type == 3) ? 3 : 1);
+    double pa[3][3], pb[3][3], d[3][3], d3[3] = {0.0, 0.0, 0.0};
+    float e[3][3], e3[3] = {0.f, 0.f, 0.f};
     load3(J.pa1, K, k, pa[0]);
     load3(J.pb1, K, k, pb[0]);
-    if (type == 1) {
+    if (type == 1 || (XJ && type == 3)) {
       load3(J.pa2, K, k, pa[1]);
       load3(J.pb2, K, k, pb[1]);
     }
-    for (int t = 0; t < 2; ++t)
+    if ((XJ && type == 3)) {
+      load3(J.pa3, K, k, pa[2]);
+      load3(J.pb3, K, k, pb[2]);
+    }
+    for (int t = 0; t < 3; ++t)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         d[t][a] = 0.0;
@@ -442,7 +506,9 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
       for (int t = 0; t < npt; ++t) {
         const double *pp = sd == 0 ? pa[t] : pb[t];
         float pf[3];
-        load3f(sd == 0 ? (t == 0 ? J.pa1f : J.pa2f) : (t == 0 ? J.pb1f : J.pb2f), K, k, pf);
+        const float *src = sd == 0 ? (t == 0 ? J.pa1f : (t == 1 ? J.pa2f : J.pa3f))
+                                   : (t == 0 ? J.pb1f : (t == 1 ? J.pb2f : J.pb3f));
+        load3f(src, K, k, pf);
         double xd[3];
         float xf[3];
         disp_at(R, x, pp, xd);
@@ -453,7 +519,7 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
           e[t][a] += sd == 0 ? xf[a] : -xf[a];
         }
       }
-      if (type == 2 && sd == 1) {
+      if ((XJ && type == 2) && sd == 1) {
         // universal row 3: b's axis vector l a2 moved by dq (FP64) and by z (FP32)
         double vb[3], l[3];
         float vbf[3], lf[3];
@@ -477,7 +543,7 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
         v[r] = d[0][r];
         w[r] = e[0][r];
       }
-    } else if (type == 2) {
+    } else if ((XJ && type == 2)) {
       C = 4;
       double RU[9];
       float RUf[9];
@@ -491,6 +557,21 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
       }
       v[3] = RU[3] * d3[0] + RU[4] * d3[1] + RU[5] * d3[2];
       w[3] = RUf[3] * e3[0] + RUf[4] * e3[1] + RUf[5] * e3[2];
+    } else if ((XJ && type == 3)) {
+      // prismatic: x~, z~ at the anchors, x~, z~ on the axis, z~ off it
+      C = 5;
+      double RP[9];
+      float RPf[9];
+      load_R(J.RH, K, k, RP);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) RPf[i] = J.RHf[(size_t)i * K + k];
+      const int tpt[5] = {0, 0, 1, 1, 2};
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const int o = (r == 0 || r == 2) ? 0 : 6, q = tpt[r];
+        v[r] = RP[o] * d[q][0] + RP[o + 1] * d[q][1] + RP[o + 2] * d[q][2];
+        w[r] = RPf[o] * e[q][0] + RPf[o + 1] * e[q][1] + RPf[o + 2] * e[q][2];
+      }
     } else {
       C = 5;
       double RH[9];
@@ -527,6 +608,7 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
 // starts at zero), else l = the last correction dlambda; tree (MX_FROM_DQB):
 // dqb as the eliminations left it.  Then dq = diag4(R) dqb, q += dq,
 // qdot = dq / h (implicit Euler, Sec. 3.4).
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevIncidence I,
                                                   StepParams p, int mode) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -544,7 +626,7 @@ __global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevI
     float Rf[9], hf[16], gf[12], w[12];
     load_Rf(B, j, Rf);
     load_hinvf(B, j, hf);
-    gen_force<float, true>(J, I, j, Rf, from_u ? J.lambda : J.dlam, gf);
+    gen_force<float, XJ, true>(J, I, j, Rf, from_u ? J.lambda : J.dlam, gf);
     hinv_apply_t(hf, gf, w);
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
@@ -574,25 +656,38 @@ void launch_mx_body_prep(const DevBodies &B, const StepParams &p, int *status, c
 
 void launch_mx_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,
                           cudaStream_t s) {
-  if (J.K > 0) k_mx_joint_prep<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, status);
+  if (J.K == 0) return;
+  if (J.xj) k_mx_joint_prep<true><<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, status);
+  else k_mx_joint_prep<false><<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, status);
 }
 
 void launch_mx_res_body(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
                         const StepParams &p, int mode, cudaStream_t s) {
   if (B.M <= 0) return;
-  if (mode == MX_FROM_U) k_mx_res_body<MX_FROM_U><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
-  else if (mode == MX_FROM_CORRECTION) k_mx_res_body<MX_FROM_CORRECTION><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
-  else k_mx_res_body<MX_FROM_DQB><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p);
+  const dim3 g(nblk(B.M, 128));
+  if (J.xj) {
+    if (mode == MX_FROM_U) k_mx_res_body<MX_FROM_U, true><<<g, 128, 0, s>>>(B, J, I, p);
+    else if (mode == MX_FROM_CORRECTION) k_mx_res_body<MX_FROM_CORRECTION, true><<<g, 128, 0, s>>>(B, J, I, p);
+    else k_mx_res_body<MX_FROM_DQB, true><<<g, 128, 0, s>>>(B, J, I, p);
+  } else {
+    if (mode == MX_FROM_U) k_mx_res_body<MX_FROM_U, false><<<g, 128, 0, s>>>(B, J, I, p);
+    else if (mode == MX_FROM_CORRECTION) k_mx_res_body<MX_FROM_CORRECTION, false><<<g, 128, 0, s>>>(B, J, I, p);
+    else k_mx_res_body<MX_FROM_DQB, false><<<g, 128, 0, s>>>(B, J, I, p);
+  }
 }
 
 void launch_mx_res_joint(const DevBodies &B, const DevJoints &J, const StepParams &p,
                          unsigned long long *maxbit, cudaStream_t s, bool add_gz) {
-  if (J.K > 0) k_mx_res_joint<<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbit, add_gz);
+  if (J.K == 0) return;
+  if (J.xj) k_mx_res_joint<true><<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbit, add_gz);
+  else k_mx_res_joint<false><<<nblk(J.K, 128), 128, 0, s>>>(B, J, p, maxbit, add_gz);
 }
 
 void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
                      const StepParams &p, int mode, cudaStream_t s) {
-  if (B.M > 0) k_mx_final<<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p, mode);
+  if (B.M == 0) return;
+  if (J.xj) k_mx_final<true><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p, mode);
+  else k_mx_final<false><<<nblk(B.M, 128), 128, 0, s>>>(B, J, I, p, mode);
 }
 
 }  // namespace mabd

@@ -21,7 +21,7 @@ __device__ __forceinline__ int pk5(int r, int c) { return r >= c ? r * (r + 1) /
 __device__ __forceinline__ int joint_side_rows(const DevBodies &B, const DevJoints &J, int k, int side,
                                                double W[5][12]) {
   const int j = side == 0 ? J.ja[k] : J.jb[k];
-  double R[9], E[5][3], P[2][3], wt[2];
+  double R[9], E[5][3], P[3][3], wt[3];
   int pt[5];
   load_R(B.R, B.M, j, R);
   const int C = joint_rows_rest(J, k, side, R, E, P, pt, wt);
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(128) k_pcg_body(DevBodies B, DevJoints J, DevI
   for (int a = 0; a < 12; ++a) g[a] = 0.0;
   for (int e = I.off[j]; e < I.off[j + 1]; ++e) {
     const int k = I.joint[e];
-    double E[5][3], Pt[2][3], wt[2];
+    double E[5][3], Pt[3][3], wt[3];
     int pt[5];
     const int C = joint_rows_rest(J, k, I.side[e], R, E, Pt, pt, wt);
     for (int r = 0; r < C; ++r) {

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(128) k_p32_setup(DevBodies B, DevJoints J, Dev
     for (int side = 0; side < 2; ++side) {
       if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
       const int j = side == 0 ? J.ja[k] : J.jb[k];
-      float R[9], h[16], E[5][3], Pt[2][3], wt[2];
+      float R[9], h[16], E[5][3], Pt[3][3], wt[3];
       int pt[5];
       load_Rf(B, j, R);
       load_hf(B, j, h);
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(128) k_p32_body(DevBodies B, DevJoints J, DevI
   for (int a = 0; a < 12; ++a) g[a] = 0.f;
   for (int e = I.off[j]; e < I.off[j + 1]; ++e) {
     const int k = I.joint[e];
-    float E[5][3], Pt[2][3], wt[2];
+    float E[5][3], Pt[3][3], wt[3];
     int pt[5];
     const int C = rows_rest_f(J, k, I.side[e], R, E, Pt, pt, wt);
     for (int r = 0; r < C; ++r) {
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(128) k_p32_joint_sp(DevBodies B, DevJoints J, 
     for (int side = 0; side < 2; ++side) {
       if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
       const int j = side == 0 ? J.ja[k] : J.jb[k];
-      float R[9], E[5][3], Pt[2][3], zb[12], wt[2];
+      float R[9], E[5][3], Pt[3][3], zb[12], wt[3];
       int pt[5];
       load_Rf(B, j, R);
       rows_rest_f(J, k, side, R, E, Pt, pt, wt);

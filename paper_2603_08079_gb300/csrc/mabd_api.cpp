@@ -718,7 +718,8 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
   if ((int64_t)ctx->joints.size() + n > (int64_t)INT32_MAX / 16) return MABD_ERR_INVALID_ARG;
   for (int64_t i = 0; i < n; ++i) {
     const auto &j = d[i];
-    if (j.type != MABD_JOINT_BALL && j.type != MABD_JOINT_HINGE && j.type != MABD_JOINT_UNIVERSAL)
+    if (j.type != MABD_JOINT_BALL && j.type != MABD_JOINT_HINGE && j.type != MABD_JOINT_UNIVERSAL &&
+        j.type != MABD_JOINT_PRISMATIC)
       return MABD_ERR_INVALID_ARG;
     // a universal joint's fourth row lies on body b alone: b must be a body
     if (j.type == MABD_JOINT_UNIVERSAL && j.body_b < 0) return MABD_ERR_INVALID_ARG;
@@ -729,6 +730,17 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
       double na = j.axis_a[0] * j.axis_a[0] + j.axis_a[1] * j.axis_a[1] + j.axis_a[2] * j.axis_a[2];
       double nb = j.axis_b[0] * j.axis_b[0] + j.axis_b[1] * j.axis_b[1] + j.axis_b[2] * j.axis_b[2];
       if (!(na > 0.0) || !(nb > 0.0) || !(j.axis_len > 0.0) || !std::isfinite(j.axis_len))
+        return MABD_ERR_INVALID_ARG;
+    }
+    if (j.type == MABD_JOINT_PRISMATIC) {
+      // reference directions: finite, non-zero, and ref_a not along axis_a
+      if (!finite_arr(j.ref_a, 3) || !finite_arr(j.ref_b, 3)) return MABD_ERR_INVALID_ARG;
+      const double *u = j.axis_a, *c = j.ref_a;
+      const double nu = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      const double nc = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+      const double cx = u[1] * c[2] - u[2] * c[1], cy = u[2] * c[0] - u[0] * c[2], cz = u[0] * c[1] - u[1] * c[0];
+      const double nrb = std::sqrt(j.ref_b[0] * j.ref_b[0] + j.ref_b[1] * j.ref_b[1] + j.ref_b[2] * j.ref_b[2]);
+      if (!(nc > 0.0) || !(nrb > 0.0) || !(std::sqrt(cx * cx + cy * cy + cz * cz) > 1e-6 * nu * nc))
         return MABD_ERR_INVALID_ARG;
     }
   }
@@ -870,10 +882,14 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   Graph g = build_graph(ctx);
   std::vector<int32_t> border, jorder, cborder, cjorder;
   TreeOrder tord;
-  // the chain, tree and loop solvers take 3- and 5-row joints; a scene with
-  // universal joints (4 rows) takes the PCG solver
-  bool has_univ = false;
-  for (int k = 0; k < K; ++k) has_univ = has_univ || g.jtype[k] == MABD_JOINT_UNIVERSAL;
+  // the chain, tree and loop solvers take ball and hinge joints; a scene
+  // with universal (4 rows) or prismatic joints (three point pairs) takes
+  // the PCG solver
+  bool pcg_only = false, has_prism = false;
+  for (int k = 0; k < K; ++k) {
+    pcg_only = pcg_only || g.jtype[k] == MABD_JOINT_UNIVERSAL || g.jtype[k] == MABD_JOINT_PRISMATIC;
+    has_prism = has_prism || g.jtype[k] == MABD_JOINT_PRISMATIC;
+  }
   const bool is_chain = K > 0 && chain_order(g, cborder, cjorder);
   const bool is_tree = K > 0 && tree_order(ctx, g, tord);
   std::vector<int32_t> rborder, rjorder;
@@ -891,10 +907,10 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
                                    : ((is_ring && ctx->cfg.precision == MABD_FP64) ? MABD_SOLVER_LOOP
                                                                                    : MABD_SOLVER_PCG));
   }
-  if (has_univ && solver != MABD_SOLVER_PCG) {
+  if (pcg_only && solver != MABD_SOLVER_PCG) {
     if (ctx->cfg.solver != MABD_SOLVER_AUTO) {
       std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
-                    "universal joints are solved by the PCG solver only");
+                    "universal and prismatic joints are solved by the PCG solver only");
       return MABD_ERR_UNSUPPORTED;
     }
     solver = MABD_SOLVER_PCG;
@@ -967,7 +983,11 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   std::vector<int32_t> ja(K), jb(K);
   std::vector<uint8_t> jfl(K);
   std::vector<double> pa1(3 * (size_t)K), pb1(3 * (size_t)K), pa2(3 * (size_t)K), pb2(3 * (size_t)K),
-      ua(3 * (size_t)K);
+      ua(3 * (size_t)K), pa3, pb3;
+  if (has_prism) {
+    pa3.assign(3 * (size_t)K, 0.0);
+    pb3.assign(3 * (size_t)K, 0.0);
+  }
   for (int i = 0; i < K; ++i) {
     const auto &d = ctx->joints[jorder[i]];
     jtype[i] = (int8_t)d.type;
@@ -994,6 +1014,15 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       } else {
         pa2[(size_t)a * K + i] = d.anchor_a[a] + d.axis_len * uaa;
         pb2[(size_t)a * K + i] = d.anchor_b[a] + d.axis_len * ubb;
+      }
+    }
+    if (d.type == MABD_JOINT_PRISMATIC) {
+      // the off-axis points p + l c (c: the unit reference directions)
+      const double nca = std::sqrt(d.ref_a[0] * d.ref_a[0] + d.ref_a[1] * d.ref_a[1] + d.ref_a[2] * d.ref_a[2]);
+      const double ncb = std::sqrt(d.ref_b[0] * d.ref_b[0] + d.ref_b[1] * d.ref_b[1] + d.ref_b[2] * d.ref_b[2]);
+      for (int a = 0; a < 3; ++a) {
+        pa3[(size_t)a * K + i] = d.anchor_a[a] + d.axis_len * (d.ref_a[a] / nca);
+        pb3[(size_t)a * K + i] = d.anchor_b[a] + d.axis_len * (d.ref_b[a] / ncb);
       }
     }
   }
@@ -1034,9 +1063,9 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     std::vector<int> jkey(K), bkey(M);
     for (int i = 0; i < K; ++i) jkey[i] = jtype[i];
     for (int j = 0; j < M; ++j) {
-      // joint types in incidence order, base 4 (0: none), first four joints
+      // joint types in incidence order, base 5 (0: none), first four joints
       int kv = 0;
-      for (int e = ioff[j], t = 0; e < ioff[j + 1] && t < 4; ++e, ++t) kv = kv * 4 + 1 + jtype[ijoint[e]];
+      for (int e = ioff[j], t = 0; e < ioff[j + 1] && t < 4; ++e, ++t) kv = kv * 5 + 1 + jtype[ijoint[e]];
       bkey[j] = kv;
     }
     chunk_order(K, jkey, jord);
@@ -1093,6 +1122,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   double *dpa2 = dnew<double>(ctx, 3 * (size_t)Kx, ok);
   double *dpb2 = dnew<double>(ctx, 3 * (size_t)Kx, ok);
   double *dua = dnew<double>(ctx, 3 * (size_t)Kx, ok);
+  double *dpa3 = has_prism ? dnew<double>(ctx, 3 * (size_t)Kx, ok) : nullptr;
+  double *dpb3 = has_prism ? dnew<double>(ctx, 3 * (size_t)Kx, ok) : nullptr;
   J.RH = dnew<double>(ctx, 9 * (size_t)Kx, ok);
   J.c = dnew<double>(ctx, 5 * (size_t)Kx, ok);
   J.b = dnew<double>(ctx, 5 * (size_t)Kx, ok);
@@ -1100,7 +1131,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   const bool mixed = ctx->cfg.precision != MABD_FP64;
   const bool f32dual = ctx->cfg.precision == MABD_MIXED_FP32_DUAL;
   float *dhinvf = nullptr;
-  float *dpf[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *dpf[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const int npf = has_prism ? 6 : 4;
   if (mixed) {
     dhinvf = dnew<float>(ctx, HINV_N * (size_t)Mx, ok);
     B.fbar = dnew<double>(ctx, 12 * (size_t)Mx, ok);
@@ -1109,7 +1141,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     B.Rf = dnew<float>(ctx, 9 * (size_t)Mx, ok);
     J.dlam = dnew<double>(ctx, 5 * (size_t)Kx, ok);
     J.RHf = dnew<float>(ctx, 9 * (size_t)Kx, ok);
-    for (int i = 0; i < 4; ++i) dpf[i] = dnew<float>(ctx, 3 * (size_t)Kx, ok);
+    for (int i = 0; i < npf; ++i) dpf[i] = dnew<float>(ctx, 3 * (size_t)Kx, ok);
   }
   int32_t *djord = jord.empty() ? nullptr : dnew<int32_t>(ctx, jord.size(), ok);
   int32_t *dbord = bord.empty() ? nullptr : dnew<int32_t>(ctx, bord.size(), ok);
@@ -1135,8 +1167,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     CK(cudaMemsetAsync(B.dqb, 0, 12 * (size_t)Mx * 8, ctx->stream));
     CK(cudaMemsetAsync(J.dlam, 0, 5 * (size_t)Kx * 8, ctx->stream));
     CK(cudaMemsetAsync(J.RHf, 0, 9 * (size_t)Kx * 4, ctx->stream));
-    const std::vector<double> *src[4] = {&pa1, &pb1, &pa2, &pb2};
-    for (int i = 0; i < 4; ++i) {
+    const std::vector<double> *src[6] = {&pa1, &pb1, &pa2, &pb2, &pa3, &pb3};
+    for (int i = 0; i < npf; ++i) {
       std::vector<float> f(src[i]->begin(), src[i]->end());
       CK(up(dpf[i], f.data(), f.size() * 4));
     }
@@ -1144,6 +1176,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     J.pb1f = dpf[1];
     J.pa2f = dpf[2];
     J.pb2f = dpf[3];
+    J.pa3f = dpf[4];
+    J.pb3f = dpf[5];
   }
   CK(up(dfixed, fixed.data(), fixed.size()));
   CK(up(djt, jtype.data(), jtype.size()));
@@ -1155,6 +1189,10 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   CK(up(dpa2, pa2.data(), pa2.size() * 8));
   CK(up(dpb2, pb2.data(), pb2.size() * 8));
   CK(up(dua, ua.data(), ua.size() * 8));
+  if (has_prism) {
+    CK(up(dpa3, pa3.data(), pa3.size() * 8));
+    CK(up(dpb3, pb3.data(), pb3.size() * 8));
+  }
   if (djord) CK(up(djord, jord.data(), jord.size() * 4));
   if (dbord) CK(up(dbord, bord.data(), bord.size() * 4));
   J.order = djord;
@@ -1179,6 +1217,9 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   J.pb1 = dpb1;
   J.pa2 = dpa2;
   J.pb2 = dpb2;
+  J.pa3 = dpa3;
+  J.pb3 = dpb3;
+  J.xj = pcg_only;
   J.ua = dua;
   ctx->I.off = dioff;
   ctx->I.joint = dij;

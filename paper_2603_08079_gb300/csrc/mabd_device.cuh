@@ -130,13 +130,21 @@ __device__ __forceinline__ void hinge_frame(const double a[3], double RH[9]) {
 }
 
 // world direction of constraint row r (Eq. ball: identity rows; Eq. hinge:
-// rows 0-2 are the rows of R_H, rows 3 and 4 its x and z rows at the second point)
+// rows 0-2 are the rows of R_H, rows 3 and 4 its x and z rows at the second
+// point; Eq. prismatic: the x and z rows of R_P at the anchors, x and z at
+// the on-axis points, z at the off-axis points)
 template <typename S>
 __device__ __forceinline__ void row_dir(int type, const S RH[9], int r, S d[3]) {
   if (type == 0) {
     d[0] = r == 0 ? S(1) : S(0);
     d[1] = r == 1 ? S(1) : S(0);
     d[2] = r == 2 ? S(1) : S(0);
+  } else if (type == 3) {
+    // prismatic (R_P in RH): rows x, z, x, z, z
+    const int rr = (r == 0 || r == 2) ? 0 : 2;
+    d[0] = RH[3 * rr];
+    d[1] = RH[3 * rr + 1];
+    d[2] = RH[3 * rr + 2];
   } else {
     // hinge: rows 3, 4 are R_H's x and z rows; universal (R_U in RH): row 3
     // is its a1 row
@@ -177,11 +185,13 @@ template <typename S> struct JP;
 template <> struct JP<double> {
   __device__ static const double *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1 : J.pb1; }
   __device__ static const double *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2 : J.pb2; }
+  __device__ static const double *p3(const DevJoints &J, int side) { return side == 0 ? J.pa3 : J.pb3; }
   __device__ static const double *RH(const DevJoints &J) { return J.RH; }
 };
 template <> struct JP<float> {
   __device__ static const float *p1(const DevJoints &J, int side) { return side == 0 ? J.pa1f : J.pb1f; }
   __device__ static const float *p2(const DevJoints &J, int side) { return side == 0 ? J.pa2f : J.pb2f; }
+  __device__ static const float *p3(const DevJoints &J, int side) { return side == 0 ? J.pa3f : J.pb3f; }
   __device__ static const float *RH(const DevJoints &J) { return J.RHf; }
 };
 
@@ -189,24 +199,28 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
 // Rows of joint k on the body with rotation R that is its side `side`
-// (0: body a, 1: body b): row r is s [p; 1] (x) (R^T d_r) in that body's rest
-// frame (frozen frame, Eq. pcpq), s = +1 on a and -1 on b.  Writes the
-// directions E[r], the points P[0..1] and the point index pt[r]; returns C.
-template <typename S>
+// (0: body a, 1: body b): row r is s [p; w] (x) (R^T d_r) in that body's rest
+// frame (frozen frame, Eq. pcpq), s = +1 on a and -1 on b, p the row's point
+// and w its translation weight (0 for a point difference).  Writes the
+// directions E[r], the points P[0..NP-1], their weights and the point index
+// pt[r]; returns C.  NP = 3 holds the prismatic joint's third point pair;
+// the solvers that take only ball and hinge joints pass NP = 2.
+template <typename S, int NP>
 __device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int side, const S R[9],
-                                               S E[5][3], S P[2][3], int pt[5], S wgt[2]) {
+                                               S E[5][3], S (&P)[NP][3], int pt[5], S (&wgt)[NP]) {
   const int K = J.K;
   const int type = J.type[k];
   const S sgn = side == 0 ? S(1) : S(-1);
   load3(JP<S>::p1(J, side), K, k, P[0]);
-  wgt[0] = S(1);
-  wgt[1] = S(1);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) wgt[i] = S(1);
   S RH[9];
   if (type != 0) {
     load3(JP<S>::p2(J, side), K, k, P[1]);
 #pragma unroll
     for (int i = 0; i < 9; ++i) RH[i] = JP<S>::RH(J)[(size_t)i * K + k];
   }
+  if (NP > 2 && type == 3) load3(JP<S>::p3(J, side), K, k, P[NP > 2 ? 2 : 0]);
   const int C = joint_nrows(type);
   for (int r = 0; r < C; ++r) {
     S d[3], e[3];
@@ -218,17 +232,39 @@ __device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int si
     E[r][0] = s * e[0];
     E[r][1] = s * e[1];
     E[r][2] = s * e[2];
-    pt[r] = r < 3 ? 0 : 1;
+    pt[r] = type == 3 ? (r >> 1) : (r < 3 ? 0 : 1);
   }
   if (type == 2) wgt[1] = S(0);
   return C;
 }
 
-template <typename S>
+template <typename S, int NP>
 __device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int side, const S R[9],
-                                               S E[5][3], S P[2][3], int pt[5]) {
-  S wgt[2];
+                                               S E[5][3], S (&P)[NP][3], int pt[5]) {
+  S wgt[NP];
   return joint_rows_rest(J, k, side, R, E, P, pt, wgt);
+}
+
+// Sec. 4.5 prismatic joint frame R_P = [x~; y~; z~] (rows), frozen at q_n and
+// attached to alpha (Sec. 5.1 writes a joint frame as a constant rotation
+// times alpha's R^T): y~ = Ra ua (the sliding axis), x~ = Ra ca made normal
+// to y~ (ca: alpha's reference direction, any length), z~ = x~ x y~
+template <typename S>
+__device__ __forceinline__ void prismatic_frame(const S Ra[9], const S ua[3], const S ca[3], S RP[9]) {
+  S y[3], x[3];
+  mv3(Ra, ua, y);
+  mv3(Ra, ca, x);
+  S n = rsq(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+  y[0] *= n; y[1] *= n; y[2] *= n;
+  const S d = y[0] * x[0] + y[1] * x[1] + y[2] * x[2];
+  x[0] -= d * y[0]; x[1] -= d * y[1]; x[2] -= d * y[2];
+  n = rsq(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  x[0] *= n; x[1] *= n; x[2] *= n;
+  RP[0] = x[0]; RP[1] = x[1]; RP[2] = x[2];
+  RP[3] = y[0]; RP[4] = y[1]; RP[5] = y[2];
+  RP[6] = x[1] * y[2] - x[2] * y[1];
+  RP[7] = x[2] * y[0] - x[0] * y[2];
+  RP[8] = x[0] * y[1] - x[1] * y[0];
 }
 
 // Sec. 4.4 universal joint frame R_U = [a1 x a2; a1; a2] (rows), frozen at
@@ -253,8 +289,8 @@ __device__ __forceinline__ void universal_frame(const S Ra[9], const S ua[3], co
   RU[6] = w[0]; RU[7] = w[1]; RU[8] = w[2];
 }
 
-// w = [p; 1] (x) e as a 12-vector
-// w = [p; wt] (x) e (wt = 0: a point difference, no translation part)
+// w = [p; wt] (x) e as a 12-vector (wt = 0: a point difference, no
+// translation part)
 template <typename S>
 __device__ __forceinline__ void kron_row_w(const S p[3], S wt, const S e[3], S w[12]) {
 #pragma unroll

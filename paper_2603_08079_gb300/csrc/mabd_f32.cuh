@@ -42,8 +42,8 @@ __device__ __forceinline__ void load3f(const float *p, int N, int k, float out[3
 // are the points' translation weights (0 for the universal joint's point
 // difference)
 __device__ __forceinline__ int rows_rest_f(const DevJoints &J, int k, int side, const float R[9],
-                                           float E[5][3], float P[2][3], int pt[5], float wt[2]) {
-  return joint_rows_rest<float>(J, k, side, R, E, P, pt, wt);
+                                           float E[5][3], float (&P)[3][3], int pt[5], float (&wt)[3]) {
+  return joint_rows_rest<float, 3>(J, k, side, R, E, P, pt, wt);
 }
 
 }  // namespace mabd

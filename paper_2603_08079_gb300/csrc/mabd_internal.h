@@ -54,15 +54,15 @@ struct DevBodies {
 // joint flags
 enum : uint8_t { JF_A_FREE = 1, JF_B_BODY = 2, JF_B_FREE = 4 };
 
-// constraint rows of a joint type: ball 3, hinge 5, universal 4
+// constraint rows of a joint type: ball 3, hinge 5, universal 4, prismatic 5
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-inline int joint_nrows(int type) { return type == 1 ? 5 : (type == 2 ? 4 : 3); }
+inline int joint_nrows(int type) { return type == 1 || type == 3 ? 5 : (type == 2 ? 4 : 3); }
 
 struct DevJoints {
   int32_t K;
-  const int8_t *type;    // [K] 0 ball, 1 hinge, 2 universal
+  const int8_t *type;    // [K] 0 ball, 1 hinge, 2 universal, 3 prismatic
   const int32_t *ja;     // [K] internal body index of a
   const int32_t *jb;     // [K] internal body index of b, -1 for the world
   const uint8_t *flags;  // [K] JF_*
@@ -71,18 +71,26 @@ struct DevJoints {
   const double *pa2;     // [3][K] second on-axis point on a (hinge)
   const double *pb2;     // [3][K] second on-axis point on b (hinge); universal: l a2,
                          //        b's axis as a point difference
+  const double *pa3;     // [3][K] prismatic: off-axis point p + l c on a (null: no prismatic joint)
+  const double *pb3;     // [3][K] ... on b
   const double *ua;      // [3][K] unit hinge axis in a's rest frame
-  double *RH;            // [9][K] hinge frame R_H, or the universal frame R_U, of the step
+  double *RH;            // [9][K] hinge frame R_H, universal frame R_U or prismatic frame R_P
+                         //        of the step
   double *c;             // [5][K] C(q_n)
   double *b;             // [5][K] dual rhs G u + C(q_n)
   double *lambda;        // [5][K] multipliers (rows beyond C_k are zero)
   double *dlam;          // [5][K] mixed form: multiplier correction of a refinement sweep
   // mixed form: FP32 copies of the joint points and of the hinge frame
   const float *pa1f, *pb1f, *pa2f, *pb2f;  // [3][K]
+  const float *pa3f, *pb3f;                // [3][K] (null: no prismatic joint)
   float *RHf;                              // [9][K]
   // processing order of the per-joint kernels: thread t handles joint
   // order[t] (null: joint t); see CHUNK_ORDER
   const int32_t *order;
+  // the scene has universal or prismatic joints: the per-body and per-joint
+  // kernels run their instantiation with those branches (the others carry
+  // only the ball and hinge code, fewer registers)
+  bool xj;
 };
 
 // Per-joint and per-body kernels run CTAs of CHUNK_ORDER threads over runs of

@@ -62,8 +62,8 @@ BODY_DTYPE = np.dtype([("mass", "f8"), ("second_moment", "f8", 6), ("volume", "f
                        ("fixed", "i4")], align=True)
 JOINT_DTYPE = np.dtype([("type", "i4"), ("body_a", "i8"), ("body_b", "i8"), ("anchor_a", "f8", 3),
                         ("anchor_b", "f8", 3), ("axis_a", "f8", 3), ("axis_b", "f8", 3),
-                        ("axis_len", "f8")], align=True)
-assert BODY_DTYPE.itemsize == 280 and JOINT_DTYPE.itemsize == 128
+                        ("axis_len", "f8"), ("ref_a", "f8", 3), ("ref_b", "f8", 3)], align=True)
+assert BODY_DTYPE.itemsize == 280 and JOINT_DTYPE.itemsize == 176
 
 _lib = None
 
@@ -153,6 +153,9 @@ def joint_array(sc: dict) -> np.ndarray:
     d = np.zeros(K, dtype=JOINT_DTYPE)
     for f in ("anchor_a", "anchor_b", "axis_a", "axis_b", "axis_len", "body_a", "body_b"):
         d[f] = sc[f]
+    for f in ("ref_a", "ref_b"):  # prismatic joints only
+        if f in sc:
+            d[f] = sc[f]
     d["type"] = sc["jtype"]
     return d
 

@@ -47,6 +47,7 @@ int main(void) {
          offsetof(mabd_joint_desc, body_a), offsetof(mabd_joint_desc, axis_len));
   printf("%zu %zu %zu\n", offsetof(mabd_config, stream), offsetof(mabd_config, dev_alloc),
          offsetof(mabd_config, residual_rhs));
+  printf("%zu %zu\n", offsetof(mabd_joint_desc, ref_a), offsetof(mabd_joint_desc, ref_b));
   return 0;
 }
 ''')
@@ -66,6 +67,8 @@ int main(void) {
     assert vals[9] == mabd.Config.stream.offset
     assert vals[10] == mabd.Config.dev_alloc.offset
     assert vals[11] == mabd.Config.residual_rhs.offset
+    assert vals[12] == mabd.JOINT_DTYPE.fields["ref_a"][1]
+    assert vals[13] == mabd.JOINT_DTYPE.fields["ref_b"][1]
 
 
 def test_config_defaults_and_status_strings(lib):
