@@ -18,6 +18,7 @@
 // All body-space work is done in the body's rest frame: with
 // dqb = diag4(R^T) dq, H dq = diag4(R) Hbar dqb (Eq. abd_final).
 #include "mabd_f32.cuh"
+#include "ff.h"
 
 namespace mabd {
 
@@ -174,68 +175,141 @@ __device__ __forceinline__ void disp_at(const T R[9], const T x[12], const T p[3
   for (int a = 0; a < 3; ++a) out[a] = R[3 * a] * l[0] + R[3 * a + 1] * l[1] + R[3 * a + 2] * l[2];
 }
 
+// Eq. polar in double-float: Newton's iteration X <- (X + X^{-T})/2 with
+// X^{-T} = cof(X)/det(X), the same steps and stopping test as the FP64
+// iteration (polar3); the first determinant is det A (det A <= 0: ST_INVERTED).
+__device__ __forceinline__ int polar3_ff(const ff A[9], ff R[9], int *iters) {
+  ff X[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) X[i] = A[i];
+  int it = 0;
+  for (; it < 40; ++it) {
+    // cof(X)_rc: a b - c d as fma(a, b, -(c d))
+    auto cof = [](ff a, ff b, ff c, ff d) { return ff_fma(a, b, ff_neg(ff_mul(c, d))); };
+    ff C[9];
+    C[0] = cof(X[4], X[8], X[5], X[7]);
+    C[1] = cof(X[5], X[6], X[3], X[8]);
+    C[2] = cof(X[3], X[7], X[4], X[6]);
+    C[3] = cof(X[2], X[7], X[1], X[8]);
+    C[4] = cof(X[0], X[8], X[2], X[6]);
+    C[5] = cof(X[1], X[6], X[0], X[7]);
+    C[6] = cof(X[1], X[5], X[2], X[4]);
+    C[7] = cof(X[2], X[3], X[0], X[5]);
+    C[8] = cof(X[0], X[4], X[1], X[3]);
+    const ff d = ff_fma(X[0], C[0], ff_fma(X[1], C[1], ff_mul(X[2], C[2])));
+    if (!(d.h > 0.0f)) return isfinite(d.h) ? ST_INVERTED : ST_NONFINITE;
+    ff hid = ff_rcp(d);
+    hid.h *= 0.5f;  // exact
+    hid.l *= 0.5f;
+    float diff = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const ff y = ff_fma(hid, C[i], ff{0.5f * X[i].h, 0.5f * X[i].l});
+      const float dx = (y.h - X[i].h) + (y.l - X[i].l);
+      diff = fmaf(dx, dx, diff);
+      X[i] = y;
+    }
+    if (diff <= 3e-18f) break;
+  }
+  if (it == 40) return ST_POLAR_NOCONV;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = X[i];
+  if (iters) *iters = it + 1;
+  return 0;
+}
+
 // One thread per body: R = polar(A) and the rest-frame rhs
-// fbar = diag4(R^T)(M_A qdot/h + [0; m g]) - [V vec P(R^T A); 0] in FP64
-// (Sec. 3.3-3.4); u = Hbar^{-1} fbar in FP32.
+// fbar = diag4(R^T)(M_A qdot/h + [0; m g]) - [V vec P(R^T A); 0]
+// (Sec. 3.3-3.4) in double-float arithmetic (ff.h: ~46 bits, the binary64
+// values of the state split exactly enough, R and fbar stored as binary64),
+// which keeps them off the FP64 unit; u = Hbar^{-1} fbar in FP32.
 __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p, int *status,
                                                       unsigned long long *iters) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= B.M) return;
   const int M = B.M;
-  double q[12], qd[12], A[9], R[9];
-  load12(B.q, M, j, q);
-  A_from_q(q, A);
+  // every load issued before the polar iteration, so that their latency
+  // hides behind it
+  double qa[9], qv[12], cst[6];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) qa[i] = B.q[(size_t)i * M + j];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) qv[i] = B.qd[(size_t)i * M + j];
+  cst[0] = ldg(B.sig + j);
+  cst[1] = ldg(B.sig + M + j);
+  cst[2] = ldg(B.sig + 2 * (size_t)M + j);
+  cst[3] = ldg(B.mass + j);
+  cst[4] = ldg(B.vmu + j);
+  cst[5] = ldg(B.vlam + j);
+  const bool fixed = B.fixed[j] != 0;
+  ff A[9], R[9];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) A[3 * r + c] = ff_from(qa[3 * c + r]);
   int nit = 0;
-  int st = polar3(A, R, &nit);
+  int st = polar3_ff(A, R, &nit);
   if (iters) count_add(iters, (unsigned)nit);
   if (st) {
     set_status(status, st);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    for (int i = 0; i < 9; ++i) R[i] = ff_make((i % 4 == 0) ? 1.0f : 0.0f);
   }
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    B.R[(size_t)i * M + j] = R[i];
-    B.Rf[(size_t)i * M + j] = d2f(R[i]);
+    B.R[(size_t)i * M + j] = ff_to(R[i]);
+    B.Rf[(size_t)i * M + j] = R[i].h;
   }
-  if (B.fixed[j]) return;  // no unknowns; its rotation may still orient a hinge
-  load12(B.qd, M, j, qd);
-  const double s0 = ldg(B.sig + j), s1 = ldg(B.sig + M + j), s2 = ldg(B.sig + 2 * (size_t)M + j);
-  const double m = ldg(B.mass + j);
-  const double sh0 = s0 * p.inv_h, sh1 = s1 * p.inv_h, sh2 = s2 * p.inv_h, mh = m * p.inv_h;
-  const double vmu = ldg(B.vmu + j), vlam = ldg(B.vlam + j);
-  double fw[12];
+  if (fixed) return;  // no unknowns; its rotation may still orient a hinge
+  ff qd[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) qd[i] = ff_from(qv[i]);
+  const ff ih = ff_from(p.inv_h);
+  const ff sh0 = ff_mul(ff_from(cst[0]), ih), sh1 = ff_mul(ff_from(cst[1]), ih), sh2 = ff_mul(ff_from(cst[2]), ih);
+  const ff m = ff_from(cst[3]);
+  const ff mh = ff_mul(m, ih);
+  const ff vmu = ff_from(cst[4]), vlam = ff_from(cst[5]);
+  ff fw[12];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    fw[a] = sh0 * qd[a];
-    fw[3 + a] = sh1 * qd[3 + a];
-    fw[6 + a] = sh2 * qd[6 + a];
-    fw[9 + a] = mh * qd[9 + a] + m * p.g[a];
+    fw[a] = ff_mul(sh0, qd[a]);
+    fw[3 + a] = ff_mul(sh1, qd[3 + a]);
+    fw[6 + a] = ff_mul(sh2, qd[6 + a]);
+    fw[9 + a] = ff_fma(mh, qd[9 + a], ff_mul(m, ff_from(p.g[a])));
   }
-  double fb[12];
+  // fb = diag4(R^T) fw
+  ff fb[12];
 #pragma unroll
-  for (int blk = 0; blk < 4; ++blk) mtv3(R, fw + 3 * blk, fb + 3 * blk);
-  double F[9];
+  for (int blk = 0; blk < 4; ++blk)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      fb[3 * blk + a] = ff_fma(R[a], fw[3 * blk], ff_fma(R[3 + a], fw[3 * blk + 1], ff_mul(R[6 + a], fw[3 * blk + 2])));
+  // F = R^T A and the co-rotated stress P(F) = mu (F + F^T - 2I) + lambda tr(F - I) I
+  ff F[9];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) F[3 * r + c] = R[r] * A[c] + R[3 + r] * A[3 + c] + R[6 + r] * A[6 + c];
-  const double tr = vlam * (F[0] + F[4] + F[8] - 3.0);
+    for (int c = 0; c < 3; ++c)
+      F[3 * r + c] = ff_fma(R[r], A[c], ff_fma(R[3 + r], A[3 + c], ff_mul(R[6 + r], A[6 + c])));
+  const ff tr = ff_mul(vlam, ff_add(ff_add(F[0], F[4]), ff_add(F[8], ff_make(-3.0f))));
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double P = vmu * (F[3 * a + i] + F[3 * i + a] - (a == i ? 2.0 : 0.0)) + (a == i ? tr : 0.0);
-      fb[3 * i + a] -= P;
+      ff e = ff_add(F[3 * a + i], F[3 * i + a]);
+      if (a == i) e = ff_add(e, ff_make(-2.0f));
+      ff P = ff_mul(vmu, e);
+      if (a == i) P = ff_add(P, tr);
+      fb[3 * i + a] = ff_sub(fb[3 * i + a], P);
     }
-  float hf[16], ff[12], u[12];
+  float hf[16], ff32[12], u[12];
   load_hinvf(B, j, hf);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    B.fbar[(size_t)i * M + j] = fb[i];
-    ff[i] = d2f(fb[i]);
+    B.fbar[(size_t)i * M + j] = ff_to(fb[i]);
+    ff32[i] = fb[i].h;
   }
-  hinv_apply_t(hf, ff, u);
+  hinv_apply_t(hf, ff32, u);
 #pragma unroll
   for (int i = 0; i < 12; ++i) B.ubf[(size_t)i * M + j] = u[i];
 }
