@@ -81,11 +81,13 @@ def make_scene(name: str, M: int | None = None) -> dict:
 FORMS = {
     "fp64": "FP64 throughout",
     "mixed": "FP32 per-body/per-joint products (and Gram blocks on chains, PCG iterations on "
-             "graphs); FP64 polar, rhs, constraint values, chain cyclic reduction and %d FP64 "
-             "residual-correction sweep(s)",
+             "graphs); polar and rhs in double-float (FP32 pairs, ~46 bits), FP64 constraint "
+             "values and chain cyclic reduction, %d residual-correction sweep(s) with the primal "
+             "residual in double-float and the dual residual in FP64",
     "mixed_fp32_dual": "FP32 per-body/per-joint products, Gram blocks and chain cyclic reduction "
-                       "or tree elimination (FP32 PCG on graphs); FP64 polar, rhs, constraint "
-                       "values and %d FP64 residual-correction sweep(s) of the FP64 system",
+                       "or tree elimination (FP32 PCG on graphs); polar and rhs in double-float "
+                       "(FP32 pairs, ~46 bits), FP64 constraint values, %d residual-correction "
+                       "sweep(s) of the FP64 system (primal residual in double-float, dual in FP64)",
 }
 
 

@@ -83,9 +83,11 @@ typedef enum {
    MABD_FP64   every product in FP64.
    MABD_MIXED  chains: the unconstrained solve, the Jacobian products, the
                dual Gram blocks and the back-propagation in FP32; the polar
-               rotation, the rhs, the constraint values, the
-               prefactorization and the block cyclic reduction of the dual in
-               FP64; then refine_steps FP64 residual-correction sweeps
+               rotation and the rhs in double-float (pairs of FP32 numbers,
+               ~46 bits); the constraint values, the prefactorization and
+               the block cyclic reduction of the dual in FP64; then
+               refine_steps residual-correction sweeps (primal residual in
+               double-float, dual residual in FP64)
                (iterative refinement of the KKT system through the stored
                FP64 factors).  Graphs (PCG solver): every dual solve by FP32
                PCG, refined the same way.  Trees and the loop solver:

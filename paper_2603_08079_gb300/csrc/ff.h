@@ -133,15 +133,26 @@ MABD_FC ff ff_rcp(ff a) {
 // binary64 exponents e in 950..1140 (|x| in [2^-73, 2^118)); zeros keep
 // their sign.  Other values (tiny, huge, non-finite) take the conversion
 // instructions.
+// (kept out of line: inlined, the compiler may evaluate its conversions for
+// every value instead of branching around them)
+#ifdef __CUDA_ARCH__
+__device__ __noinline__
+#else
+inline
+#endif
+ff ff_from_rare(double x) {
+  const float h = (float)x;
+  const double r = x - (double)h;
+  return {h, r == r ? (float)r : 0.0f};  // infinities and NaN: l = 0
+}
+
 MABD_FC ff ff_from(double x) {
   const uint64_t u = fc_bits64(x);
   const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
   const uint32_t e = (hi >> 20) & 0x7ffu;
   if (e - 950u > 190u) {
     if ((u << 1) == 0) return {fc_float(hi), 0.0f};  // signed zero
-    const float h = (float)x;
-    const double r = x - (double)h;
-    return {h, r == r ? (float)r : 0.0f};  // infinities and NaN: l = 0
+    return ff_from_rare(x);
   }
   const uint32_t sign = hi & 0x80000000u;
   const float h = fc_float(sign | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));

@@ -164,6 +164,86 @@ __device__ __forceinline__ void gen_force(const DevJoints &J, const DevIncidence
   }
 }
 
+// gen_force for ball and hinge joints in double-float: g = diag4(R^T)
+// sum_k G_kj^T lam_k
+__device__ __forceinline__ void gen_force_ff(const DevJoints &J, const DevIncidence &I, int j,
+                                             const ff R[9], const double *lam, ff g[12]) {
+  const int K = J.K;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) g[i] = ff_make(0.0f);
+  auto add_point = [&](const ff F[3], const ff P[3], bool neg) {
+    ff f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      f[a] = ff_fma(R[a], F[0], ff_fma(R[3 + a], F[1], ff_mul(R[6 + a], F[2])));
+      if (neg) f[a] = ff_neg(f[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      g[a] = ff_fma(P[0], f[a], g[a]);
+      g[3 + a] = ff_fma(P[1], f[a], g[3 + a]);
+      g[6 + a] = ff_fma(P[2], f[a], g[6 + a]);
+      g[9 + a] = ff_add(g[9 + a], f[a]);
+    }
+  };
+  const int e0 = I.off[j], e1 = I.off[j + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int k = I.joint[e];
+    const int side = I.side[e];
+    const int type = J.type[k];
+    const double *p1 = side == 0 ? J.pa1 : J.pb1;
+    ff P1[3], l[5], F1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P1[a] = ff_from(__ldg(p1 + (size_t)a * K + k));
+#pragma unroll
+    for (int r = 0; r < 3; ++r) l[r] = ff_from(lam[(size_t)r * K + k]);
+    if (type == 0) {
+      F1[0] = l[0];
+      F1[1] = l[1];
+      F1[2] = l[2];
+      add_point(F1, P1, side == 1);
+    } else {
+      l[3] = ff_from(lam[(size_t)3 * K + k]);
+      l[4] = ff_from(lam[(size_t)4 * K + k]);
+      const double *p2 = side == 0 ? J.pa2 : J.pb2;
+      ff RH[9], F2[3], P2[3];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) RH[i] = ff_from(J.RH[(size_t)i * K + k]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        F1[a] = ff_fma(RH[a], l[0], ff_fma(RH[3 + a], l[1], ff_mul(RH[6 + a], l[2])));
+        F2[a] = ff_fma(RH[a], l[3], ff_mul(RH[6 + a], l[4]));
+        P2[a] = ff_from(__ldg(p2 + (size_t)a * K + k));
+      }
+      add_point(F1, P1, side == 1);
+      add_point(F2, P2, side == 1);
+    }
+  }
+}
+
+// hbar_apply in double-float
+__device__ __forceinline__ void hbar_apply_ff(const ff s[3], ff m, ff vmu, ff vlam, ff ih2, const ff x[12],
+                                              ff y[12]) {
+  const ff tr = ff_mul(vlam, ff_add(ff_add(x[0], x[4]), x[8]));
+  const ff v2 = ff{2.0f * vmu.h, 2.0f * vmu.l};
+  ff d[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) d[i] = ff_mul(s[i], ih2);
+  y[0] = ff_fma(ff_add(d[0], v2), x[0], tr);
+  y[4] = ff_fma(ff_add(d[1], v2), x[4], tr);
+  y[8] = ff_fma(ff_add(d[2], v2), x[8], tr);
+  y[1] = ff_fma(ff_add(d[0], vmu), x[1], ff_mul(vmu, x[3]));
+  y[3] = ff_fma(vmu, x[1], ff_mul(ff_add(d[1], vmu), x[3]));
+  y[2] = ff_fma(ff_add(d[0], vmu), x[2], ff_mul(vmu, x[6]));
+  y[6] = ff_fma(vmu, x[2], ff_mul(ff_add(d[2], vmu), x[6]));
+  y[5] = ff_fma(ff_add(d[1], vmu), x[5], ff_mul(vmu, x[7]));
+  y[7] = ff_fma(vmu, x[5], ff_mul(ff_add(d[2], vmu), x[7]));
+  const ff mt = ff_mul(m, ih2);
+  y[9] = ff_mul(mt, x[9]);
+  y[10] = ff_mul(mt, x[10]);
+  y[11] = ff_mul(mt, x[11]);
+}
+
 // world displacement of rest point p under the rest-frame increment x:
 // J(p) diag4(R) x = R (J(p) x)
 template <typename T>
@@ -220,9 +300,10 @@ __device__ __forceinline__ int polar3_ff(const ff A[9], ff R[9], int *iters) {
 
 // One thread per body: R = polar(A) and the rest-frame rhs
 // fbar = diag4(R^T)(M_A qdot/h + [0; m g]) - [V vec P(R^T A); 0]
-// (Sec. 3.3-3.4) in double-float arithmetic (ff.h: ~46 bits, the binary64
-// values of the state split exactly enough, R and fbar stored as binary64),
-// which keeps them off the FP64 unit; u = Hbar^{-1} fbar in FP32.
+// (Sec. 3.3-3.4) in double-float arithmetic (ff.h: ~46 bits; the binary64
+// state split with integer instructions; R stored as binary64 and as the
+// pair (Rf, Rlo), fbar as the pair (fbh, fbl)), which keeps them off the
+// FP64 unit; u = Hbar^{-1} fbar in FP32.
 __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p, int *status,
                                                       unsigned long long *iters) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -259,6 +340,7 @@ __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p,
   for (int i = 0; i < 9; ++i) {
     B.R[(size_t)i * M + j] = ff_to(R[i]);
     B.Rf[(size_t)i * M + j] = R[i].h;
+    B.Rlo[(size_t)i * M + j] = R[i].l;
   }
   if (fixed) return;  // no unknowns; its rotation may still orient a hinge
   ff qd[12];
@@ -306,7 +388,8 @@ __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p,
   load_hinvf(B, j, hf);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    B.fbar[(size_t)i * M + j] = ff_to(fb[i]);
+    B.fbh[(size_t)i * M + j] = fb[i].h;
+    B.fbl[(size_t)i * M + j] = fb[i].l;
     ff32[i] = fb[i].h;
   }
   hinv_apply_t(hf, ff32, u);
@@ -485,8 +568,9 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
 // One thread per body, start of a correction sweep.  First chain sweep:
 // dqb = u - Hbar^{-1} g(lambda) in FP32 (back-propagation of the approximate
 // solve); later chain sweeps: dqb += z - Hbar^{-1} g(dlambda) (the previous
-// correction); tree: dqb as the elimination left it.  Then the FP64 primal residual
-// rb = fbar - Hbar dqb - g(lambda) and the correction's unconstrained solve
+// correction); tree: dqb as the elimination left it.  Then the primal residual
+// rb = fbar - Hbar dqb - g(lambda) in double-float (the FP64 system's
+// residual to ~46 bits) and the correction's unconstrained solve
 // z = Hbar^{-1} rb in FP32 (kept in ubf).
 template <int MODE, bool XJ>
 __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, DevIncidence I,
@@ -496,39 +580,56 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
   const int j = ordered(B.order, t);
   if (B.fixed[j]) return;
   const int M = B.M;
-  double R[9], g64[12], dq[12];
-  load_R(B.R, M, j, R);
   float hf[16], uf[12], w[12], gf[12];
   load_hinvf(B, j, hf);
 #pragma unroll
   for (int i = 0; i < 12; ++i) uf[i] = B.ubf[(size_t)i * M + j];
-  gen_force<double, XJ>(J, I, j, R, J.lambda, g64);
+  ff R[9], g[12], dq[12];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = ff{B.Rf[(size_t)i * M + j], B.Rlo[(size_t)i * M + j]};
+  if (XJ) {
+    // universal and prismatic joints: the FP64 generalized force
+    double Rd[9], g64[12];
+    load_R(B.R, M, j, Rd);
+    gen_force<double, XJ>(J, I, j, Rd, J.lambda, g64);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) g[i] = ff_from(g64[i]);
+  } else {
+    gen_force_ff(J, I, j, R, J.lambda, g);
+  }
   if (MODE == MX_FROM_U) {
 #pragma unroll
-    for (int i = 0; i < 12; ++i) gf[i] = d2f(g64[i]);
+    for (int i = 0; i < 12; ++i) gf[i] = g[i].h;
     hinv_apply_t(hf, gf, w);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) dq[i] = f2d(uf[i] - w[i]);
+    for (int i = 0; i < 12; ++i) dq[i] = ff_make(uf[i] - w[i]);
   } else if (MODE == MX_FROM_CORRECTION) {
     float Rf[9];
     load_Rf(B, j, Rf);
     gen_force<float, XJ>(J, I, j, Rf, J.dlam, gf);
     hinv_apply_t(hf, gf, w);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) dq[i] = B.dqb[(size_t)i * M + j] + f2d(uf[i] - w[i]);
+    for (int i = 0; i < 12; ++i) dq[i] = ff_add(ff_from(B.dqb[(size_t)i * M + j]), ff_make(uf[i] - w[i]));
   } else {
-    load12(B.dqb, M, j, dq);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) dq[i] = ff_from(B.dqb[(size_t)i * M + j]);
   }
-  const double s[3] = {ldg(B.sig + j), ldg(B.sig + M + j), ldg(B.sig + 2 * (size_t)M + j)};
-  double hq[12];
-  hbar_apply(s, ldg(B.mass + j), ldg(B.vmu + j), ldg(B.vlam + j), p.inv_h * p.inv_h, dq, hq);
+  const ff s[3] = {ff_from(ldg(B.sig + j)), ff_from(ldg(B.sig + M + j)), ff_from(ldg(B.sig + 2 * (size_t)M + j))};
+  const ff ih = ff_from(p.inv_h);
+  ff hq[12];
+  hbar_apply_ff(s, ff_from(ldg(B.mass + j)), ff_from(ldg(B.vmu + j)), ff_from(ldg(B.vlam + j)), ff_mul(ih, ih),
+                dq, hq);
   float rf[12], z[12];
 #pragma unroll
-  for (int i = 0; i < 12; ++i) rf[i] = d2f(B.fbar[(size_t)i * M + j] - hq[i] - g64[i]);
+  for (int i = 0; i < 12; ++i) {
+    const ff fb = ff{B.fbh[(size_t)i * M + j], B.fbl[(size_t)i * M + j]};
+    rf[i] = ff_sub(ff_sub(fb, hq[i]), g[i]).h;
+  }
   hinv_apply_t(hf, rf, z);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    if (MODE != MX_FROM_DQB) B.dqb[(size_t)i * M + j] = dq[i];
+    if (MODE == MX_FROM_U) B.dqb[(size_t)i * M + j] = f2d(dq[i].h);
+    else if (MODE == MX_FROM_CORRECTION) B.dqb[(size_t)i * M + j] = ff_to(dq[i]);
     B.ubf[(size_t)i * M + j] = z[i];
   }
 }

@@ -1135,7 +1135,9 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   const int npf = has_prism ? 6 : 4;
   if (mixed) {
     dhinvf = dnew<float>(ctx, HINV_N * (size_t)Mx, ok);
-    B.fbar = dnew<double>(ctx, 12 * (size_t)Mx, ok);
+    B.fbh = dnew<float>(ctx, 12 * (size_t)Mx, ok);
+    B.fbl = dnew<float>(ctx, 12 * (size_t)Mx, ok);
+    B.Rlo = dnew<float>(ctx, 9 * (size_t)Mx, ok);
     B.dqb = dnew<double>(ctx, 12 * (size_t)Mx, ok);
     B.ubf = dnew<float>(ctx, 12 * (size_t)Mx, ok);
     B.Rf = dnew<float>(ctx, 9 * (size_t)Mx, ok);

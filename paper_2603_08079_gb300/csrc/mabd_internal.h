@@ -42,10 +42,11 @@ struct DevBodies {
   double *ubar;         // [12][M] unconstrained solve in the rest frame
   // mixed-precision form only (null otherwise)
   const float *hinvf;   // [16][M] structured Hbar^{-1} rounded to FP32
-  double *fbar;         // [12][M] rest-frame rhs of the step (FP64)
+  float *fbh, *fbl;     // [12][M] rest-frame rhs of the step, double-float (high, low parts)
   double *dqb;          // [12][M] rest-frame increment diag4(R^T) dq (FP64 accumulator)
   float *ubf;           // [12][M] FP32 Hbar^{-1} of the current rhs (u, then each correction)
   float *Rf;            // [9][M]  R rounded to FP32 (written with R)
+  float *Rlo;           // [9][M]  R - Rf: R as a double-float pair (Rf, Rlo)
   // processing order of the per-body kernels that visit joints: thread t
   // handles body order[t] (null: body t); see CHUNK_ORDER
   const int32_t *order;
