@@ -313,6 +313,24 @@ def cr_back_bytes(jtype_chain: np.ndarray, elem: int) -> float:
     return total
 
 
+def mx_res_body_bytes(jtype: np.ndarray, M: int) -> float:
+    """Algorithmic HBM bytes of one k_mx_res_body launch (the mixed forms'
+    primal residual, first sweep, ball and hinge joints), every datum counted
+    once.  Per body: R as an FP32 pair (72), FP32 Hbar^{-1} (64), the FP32
+    solve u (48), fbar as an FP32 pair (96), the FP64 constants sigma, m,
+    V mu, V lambda (48), incidence offset (4) read; dqb (FP64, 96) and the
+    FP32 correction solve (48) written.  Per joint: its type (1), multipliers
+    (8 per row), both anchors (48); a hinge also its frame (72) and second
+    points (48).  Per incidence entry: joint index and side (5)."""
+    jt = np.asarray(jtype)
+    hinge = int(np.sum(jt == 1))
+    ball = len(jt) - hinge
+    per_body = 72 + 64 + 48 + 96 + 48 + 4 + 96 + 48
+    per_ball = 1 + 24 + 48
+    per_hinge = 1 + 40 + 48 + 72 + 48
+    return float(M * per_body + ball * per_ball + hinge * per_hinge + 2 * len(jt) * 5)
+
+
 def chain_gram_flops(jtype_chain: np.ndarray) -> float:
     """FP64 flops of the per-body Gram blocks (FMA = 2).  Rows are grouped by
     point; a block is E^T Mbar(p, p') E' with the 3x3 point compliance Mbar
@@ -328,11 +346,13 @@ def chain_gram_flops(jtype_chain: np.ndarray) -> float:
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
-# kernel, from one ncu capture of the current kernel on the named workload;
-# an entry is removed when its kernel changes.  mx_body_prep: one launch on
-# the 524,288-body chain (147.4 + 87.5 MB), scaled to 1,048,576 bodies (the
-# kernel's traffic is per body; profiles/chain512k_mixed_fp32_dual_kernels.md).
-TRAFFIC: dict = {("chain1m", "mixed_fp32_dual", "mx_body_prep"): 469.8e6}
+# kernel (averaged over its launches in one step), from one ncu capture of the
+# current kernel on the named workload; an entry is removed when its kernel
+# changes.  profiles/chain1m_mx_res_body_cr_back_dram.md: one step of the 1M
+# chain, k_mx_res_body (1 launch: 583.1 + 125.3 MB) and the 24 back-substitution
+# launches (k_cr_back_pair + k_cr_back_w: 453.8 + 72.6 MB in all).
+TRAFFIC: dict = {("chain1m", "mixed_fp32_dual", "mx_res_body"): 708.4e6,
+                 ("chain1m", "mixed_fp32_dual", "cr_back"): 21.93e6}
 
 
 def measured_hbm_gbs() -> float:
@@ -358,16 +378,18 @@ def body_prep_flops(M: int, polar_iters: float, form: str) -> float:
 def kernel_model(name: str, jtype_chain: np.ndarray, form: str = "fp64", polar_iters: float | None = None):
     """(bound, algorithmic work of one step's launches of `name`): FP64 flops
     ("alu") or HBM bytes ("hbm"), or None without a model."""
-    if name in ("body_prep", "mx_body_prep") and polar_iters is not None:
+    if name == "body_prep" and polar_iters is not None:
         return "alu", body_prep_flops(len(jtype_chain) - 1, polar_iters, form)
+    # mx_body_prep computes in double-float on the FP32 pipe: no FP64-flop model
     if form != "mixed_fp32_dual" and (name.startswith("cr_reduce") or name == "cr_level"):
         return "alu", cr_reduce_flops(jtype_chain)
     if name == "chain_gram":
         return "alu", chain_gram_flops(jtype_chain)
+    if name == "mx_res_body" and form != "fp64":
+        return "hbm", mx_res_body_bytes(jtype_chain, len(jtype_chain) - 1)
     if name == "cr_back":
         passes = 1 if form == "fp64" else 2   # factorization + the correction sweep's pass
         return "hbm", passes * cr_back_bytes(jtype_chain, 4 if form == "mixed_fp32_dual" else 8)
-    return None
     return None
 
 

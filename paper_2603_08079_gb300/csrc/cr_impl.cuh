@@ -475,10 +475,18 @@ __device__ __forceinline__ void cr_back_one(CRLevelT<T> cur, CRLevelT<T> next, D
   }
 }
 
+// Back-substitution of one level with one thread per row pair: even row 2m
+// (a copy from the next level) and odd row 2m+1 (the solve).  With a thread
+// per row the odd and even lanes of a warp diverge and each path runs with
+// half the lanes; here every lane solves, and the factor loads of a warp
+// cover 32 consecutive m.
 template <typename T>
-__global__ void __launch_bounds__(128) k_cr_back(CRLevelT<T> cur, CRLevelT<T> next, DevChain C, DevJoints J,
-                                                 int level, double *acc) {
-  cr_back_one<T>(cur, next, C, J, level, acc, blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(128) k_cr_back_pair(CRLevelT<T> cur, CRLevelT<T> next, DevChain C,
+                                                      DevJoints J, int level, double *acc) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * m >= cur.N) return;
+  cr_back_one<T>(cur, next, C, J, level, acc, 2 * m);
+  cr_back_one<T>(cur, next, C, J, level, acc, 2 * m + 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -250,7 +250,7 @@ void launch_cr_back(const DevChain &C, const DevJoints &J, const CRLevelT<T> &cu
     k_cr_back_w<T><<<(rows + 3) / 4, 128, 0, s>>>(cur, next, C, J, level, acc);
     return;
   }
-  k_cr_back<T><<<nblk(cur.N, 128), 128, 0, s>>>(cur, next, C, J, level, acc);
+  k_cr_back_pair<T><<<nblk((cur.N + 1) / 2, 128), 128, 0, s>>>(cur, next, C, J, level, acc);
 }
 
 template <typename T>
