@@ -18,19 +18,22 @@ __device__ __forceinline__ int pk5(int r, int c) { return r >= c ? r * (r + 1) /
 
 // rows of joint k on one of its free bodies, with that body's Hbar^{-1}
 // applied: W[r] = [p;1] (x) s R^T d_r and Z[r] = Hbar^{-1} W[r]
+template <bool XJ>
 __device__ __forceinline__ int joint_side_rows(const DevBodies &B, const DevJoints &J, int k, int side,
                                                double W[5][12]) {
   const int j = side == 0 ? J.ja[k] : J.jb[k];
-  double R[9], E[5][3], P[3][3], wt[3];
-  int pt[5];
+  double R[9], E[5][3], PR[5][3], WR[5];
   load_R(B.R, B.M, j, R);
-  const int C = joint_rows_rest(J, k, side, R, E, P, pt, wt);
-  for (int r = 0; r < C; ++r) kron_row_w(P[pt[r]], wt[pt[r]], E[r], W[r]);
+  const int C = joint_rows_pt<double, XJ>(J, k, side, R, E, PR, WR);
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+    if (r < C) kron_row_w(PR[r], WR[r], E[r], W[r]);
   return C;
 }
 
 // per joint: D_k = sum_j G_kj H_j^{-1} G_kj^T, its Cholesky factor, and the
 // start of the iteration: lambda = 0, r = b, z = D^{-1} r, p = 0, rz = r.z
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_pcg_setup(DevBodies B, DevJoints J, DevPCG P, int *status) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int K = J.K;
@@ -45,7 +48,7 @@ __global__ void __launch_bounds__(128) k_pcg_setup(DevBodies B, DevJoints J, Dev
       if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
       const int j = side == 0 ? J.ja[k] : J.jb[k];
       double W[5][12], h[16];
-      joint_side_rows(B, J, k, side, W);
+      joint_side_rows<XJ>(B, J, k, side, W);
       load_hinv(B, j, h);
       for (int t = 0; t < C; ++t) {
         double z[12];
@@ -155,6 +158,7 @@ __global__ void k_pcg_setup_reduce(DevPCG P, double rtol) {
 }
 
 // per body: zb_j = Hbar^{-1} sum_rows p_r W_r with p = z + beta p_old
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_pcg_body(DevBodies B, DevJoints J, DevIncidence I, DevPCG P) {
   if (P.iter[1]) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -167,13 +171,14 @@ __global__ void __launch_bounds__(128) k_pcg_body(DevBodies B, DevJoints J, DevI
   for (int a = 0; a < 12; ++a) g[a] = 0.0;
   for (int e = I.off[j]; e < I.off[j + 1]; ++e) {
     const int k = I.joint[e];
-    double E[5][3], Pt[3][3], wt[3];
-    int pt[5];
-    const int C = joint_rows_rest(J, k, I.side[e], R, E, Pt, pt, wt);
-    for (int r = 0; r < C; ++r) {
+    double E[5][3], PR[5][3], WR[5];
+    const int C = joint_rows_pt<double, XJ>(J, k, I.side[e], R, E, PR, WR);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      if (r >= C) break;
       const double pr = P.z[(size_t)r * K + k] + beta * P.p[(size_t)r * K + k];
-      const double *pp = Pt[pt[r]];
-      const double w = wt[pt[r]];
+      const double *pp = PR[r];
+      const double w = WR[r];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double v = pr * E[r][a];
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(128) k_pcg_body(DevBodies B, DevJoints J, DevI
 }
 
 // per joint: p = z + beta p_old (stored), Sp = sum_bodies W zb, partial p.Sp
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_pcg_joint_sp(DevBodies B, DevJoints J, DevPCG P) {
   if (P.iter[1]) return;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,9 +216,11 @@ __global__ void __launch_bounds__(128) k_pcg_joint_sp(DevBodies B, DevJoints J, 
       if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
       const int j = side == 0 ? J.ja[k] : J.jb[k];
       double W[5][12], zb[12];
-      joint_side_rows(B, J, k, side, W);
+      joint_side_rows<XJ>(B, J, k, side, W);
       load12(P.zb, B.M, j, zb);
-      for (int r = 0; r < C; ++r) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        if (r >= C) break;
         double v = 0.0;
 #pragma unroll
         for (int a = 0; a < 12; ++a) v += W[r][a] * zb[a];
@@ -314,14 +322,20 @@ __global__ void k_pcg_beta(DevPCG P, int max_iters) {
 
 void launch_pcg_setup(const DevBodies &B, const DevJoints &J, const DevPCG &P, double rtol,
                       int *status, cudaStream_t s) {
-  k_pcg_setup<<<P.nblocks, 128, 0, s>>>(B, J, P, status);
+  if (J.xj) k_pcg_setup<true><<<P.nblocks, 128, 0, s>>>(B, J, P, status);
+  else k_pcg_setup<false><<<P.nblocks, 128, 0, s>>>(B, J, P, status);
   k_pcg_setup_reduce<<<1, PCG_THREADS, 0, s>>>(P, rtol);
 }
 
 void launch_pcg_iteration(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
                           const DevPCG &P, int max_iters, cudaStream_t s) {
-  k_pcg_body<<<(B.M + 127) / 128, 128, 0, s>>>(B, J, I, P);
-  k_pcg_joint_sp<<<P.nblocks, 128, 0, s>>>(B, J, P);
+  if (J.xj) {
+    k_pcg_body<true><<<(B.M + 127) / 128, 128, 0, s>>>(B, J, I, P);
+    k_pcg_joint_sp<true><<<P.nblocks, 128, 0, s>>>(B, J, P);
+  } else {
+    k_pcg_body<false><<<(B.M + 127) / 128, 128, 0, s>>>(B, J, I, P);
+    k_pcg_joint_sp<false><<<P.nblocks, 128, 0, s>>>(B, J, P);
+  }
   k_pcg_alpha<<<1, PCG_THREADS, 0, s>>>(P);
   k_pcg_joint_update<<<P.nblocks, 128, 0, s>>>(J, P);
   k_pcg_beta<<<1, PCG_THREADS, 0, s>>>(P, max_iters);

@@ -81,6 +81,7 @@ __device__ __forceinline__ void block_sum2_32(const double *part, int n, int nb,
 }
 
 // per joint: D_k in FP32, its Cholesky factor; x = 0, r = rhs, z = D^{-1} r, p = 0
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_p32_setup(DevBodies B, DevJoints J, DevPCG32 P,
                                                    const double *rhs, int *status) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,25 +96,29 @@ __global__ void __launch_bounds__(128) k_p32_setup(DevBodies B, DevJoints J, Dev
     for (int side = 0; side < 2; ++side) {
       if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
       const int j = side == 0 ? J.ja[k] : J.jb[k];
-      float R[9], h[16], E[5][3], Pt[3][3], wt[3];
-      int pt[5];
+      float R[9], h[16], E[5][3], PR[5][3], WR[5];
       load_Rf(B, j, R);
       load_hf(B, j, h);
-      rows_rest_f(J, k, side, R, E, Pt, pt, wt);
+      rows_pt_f<XJ>(J, k, side, R, E, PR, WR);
       float W[5][12], Z[5][12];
-      for (int r = 0; r < C; ++r) {
-        const float *pp = Pt[pt[r]];
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        if (r >= C) break;
+        const float *pp = PR[r];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           W[r][a] = pp[0] * E[r][a];
           W[r][3 + a] = pp[1] * E[r][a];
           W[r][6 + a] = pp[2] * E[r][a];
-          W[r][9 + a] = wt[pt[r]] * E[r][a];
+          W[r][9 + a] = WR[r] * E[r][a];
         }
         hinvf_apply(h, W[r], Z[r]);
       }
-      for (int r = 0; r < C; ++r)
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
         for (int t = 0; t <= r; ++t) {
+          if (r >= C) continue;
           float v = 0.f;
 #pragma unroll
           for (int a = 0; a < 12; ++a) v += W[r][a] * Z[t][a];
@@ -185,6 +190,7 @@ __global__ void k_p32_setup_reduce(DevPCG32 P, double rtol) {
 }
 
 // per body: zb_j = Hbar^{-1} sum_rows p_r W_r with p = z + beta p_old
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_p32_body(DevBodies B, DevJoints J, DevIncidence I, DevPCG32 P) {
   if (P.iter[1]) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,13 +203,14 @@ __global__ void __launch_bounds__(128) k_p32_body(DevBodies B, DevJoints J, DevI
   for (int a = 0; a < 12; ++a) g[a] = 0.f;
   for (int e = I.off[j]; e < I.off[j + 1]; ++e) {
     const int k = I.joint[e];
-    float E[5][3], Pt[3][3], wt[3];
-    int pt[5];
-    const int C = rows_rest_f(J, k, I.side[e], R, E, Pt, pt, wt);
-    for (int r = 0; r < C; ++r) {
+    float E[5][3], PR[5][3], WR[5];
+    const int C = rows_pt_f<XJ>(J, k, I.side[e], R, E, PR, WR);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      if (r >= C) break;
       const float pr = P.z[(size_t)r * K + k] + beta * P.p[(size_t)r * K + k];
-      const float *pp = Pt[pt[r]];
-      const float w = wt[pt[r]];
+      const float *pp = PR[r];
+      const float w = WR[r];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const float v = pr * E[r][a];
@@ -222,6 +229,7 @@ __global__ void __launch_bounds__(128) k_p32_body(DevBodies B, DevJoints J, DevI
 }
 
 // per joint: p = z + beta p_old (stored), Sp = sum_bodies W zb, partial p.Sp
+template <bool XJ>
 __global__ void __launch_bounds__(128) k_p32_joint_sp(DevBodies B, DevJoints J, DevPCG32 P) {
   if (P.iter[1]) return;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -240,15 +248,16 @@ __global__ void __launch_bounds__(128) k_p32_joint_sp(DevBodies B, DevJoints J, 
     for (int side = 0; side < 2; ++side) {
       if (!(fl & (side == 0 ? JF_A_FREE : JF_B_FREE))) continue;
       const int j = side == 0 ? J.ja[k] : J.jb[k];
-      float R[9], E[5][3], Pt[3][3], zb[12], wt[3];
-      int pt[5];
+      float R[9], E[5][3], PR[5][3], zb[12], WR[5];
       load_Rf(B, j, R);
-      rows_rest_f(J, k, side, R, E, Pt, pt, wt);
+      rows_pt_f<XJ>(J, k, side, R, E, PR, WR);
 #pragma unroll
       for (int a = 0; a < 12; ++a) zb[a] = P.zb[(size_t)a * B.M + j];
-      for (int r = 0; r < C; ++r) {
-        const float *pp = Pt[pt[r]];
-        const float w = wt[pt[r]];
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        if (r >= C) break;
+        const float *pp = PR[r];
+        const float w = WR[r];
         float v = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -342,7 +351,8 @@ __global__ void __launch_bounds__(128) k_p32_finish(DevJoints J, DevPCG32 P, dou
 
 void launch_p32_setup(const DevBodies &B, const DevJoints &J, const DevPCG32 &P, const double *rhs,
                       double rtol, int *status, cudaStream_t s, const LpcGraph *lg, const LpcAct *la) {
-  k_p32_setup<<<P.nblocks, 128, 0, s>>>(B, J, P, rhs, status);
+  if (J.xj) k_p32_setup<true><<<P.nblocks, 128, 0, s>>>(B, J, P, rhs, status);
+  else k_p32_setup<false><<<P.nblocks, 128, 0, s>>>(B, J, P, rhs, status);
   if (P.t) launch_lpc_apply(*lg, *la, P.t, P.y, P.r, P.z, P.part, P.nblocks, s, nullptr);
   k_p32_setup_reduce<<<1, P32_THREADS, 0, s>>>(P, rtol);
 }
@@ -350,8 +360,13 @@ void launch_p32_setup(const DevBodies &B, const DevJoints &J, const DevPCG32 &P,
 void launch_p32_iteration(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
                           const DevPCG32 &P, int max_iters, cudaStream_t s, const LpcGraph *lg,
                           const LpcAct *la) {
-  k_p32_body<<<(B.M + 127) / 128, 128, 0, s>>>(B, J, I, P);
-  k_p32_joint_sp<<<P.nblocks, 128, 0, s>>>(B, J, P);
+  if (J.xj) {
+    k_p32_body<true><<<(B.M + 127) / 128, 128, 0, s>>>(B, J, I, P);
+    k_p32_joint_sp<true><<<P.nblocks, 128, 0, s>>>(B, J, P);
+  } else {
+    k_p32_body<false><<<(B.M + 127) / 128, 128, 0, s>>>(B, J, I, P);
+    k_p32_joint_sp<false><<<P.nblocks, 128, 0, s>>>(B, J, P);
+  }
   k_p32_alpha<<<1, P32_THREADS, 0, s>>>(P);
   k_p32_joint_update<<<P.nblocks, 128, 0, s>>>(J, P);
   if (P.t) launch_lpc_apply(*lg, *la, P.t, P.y, P.r, P.z, P.part, P.nblocks, s, P.iter);

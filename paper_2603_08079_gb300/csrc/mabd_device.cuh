@@ -139,19 +139,13 @@ __device__ __forceinline__ void row_dir(int type, const S RH[9], int r, S d[3]) 
     d[0] = r == 0 ? S(1) : S(0);
     d[1] = r == 1 ? S(1) : S(0);
     d[2] = r == 2 ? S(1) : S(0);
-  } else if (type == 3) {
-    // prismatic (R_P in RH): rows x, z, x, z, z
-    const int rr = (r == 0 || r == 2) ? 0 : 2;
-    d[0] = RH[3 * rr];
-    d[1] = RH[3 * rr + 1];
-    d[2] = RH[3 * rr + 2];
   } else {
     // hinge: rows 3, 4 are R_H's x and z rows; universal (R_U in RH): row 3
-    // is its a1 row
-    int rr = r < 3 ? r : (type == 2 ? 1 : (r == 3 ? 0 : 2));
-    d[0] = RH[3 * rr];
-    d[1] = RH[3 * rr + 1];
-    d[2] = RH[3 * rr + 2];
+    // is its a1 row; prismatic (R_P in RH): rows x, z, x, z, z
+    const int rr = type == 3 ? ((r == 0 || r == 2) ? 0 : 2) : (r < 3 ? r : (type == 2 ? 1 : (r == 3 ? 0 : 2)));
+    // selects, not RH[3 * rr]: a run-time index would put RH in local memory
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = rr == 0 ? RH[a] : (rr == 1 ? RH[3 + a] : RH[6 + a]);
   }
 }
 
@@ -203,8 +197,9 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // frame (frozen frame, Eq. pcpq), s = +1 on a and -1 on b, p the row's point
 // and w its translation weight (0 for a point difference).  Writes the
 // directions E[r], the points P[0..NP-1], their weights and the point index
-// pt[r]; returns C.  NP = 3 holds the prismatic joint's third point pair;
-// the solvers that take only ball and hinge joints pass NP = 2.
+// pt[r]; returns C.  NP = 3 holds the prismatic joint's third point pair
+// (universal and prismatic joints need it); the solvers and scenes with
+// only ball and hinge joints pass NP = 2.
 template <typename S, int NP>
 __device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int side, const S R[9],
                                                S E[5][3], S (&P)[NP][3], int pt[5], S (&wgt)[NP]) {
@@ -220,21 +215,32 @@ __device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int si
 #pragma unroll
     for (int i = 0; i < 9; ++i) RH[i] = JP<S>::RH(J)[(size_t)i * K + k];
   }
-  if (NP > 2 && type == 3) load3(JP<S>::p3(J, side), K, k, P[NP > 2 ? 2 : 0]);
+  if (NP > 2) {
+    if (type == 3) {
+      load3(JP<S>::p3(J, side), K, k, P[NP > 2 ? 2 : 0]);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) P[NP > 2 ? 2 : 0][a] = S(0);
+    }
+  }
   const int C = joint_nrows(type);
-  for (int r = 0; r < C; ++r) {
+  // unrolled over the five possible rows, so that E and pt stay in registers
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    if (r >= C) break;
     S d[3], e[3];
-    row_dir(type, RH, r, d);
+    // two point slots: only ball and hinge joints reach here
+    row_dir(NP > 2 ? type : (type == 0 ? 0 : 1), RH, r, d);
     mtv3(R, d, e);
     // the universal joint's row 3: + a1 (x) [l a2; 0] on beta (a point
     // difference: weight 0 on the translation), nothing on alpha
-    const S s = (type == 2 && r == 3) ? (side == 0 ? S(0) : S(1)) : sgn;
+    const S s = (NP > 2 && type == 2 && r == 3) ? (side == 0 ? S(0) : S(1)) : sgn;
     E[r][0] = s * e[0];
     E[r][1] = s * e[1];
     E[r][2] = s * e[2];
-    pt[r] = type == 3 ? (r >> 1) : (r < 3 ? 0 : 1);
+    pt[r] = (NP > 2 && type == 3) ? (r >> 1) : (r < 3 ? 0 : 1);
   }
-  if (type == 2) wgt[1] = S(0);
+  if (NP > 2 && type == 2) wgt[1] = S(0);
   return C;
 }
 
@@ -243,6 +249,28 @@ __device__ __forceinline__ int joint_rows_rest(const DevJoints &J, int k, int si
                                                S E[5][3], S (&P)[NP][3], int pt[5]) {
   S wgt[NP];
   return joint_rows_rest(J, k, side, R, E, P, pt, wgt);
+}
+
+// The rows with each row's own point PR[r] and translation weight WR[r]
+// (every joint type, three point slots).  The point of a row is picked with
+// selects on registers: indexing a 3-point array with a run-time row index
+// would put the array in local memory.
+// XJ: the scene may hold prismatic joints (three point slots); without, two.
+template <typename S, bool XJ = true>
+__device__ __forceinline__ int joint_rows_pt(const DevJoints &J, int k, int side, const S R[9], S E[5][3],
+                                             S PR[5][3], S WR[5]) {
+  constexpr int NP = XJ ? 3 : 2;
+  S P[NP][3], wt[NP];
+  int pt[5] = {0, 0, 0, 0, 0};
+  const int C = joint_rows_rest<S, NP>(J, k, side, R, E, P, pt, wt);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int q = pt[r];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) PR[r][a] = q == 0 ? P[0][a] : (q == 1 || NP == 2 ? P[1][a] : P[NP - 1][a]);
+    WR[r] = q == 0 ? wt[0] : (q == 1 || NP == 2 ? wt[1] : wt[NP - 1]);
+  }
+  return C;
 }
 
 // Sec. 4.5 prismatic joint frame R_P = [x~; y~; z~] (rows), frozen at q_n and

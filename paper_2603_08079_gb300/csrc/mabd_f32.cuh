@@ -38,12 +38,13 @@ __device__ __forceinline__ void load3f(const float *p, int N, int k, float out[3
 }
 
 // rows of joint k on its side `side` (body with FP32 rotation R), from the
-// FP32 copies of the joint points and frame: joint_rows_rest<float>; wt[]
-// are the points' translation weights (0 for the universal joint's point
-// difference)
-__device__ __forceinline__ int rows_rest_f(const DevJoints &J, int k, int side, const float R[9],
-                                           float E[5][3], float (&P)[3][3], int pt[5], float (&wt)[3]) {
-  return joint_rows_rest<float, 3>(J, k, side, R, E, P, pt, wt);
+// FP32 copies of the joint points and frame: joint_rows_pt<float>; PR[r] and
+// WR[r] are row r's point and its translation weight (0 for the universal
+// joint's point difference)
+template <bool XJ>
+__device__ __forceinline__ int rows_pt_f(const DevJoints &J, int k, int side, const float R[9],
+                                         float E[5][3], float PR[5][3], float WR[5]) {
+  return joint_rows_pt<float, XJ>(J, k, side, R, E, PR, WR);
 }
 
 }  // namespace mabd
