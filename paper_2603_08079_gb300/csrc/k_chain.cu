@@ -75,7 +75,11 @@ __device__ __forceinline__ void chain_gram_body(const DevBodies &B, const DevJoi
   // per slot: directions E (rest frame, columns = rows' directions), points
   T E[2][3][3], P[2][2][3];
   int kk[2], ty[2];
-  for (int s = 0; s < n; ++s) {
+  // the slot loops run over both slots (unrolled), so that E and P stay in
+  // registers; a run-time slot index would put them in local memory
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    if (s >= n) break;
     const int k = I.joint[e0 + s];
     const int side = I.side[e0 + s];
     const int type = J.type[k];
@@ -109,7 +113,9 @@ __device__ __forceinline__ void chain_gram_body(const DevBodies &B, const DevJoi
   const int c012[3] = {0, 1, 2}, c02[3] = {0, 2, 0};
   T Mb[3][3], blk[3][3];
   // self blocks of each joint -> its slot (lower body: Dfirst, upper: Dsecond)
-  for (int s = 0; s < n; ++s) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    if (s >= n) break;
     OT *dst = const_cast<OT *>(C.islot[e0 + s] == 0 ? CRS<OT>::Df(C) : CRS<OT>::Ds(C));
     const int k = kk[s];
     OT Dp[15];

@@ -304,7 +304,7 @@ __device__ __forceinline__ int polar3_ff(const ff A[9], ff R[9], int *iters) {
 // state split with integer instructions; R stored as binary64 and as the
 // pair (Rf, Rlo), fbar as the pair (fbh, fbl)), which keeps them off the
 // FP64 unit; u = Hbar^{-1} fbar in FP32.
-__global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p, int *status,
+__global__ void __launch_bounds__(128, 5) k_mx_body_prep(DevBodies B, StepParams p, int *status,
                                                       unsigned long long *iters) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= B.M) return;
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(128) k_mx_body_prep(DevBodies B, StepParams p,
 // universal / prismatic; hinge axis from body a with a_y >= 0),
 // b = G u + C(q_n) with G u in FP32.
 template <bool XJ>
-__global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J, StepParams p,
+__global__ void __launch_bounds__(128, 6) k_mx_joint_prep(DevBodies B, DevJoints J, StepParams p,
                                                        int *status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= J.K) return;
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(128) k_mx_joint_prep(DevBodies B, DevJoints J,
 // residual to ~46 bits) and the correction's unconstrained solve
 // z = Hbar^{-1} rb in FP32 (kept in ubf).
 template <int MODE, bool XJ>
-__global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, DevIncidence I,
+__global__ void __launch_bounds__(128, 5) k_mx_res_body(DevBodies B, DevJoints J, DevIncidence I,
                                                      StepParams p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= B.M) return;
@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(128) k_mx_res_body(DevBodies B, DevJoints J, D
 // largest |C + G dq| goes to *maxbit when it is given.  With the printed zero
 // bottom rhs (residual_rhs = 0) the constraint is G dq = 0 and C drops out.
 template <bool XJ>
-__global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, StepParams p,
+__global__ void __launch_bounds__(128, 6) k_mx_res_joint(DevBodies B, DevJoints J, StepParams p,
                                                       unsigned long long *maxbit, bool add_gz) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double worst = 0.0;
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(128) k_mx_res_joint(DevBodies B, DevJoints J, 
 // dqb as the eliminations left it.  Then dq = diag4(R) dqb, q += dq,
 // qdot = dq / h (implicit Euler, Sec. 3.4).
 template <bool XJ>
-__global__ void __launch_bounds__(128) k_mx_final(DevBodies B, DevJoints J, DevIncidence I,
+__global__ void __launch_bounds__(128, 6) k_mx_final(DevBodies B, DevJoints J, DevIncidence I,
                                                   StepParams p, int mode) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= B.M) return;
