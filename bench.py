@@ -349,10 +349,10 @@ def chain_gram_flops(jtype_chain: np.ndarray) -> float:
 # kernel (averaged over its launches in one step), from one ncu capture of the
 # current kernel on the named workload; an entry is removed when its kernel
 # changes.  profiles/chain1m_mx_res_body_cr_back_dram.md: one step of the 1M
-# chain, k_mx_res_body (1 launch: 583.1 + 125.3 MB) and the 24 back-substitution
-# launches (k_cr_back_pair + k_cr_back_w: 453.8 + 72.6 MB in all).
-TRAFFIC: dict = {("chain1m", "mixed_fp32_dual", "mx_res_body"): 708.4e6,
-                 ("chain1m", "mixed_fp32_dual", "cr_back"): 21.93e6}
+# chain, k_mx_res_body (1 launch: 584.2 + 142.0 MB) and the 24 back-substitution
+# launches (k_cr_back_pair + k_cr_back_w: 453.4 + 72.2 MB in all).
+TRAFFIC: dict = {("chain1m", "mixed_fp32_dual", "mx_res_body"): 726.2e6,
+                 ("chain1m", "mixed_fp32_dual", "cr_back"): 21.90e6}
 
 
 def measured_hbm_gbs() -> float:
