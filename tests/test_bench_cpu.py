@@ -38,3 +38,25 @@ def test_parallel_oracle_baseline_runs():
     from paper_2603_08079_gb300 import scenes
     assert bodies == len(scenes.assemblies(16, seed=3)["mass"])
     assert dt > 0 and cores >= 1
+
+
+def test_roofline_byte_models_by_hand():
+    """The algorithmic-bytes models behind the bench line's roofline, against
+    hand counts on tiny chains: the residual kernel (per body 476 B, per ball
+    joint 73 B, per hinge joint 209 B, 10 B of incidence per joint) and the
+    back-substitution of a 3-row chain of two levels."""
+    import bench
+    from paper_2603_08079_gb300 import scenes
+    jt = np.array([0, 1, 0, 1, 0])          # 4 bodies, ball/hinge alternating
+    assert bench.mx_res_body_bytes(jt, 4) == 4 * 476 + 3 * 73 + 2 * 209 + 5 * 10
+    assert list(scenes.joint_rows([0, 1, 2, 3])) == [3, 5, 4, 5]
+    # three ball rows: one level eliminates row 1 (neighbours 0 and 2) and
+    # keeps rows 0, 2; the next level eliminates row 1 of (0, 2) with only a
+    # left neighbour (FP32 records, level 0 writes FP64 multipliers)
+    # (the odd row reads its factor record n(n+1)/2 + n l + n r + n and its
+    # neighbours' l + r multipliers and writes n; each even row copies n)
+    balls = np.zeros(3, dtype=np.int64)
+    assert bench._cr_sizes(balls).tolist() == [3, 3, 3]
+    first = (6 + 9 + 9 + 3 + 3 + 3) * 4 + 3 * 8 + 2 * 3 * (4 + 8)
+    second = (6 + 9 + 0 + 3 + 3 + 0) * 4 + 3 * 4 + 1 * 3 * (4 + 4)
+    assert bench.cr_back_bytes(balls, 4) == first + second
