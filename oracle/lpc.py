@@ -29,9 +29,12 @@ with dense matrices (small systems only):
   (dL/dG = (D V^T + V D^T) G S~ with D = dL/dY, Y = X V; the GPU uses the
   sparse chain rule instead).
 
-Parity unpinned by the paper (there is nothing to pin it to there); the
-tests pin this module by finite differences of the loss, by the block-Jacobi
-special case and by the symmetry and definiteness of M^{-1}.
+The paper prints no values for this part (the network design is this
+project's reading); the tests pin this module against the mathematics
+instead: finite differences of the loss for every parameter, the
+block-Jacobi special case (zero heads and a closed gate leave G = I, so
+M^{-1} is the inverse of the diagonal blocks), and the symmetry and
+definiteness of M^{-1}.
 """
 from __future__ import annotations
 
