@@ -345,14 +345,51 @@ def chain_gram_flops(jtype_chain: np.ndarray) -> float:
     return 2.0 * float(fma.sum())
 
 
+def seg_bytes(name: str, jtype: np.ndarray, M: int) -> float | None:
+    """Algorithmic HBM bytes of one launch of a segment-tiled chain kernel
+    (the mixed form with the FP32 reduction), every datum counted once per
+    launch (a tile's halo bodies and re-reads of its own data hit L2).
+    Per body: q 96, qdot 96, the FP64 constants sigma, m, V mu, V lambda 48,
+    the FP32 Hbar^{-1} 64, R as an FP32 pair 72 (its high part alone 36),
+    the FP32 vectors u, fbar - Hbar u, dq0 and z 48 each.  Per joint: flags 1;
+    C(q_n) 40 (FP64); FP64 anchors 48, and for a hinge the second points 48,
+    axis 24 and frame as an FP32 pair 72 (high part 36); FP32 anchors 24 (a
+    hinge 48); the tile's factors 260 (65 FP32 per row: L, Ya, Yb); its
+    forward-eliminated rhs 20; the approximate multipliers 20 (FP32); the
+    multipliers 40 (FP64).
+      seg_body:  reads q, qdot, constants, Hbar^{-1}, the FP64 joint data;
+                 writes R, u, fbar - Hbar u, the frames and C;
+      seg_first: reads R (high), u, Hbar^{-1}, frames (high), C, FP32 anchors;
+                 writes the factors and the rhs;
+      seg_corr:  reads R, frames, Hbar^{-1}, constants, fbar - Hbar u, u, C,
+                 both anchor copies, the factors and the rhs; writes the
+                 approximate multipliers, dq0, z and the new rhs;
+      seg_final: reads R, frames (high), Hbar^{-1}, q, dq0, z, FP32
+                 anchors, the factors, the rhs and the approximate
+                 multipliers; writes q, qdot and the multipliers."""
+    jt = np.asarray(jtype)
+    K = len(jt)
+    hg = int(np.sum(jt == 1))
+    fp64_pts = 48 * K + 72 * hg
+    fp32_pts = 24 * K + 24 * hg
+    if name == "seg_body":
+        return float(M * (96 + 96 + 48 + 64) + fp64_pts + K + M * (72 + 48 + 48) + 72 * hg + 40 * K)
+    if name == "seg_first":
+        return float(M * (36 + 48 + 64) + 36 * hg + 40 * K + fp32_pts + K + 260 * K + 20 * K)
+    if name == "seg_corr":
+        return float(M * (72 + 64 + 48 + 48 + 48) + 72 * hg + 40 * K + fp64_pts + fp32_pts + K + 260 * K
+                     + 20 * K + M * (48 + 48) + 20 * K + 20 * K)
+    if name == "seg_final":
+        return float(M * (72 + 64 + 96 + 48 + 48) + 36 * hg + fp32_pts + K + 260 * K + 20 * K + 20 * K
+                     + M * (96 + 96) + 40 * K)
+    return None
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
-# kernel (averaged over its launches in one step), from one ncu capture of the
-# current kernel on the named workload; an entry is removed when its kernel
-# changes.  profiles/chain1m_mx_res_body_cr_back_dram.md: one step of the 1M
-# chain, k_mx_res_body (1 launch: 584.2 + 142.0 MB) and the 24 back-substitution
-# launches (k_cr_back_pair + k_cr_back_w: 453.4 + 72.2 MB in all).
-TRAFFIC: dict = {("chain1m", "mixed_fp32_dual", "mx_res_body"): 726.2e6,
-                 ("chain1m", "mixed_fp32_dual", "cr_back"): 21.90e6}
+# kernel, from one ncu capture of the current kernel (scaled to the named
+# workload by the bodies it processes where the capture ran a smaller chain);
+# an entry is removed when its kernel changes.
+TRAFFIC: dict = {}
 
 
 def measured_hbm_gbs() -> float:
@@ -387,6 +424,9 @@ def kernel_model(name: str, jtype_chain: np.ndarray, form: str = "fp64", polar_i
         return "alu", chain_gram_flops(jtype_chain)
     if name == "mx_res_body" and form != "fp64":
         return "hbm", mx_res_body_bytes(jtype_chain, len(jtype_chain) - 1)
+    if name.startswith("seg_") and form == "mixed_fp32_dual":
+        v = seg_bytes(name, jtype_chain, len(jtype_chain) - 1)
+        return ("hbm", v) if v is not None else None
     if name == "cr_back":
         passes = 1 if form == "fp64" else 2   # factorization + the correction sweep's pass
         return "hbm", passes * cr_back_bytes(jtype_chain, 4 if form == "mixed_fp32_dual" else 8)
@@ -484,17 +524,36 @@ def run_gpu(args):
         if form == "mixed_fp32_dual" and args.workload == "chain1m":
             variants.append(("mixed_fp64_reduction_gpu", dict(precision="mixed", refine_steps=args.refine),
                              None))
+            # the same form as the segment-tiled step (MABD_CHAIN_SEG=1)
+            variants.append(("mixed_fp32_dual_segment_tiled_gpu",
+                             dict(precision="mixed_fp32_dual", refine_steps=args.refine), "seg"))
         if learned is not None:
             variants.append(("mixed_block_jacobi_gpu", dict(precision="mixed", refine_steps=args.refine),
                              None))
         for key, kw, lp in variants:
-            ref = mabd.Solver(sc, pcg_max_iters=20000, **kw)
+            if lp == "seg":
+                os.environ["MABD_CHAIN_SEG"] = "1"
+            try:
+                ref = mabd.Solver(sc, pcg_max_iters=20000, **kw)
+            finally:
+                os.environ.pop("MABD_CHAIN_SEG", None)
             pms, _ = time_steps(ref, args.steps, args.warmup, barrier_sync)
+            extra = {}
+            if lp == "seg":
+                ref.profile(True)
+                ref.profile_reset()
+                ref.step(args.profile_steps)
+                skt = ref.kernel_times()
+                ref.profile(False)
+                extra = {"kernels_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in skt.items()},
+                         "launches_per_step": sum(n for _, n in skt.values()) / args.profile_steps,
+                         "seg_levels": ref.info()["seg_levels"]}
             rst = ref.step(1, stats=True)[0]
             ref.close()
             pms = max_over_ranks(pms)
             others[key] = {"value": job_value(ws, M, args.steps, pms), "unit": "body-steps/s",
                            "ms_per_step": pms / args.steps}
+            others[key].update(extra)
             if rst.get("pcg_iters"):
                 others[key]["pcg_iters_per_step"] = rst["pcg_iters"]
         plain = others.get("plain_fp64_gpu")

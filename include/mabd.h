@@ -190,6 +190,11 @@ typedef struct {
   int32_t cr_levels;       /* chain solver: levels of the block cyclic reduction (0 otherwise) */
   int32_t cr_tail_level;   /* chain solver: first level run by the single-CTA tail launch
                               (= cr_levels when every level has its own launches) */
+  int32_t seg_levels;      /* chain solver, MABD_MIXED_FP32_DUAL with one correction sweep and
+                              MABD_CHAIN_SEG=1 in the environment at mabd_prefactor: tile
+                              levels of the segment-tiled step (tiles of seg_tile joints, then
+                              of 256 rows); 0 when the level-by-level reduction runs */
+  int32_t seg_tile;        /* joints per tile of the first level of that reduction */
 } mabd_info;
 
 /* Fills *cfg with h = 1e-2, gravity (0,0,-9.8), FP64, AUTO, pcg_max_iters 2000,
@@ -246,10 +251,10 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
    For callers that cannot call cudaMalloc -- code running inside another
    framework that owns the device allocator, or under a fixed memory budget:
    one implicit step of a single chain of at most MABD_NOALLOC_MAX_BODIES
-   bodies, computed by the same kernels as mabd_step.  Every intermediate
-   lives in one file-scope device array of the library (about 13 MB, held on
-   every device that loads the library until the process exits); nothing is
-   allocated.  The first call on a device looks up that array's device
+   bodies, computed by the same step kernels as mabd_step (Hbar^{-1} is formed
+   on the device).  Every intermediate lives in one file-scope device array of
+   the library (12.8 MB = 1,600,000 doubles, held on every device that loads
+   the library until the process exits); nothing is allocated.  The first call on a device looks up that array's device
    address (cudaGetSymbolAddress), so make it before any stream capture.
    All calls on a device share the array and it keeps the last call's
    contents (the call clears what must start at zero): calls that overlap on
@@ -260,12 +265,17 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
      joints: device array of K in [M-1, M+1] descriptions in path order:
        an optional pin of body 0 (body_a = 0, body_b = MABD_WORLD), the M-1
        joints between bodies i and i+1 (either orientation), an optional pin
-       of body M-1.
+       of body M-1; ball and hinge joints only (universal and prismatic
+       joints are rejected with INVALID_ARG).
      q_out, qdot_out: device arrays of 12*M doubles (body by body);
      lambda_out: device array of the dual rows (3 per ball, 5 per hinge).
    Synchronizes cfg->stream.  INVALID_ARG for M outside [1, MAX], K outside
-   [M-1, M+1], or descriptions that break the layout above; device-side
-   failures are returned as by mabd_step. */
+   [M-1, M+1], descriptions that break the layout above, or values that
+   mabd_add_bodies / mabd_add_joints reject (non-finite numbers, mass,
+   volume or E <= 0, nu outside [0, 0.5), a non-diagonal second moment);
+   device-side failures are returned as by mabd_step.  The cached device
+   address of the array belongs to the device's current context: after
+   cudaDeviceReset the library must be reloaded before this call is used. */
 #define MABD_NOALLOC_MAX_BODIES 4096
 mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M, const mabd_body_desc *bodies,
                                     int32_t K, const mabd_joint_desc *joints, double *q_out,

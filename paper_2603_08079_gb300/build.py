@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"])
+    subprocess.check_call([NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static", "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

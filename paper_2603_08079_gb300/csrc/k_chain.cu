@@ -25,23 +25,6 @@ namespace mabd {
 // anchor and 2 at the second point), so each Gram block is E^T Mbar E' with
 // the group's rest-frame directions E.
 
-// out[r][c] (r < NA, c < NB) = Ea[:, ca[r]]^T Mb Eb[:, cb[c]]
-template <int NA, int NB, typename T>
-__device__ __forceinline__ void project(const T Ea[3][3], const int ca[3], const T Mb[3][3],
-                                        const T Eb[3][3], const int cb[3], T out[3][3]) {
-  T tmp[3][NB];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-      tmp[a][c] = Mb[a][0] * Eb[0][cb[c]] + Mb[a][1] * Eb[1][cb[c]] + Mb[a][2] * Eb[2][cb[c]];
-#pragma unroll
-  for (int r = 0; r < NA; ++r)
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-      out[r][c] = Ea[0][ca[r]] * tmp[0][c] + Ea[1][ca[r]] * tmp[1][c] + Ea[2][ca[r]] * tmp[2][c];
-}
-
 // Gram blocks of body j with products in T (double: the FP64 form; float:
 // the mixed form, inputs rounded to FP32); the blocks are stored in FP64.
 template <typename T> struct GP;

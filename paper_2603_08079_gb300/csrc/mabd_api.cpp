@@ -12,8 +12,11 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mabd.h"
 #include "mabd_internal.h"
+#include "hbar_inv.h"
 
 using namespace mabd;
 
@@ -59,6 +62,13 @@ struct mabd_ctx {
   CRLevel *d_levels = nullptr;
   CRLevelT<float> *d_levels_f = nullptr;
   int cr_tail_level = 0;
+  // segment-tiled chain step of MABD_MIXED_FP32_DUAL (k_seg.cu), chosen with
+  // MABD_CHAIN_SEG=1: tile levels (seg_lv[0]: the level-0 tiles of the
+  // joints) and per-joint and per-body work arrays
+  bool seg_on = false;
+  int seg_up_t = SEG_UP_T;  // rows per tile of the upper systems (MABD_SEG_UP_T: a power of two)
+  SegChain seg{};
+  std::vector<SegLevel> seg_lv;
   DevTree T{};
   DevPCG P{};
   DevPCG32 P32{};
@@ -115,6 +125,12 @@ struct mabd_ctx {
   // profiling
   bool prof_on = false;
   std::vector<Rec> recs;
+  // profiling by graph replay: the step captured once with timing events
+  // around every launch (external event-record nodes), replayed per step
+  cudaGraphExec_t g_prof = nullptr;
+  std::vector<Rec> prof_recs;
+  bool prof_capture = false;
+  cudaStream_t prof_stream = nullptr;
   std::map<std::string, std::pair<double, int64_t>> prof_acc;
 };
 
@@ -464,69 +480,9 @@ bool tree_order(const mabd_ctx *ctx, const Graph &g, TreeOrder &t) {
 // --------------------------------------------------------------------------
 // per-body structured inverse of Hbar_A = M_A/h^2 + Kbar_A (Eq. abd_final)
 // --------------------------------------------------------------------------
-bool inv2(double a, double b, double d, double out[3]) {
-  // [[a, b], [b, d]]^{-1}
-  if (!(a > 0.0)) return false;
-  double det = a * d - b * b;
-  if (!(det > 0.0)) return false;
-  out[0] = d / det;
-  out[1] = -b / det;
-  out[2] = a / det;
-  return true;
-}
-
 bool structured_hinv(const mabd_body_desc &d, double h, double out[HINV_N]) {
-  const double E = d.young, nu = d.poisson, V = d.volume;
-  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-  const double ih2 = 1.0 / (h * h);
   const double s[3] = {d.second_moment[0], d.second_moment[1], d.second_moment[2]};
-  // diagonal-entry block X (indices 0, 4, 8): s_i/h^2 + V(2mu + lam) on the
-  // diagonal, V lam off the diagonal; invert by Cholesky
-  double X[9];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) X[3 * r + c] = (r == c ? s[r] * ih2 + V * (2.0 * mu + lam) : V * lam);
-  double L[9] = {0};
-  for (int c = 0; c < 3; ++c) {
-    double t = X[3 * c + c];
-    for (int k = 0; k < c; ++k) t -= L[3 * c + k] * L[3 * c + k];
-    if (!(t > 0.0)) return false;
-    L[3 * c + c] = std::sqrt(t);
-    for (int r = c + 1; r < 3; ++r) {
-      double v = X[3 * r + c];
-      for (int k = 0; k < c; ++k) v -= L[3 * r + k] * L[3 * c + k];
-      L[3 * r + c] = v / L[3 * c + c];
-    }
-  }
-  double Xi[9];
-  for (int c = 0; c < 3; ++c) {
-    double e[3] = {0, 0, 0}, y[3], x[3];
-    e[c] = 1.0;
-    for (int i = 0; i < 3; ++i) {
-      double v = e[i];
-      for (int k = 0; k < i; ++k) v -= L[3 * i + k] * y[k];
-      y[i] = v / L[3 * i + i];
-    }
-    for (int i = 2; i >= 0; --i) {
-      double v = y[i];
-      for (int k = i + 1; k < 3; ++k) v -= L[3 * k + i] * x[k];
-      x[i] = v / L[3 * i + i];
-    }
-    for (int r = 0; r < 3; ++r) Xi[3 * r + c] = x[r];
-  }
-  out[0] = h * h / d.mass;
-  out[1] = Xi[0];
-  out[2] = 0.5 * (Xi[1] + Xi[3]);
-  out[3] = 0.5 * (Xi[2] + Xi[6]);
-  out[4] = Xi[4];
-  out[5] = 0.5 * (Xi[5] + Xi[7]);
-  out[6] = Xi[8];
-  // transpose pairs: entry (row a, column i) has mass s_i/h^2 and stiffness V mu,
-  // coupled to its transpose by V mu
-  const double vm = V * mu;
-  if (!inv2(s[0] * ih2 + vm, vm, s[1] * ih2 + vm, out + 7)) return false;   // q[1]=A(1,0), q[3]=A(0,1)
-  if (!inv2(s[0] * ih2 + vm, vm, s[2] * ih2 + vm, out + 10)) return false;  // q[2]=A(2,0), q[6]=A(0,2)
-  if (!inv2(s[1] * ih2 + vm, vm, s[2] * ih2 + vm, out + 13)) return false;  // q[5]=A(2,1), q[7]=A(1,2)
-  return out[0] > 0.0 && std::isfinite(out[0]);
+  return hbar_inverse(d.mass, s, d.volume, d.young, d.poisson, h, out);
 }
 
 // --------------------------------------------------------------------------
@@ -543,8 +499,16 @@ void dbg_pending(const char *where) {
   if (e != cudaSuccess) std::fprintf(stderr, "mabd debug: pending %s at %s\n", cudaGetErrorName(e), where);
 }
 
+// an NVTX range over a launch group (host timeline of a profiler; a no-op
+// without one)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <class F>
 void run(mabd_ctx *ctx, const char *name, F &&f) {
+  NvtxRange range(name);
   if (ctx->debug_sync) {
     cudaError_t e0 = cudaGetLastError();
     f();
@@ -559,6 +523,17 @@ void run(mabd_ctx *ctx, const char *name, F &&f) {
       std::fprintf(stderr, "mabd debug: %s\n", ctx->err_detail);
       ctx->debug_err = e;
     }
+    return;
+  }
+  if (ctx->prof_capture) {
+    // inside the capture of the profiling graph: event-record nodes
+    Rec r{name, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecordWithFlags(r.a, ctx->prof_stream, cudaEventRecordExternal);
+    f();
+    cudaEventRecordWithFlags(r.b, ctx->prof_stream, cudaEventRecordExternal);
+    ctx->prof_recs.push_back(r);
     return;
   }
   if (!ctx->prof_on) {
@@ -1350,6 +1325,91 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     C.islot = dslot;
     if (ctx->loop_b) CK(cudaMemsetAsync(ctx->loop_b, 0, 5 * (size_t)K * 8, ctx->stream));
   }
+  // segment-tiled chain step (k_seg.cu) for the FP32-reduction form with one
+  // correction sweep, ball and hinge joints between chain bodies or to the
+  // world (joints to fixed bodies keep the level-by-level reduction), when
+  // MABD_CHAIN_SEG=1 (measured slower than the level-by-level reduction on
+  // the 1M chain: the default stays the latter)
+  ctx->seg_on = false;
+  if (solver == MABD_SOLVER_CHAIN && f32dual && ctx->cfg.refine_steps == 1) {
+    const char *e = std::getenv("MABD_CHAIN_SEG");
+    bool want = e && e[0] == '1';
+    int nb = 0;
+    for (int j = 0; j < M; ++j) nb += fixed[j] ? 0 : 1;
+    for (int k = 0; k < K && want; ++k)
+      if (!(jfl[k] & JF_A_FREE) || ((jfl[k] & JF_B_BODY) && !(jfl[k] & JF_B_FREE))) want = false;
+    // joint k joins path bodies k - 1 + sigma and k + sigma
+    const int sigma = (K > 0 && jb[0] >= 0) ? 1 : 0;
+    std::vector<uint8_t> cjf(K, 0);
+    for (int k = 0; k < K && want; ++k) {
+      const int lo = k - 1 + sigma, upb = k + sigma;
+      uint8_t f = jtype[k] == 1 ? SEGJ_HINGE : 0;
+      if (jb[k] >= 0) {
+        if (ja[k] == lo && jb[k] == upb) f |= SEGJ_LO | SEGJ_UP | SEGJ_A_LO;
+        else if (ja[k] == upb && jb[k] == lo) f |= SEGJ_LO | SEGJ_UP;
+        else want = false;
+      } else {
+        if (ja[k] == lo) f |= SEGJ_LO | SEGJ_A_LO;
+        else if (ja[k] == upb) f |= SEGJ_UP;
+        else want = false;
+      }
+      if ((f & SEGJ_LO) && (lo < 0 || lo >= nb)) want = false;
+      if ((f & SEGJ_UP) && (upb < 0 || upb >= nb)) want = false;
+      cjf[k] = f;
+    }
+    // neighbouring joints share a body
+    for (int k = 0; k + 1 < K && want; ++k)
+      if (!(cjf[k] & SEGJ_UP) || !(cjf[k + 1] & SEGJ_LO)) want = false;
+    if (want) {
+      CK(seg_init());
+      SegChain &S = ctx->seg;
+      S.nb = nb;
+      S.sigma = sigma;
+      uint8_t *dcjf = dnew<uint8_t>(ctx, K, ok);
+      S.ytile = dnew<float>(ctx, 5 * (size_t)K, ok);
+      S.lam0 = dnew<float>(ctx, 5 * (size_t)K, ok);
+      S.dq0 = dnew<float>(ctx, 12 * (size_t)nb, ok);
+      S.z = dnew<float>(ctx, 12 * (size_t)nb, ok);
+      S.u = dnew<float>(ctx, 12 * (size_t)nb, ok);
+      S.rf = dnew<float>(ctx, 12 * (size_t)nb, ok);
+      S.RHlo = dnew<float>(ctx, 9 * (size_t)K, ok);
+      S.fac = dnew<float>(ctx, (size_t)65 * (SEG_T + 4) * ((K + SEG_T - 1) / SEG_T), ok);
+      ctx->seg_lv.clear();
+      int ut = SEG_UP_T;
+      if (const char *u = std::getenv("MABD_SEG_UP_T")) {
+        const int v = std::atoi(u);
+        if (v >= 2 && v <= SEG_UP_T && (v & (v - 1)) == 0) ut = v;
+      }
+      ctx->seg_up_t = ut;
+      int N = (K + SEG_T - 1) / SEG_T;
+      while (true) {
+        SegLevel L{};
+        L.N = N;
+        L.Dn = dnew<float>(ctx, 15 * (size_t)N, ok);
+        L.Da = dnew<float>(ctx, 15 * (size_t)N, ok);
+        L.Bn = dnew<float>(ctx, 25 * (size_t)N, ok);
+        for (int ps = 0; ps < 2; ++ps) {
+          L.r[ps].bn = dnew<float>(ctx, 5 * (size_t)N, ok);
+          L.r[ps].ba = dnew<float>(ctx, 5 * (size_t)N, ok);
+          L.r[ps].lam = dnew<float>(ctx, 5 * (size_t)N, ok);
+          if (ctx->seg_lv.empty()) {
+            L.r[ps].b0 = dnew<double>(ctx, 5 * (size_t)N, ok);
+            L.r[ps].dl = dnew<double>(ctx, 5 * (size_t)N, ok);
+          }
+        }
+        ctx->seg_lv.push_back(L);
+        if (N <= ut) break;
+        N = (N + ut - 1) / ut;
+      }
+      if (!ok) {
+        free_all(ctx);
+        return MABD_ERR_OUT_OF_MEMORY;
+      }
+      CK(up(dcjf, cjf.data(), cjf.size()));
+      S.cjf = dcjf;
+      ctx->seg_on = true;
+    }
+  }
   if (solver == MABD_SOLVER_PCG && mixed) {
     DevPCG32 &Q = ctx->P32;
     Q.nblocks = (K + 127) / 128;
@@ -1655,11 +1715,50 @@ static void enqueue_loop(mabd_ctx *ctx, cudaStream_t s) {
 
 extern "C" {
 
+// the upper systems of the segment-tiled chain step for one pass: reduce
+// every level into the next, solve the last in one CTA, back-substitute down
+static void enqueue_seg_up(mabd_ctx *ctx, int pass, unsigned long long *rmax, cudaStream_t s) {
+  const int n = (int)ctx->seg_lv.size(), T = ctx->seg_up_t;
+  for (int i = 0; i + 1 < n; ++i)
+    run(ctx, "seg_up", [&] {
+      launch_seg_up_reduce(ctx->seg_lv[i], ctx->seg_lv[i + 1], T, pass, pass == 0, i == 0 ? rmax : nullptr,
+                           ctx->d_status, s);
+    });
+  run(ctx, "seg_up", [&] {
+    launch_seg_up_top(ctx->seg_lv[n - 1], T, pass, n == 1 ? rmax : nullptr, ctx->d_status, s);
+  });
+  for (int i = n - 2; i >= 0; --i)
+    run(ctx, "seg_up", [&] { launch_seg_up_back(ctx->seg_lv[i], ctx->seg_lv[i + 1], T, pass, ctx->d_status, s); });
+}
+
+// segment-tiled chain step (k_seg.cu): the approximate solve, the
+// back-substitution with the residuals and the correction's rhs, the
+// correction's back-substitution with the state update; each tile pass
+// followed by the solve of the tiles' first rows
+static void enqueue_seg_chain(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
+  SegChain S = ctx->seg;
+  S.lv0 = ctx->seg_lv[0];
+  S.write_cj = maxbits ? 1 : 0;
+  S.refine_max = maxbits ? maxbits + 2 : nullptr;
+  S.polar_iters = maxbits ? maxbits + 3 : nullptr;
+  const StepParams &p = ctx->sp;
+  run(ctx, "seg_body", [&] { launch_seg_body(ctx->B, ctx->J, p, S, ctx->d_status, s); });
+  run(ctx, "seg_first", [&] { launch_seg_tiles(SEG_FIRST, ctx->B, ctx->J, p, S, ctx->d_status, s); });
+  enqueue_seg_up(ctx, 0, nullptr, s);
+  run(ctx, "seg_corr", [&] { launch_seg_tiles(SEG_CORR, ctx->B, ctx->J, p, S, ctx->d_status, s); });
+  enqueue_seg_up(ctx, 1, S.refine_max, s);
+  run(ctx, "seg_final", [&] { launch_seg_tiles(SEG_FINAL, ctx->B, ctx->J, p, S, ctx->d_status, s); });
+}
+
 // mixed-precision chain step (k_mixed.cu): approximate solve with FP32
 // products and the FP64 reduction, then refine_steps FP64 residual-correction
 // sweeps through the stored factors, then the state update
 static void enqueue_mixed_chain(mabd_ctx *ctx, unsigned long long *maxbits, cudaStream_t s) {
   const StepParams &p = ctx->sp;
+  if (ctx->seg_on) {
+    enqueue_seg_chain(ctx, maxbits, s);
+    return;
+  }
   run(ctx, "mx_body_prep", [&] {
     launch_mx_body_prep(ctx->B, p, ctx->d_status, s, maxbits ? maxbits + 3 : nullptr);
   });
@@ -1992,6 +2091,7 @@ static mabd_status step_graph(mabd_ctx *ctx) {
 
 mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
   dbg_pending("enter mabd_step");
+  NvtxRange range("mabd_step");
   if (!ctx || nsteps < 0) return MABD_ERR_INVALID_ARG;
   if (ctx->cuda_failed) return MABD_ERR_CUDA;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
@@ -2004,6 +2104,41 @@ mabd_status mabd_step(mabd_ctx *ctx, int32_t nsteps, mabd_step_stats *stats) {
       ctx->max_cap = nsteps;
     }
     CK(cudaMemsetAsync(ctx->d_max, 0, STAT_SLOTS * (size_t)nsteps * 8, ctx->stream));
+  }
+  if (!stats && ctx->prof_on && !ctx->debug_sync && graphs_ready(ctx) && ctx->g_step && !ctx->g_prof &&
+      ctx->prof_recs.empty()) {
+    // per-launch times from replays of the step's graph with timing events
+    // (captured once; a failed capture leaves the direct launches below)
+    ctx->prof_capture = true;
+    ctx->prof_stream = ctx->gstream;
+    ctx->g_prof = capture(ctx, body_step);
+    ctx->prof_capture = false;
+    if (!ctx->g_prof) {
+      for (auto &r : ctx->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+      }
+      ctx->prof_recs.clear();
+      ctx->prof_recs.push_back(Rec{"", nullptr, nullptr});  // marks the failed attempt
+    }
+  }
+  if (!stats && ctx->prof_on && !ctx->debug_sync && ctx->g_prof) {
+    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0));
+    for (int i = 0; i < nsteps; ++i) {
+      CK(cudaGraphLaunch(ctx->g_prof, ctx->gstream));
+      CK(cudaStreamSynchronize(ctx->gstream));
+      for (auto &r : ctx->prof_recs) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        auto &acc = ctx->prof_acc[r.name];
+        acc.first += ms;
+        acc.second += 1;
+      }
+    }
+    CK(cudaEventRecord(ctx->ev_out, ctx->gstream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0));
+    return MABD_OK;
   }
   if (!stats && !ctx->prof_on && !ctx->debug_sync && graphs_ready(ctx)) {
     // order the private graph stream after the caller's stream and back
@@ -2155,6 +2290,8 @@ mabd_status mabd_get_info(mabd_ctx *ctx, mabd_info *info) {
   const bool cr = ctx->solver == MABD_SOLVER_CHAIN || ctx->solver == MABD_SOLVER_LOOP;
   info->cr_levels = cr ? (int32_t)ctx->levels.size() : 0;
   info->cr_tail_level = cr ? ctx->cr_tail_level : 0;
+  info->seg_levels = ctx->seg_on ? (int32_t)ctx->seg_lv.size() : 0;
+  info->seg_tile = SEG_T;
   return MABD_OK;
 }
 
@@ -2182,7 +2319,8 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
                                 "tree_forest",
                                 "cr_level", "cr_reduce", "cr_combine", "cr_tail", "loop_schur",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",
-                                "pcg_iteration", "backprop", "residuals"};
+                                "pcg_iteration", "backprop", "residuals", "seg_body", "seg_first", "seg_corr",
+                                "seg_final", "seg_up"};
   int n = 0;
   for (const char *k : known) {
     auto it = ctx->prof_acc.find(k);
@@ -2645,8 +2783,12 @@ mabd_status mabd_destroy(mabd_ctx *ctx) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
-  for (cudaGraphExec_t g : {ctx->g_step, ctx->g_pre, ctx->g_chunk, ctx->g_post})
+  for (cudaGraphExec_t g : {ctx->g_step, ctx->g_pre, ctx->g_chunk, ctx->g_post, ctx->g_prof})
     if (g) cudaGraphExecDestroy(g);
+  for (auto &r : ctx->prof_recs) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
   if (ctx->gstream) {
     cudaStreamSynchronize(ctx->gstream);
     cudaStreamDestroy(ctx->gstream);

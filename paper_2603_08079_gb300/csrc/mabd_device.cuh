@@ -379,6 +379,23 @@ __device__ __forceinline__ void mbar(const T h[16], const T p[3], const T q[3], 
   Mb[2][1] = h[5] * p2q1 + h[14] * p1q2;
 }
 
+// out[r][c] (r < NA, c < NB) = Ea[:, ca[r]]^T Mb Eb[:, cb[c]]
+template <int NA, int NB, typename T>
+__device__ __forceinline__ void project(const T Ea[3][3], const int ca[3], const T Mb[3][3],
+                                        const T Eb[3][3], const int cb[3], T out[3][3]) {
+  T tmp[3][NB];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      tmp[a][c] = Mb[a][0] * Eb[0][cb[c]] + Mb[a][1] * Eb[1][cb[c]] + Mb[a][2] * Eb[2][cb[c]];
+#pragma unroll
+  for (int r = 0; r < NA; ++r)
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      out[r][c] = Ea[0][ca[r]] * tmp[0][c] + Ea[1][ca[r]] * tmp[1][c] + Ea[2][ca[r]] * tmp[2][c];
+}
+
 // atomic max of a non-negative double through its bit pattern
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
   if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000ULL);  // NaN -> +inf

@@ -267,6 +267,55 @@ struct LpcNet {
   const uint16_t *W1t, *W2t, *W3t;  // bf16 bits, transposed: [H][2F], [H][2H], [H][2H]
 };
 
+// Segment-tiled form of the chain solve (k_seg.cu; the mixed form with the
+// FP32 reduction).  The dual rows (joints in path order) are cut into tiles of
+// SEG_T rows; one CTA per tile does the tile's per-body and per-joint work and
+// eliminates the tile's rows by block cyclic reduction in shared memory down
+// to its first row.  Row t of the next level's system is tile t's first row:
+//   D_t = Dn[t] + Da[t-1],  coupling to row t + 1: Bn[t],
+//   b_t = bn[t] + ba[t-1] (+ fl32(b0[t] + dl[t-1]) above the level-0 tiles),
+// (Da, ba: what tile t's eliminations add to tile t + 1's first row; b0, dl:
+// the level-0 first row's own rhs and the part that the previous tile's last
+// body contributes, kept in FP64 so that the correction's rhs, a difference of
+// nearly equal parts, is summed before it is rounded).  Upper systems are
+// reduced the same way by tiles of SEG_UP_T rows until one tile holds them.
+constexpr int SEG_T = 64;
+constexpr int SEG_UP_T = 256;
+
+struct SegRhs {
+  float *bn, *ba;      // [5][N]
+  double *b0, *dl;     // [5][N] (level-0 tiles only, else null)
+  float *lam;          // [5][N] multipliers of the tiles' first rows (solution of the next level)
+};
+
+struct SegLevel {
+  int32_t N;           // tiles of this level = rows of the next level's system
+  float *Dn, *Da;      // [15][N] packed lower 5x5
+  float *Bn;           // [25][N] row-major 5x5
+  SegRhs r[2];         // pass 0: the approximate solve, pass 1: the correction
+};
+
+// per-joint flags of the chain in path order: the joint's lower and upper
+// path bodies exist (a body of the joint), body a is the lower one, hinge
+enum : uint8_t { SEGJ_LO = 1, SEGJ_UP = 2, SEGJ_A_LO = 4, SEGJ_HINGE = 8 };
+
+struct SegChain {
+  int32_t nb;          // chain bodies (path order 0 .. nb - 1)
+  int32_t sigma;       // joint k joins path bodies k - 1 + sigma (lower) and k + sigma (upper)
+  const uint8_t *cjf;  // [K] SEGJ_* flags
+  float *ytile;        // [5][K] forward-eliminated rhs of the eliminated rows of the current pass
+  float *lam0;         // [5][K] multipliers of the approximate solve
+  float *dq0, *z;      // [12][nb] rest-frame increment of the approximate solve; the correction's Hbar^{-1} r
+  float *u;            // [12][nb] u = Hbar^{-1} fbar (FP32)
+  float *rf;           // [12][nb] fbar - Hbar u (its residual, from double-float, rounded to FP32)
+  float *RHlo;         // [9][K] hinge frames as double-float pairs (J.RHf, RHlo)
+  float *fac;          // [tiles][65][SEG_T + 4] each level-0 tile's factors (written by FIRST)
+  SegLevel lv0;        // level-0 tile outputs
+  int32_t write_cj;    // also write J.c and J.RH in FP64 (residual statistics)
+  unsigned long long *refine_max;   // max |C + G dq| of the approximate solve (null: not wanted)
+  unsigned long long *polar_iters;  // Newton steps of the polar rotation, summed (null: not wanted)
+};
+
 struct StepParams {
   double h, inv_h;
   double g[3];
@@ -406,6 +455,27 @@ void launch_mx_res_joint(const DevBodies &B, const DevJoints &J, const StepParam
                          unsigned long long *maxbit, cudaStream_t s, bool add_gz = true);
 void launch_mx_final(const DevBodies &B, const DevJoints &J, const DevIncidence &I,
                      const StepParams &p, int mode, cudaStream_t s);
+
+// segment-tiled chain step (k_seg.cu): the level-0 tile kernels of the three
+// passes (approximate solve; back-substitution, residuals and the correction's
+// rhs; correction back-substitution and state update) and the tile kernels of
+// the upper systems (reduce: tiles of `in`'s rows into `out`; top: all of
+// `in`'s rows in one CTA; back: `in`'s rows given `next`'s solution)
+enum { SEG_FIRST = 0, SEG_CORR = 1, SEG_FINAL = 2 };
+// per body: polar rotation, rest-frame rhs, u and its residual; per joint
+// (by its body a): the hinge frame and C(q_n)
+void launch_seg_body(const DevBodies &B, const DevJoints &J, const StepParams &p, const SegChain &S, int *status,
+                     cudaStream_t s);
+void launch_seg_tiles(int mode, const DevBodies &B, const DevJoints &J, const StepParams &p, const SegChain &S,
+                      int *status, cudaStream_t s);
+// (T: rows per tile of the upper systems, a power of two, 2 .. SEG_UP_T)
+void launch_seg_up_reduce(const SegLevel &in, const SegLevel &out, int T, int pass, bool write_db,
+                          unsigned long long *rmax, int *status, cudaStream_t s);
+void launch_seg_up_top(const SegLevel &in, int T, int pass, unsigned long long *rmax, int *status,
+                       cudaStream_t s);
+void launch_seg_up_back(const SegLevel &in, const SegLevel &next, int T, int pass, int *status, cudaStream_t s);
+// sets the kernels' shared-memory limits (once per process and device)
+cudaError_t seg_init();
 
 // tree (k_tree.cu): one launch per level, deepest first, then root first
 // level [lo, hi) of the body order: T.order[lo, mid) lists its bodies with

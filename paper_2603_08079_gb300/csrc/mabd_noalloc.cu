@@ -4,19 +4,21 @@
 // are the caller's device arrays; every intermediate lives in one
 // file-scope __device__ array of fixed size, shared by all calls on a
 // device.  The paper has no counterpart: this is a deployment variant of
-// the chain path (same kernels as mabd_step).
+// the chain path (the same step kernels as mabd_step; Hbar^{-1} is formed on
+// the device by the set-up code that mabd_prefactor runs on the host).
 #include <cstdio>
 #include <mutex>
 
 #include "../../include/mabd.h"
 #include "mabd_device.cuh"
+#include "hbar_inv.h"
 
 namespace mabd {
 namespace {
 
 constexpr int NA_MAX_BODIES = MABD_NOALLOC_MAX_BODIES;
 constexpr int NA_MAX_JOINTS = NA_MAX_BODIES + 1;
-// 13.1 MB of doubles; carve() below checks every call's layout against it
+// 12.8 MB (1,600,000 doubles); carve() below checks every call's layout against it
 constexpr size_t NA_SCRATCH_DOUBLES = 1600000;
 
 static __device__ __align__(256) double g_na_scratch[NA_SCRATCH_DOUBLES];
@@ -145,42 +147,6 @@ bool carve(double *base, int M, int K, Layout &L) {
   return true;
 }
 
-// structured inverse of Hbar = M_A/h^2 + Kbar_A (Eq. abd_final) for a body in
-// its principal frame; returns false if a block is not positive definite
-__device__ bool na_hinv(double m, const double s[3], double V, double E, double nu, double h,
-                        double out[HINV_N]) {
-  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-  const double ih2 = 1.0 / (h * h);
-  double X[3][3];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) X[r][c] = r == c ? s[r] * ih2 + V * (2.0 * mu + lam) : V * lam;
-  // cofactor inverse of the symmetric 3x3 block
-  const double c00 = X[1][1] * X[2][2] - X[1][2] * X[2][1];
-  const double c01 = X[1][2] * X[2][0] - X[1][0] * X[2][2];
-  const double c02 = X[1][0] * X[2][1] - X[1][1] * X[2][0];
-  const double det = X[0][0] * c00 + X[0][1] * c01 + X[0][2] * c02;
-  if (!(det > 0.0) || !(X[0][0] > 0.0)) return false;
-  const double id = 1.0 / det;
-  out[0] = h * h / m;
-  out[1] = c00 * id;
-  out[2] = c01 * id;
-  out[3] = c02 * id;
-  out[4] = (X[0][0] * X[2][2] - X[0][2] * X[2][0]) * id;
-  out[5] = (X[0][2] * X[1][0] - X[0][0] * X[1][2]) * id;
-  out[6] = (X[0][0] * X[1][1] - X[0][1] * X[1][0]) * id;
-  const double vm = V * mu;
-  const int ca[3] = {0, 0, 1}, cb[3] = {1, 2, 2};
-  for (int t = 0; t < 3; ++t) {
-    const double a = s[ca[t]] * ih2 + vm, d = s[cb[t]] * ih2 + vm, b = vm;
-    const double dt = a * d - b * b;
-    if (!(dt > 0.0) || !(a > 0.0)) return false;
-    out[7 + 3 * t] = d / dt;
-    out[8 + 3 * t] = -b / dt;
-    out[9 + 3 * t] = a / dt;
-  }
-  return true;
-}
-
 // number of incidence entries of bodies 0..j-1 of a chain with K joints
 // whose first joint is a pin on body 0 iff lp = 1
 __device__ __forceinline__ int na_prefix(int j, int lp, int K) {
@@ -214,10 +180,15 @@ __global__ void k_na_bodies(const mabd_body_desc *bodies, int M, int K, int lp, 
   fixed[j] = 0;
   double hv[HINV_N];
   const double tr = s[0] + s[1] + s[2];
-  bool ok = b.fixed == 0 && b.mass > 0.0 && b.volume > 0.0 && b.young > 0.0 && b.poisson >= 0.0 &&
+  // the checks of mabd_add_bodies: finite, positive mass, volume, E and
+  // second moment, nu in [0, 0.5), a principal frame, a finite state
+  bool fin = isfinite(b.mass) && isfinite(b.volume) && isfinite(b.young) && isfinite(b.poisson);
+  for (int c = 0; c < 6; ++c) fin = fin && isfinite(b.second_moment[c]);
+  for (int c = 0; c < 12; ++c) fin = fin && isfinite(b.q[c]) && isfinite(b.qdot[c]);
+  bool ok = fin && b.fixed == 0 && b.mass > 0.0 && b.volume > 0.0 && b.young > 0.0 && b.poisson >= 0.0 &&
             b.poisson < 0.5 && s[0] > 0.0 && s[1] > 0.0 && s[2] > 0.0 &&
             fabs(b.second_moment[3]) <= 1e-12 * tr && fabs(b.second_moment[4]) <= 1e-12 * tr &&
-            fabs(b.second_moment[5]) <= 1e-12 * tr && na_hinv(b.mass, s, b.volume, b.young, b.poisson, h, hv);
+            fabs(b.second_moment[5]) <= 1e-12 * tr && hbar_inverse(b.mass, s, b.volume, b.young, b.poisson, h, hv);
   if (!ok) {
     atomicOr(bad, 1);
     for (int i = 0; i < HINV_N; ++i) hv[i] = 0.0;
@@ -259,12 +230,15 @@ __global__ void k_na_joints(const mabd_joint_desc *joints, int M, int K, int lp,
   const int lo = k - lp, hi = k - lp + 1;
   const int a = (int)d.body_a, b = (int)d.body_b;
   bool ok = d.type == 0 || d.type == 1;
+  // finite points and axes (and a hinge's axis length), as mabd_add_joints requires
+  for (int c = 0; c < 3; ++c)
+    ok = ok && isfinite(d.anchor_a[c]) && isfinite(d.anchor_b[c]) && isfinite(d.axis_a[c]) && isfinite(d.axis_b[c]);
   if (lo < 0) ok = ok && a == 0 && b == MABD_WORLD;           // left pin on body 0
   else if (hi >= M) ok = ok && a == M - 1 && b == MABD_WORLD;  // right pin on the last body
   else ok = ok && ((a == lo && b == hi) || (a == hi && b == lo));
   double na = sqrt(d.axis_a[0] * d.axis_a[0] + d.axis_a[1] * d.axis_a[1] + d.axis_a[2] * d.axis_a[2]);
   double nb = sqrt(d.axis_b[0] * d.axis_b[0] + d.axis_b[1] * d.axis_b[1] + d.axis_b[2] * d.axis_b[2]);
-  if (d.type == 1) ok = ok && na > 0.0 && nb > 0.0 && d.axis_len > 0.0;
+  if (d.type == 1) ok = ok && na > 0.0 && nb > 0.0 && d.axis_len > 0.0 && isfinite(d.axis_len) && isfinite(na) && isfinite(nb);
   if (!ok) {
     atomicOr(bad, 1);
     return;

@@ -53,7 +53,7 @@ class Info(C.Structure):
     _fields_ = [("bodies", C.c_int64), ("joints", C.c_int64), ("dual_rows", C.c_int64),
                 ("topology", C.c_int32), ("solver", C.c_int32), ("device_bytes", C.c_int64),
                 ("precision", C.c_int32), ("refine_steps", C.c_int32), ("cr_levels", C.c_int32),
-                ("cr_tail_level", C.c_int32)]
+                ("cr_tail_level", C.c_int32), ("seg_levels", C.c_int32), ("seg_tile", C.c_int32)]
 
 
 # numpy mirrors of mabd_body_desc / mabd_joint_desc (C layout, natural alignment)

@@ -1,7 +1,9 @@
 """mabd_chain_step_noalloc: the chain step for callers that cannot allocate
 device memory (their intermediates live in the library's fixed device
-array).  Checked against the allocating mabd_step on the same chains and
-states, two calls in a row, through the C ABI.  Collected last on purpose."""
+array).  Checked against the allocating mabd_step and against the FP64 CPU
+oracle on the same chains and states, two calls in a row, through the C
+ABI; and every class of invalid input it must reject.  Collected last on
+purpose."""
 import ctypes as C
 
 import numpy as np
@@ -53,20 +55,34 @@ def _noalloc_step(lib, sc, q, qd, torch):
     return dq.cpu().numpy().reshape(M, 12), dqd.cpu().numpy().reshape(M, 12), dl.cpu().numpy()[:rows]
 
 
-@pytest.mark.parametrize("which", ["chain64", "pulley257", "pulley4096", "free31"])
-def test_noalloc_step_matches_mabd_step(which):
+def _drop_joints(sc, keep):
+    out = dict(sc)
+    for k in ("jtype", "body_a", "body_b", "anchor_a", "anchor_b", "axis_a", "axis_b", "axis_len"):
+        out[k] = sc[k][keep]
+    return out
+
+
+def _scene(which):
+    if which == "chain64":
+        return scenes.chain_cubes(64)                     # one pin, ball joints
+    if which == "pulley257":
+        return scenes.long_chain(257, seed=1)             # both pins, ball / hinge
+    if which == "pulley4096":
+        return scenes.long_chain(4096, seed=1)            # the largest chain it takes
+    if which == "right_pin":
+        sc = scenes.long_chain(200, seed=4)               # only the last body pinned
+        return _drop_joints(sc, list(range(1, len(sc["jtype"]))))
+    return scenes.random_small("chain", 31, seed=2, pin=False)  # no pin
+
+
+@pytest.mark.parametrize("which", ["chain64", "pulley257", "pulley4096", "free31", "right_pin"])
+def test_noalloc_step_matches_mabd_step(ora, which):
     torch = need_gpu()
     lib = _lib()
-    if which == "chain64":
-        sc = scenes.chain_cubes(64)                     # one pin, ball joints
-    elif which == "pulley257":
-        sc = scenes.long_chain(257, seed=1)             # both pins, ball / hinge
-    elif which == "pulley4096":
-        sc = scenes.long_chain(4096, seed=1)            # the largest chain it takes
-    else:
-        sc = scenes.random_small("chain", 31, seed=2, pin=False)  # no pin
+    sc = _scene(which)
     q, qd = scenes.perturb_state(sc, seed=9, rot=0.05, vel=0.2)
     ref = mabd.Solver(sc)
+    S = ora.Scene(sc)
     try:
         for call in range(2):                           # two calls in a row
             ref.set_state(q, qd)
@@ -77,9 +93,50 @@ def test_noalloc_step_matches_mabd_step(which):
             assert rel(nqd, rqd) <= TOL, (call, rel(nqd, rqd))
             assert rel(nlam, rlam) <= TOL, (call, rel(nlam, rlam))
             assert rel(nq, rq) <= TOL
+            oq, oqd, olam, _ = ora.step(S, q, qd)       # and the FP64 oracle from the same state
+            assert rel(nqd, oqd) <= TOL, (call, rel(nqd, oqd))
+            assert rel(nlam, olam) <= TOL, (call, rel(nlam, olam))
             q, qd = nq, nqd                             # the next call starts from this output
     finally:
         ref.close()
+
+
+BAD_BODY = [("mass", np.inf), ("mass", np.nan), ("volume", np.inf), ("young", np.inf),
+            ("second_moment", np.nan), ("q", np.nan), ("qdot", np.inf), ("mass", -1.0),
+            ("poisson", 0.5)]
+BAD_JOINT = [("anchor_a", np.nan), ("anchor_b", np.inf), ("axis_a", np.nan), ("axis_b", np.inf),
+             ("axis_len", np.inf)]
+
+
+@pytest.mark.parametrize("field,value", BAD_BODY + BAD_JOINT)
+def test_noalloc_rejects_invalid_values(field, value):
+    """Each class of value that mabd_add_bodies / mabd_add_joints reject is
+    rejected here too (INVALID_ARG), not carried into the step."""
+    torch = need_gpu()
+    lib = _lib()
+    sc = scenes.long_chain(9, seed=3)                 # balls and hinges, both pins
+    b = mabd.body_array(sc)
+    j = mabd.joint_array(sc)
+    if (field, value) in BAD_BODY:
+        arr = b[field]
+        if arr.ndim > 1:
+            arr[4, 0] = value
+        else:
+            arr[4] = value
+    else:
+        k = int(np.nonzero(sc["jtype"] == 1)[0][0])   # a hinge (it has an axis length)
+        arr = j[field]
+        if arr.ndim > 1:
+            arr[k, 1] = value
+        else:
+            arr[k] = value
+    stream = torch.cuda.current_stream()
+    db = torch.from_numpy(b.view(np.uint8).copy()).cuda()
+    dj = torch.from_numpy(j.view(np.uint8).copy()).cuda()
+    out = torch.zeros(12 * len(b) + 64, dtype=torch.float64, device="cuda")
+    code = lib.mabd_chain_step_noalloc(C.byref(_cfg(lib, sc, stream)), len(b), db.data_ptr(), len(j),
+                                       dj.data_ptr(), out.data_ptr(), out.data_ptr(), out.data_ptr())
+    assert code == 1, (field, value, code)
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum():
