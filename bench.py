@@ -385,6 +385,32 @@ def seg_bytes(name: str, jtype: np.ndarray, M: int) -> float | None:
     return None
 
 
+def tree_up_bytes(M: int, nroots: int, form: str) -> float:
+    """Algorithmic HBM bytes of one step's upward elimination passes of the
+    tree solver (Alg. 2 read as exact constraint-row elimination), every
+    datum counted once per pass.  Per body (FP32 elimination, x2 in FP64):
+    its rotation 36 (72), Hbar^{-1} 64 (128), rhs u 48 (96), its joint's
+    points and frame 60 (120) read; X = Hhat^{-1} G^T 240, L_D 60, y 48,
+    e 20, U = P^T L_D^{-T} 240 and v 48 written (x2 in FP64); per non-root
+    body its U and v read again by its parent 288 (576).  The mixed form runs
+    two passes per step (the approximate solve and the correction), the FP64
+    form one."""
+    s = 1 if form != "fp64" else 2
+    per_body = s * (36 + 64 + 48 + 60 + 240 + 60 + 48 + 20 + 240 + 48)
+    per_child = s * 288
+    passes = 2 if form != "fp64" else 1
+    return float(passes * (M * per_body + (M - nroots) * per_child))
+
+
+def pcg_iteration_bytes(M: int, K: int, nfixed: int) -> float:
+    """Algorithmic HBM bytes of one FP32 block-Jacobi PCG iteration on the
+    dual (matrix-free S p, Sec. 5.5 stand-in), per ball joint: p 12, the
+    two FP32 anchors 24, S p written 12, r, z, x read and written 72, the
+    preconditioner's Cholesky factor 24, and its bodies' indices 8; per free
+    body: R 36, Hbar^{-1} 64, the rest-frame G^T p written and read 96."""
+    return float(K * (12 + 24 + 12 + 72 + 24 + 8) + (M - nfixed) * (36 + 64 + 96))
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel, from one ncu capture of the current kernel (scaled to the named
 # workload by the bodies it processes where the capture ran a smaller chain);
@@ -621,10 +647,89 @@ def run_gpu(args):
             result["cpu_baseline"] = cpu_baseline(args)
             if args.workload == "batch4096":
                 result["cpu_baseline_all_cores"] = cpu_baseline_parallel(args)
+    # the other paper-shaped workloads in their chosen forms (one GPU only,
+    # default run of the chain)
+    if ws == 1 and args.workload == "chain1m" and not args.no_sub:
+        subs = {}
+        for name in SUB_WORKLOADS:
+            subs[name] = sub_record(name, args, barrier_sync)
+        if result is not None:
+            result.update(subs)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+SUB_WORKLOADS = ("tree256k", "batch4096", "net64x64x16")
+
+
+def sub_record(name: str, args, barrier_sync) -> dict:
+    """One of the other paper-shaped workloads, timed like the main one in
+    its chosen form with the plain FP64 GPU path beside it (one GPU)."""
+    from paper_2603_08079_gb300 import mabd
+
+    sc = make_scene(name)
+    M = len(sc["mass"])
+    form = "mixed" if name == "net64x64x16" else "mixed_fp32_dual"
+    steps = 10 if name == "net64x64x16" else args.steps
+    warm = 3
+    s = mabd.Solver(sc, precision=form, refine_steps=args.refine, pcg_max_iters=20000)
+    sargs = argparse.Namespace(**vars(args))
+    sargs.workload = name
+    learned = use_learned(sargs, form)
+    if learned is not None:
+        s.set_preconditioner(learned)
+    info = s.info()
+    ms, _ = time_steps(s, steps, warm, barrier_sync)
+    s.profile(True)
+    s.profile_reset()
+    s.step(args.profile_steps)
+    kt = s.kernel_times()
+    s.profile(False)
+    st = s.step(1, stats=True)[0]
+    sched = s.tree_schedule() if info["solver"] == "tree" else None
+    s.close()
+    rec = {"config": workload_config(M, info["joints"], info["dual_rows"], name, form, args.refine),
+           "form": form, "ms_per_step": ms / steps, "value": M * steps / (ms / 1e3), "unit": "body-steps/s",
+           "steps": steps, "warmup": warm,
+           "parity": "1e-6 normwise on qdot and lambda against the FP64 oracle, one step from the same "
+                     "state, full size (tests/test_gpu_tree_mixed.py, test_gpu_mixed.py, test_gpu_lpc.py)",
+           "kernels_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in kt.items()},
+           "launches_per_step": sum(n for _, n in kt.values()) / args.profile_steps,
+           "refine_residual": st["refine_residual"], "joint_residual": st["joint_residual"]}
+    if learned is not None:
+        rec["config"]["preconditioner"] = "learned, trained parameters %s" % LPC_PARAMS_REL
+    if st.get("pcg_iters"):
+        rec["pcg_iters_per_step"] = st["pcg_iters"]
+    if sched is not None:
+        rec["config"]["tree_schedule"] = sched
+    dname, (dms, dn) = max(kt.items(), key=lambda kv: kv[1][0])
+    per_launch_ms = dms / dn
+    model = None
+    if dname == "tree_up":
+        nroots = int(np.sum(np.asarray(sc["fixed"]) != 0)) if name == "batch4096" else 1
+        model = tree_up_bytes(M, nroots, form) / (dn / args.profile_steps)
+    elif dname == "p32_iteration":
+        nfixed = int(np.sum(np.asarray(sc["fixed"]) != 0))
+        model = pcg_iteration_bytes(M, info["joints"], nfixed)
+    if model is not None:
+        achieved = model / (per_launch_ms / 1e3) / 1e9
+        peak = measured_hbm_gbs()
+        rec["roofline"] = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                           "frac": round(achieved / peak, 4), "traffic": None, "kernel": dname,
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                           "kernel_ms_per_launch": round(per_launch_ms, 5), "bytes_per_launch": model}
+    else:
+        rec["roofline"] = {"bound": "hbm", "achieved": None, "frac": None, "kernel": dname}
+    # the plain FP64 GPU path on the same workload
+    ref = mabd.Solver(sc, precision="fp64", pcg_max_iters=20000)
+    psteps = 3 if name == "net64x64x16" else steps
+    pms, _ = time_steps(ref, psteps, warm, barrier_sync)
+    ref.close()
+    rec["plain_fp64_gpu"] = {"value": M * psteps / (pms / 1e3), "unit": "body-steps/s",
+                             "ms_per_step": pms / psteps}
+    return rec
 
 
 def split_assemblies(sc: dict) -> list:
@@ -790,6 +895,8 @@ def main():
                     help="form of the step (auto: mixed with the FP32 reduction for the chain, "
                          "mixed with the learned preconditioner for the net, FP64 otherwise)")
     ap.add_argument("--refine", type=int, default=1, help="FP64 correction sweeps of the mixed form")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="chain workload: skip the tree, batch and net records")
     ap.add_argument("--no-lpc", action="store_true",
                     help="net workload: block Jacobi instead of the learned preconditioner")
     args = ap.parse_args()
