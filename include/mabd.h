@@ -282,13 +282,12 @@ mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M, const mab
                                     double *qdot_out, double *lambda_out);
 
 /* Schedule of a tree context's elimination, tuned at mabd_prefactor by
-   timing the candidates on the scene's first state: counts[0..2] = number
-   of levels whose bodies with children are eliminated one per thread, by 8
-   lanes, by 4 lanes per body (level-scheduled path); counts[3] = 0 for the
-   level-scheduled path (one launch per level), or 8 / 4 for the persistent
-   kernel (one block per tree, both passes in one launch, that many lanes per
-   body with children).  MABD_TREE_VARIANT=0|1|2 and MABD_TREE_MODE=
-   levels|forest8|forest4 in the environment force a choice (tests). */
+   timing the candidates on the scene's first state: counts[0] = number of
+   levels below the roots, counts[1] = counts[2] = 0 (unused), counts[3] = 0
+   for the level-scheduled path (one launch per level and pass), or 128 / 64
+   for the persistent kernel (one block of that many threads per tree, both
+   passes in one launch).  MABD_TREE_MODE=levels|forest128|forest64 in the
+   environment forces the path (tests). */
 mabd_status mabd_tree_schedule(mabd_ctx *ctx, int32_t *counts);
 
 /* ---- Learned block preconditioner of the mixed-precision PCG path -------

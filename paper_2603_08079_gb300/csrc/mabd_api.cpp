@@ -84,14 +84,13 @@ struct mabd_ctx {
   double *h_scal = nullptr;  // pinned [8]
   std::vector<int32_t> tree_lvl;  // level offsets (internal body order)
   std::vector<int32_t> tree_mid;  // per level: first leaf (bodies before it have children)
-  std::vector<int32_t> tree_variant;  // per level: TREE_UP_* chosen by the tuner
   DevForest F{};                       // the forest tree by tree (persistent kernel)
   DevTreeT<float> Tf{};                // FP32 elimination of the mixed tree form
   // loop solver: right-hand side and solution of a pass through the chain's
   // factors ([5][K]), and the chain's response at its two ends per breaker row
   double *loop_b = nullptr, *loop_x = nullptr, *loop_w = nullptr;
   int loop_rows = 0;  // rows of the loop breaker (3 or 5)
-  int tree_mode = 0;                   // 0: level-scheduled launches; 8 or 4: persistent kernel, lanes
+  int tree_mode = 0;                   // 0: level-scheduled launches; 128 or 64: persistent kernel, threads
   double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
   int *d_status = nullptr;
   unsigned long long *d_max = nullptr;
@@ -726,31 +725,23 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
 
 }  // extern "C"
 
-// Level schedule of the tree's upward pass.  Each level's bodies with
-// children can be eliminated one per thread or by a group of 8 or 4 lanes
-// per body (k_tree.cu); which is faster depends on how many such bodies the
-// level has and on their rows.  The tuner runs the body and joint kernels
-// on the initial state, then, deepest level first, times every variant on
-// the level (best of two CUDA-event timings) and keeps the fastest; every
-// variant computes the same outputs, so the level's results are in place for
-// the next level up.  Then the whole elimination with that schedule is
-// timed against the persistent forest kernel (one block per tree, both
-// passes in one launch) and the faster is kept.  MABD_TREE_VARIANT=0|1|2
-// forces one level variant (and the level path); MABD_TREE_MODE=levels|
-// forest8|forest4 forces the path.
+// Path of the tree elimination: one launch per level (upward deepest
+// first, then downward), or the persistent forest kernel with one block of
+// 128 or 64 threads per tree (both passes in one launch).  The tuner runs
+// the body and joint kernels on the initial state, then times each path on
+// it (best of two CUDA-event timings; the downward pass moves the state, so
+// it is saved and put back around every trial) and keeps the fastest.
+// MABD_TREE_MODE=levels|forest128|forest64 forces the path.
 template <typename S>
 static mabd_status tune_tree_t(mabd_ctx *ctx, const DevTreeT<S> &TT) {
   const auto &lv = ctx->tree_lvl;
-  const auto &mid = ctx->tree_mid;
   const int nl = (int)lv.size() - 1;
-  ctx->tree_variant.assign(std::max(nl, 0), TREE_UP_THREAD);
-  const char *fv = std::getenv("MABD_TREE_VARIANT");
-  if (fv) {
-    const int v = std::atoi(fv);
-    if (v >= 0 && v < TREE_UP_NVARIANTS) ctx->tree_variant.assign(std::max(nl, 0), v);
-    // a forced level variant also forces the level-scheduled path
-    if (!std::getenv("MABD_TREE_MODE")) return MABD_OK;
+  const char *fm = std::getenv("MABD_TREE_MODE");
+  if (fm) {
+    ctx->tree_mode = std::strcmp(fm, "forest128") == 0 ? 128 : (std::strcmp(fm, "forest64") == 0 ? 64 : 0);
+    return MABD_OK;
   }
+  if (ctx->F.ntrees <= 0) return MABD_OK;
   cudaStream_t s = ctx->stream;
   const StepParams &p = ctx->sp;
   // inputs of the elimination in its precision
@@ -764,63 +755,34 @@ static mabd_status tune_tree_t(mabd_ctx *ctx, const DevTreeT<S> &TT) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (int l = nl - 1; l >= 1 && !fv; --l) {
-    if (mid[l] <= lv[l]) {
-      launch_tree_up(ctx->B, ctx->J, TT, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s);
-      continue;
-    }
-    float best = 1e30f;
-    for (int v = 0; v < TREE_UP_NVARIANTS; ++v)
-      for (int rep = 0; rep < 2; ++rep) {
-        CK(cudaEventRecord(e0, s));
-        launch_tree_up(ctx->B, ctx->J, TT, lv[l], mid[l], lv[l + 1], false, p, ctx->d_status, s, v);
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          ctx->tree_variant[l] = v;
-        }
-      }
-  }
-  // whole elimination: the tuned level schedule against the persistent
-  // kernel (8 or 4 lanes per body with children); the downward pass moves
-  // the state, so it is saved and put back around every trial
   const int M = ctx->B.M;
-  const char *fm = std::getenv("MABD_TREE_MODE");
-  if (fm) {
-    ctx->tree_mode = std::strcmp(fm, "forest8") == 0 ? 8 : (std::strcmp(fm, "forest4") == 0 ? 4 : 0);
-  } else if (ctx->F.ntrees > 0) {
-    double *sq = nullptr;
-    CK(cudaMallocAsync((void **)&sq, 24 * (size_t)M * sizeof(double), s));
-    CK(cudaMemcpyAsync(sq, ctx->B.q, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(sq + 12 * (size_t)M, ctx->B.qd, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
-    float best = 1e30f;
-    for (int mode : {0, 8, 4})
-      for (int rep = 0; rep < 2; ++rep) {
-        CK(cudaEventRecord(e0, s));
-        if (mode == 0) {
-          for (int l = nl - 1; l >= 0; --l)
-            launch_tree_up(ctx->B, ctx->J, TT, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s,
-                           ctx->tree_variant[l]);
-          for (int l = 0; l < nl; ++l) launch_tree_down(ctx->B, ctx->J, TT, lv[l], lv[l + 1], p, ctx->d_status, s);
-        } else {
-          launch_tree_forest(ctx->B, ctx->J, TT, ctx->F, p, ctx->d_status, s, mode);
-        }
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          ctx->tree_mode = mode;
-        }
-        CK(cudaMemcpyAsync(ctx->B.q, sq, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(ctx->B.qd, sq + 12 * (size_t)M, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+  double *sq = nullptr;
+  CK(cudaMallocAsync((void **)&sq, 24 * (size_t)M * sizeof(double), s));
+  CK(cudaMemcpyAsync(sq, ctx->B.q, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sq + 12 * (size_t)M, ctx->B.qd, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+  float best = 1e30f;
+  for (int mode : {0, 128, 64})
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(e0, s));
+      if (mode == 0) {
+        for (int l = nl - 1; l >= 0; --l)
+          launch_tree_up(ctx->B, ctx->J, TT, lv[l], lv[l + 1], l == 0, p, ctx->d_status, s);
+        for (int l = 0; l < nl; ++l) launch_tree_down(ctx->B, ctx->J, TT, lv[l], lv[l + 1], p, ctx->d_status, s);
+      } else {
+        launch_tree_forest(ctx->B, ctx->J, TT, ctx->F, p, ctx->d_status, s, mode);
       }
-    CK(cudaFreeAsync(sq, s));
-  }
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        ctx->tree_mode = mode;
+      }
+      CK(cudaMemcpyAsync(ctx->B.q, sq, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(ctx->B.qd, sq + 12 * (size_t)M, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
+    }
+  CK(cudaFreeAsync(sq, s));
   CK(cudaStreamSynchronize(s));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1580,11 +1542,22 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
           if ((int)bt.size() <= l) bt.resize(l + 1);
           bt[l].push_back(i);
         }
+      // deepest trees first (then the larger): the persistent kernel's blocks
+      // take trees in this order, so the longest dependent chains start first
+      std::vector<int32_t> tsz(ntrees, 0), torder(ntrees);
+      for (int t = 0; t < ntrees; ++t) {
+        for (auto &lvl : bucket[t]) tsz[t] += (int32_t)lvl.size();
+        torder[t] = t;
+      }
+      std::stable_sort(torder.begin(), torder.end(), [&](int32_t a, int32_t b) {
+        if (bucket[a].size() != bucket[b].size()) return bucket[a].size() > bucket[b].size();
+        return tsz[a] > tsz[b];
+      });
       std::vector<int32_t> tlvl(std::max(ntrees, 1)), tnl(std::max(ntrees, 1)), flo, fmid, ford;
       for (int t = 0; t < ntrees; ++t) {
         tlvl[t] = (int32_t)flo.size();
-        tnl[t] = (int32_t)bucket[t].size();
-        for (auto &lvl : bucket[t]) {
+        tnl[t] = (int32_t)bucket[torder[t]].size();
+        for (auto &lvl : bucket[torder[t]]) {
           flo.push_back((int32_t)ford.size());
           for (int i : lvl)
             if (tord.ccount[i] > 0) ford.push_back(i);
@@ -1804,12 +1777,8 @@ static void enqueue_tree_solve(mabd_ctx *ctx, const DevTreeT<S> &T, cudaStream_t
   }
   const auto &lv = ctx->tree_lvl;
   const int nl = (int)lv.size() - 1;
-  const auto &mid = ctx->tree_mid;
   for (int l = nl - 1; l >= 0; --l)
-    run(ctx, "tree_up", [&] {
-      launch_tree_up(ctx->B, ctx->J, T, lv[l], mid[l], lv[l + 1], l == 0, p, ctx->d_status, s,
-                     ctx->tree_variant.empty() ? TREE_UP_THREAD : ctx->tree_variant[l]);
-    });
+    run(ctx, "tree_up", [&] { launch_tree_up(ctx->B, ctx->J, T, lv[l], lv[l + 1], l == 0, p, ctx->d_status, s); });
   for (int l = 0; l < nl; ++l)
     run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, T, lv[l], lv[l + 1], p, ctx->d_status, s); });
 }
@@ -2566,10 +2535,9 @@ extern "C" {
 mabd_status mabd_tree_schedule(mabd_ctx *ctx, int32_t *counts) {
   if (!ctx || !counts) return MABD_ERR_INVALID_ARG;
   if (!ctx->frozen) return MABD_ERR_BAD_STATE;
-  for (int v = 0; v < TREE_UP_NVARIANTS; ++v) counts[v] = 0;
-  const int nl = (int)ctx->tree_variant.size();
-  for (int l = 1; l < nl; ++l)
-    if (ctx->tree_mid[l] > ctx->tree_lvl[l]) ++counts[ctx->tree_variant[l]];
+  const int nl = (int)ctx->tree_lvl.size() - 1;
+  counts[0] = std::max(nl, 0);
+  counts[1] = counts[2] = 0;
   counts[3] = ctx->tree_mode;
   return MABD_OK;
 }

@@ -477,23 +477,18 @@ void launch_seg_up_back(const SegLevel &in, const SegLevel &next, int T, int pas
 // sets the kernels' shared-memory limits (once per process and device)
 cudaError_t seg_init();
 
-// tree (k_tree.cu): one launch per level, deepest first, then root first
-// level [lo, hi) of the body order: T.order[lo, mid) lists its bodies with
-// children and T.order[mid, hi) its leaves; the roots' level (roots = true)
-// is run by one kernel
+// tree (k_tree.cu): one launch per level, deepest first, then root first;
+// level [lo, hi) of the body order T.order (roots = true: the roots' level,
+// bodies lo .. hi - 1); a 16-lane group per body of the upward pass
 // whole tree elimination (upward and downward passes) of every tree of the
-// forest in one launch, one block per tree; lanes = 8 or 4 per body with children
+// forest in one launch, one block of `threads` (128 or 64) per tree
 // (S = double or float, the elimination's type, for these three launchers)
 template <typename S>
 void launch_tree_forest(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, const DevForest &F,
-                        const StepParams &p, int *status, cudaStream_t s, int lanes);
-// variants of the upward pass for the bodies with children: one thread per
-// body, or a group of 8 or 4 lanes per body (chosen per level by the tuner)
-enum { TREE_UP_THREAD = 0, TREE_UP_COOP8 = 1, TREE_UP_COOP4 = 2, TREE_UP_NVARIANTS = 3 };
+                        const StepParams &p, int *status, cudaStream_t s, int threads);
 template <typename S>
-void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int lo, int mid,
-                    int hi, bool roots, const StepParams &p, int *status, cudaStream_t s,
-                    int variant = TREE_UP_THREAD);
+void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int lo, int hi, bool roots,
+                    const StepParams &p, int *status, cudaStream_t s);
 template <typename S>
 void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int lo, int hi,
                       const StepParams &p, int *status, cudaStream_t s);

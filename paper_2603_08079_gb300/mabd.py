@@ -283,11 +283,12 @@ class Solver:
         self._check("mabd_set_preconditioner", self._lib.mabd_set_preconditioner(self.ctx, _ptr(p)))
 
     def tree_schedule(self) -> dict:
-        """Levels of the tree's upward pass per variant (thread, 8 lanes, 4 lanes)."""
+        """Levels below the roots and the path (levels, or the persistent
+        kernel's block size)."""
         c = np.zeros(4, dtype=np.int32)
         self._check("mabd_tree_schedule", self._lib.mabd_tree_schedule(self.ctx, _ptr(c)))
-        return {"thread": int(c[0]), "lanes8": int(c[1]), "lanes4": int(c[2]),
-                "path": {0: "levels", 8: "forest8", 4: "forest4"}.get(int(c[3]), int(c[3]))}
+        return {"levels": int(c[0]),
+                "path": {0: "levels", 128: "forest128", 64: "forest64"}.get(int(c[3]), int(c[3]))}
 
     def lpc_fallbacks(self) -> int:
         n = C.c_int32(0)

@@ -89,13 +89,12 @@ def test_full_size_tree(ora):
 
 @pytest.fixture
 def forced_variant():
-    """Sets MABD_TREE_VARIANT (or MABD_TREE_MODE) for the contexts created
-    inside the test."""
+    """Sets MABD_TREE_MODE for the contexts created inside the test."""
     import os
-    keys = ("MABD_TREE_VARIANT", "MABD_TREE_MODE")
+    keys = ("MABD_TREE_MODE",)
     old = {k: os.environ.get(k) for k in keys}
 
-    def set_(v, key="MABD_TREE_VARIANT"):
+    def set_(v, key="MABD_TREE_MODE"):
         os.environ[key] = str(v)
 
     yield set_
@@ -106,17 +105,11 @@ def forced_variant():
             os.environ[k] = v
 
 
-def level_counts(sched):
-    return [sched["thread"], sched["lanes8"], sched["lanes4"]]
-
-
-@pytest.mark.parametrize("variant", [0, 1, 2])
-def test_every_upward_variant(ora, forced_variant, variant):
-    """Each elimination variant of the bodies with children (one thread per
-    body, 8 lanes, 4 lanes) alone: hinge and mixed trees, a root with two
-    world joints, a fixed-base assembly batch."""
+def test_level_scheduled_path(ora, forced_variant):
+    """One launch per level (lane group per body): hinge and mixed trees, a
+    root with two world joints, a fixed-base assembly batch."""
     need_gpu()
-    forced_variant(variant)
+    forced_variant("levels")
     cases = [scenes.random_tree(3000, seed=2),
              scenes.random_small("tree", 30, seed=7),
              scenes.assemblies(16, seed=3)]
@@ -124,15 +117,14 @@ def test_every_upward_variant(ora, forced_variant, variant):
         s = gpu_solver(sc, solver="tree")
         try:
             sched = s.tree_schedule()
-            c = level_counts(sched)
-            assert sched["path"] == "levels" and sum(c) > 0 and c[variant] == sum(c)
+            assert sched["path"] == "levels" and sched["levels"] > 0
             q, qd = scenes.perturb_state(sc, seed=11, rot=0.05, vel=0.3)
             assert_parity(ora, sc, q, qd, solver=s)
         finally:
             s.close()
 
 
-@pytest.mark.parametrize("mode", ["forest8", "forest4"])
+@pytest.mark.parametrize("mode", ["forest128", "forest64"])
 def test_persistent_forest_kernel(ora, forced_variant, mode):
     """One block per tree, both passes in one launch: forests of fixed-base
     assemblies (many small trees), a single large tree, mixed joints, and
@@ -160,14 +152,13 @@ def test_persistent_forest_kernel(ora, forced_variant, mode):
 
 
 def test_tuned_schedule(ora):
-    """The tuner picks a variant per level and a path; the tuned step keeps
-    parity."""
+    """The tuner picks a path; the tuned step keeps parity."""
     need_gpu()
     for sc in (scenes.random_tree(20000, seed=2), scenes.assemblies(256, seed=3)):
         s = gpu_solver(sc, solver="tree")
         try:
             sched = s.tree_schedule()
-            assert sum(level_counts(sched)) > 0 and sched["path"] in ("levels", "forest8", "forest4")
+            assert sched["levels"] > 0 and sched["path"] in ("levels", "forest128", "forest64")
             assert_parity(ora, sc, sc["q"], sc["qdot"], solver=s)
         finally:
             s.close()

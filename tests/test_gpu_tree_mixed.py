@@ -19,7 +19,7 @@ TOL = 1e-6
 
 @pytest.fixture
 def forced():
-    keys = ("MABD_TREE_VARIANT", "MABD_TREE_MODE")
+    keys = ("MABD_TREE_MODE",)
     old = {k: os.environ.get(k) for k in keys}
 
     def set_(key, v):
@@ -89,18 +89,17 @@ def test_root_with_two_world_joints(ora):
     assert_parity(ora, sc, q, qd, tol=TOL, gpu_kw=F32)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
-def test_every_upward_variant(ora, forced, variant):
-    """The FP32 elimination with each variant for the bodies with children."""
+def test_level_scheduled_path(ora, forced):
+    """The FP32 elimination, one launch per level."""
     need_gpu()
-    forced("MABD_TREE_VARIANT", variant)
+    forced("MABD_TREE_MODE", "levels")
     for sc in (scenes.random_tree(3000, seed=2), scenes.random_small("tree", 30, seed=7),
                scenes.assemblies(16, seed=3)):
         q, qd = scenes.perturb_state(sc, seed=11, rot=0.05, vel=0.3)
         assert_parity(ora, sc, q, qd, tol=TOL, gpu_kw=F32)
 
 
-@pytest.mark.parametrize("mode", ["forest8", "forest4"])
+@pytest.mark.parametrize("mode", ["forest128", "forest64"])
 def test_persistent_forest_kernel(ora, forced, mode):
     need_gpu()
     forced("MABD_TREE_MODE", mode)
