@@ -243,13 +243,17 @@ __device__ __noinline__ void up_body(const DevBodies &B, const DevJoints &J, con
     const int c0 = T.cfirst[j];
 #pragma unroll 1
     for (int c = c0; c < c0 + nch; ++c) {
+      // the child's rows issued together (a ball joint's rows 3 and 4 are zero)
+      S u[NJ];
+#pragma unroll
+      for (int t = 0; t < NJ; ++t) u[t] = act ? T.U[(size_t)(NJ * l + t) * M + c] : S(0);
       if (act) f -= T.v[(size_t)l * M + c];
       const int Cc = J.type[T.pjoint[c]] == 0 ? 3 : 5;
-#pragma unroll 1
-      for (int t = 0; t < Cc; ++t) {
-        const S u = act ? T.U[(size_t)(NJ * l + t) * M + c] : S(0);
 #pragma unroll
-        for (int q = 0; q < 12; ++q) h[q] += u * gshfl(gm, u, q);
+      for (int t = 0; t < NJ; ++t) {
+        if (t >= Cc) break;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) h[q] += u[t] * gshfl(gm, u[t], q);
       }
     }
     b[0] = act ? f : S(0);
