@@ -16,6 +16,7 @@
 // alpha = 0 and s = 1 it is block Jacobi.
 #include <cuda_bf16.h>
 
+#include "lpc_apply.cuh"
 #include "mabd_f32.cuh"
 
 namespace mabd {
@@ -344,59 +345,19 @@ void launch_lpc_forward(const LpcGraph &G, const LpcNet &N, const LpcAct &A, boo
 // ---------------------------------------------------------------------------
 // preconditioner application inside the FP32 PCG ([5][K] vectors, rows 0-2)
 // ---------------------------------------------------------------------------
-// y_k = s_k (t_k - sum_{lower e} alpha_e E_e t_n)
 __global__ void __launch_bounds__(128) k_lpc_y(LpcGraph G, LpcAct A, const float *t, float *y,
                                                const int *iter) {
   if (iter && iter[1]) return;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int K = G.K;
-  if (k >= K) return;
-  float v[3] = {t[k], t[(size_t)K + k], t[2 * (size_t)K + k]};
-  for (int e = G.off[k]; e < G.off[k + 1]; ++e) {
-    const int n = G.nbr[e];
-    if (n >= k) continue;
-    const float al = A.alpha[e];
-    const float *Ee = A.E + (size_t)9 * e;
-    const float tn[3] = {t[n], t[(size_t)K + n], t[2 * (size_t)K + n]};
-#pragma unroll
-    for (int r = 0; r < 3; ++r) v[r] -= al * (Ee[3 * r] * tn[0] + Ee[3 * r + 1] * tn[1] + Ee[3 * r + 2] * tn[2]);
-  }
-  const float sk = A.s[k];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) y[(size_t)r * K + k] = sk * v[r];
+  if (k < G.K) lpc_y_one(G, A, t, y, k);
 }
 
-// z_k = C_k^T (s_k y_k - sum_{upper e} alpha_rev(e) E_e s_n y_n); partial r.z
+// z = C^T G^T y and the per-block partial sums of r . z
 __global__ void __launch_bounds__(128) k_lpc_z(LpcGraph G, LpcAct A, const float *y, const float *r,
                                                float *z, double *part, const int *iter) {
   if (iter && iter[1]) return;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int K = G.K;
-  float rz = 0.f;
-  if (k < K) {
-    const float sk = A.s[k];
-    float u[3] = {sk * y[k], sk * y[(size_t)K + k], sk * y[2 * (size_t)K + k]};
-    for (int e = G.off[k]; e < G.off[k + 1]; ++e) {
-      const int n = G.nbr[e];
-      if (n <= k) continue;
-      const float al = A.alpha[G.rev[e]] * A.s[n];
-      const float *Ee = A.E + (size_t)9 * e;
-      const float yn[3] = {y[n], y[(size_t)K + n], y[2 * (size_t)K + n]};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) u[c] -= al * (Ee[3 * c] * yn[0] + Ee[3 * c + 1] * yn[1] + Ee[3 * c + 2] * yn[2]);
-    }
-    const float *Cp = A.C + (size_t)6 * k;
-    // z = C^T u with C packed lower (c00 c10 c11 c20 c21 c22)
-    const float z0 = Cp[0] * u[0] + Cp[1] * u[1] + Cp[3] * u[2];
-    const float z1 = Cp[2] * u[1] + Cp[4] * u[2];
-    const float z2 = Cp[5] * u[2];
-    z[k] = z0;
-    z[(size_t)K + k] = z1;
-    z[2 * (size_t)K + k] = z2;
-    z[3 * (size_t)K + k] = 0.f;
-    z[4 * (size_t)K + k] = 0.f;
-    rz = r[k] * z0 + r[(size_t)K + k] * z1 + r[2 * (size_t)K + k] * z2;
-  }
+  const float rz = k < G.K ? lpc_z_one(G, A, y, r, z, k) : 0.f;
   __shared__ double s1[128];
   s1[threadIdx.x] = (double)rz;
   __syncthreads();

@@ -72,6 +72,7 @@ struct mabd_ctx {
   DevTree T{};
   DevPCG P{};
   DevPCG32 P32{};
+  int p32_nb[2] = {0, 0};  // blocks of the persistent FP32 solve (block Jacobi, learned); 0: off
   // learned preconditioner of the mixed PCG (joint graph, activations, weights)
   bool lpc_graph = false, lpc_on = false;
   LpcGraph lg{};
@@ -195,6 +196,7 @@ mabd_status map_status_bits(int bits) {
   if (bits & ST_NONFINITE) return MABD_ERR_NONFINITE;
   if (bits & ST_NOT_SPD) return MABD_ERR_NOT_SPD;
   if (bits & (ST_POLAR_NOCONV | ST_PCG_NOCONV)) return MABD_ERR_NO_CONVERGENCE;
+  if (bits & ST_TIMEOUT) return MABD_ERR_TIMEOUT;
   return MABD_OK;
 }
 
@@ -1385,6 +1387,8 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     Q.part = dnew<double>(ctx, 2 * (size_t)std::max(Q.nblocks, 1), ok);
     Q.scal = dnew<double>(ctx, 8, ok);
     Q.iter = dnew<int>(ctx, 2, ok);
+    Q.ppart = dnew<double>(ctx, 3 * (size_t)P32_MAXB, ok);
+    Q.bar = dnew<unsigned>(ctx, 4, ok);
     if (!ok) {
       free_all(ctx);
       return MABD_ERR_OUT_OF_MEMORY;
@@ -1392,6 +1396,20 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     if (!ctx->h_iter) {
       CK(cudaMallocHost((void **)&ctx->h_iter, 2 * sizeof(int)));
       CK(cudaMallocHost((void **)&ctx->h_scal, 8 * sizeof(double)));
+    }
+    // MABD_PCG_PERSIST=1: the persistent solve (one cooperative launch per
+    // solve, the loop and its convergence test on the device) when the
+    // device can run it.  Off by default: on the 64x64x16 net it measured
+    // 63.4 ms per step against 57.9 ms for one launch per step of an
+    // iteration (both ~0.1 ms per iteration, bound by the gathers' memory
+    // latency; the persistent form adds five grid barriers per iteration).
+    const char *pe = std::getenv("MABD_PCG_PERSIST");
+    int coop = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (coop && pe && pe[0] == '1') {
+      ctx->p32_nb[0] = p32_persist_blocks(ctx->J.xj, false);
+      ctx->p32_nb[1] = p32_persist_blocks(ctx->J.xj, true);
     }
   }
   if (solver == MABD_SOLVER_PCG && !mixed) {
@@ -1920,8 +1938,24 @@ static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, d
   if (!learned) P.t = nullptr;
   const LpcGraph *lg = learned ? &ctx->lg : nullptr;
   const LpcAct *la = learned ? &ctx->la : nullptr;
-  run(ctx, "p32_setup", [&] { launch_p32_setup(ctx->B, ctx->J, P, rhs, rtol, ctx->d_status, s, lg, la); });
   const int max_it = ctx->cfg.pcg_max_iters;
+  const int nb = ctx->p32_nb[learned ? 1 : 0];
+  if (nb > 0) {
+    cudaError_t e = cudaSuccess;
+    run(ctx, "p32_solve", [&] {
+      e = launch_p32_persist(ctx->B, ctx->J, ctx->I, P, lg, la, rhs, rtol, max_it, out, learned ? nullptr : acc,
+                             ctx->d_status, nb, s);
+    });
+    CK(e);
+    CK(cudaMemcpyAsync(ctx->h_scal, ctx->P32.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_iter, ctx->P32.iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->pcg_last_iters += ctx->h_iter[0];
+    const double bb = ctx->h_scal[4], rr = ctx->h_scal[3];
+    ctx->pcg_last_rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    return MABD_OK;
+  }
+  run(ctx, "p32_setup", [&] { launch_p32_setup(ctx->B, ctx->J, P, rhs, rtol, ctx->d_status, s, lg, la); });
   int done = 0;
   for (int launched = 0; launched < max_it && !done; launched += PCG_CHUNK) {
     for (int i = 0; i < PCG_CHUNK; ++i)
@@ -2284,7 +2318,7 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
   if (st) return st;
   static const char *known[] = {"body_prep", "joint_prep", "chain_gram", "mx_body_prep", "mx_joint_prep",
                                 "mx_chain_gram", "mx_res_body", "mx_res_joint", "cr_rhs", "mx_final",
-                                "p32_setup", "p32_iteration", "p32_finish", "lpc_blocks", "lpc_forward",
+                                "p32_setup", "p32_iteration", "p32_solve", "p32_finish", "lpc_blocks", "lpc_forward",
                                 "tree_forest",
                                 "cr_level", "cr_reduce", "cr_combine", "cr_tail", "loop_schur",
                                 "cr_top", "cr_back", "tree_up", "tree_down", "pcg_setup",

@@ -17,6 +17,7 @@ enum : int {
   ST_POLAR_NOCONV = 4,
   ST_NOT_SPD = 8,
   ST_PCG_NOCONV = 16,
+  ST_TIMEOUT = 32,  // a bounded device-side wait gave up
 };
 
 // Structured inverse of Hbar_A = M_A/h^2 + Kbar_A for a body whose second
@@ -212,7 +213,12 @@ struct DevPCG32 {
   // learned preconditioner (t null: block Jacobi): t = C r, y = G t
   float *t, *y;               // [5][K]
   const float *Cl;            // [K][6] inverse Cholesky factors C_k of the learned form
+  // persistent solve: per-block partial sums [3][P32_MAXB] and the grid
+  // barrier's words (arrivals, generation, error flag, spare)
+  double *ppart;
+  unsigned *bar;
 };
+constexpr int P32_MAXB = 4096;  // blocks of the persistent solve at most
 
 // Learned block preconditioner of the dual PCG (k_lpc.cu), ball joints.
 // Joints are the nodes of a graph whose edges join joints sharing a free
@@ -399,6 +405,12 @@ void launch_p32_iteration(const DevBodies &B, const DevJoints &J, const DevIncid
                           const DevPCG32 &P, int max_iters, cudaStream_t s, const LpcGraph *lg = nullptr,
                           const LpcAct *la = nullptr);
 void launch_p32_finish(const DevJoints &J, const DevPCG32 &P, double *out, double *acc, cudaStream_t s);
+// the whole solve in one cooperative launch of nblocks co-resident blocks
+// (p32_persist_blocks: the most that fit, 0 if the query fails)
+int p32_persist_blocks(bool xj, bool lpc);
+cudaError_t launch_p32_persist(const DevBodies &B, const DevJoints &J, const DevIncidence &I, const DevPCG32 &P,
+                               const LpcGraph *lg, const LpcAct *la, const double *rhs, double rtol,
+                               int max_iters, double *out, double *acc, int *status, int nblocks, cudaStream_t s);
 
 // learned preconditioner (k_lpc.cu)
 // C_k and the normalized blocks E of the current state (needs R/Rf, hinvf)

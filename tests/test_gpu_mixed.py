@@ -151,6 +151,30 @@ def test_mixed_full_size_net(ora):
     assert max(e_qd, e_lam) <= TOL
 
 
+@pytest.mark.parametrize("dims", [(6, 6, 3), (24, 24, 8)])
+def test_persistent_and_per_launch_pcg_agree(ora, dims, monkeypatch):
+    """The FP32 PCG as one cooperative launch per solve (device-side loop and
+    convergence test) and as one launch per step of an iteration: both meet
+    the oracle at the mixed bound; their iteration counts differ by at most a
+    few (the partial sums are blocked differently)."""
+    need_gpu()
+    sc = scenes.jittered_net(*dims, seed=4)
+    q, qd = scenes.perturb_state(sc, seed=3, rot=0.05, vel=0.2)
+    res = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("MABD_PCG_PERSIST", mode)
+        s = gpu_solver(sc, **dict(MIXED, refine_steps=NET_SWEEPS))
+        try:
+            q1, qd1, lam, st = gpu_step(s, q, qd)
+        finally:
+            s.close()
+        res[mode] = (qd1, lam, st[0]["pcg_iters"])
+    _, oqd, olam, _ = oracle_step(ora, sc, q, qd)
+    for mode, (qd1, lam, it) in res.items():
+        assert rel(qd1, oqd) <= TOL and rel(lam, olam) <= TOL, (mode, rel(qd1, oqd), rel(lam, olam))
+    assert abs(res["1"][2] - res["0"][2]) <= max(3, res["0"][2] // 20), (res["1"][2], res["0"][2])
+
+
 def test_mixed_rejects_other_topologies():
     """MABD_MIXED (FP64 dual elimination) has no tree form: the tree's mixed
     form is MABD_MIXED_FP32_DUAL (tests/test_gpu_tree_mixed.py)."""
