@@ -139,11 +139,14 @@ typedef struct {
   int32_t solver;       /* MABD_SOLVER_*; AUTO picks chain, then tree, then loop (FP64), then PCG */
   int32_t pcg_max_iters;/* cap on PCG iterations (>= 1) */
   double pcg_rtol;      /* PCG stops when |r| <= pcg_rtol |b|.  The mixed forms' FP32
-                           PCG runs one launch per step of an iteration; with
-                           MABD_PCG_PERSIST=1 in the environment at
-                           mabd_prefactor it runs each solve as one cooperative
-                           launch whose phases meet at a grid barrier; a barrier
-                           wait that gives up (about a second) ends the step with
+                           PCG with the learned preconditioner on (ball-joint
+                           graphs) runs each solve as one cooperative launch in
+                           the normalized dual space (MABD_PCG_NORMALIZED=0 in
+                           the environment turns that off); otherwise one launch
+                           per step of an iteration, or with MABD_PCG_PERSIST=1
+                           one cooperative launch per solve.  In a cooperative
+                           solve the phases meet at a grid barrier; a wait that
+                           gives up (about a second) ends the step with
                            MABD_ERR_TIMEOUT. */
   int32_t refine_steps; /* MABD_MIXED: FP64 correction sweeps per step, 0..MABD_MAX_REFINE */
   int32_t residual_rhs; /* 1: bottom KKT rhs is -C(q_n) (Sec. 5 footnote); 0: zero as printed */

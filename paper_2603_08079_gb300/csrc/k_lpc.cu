@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(128) k_lpc_edges(DevBodies B, DevJoints J, Lpc
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int c = 0; c < 3; ++c) T[3 * r + c] = Ck[3 * r] * S[c] + Ck[3 * r + 1] * S[3 + c] + Ck[3 * r + 2] * S[6 + c];
-    float *Ee = A.E + (size_t)9 * e;
+    float *Ee = A.E + (size_t)LPC_ES * e;
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(128) k_lpc_features(LpcGraph G, LpcAct A) {
   float f2 = 0.f, fmx = 0.f, ftr = 0.f, flo = 0.f;
   int lower = 0;
   for (int e = G.off[k]; e < G.off[k + 1]; ++e) {
-    const float *Ee = A.E + (size_t)9 * e;
+    const float *Ee = A.E + (size_t)LPC_ES * e;
     float n2 = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) n2 += Ee[i] * Ee[i];
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(128) k_lpc_head_edge(LpcGraph G, LpcNet N, Lpc
       continue;
     }
     float nrm, tr;
-    edge_feats(A.E + (size_t)9 * e, nrm, tr);
+    edge_feats(A.E + (size_t)LPC_ES * e, nrm, tr);
     float z = P[LPC_OFF_CE] + P[LPC_OFF_WE] * nrm + P[LPC_OFF_WE + 1] * tr;
 #pragma unroll
     for (int r = 0; r < LPC_R; ++r) z += a[r] * A.b[(size_t)LPC_R * n + r];

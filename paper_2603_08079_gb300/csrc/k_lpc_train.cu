@@ -76,7 +76,7 @@ __device__ __forceinline__ void spmv_row(const LpcGraph &G, const LpcAct &A, int
     }
     if (scale_n) c *= scale_n[n];
     float y[3];
-    mv3f(A.E + (size_t)9 * e, in + (size_t)3 * n, y);
+    mv3f(A.E + (size_t)LPC_ES * e, in + (size_t)3 * n, y);
     out[0] += sgn * c * y[0];
     out[1] += sgn * c * y[1];
     out[2] += sgn * c * y[2];
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(128) k_lpc_l4b(LpcGraph G, LpcAct A, LpcTrainW
       const int n = G.nbr[e];
       if (n >= k) continue;
       float y[3];
-      mv3f(A.E + (size_t)9 * e, wi + (size_t)3 * n, y);
+      mv3f(A.E + (size_t)LPC_ES * e, wi + (size_t)3 * n, y);
       W.dalpha[e] -= q[0] * y[0] + q[1] * y[1] + q[2] * y[2];
     }
   }
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(128) k_lpc_l7(LpcGraph G, LpcAct A, LpcTrainWo
       const int n = G.nbr[e];
       if (n >= k) continue;
       float y[3];
-      mv3f(A.E + (size_t)9 * e, gui + (size_t)3 * n, y);
+      mv3f(A.E + (size_t)LPC_ES * e, gui + (size_t)3 * n, y);
       W.dalpha[e] -= tk[0] * y[0] + tk[1] * y[1] + tk[2] * y[2];
     }
   }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(128) k_lpc_head_bwd(LpcGraph G, LpcAct A, LpcN
         const float dz = W.dalpha[e];
 #pragma unroll
         for (int r = 0; r < LPC_R; ++r) da[r] += dz * A.b[(size_t)LPC_R * n + r];
-        const float *Ee = A.E + (size_t)9 * e;
+        const float *Ee = A.E + (size_t)LPC_ES * e;
         float n2 = 0.f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) n2 += Ee[i] * Ee[i];

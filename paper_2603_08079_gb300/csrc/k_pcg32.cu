@@ -11,12 +11,11 @@
 // step of an iteration (host-paced), and a persistent cooperative kernel
 // that keeps the whole solve on the device, the phases separated by a grid
 // barrier whose waits are bounded (k_p32_persist).
+#include "grid_sync.cuh"
 #include "lpc_apply.cuh"
 #include "mabd_f32.cuh"
 
 namespace mabd {
-
-constexpr int P32_THREADS = 256;
 
 __device__ __forceinline__ int pkf(int r, int c) { return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r; }
 
@@ -382,59 +381,6 @@ __global__ void __launch_bounds__(128) k_p32_finish(DevJoints J, DevPCG32 P, dou
 // ---------------------------------------------------------------------------
 // persistent solve: one cooperative launch per solve
 // ---------------------------------------------------------------------------
-// Grid barrier over the co-resident blocks of a cooperative launch: bar[0]
-// counts arrivals, bar[1] is the generation, bar[2] an error flag.  A wait
-// gives up after P32_BAR_SPINS polls (about a second), sets the flag and
-// returns; every block then leaves the solve at its next barrier.
-constexpr unsigned P32_BAR_SPINS = 1u << 24;
-
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblk, unsigned &gen) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *vb = bar;
-    __threadfence();
-    if (atomicAdd(&bar[0], 1u) == nblk - 1) {
-      atomicExch(&bar[0], 0u);
-      __threadfence();
-      atomicExch(&bar[1], gen + 1);
-    } else {
-      unsigned spins = 0;
-      while (vb[1] == gen) {
-        if (++spins > P32_BAR_SPINS) {
-          atomicExch(&bar[2], 1u);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  ++gen;
-  return ((volatile unsigned *)bar)[2] == 0u;
-}
-
-// sum over the block of one value per thread (every thread gets it)
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int o = P32_THREADS / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double s = sh[0];
-  __syncthreads();
-  return s;
-}
-
-// the grid's sum of the per-block partials part[0 .. n): every block adds
-// them in the same order, so every block holds the same value
-__device__ __forceinline__ double grid_sum(const double *part, int n, double *sh) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += P32_THREADS) v += ((const volatile double *)part)[i];
-  return block_sum(v, sh);
-}
-
 // The iterations of an FP32 PCG solve in one launch, from the state that
 // the setup kernels left (grid-stride loops over joints and bodies; partial
 // sums per block in P.ppart: [0] r.z, [1] r.r, [2] p.Sp).  LPC: the learned

@@ -15,7 +15,7 @@ __device__ __forceinline__ void lpc_y_one(const LpcGraph &G, const LpcAct &A, co
     const int n = G.nbr[e];
     if (n >= k) continue;
     const float al = A.alpha[e];
-    const float *Ee = A.E + (size_t)9 * e;
+    const float *Ee = A.E + (size_t)LPC_ES * e;
     const float tn[3] = {t[n], t[(size_t)K + n], t[2 * (size_t)K + n]};
 #pragma unroll
     for (int r = 0; r < 3; ++r) v[r] -= al * (Ee[3 * r] * tn[0] + Ee[3 * r + 1] * tn[1] + Ee[3 * r + 2] * tn[2]);
@@ -35,7 +35,7 @@ __device__ __forceinline__ float lpc_z_one(const LpcGraph &G, const LpcAct &A, c
     const int n = G.nbr[e];
     if (n <= k) continue;
     const float al = A.alpha[G.rev[e]] * A.s[n];
-    const float *Ee = A.E + (size_t)9 * e;
+    const float *Ee = A.E + (size_t)LPC_ES * e;
     const float yn[3] = {y[n], y[(size_t)K + n], y[2 * (size_t)K + n]};
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[c] -= al * (Ee[3 * c] * yn[0] + Ee[3 * c + 1] * yn[1] + Ee[3 * c + 2] * yn[2]);

@@ -73,6 +73,8 @@ struct mabd_ctx {
   DevPCG P{};
   DevPCG32 P32{};
   int p32_nb[2] = {0, 0};  // blocks of the persistent FP32 solve (block Jacobi, learned); 0: off
+  DevPCGN pn{};              // normalized-space solve of ball-joint graphs (k_pcgn.cu)
+  int pn_nb[2] = {0, 0};     // its blocks (block Jacobi, learned); 0: off
   // learned preconditioner of the mixed PCG (joint graph, activations, weights)
   bool lpc_graph = false, lpc_on = false;
   LpcGraph lg{};
@@ -1939,6 +1941,24 @@ static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, d
   const LpcGraph *lg = learned ? &ctx->lg : nullptr;
   const LpcAct *la = learned ? &ctx->la : nullptr;
   const int max_it = ctx->cfg.pcg_max_iters;
+  // ball-joint graphs whose C and E are current (learned preconditioner on):
+  // the normalized-space solve
+  const int nbn = ctx->lpc_on ? ctx->pn_nb[learned ? 1 : 0] : 0;
+  if (nbn > 0) {
+    cudaError_t e = cudaSuccess;
+    run(ctx, "p32_solve", [&] {
+      e = launch_pcgn(ctx->lg, ctx->la, ctx->pn, ctx->P32, learned, rhs, rtol, max_it, out,
+                      learned ? nullptr : acc, ctx->d_status, nbn, s);
+    });
+    CK(e);
+    CK(cudaMemcpyAsync(ctx->h_scal, ctx->P32.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_iter, ctx->P32.iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->pcg_last_iters += ctx->h_iter[0];
+    const double bb = ctx->h_scal[4], rr = ctx->h_scal[3];
+    ctx->pcg_last_rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    return MABD_OK;
+  }
   const int nb = ctx->p32_nb[learned ? 1 : 0];
   if (nb > 0) {
     cudaError_t e = cudaSuccess;
@@ -2422,7 +2442,7 @@ mabd_status build_lpc_graph(mabd_ctx *ctx) {
   int8_t *dsk = dnew<int8_t>(ctx, nz, ok), *dsn = dnew<int8_t>(ctx, nz, ok);
   uint8_t *dones = dnew<uint8_t>(ctx, K, ok);
   LpcAct &A = ctx->la;
-  A.E = dnew<float>(ctx, 9 * nz, ok);
+  A.E = dnew<float>(ctx, LPC_ES * nz, ok);
   A.C = dnew<float>(ctx, 6 * (size_t)K, ok);
   A.x = dnew<float>(ctx, LPC_F * (size_t)K, ok);
   A.h1 = dnew<float>(ctx, LPC_H * (size_t)K, ok);
@@ -2434,6 +2454,16 @@ mabd_status build_lpc_graph(mabd_ctx *ctx) {
   A.alpha = dnew<float>(ctx, nz, ok);
   ctx->P32.t = dnew<float>(ctx, 5 * (size_t)K, ok);
   ctx->P32.y = dnew<float>(ctx, 5 * (size_t)K, ok);
+  DevPCGN &V = ctx->pn;
+  V.r[0] = dnew<float4>(ctx, K, ok);
+  V.r[1] = dnew<float4>(ctx, K, ok);
+  V.p[0] = dnew<float4>(ctx, K, ok);
+  V.p[1] = dnew<float4>(ctx, K, ok);
+  V.q = dnew<float4>(ctx, K, ok);
+  V.x = dnew<float4>(ctx, K, ok);
+  V.y = dnew<float4>(ctx, K, ok);
+  V.z = dnew<float4>(ctx, K, ok);
+  V.cu = dnew<float>(ctx, nz, ok);
   float *dP = dnew<float>(ctx, LPC_NPARAM, ok);
   uint16_t *w1 = dnew<uint16_t>(ctx, 2 * LPC_F * LPC_H, ok), *w2 = dnew<uint16_t>(ctx, 2 * LPC_H * LPC_H, ok),
            *w3 = dnew<uint16_t>(ctx, 2 * LPC_H * LPC_H, ok);
@@ -2465,6 +2495,18 @@ mabd_status build_lpc_graph(mabd_ctx *ctx) {
   ctx->ln.W1t = w1;
   ctx->ln.W2t = w2;
   ctx->ln.W3t = w3;
+  // the normalized-space solve unless MABD_PCG_NORMALIZED=0 or the device
+  // cannot run a cooperative launch
+  {
+    const char *pe = std::getenv("MABD_PCG_NORMALIZED");
+    int coop = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (coop && !(pe && pe[0] == '0')) {
+      ctx->pn_nb[0] = pcgn_blocks(false);
+      ctx->pn_nb[1] = pcgn_blocks(true);
+    }
+  }
   ctx->lpc_graph = true;
   return MABD_OK;
 }
@@ -2699,9 +2741,9 @@ mabd_status mabd_lpc_capture(mabd_lpc *t, mabd_ctx *ctx, int32_t *batch) {
   } else if (t->g.K != G.K || t->g.nnz != G.nnz) {
     return MABD_ERR_INVALID_ARG;  // every batch has the first context's joint graph
   }
-  float *E = tnew<float>(t, 9 * (size_t)std::max(G.nnz, 1), ok);
+  float *E = tnew<float>(t, LPC_ES * (size_t)std::max(G.nnz, 1), ok);
   if (!ok) return MABD_ERR_OUT_OF_MEMORY;
-  CK(cudaMemcpyAsync(E, ctx->la.E, 9 * (size_t)G.nnz * 4, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(E, ctx->la.E, LPC_ES * (size_t)G.nnz * 4, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   t->batches.push_back(E);
   if (batch) *batch = (int32_t)t->batches.size() - 1;
@@ -2714,7 +2756,8 @@ mabd_status mabd_lpc_batch_blocks(mabd_lpc *t, int32_t batch, int32_t *off, int3
   const LpcGraph &g = t->g;
   if (cudaMemcpyAsync(off, g.off, 4 * ((size_t)g.K + 1), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
       cudaMemcpyAsync(nbr, g.nbr, 4 * (size_t)g.nnz, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
-      cudaMemcpyAsync(E, t->batches[batch], 36 * (size_t)g.nnz, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
+      cudaMemcpy2DAsync(E, 36, t->batches[batch], 4 * LPC_ES, 36, (size_t)g.nnz, cudaMemcpyDeviceToHost,
+                        t->stream) != cudaSuccess ||
       cudaStreamSynchronize(t->stream) != cudaSuccess)
     return MABD_ERR_CUDA;
   return MABD_OK;

@@ -256,8 +256,10 @@ struct LpcGraph {
   const uint8_t *onesided;  // [K] 1 if the joint has a single free body
 };
 
+constexpr int LPC_ES = 12;  // floats per stored block E_e: 3x3 row-major, padded for 16-byte loads
+
 struct LpcAct {
-  float *E;                     // [nnz][9] E_kk' row-major (rows: joint k, columns: neighbour)
+  float *E;                     // [nnz][LPC_ES] E_kk' row-major (rows: joint k, columns: neighbour)
   float *C;                     // [K][6] inverse Cholesky factor of D_k, packed lower
   float *x;                     // [K][F]
   float *A1, *A2, *A3;          // [K][2F], [K][2H], [K][2H] layer inputs as multiplied (training)
@@ -266,6 +268,13 @@ struct LpcAct {
   float *a, *b;                 // [K][R]
   float *s;                     // [K]
   float *alpha;                 // [nnz] (entries to higher-index neighbours hold 0)
+};
+
+// vectors of the normalized-space PCG (k_pcgn.cu), one float4 per joint;
+// r and p double-buffered
+struct DevPCGN {
+  float4 *r[2], *p[2], *q, *x, *y, *z;
+  float *cu;  // [nnz] alpha of the reverse entry times s of the neighbour
 };
 
 struct LpcNet {
@@ -411,6 +420,14 @@ int p32_persist_blocks(bool xj, bool lpc);
 cudaError_t launch_p32_persist(const DevBodies &B, const DevJoints &J, const DevIncidence &I, const DevPCG32 &P,
                                const LpcGraph *lg, const LpcAct *la, const double *rhs, double rtol,
                                int max_iters, double *out, double *acc, int *status, int nblocks, cudaStream_t s);
+
+// FP32 PCG of a ball-joint graph in the normalized dual space, the whole
+// solve in one cooperative launch (k_pcgn.cu); needs the current C and E of
+// launch_lpc_blocks (and, lpc, the network's alpha and s)
+int pcgn_blocks(bool lpc);
+cudaError_t launch_pcgn(const LpcGraph &G, const LpcAct &A, const DevPCGN &V, const DevPCG32 &P, bool lpc,
+                        const double *rhs, double rtol, int max_iters, double *out, double *acc, int *status,
+                        int nblocks, cudaStream_t s);
 
 // learned preconditioner (k_lpc.cu)
 // C_k and the normalized blocks E of the current state (needs R/Rf, hinvf)

@@ -130,6 +130,35 @@ def test_learned_preconditioner_step_parity(ora, dims):
         s.close()
 
 
+@pytest.mark.parametrize("dims", [(6, 6, 3), (24, 24, 8)])
+def test_normalized_and_matrix_free_solves_agree(ora, dims, monkeypatch):
+    """The learned-preconditioner step solved in the normalized dual space
+    (one cooperative launch per solve over the stored blocks E) and by the
+    matrix-free per-body S-apply: both within 1e-6 of the oracle, with
+    iteration counts within a few of each other (the same iteration in exact
+    arithmetic; FP32 rounding and the partial sums' blocking differ)."""
+    from parity_util import gpu_step, oracle_step
+    need_gpu()
+    p = trained_params()
+    sc = scenes.jittered_net(*dims, seed=4)
+    q, qd = scenes.perturb_state(sc, seed=2, rot=0.05, vel=0.2)
+    res = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("MABD_PCG_NORMALIZED", mode)
+        s = gpu_solver(sc, **MIXED)
+        try:
+            s.set_preconditioner(p)
+            q1, qd1, lam, st = gpu_step(s, q, qd)
+        finally:
+            s.close()
+        res[mode] = (qd1, lam, st[0]["pcg_iters"])
+    _, oqd, olam, _ = oracle_step(ora, sc, q, qd)
+    for mode, (qd1, lam, it) in res.items():
+        assert rel(qd1, oqd) <= TOL and rel(lam, olam) <= TOL, (mode, rel(qd1, oqd), rel(lam, olam))
+    i1, i0 = res["1"][2], res["0"][2]
+    assert abs(i1 - i0) <= max(4, i0 // 10), (i1, i0)
+
+
 @pytest.mark.parametrize("dims", [(16, 16, 8), (64, 64, 16)])
 def test_learned_beats_block_jacobi(dims):
     """Fewer FP32 PCG iterations per step than block Jacobi on nets the
