@@ -48,7 +48,9 @@ WORKLOADS = {
                  "level-scheduled body-space elimination (tree)"),
     "net64x64x16": ("jittered net: %d unit cubes on a 64x64x16 lattice (sigma 0.05, bottom layer fixed), "
                     "%d ball joints kept with p=0.7, %d dual rows, h=1e-2 s, seed 4",
-                    "block-Jacobi PCG on the dual, rtol 1e-13 (graph)"),
+                    "PCG on the dual (graph), rtol 1e-13: block Jacobi in FP64; in the mixed form FP32 "
+                    "with the learned preconditioner in the normalized dual space, one cooperative launch "
+                    "per solve"),
     "loop1m": ("pulley-cable loop: %d boxes (sides U[0.5,1.5], rho 10^U[2,4]) along a closed polygon, "
                "%d joints (ball/hinge alternating, the last one closing the loop, no world joints), "
                "%d dual rows, h=1e-2 s, seed 1",
@@ -411,6 +413,29 @@ def pcg_iteration_bytes(M: int, K: int, nfixed: int) -> float:
     return float(K * (12 + 24 + 12 + 72 + 24 + 8) + (M - nfixed) * (36 + 64 + 96))
 
 
+def pcgn_iteration_bytes(K: int, nnz: int) -> float:
+    """Algorithmic bytes of one iteration of the normalized-space FP32 PCG
+    (ball joints, S~ = I + E, learned preconditioner G^T G), every datum
+    counted once per phase that touches it.  Per joint: (A) z, p_old read,
+    p, q written 64; (B) r, q, x, p read, r', x, y written and C read 120;
+    (C) y, r' read, z written 48.  Per stored block (nnz, both directions):
+    (A) E 36 and the neighbour's z, p 32; (B, lower half) E 36, its gate 4,
+    the neighbour's r, q 32; (C, upper half) E 36, its coefficient 4, the
+    neighbour's y 16."""
+    return float(K * (64 + 120 + 48) + nnz * (36 + 32) + nnz / 2 * (36 + 4 + 32) + nnz / 2 * (36 + 4 + 16))
+
+
+def joint_graph_entries(sc: dict) -> int:
+    """Entries of the joint graph (ordered pairs of joints sharing a free body)."""
+    fixed = np.asarray(sc["fixed"]) != 0
+    deg = np.zeros(len(fixed), dtype=np.int64)
+    for ids in (np.asarray(sc["body_a"]), np.asarray(sc["body_b"])):
+        ok = ids >= 0
+        ok[ok] &= ~fixed[ids[ok]]
+        np.add.at(deg, ids[ok], 1)
+    return int(np.sum(deg * (deg - 1)))
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel, from one ncu capture of the current kernel (scaled to the named
 # workload by the bodies it processes where the capture ran a smaller chain);
@@ -713,6 +738,10 @@ def sub_record(name: str, args, barrier_sync) -> dict:
     elif dname == "p32_iteration":
         nfixed = int(np.sum(np.asarray(sc["fixed"]) != 0))
         model = pcg_iteration_bytes(M, info["joints"], nfixed)
+    elif dname == "p32_solve" and st.get("pcg_iters"):
+        # one launch is a whole solve: its iterations times an iteration's bytes
+        iters_per_launch = st["pcg_iters"] / (dn / args.profile_steps)
+        model = iters_per_launch * pcgn_iteration_bytes(info["joints"], joint_graph_entries(sc))
     if model is not None:
         achieved = model / (per_launch_ms / 1e3) / 1e9
         peak = measured_hbm_gbs()
