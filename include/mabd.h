@@ -293,9 +293,9 @@ mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M, const mab
 /* Schedule of a tree context's elimination, tuned at mabd_prefactor by
    timing the candidates on the scene's first state: counts[0] = number of
    levels below the roots, counts[1] = counts[2] = 0 (unused), counts[3] = 0
-   for the level-scheduled path (one launch per level and pass), or 128 / 64
+   for the level-scheduled path (one launch per level and pass), or 128 / 64 / 32
    for the persistent kernel (one block of that many threads per tree, both
-   passes in one launch).  MABD_TREE_MODE=levels|forest128|forest64 in the
+   passes in one launch).  MABD_TREE_MODE=levels|forest128|forest64|forest32 in the
    environment forces the path (tests). */
 mabd_status mabd_tree_schedule(mabd_ctx *ctx, int32_t *counts);
 

@@ -609,7 +609,8 @@ template <typename S>
 void launch_tree_forest(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, const DevForest &F,
                         const StepParams &p, int *status, cudaStream_t s, int threads) {
   if (F.ntrees <= 0) return;
-  if (threads == 64) k_tree_forest<S, 64><<<F.ntrees, 64, 0, s>>>(B, J, T, F, p, status);
+  if (threads == 32) k_tree_forest<S, 32><<<F.ntrees, 32, 0, s>>>(B, J, T, F, p, status);
+  else if (threads == 64) k_tree_forest<S, 64><<<F.ntrees, 64, 0, s>>>(B, J, T, F, p, status);
   else k_tree_forest<S, 128><<<F.ntrees, 128, 0, s>>>(B, J, T, F, p, status);
 }
 

@@ -93,7 +93,7 @@ struct mabd_ctx {
   // factors ([5][K]), and the chain's response at its two ends per breaker row
   double *loop_b = nullptr, *loop_x = nullptr, *loop_w = nullptr;
   int loop_rows = 0;  // rows of the loop breaker (3 or 5)
-  int tree_mode = 0;                   // 0: level-scheduled launches; 128 or 64: persistent kernel, threads
+  int tree_mode = 0;                   // 0: level-scheduled launches; 128, 64 or 32: persistent kernel, threads
   double *cL = nullptr, *cR = nullptr, *Bn = nullptr;
   int *d_status = nullptr;
   unsigned long long *d_max = nullptr;
@@ -731,18 +731,21 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
 
 // Path of the tree elimination: one launch per level (upward deepest
 // first, then downward), or the persistent forest kernel with one block of
-// 128 or 64 threads per tree (both passes in one launch).  The tuner runs
+// 128, 64 or 32 threads per tree (both passes in one launch).  The tuner runs
 // the body and joint kernels on the initial state, then times each path on
 // it (best of two CUDA-event timings; the downward pass moves the state, so
 // it is saved and put back around every trial) and keeps the fastest.
-// MABD_TREE_MODE=levels|forest128|forest64 forces the path.
+// MABD_TREE_MODE=levels|forest128|forest64|forest32 forces the path.
 template <typename S>
 static mabd_status tune_tree_t(mabd_ctx *ctx, const DevTreeT<S> &TT) {
   const auto &lv = ctx->tree_lvl;
   const int nl = (int)lv.size() - 1;
   const char *fm = std::getenv("MABD_TREE_MODE");
   if (fm) {
-    ctx->tree_mode = std::strcmp(fm, "forest128") == 0 ? 128 : (std::strcmp(fm, "forest64") == 0 ? 64 : 0);
+    ctx->tree_mode = std::strcmp(fm, "forest128") == 0 ? 128
+                     : std::strcmp(fm, "forest64") == 0  ? 64
+                     : std::strcmp(fm, "forest32") == 0  ? 32
+                                                         : 0;
     return MABD_OK;
   }
   if (ctx->F.ntrees <= 0) return MABD_OK;
@@ -765,7 +768,7 @@ static mabd_status tune_tree_t(mabd_ctx *ctx, const DevTreeT<S> &TT) {
   CK(cudaMemcpyAsync(sq, ctx->B.q, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(sq + 12 * (size_t)M, ctx->B.qd, 12 * (size_t)M * 8, cudaMemcpyDeviceToDevice, s));
   float best = 1e30f;
-  for (int mode : {0, 128, 64})
+  for (int mode : {0, 128, 64, 32})
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
       if (mode == 0) {

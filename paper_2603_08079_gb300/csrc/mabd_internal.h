@@ -510,7 +510,7 @@ cudaError_t seg_init();
 // level [lo, hi) of the body order T.order (roots = true: the roots' level,
 // bodies lo .. hi - 1); a 16-lane group per body of the upward pass
 // whole tree elimination (upward and downward passes) of every tree of the
-// forest in one launch, one block of `threads` (128 or 64) per tree
+// forest in one launch, one block of `threads` (128, 64 or 32) per tree
 // (S = double or float, the elimination's type, for these three launchers)
 template <typename S>
 void launch_tree_forest(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, const DevForest &F,

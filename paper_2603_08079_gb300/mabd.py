@@ -288,7 +288,7 @@ class Solver:
         c = np.zeros(4, dtype=np.int32)
         self._check("mabd_tree_schedule", self._lib.mabd_tree_schedule(self.ctx, _ptr(c)))
         return {"levels": int(c[0]),
-                "path": {0: "levels", 128: "forest128", 64: "forest64"}.get(int(c[3]), int(c[3]))}
+                "path": {0: "levels", 128: "forest128", 64: "forest64", 32: "forest32"}.get(int(c[3]), int(c[3]))}
 
     def lpc_fallbacks(self) -> int:
         n = C.c_int32(0)

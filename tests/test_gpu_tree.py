@@ -124,7 +124,7 @@ def test_level_scheduled_path(ora, forced_variant):
             s.close()
 
 
-@pytest.mark.parametrize("mode", ["forest128", "forest64"])
+@pytest.mark.parametrize("mode", ["forest128", "forest64", "forest32"])
 def test_persistent_forest_kernel(ora, forced_variant, mode):
     """One block per tree, both passes in one launch: forests of fixed-base
     assemblies (many small trees), a single large tree, mixed joints, and
@@ -158,7 +158,7 @@ def test_tuned_schedule(ora):
         s = gpu_solver(sc, solver="tree")
         try:
             sched = s.tree_schedule()
-            assert sched["levels"] > 0 and sched["path"] in ("levels", "forest128", "forest64")
+            assert sched["levels"] > 0 and sched["path"] in ("levels", "forest128", "forest64", "forest32")
             assert_parity(ora, sc, sc["q"], sc["qdot"], solver=s)
         finally:
             s.close()

@@ -99,7 +99,7 @@ def test_level_scheduled_path(ora, forced):
         assert_parity(ora, sc, q, qd, tol=TOL, gpu_kw=F32)
 
 
-@pytest.mark.parametrize("mode", ["forest128", "forest64"])
+@pytest.mark.parametrize("mode", ["forest128", "forest64", "forest32"])
 def test_persistent_forest_kernel(ora, forced, mode):
     need_gpu()
     forced("MABD_TREE_MODE", mode)
