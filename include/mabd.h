@@ -41,7 +41,10 @@
  *   MABD_DEBUG_SYNC=1 checks every launch synchronously).
  *   Errors: no C++ exception crosses this ABI; every call returns a status.
  *   MABD_ERR_CUDA is sticky (destroy the context).  Device-side failures
- *   (non-positive det A, non-finite state, polar or PCG non-convergence) set
+ *   (non-positive det A, non-finite state, polar or PCG non-convergence, a
+ *   bounded wait that gave up; in a library built with -DMABD_DEBUG also an
+ *   out-of-range index read from device memory, reported as
+ *   MABD_ERR_INVALID_ARG) set
  *   a status word that the next synchronizing call (mabd_step with stats,
  *   mabd_get_state, mabd_get_lambda, mabd_synchronize) returns and clears;
  *   the state is then undefined until mabd_set_state.
@@ -75,7 +78,7 @@ typedef enum {
   MABD_ERR_INVERTED = 6,       /* det A <= 0 for some body */
   MABD_ERR_NONFINITE = 7,
   MABD_ERR_NO_CONVERGENCE = 8, /* polar iteration or PCG hit its cap */
-  MABD_ERR_TIMEOUT = 9,
+  MABD_ERR_TIMEOUT = 9,        /* a bounded device-side wait gave up (cooperative PCG) */
   MABD_ERR_UNSUPPORTED = 10
 } mabd_status;
 

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, St
   const int type = J.type[k];
   const int ia = J.ja[k], ib = J.jb[k];
   const uint8_t fl = J.flags[k];
+  if (!MABD_INDEX_OK(ia, M, status) || ((fl & JF_B_BODY) && !MABD_INDEX_OK(ib, M, status))) return;
   double qa[12], pa1[3], pb1[3];
   load12(B.q, M, ia, qa);
   load3(J.pa1, K, k, pa1);

@@ -59,6 +59,16 @@ __device__ __forceinline__ float3 cinv(const float *Cp, float3 t) {
 // round trips.
 constexpr int EU = 4;
 
+// neighbour of entry e; a MABD_DEBUG build treats one out of range as absent
+// (the solve's first pass has already flagged it in the status word)
+__device__ __forceinline__ int nbr_at(const LpcGraph &G, int e) {
+  const int n = G.nbr[e];
+#ifdef MABD_DEBUG
+  if (n < 0 || n >= G.K) return -1;
+#endif
+  return n;
+}
+
 // q_k = p_k + sum_e E_e p_n with p = z + beta p_old formed on the fly
 __device__ __forceinline__ float3 sapply_row(const LpcGraph &G, const LpcAct &A, const float4 *z, const float4 *po,
                                              float beta, int k, float3 pk) {
@@ -68,7 +78,7 @@ __device__ __forceinline__ float3 sapply_row(const LpcGraph &G, const LpcAct &A,
     int n[EU];
     float3 w[EU];
 #pragma unroll
-    for (int u = 0; u < EU; ++u) n[u] = e + u < e1 ? G.nbr[e + u] : -1;
+    for (int u = 0; u < EU; ++u) n[u] = e + u < e1 ? nbr_at(G, e + u) : -1;
 #pragma unroll
     for (int u = 0; u < EU; ++u)
       w[u] = n[u] >= 0 ? axpy3(beta, ld3(po, n[u]), ld3(z, n[u])) : make_float3(0.f, 0.f, 0.f);
@@ -94,7 +104,7 @@ __device__ __forceinline__ float3 lower_row(const LpcGraph &G, const LpcAct &A, 
     float3 w[EU];
 #pragma unroll
     for (int u = 0; u < EU; ++u) {
-      n[u] = e + u < e1 ? G.nbr[e + u] : k;
+      n[u] = e + u < e1 ? nbr_at(G, e + u) : -1;
       if (n[u] >= k) n[u] = -1;  // lower neighbours only
     }
 #pragma unroll
@@ -129,7 +139,7 @@ __device__ __forceinline__ float3 upper_row(const LpcGraph &G, const LpcAct &A, 
     float al[EU];
 #pragma unroll
     for (int u = 0; u < EU; ++u) {
-      n[u] = e - u >= e0 ? G.nbr[e - u] : k;
+      n[u] = e - u >= e0 ? nbr_at(G, e - u) : -1;
       if (n[u] <= k) n[u] = -1;  // upper neighbours only
     }
 #pragma unroll
@@ -165,6 +175,11 @@ __global__ void __launch_bounds__(PN_THREADS, 1)
   const unsigned nblk = gridDim.x;
   const int tid = blockIdx.x * PN_THREADS + threadIdx.x, nth = nblk * PN_THREADS;
   const int K = G.K;
+#ifdef MABD_DEBUG
+  // the joint graph once per solve: every neighbour and reverse entry in range
+  for (int e = tid; e < G.nnz; e += nth)
+    if (!MABD_INDEX_OK(G.nbr[e], K, status) || !MABD_INDEX_OK(G.rev[e], G.nnz, status)) break;
+#endif
   // the scalar reductions in FP32 (the vectors are FP32; FP64 arithmetic is
   // the slow pipe here); fixed order, so every block gets the same sums
   float *fp = reinterpret_cast<float *>(P.ppart);
@@ -190,8 +205,8 @@ __global__ void __launch_bounds__(PN_THREADS, 1)
     }
     if (LPC) {
       for (int e = tid; e < G.nnz; e += nth) {
-        const int n = G.nbr[e];
-        V.cu[e] = A.alpha[G.rev[e]] * A.s[n];
+        const int n = nbr_at(G, e), r = G.rev[e];
+        V.cu[e] = (n >= 0 && r >= 0 && r < G.nnz) ? A.alpha[r] * A.s[n] : 0.f;
       }
       ok = ok && grid_barrier(P.bar, nblk, gen);
       for (int k = tid; ok && k < K; k += nth) st3(V.y, k, lower_row(G, A, V.r[0], V.q, 0.f, k, ld3(V.r[0], k)));

@@ -554,7 +554,12 @@ __global__ void __launch_bounds__(GB) k_tree_up_level(DevBodies B, DevJoints J, 
   const int i = lo + blockIdx.x * GNG + g;
   if (i >= hi) return;  // uniform in the group
   const int j = T.order[i];
+  if (!MABD_INDEX_OK(j, B.M, status)) return;
   if (T.parent[j] < 0) return;
+  if (!MABD_INDEX_OK(T.parent[j], B.M, status) || !MABD_INDEX_OK(T.pjoint[j], J.K, status)) return;
+  if (T.ccount[j] > 0 && !(MABD_INDEX_OK(T.cfirst[j], B.M, status) &&
+                           MABD_INDEX_OK(T.cfirst[j] + T.ccount[j] - 1, B.M, status)))
+    return;
   up_inner<S>(B, J, T, j, p, status, l, gm, scr[g]);
 }
 

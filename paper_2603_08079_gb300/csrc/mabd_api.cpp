@@ -199,6 +199,7 @@ mabd_status map_status_bits(int bits) {
   if (bits & ST_NOT_SPD) return MABD_ERR_NOT_SPD;
   if (bits & (ST_POLAR_NOCONV | ST_PCG_NOCONV)) return MABD_ERR_NO_CONVERGENCE;
   if (bits & ST_TIMEOUT) return MABD_ERR_TIMEOUT;
+  if (bits & ST_BOUNDS) return MABD_ERR_INVALID_ARG;
   return MABD_OK;
 }
 

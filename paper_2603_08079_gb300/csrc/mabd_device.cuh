@@ -16,6 +16,22 @@ __device__ __forceinline__ void set_status(int *status, int bits) {
   if (status) atomicOr(status, bits);
 }
 
+// Index checks of a MABD_DEBUG build: an index that a kernel read from
+// memory (a joint's bodies, a tree link, a graph neighbour) is checked
+// against its range before use; a bad one sets ST_BOUNDS in the status word
+// and the caller skips the access (never a trap).  Other builds compile the
+// checks to true.
+__device__ __forceinline__ bool index_in_range(long long i, long long n, int *status) {
+  if (i >= 0 && i < n) return true;
+  set_status(status, ST_BOUNDS);
+  return false;
+}
+#ifdef MABD_DEBUG
+#define MABD_INDEX_OK(i, n, status) ::mabd::index_in_range((i), (n), (status))
+#else
+#define MABD_INDEX_OK(i, n, status) true
+#endif
+
 // A(r,c) = q[3c+r] (Eq. abd_dof: vec stacks the columns of A)
 __device__ __forceinline__ void A_from_q(const double q[12], double A[9]) {
 #pragma unroll

@@ -18,6 +18,7 @@ enum : int {
   ST_NOT_SPD = 8,
   ST_PCG_NOCONV = 16,
   ST_TIMEOUT = 32,  // a bounded device-side wait gave up
+  ST_BOUNDS = 64,   // MABD_DEBUG builds: an index read from memory was out of range
 };
 
 // Structured inverse of Hbar_A = M_A/h^2 + Kbar_A for a body whose second

@@ -81,15 +81,17 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Load libmabd.so (building it in-tree with nvcc if it is missing)."""
+    """Load libmabd.so (building it in-tree with nvcc if it is missing);
+    MABD_LIB=debug in the environment loads the MABD_DEBUG build instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if not os.path.exists(path) or not _build.up_to_date():
+    debug = os.environ.get("MABD_LIB") == "debug"
+    path = _build.LIB_DEBUG if debug else _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date(debug):
         if not build_if_missing:
             raise RuntimeError(f"CUDA library not built: {path}")
-        _build.build()
+        _build.build(debug=debug)
     lib = C.CDLL(path)
     P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
     lib.mabd_config_default.argtypes = [C.POINTER(Config)]
