@@ -243,18 +243,17 @@ __device__ __noinline__ void up_body(const DevBodies &B, const DevJoints &J, con
     const int c0 = T.cfirst[j];
 #pragma unroll 1
     for (int c = c0; c < c0 + nch; ++c) {
-      // the child's rows issued together (a ball joint's rows 3 and 4 are zero)
+      // the child's five rows issued together; a ball joint's rows 3 and 4
+      // are exact zeros (padding), so all five are added without looking up
+      // the child's joint type (one dependent load round fewer)
       S u[NJ];
 #pragma unroll
       for (int t = 0; t < NJ; ++t) u[t] = act ? T.U[(size_t)(NJ * l + t) * M + c] : S(0);
       if (act) f -= T.v[(size_t)l * M + c];
-      const int Cc = J.type[T.pjoint[c]] == 0 ? 3 : 5;
 #pragma unroll
-      for (int t = 0; t < NJ; ++t) {
-        if (t >= Cc) break;
+      for (int t = 0; t < NJ; ++t)
 #pragma unroll
         for (int q = 0; q < 12; ++q) h[q] += u[t] * gshfl(gm, u[t], q);
-      }
     }
     b[0] = act ? f : S(0);
     // right-looking Cholesky (reciprocal diagonal) carrying the right-hand
@@ -438,11 +437,13 @@ __device__ __noinline__ void down_one(const DevBodies &B, const DevJoints &J, co
 #pragma unroll
     for (int a = 0; a < 12; ++a) dqp[a] = T.dq[(size_t)a * M + par];
     S pts[2][3], x[2][3], RH[9];
+    // every joint's second point and frame are loaded (valid storage for a
+    // ball joint too) alongside its type, then a ball joint takes the
+    // identity frame: no load waits for the type
     load3(JP<S>::p1(J, pside), K, k, pts[0]);
-    if (type != 0) {
-      load3(JP<S>::p2(J, pside), K, k, pts[1]);
-      load_R(JP<S>::RH(J), K, k, RH);
-    } else {
+    load3(JP<S>::p2(J, pside), K, k, pts[1]);
+    load_R(JP<S>::RH(J), K, k, RH);
+    if (type == 0) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) pts[1][a] = S(0);
 #pragma unroll
