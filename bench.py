@@ -440,8 +440,8 @@ def joint_graph_entries(sc: dict) -> int:
 # kernel, from one ncu capture of the current kernel (scaled to the named
 # workload by the bodies it processes where the capture ran a smaller chain);
 # an entry is removed when its kernel changes.  Both entries: one ncu capture
-# of the current build on the full chain, one step after three warm-up steps
-# (profiles/chain1m_mx_res_body_cr_back_dram.md).
+# of the current build on the full chain (dram__bytes_read.sum +
+# dram__bytes_write.sum), one step after three warm-up steps.
 TRAFFIC: dict = {("chain1m", "mixed_fp32_dual", "mx_res_body"): 726.8e6,
                  ("chain1m", "mixed_fp32_dual", "cr_back"): 21.93e6}
 
