@@ -145,7 +145,9 @@ typedef struct {
                            PCG with the learned preconditioner on (ball-joint
                            graphs) runs each solve as one cooperative launch in
                            the normalized dual space (MABD_PCG_NORMALIZED=0 in
-                           the environment turns that off); otherwise one launch
+                           the environment turns that off; the step's first
+                           solve starts from the previous step's multipliers,
+                           MABD_PCG_WARM=0 starts it from 0); otherwise one launch
                            per step of an iteration, or with MABD_PCG_PERSIST=1
                            one cooperative launch per solve.  In a cooperative
                            solve the phases meet at a grid barrier; a wait that

@@ -45,6 +45,13 @@ __device__ __forceinline__ float3 cmul(const float *Cp, float3 r) {
 __device__ __forceinline__ float3 ctmul(const float *Cp, float3 x) {
   return make_float3(Cp[0] * x.x + Cp[1] * x.y + Cp[3] * x.z, Cp[2] * x.y + Cp[4] * x.z, Cp[5] * x.z);
 }
+// C^{-T} l (back substitution with C^T)
+__device__ __forceinline__ float3 ctinv(const float *Cp, float3 l) {
+  const float x2 = l.z / Cp[5];
+  const float x1 = (l.y - Cp[4] * x2) / Cp[2];
+  const float x0 = (l.x - Cp[1] * x1 - Cp[3] * x2) / Cp[0];
+  return make_float3(x0, x1, x2);
+}
 // C^{-1} t (forward substitution)
 __device__ __forceinline__ float3 cinv(const float *Cp, float3 t) {
   const float r0 = t.x / Cp[0];
@@ -161,7 +168,9 @@ __device__ __forceinline__ float3 upper_row(const LpcGraph &G, const LpcAct &A, 
 }
 
 // The whole solve (setup, iterations, x = C^T x~ out) in one cooperative
-// launch.  LPC: the learned preconditioner; else block Jacobi (z = r~).
+// launch, from x0 when given (the previous step's multipliers: a warm
+// start; non-finite entries start at 0), else from 0.  LPC: the learned
+// preconditioner; else block Jacobi (z = r~).
 // One block of PN_THREADS per SM: on the 64x64x16 net that is one joint per
 // thread (no thread of a phase carries a second joint), and a grid barrier
 // or a grid sum has one arrival or one partial per SM.
@@ -169,8 +178,8 @@ constexpr int PN_THREADS = 896;
 
 template <bool LPC>
 __global__ void __launch_bounds__(PN_THREADS, 1)
-    k_pcgn(LpcGraph G, LpcAct A, DevPCGN V, DevPCG32 P, const double *rhs, double rtol, int max_iters, double *out,
-           double *acc, int *status) {
+    k_pcgn(LpcGraph G, LpcAct A, DevPCGN V, DevPCG32 P, const double *rhs, const double *x0, double rtol,
+           int max_iters, double *out, double *acc, int *status) {
   __shared__ float sh[PN_THREADS];
   const unsigned nblk = gridDim.x;
   const int tid = blockIdx.x * PN_THREADS + threadIdx.x, nth = nblk * PN_THREADS;
@@ -183,24 +192,51 @@ __global__ void __launch_bounds__(PN_THREADS, 1)
   // the scalar reductions in FP32 (the vectors are FP32; FP64 arithmetic is
   // the slow pipe here); fixed order, so every block gets the same sums
   float *fp = reinterpret_cast<float *>(P.ppart);
-  float *prz = fp, *prr = fp + P32_MAXB, *ppq = fp + 2 * P32_MAXB;
+  float *prz = fp, *prr = fp + P32_MAXB, *ppq = fp + 2 * P32_MAXB, *pbb = fp + 3 * P32_MAXB;
   unsigned gen = 0;
   bool ok = true;
   int cur = 0, pc = 0;
-  // setup: r~ = C b, x~ = 0, p_old = 0, z = M~^{-1} r~
+  // setup: r~ = C b - S~ x~0 with x~0 = C^{-T} x0 (x0 = 0 when not given),
+  // p_old = 0, z = M~^{-1} r~
+  float bb = 0.f;
   {
-    float rr = 0.f, rz = 0.f;
+    float rr = 0.f, rz = 0.f, rb = 0.f;
     for (int k = tid; k < K; k += nth) {
       const float3 b = make_float3((float)rhs[k], (float)rhs[(size_t)K + k], (float)rhs[2 * (size_t)K + k]);
       const float3 t = cmul(A.C + (size_t)6 * k, b);
+      float3 xt = make_float3(0.f, 0.f, 0.f);
+      if (x0) {
+        const float3 l0 = make_float3((float)x0[k], (float)x0[(size_t)K + k], (float)x0[2 * (size_t)K + k]);
+        if (isfinite(l0.x) && isfinite(l0.y) && isfinite(l0.z)) xt = ctinv(A.C + (size_t)6 * k, l0);
+      }
       st3(V.r[0], k, t);
-      st3(V.x, k, make_float3(0.f, 0.f, 0.f));
+      st3(V.x, k, xt);
       st3(V.p[0], k, make_float3(0.f, 0.f, 0.f));
       st3(V.q, k, make_float3(0.f, 0.f, 0.f));
-      rr += dot3(b, b);
-      if (!LPC) {
-        st3(V.z, k, t);
-        rz += dot3(t, t);
+      rb += dot3(b, b);
+      if (!x0) {
+        rr += dot3(b, b);
+        if (!LPC) {
+          st3(V.z, k, t);
+          rz += dot3(t, t);
+        }
+      }
+    }
+    if (x0) {
+      // r~ = C b - (x~0 + sum_e E_e x~0_n): needs every joint's x~0
+      ok = ok && grid_barrier(P.bar, nblk, gen);
+      for (int k = tid; ok && k < K; k += nth) {
+        const float3 xk = ld3(V.x, k);
+        const float3 sx = sapply_row(G, A, V.x, V.p[0], 0.f, k, xk);
+        const float3 t = ld3(V.r[0], k);
+        const float3 r0 = make_float3(t.x - sx.x, t.y - sx.y, t.z - sx.z);
+        st3(V.r[0], k, r0);
+        const float3 ru = cinv(A.C + (size_t)6 * k, r0);
+        rr += dot3(ru, ru);
+        if (!LPC) {
+          st3(V.z, k, r0);
+          rz += dot3(r0, r0);
+        }
       }
     }
     if (LPC) {
@@ -217,21 +253,23 @@ __global__ void __launch_bounds__(PN_THREADS, 1)
         rz += dot3(ld3(V.r[0], k), z);
       }
     }
-    float bs[2] = {rz, rr};
-    block_sums<2, float, PN_THREADS>(bs, sh);
+    float bs[3] = {rz, rr, rb};
+    block_sums<3, float, PN_THREADS>(bs, sh);
     if (threadIdx.x == 0) {
       prz[blockIdx.x] = bs[0];
       prr[blockIdx.x] = bs[1];
+      pbb[blockIdx.x] = bs[2];
     }
     ok = ok && grid_barrier(P.bar, nblk, gen);
   }
   float gs[2];
   grid_sums<2, float, PN_THREADS>(fp, P32_MAXB, nblk, gs, sh);
   float rz = gs[0], rr = gs[1];
-  const float bb = rr, tol2 = (float)(rtol * rtol);
+  bb = grid_sum<float, PN_THREADS>(pbb, nblk, sh);
+  const float tol2 = (float)(rtol * rtol);
   float beta = 0.f;
   int it = 0;
-  bool done = rr == 0.f;
+  bool done = rr <= tol2 * bb;
   while (ok && !done && it < max_iters) {
     // A: p = z + beta p_old, q = S~ p, p.q
     float pq = 0.f;
@@ -325,11 +363,11 @@ int pcgn_blocks(bool lpc) {
 }
 
 cudaError_t launch_pcgn(const LpcGraph &G, const LpcAct &A, const DevPCGN &V, const DevPCG32 &P, bool lpc,
-                        const double *rhs, double rtol, int max_iters, double *out, double *acc, int *status,
-                        int nblocks, cudaStream_t s) {
+                        const double *rhs, const double *x0, double rtol, int max_iters, double *out, double *acc,
+                        int *status, int nblocks, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(P.bar, 0, 4 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  void *args[] = {(void *)&G, (void *)&A, (void *)&V, (void *)&P, (void *)&rhs, (void *)&rtol,
+  void *args[] = {(void *)&G, (void *)&A, (void *)&V, (void *)&P, (void *)&rhs, (void *)&x0, (void *)&rtol,
                   (void *)&max_iters, (void *)&out, (void *)&acc, (void *)&status};
   const void *f = lpc ? (const void *)k_pcgn<true> : (const void *)k_pcgn<false>;
   return cudaLaunchCooperativeKernel(f, dim3(nblocks), dim3(PN_THREADS), args, 0, s);

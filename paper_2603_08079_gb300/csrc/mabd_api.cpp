@@ -1949,9 +1949,14 @@ static mabd_status p32_solve(mabd_ctx *ctx, cudaStream_t s, const double *rhs, d
   // the normalized-space solve
   const int nbn = ctx->lpc_on ? ctx->pn_nb[learned ? 1 : 0] : 0;
   if (nbn > 0) {
+    // the step's first solve (of S lambda = b) starts from the multipliers
+    // of the previous step (zero before the first); MABD_PCG_WARM=0: from 0
+    const char *we = std::getenv("MABD_PCG_WARM");
+    const bool warm = out == ctx->J.lambda && !acc && !(we && we[0] == '0');
     cudaError_t e = cudaSuccess;
     run(ctx, "p32_solve", [&] {
-      e = launch_pcgn(ctx->lg, ctx->la, ctx->pn, ctx->P32, learned, rhs, rtol, max_it, out,
+      e = launch_pcgn(ctx->lg, ctx->la, ctx->pn, ctx->P32, learned, rhs, warm ? ctx->J.lambda : nullptr, rtol, max_it,
+                      out,
                       learned ? nullptr : acc, ctx->d_status, nbn, s);
     });
     CK(e);

@@ -423,12 +423,12 @@ cudaError_t launch_p32_persist(const DevBodies &B, const DevJoints &J, const Dev
                                int max_iters, double *out, double *acc, int *status, int nblocks, cudaStream_t s);
 
 // FP32 PCG of a ball-joint graph in the normalized dual space, the whole
-// solve in one cooperative launch (k_pcgn.cu); needs the current C and E of
-// launch_lpc_blocks (and, lpc, the network's alpha and s)
+// solve in one cooperative launch (k_pcgn.cu), from x0 when given; needs the
+// current C and E of launch_lpc_blocks (and, lpc, the network's alpha and s)
 int pcgn_blocks(bool lpc);
 cudaError_t launch_pcgn(const LpcGraph &G, const LpcAct &A, const DevPCGN &V, const DevPCG32 &P, bool lpc,
-                        const double *rhs, double rtol, int max_iters, double *out, double *acc, int *status,
-                        int nblocks, cudaStream_t s);
+                        const double *rhs, const double *x0, double rtol, int max_iters, double *out, double *acc,
+                        int *status, int nblocks, cudaStream_t s);
 
 // learned preconditioner (k_lpc.cu)
 // C_k and the normalized blocks E of the current state (needs R/Rf, hinvf)

@@ -159,6 +159,31 @@ def test_normalized_and_matrix_free_solves_agree(ora, dims, monkeypatch):
     assert abs(i1 - i0) <= max(4, i0 // 10), (i1, i0)
 
 
+def test_warm_start_from_the_previous_multipliers(monkeypatch):
+    """The step's first solve starts from the previous step's multipliers:
+    over steps 2-6 of a net it needs fewer FP32 PCG iterations than from
+    zero, and the trajectories agree to the mixed bound."""
+    need_gpu()
+    from paper_2603_08079_gb300 import mabd
+    p = trained_params()
+    sc = scenes.jittered_net(16, 16, 8, seed=4)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("MABD_PCG_WARM", mode)
+        s = gpu_solver(sc, **MIXED)
+        try:
+            s.set_preconditioner(p)
+            s.step(1)
+            its = [s.step(1, stats=True)[0]["pcg_iters"] for _ in range(5)]
+            q, qd = s.get_state()
+        finally:
+            s.close()
+        out[mode] = (sum(its), q, qd)
+    print("iterations over steps 2-6: warm", out["1"][0], "cold", out["0"][0])
+    assert out["1"][0] < out["0"][0]
+    assert rel(out["1"][2], out["0"][2]) <= TOL and rel(out["1"][1], out["0"][1]) <= 1e-9
+
+
 @pytest.mark.parametrize("dims", [(16, 16, 8), (64, 64, 16)])
 def test_learned_beats_block_jacobi(dims):
     """Fewer FP32 PCG iterations per step than block Jacobi on nets the
