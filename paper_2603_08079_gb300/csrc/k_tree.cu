@@ -583,6 +583,23 @@ __global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, Dev
   if (j < hi) down_one(B, J, T, j, p);
 }
 
+// Consecutive narrow levels [la, lb) of the downward pass in one block of RB
+// threads, root first, a block barrier between levels.  A narrow level's
+// own launch costs more than its bodies (one thread each: a few loads and a
+// 5x5 solve), so a run of them shares one launch.  (The upward pass keeps
+// a launch per level: there a body's latency, not the launch, sets the cost.)
+constexpr int RB = 256;
+
+template <typename S>
+__global__ void __launch_bounds__(RB) k_tree_down_run(DevBodies B, DevJoints J, DevTreeT<S> T, int la, int lb,
+                                                      StepParams p) {
+  for (int d = la; d < lb; ++d) {
+    const int lo = T.lv_lo[d], hi = T.lv_lo[d + 1];
+    for (int j = lo + threadIdx.x; j < hi; j += RB) down_one(B, J, T, j, p);
+    __syncthreads();
+  }
+}
+
 // Persistent kernel, one block of NT threads per tree in the forest's record
 // order (deepest trees first): per level of the upward pass the NT / GL lane
 // groups take its bodies, then the root, then the downward pass a thread per
@@ -635,7 +652,15 @@ void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTreeT<S> 
   if (n > 0) k_tree_down<S><<<(n + 127) / 128, 128, 0, s>>>(B, J, T, lo, hi, p);
 }
 
+template <typename S>
+void launch_tree_down_run(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int la, int lb,
+                          const StepParams &p, cudaStream_t s) {
+  if (lb > la) k_tree_down_run<S><<<1, RB, 0, s>>>(B, J, T, la, lb, p);
+}
+
 #define MABD_TREE_INSTANTIATE(S)                                                                   \
+  template void launch_tree_down_run<S>(const DevBodies &, const DevJoints &, const DevTreeT<S> &,  \
+                                        int, int, const StepParams &, cudaStream_t);               \
   template void launch_tree_forest<S>(const DevBodies &, const DevJoints &, const DevTreeT<S> &,    \
                                       const DevForest &, const StepParams &, int *, cudaStream_t,  \
                                       int);                                                        \

@@ -87,6 +87,7 @@ struct mabd_ctx {
   double *h_scal = nullptr;  // pinned [8]
   std::vector<int32_t> tree_lvl;  // level offsets (internal body order)
   std::vector<int32_t> tree_mid;  // per level: first leaf (bodies before it have children)
+  std::vector<int8_t> tree_narrow;  // per level: its downward pass joins a single-block run
   DevForest F{};                       // the forest tree by tree (persistent kernel)
   DevTreeT<float> Tf{};                // FP32 elimination of the mixed tree form
   // loop solver: right-hand side and solution of a pass through the chain's
@@ -730,6 +731,31 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
 
 }  // extern "C"
 
+// The level-scheduled elimination of T: upward one launch per level,
+// deepest first; downward root first, one launch per wide level and one
+// single-block launch per run of consecutive narrow levels.  R(name,
+// launch) issues a launch (the step wraps it for profiling).
+template <typename S, typename R>
+static void tree_levels(mabd_ctx *ctx, const DevTreeT<S> &T, cudaStream_t s, R &&runl) {
+  const StepParams &p = ctx->sp;
+  const auto &lv = ctx->tree_lvl;
+  const auto &nw = ctx->tree_narrow;
+  const int nl = (int)lv.size() - 1;
+  for (int l = nl - 1; l >= 0; --l)
+    runl("tree_up", [&] { launch_tree_up(ctx->B, ctx->J, T, lv[l], lv[l + 1], l == 0, p, ctx->d_status, s); });
+  for (int l = 0; l < nl;) {
+    if (nw[l]) {
+      int lb = l + 1;
+      while (lb < nl && nw[lb]) ++lb;
+      runl("tree_down", [&] { launch_tree_down_run(ctx->B, ctx->J, T, l, lb, p, s); });
+      l = lb;
+    } else {
+      runl("tree_down", [&] { launch_tree_down(ctx->B, ctx->J, T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+      ++l;
+    }
+  }
+}
+
 // Path of the tree elimination: one launch per level (upward deepest
 // first, then downward), or the persistent forest kernel with one block of
 // 128, 64 or 32 threads per tree (both passes in one launch).  The tuner runs
@@ -739,8 +765,6 @@ mabd_status mabd_add_joints(mabd_ctx *ctx, int64_t n, const mabd_joint_desc *d, 
 // MABD_TREE_MODE=levels|forest128|forest64|forest32 forces the path.
 template <typename S>
 static mabd_status tune_tree_t(mabd_ctx *ctx, const DevTreeT<S> &TT) {
-  const auto &lv = ctx->tree_lvl;
-  const int nl = (int)lv.size() - 1;
   const char *fm = std::getenv("MABD_TREE_MODE");
   if (fm) {
     ctx->tree_mode = std::strcmp(fm, "forest128") == 0 ? 128
@@ -773,9 +797,7 @@ static mabd_status tune_tree_t(mabd_ctx *ctx, const DevTreeT<S> &TT) {
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
       if (mode == 0) {
-        for (int l = nl - 1; l >= 0; --l)
-          launch_tree_up(ctx->B, ctx->J, TT, lv[l], lv[l + 1], l == 0, p, ctx->d_status, s);
-        for (int l = 0; l < nl; ++l) launch_tree_down(ctx->B, ctx->J, TT, lv[l], lv[l + 1], p, ctx->d_status, s);
+        tree_levels(ctx, TT, s, [](const char *, auto &&f) { f(); });
       } else {
         launch_tree_forest(ctx->B, ctx->J, TT, ctx->F, p, ctx->d_status, s, mode);
       }
@@ -1528,13 +1550,25 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       for (int i = tord.lvl_off[l]; i < tord.lvl_off[l + 1]; ++i)
         if (tord.ccount[i] == 0) ids.push_back(i);
     }
+    // narrow levels (at most MABD_TREE_NARROW bodies, default 256; 0: none)
+    // run their downward pass together in one block
+    {
+      int nn = 256;
+      if (const char *e = std::getenv("MABD_TREE_NARROW")) nn = std::max(0, std::atoi(e));
+      const int nlev = (int)tord.lvl_off.size() - 1;
+      ctx->tree_narrow.assign(std::max(nlev, 0), 0);
+      for (int l = 0; l < nlev; ++l) ctx->tree_narrow[l] = tord.lvl_off[l + 1] - tord.lvl_off[l] <= nn;
+    }
     int32_t *dids = dnew<int32_t>(ctx, std::max<size_t>(ids.size(), 1), ok);
+    int32_t *dlo = dnew<int32_t>(ctx, tord.lvl_off.size(), ok);
     if (!ok) {
       free_all(ctx);
       return MABD_ERR_OUT_OF_MEMORY;
     }
     CK(up(dids, ids.data(), ids.size() * 4));
+    CK(up(dlo, tord.lvl_off.data(), tord.lvl_off.size() * 4));
     ctx->T.order = dids;
+    ctx->T.lv_lo = dlo;
     if (f32dual) {
       DevTreeT<float> &Tf = ctx->Tf;
       Tf.parent = T.parent;
@@ -1547,6 +1581,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
       Tf.root_side = T.root_side;
       Tf.nroots = T.nroots;
       Tf.order = dids;
+      Tf.lv_lo = dlo;
     }
     // the same bodies tree by tree: per tree and depth, bodies with children
     // first, then leaves; a sentinel record closes each tree
@@ -1799,12 +1834,7 @@ static void enqueue_tree_solve(mabd_ctx *ctx, const DevTreeT<S> &T, cudaStream_t
     });
     return;
   }
-  const auto &lv = ctx->tree_lvl;
-  const int nl = (int)lv.size() - 1;
-  for (int l = nl - 1; l >= 0; --l)
-    run(ctx, "tree_up", [&] { launch_tree_up(ctx->B, ctx->J, T, lv[l], lv[l + 1], l == 0, p, ctx->d_status, s); });
-  for (int l = 0; l < nl; ++l)
-    run(ctx, "tree_down", [&] { launch_tree_down(ctx->B, ctx->J, T, lv[l], lv[l + 1], p, ctx->d_status, s); });
+  tree_levels(ctx, T, s, [&](const char *name, auto &&f) { run(ctx, name, f); });
 }
 
 extern "C" {

@@ -155,6 +155,7 @@ struct DevTreeT {
   const int8_t *root_side;    // [2][nroots]
   int32_t nroots;
   const int32_t *order;       // [nfree] per level: bodies with children, then leaves
+  const int32_t *lv_lo;       // [levels + 1] first body of each level
   S *X;                       // [60][M]  Hhat^{-1} G^T in the rest frame (12 x 5)
   S *LD;                      // [15][M]  Cholesky factor of D = G Hhat^{-1} G^T
   S *y;                       // [12][M]  Hhat^{-1} fhat (rest frame)
@@ -522,6 +523,10 @@ void launch_tree_up(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T
 template <typename S>
 void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int lo, int hi,
                       const StepParams &p, int *status, cudaStream_t s);
+// narrow levels [la, lb) of the downward pass, root first, in one block
+template <typename S>
+void launch_tree_down_run(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int la, int lb,
+                          const StepParams &p, cudaStream_t s);
 
 // PCG (k_pcg.cu)
 void launch_pcg_setup(const DevBodies &B, const DevJoints &J, const DevPCG &P, double rtol,
