@@ -33,8 +33,9 @@
  *   Ordering: all device work is ordered on cfg.stream (NULL = the legacy
  *   default stream).  mabd_step returns once the work is enqueued unless
  *   stats is non-NULL, in which case it synchronizes the stream; with the
- *   PCG solver it also synchronizes between chunks of 16 iterations (the
- *   host reads the convergence flag there).  Without statistics the step's
+ *   PCG solver it also synchronizes after each cooperative solve, or
+ *   between chunks of 16 iterations of the one-launch-per-step driver (the
+ *   host reads the iteration count and the convergence flag there).  Without statistics the step's
  *   launches are replayed from CUDA graphs recorded at the first such call
  *   on a private stream that is ordered after cfg.stream by events
  *   (environment MABD_NO_GRAPHS=1 launches kernels directly instead;
