@@ -60,3 +60,19 @@ def test_roofline_byte_models_by_hand():
     first = (6 + 9 + 9 + 3 + 3 + 3) * 4 + 3 * 8 + 2 * 3 * (4 + 8)
     second = (6 + 9 + 0 + 3 + 3 + 0) * 4 + 3 * 4 + 1 * 3 * (4 + 4)
     assert bench.cr_back_bytes(balls, 4) == first + second
+
+
+def test_normalized_pcg_byte_model_and_graph_entries(ora):
+    """The joint graph's entry count used by the net's roofline equals the
+    oracle's joint graph (ordered pairs of joints sharing a free body), and
+    the per-iteration byte model adds up its per-joint and per-entry terms
+    (232 B per joint, 132 B per stored block on average)."""
+    import bench
+    from oracle import lpc
+    from paper_2603_08079_gb300 import scenes
+    sc = scenes.jittered_net(5, 4, 3, seed=7)
+    ent, ones = lpc.joint_graph(sc)
+    nnz = sum(len(e) for e in ent)
+    assert bench.joint_graph_entries(sc) == nnz
+    K = len(sc["jtype"])
+    assert bench.pcgn_iteration_bytes(K, nnz) == K * 232 + nnz * 132
