@@ -45,7 +45,7 @@ class _Scene(C.Structure):
                 ("jtype", C.c_void_p), ("body_a", C.c_void_p), ("body_b", C.c_void_p),
                 ("anchor_a", C.c_void_p), ("anchor_b", C.c_void_p), ("axis_a", C.c_void_p),
                 ("axis_b", C.c_void_p), ("axis_len", C.c_void_p), ("ref_a", C.c_void_p),
-                ("ref_b", C.c_void_p)]
+                ("ref_b", C.c_void_p), ("rotation_mode", C.c_int32), ("jacobian_mode", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -82,6 +82,9 @@ def lib():
         _lib.ora_topology.argtypes = [P]
         _lib.ora_assemble_dense.argtypes = [P, P, P, P, P, P, P]
         _lib.ora_step.argtypes = [P, C.c_int32, P, P, P, P, P, P]
+        _lib.ora_alg1_solve.argtypes = [P, P, P, P]
+        _lib.ora_alg1_solve.restype = None
+        _lib.ora_joint_eval_attached.argtypes = [P, P, P, C.c_int64, P]
     return _lib
 
 
@@ -89,10 +92,18 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
 
-class Scene:
-    """Keeps contiguous copies of a scene dict alive behind an ``ora_scene``."""
+ROTATION_MODES = {"polar": 0, "normalized": 1}
+JACOBIAN_MODES = {"frozen": 0, "full": 1}
 
-    def __init__(self, sc: dict, residual_rhs: int = 1):
+
+class Scene:
+    """Keeps contiguous copies of a scene dict alive behind an ``ora_scene``.
+    rotation_mode "normalized": the unconstrained solve by Alg. 1 (Sec. 3.4);
+    jacobian_mode "full": the constraint gradient of Eq. constraint_gradient
+    with the joint frame attached to body alpha (Sec. 5.1)."""
+
+    def __init__(self, sc: dict, residual_rhs: int = 1, rotation_mode: str = "polar",
+                 jacobian_mode: str = "frozen"):
         f64 = lambda k: np.ascontiguousarray(sc[k], dtype=np.float64)
         K = len(sc["jtype"])
         ref = lambda k: np.ascontiguousarray(sc.get(k, np.zeros((K, 3))), dtype=np.float64)
@@ -115,6 +126,8 @@ class Scene:
         for i in range(3):
             s.g[i] = float(sc["gravity"][i])
         s.residual_rhs = residual_rhs
+        s.rotation_mode = ROTATION_MODES[rotation_mode]
+        s.jacobian_mode = JACOBIAN_MODES[jacobian_mode]
         for k, v in self.arrays.items():
             setattr(s, k, v.ctypes.data)
         self.s = s
@@ -214,6 +227,30 @@ def joint_eval(scene: Scene, q: np.ndarray, k: int):
     return c[:n], Ga.reshape(5, 12)[:n], Gb.reshape(5, 12)[:n]
 
 
+def joint_eval_attached(scene: Scene, q_ref: np.ndarray, q: np.ndarray, k: int) -> np.ndarray:
+    """C_k(q) with the joint frame carried by body alpha's polar rotation from
+    q_ref (R_J = dR R^T, Sec. 5.1 Eq. r_gradient); its derivative at q = q_ref
+    is the full gradient of Eq. constraint_gradient."""
+    q_ref = np.ascontiguousarray(q_ref, dtype=np.float64).reshape(-1)
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    c = np.zeros(5)
+    _check(lib().ora_joint_eval_attached(scene.ptr, _p(q_ref), _p(q), k, _p(c)), "joint_eval_attached")
+    t = int(scene.arrays["jtype"][k])
+    return c[:(5 if t in (1, 3) else 3)]
+
+
+def alg1_solve(L: np.ndarray, A: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """Alg. 1 (Sec. 3.4): u from Hbar_A = L L^T, the affine matrix A and the
+    world-frame force f, every block rotation by the length-preserving map of
+    Eq. len_preserving."""
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(3, 3))
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(12)
+    u = np.zeros(12)
+    lib().ora_alg1_solve(_p(L), _p(A), _p(f), _p(u))
+    return u
+
+
 def topology(scene: Scene) -> int:
     return int(lib().ora_topology(scene.ptr))
 
@@ -247,9 +284,10 @@ def step(scene: Scene, q: np.ndarray, qd: np.ndarray, solver: str = "auto"):
     return q1.reshape(-1, 12), qd1.reshape(-1, 12), lam[:scene.rows], st.as_dict()
 
 
-def run(sc: dict, nsteps: int, solver: str = "auto", q=None, qd=None, residual_rhs: int = 1):
+def run(sc: dict, nsteps: int, solver: str = "auto", q=None, qd=None, residual_rhs: int = 1,
+        **modes):
     """Advance a scene dict nsteps from (q, qd) (default: the scene's state)."""
-    scene = Scene(sc, residual_rhs)
+    scene = Scene(sc, residual_rhs, **modes)
     q = sc["q"] if q is None else q
     qd = sc["qdot"] if qd is None else qd
     stats = []

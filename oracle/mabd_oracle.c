@@ -17,6 +17,9 @@
  *            elimination in body space (leaf-to-root, then root-to-leaf)
  *   Sec. 5.5 graph: block-Jacobi preconditioned CG on the dual matrix
  *   Sec. 5.2 Eq. recover-dq-explicit  dq_j = H_j^{-1}(f_j - sum_k G_kj^T lambda_k)
+ * Variants (scene flags): Alg. 1 / Eq. len_preserving for the unconstrained
+ * solve (rotation_mode 1); the full constraint gradient of Eq.
+ * constraint_gradient / pcpr / r_gradient (jacobian_mode 1).
  * No blocking, fusion or reordering beyond the definitions.
  */
 #include "mabd_oracle.h"
@@ -284,6 +287,70 @@ void ora_hinge_frame(const double a[3], double RH[9]) {
   for (int i = 0; i < 9; ++i) RH[i] = (i % 4 == 0 ? 1.0 : 0.0) + Vx[i] + V2[i] / (1.0 + a[1]);
 }
 
+/* Alg. 1 (Sec. 3.4): the unconstrained solve of one body with each
+   rotation of a 3-block replaced by the length-preserving map of Eq.
+   len_preserving.  The four blocks f_k of f are taken to the rest frame as
+   A^T f_k rescaled to |f_k|, Hbar_A dp = f~ is solved with the prefactored
+   L, and each block dp_k is taken back as A dp_k rescaled to |dp_k|.  A
+   zero block stays zero (the rescaling is bounded; its limit is 0). */
+void ora_alg1_solve(const double L[144], const double A[9], const double f[12], double u[12]) {
+  double ft[12], dp[12];
+  for (int k = 0; k < 4; ++k) {
+    const double *fk = f + 3 * k;
+    double *t = ft + 3 * k;
+    const double l2 = fk[0] * fk[0] + fk[1] * fk[1] + fk[2] * fk[2];
+    mtv3(A, fk, t);
+    const double n2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double s = n2 > 0.0 ? sqrt(l2 / n2) : 0.0;
+    for (int a = 0; a < 3; ++a) t[a] *= s;
+  }
+  chol_solve(12, L, ft, dp);
+  for (int k = 0; k < 4; ++k) {
+    const double *pk = dp + 3 * k;
+    double *t = u + 3 * k;
+    const double l2 = pk[0] * pk[0] + pk[1] * pk[1] + pk[2] * pk[2];
+    mv3(A, pk, t);
+    const double n2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double s = n2 > 0.0 ? sqrt(l2 / n2) : 0.0;
+    for (int a = 0; a < 3; ++a) t[a] *= s;
+  }
+}
+
+/* Sec. 5.1, Eq. constraint_gradient: the part of a row's gradient that
+   comes through the joint frame.  The frame is attached to body alpha
+   (Eq. r_gradient: R_J = dR R^T with dR constant), so a row
+   c = e^T R_J d = n . d (n the row's world direction, d the world gap of its
+   point pair) changes by e^T dR_J d with dR_J = -R_J [omega]x, omega the
+   world rotation rate of alpha's polar factor: from A = R P,
+   R^T dA - dA^T R = Omega P + P Omega with Omega = R^T dR = [w]x, which is
+   [(tr(P) I - P) w]x, and omega = R w.  The row gains omega . (n x d) for
+   each of the nine A-entries of q_alpha (entry 3c + a: dA = e_a e_c^T). */
+static void full_row_term(const double A[9], const double R[9], const double n[3],
+                          const double d[3], double g[12]) {
+  double P[9], Ms[9], Mi[9];
+  mtm3(R, A, P);
+  const double tr = P[0] + P[4] + P[8];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      Ms[3 * r + c] = (r == c ? tr : 0.0) - 0.5 * (P[3 * r + c] + P[3 * c + r]);
+  inv3(Ms, Mi);
+  const double m[3] = {n[1] * d[2] - n[2] * d[1], n[2] * d[0] - n[0] * d[2],
+                       n[0] * d[1] - n[1] * d[0]};
+  for (int c = 0; c < 3; ++c)
+    for (int a = 0; a < 3; ++a) {
+      double X[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int r = 0; r < 3; ++r) X[3 * r + c] = R[3 * a + r]; /* (R^T e_a) e_c^T */
+      double W[9];
+      for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) W[3 * r + s] = X[3 * r + s] - X[3 * s + r];
+      const double ax[3] = {W[7], W[2], W[3]}; /* W = [ax]x */
+      double w[3], om[3];
+      mv3(Mi, ax, w);
+      mv3(R, w, om);
+      g[3 * c + a] += om[0] * m[0] + om[1] * m[1] + om[2] * m[2];
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* joints: Eq. ball, Eq. hinge, frozen-frame Jacobian Eq. pcpq          */
 /* ------------------------------------------------------------------ */
@@ -307,6 +374,9 @@ int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
   }
   const double *qa = q + 12 * ja;
   double wb1 = 1.0; /* homogeneous weight of beta's second point (0: a difference vector) */
+  /* jacobian_mode 1: alpha's A and R and the world gaps of the point pairs */
+  double fA[9], fR[9], fd[3][3];
+  int full = 0;
   int arow3 = 1;    /* does row 3 act on alpha */
   if (sc->jtype[k] == 2) {
     /* Sec. 4.4 universal joint: R_U = [a1 x a2, a1, a2]^T with a1 fixed in
@@ -398,6 +468,12 @@ int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
       c[r] = tdir[r][0] * g[pt[r]][0] + tdir[r][1] * g[pt[r]][1] + tdir[r][2] * g[pt[r]][2];
       for (int a = 0; a < 3; ++a) dir[r][a] = tdir[r][a];
     }
+    if (sc->jacobian_mode == 1) {
+      full = 1;
+      memcpy(fA, A, sizeof(fA));
+      memcpy(fR, R, sizeof(fR));
+      memcpy(fd, g, sizeof(fd));
+    }
   } else if (C == 3) {
     for (int r = 0; r < 3; ++r) {
       pt[r] = 0;
@@ -434,6 +510,13 @@ int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
       pt[r] = r < 3 ? 0 : 1;
       for (int a2 = 0; a2 < 3; ++a2) dir[r][a2] = RH[3 * rsel[r] + a2];
     }
+    if (sc->jacobian_mode == 1) {
+      full = 1;
+      memcpy(fA, A, sizeof(fA));
+      memcpy(fR, R, sizeof(fR));
+      memcpy(fd[0], d1, sizeof(d1));
+      memcpy(fd[1], d2, sizeof(d2));
+    }
   }
   if (Ga) memset(Ga, 0, 60 * sizeof(double));
   if (Gb) memset(Gb, 0, 60 * sizeof(double));
@@ -451,6 +534,64 @@ int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
       if (Ga) Ga[12 * r + 9 + a] = sa * dir[r][a];
       if (Gb && jb != ORA_WORLD) Gb[12 * r + 9 + a] = sb * wb * dir[r][a];
     }
+  }
+  if (full && Ga)
+    for (int r = 0; r < C; ++r) full_row_term(fA, fR, dir[r], fd[pt[r]], Ga + 12 * r);
+  return ORA_OK;
+}
+
+int ora_joint_eval_attached(const ora_scene *sc, const double *q_ref, const double *q, int64_t k,
+                            double c[5]) {
+  const int t = sc->jtype[k];
+  if (t == 2) return ORA_ERR_ARG;
+  const int64_t ja = sc->body_a[k], jb = sc->body_b[k];
+  const double *qa = q + 12 * ja, *qb = jb == ORA_WORLD ? NULL : q + 12 * jb;
+  double pa[3][3], pb[3][3];
+  for (int i = 0; i < 3; ++i) {
+    pa[0][i] = sc->anchor_a[3 * k + i];
+    pb[0][i] = sc->anchor_b[3 * k + i];
+  }
+  if (t == 0) {
+    gap_of(qa, pa[0], qb, pb[0], c);
+    return ORA_OK;
+  }
+  /* the frame's rows at q_ref: the translation part of alpha's Jacobian rows */
+  double cr[5], Ga[60], Ar[9], Rr[9], A[9], R[9];
+  int32_t C;
+  int st = ora_joint_eval(sc, q_ref, k, cr, Ga, NULL, &C);
+  if (st) return st;
+  A_of_q(q_ref + 12 * ja, Ar);
+  st = ora_polar(Ar, Rr, NULL);
+  if (st) return st;
+  A_of_q(qa, A);
+  st = ora_polar(A, R, NULL);
+  if (st) return st;
+  /* the point pairs (as in ora_joint_eval) */
+  double ua[3], ub[3];
+  normalize3(sc->axis_a + 3 * k, ua);
+  normalize3(sc->axis_b + 3 * k, ub);
+  const double l = sc->axis_len[k];
+  for (int i = 0; i < 3; ++i) {
+    pa[1][i] = pa[0][i] + l * ua[i];
+    pb[1][i] = pb[0][i] + l * ub[i];
+  }
+  if (t == 3) {
+    double ca[3], cb[3];
+    normalize3(sc->ref_a + 3 * k, ca);
+    normalize3(sc->ref_b + 3 * k, cb);
+    for (int i = 0; i < 3; ++i) {
+      pa[2][i] = pa[0][i] + l * ca[i];
+      pb[2][i] = pb[0][i] + l * cb[i];
+    }
+  }
+  const int hpt[5] = {0, 0, 0, 1, 1}, ppt[5] = {0, 0, 1, 1, 2};
+  for (int r = 0; r < C; ++r) {
+    const int i = t == 3 ? ppt[r] : hpt[r];
+    double n0[3] = {Ga[12 * r + 9], Ga[12 * r + 10], Ga[12 * r + 11]}, t1[3], n[3], d[3];
+    mtv3(Rr, n0, t1);
+    mv3(R, t1, n);
+    gap_of(qa, pa[i], qb, pb[i], d);
+    c[r] = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
   }
   return ORA_OK;
 }
@@ -506,6 +647,9 @@ static void free_incidence(incidence *inc) {
 
 static int validate(const ora_scene *sc) {
   if (sc->M < 0 || sc->K < 0 || !(sc->h > 0.0)) return ORA_ERR_ARG;
+  if (sc->rotation_mode < 0 || sc->rotation_mode > 1 || sc->jacobian_mode < 0 ||
+      sc->jacobian_mode > 1)
+    return ORA_ERR_ARG;
   for (int64_t j = 0; j < sc->M; ++j)
     if (!(sc->mass[j] > 0.0) || !(sc->volume[j] > 0.0) || !(sc->young[j] > 0.0) ||
         !(sc->poisson[j] >= 0.0 && sc->poisson[j] < 0.5))
@@ -517,6 +661,8 @@ static int validate(const ora_scene *sc) {
     if (!is_free(sc, a) && !is_free(sc, b)) return ORA_ERR_ARG;
     /* a universal joint's fourth row lies on body beta alone */
     if (sc->jtype[k] == 2 && !is_free(sc, b)) return ORA_ERR_ARG;
+    /* the universal frame follows both bodies: no attached-frame gradient */
+    if (sc->jtype[k] == 2 && sc->jacobian_mode == 1) return ORA_ERR_ARG;
   }
   return ORA_OK;
 }
@@ -677,6 +823,23 @@ static void hinv_apply(const double *L, const double R[9], const double *x, doub
   diag4T(R, x, t);
   chol_solve(12, L, t, s);
   diag4(R, s, y);
+}
+
+/* H_A x = diag4(R) L L^T diag4(R^T) x */
+static void h_apply(const double *L, const double R[9], const double *x, double *y) {
+  double t[12], s[12];
+  diag4T(R, x, t);
+  for (int r = 0; r < 12; ++r) {
+    double v = 0.0;
+    for (int k = r; k < 12; ++k) v += L[12 * k + r] * t[k];
+    s[r] = v;
+  }
+  for (int r = 0; r < 12; ++r) {
+    double v = 0.0;
+    for (int k = 0; k <= r; ++k) v += L[12 * r + k] * s[k];
+    t[r] = v;
+  }
+  diag4(R, t, y);
 }
 
 /* W = L^{-1} diag4(R^T) g for one constraint row g (12) */
@@ -1147,7 +1310,17 @@ static int setup(const ora_scene *sc, const double *q, const double *qd, body_da
     if (st) return st;
     st = ora_body_rhs(sc, j, q, qd, bd->f + 12 * j, bd->R + 9 * j);
     if (st) return st;
-    hinv_apply(bd->L + 144 * j, bd->R + 9 * j, bd->f + 12 * j, bd->u + 12 * j);
+    if (sc->rotation_mode == 1) {
+      /* u by Alg. 1; f becomes H_A u, so that the dual rhs, the tree
+         elimination and the recovery of dq, which reach u through the
+         linear H_A, all use Alg. 1's u */
+      double A[9];
+      A_of_q(q + 12 * j, A);
+      ora_alg1_solve(bd->L + 144 * j, A, bd->f + 12 * j, bd->u + 12 * j);
+      h_apply(bd->L + 144 * j, bd->R + 9 * j, bd->u + 12 * j, bd->f + 12 * j);
+    } else {
+      hinv_apply(bd->L + 144 * j, bd->R + 9 * j, bd->f + 12 * j, bd->u + 12 * j);
+    }
   }
   for (int64_t k = 0; k < K; ++k) {
     double c[5];

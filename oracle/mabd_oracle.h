@@ -40,6 +40,15 @@ typedef struct {
   const double *anchor_a, *anchor_b, *axis_a, *axis_b; /* 3K each */
   const double *axis_len;    /* K */
   const double *ref_a, *ref_b; /* 3K each: prismatic reference directions normal to the axis */
+  /* 0: every world <-> rest rotation by the polar R (Eq. polar); 1: the
+     unconstrained solve H_A^{-1} f by Alg. 1 (the per-vector length-preserving
+     map of Eq. len_preserving), the dual operator and the constraint forces
+     by R (a linear H_A^{-1} is needed there) */
+  int32_t rotation_mode;
+  /* 0: frozen-frame Jacobian (Eq. pcpq); 1: full gradient of Eq.
+     constraint_gradient, the joint frame attached to body alpha's polar
+     rotation (Eq. r_gradient); hinge and prismatic joints (universal: error) */
+  int32_t jacobian_mode;
 } ora_scene;
 
 typedef struct {
@@ -65,6 +74,15 @@ void ora_hinge_frame(const double a[3], double RH[9]);
 int ora_joint_eval(const ora_scene *sc, const double *q, int64_t k, double c[5],
                    double Ga[60], double Gb[60], int32_t *rows);
 int64_t ora_dual_rows(const ora_scene *sc);
+/* Alg. 1: one body's unconstrained solve u = H_A^{-1} f with every rotation
+   of a 3-block replaced by A (resp. A^T) rescaled to keep the block's
+   length; L = Cholesky factor of Hbar_A, A the body's affine matrix */
+void ora_alg1_solve(const double L[144], const double A[9], const double f[12], double u[12]);
+/* C_k(q) with the joint frame attached to body alpha as it is at q_ref:
+   R_J(q) = R_J(q_ref) R_alpha(q_ref) R_alpha(q)^T (Eq. r_gradient's reading
+   of R_H as a constant rotation times alpha's R^T); ball joints: C(q) */
+int ora_joint_eval_attached(const ora_scene *sc, const double *q_ref, const double *q, int64_t k,
+                            double c[5]);
 int ora_topology(const ora_scene *sc);   /* 1 chain, 2 tree/forest, 3 graph, <0 error */
 
 /* dense assembly for small systems: Hw (M*144, world-frame H_A), f (12M),
