@@ -113,6 +113,28 @@ enum { MABD_FP64 = 0, MABD_MIXED = 1, MABD_MIXED_FP32_DUAL = 2 };
    chain's factors).  FP64 form only. */
 enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_SOLVER_PCG = 3,
        MABD_SOLVER_LOOP = 4 };
+/* Step variants of the paper, FP64 form only (another precision returns
+   MABD_ERR_UNSUPPORTED from mabd_prefactor).
+   MABD_ROTATION_NORMALIZED (Sec. 3.4, Alg. 1, Eq. len_preserving): each
+     body's unconstrained solve u = H_A^{-1} f_A takes its four 3-blocks to
+     the rest frame as A^T f_k rescaled to |f_k| and back as A dp_k rescaled to
+     |dp_k| (a zero block stays zero).  That map is not linear, so the dual
+     operator G H_A^{-1} G^T and the constraint forces keep the polar R
+     (Eq. polar); the step's constraints are still met to first order.  Any
+     solver.
+   MABD_JACOBIAN_FULL (Sec. 5.1, Eq. constraint_gradient, pcpr, r_gradient):
+     the hinge and prismatic rows gain the derivative of their frame, which
+     is attached to body a (R_J = dR R_a^T): a row n . d (world direction n,
+     gap d of its point pair) adds omega . (n x d) on body a, omega the
+     rotation rate of a's polar factor, (tr(P) I - P) w = axial(R^T dA -
+     dA^T R), omega = R w, P = R^T A.  This is the exact derivative that the
+     printed R ~ A approximation stands in for.  PCG solver only (AUTO picks
+     it; CHAIN, TREE and LOOP return MABD_ERR_UNSUPPORTED); a universal joint,
+     whose frame follows both bodies, returns MABD_ERR_UNSUPPORTED.  The
+     default frozen frame (Eq. pcpq) keeps the anchor rows affine in q, so a
+     step closes them exactly; the full gradient does not. */
+enum { MABD_ROTATION_POLAR = 0, MABD_ROTATION_NORMALIZED = 1 };
+enum { MABD_JACOBIAN_FROZEN = 0, MABD_JACOBIAN_FULL = 1 };
 /* MABD_JOINT_UNIVERSAL (Sec. 4.4, 4 rows): anchor_a / anchor_b are the joint
    centre in each rest frame, axis_a the first axis a1 (fixed in body a),
    axis_b the second axis a2 (fixed in body b, perpendicular to a1 at rest),
@@ -160,6 +182,8 @@ typedef struct {
   void *(*dev_alloc)(size_t bytes, void *user); /* optional device allocator */
   void (*dev_free)(void *ptr, void *user);
   void *alloc_user;
+  int32_t rotation_mode; /* MABD_ROTATION_POLAR (default) or MABD_ROTATION_NORMALIZED */
+  int32_t jacobian_mode; /* MABD_JACOBIAN_FROZEN (default) or MABD_JACOBIAN_FULL */
 } mabd_config;
 
 typedef struct {
@@ -210,6 +234,8 @@ typedef struct {
                               levels of the segment-tiled step (tiles of seg_tile joints, then
                               of 256 rows); 0 when the level-by-level reduction runs */
   int32_t seg_tile;        /* joints per tile of the first level of that reduction */
+  int32_t rotation_mode;   /* MABD_ROTATION_* of the context */
+  int32_t jacobian_mode;   /* MABD_JACOBIAN_* of the context */
 } mabd_info;
 
 /* Fills *cfg with h = 1e-2, gravity (0,0,-9.8), FP64, AUTO, pcg_max_iters 2000,
@@ -274,7 +300,9 @@ mabd_status mabd_kernel_times(mabd_ctx *ctx, int32_t cap, const char **names, do
    All calls on a device share the array and it keeps the last call's
    contents (the call clears what must start at zero): calls that overlap on
    the GPU (two host threads, or two streams) race and give wrong results.
-     cfg: h, gravity, residual_rhs and stream are used (precision FP64).
+     cfg: h, gravity, residual_rhs and stream are used (precision FP64;
+       rotation_mode and jacobian_mode must be the defaults, else
+       UNSUPPORTED).
      bodies: device array of M descriptions (their q, qdot are the input
        state), in path order; fixed must be 0.
      joints: device array of K in [M-1, M+1] descriptions in path order:

@@ -3,14 +3,51 @@
 //   k_joint_prep (Sec. 4.2-4.3, Sec. 5.1 Eq. pcpq)  C(q_n), hinge frame, dual rhs
 //   k_backprop   (Sec. 5.2 Eq. recover-dq-explicit) dq, q, qdot
 //   k_residuals  (Table 1 |r|)  max |G dq + C(q_n)| and max |C(q_{n+1})|
+// Variants: Alg. 1 for the unconstrained solve (StepParams::rot_norm) and the
+// frame term of the full constraint gradient (DevJoints::qf non-null).
 #include "mabd_device.cuh"
 
 namespace mabd {
+
+// Alg. 1 (Sec. 3.4, Eq. len_preserving): the unconstrained solve with each
+// 3-block taken to the rest frame as A^T f_k rescaled to |f_k| and back as
+// A dp_k rescaled to |dp_k| (a zero block stays zero).  fb is the rest-frame
+// force of the polar form, so R fb_k is the world block f_k; ub receives the
+// rest-frame copy R^T u_k of the result, as the rest of the step expects.
+__device__ __forceinline__ void alg1_solve(const double A[9], const double R[9], const double fb[12],
+                                           const double h[16], double ub[12]) {
+  double ft[12], dp[12];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double f[3], t[3];
+    mv3(R, fb + 3 * k, f);
+    mtv3(A, f, t);
+    const double l2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
+    const double n2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double sc = n2 > 0.0 ? sqrt(l2 / n2) : 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ft[3 * k + a] = sc * t[a];
+  }
+  hinv_apply(h, ft, dp);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double w[3];
+    mv3(A, dp + 3 * k, w);
+    const double l2 = dp[3 * k] * dp[3 * k] + dp[3 * k + 1] * dp[3 * k + 1] + dp[3 * k + 2] * dp[3 * k + 2];
+    const double n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const double sc = n2 > 0.0 ? sqrt(l2 / n2) : 0.0;
+    w[0] *= sc; w[1] *= sc; w[2] *= sc;
+    mtv3(R, w, ub + 3 * k);
+  }
+}
 
 // One thread per body.  f = M_A qdot/h + [0; m g] - diag4(R)[V vec(P(R^T A)); 0]
 // (Eq. newton_abd rhs at x = x_n, co-rotated linear elasticity of Sec. 3.3),
 // expressed in the rest frame: fbar = diag4(R^T)(M_A qdot/h + [0; m g]) - [V vec P; 0];
 // ubar = Hbar^{-1} fbar (Eq. abd_final).
+// NORM: Alg. 1 for the unconstrained solve (its own instantiation: the
+// default keeps its register count)
+template <bool NORM>
 __global__ void __launch_bounds__(128) k_body_prep(DevBodies B, StepParams p, int *status,
                                                       unsigned long long *iters) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -68,7 +105,8 @@ __global__ void __launch_bounds__(128) k_body_prep(DevBodies B, StepParams p, in
     }
   double h[16], u[12];
   load_hinv(B, j, h);
-  hinv_apply(h, fb, u);
+  if (NORM) alg1_solve(A, R, fb, h, u);
+  else hinv_apply(h, fb, u);
 #pragma unroll
   for (int i = 0; i < 9; ++i) B.R[(size_t)i * M + j] = R[i];
 #pragma unroll
@@ -83,6 +121,33 @@ __device__ __forceinline__ void u_at(const double R[9], const double ub[12], con
 #pragma unroll
   for (int a = 0; a < 3; ++a) l[a] = ub[a] * p[0] + ub[3 + a] * p[1] + ub[6 + a] * p[2] + ub[9 + a];
   mv3(R, l, x);
+}
+
+// MABD_JACOBIAN_FULL: the frame term of each of a hinge's or prismatic
+// joint's five rows on body a (frame rows RJ[3 * sel[r] ..], world gaps
+// dv[r]).  Stores qh_r = K R_a^T (n_r x d_r) (zero when a is not free) and
+// returns in ext[r] the term's share of the dual rhs, qh_r . axial(U - U^T)
+// with U the 3x3 block of a's unconstrained rest-frame solve ua.
+__device__ __forceinline__ void full_rows(const double qa[12], const double Ra[9], const double ua[12],
+                                          const double RJ[9], const double *const dv[5], uint8_t fl,
+                                          double *qf, int K, int k, const int sel[5], double ext[5]) {
+  double KRt[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, w[3] = {0.0, 0.0, 0.0};
+  const bool af = (fl & JF_A_FREE) != 0;
+  if (af) {
+    double A[9];
+    A_from_q(qa, A);
+    full_frame_map(A, Ra, KRt);
+    skew_axial(ua, w);
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const double n[3] = {RJ[3 * sel[r]], RJ[3 * sel[r] + 1], RJ[3 * sel[r] + 2]};
+    double qh[3];
+    full_row_vec(KRt, n, dv[r], qh);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) qf[(size_t)(3 * r + i) * K + k] = qh[i];
+    ext[r] = af ? qh[0] * w[0] + qh[1] * w[1] + qh[2] * w[2] : 0.0;
+  }
 }
 
 // One thread per joint: C(q_n) (Eq. ball / hinge / universal / prismatic),
@@ -205,13 +270,18 @@ __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, St
     const double *x = RP, *z = RP + 6;
     const double *dv[5] = {d1, d1, dd[0], dd[0], dd[1]};
     const double *gv[5] = {g1, g1, gg[0], gg[0], gg[1]};
+    double ext[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (J.qf) {
+      const int sel[5] = {0, 2, 0, 2, 2};
+      full_rows(qa, Ra, ua, RP, dv, fl, J.qf, K, k, sel, ext);
+    }
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
       const double *e = (r == 0 || r == 2) ? x : z;
       const double c = e[0] * dv[r][0] + e[1] * dv[r][1] + e[2] * dv[r][2];
       const double g = e[0] * gv[r][0] + e[1] * gv[r][1] + e[2] * gv[r][2];
       J.c[(size_t)r * K + k] = c;
-      J.b[(size_t)r * K + k] = g + rr * c;
+      J.b[(size_t)r * K + k] = (g + ext[r]) + rr * c;
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) J.RH[(size_t)i * K + k] = RP[i];
@@ -250,10 +320,16 @@ __global__ void __launch_bounds__(128) k_joint_prep(DevBodies B, DevJoints J, St
   mv3(RH, g2, e2);
   const double cc[5] = {c1[0], c1[1], c1[2], c2[0], c2[2]};
   const double gg[5] = {e1[0], e1[1], e1[2], e2[0], e2[2]};
+  double ext[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (J.qf) {
+    const double *dv[5] = {d1, d1, d1, d2, d2};
+    const int sel[5] = {0, 1, 2, 0, 2};
+    full_rows(qa, Ra, ua, RH, dv, fl, J.qf, K, k, sel, ext);
+  }
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
     J.c[(size_t)r * K + k] = cc[r];
-    J.b[(size_t)r * K + k] = gg[r] + rr * cc[r];
+    J.b[(size_t)r * K + k] = (gg[r] + ext[r]) + rr * cc[r];
   }
 #pragma unroll
   for (int i = 0; i < 9; ++i) J.RH[(size_t)i * K + k] = RH[i];
@@ -343,6 +419,15 @@ __global__ void __launch_bounds__(128) k_backprop(DevBodies B, DevJoints J, DevI
         g[9 + a] += w2 * v;
       }
     }
+    if (J.qf && side == 0 && (type == 1 || (XJ && type == 3))) {
+      // MABD_JACOBIAN_FULL: the rows' frame term on body a
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        double qh[3];
+        load_qf(J.qf, K, k, r, qh);
+        add_skew_force(qh, lam[r], g);
+      }
+    }
     if ((XJ && type == 3)) {
       double f3[3];
       mtv3(R, F3, f3);
@@ -430,11 +515,30 @@ __device__ __forceinline__ void joint_residuals(const DevBodies &B, const DevJoi
         db[pt][a] = p.h * (dqb[a] * Q[pt][0] + dqb[3 + a] * Q[pt][1] + dqb[6 + a] * Q[pt][2] + wt * dqb[9 + a]);
     }
   }
+  // MABD_JACOBIAN_FULL: axial(X - X^T) of a's rest-frame displacement block
+  double wa[3] = {0.0, 0.0, 0.0};
+  const bool full = J.qf && (fl & JF_A_FREE) && (type == 1 || (XJ && type == 3));
+  if (full) {
+    double Ra[9], xr[12];
+    load_R(B.R, M, ia, Ra);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double dA[3] = {p.h * dqa[3 * c], p.h * dqa[3 * c + 1], p.h * dqa[3 * c + 2]};
+      mtv3(Ra, dA, xr + 3 * c);
+    }
+    xr[9] = xr[10] = xr[11] = 0.0;
+    skew_axial(xr, wa);
+  }
   for (int r = 0; r < C; ++r) {
     double d[3];
     row_dir(type, RH, r, d);
     const int pt = (XJ && type == 3) ? (r >> 1) : (r < 3 ? 0 : 1);
     double v = J.c[(size_t)r * K + k];
+    if (full) {
+      double qh[3];
+      load_qf(J.qf, K, k, r, qh);
+      v += qh[0] * wa[0] + qh[1] * wa[1] + qh[2] * wa[2];
+    }
     if ((XJ && type == 2) && r == 3) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) v += d[a] * db[1][a];
@@ -570,7 +674,9 @@ void launch_state_out(const DevBodies &B, const int32_t *boi, double *stage, cud
 
 void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s,
                       unsigned long long *iters) {
-  if (B.M > 0) k_body_prep<<<nblk(B.M, 128), 128, 0, s>>>(B, p, status, iters);
+  if (B.M <= 0) return;
+  if (p.rot_norm) k_body_prep<true><<<nblk(B.M, 128), 128, 0, s>>>(B, p, status, iters);
+  else k_body_prep<false><<<nblk(B.M, 128), 128, 0, s>>>(B, p, status, iters);
 }
 
 void launch_joint_prep(const DevBodies &B, const DevJoints &J, const StepParams &p, int *status,

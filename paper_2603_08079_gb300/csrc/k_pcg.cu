@@ -28,6 +28,16 @@ __device__ __forceinline__ int joint_side_rows(const DevBodies &B, const DevJoin
 #pragma unroll
   for (int r = 0; r < 5; ++r)
     if (r < C) kron_row_w(PR[r], WR[r], E[r], W[r]);
+  const int type = J.type[k];
+  if (J.qf && side == 0 && (type == 1 || (XJ && type == 3))) {
+    // MABD_JACOBIAN_FULL: the frame term of each row on body a
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      double qh[3];
+      load_qf(J.qf, J.K, k, r, qh);
+      add_skew_force(qh, 1.0, W[r]);
+    }
+  }
   return C;
 }
 
@@ -172,11 +182,19 @@ __global__ void __launch_bounds__(128) k_pcg_body(DevBodies B, DevJoints J, DevI
   for (int e = I.off[j]; e < I.off[j + 1]; ++e) {
     const int k = I.joint[e];
     double E[5][3], PR[5][3], WR[5];
-    const int C = joint_rows_pt<double, XJ>(J, k, I.side[e], R, E, PR, WR);
+    const int side = I.side[e];
+    const int C = joint_rows_pt<double, XJ>(J, k, side, R, E, PR, WR);
+    const int type = J.type[k];
+    const bool full = J.qf && side == 0 && (type == 1 || (XJ && type == 3));
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
       if (r >= C) break;
       const double pr = P.z[(size_t)r * K + k] + beta * P.p[(size_t)r * K + k];
+      if (full) {  // MABD_JACOBIAN_FULL: the frame term on body a
+        double qh[3];
+        load_qf(J.qf, K, k, r, qh);
+        add_skew_force(qh, pr, g);
+      }
       const double *pp = PR[r];
       const double w = WR[r];
 #pragma unroll

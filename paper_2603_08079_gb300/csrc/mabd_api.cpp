@@ -642,6 +642,9 @@ mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out) {
   if (cfg->refine_steps < 0 || cfg->refine_steps > MABD_MAX_REFINE) return MABD_ERR_INVALID_ARG;
   if (cfg->solver < MABD_SOLVER_AUTO || cfg->solver > MABD_SOLVER_LOOP) return MABD_ERR_INVALID_ARG;
   if (cfg->pcg_max_iters < 1 || !(cfg->pcg_rtol > 0.0)) return MABD_ERR_INVALID_ARG;
+  if ((cfg->rotation_mode != MABD_ROTATION_POLAR && cfg->rotation_mode != MABD_ROTATION_NORMALIZED) ||
+      (cfg->jacobian_mode != MABD_JACOBIAN_FROZEN && cfg->jacobian_mode != MABD_JACOBIAN_FULL))
+    return MABD_ERR_INVALID_ARG;
   if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) return MABD_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -857,6 +860,22 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     pcg_only = pcg_only || g.jtype[k] == MABD_JOINT_UNIVERSAL || g.jtype[k] == MABD_JOINT_PRISMATIC;
     has_prism = has_prism || g.jtype[k] == MABD_JOINT_PRISMATIC;
   }
+  // the paper's variants (Alg. 1, the full constraint gradient) exist in
+  // the FP64 form; the full gradient's frame term is carried by the PCG
+  // solver's kernels only, and needs a frame attached to one body
+  const bool full_grad = ctx->cfg.jacobian_mode == MABD_JACOBIAN_FULL;
+  if ((ctx->cfg.rotation_mode != MABD_ROTATION_POLAR || full_grad) && ctx->cfg.precision != MABD_FP64) {
+    std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
+                  "MABD_ROTATION_NORMALIZED and MABD_JACOBIAN_FULL exist in the FP64 form only");
+    return MABD_ERR_UNSUPPORTED;
+  }
+  if (full_grad)
+    for (int k = 0; k < K; ++k)
+      if (g.jtype[k] == MABD_JOINT_UNIVERSAL) {
+        std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
+                      "MABD_JACOBIAN_FULL: the universal joint's frame follows both bodies");
+        return MABD_ERR_UNSUPPORTED;
+      }
   const bool is_chain = K > 0 && chain_order(g, cborder, cjorder);
   const bool is_tree = K > 0 && tree_order(ctx, g, tord);
   std::vector<int32_t> rborder, rjorder;
@@ -878,6 +897,14 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     if (ctx->cfg.solver != MABD_SOLVER_AUTO) {
       std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
                     "universal and prismatic joints are solved by the PCG solver only");
+      return MABD_ERR_UNSUPPORTED;
+    }
+    solver = MABD_SOLVER_PCG;
+  }
+  if (full_grad && K > 0 && solver != MABD_SOLVER_PCG) {
+    if (ctx->cfg.solver != MABD_SOLVER_AUTO) {
+      std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
+                    "MABD_JACOBIAN_FULL is solved by the PCG solver only");
       return MABD_ERR_UNSUPPORTED;
     }
     solver = MABD_SOLVER_PCG;
@@ -1095,6 +1122,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   J.c = dnew<double>(ctx, 5 * (size_t)Kx, ok);
   J.b = dnew<double>(ctx, 5 * (size_t)Kx, ok);
   J.lambda = dnew<double>(ctx, 5 * (size_t)Kx, ok);
+  J.qf = full_grad ? dnew<double>(ctx, 15 * (size_t)Kx, ok) : nullptr;
   const bool mixed = ctx->cfg.precision != MABD_FP64;
   const bool f32dual = ctx->cfg.precision == MABD_MIXED_FP32_DUAL;
   float *dhinvf = nullptr;
@@ -1654,6 +1682,7 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
   ctx->sp.inv_h = 1.0 / h;
   for (int a = 0; a < 3; ++a) ctx->sp.g[a] = ctx->cfg.gravity[a];
   ctx->sp.residual_rhs = ctx->cfg.residual_rhs ? 1 : 0;
+  ctx->sp.rot_norm = ctx->cfg.rotation_mode == MABD_ROTATION_NORMALIZED ? 1 : 0;
   if (solver == MABD_SOLVER_TREE && K > 0) {
     mabd_status st = tune_tree(ctx);
     if (st) return st;
@@ -2348,6 +2377,8 @@ mabd_status mabd_get_info(mabd_ctx *ctx, mabd_info *info) {
   info->solver = ctx->solver;
   info->device_bytes = ctx->device_bytes;
   info->precision = ctx->cfg.precision;
+  info->rotation_mode = ctx->cfg.rotation_mode;
+  info->jacobian_mode = ctx->cfg.jacobian_mode;
   info->refine_steps = ctx->cfg.refine_steps;
   const bool cr = ctx->solver == MABD_SOLVER_CHAIN || ctx->solver == MABD_SOLVER_LOOP;
   info->cr_levels = cr ? (int32_t)ctx->levels.size() : 0;

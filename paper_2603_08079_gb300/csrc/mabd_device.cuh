@@ -418,4 +418,65 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, doub
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
+// ---- MABD_JACOBIAN_FULL (Sec. 5.1, Eq. constraint_gradient / r_gradient) ----
+// The joint frame is attached to body a (R_J = dR R_a^T), so a row n . d
+// (world direction n, world gap d of its point pair) also changes through
+// R_J: by omega . (n x d), omega = R K axial(R^T dA - dA^T R) the world
+// rotation rate of a's polar factor, K = (tr(P) I - P)^{-1}, P = R^T A
+// (A = R P gives R^T dA - dA^T R = Omega P + P Omega = [(tr(P) I - P) w]x
+// with R^T dR = Omega = [w]x).  In a's rest frame the term acting on a
+// 12-vector x is qh . axial(X - X^T), X the 3x3 block of x (x[3c + r] =
+// X(r, c)) and qh = K R^T (n x d).
+
+// KRt = K R^T for body a
+__device__ __forceinline__ void full_frame_map(const double A[9], const double R[9], double KRt[9]) {
+  double P[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P[3 * r + c] = R[r] * A[c] + R[3 + r] * A[3 + c] + R[6 + r] * A[6 + c];
+  const double tr = P[0] + P[4] + P[8];
+  // Ms = tr(P) I - sym(P) (symmetric, about 2 I near rigid states)
+  const double m00 = tr - P[0], m11 = tr - P[4], m22 = tr - P[8];
+  const double m01 = -0.5 * (P[1] + P[3]), m02 = -0.5 * (P[2] + P[6]), m12 = -0.5 * (P[5] + P[7]);
+  const double c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+  const double c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
+  const double inv = 1.0 / (m00 * c00 + m01 * c01 + m02 * c02);
+  const double K[9] = {c00 * inv, c01 * inv, c02 * inv, c01 * inv, c11 * inv, c12 * inv,
+                       c02 * inv, c12 * inv, c22 * inv};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) KRt[3 * r + c] = K[3 * r] * R[3 * c] + K[3 * r + 1] * R[3 * c + 1] + K[3 * r + 2] * R[3 * c + 2];
+}
+
+// qh = KRt (n x d)
+__device__ __forceinline__ void full_row_vec(const double KRt[9], const double n[3], const double d[3],
+                                             double qh[3]) {
+  const double m[3] = {n[1] * d[2] - n[2] * d[1], n[2] * d[0] - n[0] * d[2], n[0] * d[1] - n[1] * d[0]};
+  mv3(KRt, m, qh);
+}
+
+// axial(X - X^T) of the 3x3 block of a rest-frame 12-vector
+__device__ __forceinline__ void skew_axial(const double x[12], double w[3]) {
+  w[0] = x[5] - x[7];
+  w[1] = x[6] - x[2];
+  w[2] = x[1] - x[3];
+}
+
+// g += s * (the transpose of x -> qh . axial(X - X^T)) = s [qh]x on X
+__device__ __forceinline__ void add_skew_force(const double qh[3], double s, double g[12]) {
+  g[5] += s * qh[0];
+  g[7] -= s * qh[0];
+  g[6] += s * qh[1];
+  g[2] -= s * qh[1];
+  g[1] += s * qh[2];
+  g[3] -= s * qh[2];
+}
+
+__device__ __forceinline__ void load_qf(const double *qf, int K, int k, int r, double qh[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) qh[i] = qf[(size_t)(3 * r + i) * K + k];
+}
+
 }  // namespace mabd

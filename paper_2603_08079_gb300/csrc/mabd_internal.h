@@ -82,6 +82,9 @@ struct DevJoints {
   double *c;             // [5][K] C(q_n)
   double *b;             // [5][K] dual rhs G u + C(q_n)
   double *lambda;        // [5][K] multipliers (rows beyond C_k are zero)
+  double *qf;            // [15][K] MABD_JACOBIAN_FULL (null otherwise): per hinge / prismatic
+                         //        row r the rest-frame vector qh_r (components [3r + i]) of
+                         //        the frame's gradient term on body a (see full_frame_map)
   double *dlam;          // [5][K] mixed form: multiplier correction of a refinement sweep
   // mixed form: FP32 copies of the joint points and of the hinge frame
   const float *pa1f, *pb1f, *pa2f, *pb2f;  // [3][K]
@@ -337,6 +340,7 @@ struct StepParams {
   double h, inv_h;
   double g[3];
   int32_t residual_rhs;
+  int32_t rot_norm;  // 1: unconstrained solve by Alg. 1 (MABD_ROTATION_NORMALIZED)
 };
 
 // kernel launchers (k_body.cu)

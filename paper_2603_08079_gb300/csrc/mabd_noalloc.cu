@@ -311,6 +311,8 @@ extern "C" mabd_status mabd_chain_step_noalloc(const mabd_config *cfg, int32_t M
   if (M < 1 || M > NA_MAX_BODIES || K < 0 || K > NA_MAX_JOINTS || K < M - 1 || K > M + 1)
     return MABD_ERR_INVALID_ARG;
   if (!(cfg->h > 0.0) || cfg->precision != MABD_FP64) return MABD_ERR_INVALID_ARG;
+  if (cfg->rotation_mode != MABD_ROTATION_POLAR || cfg->jacobian_mode != MABD_JACOBIAN_FROZEN)
+    return MABD_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)cfg->stream;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {

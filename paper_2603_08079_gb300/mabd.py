@@ -19,6 +19,8 @@ from . import build as _build
 WORLD = -1
 SOLVERS = {"auto": 0, "chain": 1, "tree": 2, "pcg": 3, "loop": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_fp32_dual": 2}
+ROTATION_MODES = {"polar": 0, "normalized": 1}
+JACOBIAN_MODES = {"frozen": 0, "full": 1}
 TOPOLOGIES = {0: "none", 1: "chain", 2: "tree", 3: "graph", 4: "loop"}
 STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of device memory",
           4: "CUDA error", 5: "not positive definite", 6: "inverted body", 7: "non-finite",
@@ -40,7 +42,8 @@ class Config(C.Structure):
     _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("precision", C.c_int32),
                 ("solver", C.c_int32), ("pcg_max_iters", C.c_int32), ("pcg_rtol", C.c_double),
                 ("refine_steps", C.c_int32), ("residual_rhs", C.c_int32), ("stream", C.c_void_p),
-                ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", C.c_void_p)]
+                ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", C.c_void_p),
+                ("rotation_mode", C.c_int32), ("jacobian_mode", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -53,7 +56,8 @@ class Info(C.Structure):
     _fields_ = [("bodies", C.c_int64), ("joints", C.c_int64), ("dual_rows", C.c_int64),
                 ("topology", C.c_int32), ("solver", C.c_int32), ("device_bytes", C.c_int64),
                 ("precision", C.c_int32), ("refine_steps", C.c_int32), ("cr_levels", C.c_int32),
-                ("cr_tail_level", C.c_int32), ("seg_levels", C.c_int32), ("seg_tile", C.c_int32)]
+                ("cr_tail_level", C.c_int32), ("seg_levels", C.c_int32), ("seg_tile", C.c_int32),
+                ("rotation_mode", C.c_int32), ("jacobian_mode", C.c_int32)]
 
 
 # numpy mirrors of mabd_body_desc / mabd_joint_desc (C layout, natural alignment)
@@ -167,7 +171,8 @@ class Solver:
 
     def __init__(self, sc: dict, solver: str = "auto", residual_rhs: int = 1,
                  stream=None, allocator: str = "torch", pcg_rtol: float = 1e-13,
-                 pcg_max_iters: int = 2000, precision: str = "fp64", refine_steps: int = 1):
+                 pcg_max_iters: int = 2000, precision: str = "fp64", refine_steps: int = 1,
+                 rotation_mode: str = "polar", jacobian_mode: str = "frozen"):
         import torch
 
         if not torch.cuda.is_available():
@@ -186,6 +191,8 @@ class Solver:
         cfg.pcg_max_iters = int(pcg_max_iters)
         cfg.precision = PRECISIONS[precision]
         cfg.refine_steps = int(refine_steps)
+        cfg.rotation_mode = ROTATION_MODES[rotation_mode]
+        cfg.jacobian_mode = JACOBIAN_MODES[jacobian_mode]
         cfg.stream = C.c_void_p(self.stream.cuda_stream)
         if allocator == "torch":
             dev, strm = self.device, self.stream
@@ -256,6 +263,10 @@ class Solver:
         d["topology"] = TOPOLOGIES.get(d["topology"], d["topology"])
         d["solver"] = {v: k for k, v in SOLVERS.items()}.get(d["solver"], d["solver"])
         d["precision"] = {v: k for k, v in PRECISIONS.items()}.get(d["precision"], d["precision"])
+        d["rotation_mode"] = {v: k for k, v in ROTATION_MODES.items()}.get(d["rotation_mode"],
+                                                                            d["rotation_mode"])
+        d["jacobian_mode"] = {v: k for k, v in JACOBIAN_MODES.items()}.get(d["jacobian_mode"],
+                                                                            d["jacobian_mode"])
         return d
 
     def profile(self, enable: bool):

@@ -48,6 +48,8 @@ int main(void) {
   printf("%zu %zu %zu\n", offsetof(mabd_config, stream), offsetof(mabd_config, dev_alloc),
          offsetof(mabd_config, residual_rhs));
   printf("%zu %zu\n", offsetof(mabd_joint_desc, ref_a), offsetof(mabd_joint_desc, ref_b));
+  printf("%zu %zu %zu %zu\n", offsetof(mabd_config, rotation_mode), offsetof(mabd_config, jacobian_mode),
+         offsetof(mabd_info, rotation_mode), offsetof(mabd_info, jacobian_mode));
   return 0;
 }
 ''')
@@ -69,6 +71,8 @@ int main(void) {
     assert vals[11] == mabd.Config.residual_rhs.offset
     assert vals[12] == mabd.JOINT_DTYPE.fields["ref_a"][1]
     assert vals[13] == mabd.JOINT_DTYPE.fields["ref_b"][1]
+    assert vals[14:18] == [mabd.Config.rotation_mode.offset, mabd.Config.jacobian_mode.offset,
+                           mabd.Info.rotation_mode.offset, mabd.Info.jacobian_mode.offset]
 
 
 def test_config_defaults_and_status_strings(lib):
@@ -77,6 +81,7 @@ def test_config_defaults_and_status_strings(lib):
     lib.mabd_config_default(C.byref(cfg))
     assert cfg.h == 1e-2 and cfg.gravity[2] == -9.8 and cfg.residual_rhs == 1
     assert cfg.pcg_max_iters > 0 and cfg.pcg_rtol > 0
+    assert cfg.rotation_mode == 0 and cfg.jacobian_mode == 0  # polar R, frozen frame
     for code in range(11):
         assert lib.mabd_status_string(code).decode() != "unknown status"
 
@@ -92,6 +97,11 @@ def test_argument_validation_without_a_device(lib):
     cfg.h = 1e-2
     cfg.solver = 9
     assert lib.mabd_create(C.byref(cfg), C.byref(out)) == 1
+    cfg.solver = 0
+    for field in ("rotation_mode", "jacobian_mode"):
+        setattr(cfg, field, 2)
+        assert lib.mabd_create(C.byref(cfg), C.byref(out)) == 1
+        setattr(cfg, field, 0)
     # calls on a NULL context are rejected, not dereferenced
     assert lib.mabd_step(None, 1, None) == 1
     assert lib.mabd_prefactor(None) == 1
