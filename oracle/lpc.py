@@ -33,8 +33,10 @@ The paper prints no values for this part (the network design is this
 project's reading); the tests pin this module against the mathematics
 instead: finite differences of the loss for every parameter, the
 block-Jacobi special case (zero heads and a closed gate leave G = I, so
-M^{-1} is the inverse of the diagonal blocks), and the symmetry and
-definiteness of M^{-1}.
+M^{-1} is the inverse of the diagonal blocks), the symmetry and
+definiteness of M^{-1}, and the network's structure (outputs depend on the
+coupling blocks within four hops only; disjoint graphs are processed
+independently).
 """
 from __future__ import annotations
 

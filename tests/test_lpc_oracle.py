@@ -150,3 +150,81 @@ def test_preconditioner_is_spd_and_pcg_solves(small_system, lpc):
             rz, rz_old = r @ z, rz
             d = z + (rz / rz_old) * d
         np.testing.assert_allclose(x, np.linalg.solve(S, b), rtol=1e-9, atol=1e-9 * np.linalg.norm(x))
+
+
+def _path_graph(K, seed):
+    """A path of K joints (joint k shares body k+1 with joint k+1) with random
+    coupling blocks E_k,k+1 = B, E_k+1,k = B^T, the first joint one-sided."""
+    rng = np.random.default_rng(seed)
+    ent = [[] for _ in range(K)]
+    E = [[] for _ in range(K)]
+    for k in range(K - 1):
+        B = rng.standard_normal((3, 3)) * 0.3
+        ent[k].append((k + 1, k + 1, 1, 0))
+        E[k].append(B)
+        ent[k + 1].insert(0, (k, k + 1, 0, 1))
+        E[k + 1].insert(0, B.T.copy())
+    ones = np.zeros(K, dtype=bool)
+    ones[0] = True
+    return E, ent, ones
+
+
+def _net_params(lpc, seed):
+    p = lpc.unpack(scenes.lpc_init_params(seed).astype(np.float64))
+    rng = np.random.default_rng(seed + 100)
+    p["Wa"][:] = rng.standard_normal(p["Wa"].shape) * 0.3
+    p["Wb"][:] = rng.standard_normal(p["Wb"].shape) * 0.3
+    p["wd"][:] = rng.standard_normal(p["wd"].shape) * 0.1
+    for l in (1, 2, 3):
+        p["b%d" % l][:] = rng.standard_normal(p["b%d" % l].shape) * 0.1
+    return lpc.pack(p)
+
+
+@pytest.mark.parametrize("use_bf16", [False, True])
+def test_network_is_local(lpc, use_bf16):
+    """Three mean-aggregation layers over features of one-hop blocks: a
+    joint's state, scale and gates depend on the coupling blocks within four
+    hops only.  Changing a block six hops away leaves them bit-identical,
+    while the joints next to that block change (a global or mis-indexed
+    aggregation would break the first, a dropped one the second)."""
+    K = 24
+    E, ent, ones = _path_graph(K, seed=1)
+    theta = _net_params(lpc, 3)
+    base = lpc.forward(theta, E, ent, ones, use_bf16=use_bf16)
+    E2 = [[b.copy() for b in row] for row in E]
+    B = np.random.default_rng(9).standard_normal((3, 3))
+    E2[16][1] = B            # block (16, 17)
+    E2[17][0] = B.T.copy()   # block (17, 16)
+    pert = lpc.forward(theta, E2, ent, ones, use_bf16=use_bf16)
+    for k in range(K):
+        far = min(abs(k - 16), abs(k - 17)) >= 6
+        same = np.array_equal(base["h3"][k], pert["h3"][k]) and base["s"][k] == pert["s"][k]
+        if far:
+            assert same, k
+            for i, (n, _, _, _) in enumerate(ent[k]):
+                if n < k:
+                    assert base["alpha"][(k, i)] == pert["alpha"][(k, i)]
+        elif k in (15, 16, 17, 18):
+            assert not same, k
+
+
+def test_network_acts_per_component(lpc):
+    """Two disjoint graphs numbered one after the other give the outputs of
+    each graph alone (no message crosses between components, and the
+    lower-neighbour features keep their order)."""
+    E1, ent1, ones1 = _path_graph(7, seed=2)
+    E2, ent2, ones2 = _path_graph(11, seed=3)
+    off = len(ent1)
+    ent = ent1 + [[(n + off, j + off, s, t) for (n, j, s, t) in row] for row in ent2]
+    E = E1 + E2
+    ones = np.concatenate([ones1, ones2])
+    theta = _net_params(lpc, 4)
+    both = lpc.forward(theta, E, ent, ones, use_bf16=False)
+    a = lpc.forward(theta, E1, ent1, ones1, use_bf16=False)
+    b = lpc.forward(theta, E2, ent2, ones2, use_bf16=False)
+    np.testing.assert_allclose(both["h3"], np.vstack([a["h3"], b["h3"]]), rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(both["s"], np.concatenate([a["s"], b["s"]]), rtol=1e-13)
+    for (k, i), v in a["alpha"].items():
+        assert abs(both["alpha"][(k, i)] - v) <= 1e-13
+    for (k, i), v in b["alpha"].items():
+        assert abs(both["alpha"][(k + off, i)] - v) <= 1e-13
