@@ -22,10 +22,16 @@
  * Conventions
  *   Affine coordinates q = [vec(A); t] (12 doubles) with vec stacking the
  *   three columns of A (Eq. abd_dof): A(r,c) = q[3c+r].  A body's rest frame
- *   has its origin at the centre of mass and its axes along the principal
- *   axes, so second_moment must be diagonal (off-diagonal entries at most
- *   1e-12 of the trace; otherwise mabd_add_bodies returns
- *   MABD_ERR_UNSUPPORTED).
+ *   has its origin at the centre of mass.  The step works in the principal
+ *   frame, where second_moment is diagonal (Hbar_A then splits into small
+ *   blocks).  A body given with off-diagonal entries above 1e-12 of the
+ *   trace is kept in its principal frame Sigma = V diag(w) V^T (V a rotation
+ *   found by Jacobi rotations on the host): the library holds A V, turns the
+ *   rest-frame anchors, axes and reference directions of its joints by V^T,
+ *   and every state it takes or returns (mabd_body_desc, mabd_set_state,
+ *   mabd_get_state) stays in the caller's frame.  The step is the same
+ *   physical step: elasticity is isotropic, and the polar factor satisfies
+ *   polar(A V) = polar(A) V.
  *   Ownership: every host array passed in belongs to the caller; the library
  *   copies what it needs during the call and keeps no pointer.  All device
  *   memory belongs to the context (through dev_alloc/dev_free when given,
@@ -248,7 +254,9 @@ mabd_status mabd_create(const mabd_config *cfg, mabd_ctx **out);
 
 /* Appends n bodies (host array, copied).  *first_id (optional) receives the id
    of the first.  INVALID_ARG on non-positive mass/volume/E, nu outside
-   [0,0.5) or non-finite state; UNSUPPORTED on a non-diagonal second moment. */
+   [0,0.5), non-finite state or a second moment that is not positive
+   definite; a non-diagonal second moment is handled as the conventions
+   above say. */
 mabd_status mabd_add_bodies(mabd_ctx *ctx, int64_t n, const mabd_body_desc *d, int64_t *first_id);
 
 /* Appends n joints (host array, copied); body ids are checked at prefactor. */

@@ -634,6 +634,30 @@ __global__ void k_state_check(const double *stage, size_t n, int *flag) {
     if (!isfinite(stage[i])) atomicOr(flag, 1);
 }
 
+// bodies kept in their principal frame (non-diagonal second moment given):
+// A_lib = A_caller V on the way in, A_caller = A_lib V^T on the way out, for
+// q and qdot alike (V row-major, 9 per body in user order)
+__global__ void __launch_bounds__(128) k_stage_frames(double *stage, int M, const double *frames,
+                                                      const uint8_t *has_frame, int to_lib) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M || !has_frame[j]) return;
+  double V[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) V[i] = frames[(size_t)9 * j + i];
+  for (int part = 0; part < 2; ++part) {
+    double *x = stage + (size_t)part * 12 * M + (size_t)12 * j;
+    double t[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        t[3 * c + r] = to_lib ? x[r] * V[c] + x[3 + r] * V[3 + c] + x[6 + r] * V[6 + c]
+                              : x[r] * V[3 * c] + x[3 + r] * V[3 * c + 1] + x[6 + r] * V[3 * c + 2];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] = t[i];
+  }
+}
+
 __global__ void __launch_bounds__(128) k_state_in(const double *stage, const int32_t *boi, DevBodies B) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int M = B.M;
@@ -670,6 +694,11 @@ void launch_state_in(const double *stage, const int32_t *boi, const DevBodies &B
 
 void launch_state_out(const DevBodies &B, const int32_t *boi, double *stage, cudaStream_t s) {
   if (B.M > 0) k_state_out<<<nblk(B.M, 128), 128, 0, s>>>(B, boi, stage);
+}
+
+void launch_stage_frames(double *stage, int M, const double *frames, const uint8_t *has_frame,
+                         bool to_lib, cudaStream_t s) {
+  if (M > 0) k_stage_frames<<<nblk(M, 128), 128, 0, s>>>(stage, M, frames, has_frame, to_lib ? 1 : 0);
 }
 
 void launch_body_prep(const DevBodies &B, const StepParams &p, int *status, cudaStream_t s,

@@ -37,6 +37,14 @@ struct mabd_ctx {
   bool cuda_failed = false;
   std::vector<mabd_body_desc> bodies;
   std::vector<mabd_joint_desc> joints;
+  // bodies given with a non-diagonal second moment are kept in their
+  // principal frame: caller's rest coordinates xbar = V xhat, A_lib = A V
+  // (V row-major, 9 per body in user order; identity where has_frame is 0)
+  std::vector<double> frames;
+  std::vector<uint8_t> has_frame;
+  bool any_frame = false;
+  double *d_frames = nullptr;
+  uint8_t *d_has_frame = nullptr;
 
   // ordering
   int32_t topology = MABD_TOPO_NONE;
@@ -596,6 +604,80 @@ mabd_status ensure_stage(mabd_ctx *ctx, size_t n) {
 
 }  // namespace
 
+// Eigen-decomposition of a symmetric 3x3 matrix (second moment xx, yy, zz,
+// xy, xz, yz) by cyclic Jacobi rotations (Jacobi's method; Golub and Van
+// Loan, Matrix Computations, Sec. 8.5): S = V diag(w) V^T with V a rotation
+// (row-major, columns the principal axes, det +1).
+static bool sym3_eigen(const double S6[6], double w[3], double V[9]) {
+  double a[3][3] = {{S6[0], S6[3], S6[4]}, {S6[3], S6[1], S6[5]}, {S6[4], S6[5], S6[2]}};
+  double v[3][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+  bool done = false;
+  for (int sweep = 0; sweep < 64 && !done; ++sweep) {
+    const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= 1e-36 * dia) {
+      done = true;
+      break;
+    }
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (a[p][q] == 0.0) continue;
+        // the rotation in the (p, q) plane that zeroes a[p][q]
+        const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < 3; ++k) {
+          const double x = a[k][p], y = a[k][q];
+          a[k][p] = c * x - sn * y;
+          a[k][q] = sn * x + c * y;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const double x = a[p][k], y = a[q][k];
+          a[p][k] = c * x - sn * y;
+          a[q][k] = sn * x + c * y;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const double x = v[k][p], y = v[k][q];
+          v[k][p] = c * x - sn * y;
+          v[k][q] = sn * x + c * y;
+        }
+      }
+  }
+  if (!done) return false;
+  const double det = v[0][0] * (v[1][1] * v[2][2] - v[1][2] * v[2][1]) -
+                     v[0][1] * (v[1][0] * v[2][2] - v[1][2] * v[2][0]) +
+                     v[0][2] * (v[1][0] * v[2][1] - v[1][1] * v[2][0]);
+  if (det < 0.0)
+    for (int k = 0; k < 3; ++k) v[k][2] = -v[k][2];
+  for (int r = 0; r < 3; ++r) {
+    w[r] = a[r][r];
+    for (int c = 0; c < 3; ++c) V[3 * r + c] = v[r][c];
+  }
+  return true;
+}
+
+// the affine part of a 12-vector (A(r, c) = x[3c + r]) times V (back = false)
+// or V^T (back = true); the translation is copied
+static void frame_A(const double x[12], const double V[9], bool back, double y[12]) {
+  double t[12];
+  for (int c = 0; c < 3; ++c)
+    for (int r = 0; r < 3; ++r) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += x[3 * k + r] * (back ? V[3 * c + k] : V[3 * k + c]);
+      t[3 * c + r] = acc;
+    }
+  for (int i = 0; i < 9; ++i) y[i] = t[i];
+  for (int i = 9; i < 12; ++i) y[i] = x[i];
+}
+
+// v in the principal frame of body j: V^T v (unchanged for bodies without one)
+static void to_principal(const mabd_ctx *ctx, int64_t j, double v[3]) {
+  if (j < 0 || !ctx->has_frame[j]) return;
+  const double *V = ctx->frames.data() + 9 * j;
+  const double x[3] = {v[0], v[1], v[2]};
+  for (int c = 0; c < 3; ++c) v[c] = V[c] * x[0] + V[3 + c] * x[1] + V[6 + c] * x[2];
+}
+
 // ==========================================================================
 // C ABI
 // ==========================================================================
@@ -676,6 +758,9 @@ mabd_status mabd_add_bodies(mabd_ctx *ctx, int64_t n, const mabd_body_desc *d, i
   if (!ctx || n < 0 || (n > 0 && !d)) return MABD_ERR_INVALID_ARG;
   if (ctx->frozen) return MABD_ERR_BAD_STATE;
   if ((int64_t)ctx->bodies.size() + n > (int64_t)INT32_MAX / 16) return MABD_ERR_INVALID_ARG;
+  std::vector<mabd_body_desc> add(d, d + n);
+  std::vector<double> fr(9 * (size_t)n, 0.0);
+  std::vector<uint8_t> hf((size_t)n, 0);
   for (int64_t i = 0; i < n; ++i) {
     const auto &b = d[i];
     if (!(b.mass > 0.0) || !(b.volume > 0.0) || !(b.young > 0.0) || !(b.poisson >= 0.0) ||
@@ -686,11 +771,29 @@ mabd_status mabd_add_bodies(mabd_ctx *ctx, int64_t n, const mabd_body_desc *d, i
     for (int a = 0; a < 3; ++a)
       if (!(b.second_moment[a] > 0.0)) return MABD_ERR_INVALID_ARG;
     const double tr = b.second_moment[0] + b.second_moment[1] + b.second_moment[2];
-    for (int a = 3; a < 6; ++a)
-      if (std::fabs(b.second_moment[a]) > 1e-12 * tr) return MABD_ERR_UNSUPPORTED;
+    double *V = fr.data() + 9 * i;
+    V[0] = V[4] = V[8] = 1.0;
+    bool diag = true;
+    for (int a = 3; a < 6; ++a) diag = diag && std::fabs(b.second_moment[a]) <= 1e-12 * tr;
+    if (diag) continue;
+    // the principal frame: Sigma = V diag(w) V^T, xbar = V xhat, so the
+    // body's affine matrix in that frame is A V (rest points, axes and
+    // reference directions of its joints are turned by V^T at prefactor)
+    double w[3];
+    if (!sym3_eigen(b.second_moment, w, V) || !(w[0] > 0.0) || !(w[1] > 0.0) || !(w[2] > 0.0))
+      return MABD_ERR_INVALID_ARG;
+    auto &o = add[i];
+    for (int a = 0; a < 3; ++a) o.second_moment[a] = w[a];
+    for (int a = 3; a < 6; ++a) o.second_moment[a] = 0.0;
+    frame_A(b.q, V, false, o.q);
+    frame_A(b.qdot, V, false, o.qdot);
+    hf[i] = 1;
   }
   if (first_id) *first_id = (int64_t)ctx->bodies.size();
-  ctx->bodies.insert(ctx->bodies.end(), d, d + n);
+  ctx->bodies.insert(ctx->bodies.end(), add.begin(), add.end());
+  ctx->frames.insert(ctx->frames.end(), fr.begin(), fr.end());
+  ctx->has_frame.insert(ctx->has_frame.end(), hf.begin(), hf.end());
+  for (uint8_t f : hf) ctx->any_frame = ctx->any_frame || f;
   return MABD_OK;
 }
 
@@ -983,7 +1086,16 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     pb3.assign(3 * (size_t)K, 0.0);
   }
   for (int i = 0; i < K; ++i) {
-    const auto &d = ctx->joints[jorder[i]];
+    mabd_joint_desc dj = ctx->joints[jorder[i]];
+    if (ctx->any_frame) {
+      to_principal(ctx, dj.body_a, dj.anchor_a);
+      to_principal(ctx, dj.body_a, dj.axis_a);
+      to_principal(ctx, dj.body_a, dj.ref_a);
+      to_principal(ctx, dj.body_b, dj.anchor_b);
+      to_principal(ctx, dj.body_b, dj.axis_b);
+      to_principal(ctx, dj.body_b, dj.ref_b);
+    }
+    const auto &d = dj;
     jtype[i] = (int8_t)d.type;
     ja[i] = ctx->internal_of_body[d.body_a];
     jb[i] = d.body_b >= 0 ? ctx->internal_of_body[d.body_b] : -1;
@@ -2286,6 +2398,15 @@ static mabd_status ensure_dstage(mabd_ctx *ctx) {
   if (!ok) return MABD_ERR_OUT_OF_MEMORY;
   if (M > 0)
     CK(cudaMemcpyAsync(boi, ctx->body_of_internal.data(), (size_t)M * 4, cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->any_frame && M > 0) {
+    double *fr = dnew<double>(ctx, 9 * (size_t)M, ok);
+    uint8_t *hf = dnew<uint8_t>(ctx, (size_t)M, ok);
+    if (!ok) return MABD_ERR_OUT_OF_MEMORY;
+    CK(cudaMemcpyAsync(fr, ctx->frames.data(), 9 * (size_t)M * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(hf, ctx->has_frame.data(), (size_t)M, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->d_frames = fr;
+    ctx->d_has_frame = hf;
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->d_stage = st;
   ctx->d_boi = boi;
@@ -2308,6 +2429,7 @@ mabd_status mabd_get_state(mabd_ctx *ctx, double *q, double *qdot) {
   if (st) return st;
   cudaStream_t s = ctx->stream;
   launch_state_out(ctx->B, ctx->d_boi, ctx->d_stage, s);
+  if (ctx->d_frames) launch_stage_frames(ctx->d_stage, M, ctx->d_frames, ctx->d_has_frame, false, s);
   if (q) CK(cudaMemcpyAsync(q, ctx->d_stage, 12 * (size_t)M * 8, cudaMemcpyDeviceToHost, s));
   if (qdot) CK(cudaMemcpyAsync(qdot, ctx->d_stage + 12 * (size_t)M, 12 * (size_t)M * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -2332,6 +2454,7 @@ mabd_status mabd_set_state(mabd_ctx *ctx, const double *q, const double *qdot) {
   CK(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (bad) return MABD_ERR_INVALID_ARG;  // nothing of the device state changed
+  if (ctx->d_frames) launch_stage_frames(ctx->d_stage, M, ctx->d_frames, ctx->d_has_frame, true, s);
   launch_state_in(ctx->d_stage, ctx->d_boi, ctx->B, s);
   CK(cudaGetLastError());
   return MABD_OK;

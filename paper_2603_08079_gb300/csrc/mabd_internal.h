@@ -353,6 +353,11 @@ void launch_backprop(const DevBodies &B, const DevJoints &J, const DevIncidence 
                      const StepParams &p, int *status, cudaStream_t s);
 void launch_residuals(const DevBodies &B, const DevJoints &J, const StepParams &p,
                       unsigned long long *maxbits /*2*/, int *status, cudaStream_t s);
+// stage: q then qdot, [M][12] each in user order; the affine part of every
+// body with has_frame[j] times frames[j] (to_lib: caller -> principal frame)
+// or its transpose (principal -> caller)
+void launch_stage_frames(double *stage, int M, const double *frames, const uint8_t *has_frame,
+                         bool to_lib, cudaStream_t s);
 
 // state transfer (k_body.cu): stage = the caller's q then qdot, [M][12] each
 // in user body order; boi[internal] = user body index

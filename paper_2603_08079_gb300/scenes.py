@@ -604,6 +604,36 @@ def rotate_scene(sc: dict, Q: np.ndarray) -> dict:
     return out
 
 
+def turn_rest_frames(sc: dict, seed: int) -> dict:
+    """The same assembly described in rest frames turned off the principal
+    axes: body j's rest coordinates become xbar' = Q_j xbar for a random
+    rotation Q_j, so its second moment becomes Q_j Sigma Q_j^T (no longer
+    diagonal), its affine matrix A Q_j^T (q and qdot), and the rest-frame
+    anchors, axes and reference directions of its joints Q_j times the old
+    ones.  World points and directions are unchanged; so is the motion."""
+    out = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+    M = len(sc["mass"])
+    Q = random_rotations(np.random.default_rng(seed), M)
+    S = sc["second_moment"]
+    for j in range(M):
+        Sg = np.array([[S[j, 0], S[j, 3], S[j, 4]], [S[j, 3], S[j, 1], S[j, 5]], [S[j, 4], S[j, 5], S[j, 2]]])
+        T = Q[j] @ Sg @ Q[j].T
+        out["second_moment"][j] = [T[0, 0], T[1, 1], T[2, 2], T[0, 1], T[0, 2], T[1, 2]]
+        for key in ("q", "qdot"):
+            A = sc[key][j, 0:9].reshape(3, 3).T
+            out[key][j, 0:9] = (A @ Q[j].T).T.reshape(9)
+    for side, body in (("a", sc["body_a"]), ("b", sc["body_b"])):
+        on = body != WORLD
+        for key in ("anchor_", "axis_", "ref_"):
+            k = key + side
+            if k not in sc:
+                continue
+            v = sc[k].copy()
+            v[on] = np.einsum("kij,kj->ki", Q[body[on]], sc[k][on])
+            out[k] = v
+    return out
+
+
 def concat_scenes(parts: list[dict], spacing: float = 100.0) -> dict:
     """Disjoint union of scenes with the same h and gravity: part i is moved
     by i * spacing along x and its body and joint ids are offset."""

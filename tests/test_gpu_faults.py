@@ -106,21 +106,72 @@ def test_invalid_bodies_are_rejected_and_the_context_stays_usable(chain, field, 
         c.close()
 
 
-def test_non_diagonal_second_moment_is_unsupported(chain):
-    """The CUDA path keeps each body's rest frame on its principal axes (a
-    diagonal second moment); a rotated one is refused, not silently used."""
+def test_second_moment_must_be_positive_definite(chain):
+    """A non-diagonal second moment is accepted (the body is kept in its
+    principal frame); one with a negative principal moment is refused."""
     need_gpu()
     sc, b, j = chain
     bad = b.copy()
-    bad["second_moment"][3, 3] = 0.1 * bad["second_moment"][3, 0]
+    s0 = bad["second_moment"][3, 0]
+    bad["second_moment"][3, :] = [s0, s0, s0, 2.0 * s0, 0.0, 0.0]  # eigenvalues 3, -1, 1 (x s0)
+    turned = b.copy()
+    turned["second_moment"][3, 3] = 0.1 * turned["second_moment"][3, 0]
     c = Ctx()
     try:
-        assert c.add_bodies(bad) == UNSUPPORTED
-        assert c.add_bodies(b) == OK
+        assert c.add_bodies(bad) == INVALID_ARG
+        assert c.add_bodies(turned) == OK
         assert c.add_joints(j) == OK
         assert c.prefactor() == OK
+        assert c.step() == OK
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("case", ["tree", "chain", "graph"])
+def test_bodies_given_off_their_principal_axes(ora, case):
+    """Rest frames turned off the principal axes (non-diagonal second
+    moments, turned anchors and axes): the library keeps each body in its
+    principal frame and returns states in the caller's frame.  Parity with
+    the oracle, which takes the second moments as given, and with the same
+    scene given in principal frames."""
+    need_gpu()
+    from parity_util import assert_parity, gpu_solver, gpu_step, rel
+    if case == "tree":
+        sc0 = scenes.random_tree(200, seed=2, joint="mixed")
+    elif case == "chain":
+        sc0 = scenes.random_small("chain", 30, seed=5)
+    else:
+        sc0 = scenes.random_small("graph", 20, seed=1, univ_frac=0.3, prism_frac=0.3)
+    sc = scenes.turn_rest_frames(sc0, seed=3)
+    tr = sc["second_moment"][:, :3].sum(axis=1)
+    assert np.all(np.abs(sc["second_moment"][:, 3:]).max(axis=1) > 1e-3 * tr)
+    q, qd = scenes.perturb_state(sc, seed=4, rot=0.1, vel=0.3)
+    # the graph's dual has cond(S) = 2.5e5: the 1e-9 bound scaled beyond 1e5
+    tol = 1e-9 if case != "graph" else 3e-9
+    assert_parity(ora, sc, q, qd, tol=tol, gpu_kw={"pcg_max_iters": 20000})
+    if case != "graph":
+        assert_parity(ora, sc, q, qd, tol=1e-6, gpu_kw={"precision": "mixed_fp32_dual"})
+    # the same state in the principal frames of sc0 (A Q^T -> A)
+    Q = scenes.random_rotations(np.random.default_rng(3), len(q))
+    q0, qd0 = q.copy(), qd.copy()
+    for k in range(len(q)):
+        q0[k, :9] = (q[k, :9].reshape(3, 3).T @ Q[k]).T.reshape(9)
+        qd0[k, :9] = (qd[k, :9].reshape(3, 3).T @ Q[k]).T.reshape(9)
+    s, s0 = gpu_solver(sc, pcg_max_iters=20000), gpu_solver(sc0, pcg_max_iters=20000)
+    try:
+        _, qd1, lam, _ = gpu_step(s, q, qd)
+        _, qd01, lam0, _ = gpu_step(s0, q0, qd0)
+        s.set_state(q, qd)
+        qr, qdr = s.get_state()
+    finally:
+        s.close()
+        s0.close()
+    np.testing.assert_allclose(qr, q, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(qdr, qd, rtol=1e-13, atol=1e-13)
+    back = qd1.copy()
+    for k in range(len(q)):
+        back[k, :9] = (qd1[k, :9].reshape(3, 3).T @ Q[k]).T.reshape(9)
+    assert rel(back, qd01) < tol and rel(lam, lam0) < tol
 
 
 @pytest.mark.parametrize("case", ["a_out_of_range", "b_out_of_range", "negative", "same_body",

@@ -764,3 +764,31 @@ def test_pendulum_horizontal_release_elliptic(ora):
     w_lin = math.sqrt(9.8 * 0.5 / (5.0 / 12.0))
     T_ref = 4 * sp.ellipk(0.5) / w_lin   # scipy's ellipk takes m = kappa^2
     assert abs(T - T_ref) / T_ref < 5e-3, (T, T_ref)
+
+
+@pytest.mark.parametrize("case", ["tree", "graph"])
+def test_turned_rest_frames_are_a_change_of_coordinates(ora, case):
+    """Describing each body in a rest frame turned by Q_j (second moment
+    Q Sigma Q^T, affine matrix A Q^T, joint rest vectors Q times the old)
+    leaves the motion unchanged: the step's qdot turned back and the
+    multipliers equal those of the principal-frame scene.  Pins the oracle's
+    handling of general second moments (M_A, the rest-frame rhs, the joint
+    rows) against its principal-frame path."""
+    sc0 = (scenes.random_tree(60, seed=2, joint="mixed") if case == "tree" else
+           scenes.random_small("graph", 20, seed=1, univ_frac=0.3, prism_frac=0.3))
+    sc = scenes.turn_rest_frames(sc0, seed=3)
+    q0, qd0 = scenes.perturb_state(sc0, seed=4, rot=0.1, vel=0.3)
+    M = len(q0)
+    Q = scenes.random_rotations(np.random.default_rng(3), M)
+    q, qd = q0.copy(), qd0.copy()
+    for j in range(M):
+        q[j, :9] = (q0[j, :9].reshape(3, 3).T @ Q[j].T).T.reshape(9)
+        qd[j, :9] = (qd0[j, :9].reshape(3, 3).T @ Q[j].T).T.reshape(9)
+    a = ora.step(ora.Scene(sc0), q0, qd0)
+    b = ora.step(ora.Scene(sc), q, qd)
+    back = b[1].copy()
+    for j in range(M):
+        back[j, :9] = (b[1][j, :9].reshape(3, 3).T @ Q[j]).T.reshape(9)
+    scale = np.linalg.norm(a[1])
+    assert np.linalg.norm(back - a[1]) <= 1e-10 * scale
+    assert np.linalg.norm(b[2] - a[2]) <= 1e-10 * np.linalg.norm(a[2])
