@@ -134,9 +134,11 @@ enum { MABD_SOLVER_AUTO = 0, MABD_SOLVER_CHAIN = 1, MABD_SOLVER_TREE = 2, MABD_S
      gap d of its point pair) adds omega . (n x d) on body a, omega the
      rotation rate of a's polar factor, (tr(P) I - P) w = axial(R^T dA -
      dA^T R), omega = R w, P = R^T A.  This is the exact derivative that the
-     printed R ~ A approximation stands in for.  PCG solver only (AUTO picks
-     it; CHAIN, TREE and LOOP return MABD_ERR_UNSUPPORTED); a universal joint,
-     whose frame follows both bodies, returns MABD_ERR_UNSUPPORTED.  The
+     printed R ~ A approximation stands in for.  Tree and PCG solvers (AUTO
+     picks the tree solver for a tree or forest, else PCG; CHAIN and LOOP,
+     whose blocks come from point compliances, return MABD_ERR_UNSUPPORTED);
+     a universal joint, whose frame follows both bodies, returns
+     MABD_ERR_UNSUPPORTED.  The
      default frozen frame (Eq. pcpq) keeps the anchor rows affine in q, so a
      step closes them exactly; the full gradient does not. */
 enum { MABD_ROTATION_POLAR = 0, MABD_ROTATION_NORMALIZED = 1 };

@@ -118,6 +118,17 @@ __device__ __forceinline__ void hinv_row(int l, int ih[3], int ic[3]) {
   }
 }
 
+// MABD_JACOBIAN_FULL: lane l's entry of the frame term of row r on the
+// joint's body a, [qh_r]x on the 3x3 block: +qh_0 at 5, -qh_0 at 7, +qh_1
+// at 6, -qh_1 at 2, +qh_2 at 1, -qh_2 at 3 (out of line: the frozen-frame
+// path keeps its registers)
+__device__ __noinline__ double full_lane_term(const double *qf, int K, int k, int l, int r) {
+  const int ax = (l == 5 || l == 7) ? 0 : ((l == 2 || l == 6) ? 1 : ((l == 1 || l == 3) ? 2 : -1));
+  if (ax < 0) return 0.0;
+  const double v = __ldg(qf + (size_t)(3 * r + ax) * K + k);
+  return (l == 5 || l == 6 || l == 1) ? v : -v;
+}
+
 // Lane l's entries of the rows of joint k on the body with rotation R that
 // is its side `side` (rest frame, Sec. 5.1: s [p; 1] (x) R^T d): Rc = column
 // l % 3 of R.  Ball rows (3) are followed by two zero rows.  Returns C.
@@ -149,6 +160,11 @@ __device__ __forceinline__ int lane_rows(const DevJoints &J, int k, int side, co
   w[2] = sg * p1 * g[2];
   w[3] = sg * p2 * g[0];
   w[4] = sg * p2 * g[2];
+  if constexpr (sizeof(S) == 8) {
+    if (J.qf && side == 0)  // MABD_JACOBIAN_FULL (FP64 form only)
+#pragma unroll
+      for (int r = 0; r < 5; ++r) w[r] += full_lane_term(J.qf, K, k, l, r);
+  }
   return 5;
 }
 
@@ -418,8 +434,10 @@ __device__ __forceinline__ void up_inner(const DevBodies &B, const DevJoints &J,
 }
 
 // downward pass of body j: lambda of its parent joint (or of a root's
-// one-sided joints), dq, and the state update
-template <typename S>
+// one-sided joints), dq, and the state update.  FULL (FP64 form, set when
+// J.qf holds the full gradient's frame terms): its own instantiation, so
+// that the frozen-frame kernels keep their registers
+template <typename S, bool FULL = false>
 __device__ __noinline__ void down_one(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int j,
                                       const StepParams &p) {
   const int M = B.M, K = J.K;
@@ -455,6 +473,31 @@ __device__ __noinline__ void down_one(const DevBodies &B, const DevJoints &J, co
       for (int a = 0; a < 3; ++a)
         x[q][a] = dqp[a] * pts[q][0] + dqp[3 + a] * pts[q][1] + dqp[6 + a] * pts[q][2] + dqp[9 + a];
     const S sp = pside == 0 ? S(1) : -S(1);
+    // MABD_JACOBIAN_FULL (FP64 form only): when the parent is the joint's
+    // body a, its rows also carry the frame term qh_r . axial(X - X^T), X
+    // the 3x3 block of the parent's rest-frame displacement R_p^T dq_p
+    // MABD_JACOBIAN_FULL: when the parent is the joint's body a, its rows
+    // also carry the frame term qh_r . axial(X - X^T), X the 3x3 block of the
+    // parent's rest-frame displacement R_p^T dq_p
+    S ext[NJ];
+#pragma unroll
+    for (int r = 0; r < NJ; ++r) ext[r] = S(0);
+    if constexpr (FULL && sizeof(S) == 8) {
+      if (pside == 0 && type == 1) {
+        double Rp[9], xr[12], w[3];
+        load_R(B.R, M, par, Rp);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mtv3(Rp, dqp + 3 * c, xr + 3 * c);
+        xr[9] = xr[10] = xr[11] = 0.0;
+        skew_axial(xr, w);
+#pragma unroll
+        for (int r = 0; r < NJ; ++r) {
+          double qh[3];
+          load_qf(J.qf, K, k, r, qh);
+          ext[r] = qh[0] * w[0] + qh[1] * w[1] + qh[2] * w[2];
+        }
+      }
+    }
     S t[NJ], lam[NJ], LD[15];
 #pragma unroll
     for (int i = 0; i < 15; ++i) LD[i] = T.LD[(size_t)i * M + j];
@@ -465,7 +508,7 @@ __device__ __noinline__ void down_one(const DevBodies &B, const DevJoints &J, co
       const int rr = r < 3 ? r : (r == 3 ? 0 : 2);
       const int q = r < 3 ? 0 : 1;
       const S dx = RH[3 * rr] * x[q][0] + RH[3 * rr + 1] * x[q][1] + RH[3 * rr + 2] * x[q][2];
-      const S rhs = r < C ? T.e[(size_t)r * M + j] + sp * dx : S(0);
+      const S rhs = r < C ? T.e[(size_t)r * M + j] + sp * dx + ext[r] : S(0);
       S s = rhs;
 #pragma unroll
       for (int i = 0; i < r; ++i) s -= LD[p12(r, i)] * t[i];
@@ -576,11 +619,11 @@ __global__ void __launch_bounds__(GB) k_tree_up_root(DevBodies B, DevJoints J, D
   up_root<S>(B, J, T, j, p, status, l, gm, scr[g]);
 }
 
-template <typename S>
+template <typename S, bool FULL>
 __global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, DevTreeT<S> T, int lo, int hi,
                                                    StepParams p) {
   const int j = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < hi) down_one(B, J, T, j, p);
+  if (j < hi) down_one<S, FULL>(B, J, T, j, p);
 }
 
 // Consecutive narrow levels [la, lb) of the downward pass in one block of RB
@@ -590,12 +633,12 @@ __global__ void __launch_bounds__(128) k_tree_down(DevBodies B, DevJoints J, Dev
 // a launch per level: there a body's latency, not the launch, sets the cost.)
 constexpr int RB = 256;
 
-template <typename S>
+template <typename S, bool FULL>
 __global__ void __launch_bounds__(RB) k_tree_down_run(DevBodies B, DevJoints J, DevTreeT<S> T, int la, int lb,
                                                       StepParams p) {
   for (int d = la; d < lb; ++d) {
     const int lo = T.lv_lo[d], hi = T.lv_lo[d + 1];
-    for (int j = lo + threadIdx.x; j < hi; j += RB) down_one(B, J, T, j, p);
+    for (int j = lo + threadIdx.x; j < hi; j += RB) down_one<S, FULL>(B, J, T, j, p);
     __syncthreads();
   }
 }
@@ -622,7 +665,14 @@ __global__ void __launch_bounds__(NT) k_tree_forest(DevBodies B, DevJoints J, De
     __syncthreads();
     for (int d = 0; d < nl; ++d) {
       const int lo = F.lo[r0 + d], hi = F.lo[r0 + d + 1];
-      for (int i = lo + threadIdx.x; i < hi; i += NT) down_one(B, J, T, F.order[i], p);
+      for (int i = lo + threadIdx.x; i < hi; i += NT) {
+        if constexpr (sizeof(S) == 8) {
+          if (J.qf) down_one<S, true>(B, J, T, F.order[i], p);
+          else down_one<S, false>(B, J, T, F.order[i], p);
+        } else {
+          down_one<S, false>(B, J, T, F.order[i], p);
+        }
+      }
       __syncthreads();
     }
   }
@@ -649,13 +699,17 @@ template <typename S>
 void launch_tree_down(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int lo, int hi,
                       const StepParams &p, int * /*status*/, cudaStream_t s) {
   const int n = hi - lo;
-  if (n > 0) k_tree_down<S><<<(n + 127) / 128, 128, 0, s>>>(B, J, T, lo, hi, p);
+  if (n <= 0) return;
+  if (sizeof(S) == 8 && J.qf) k_tree_down<S, true><<<(n + 127) / 128, 128, 0, s>>>(B, J, T, lo, hi, p);
+  else k_tree_down<S, false><<<(n + 127) / 128, 128, 0, s>>>(B, J, T, lo, hi, p);
 }
 
 template <typename S>
 void launch_tree_down_run(const DevBodies &B, const DevJoints &J, const DevTreeT<S> &T, int la, int lb,
                           const StepParams &p, cudaStream_t s) {
-  if (lb > la) k_tree_down_run<S><<<1, RB, 0, s>>>(B, J, T, la, lb, p);
+  if (lb <= la) return;
+  if (sizeof(S) == 8 && J.qf) k_tree_down_run<S, true><<<1, RB, 0, s>>>(B, J, T, la, lb, p);
+  else k_tree_down_run<S, false><<<1, RB, 0, s>>>(B, J, T, la, lb, p);
 }
 
 #define MABD_TREE_INSTANTIATE(S)                                                                   \

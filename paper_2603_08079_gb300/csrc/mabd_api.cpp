@@ -964,8 +964,9 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     has_prism = has_prism || g.jtype[k] == MABD_JOINT_PRISMATIC;
   }
   // the paper's variants (Alg. 1, the full constraint gradient) exist in
-  // the FP64 form; the full gradient's frame term is carried by the PCG
-  // solver's kernels only, and needs a frame attached to one body
+  // the FP64 form; the full gradient's frame term is carried by the tree
+  // and PCG solvers' kernels (the chain and loop solvers build their blocks
+  // from point compliances), and needs a frame attached to one body
   const bool full_grad = ctx->cfg.jacobian_mode == MABD_JACOBIAN_FULL;
   if ((ctx->cfg.rotation_mode != MABD_ROTATION_POLAR || full_grad) && ctx->cfg.precision != MABD_FP64) {
     std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
@@ -1004,13 +1005,13 @@ mabd_status mabd_prefactor(mabd_ctx *ctx) {
     }
     solver = MABD_SOLVER_PCG;
   }
-  if (full_grad && K > 0 && solver != MABD_SOLVER_PCG) {
+  if (full_grad && K > 0 && solver != MABD_SOLVER_PCG && solver != MABD_SOLVER_TREE) {
     if (ctx->cfg.solver != MABD_SOLVER_AUTO) {
       std::snprintf(ctx->err_detail, sizeof(ctx->err_detail),
-                    "MABD_JACOBIAN_FULL is solved by the PCG solver only");
+                    "MABD_JACOBIAN_FULL is solved by the tree or the PCG solver");
       return MABD_ERR_UNSUPPORTED;
     }
-    solver = MABD_SOLVER_PCG;
+    solver = is_tree && !pcg_only ? MABD_SOLVER_TREE : MABD_SOLVER_PCG;
   }
   if (solver == MABD_SOLVER_CHAIN && !is_chain) return MABD_ERR_UNSUPPORTED;
   if (solver == MABD_SOLVER_TREE && !is_tree) return MABD_ERR_UNSUPPORTED;

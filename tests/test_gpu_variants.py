@@ -4,7 +4,7 @@ one step from identical states, through the C ABI:
 - MABD_ROTATION_NORMALIZED: the unconstrained solve of every body by Alg. 1
   (Sec. 3.4, Eq. len_preserving) on each solver (chain, tree, loop, PCG);
 - MABD_JACOBIAN_FULL: the frame term of Eq. constraint_gradient (Sec. 5.1,
-  frame attached to body a, Eq. r_gradient) on the PCG solver.
+  frame attached to body a, Eq. r_gradient) on the tree and PCG solvers.
 
 States carry a strain of 1e-3 (so that A is not a rotation and Alg. 1
 differs from the polar step) and joint gaps (so that the frame term is not
@@ -33,7 +33,7 @@ def dual_condition(ora, sc, q, qd, **modes):
     return float(np.linalg.cond(G @ Hinv @ G.T))
 
 
-def variant_parity(ora, sc, q, qd, modes, solver=None, tol=TOL, **gpu_kw):
+def variant_parity(ora, sc, q, qd, modes, expect=None, tol=TOL, **gpu_kw):
     """GPU step against the oracle's step of the same variant; returns the
     relative change that the variant makes to the oracle's qdot_{n+1}."""
     s = gpu_solver(sc, **modes, **gpu_kw)
@@ -41,8 +41,8 @@ def variant_parity(ora, sc, q, qd, modes, solver=None, tol=TOL, **gpu_kw):
         info = s.info()
         for key, v in modes.items():
             assert info[key] == v
-        if solver is not None:
-            assert info["solver"] == solver
+        if expect is not None:
+            assert info["solver"] == expect
         q1, qd1, lam, st = gpu_step(s, q, qd)
     finally:
         s.close()
@@ -73,7 +73,7 @@ def test_normalized_rotation_on_every_solver(ora, case):
           "loop": lambda: scenes.ring_chain(96, seed=1),
           "net": lambda: scenes.jittered_net(6, 6, 4, seed=4)}[case]()
     q, qd = scenes.perturb_state(sc, seed=5, rot=0.1, vel=0.3, strain=1e-3)
-    moved = variant_parity(ora, sc, q, qd, NORMALIZED, solver=solver)
+    moved = variant_parity(ora, sc, q, qd, NORMALIZED, expect=solver)
     assert moved > 1e-7, moved
 
 
@@ -85,7 +85,7 @@ def test_normalized_rotation_with_every_joint_type(ora):
     sc = scenes.random_small("graph", 30, seed=2, univ_frac=0.3, prism_frac=0.3)
     q, qd = scenes.perturb_state(sc, seed=3, rot=0.1, vel=0.3, strain=1e-3)
     kappa = dual_condition(ora, sc, q, qd, **NORMALIZED)
-    moved = variant_parity(ora, sc, q, qd, NORMALIZED, solver="pcg",
+    moved = variant_parity(ora, sc, q, qd, NORMALIZED, expect="pcg",
                            tol=TOL * max(1.0, kappa / 1e5), pcg_max_iters=20000)
     assert moved > 1e-7
 
@@ -106,10 +106,26 @@ def test_normalized_rotation_over_steps(ora):
     assert rel(qd1, oqd) < 1e-7 and rel(q1, oq) < 1e-9
 
 
-@pytest.mark.parametrize("case", ["hinge tree", "mixed tree", "batch", "prismatic graph",
-                                  "hinge tree normalized"])
-def test_full_gradient_on_pcg(ora, case):
-    """The frame term on hinge and prismatic rows (AUTO picks PCG)."""
+@pytest.fixture
+def tree_mode():
+    import os
+    old = os.environ.get("MABD_TREE_MODE")
+
+    def set_(v):
+        if v is None:
+            os.environ.pop("MABD_TREE_MODE", None)
+        else:
+            os.environ["MABD_TREE_MODE"] = v
+
+    yield set_
+    set_(old)
+
+
+@pytest.mark.parametrize("solver", ["tree", "pcg"])
+@pytest.mark.parametrize("case", ["hinge tree", "mixed tree", "batch", "hinge tree normalized"])
+def test_full_gradient_on_trees(ora, case, solver):
+    """The frame term on hinge rows, in the tree solver's elimination (its
+    rows, and the parent's rows in the downward pass) and in the PCG."""
     need_gpu()
     modes = dict(FULL)
     if case == "hinge tree":
@@ -118,14 +134,43 @@ def test_full_gradient_on_pcg(ora, case):
         sc = scenes.random_tree(300, seed=3, joint="mixed")
     elif case == "batch":
         sc = scenes.assemblies(12, seed=4)
-    elif case == "prismatic graph":
-        sc = scenes.random_small("graph", 30, seed=1, hinge_frac=0.0, prism_frac=0.5, gap=0.01)
     else:
         sc = scenes.random_tree(300, seed=4)
         modes.update(NORMALIZED)
     q, qd = scenes.perturb_state(sc, seed=6, rot=0.05, vel=0.3, strain=1e-3)
     kappa = dual_condition(ora, sc, q, qd, **modes)
-    moved = variant_parity(ora, sc, q, qd, modes, solver="pcg", tol=TOL * max(1.0, kappa / 1e5),
+    moved = variant_parity(ora, sc, q, qd, modes, expect=solver, tol=TOL * max(1.0, kappa / 1e5),
+                           **({"solver": "pcg", "pcg_max_iters": 20000} if solver == "pcg" else {}))
+    assert moved > 1e-6, moved
+
+
+@pytest.mark.parametrize("mode", ["levels", "forest64", "forest32"])
+def test_full_gradient_on_every_tree_path(ora, tree_mode, mode):
+    """AUTO picks the tree solver for a tree; both the level schedule and
+    the persistent kernel carry the frame term."""
+    need_gpu()
+    tree_mode(mode)
+    sc = scenes.assemblies(16, seed=5)
+    q, qd = scenes.perturb_state(sc, seed=2, rot=0.05, vel=0.3, strain=1e-3)
+    s = gpu_solver(sc, **FULL)
+    try:
+        assert s.info()["solver"] == "tree" and s.tree_schedule()["path"] == mode
+        _, qd1, lam, _ = gpu_step(s, q, qd)
+    finally:
+        s.close()
+    _, oqd1, olam, _ = ora.step(ora.Scene(sc, 1, **FULL), q, qd, "auto")
+    kappa = dual_condition(ora, sc, q, qd, **FULL)
+    tol = TOL * max(1.0, kappa / 1e5)
+    assert rel(qd1, oqd1) <= tol and rel(lam, olam) <= tol, (rel(qd1, oqd1), rel(lam, olam))
+
+
+def test_full_gradient_on_pcg_prismatic(ora):
+    """The frame term on prismatic rows (a graph: AUTO picks PCG)."""
+    need_gpu()
+    sc = scenes.random_small("graph", 30, seed=1, hinge_frac=0.0, prism_frac=0.5, gap=0.01)
+    q, qd = scenes.perturb_state(sc, seed=6, rot=0.05, vel=0.3, strain=1e-3)
+    kappa = dual_condition(ora, sc, q, qd, **FULL)
+    moved = variant_parity(ora, sc, q, qd, FULL, expect="pcg", tol=TOL * max(1.0, kappa / 1e5),
                            pcg_max_iters=20000)
     assert moved > 1e-6, moved
 
@@ -134,7 +179,8 @@ def test_variants_are_refused_where_not_built():
     need_gpu()
     from paper_2603_08079_gb300 import mabd
     tree = scenes.random_tree(30, seed=1)
-    cases = [(tree, dict(FULL, solver="tree"), "PCG"),
+    cases = [(scenes.random_small("chain", 12, seed=2), dict(FULL, solver="chain"), "PCG"),
+             (scenes.ring_chain(12, seed=1), dict(FULL, solver="loop"), "PCG"),
              (scenes.random_small("graph", 12, seed=1, univ_frac=0.5), FULL, "universal"),
              (tree, dict(NORMALIZED, precision="mixed_fp32_dual"), "FP64"),
              (scenes.chain_cubes(8), dict(FULL, precision="mixed"), "FP64")]
